@@ -1,0 +1,157 @@
+"""FP64 CPU oracle for the Kruskal-Wallis SNP x trait scan (test infrastructure).
+
+Only the tests, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline /
+reference leg may import this package.  The product path (the CUDA library and
+its binding) never imports it.  The arithmetic lives in ``krux_oracle.c``
+(plain C, FP64, one pair at a time from the definition: sort, average ranks,
+group rank sums, Eq. 2, tie correction, chi-square tail); this module compiles
+it with gcc and marshals numpy arrays.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "krux_oracle.c")
+_LIB = os.path.join(_HERE, "_build", "libkrux_oracle.so")
+_lib = None
+
+
+class _Pair(ctypes.Structure):
+    _fields_ = [("H", ctypes.c_double), ("H_alt", ctypes.c_double),
+                ("p", ctypes.c_double), ("tie", ctypes.c_double),
+                ("rank2", ctypes.c_int64 * 3), ("d", ctypes.c_int64 * 3),
+                ("n", ctypes.c_int32 * 3), ("K", ctypes.c_int32),
+                ("df", ctypes.c_int32), ("hit", ctypes.c_int32)]
+
+
+def build(force=False):
+    """Compile krux_oracle.c into _build/libkrux_oracle.so (gcc, -O2, OpenMP)."""
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+        return _LIB
+    tmp = _LIB + f".{os.getpid()}.tmp"
+    subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11",
+                           "-o", tmp, _SRC, "-lm"])
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build())
+        P = ctypes.c_void_p
+        lib.oracle_pair.argtypes = [P, P, ctypes.c_int, ctypes.c_double, ctypes.POINTER(_Pair)]
+        lib.oracle_pair.restype = ctypes.c_int
+        lib.oracle_rank_row.argtypes = [P, ctypes.c_int, P, ctypes.POINTER(ctypes.c_double)]
+        lib.oracle_rank_row.restype = ctypes.c_int32
+        lib.oracle_scan.argtypes = [P, ctypes.c_int64, P, ctypes.c_int64, ctypes.c_int,
+                                    P, ctypes.c_int64, P, ctypes.c_int64, P,
+                                    ctypes.c_double, P, P, P, P, P, P, P, P]
+        lib.oracle_scan.restype = ctypes.c_int
+        lib.oracle_perm_minp.argtypes = [P, ctypes.c_int64, P, ctypes.c_int64, ctypes.c_int,
+                                         P, ctypes.c_int64, P, ctypes.c_int64, P,
+                                         ctypes.c_int, P]
+        lib.oracle_perm_minp.restype = ctypes.c_int
+        lib.oracle_num_threads.restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def num_threads():
+    """OpenMP threads the oracle uses."""
+    return int(_load().oracle_num_threads())
+
+
+def kw_pair(x, g, pthresh=0.05):
+    """Kruskal-Wallis test of one trait against one SNP.  Returns a dict with
+    H, H_alt, p, df, K, tie, n (3), rank2 (3) = 2*rank sums, d (3) = centred
+    sums 2*S_i - N_i*(K+1), hit."""
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    g = np.ascontiguousarray(g, dtype=np.int8)
+    assert x.shape == g.shape and x.ndim == 1
+    r = _Pair()
+    rc = _load().oracle_pair(_ptr(x), _ptr(g), x.size, float(pthresh), ctypes.byref(r))
+    if rc != 0:
+        raise ValueError("genotype code outside {-1,0,1,2}")
+    return dict(H=r.H, H_alt=r.H_alt, p=r.p, df=r.df, K=r.K, tie=r.tie,
+                n=list(r.n), rank2=list(r.rank2), d=list(r.d), hit=bool(r.hit))
+
+
+def rank_row(x):
+    """(2*average rank int64 array, 0 at NaN; tie sum; K) of one row."""
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    r2 = np.empty(x.size, dtype=np.int64)
+    tie = ctypes.c_double()
+    K = _load().oracle_rank_row(_ptr(x), x.size, _ptr(r2), ctypes.byref(tie))
+    return r2, tie.value, int(K)
+
+
+def scan(expr, geno, pthresh, traits=None, snps=None, perm=None):
+    """Dense per-pair results over traits x snps (defaults: all).  Returns a dict
+    of arrays shaped (len(traits), len(snps)): H, p, df, K, hit, H_alt, and
+    d / n shaped (..., 3)."""
+    expr = np.ascontiguousarray(expr, dtype=np.float32)
+    geno = np.ascontiguousarray(geno, dtype=np.int8)
+    T, N = expr.shape
+    S, N2 = geno.shape
+    assert N == N2
+    traits = np.arange(T, dtype=np.int64) if traits is None else np.ascontiguousarray(traits, dtype=np.int64)
+    snps = np.arange(S, dtype=np.int64) if snps is None else np.ascontiguousarray(snps, dtype=np.int64)
+    nt, ns = traits.size, snps.size
+    out = dict(H=np.empty((nt, ns)), p=np.empty((nt, ns)),
+               df=np.empty((nt, ns), np.int32), d=np.empty((nt, ns, 3), np.int64),
+               n=np.empty((nt, ns, 3), np.int32), K=np.empty((nt, ns), np.int32),
+               hit=np.empty((nt, ns), np.uint8), H_alt=np.empty((nt, ns)))
+    pp = None if perm is None else np.ascontiguousarray(perm, dtype=np.int32)
+    rc = _load().oracle_scan(_ptr(expr), N, _ptr(geno), N, N, _ptr(traits), nt,
+                             _ptr(snps), ns, _ptr(pp), float(pthresh),
+                             _ptr(out["H"]), _ptr(out["p"]), _ptr(out["df"]),
+                             _ptr(out["d"]), _ptr(out["n"]), _ptr(out["K"]),
+                             _ptr(out["hit"]), _ptr(out["H_alt"]))
+    if rc != 0:
+        raise ValueError("genotype code outside {-1,0,1,2}")
+    out["hit"] = out["hit"].astype(bool)
+    return out
+
+
+def hits(expr, geno, pthresh, traits=None, snps=None):
+    """Sorted hit list (trait, snp) (global indices) with p < pthresh, and the
+    dense result dict it came from."""
+    r = scan(expr, geno, pthresh, traits, snps)
+    T, S = expr.shape[0], geno.shape[0]
+    traits = np.arange(T) if traits is None else np.asarray(traits)
+    snps = np.arange(S) if snps is None else np.asarray(snps)
+    a, b = np.nonzero(r["hit"])
+    pairs = np.stack([traits[a], snps[b]], axis=1).astype(np.int64)
+    order = np.lexsort((pairs[:, 0], pairs[:, 1]))
+    return pairs[order], r
+
+
+def perm_minp(expr, geno, perms, traits=None, snps=None):
+    """P x len(traits) minimum p over the selected SNPs, expression columns
+    permuted by each row of ``perms``."""
+    expr = np.ascontiguousarray(expr, dtype=np.float32)
+    geno = np.ascontiguousarray(geno, dtype=np.int8)
+    perms = np.ascontiguousarray(perms, dtype=np.int32)
+    T, N = expr.shape
+    S = geno.shape[0]
+    traits = np.arange(T, dtype=np.int64) if traits is None else np.ascontiguousarray(traits, dtype=np.int64)
+    snps = np.arange(S, dtype=np.int64) if snps is None else np.ascontiguousarray(snps, dtype=np.int64)
+    P = perms.shape[0]
+    out = np.empty((P, traits.size))
+    rc = _load().oracle_perm_minp(_ptr(expr), N, _ptr(geno), N, N, _ptr(traits), traits.size,
+                                  _ptr(snps), snps.size, _ptr(perms), P, _ptr(out))
+    if rc != 0:
+        raise ValueError("genotype code outside {-1,0,1,2}")
+    return out
