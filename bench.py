@@ -1,0 +1,335 @@
+"""Benchmark of the fused Kruskal-Wallis scan (one JSON line on stdout).
+
+A step is one pass of the whole hot path over the paper-scale workload
+(N=102 samples, T=20,000 traits, S=500,000 SNPs; seeded synthetic stand-in for
+the STAGE data): rank transform, genotype packing, fused tcgen05 scan with
+threshold and hit compaction, FP64 finalisation of the hit list.  Inputs are
+resident in device memory; L2 is flushed between steps (outside the timed
+events).  The plain two-pass form (library GEMM to memory, then a separate
+epilogue) is timed beside it, the end-to-end number goes through the public
+host API with pinned host buffers, and the FP64 CPU oracle is timed on a
+bounded sample of the same workload on the host cores.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fused|reference]
+
+With --impl reference only the oracle arm runs (the CPU reference program),
+on a bounded sample per step, and prints the same JSON line with
+"impl": "reference".  Under torchrun (N > 1) every rank scans its own SNP shard
+of the same size (weak scaling, no collective on the data path); rank 0
+prints the line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Kruskal-Wallis SNP-trait pairs/sec at N=102 (fused vs plain GPU); % roofline"
+WORKLOAD = ("paper-scale fused scan: N=102 samples, T=20000 traits, S=500000 SNPs; HWE genotypes "
+            "in LD blocks (MAF U[0.01,0.5]); log-normal expression with 1% x10 outliers; planted "
+            "1-SD shifts on ~1% of pairs; hits at p<1e-5")
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def oracle_sample_rate(d, target_s=12.0, seed=0):
+    """Oracle throughput (pairs/s) on a bounded sample of the workload sized for
+    about target_s seconds of CPU work."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    T, S = d["expr"].shape[0], d["geno"].shape[0]
+    probe_t = rng.choice(T, 2, replace=False)
+    probe_s = np.arange(0, S, max(1, S // 50000))
+    t0 = time.perf_counter()
+    oracle.scan(d["expr"], d["geno"], d["pthresh"], traits=probe_t, snps=probe_s)
+    rate0 = probe_t.size * probe_s.size / (time.perf_counter() - t0)
+    n_pairs = rate0 * target_s
+    nt = int(max(1, min(T, n_pairs // S)))
+    traits = rng.choice(T, nt, replace=False)
+    t0 = time.perf_counter()
+    oracle.scan(d["expr"], d["geno"], d["pthresh"], traits=traits)
+    dt = time.perf_counter() - t0
+    return nt * S / dt, dict(traits=nt, snps=S, seconds=dt, cores=oracle.num_threads())
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    import synth
+    oracle.build()
+    d = synth.config(2)
+    T, S = d["expr"].shape[0], d["geno"].shape[0]
+    # each step: the oracle on a bounded sample (4 traits x all SNPs)
+    rng = np.random.default_rng(5)
+    nt = 4
+    times = []
+    for i in range(args.warmup + args.steps):
+        traits = rng.choice(T, nt, replace=False)
+        t0 = time.perf_counter()
+        oracle.scan(d["expr"], d["geno"], d["pthresh"], traits=traits)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+    pairs = nt * S
+    v = pairs * len(times) / sum(times)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "pairs/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(times)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "T": T, "S": S, "N": d["N"], "pthresh": d["pthresh"]},
+            "cpu_baseline": {"value": v, "unit": "pairs/s", "cores": oracle.num_threads(),
+                             "kind": "oracle",
+                             "sample": f"{nt} random traits x all {S} SNPs per step (FP64 per-pair oracle)"},
+            "e2e": {"value": v, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_fused(args):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_1307_3519_gb300 import build as kbuild
+    kbuild.build()
+    import paper_1307_3519_gb300 as k
+    import synth
+
+    d = synth.config(2, seed=1309 + rank)  # this rank's SNP shard (same shape on every rank)
+    T, S, N, pth = d["T"], d["S"], d["N"], d["pthresh"]
+    cap = 50_000_000
+    kx = k.Krux(local)
+    dev = torch.device("cuda", local)
+    expr = torch.from_numpy(d["expr"]).to(dev)
+    geno = torch.from_numpy(d["geno"]).to(dev)
+    stream = torch.cuda.current_stream()
+    hits = torch.empty((cap, 4), dtype=torch.int32, device=dev)
+    H = torch.empty(cap, dtype=torch.float64, device=dev)
+    P = torch.empty(cap, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    kx.set_profiling(True)
+
+    import ctypes
+    lib = kx.lib
+    opts = kx._opts(pth, cap)
+    nh = ctypes.c_int64()
+    sptr = ctypes.c_void_p(stream.cuda_stream)
+
+    def step(scan_fn):
+        h = ctypes.c_void_p()
+        st = lib.krux_rank(kx.handle, ctypes.c_void_p(expr.data_ptr()), T, N, N, ctypes.byref(h), sptr)
+        kx._check(st, "krux_rank")
+        prof_r = kx.profile()
+        st = scan_fn(kx.handle, h, ctypes.c_void_p(geno.data_ptr()), S, N, ctypes.byref(opts),
+                     ctypes.c_void_p(hits.data_ptr()), ctypes.c_void_p(H.data_ptr()),
+                     ctypes.c_void_p(P.data_ptr()), ctypes.byref(nh), sptr)
+        kx._check(st, "scan")
+        prof_s = kx.profile()
+        lib.krux_rankset_free(kx.handle, h)
+        return prof_r, prof_s, nh.value
+
+    def timed(scan_fn, steps, warmup):
+        for _ in range(warmup):
+            step(scan_fn)
+        torch.cuda.synchronize()
+        barrier(world)
+        times, scan_ms, launches, profs = [], [], 0, []
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for _ in range(steps):
+            flush.zero_()
+            ev0.record(stream)
+            pr, ps, n = step(scan_fn)
+            ev1.record(stream)
+            ev1.synchronize()
+            times.append(ev0.elapsed_time(ev1))
+            scan_ms.append(ps["ms_scan"])
+            launches += pr["launches"] + ps["launches"]
+            profs.append((pr, ps))
+        torch.cuda.synchronize()
+        barrier(world)
+        return times, scan_ms, launches, profs, n
+
+    with ClockSampler(local) as clk:
+        times, scan_ms, launches, profs, n_hits = timed(lib.krux_scan, args.steps, args.warmup)
+    tot_ms = max_over_ranks(sum(times), world)
+    pairs = T * S
+    value = pairs * world * args.steps / (tot_ms / 1e3)
+
+    # plain two-pass form, measured beside (fewer steps)
+    psteps = max(1, min(args.steps, 3))
+    ptimes, pscan, _, pprofs, pn = timed(lib.krux_scan_plain, psteps, 1)
+    pvalue = pairs * psteps / (sum(ptimes) / 1e3)
+
+    pk, pk_kind = peaks()
+    flops = 4.0 * N * pairs  # algorithmic: two indicator columns x N samples x multiply-add
+    ms_scan = float(np.mean(scan_ms))
+    achieved = flops / (ms_scan / 1e3) / 1e12
+    peak = float(pk["bf16_tflops"])  # FP16 dense rate equals the BF16 rate (nominal ratio 1)
+    roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": None,
+            "kernel": "krux_scan_kernel", "peak_kind": f"{pk_kind} bf16 burst (fp16 = bf16 x 1.0)",
+            "ms_per_launch": ms_scan, "flops_per_launch": flops}
+
+    # end to end through the public host API (pinned host buffers, H2D + D2H inside)
+    e_h = torch.from_numpy(d["expr"]).pin_memory()
+    g_h = torch.from_numpy(d["geno"]).pin_memory()
+    esteps = max(1, min(args.steps, 5))
+    kx.set_profiling(False)
+    r = kx.scan_pinned(e_h, g_h, pth, cap)  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    d2h = 0
+    for _ in range(esteps):
+        r = kx.scan_pinned(e_h, g_h, pth, cap)
+        d2h += r["d2h_bytes"]
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": pairs * esteps / e2e_s, "unit": "pairs/s",
+           "h2d_bytes_per_step": int(e_h.numel() * 4 + g_h.numel()),
+           "d2h_bytes_per_step": int(d2h // esteps)}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        rate, info = oracle_sample_rate(d)
+        cpu = {"value": rate, "unit": "pairs/s", "cores": info["cores"], "kind": "oracle",
+               "sample": f"{info['traits']} random traits x all {info['snps']} SNPs "
+                         f"({info['seconds']:.1f} s of FP64 per-pair oracle work)"}
+
+    if rank == 0:
+        c = clk.summary()
+        line = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f16",
+                "data": "synthetic",
+                "config": {"workload": WORKLOAD, "T": T, "S": S, "N": N, "pthresh": pth,
+                           "hit_capacity": cap, "l2": "flushed (256 MB write) between steps",
+                           "parallelism": f"snp-shards x{world}"},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "clocks": c, "hits": n_hits,
+                "plain": {"value": pvalue, "unit": "pairs/s", "ms_per_step": float(np.mean(ptimes)),
+                          "steps": psteps, "fused_speedup": value / world / pvalue, "hits": pn},
+                "breakdown_ms": {k2: float(np.mean([p[1][k2] for p in profs]))
+                                 for k2 in ("ms_pack", "ms_scan", "ms_finalize")}
+                | {"ms_rank": float(np.mean([p[0]["ms_rank"] for p in profs]))}}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="fused", choices=["fused", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_fused(args)
+
+
+if __name__ == "__main__":
+    main()

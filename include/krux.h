@@ -1,0 +1,177 @@
+/*
+ * krux.h -- C ABI of the GB300 (sm_103a) Kruskal-Wallis SNP x trait scan.
+ *
+ * The library computes, for every pair of an expression trait n and a genetic
+ * marker (SNP) m, the tie-corrected Kruskal-Wallis statistic H and its
+ * chi-square p-value, and returns the pairs with p < P_c (Qi et al., "kruX:
+ * Matrix-based non-parametric eQTL discovery", arXiv:1307.3519).  Notation:
+ * T traits, S SNPs, N samples (the paper's N, M, K).
+ *
+ * Conventions shared by every entry point:
+ *  - Pointers named "device" are CUDA device pointers owned by the caller; the
+ *    library never frees them.  Pointers named "host" are ordinary host memory.
+ *  - The context owns its workspace and the rank sets it creates.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Work is enqueued on it; calls that return counts (n_hits)
+ *    synchronise that stream before returning.
+ *  - Every call returns a krux_status; nothing throws across the ABI.  After a
+ *    failure krux_last_error(ctx) holds a one-line message.  A failure leaves
+ *    the caller's output buffers unspecified.
+ *  - One context per host thread; calls on one context are not re-entrant.
+ */
+#ifndef KRUX_H
+#define KRUX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  KRUX_OK = 0,
+  KRUX_EINVAL = 1,        /* bad argument or input value (e.g. genotype code outside {-1,0,1,2}) */
+  KRUX_ENOMEM = 2,        /* device or host allocation failed */
+  KRUX_ECUDA = 3,         /* a CUDA runtime / driver call failed */
+  KRUX_EOVERFLOW = 4,     /* more hits than hit_capacity: n_hits holds the exact total */
+  KRUX_ETIMEOUT = 5,      /* a bounded device-side wait gave up; outputs are invalid */
+  KRUX_EUNSUPPORTED = 6   /* valid request this build cannot serve (e.g. no sm_103a device) */
+} krux_status;
+
+typedef struct krux_ctx krux_ctx;
+typedef struct krux_rankset krux_rankset;
+
+/* One significant pair.  d0, d1 are the exact centred rank sums
+ * D_i = 2*S_i - N_i*(K+1) of genotype groups 0 and 1 (S_i of Eq. 4; D_2 = -D_0 - D_1).
+ * The FP64 statistic and p-value of hit j are written to hit_H[j], hit_p[j]. */
+typedef struct {
+  uint32_t trait;
+  uint32_t snp;
+  int32_t d0;
+  int32_t d1;
+} krux_hit;
+
+/* Scan options (section "P-value calculation and empirical FDR correction": the
+ * threshold P_c; section "Data slicing": a slice of markers starting at a given
+ * marker). */
+typedef struct {
+  double pthresh;          /* P_c, 0 < P_c < 1: a pair is a hit iff p < P_c */
+  int64_t hit_capacity;    /* entries available in hits / hit_H / hit_p */
+  int64_t snp_begin;       /* scan SNP rows [snp_begin, snp_end) of the genotype matrix */
+  int64_t snp_end;         /* snp_end <= 0 means S */
+  double *dense_H;         /* optional device [T][snp_end-snp_begin] FP64 H of every pair, NULL = off */
+  double *dense_p;         /* optional device, same layout, FP64 p of every pair */
+  double recheck_margin;   /* relative band around the threshold decided in FP64; <= 0 -> 1e-4 */
+  int32_t flags;           /* reserved, must be 0 */
+  int32_t reserved_;
+} krux_opts;
+
+/* Per-call kernel timings (CUDA events on the call's stream) when profiling is on. */
+typedef struct {
+  float ms_rank;        /* rank transform (krux_rank) */
+  float ms_pack;        /* genotype packing */
+  float ms_scan;        /* fused tcgen05 scan kernel, or plain GEMM + epilogue */
+  float ms_finalize;    /* FP64 H / p of the hit list */
+  float ms_gemm;        /* plain form: library GEMM part of ms_scan */
+  int32_t launches;     /* kernels the last call launched */
+  int32_t scan_grid;    /* CTAs of the fused scan launch */
+  int64_t pairs;        /* SNP x trait pairs the last call tested */
+} krux_profile;
+
+/* Create a context on CUDA device `device` (must be sm_103 for the fused path).
+ * *ctx receives the handle. */
+krux_status krux_create(krux_ctx **ctx, int device);
+void krux_destroy(krux_ctx *ctx);
+const char *krux_status_string(krux_status s);
+const char *krux_last_error(const krux_ctx *ctx);
+
+/* Rank transform (section "Input data": ranks per trait row; section "Handling
+ * missing values": NaN samples are left out and get 0; section "Handling tied
+ * data": ties get the average rank and the factor sum(t^3 - t) is computed while
+ * ranking).
+ *   expr : device float32 [T][ld] row-major, NaN = missing; 1 <= N <= 512, ld >= N.
+ *   *out : receives a rank set owned by ctx (free with krux_rankset_free).
+ * Stores, per trait, the centred ranks 2*rank - (K+1), the tie sum and K. */
+krux_status krux_rank(krux_ctx *ctx, const float *expr, int T, int N, int64_t ld,
+                      krux_rankset **out, void *stream);
+void krux_rankset_free(krux_ctx *ctx, krux_rankset *rs);
+/* Copies a rank set out: centred: device int16 [T][N] (2*rank - (K+1), 0 at NaN);
+ * tie: device int64 [T] (sum of t^3 - t); K: device int32 [T].  Any may be NULL. */
+krux_status krux_rankset_export(krux_ctx *ctx, const krux_rankset *rs, int16_t *centred,
+                                int64_t *tie, int32_t *K, void *stream);
+
+/* Fused scan (Eq. 4 rank sums by tensor-core contraction, Eq. 2 statistic with
+ * the tie factor, chi-square tail, threshold, hit list).
+ *   geno : device int8 [S][ldg] row-major, codes 0/1/2, -1 = missing; any other
+ *          code -> KRUX_EINVAL.  Same sample order and N as the rank set.
+ *   hits, hit_H, hit_p : device outputs of opts->hit_capacity entries, in
+ *          unspecified order.  SNP indices are rows of geno (slice offsets included).
+ *   n_hits : host; receives the exact number of hits, also when it exceeds the
+ *          capacity (then the first hit_capacity found are stored and the call
+ *          returns KRUX_EOVERFLOW).
+ * SNPs with missing genotypes are grouped by missing-sample pattern and scanned
+ * against ranks recomputed over the samples they have (section "Handling
+ * missing values"). */
+krux_status krux_scan(krux_ctx *ctx, const krux_rankset *rs, const int8_t *geno, int64_t S,
+                      int64_t ldg, const krux_opts *opts, krux_hit *hits, double *hit_H,
+                      double *hit_p, int64_t *n_hits, void *stream);
+
+/* Plain two-pass form of the same scan, kept as the measured comparison point:
+ * a library FP16 GEMM writes the T x 2S rank-sum matrix (in SNP slices) to device
+ * memory, then a separate epilogue kernel reads it back.  Same arguments and
+ * results as krux_scan (complete genotypes only: -1 codes -> KRUX_EUNSUPPORTED). */
+krux_status krux_scan_plain(krux_ctx *ctx, const krux_rankset *rs, const int8_t *geno,
+                            int64_t S, int64_t ldg, const krux_opts *opts, krux_hit *hits,
+                            double *hit_H, double *hit_p, int64_t *n_hits, void *stream);
+
+/* Permutation null (section "P-value calculation and empirical FDR correction":
+ * the scan repeated with the columns of the expression ranks permuted).
+ *   perms : device int32 [P][N], each row a permutation of 0..N-1; sample k of
+ *           permutation q takes the expression of sample perms[q][k].
+ *   minp  : device double [P][T]: per permutation and trait, the minimum p over
+ *           the scanned SNPs.
+ * The unpermuted scan's hits are returned as in krux_scan. */
+krux_status krux_permute(krux_ctx *ctx, const krux_rankset *rs, const int8_t *geno, int64_t S,
+                         int64_t ldg, const int32_t *perms, int P, const krux_opts *opts,
+                         double *minp, krux_hit *hits, double *hit_H, double *hit_p,
+                         int64_t *n_hits, void *stream);
+
+/* One cohort of a grouped scan: its own rank set (any N <= 512), genotypes and
+ * hit outputs; n_hits is written by krux_scan_grouped. */
+typedef struct {
+  const krux_rankset *rs;
+  const int8_t *geno;     /* device int8 [S][ldg] */
+  int64_t S;
+  int64_t ldg;
+  krux_hit *hits;         /* device, hit_capacity entries */
+  double *hit_H;
+  double *hit_p;
+  int64_t hit_capacity;
+  int64_t n_hits;         /* out */
+} krux_cohort;
+
+/* Several cohorts of uneven sample counts in one persistent launch.  opts gives
+ * the threshold (its hit_capacity and slice fields are ignored).  Returns
+ * KRUX_EOVERFLOW if any cohort overflowed. */
+krux_status krux_scan_grouped(krux_ctx *ctx, krux_cohort *cohorts, int n_cohorts,
+                              const krux_opts *opts, void *stream);
+
+/* P permutations of 0..N-1 into host int32 [P][N]: permutation q is a
+ * Fisher-Yates shuffle (i = N-1 .. 1, j = x mod (i+1), swap) driven by SplitMix64
+ * started at state seed + q. */
+krux_status krux_make_perms(uint64_t seed, int P, int N, int32_t *out);
+
+/* Record per-kernel CUDA-event timings of each call (adds event overhead). */
+krux_status krux_set_profiling(krux_ctx *ctx, int enable);
+krux_status krux_get_profile(const krux_ctx *ctx, krux_profile *out);
+
+/* Test hook: device-side waits give up after `cycles` SM clock cycles (0 = the
+ * default of about two seconds). */
+krux_status krux_set_wait_limit(krux_ctx *ctx, long long cycles);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KRUX_H */

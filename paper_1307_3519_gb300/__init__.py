@@ -1,0 +1,326 @@
+"""GB300 (sm_103a) Kruskal-Wallis SNP x trait scan: Python binding of libkrux.
+
+The compute path is the CUDA library built from ``csrc/`` (C ABI in
+``include/krux.h``); this module only marshals torch tensors into raw pointers
+and back.  There is no CPU fallback: if the library is missing the import
+fails.  Function names follow the C ABI (``krux_rank``, ``krux_scan``,
+``krux_scan_plain``, ``krux_permute``, ``krux_scan_grouped``); the ``Krux``
+class wraps them with allocation of outputs, and ``Krux.scan_host`` is the
+end-to-end call from host arrays.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libkrux.so")
+
+KRUX_OK, KRUX_EINVAL, KRUX_ENOMEM, KRUX_ECUDA, KRUX_EOVERFLOW, KRUX_ETIMEOUT, KRUX_EUNSUPPORTED = range(7)
+STATUS_NAMES = ["KRUX_OK", "KRUX_EINVAL", "KRUX_ENOMEM", "KRUX_ECUDA", "KRUX_EOVERFLOW",
+                "KRUX_ETIMEOUT", "KRUX_EUNSUPPORTED"]
+
+# Every entry point declared in include/krux.h.
+EXPORTS = ["krux_create", "krux_destroy", "krux_status_string", "krux_last_error", "krux_rank",
+           "krux_rankset_free", "krux_rankset_export", "krux_scan", "krux_scan_plain",
+           "krux_permute", "krux_scan_grouped", "krux_make_perms", "krux_set_profiling",
+           "krux_get_profile", "krux_set_wait_limit"]
+
+
+class KruxError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 7 else status}: {message}")
+        self.status = status
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("pthresh", ctypes.c_double), ("hit_capacity", ctypes.c_int64),
+                ("snp_begin", ctypes.c_int64), ("snp_end", ctypes.c_int64),
+                ("dense_H", ctypes.c_void_p), ("dense_p", ctypes.c_void_p),
+                ("recheck_margin", ctypes.c_double), ("flags", ctypes.c_int32),
+                ("reserved_", ctypes.c_int32)]
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("ms_rank", ctypes.c_float), ("ms_pack", ctypes.c_float),
+                ("ms_scan", ctypes.c_float), ("ms_finalize", ctypes.c_float),
+                ("ms_gemm", ctypes.c_float), ("launches", ctypes.c_int32),
+                ("scan_grid", ctypes.c_int32), ("pairs", ctypes.c_int64)]
+
+
+class Cohort(ctypes.Structure):
+    _fields_ = [("rs", ctypes.c_void_p), ("geno", ctypes.c_void_p), ("S", ctypes.c_int64),
+                ("ldg", ctypes.c_int64), ("hits", ctypes.c_void_p), ("hit_H", ctypes.c_void_p),
+                ("hit_p", ctypes.c_void_p), ("hit_capacity", ctypes.c_int64),
+                ("n_hits", ctypes.c_int64)]
+
+
+_lib = None
+
+
+def load_library(path=LIB_PATH):
+    """Loads libkrux.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libkrux.so not built at {path}; run paper_1307_3519_gb300/build.py")
+    lib = ctypes.CDLL(path)
+    P, I, I64, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+    sig = {
+        "krux_create": ([ctypes.POINTER(P), I], I),
+        "krux_destroy": ([P], None),
+        "krux_status_string": ([I], ctypes.c_char_p),
+        "krux_last_error": ([P], ctypes.c_char_p),
+        "krux_rank": ([P, P, I, I, I64, ctypes.POINTER(P), P], I),
+        "krux_rankset_free": ([P, P], None),
+        "krux_rankset_export": ([P, P, P, P, P, P], I),
+        "krux_scan": ([P, P, P, I64, I64, ctypes.POINTER(Opts), P, P, P, ctypes.POINTER(I64), P], I),
+        "krux_scan_plain": ([P, P, P, I64, I64, ctypes.POINTER(Opts), P, P, P, ctypes.POINTER(I64), P], I),
+        "krux_permute": ([P, P, P, I64, I64, P, I, ctypes.POINTER(Opts), P, P, P, P,
+                          ctypes.POINTER(I64), P], I),
+        "krux_scan_grouped": ([P, ctypes.POINTER(Cohort), I, ctypes.POINTER(Opts), P], I),
+        "krux_make_perms": ([ctypes.c_uint64, I, I, P], I),
+        "krux_set_profiling": ([P, I], I),
+        "krux_get_profile": ([P, ctypes.POINTER(Profile)], I),
+        "krux_set_wait_limit": ([P, ctypes.c_longlong], I),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def krux_make_perms(seed, P, N):
+    """Host int32 [P, N] permutations (Fisher-Yates driven by SplitMix64)."""
+    out = np.empty((P, N), dtype=np.int32)
+    st = load_library().krux_make_perms(seed, P, N, out.ctypes.data_as(ctypes.c_void_p))
+    if st != KRUX_OK:
+        raise KruxError(st, "krux_make_perms")
+    return out
+
+
+class RankSet:
+    """A rank set owned by its context (centred ranks, tie sums, K on device)."""
+
+    def __init__(self, ctx, handle, T, N):
+        self.ctx, self.handle, self.T, self.N = ctx, handle, T, N
+
+    def free(self):
+        if self.handle:
+            load_library().krux_rankset_free(self.ctx.handle, self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            if self.ctx.handle:
+                self.free()
+        except Exception:
+            pass
+
+
+class Krux:
+    """A library context on one CUDA device."""
+
+    def __init__(self, device=0):
+        import torch
+        self.lib = load_library()
+        self.device = torch.device("cuda", device)
+        torch.cuda.init()
+        h = ctypes.c_void_p()
+        st = self.lib.krux_create(ctypes.byref(h), device)
+        if st != KRUX_OK:
+            raise KruxError(st, "krux_create failed (device must be sm_103)")
+        self.handle = h
+
+    def close(self):
+        if self.handle:
+            self.lib.krux_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st, what):
+        if st not in (KRUX_OK, KRUX_EOVERFLOW):
+            msg = self.lib.krux_last_error(self.handle)
+            raise KruxError(st, f"{what}: {msg.decode() if msg else ''}")
+        return st
+
+    # ---- thin wrappers --------------------------------------------------------
+    def set_profiling(self, on=True):
+        self._check(self.lib.krux_set_profiling(self.handle, 1 if on else 0), "set_profiling")
+
+    def profile(self):
+        p = Profile()
+        self._check(self.lib.krux_get_profile(self.handle, ctypes.byref(p)), "get_profile")
+        return {f: getattr(p, f) for f, _ in Profile._fields_}
+
+    def set_wait_limit(self, cycles):
+        self._check(self.lib.krux_set_wait_limit(self.handle, int(cycles)), "set_wait_limit")
+
+    def krux_rank(self, expr, stream=None):
+        """expr: cuda float32 [T, N] (row stride may exceed N). Returns a RankSet."""
+        import torch
+        assert expr.is_cuda and expr.dtype == torch.float32 and expr.dim() == 2 and expr.stride(1) == 1
+        T, N = expr.shape
+        h = ctypes.c_void_p()
+        st = self.lib.krux_rank(self.handle, _ptr(expr), T, N, expr.stride(0), ctypes.byref(h),
+                                _stream(stream))
+        self._check(st, "krux_rank")
+        return RankSet(self, h, T, N)
+
+    def export(self, rs, stream=None):
+        """(centred int16 [T,N], tie int64 [T], K int32 [T]) as cuda tensors."""
+        import torch
+        c = torch.empty((rs.T, rs.N), dtype=torch.int16, device=self.device)
+        tie = torch.empty(rs.T, dtype=torch.int64, device=self.device)
+        K = torch.empty(rs.T, dtype=torch.int32, device=self.device)
+        self._check(self.lib.krux_rankset_export(self.handle, rs.handle, _ptr(c), _ptr(tie), _ptr(K),
+                                                 _stream(stream)), "krux_rankset_export")
+        return c, tie, K
+
+    def _opts(self, pthresh, capacity, snp_begin=0, snp_end=0, dense=None, margin=0.0):
+        o = Opts()
+        o.pthresh = pthresh
+        o.hit_capacity = capacity
+        o.snp_begin = snp_begin
+        o.snp_end = snp_end
+        o.dense_H = dense[0].data_ptr() if dense is not None else None
+        o.dense_p = dense[1].data_ptr() if dense is not None else None
+        o.recheck_margin = margin
+        o.flags = 0
+        return o
+
+    def _scan(self, fn, rs, geno, pthresh, capacity, snp_begin, snp_end, dense, margin, stream):
+        import torch
+        assert geno.is_cuda and geno.dtype == torch.int8 and geno.dim() == 2 and geno.stride(1) == 1
+        S = geno.shape[0]
+        e = snp_end if snp_end > 0 else S
+        hits = torch.empty((max(capacity, 1), 4), dtype=torch.int32, device=self.device)
+        H = torch.empty(max(capacity, 1), dtype=torch.float64, device=self.device)
+        P = torch.empty(max(capacity, 1), dtype=torch.float64, device=self.device)
+        dn = None
+        if dense:
+            dn = (torch.empty((rs.T, e - snp_begin), dtype=torch.float64, device=self.device),
+                  torch.empty((rs.T, e - snp_begin), dtype=torch.float64, device=self.device))
+        o = self._opts(pthresh, capacity, snp_begin, snp_end, dn, margin)
+        n = ctypes.c_int64()
+        st = fn(self.handle, rs.handle, _ptr(geno), S, geno.stride(0), ctypes.byref(o), _ptr(hits),
+                _ptr(H), _ptr(P), ctypes.byref(n), _stream(stream))
+        st = self._check(st, fn.__name__)
+        k = min(n.value, capacity)
+        out = dict(n_hits=n.value, overflow=st == KRUX_EOVERFLOW, hits=hits[:k], H=H[:k], p=P[:k])
+        if dn is not None:
+            out["dense_H"], out["dense_p"] = dn
+        return out
+
+    def krux_scan(self, rs, geno, pthresh, capacity, snp_begin=0, snp_end=0, dense=False,
+                  margin=0.0, stream=None):
+        """Fused scan.  Returns dict(n_hits, overflow, hits int32 [k,4] (trait, snp,
+        d0, d1), H, p float64 [k], and dense_H / dense_p [T, S] if dense)."""
+        return self._scan(self.lib.krux_scan, rs, geno, pthresh, capacity, snp_begin, snp_end,
+                          dense, margin, stream)
+
+    def krux_scan_plain(self, rs, geno, pthresh, capacity, snp_begin=0, snp_end=0, dense=False,
+                        margin=0.0, stream=None):
+        """Plain two-pass form (library GEMM, then a separate epilogue)."""
+        return self._scan(self.lib.krux_scan_plain, rs, geno, pthresh, capacity, snp_begin,
+                          snp_end, dense, margin, stream)
+
+    def krux_permute(self, rs, geno, perms, pthresh, capacity, stream=None):
+        """Permutation null: returns dict(minp float64 [P, T], and the unpermuted hits)."""
+        import torch
+        S = geno.shape[0]
+        P_ = perms.shape[0]
+        minp = torch.empty((P_, rs.T), dtype=torch.float64, device=self.device)
+        hits = torch.empty((max(capacity, 1), 4), dtype=torch.int32, device=self.device)
+        H = torch.empty(max(capacity, 1), dtype=torch.float64, device=self.device)
+        Pv = torch.empty(max(capacity, 1), dtype=torch.float64, device=self.device)
+        o = self._opts(pthresh, capacity)
+        n = ctypes.c_int64()
+        st = self.lib.krux_permute(self.handle, rs.handle, _ptr(geno), S, geno.stride(0), _ptr(perms),
+                                   P_, ctypes.byref(o), _ptr(minp), _ptr(hits), _ptr(H), _ptr(Pv),
+                                   ctypes.byref(n), _stream(stream))
+        st = self._check(st, "krux_permute")
+        k = min(n.value, capacity)
+        return dict(minp=minp, n_hits=n.value, overflow=st == KRUX_EOVERFLOW, hits=hits[:k],
+                    H=H[:k], p=Pv[:k])
+
+    def krux_scan_grouped(self, cohorts, pthresh, stream=None):
+        """cohorts: list of dict(rs, geno, capacity).  Returns a list of result dicts."""
+        import torch
+        arr = (Cohort * len(cohorts))()
+        keep = []
+        for i, c in enumerate(cohorts):
+            cap = c["capacity"]
+            hits = torch.empty((max(cap, 1), 4), dtype=torch.int32, device=self.device)
+            H = torch.empty(max(cap, 1), dtype=torch.float64, device=self.device)
+            P = torch.empty(max(cap, 1), dtype=torch.float64, device=self.device)
+            keep.append((hits, H, P))
+            g = c["geno"]
+            arr[i].rs = c["rs"].handle
+            arr[i].geno = g.data_ptr()
+            arr[i].S = g.shape[0]
+            arr[i].ldg = g.stride(0)
+            arr[i].hits = hits.data_ptr()
+            arr[i].hit_H = H.data_ptr()
+            arr[i].hit_p = P.data_ptr()
+            arr[i].hit_capacity = cap
+        o = self._opts(pthresh, 0)
+        st = self.lib.krux_scan_grouped(self.handle, arr, len(cohorts), ctypes.byref(o), _stream(stream))
+        self._check(st, "krux_scan_grouped")
+        out = []
+        for i, c in enumerate(cohorts):
+            k = min(arr[i].n_hits, c["capacity"])
+            hits, H, P = keep[i]
+            out.append(dict(n_hits=arr[i].n_hits, overflow=arr[i].n_hits > c["capacity"],
+                            hits=hits[:k], H=H[:k], p=P[:k]))
+        return out
+
+    # ---- end to end from host arrays -------------------------------------------
+    def scan_pinned(self, expr_h, geno_h, pthresh, capacity, stream=None):
+        """End-to-end scan from pinned host tensors (float32 [T,N], int8 [S,N]):
+        host->device copies, rank, fused scan, device->host copy of the hits."""
+        e_d = expr_h.to(self.device, non_blocking=True)
+        g_d = geno_h.to(self.device, non_blocking=True)
+        rs = self.krux_rank(e_d, stream)
+        r = self.krux_scan(rs, g_d, pthresh, capacity, stream=stream)
+        k = int(r["hits"].shape[0])
+        out = dict(n_hits=r["n_hits"], hits=r["hits"].cpu().numpy(), H=r["H"].cpu().numpy(),
+                   p=r["p"].cpu().numpy(), d2h_bytes=k * (16 + 8 + 8) + 8)
+        rs.free()
+        return out
+
+    def scan_host(self, expr, geno, pthresh, capacity, stream=None):
+        """End-to-end call from host numpy arrays: pinned host->device copies, rank,
+        fused scan, and device->host copy of the hit list.  Returns numpy arrays
+        (hits [k,4] int32, H, p) and the exact hit count."""
+        import torch
+        e_h = torch.from_numpy(np.ascontiguousarray(expr, dtype=np.float32)).pin_memory()
+        g_h = torch.from_numpy(np.ascontiguousarray(geno, dtype=np.int8)).pin_memory()
+        e_d = e_h.to(self.device, non_blocking=True)
+        g_d = g_h.to(self.device, non_blocking=True)
+        rs = self.krux_rank(e_d, stream)
+        r = self.krux_scan(rs, g_d, pthresh, capacity, stream=stream)
+        out = dict(n_hits=r["n_hits"], hits=r["hits"].cpu().numpy(), H=r["H"].cpu().numpy(),
+                   p=r["p"].cpu().numpy())
+        rs.free()
+        return out

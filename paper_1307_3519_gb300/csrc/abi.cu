@@ -1,0 +1,1069 @@
+// abi.cu -- the C ABI declared in include/krux.h: contexts, rank sets, argument
+// validation, device workspace, TMA descriptors, the work schedule of the fused
+// scan and the host side of missing-genotype buckets.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+using namespace krux;
+
+namespace krux {
+cudaError_t launch_missing_scan(const int8_t *geno, int64_t ldg, int N, int64_t snp_begin,
+                                int64_t n_snps, unsigned int *n_missing, int64_t *miss_idx,
+                                uint64_t *miss_mask, unsigned int *status, cudaStream_t s);
+cudaError_t launch_pack2(const int8_t *geno, int64_t ldg, int N, int Np, const int64_t *snp_list,
+                         int64_t snp_begin, int64_t n_snps, int64_t snp_out_base, double h1,
+                         double h2, int allow_missing, __half *B, ChunkMeta *meta,
+                         uint64_t *codes, unsigned int *status, cudaStream_t s);
+cudaError_t launch_rerank_bucket(const RankDev &base, int T, int N, int Np, const int32_t *drop,
+                                 int n_drop, const RankDev &out, cudaStream_t s);
+cudaError_t launch_plain_epilogue2(const float *C, int64_t ldc, int T, int n_slots,
+                                   const ChunkMeta *meta, const float *tau, const double *cfac,
+                                   const uint16_t *nan_cnt, const uint16_t *nan_idx, int N,
+                                   const int8_t *geno, int64_t ldg, float margin, double pthresh,
+                                   float h1, float h2, krux_hit *hits, HitAux *aux,
+                                   unsigned long long *counter, int64_t capacity, double *dense_H,
+                                   double *dense_p, int64_t dense_ld, int64_t dense_snp0,
+                                   cudaStream_t s);
+cudaError_t plain_gemm(void *handle, const __half *A, int T, int Np, const __half *B, int rowsB,
+                       float *C, cudaStream_t s);
+void *plain_handle_create();
+void plain_handle_destroy(void *h);
+}  // namespace krux
+
+namespace {
+
+struct DevBuf {
+  void *p = nullptr;
+  size_t n = 0;
+  cudaError_t ensure(size_t bytes) {
+    if (bytes <= n) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+    size_t want = bytes + bytes / 8 + 256;
+    cudaError_t e = cudaMalloc(&p, want);
+    if (e != cudaSuccess) {
+      p = nullptr;
+      return e;
+    }
+    n = want;
+    return cudaSuccess;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+  template <class T>
+  T *as() const {
+    return reinterpret_cast<T *>(p);
+  }
+};
+
+constexpr int kEv = 8;
+constexpr long long kDefaultWait = 4000000000LL;  // SM cycles, about two seconds
+
+// chi-square upper-tail thresholds at p for 1 and 2 degrees of freedom:
+// P(chi2_1 > h) = erfc(sqrt(h/2)) and P(chi2_2 > h) = exp(-h/2).
+double h_df1(double p) {
+  // solve erfc(x) = p for x by bisection on a bracketing interval, then Newton
+  double lo = 0.0, hi = 40.0;
+  for (int i = 0; i < 200; ++i) {
+    const double mid = 0.5 * (lo + hi);
+    if (std::erfc(mid) > p) lo = mid; else hi = mid;
+  }
+  double x = 0.5 * (lo + hi);
+  for (int i = 0; i < 3; ++i) {
+    const double f = std::erfc(x) - p;
+    const double d = -2.0 / std::sqrt(M_PI) * std::exp(-x * x);
+    if (d == 0.0) break;
+    x -= f / d;
+  }
+  return 2.0 * x * x;
+}
+double h_df2(double p) { return -2.0 * std::log(p); }
+
+}  // namespace
+
+struct krux_rankset {
+  int T = 0, N = 0, Np = 0, rows_pad = 0, n_ttiles = 0;
+  bool has_nan = false;  // decided on the host after ranking
+  RankDev dev{};
+  void *mem = nullptr;
+  size_t bytes = 0;
+};
+
+struct krux_ctx {
+  int device = 0;
+  int sm_count = 0;
+  int cc_major = 0, cc_minor = 0;
+  std::string err;
+  bool profiling = false;
+  krux_profile prof{};
+  long long wait_limit = kDefaultWait;
+  PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  cudaEvent_t ev[kEv] = {};
+  DevBuf B, meta, codes, groups, items, status, counters, aux, cfacptr, miss_idx, miss_mask,
+      list, gemm_out, bucket_ranks, permA;
+  void *blas = nullptr;
+  std::vector<std::pair<size_t, void *>> pool;  // freed rank-set blocks, reused by size
+};
+
+namespace {
+
+krux_status fail(krux_ctx *ctx, krux_status st, const char *fmt, ...) {
+  if (ctx) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    ctx->err = buf;
+  }
+  return st;
+}
+
+#define KRUX_CUDA(ctx, call)                                                              \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return fail(ctx, e_ == cudaErrorMemoryAllocation ? KRUX_ENOMEM : KRUX_ECUDA, "%s: %s", \
+                  #call, cudaGetErrorString(e_));                                         \
+  } while (0)
+
+int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+void ev_record(krux_ctx *ctx, int i, cudaStream_t s) {
+  if (ctx->profiling) cudaEventRecord(ctx->ev[i], s);
+}
+float ev_ms(krux_ctx *ctx, int a, int b) {
+  float ms = 0.f;
+  if (ctx->profiling && cudaEventElapsedTime(&ms, ctx->ev[a], ctx->ev[b]) == cudaSuccess) return ms;
+  return 0.f;
+}
+
+krux_status encode_map(krux_ctx *ctx, CUtensorMap *map, const void *base, int Np, int64_t rows) {
+  cuuint64_t dims[2] = {(cuuint64_t)Np, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)Np * 2};
+  cuuint32_t box[2] = {(cuuint32_t)kAtomK, (cuuint32_t)kTileM};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = ctx->encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<void *>(base), dims,
+                           strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                           CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(ctx, KRUX_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return KRUX_OK;
+}
+
+// Pipeline shape for a shared-memory K width: chunks kept resident (nc) and A
+// stages (nA) that fit the 227 KB of shared memory of one CTA.
+bool pick_shape(int kpad, int &nc, int &nA) {
+  const size_t limit = 232448;
+  for (int c = 4; c >= 1; --c) {
+    for (int a = 4; a >= 2; --a) {
+      if (scan_smem_bytes(c, a, kpad) <= limit) {
+        nc = c;
+        nA = a;
+        return true;
+      }
+    }
+  }
+  return false;
+}
+
+struct GroupPlan {
+  GroupDesc d;
+  int64_t n_btiles = 0;
+  int64_t steps = 0;
+};
+
+std::vector<WorkItem> make_items(const std::vector<GroupPlan> &gp, int nc, int grid) {
+  int64_t nb = 0, maxL = 1;
+  for (auto &g : gp) {
+    nb += g.n_btiles;
+    maxL = std::max(maxL, g.steps);
+  }
+  int best_split = 1;
+  double best = 1e300;
+  for (int s = 1; s <= 16 && s <= maxL; ++s) {
+    const int64_t items = nb * s;
+    const int64_t waves = (items + grid - 1) / grid;
+    const double cost = (double)waves * ((double)maxL / s + 2.0);
+    if (cost < best * 0.999) {
+      best = cost;
+      best_split = s;
+    }
+  }
+  std::vector<WorkItem> items;
+  for (size_t gi = 0; gi < gp.size(); ++gi) {
+    const auto &g = gp[gi];
+    const int64_t L = g.steps;
+    const int s = (int)std::min<int64_t>(best_split, L);
+    for (int64_t b = 0; b < g.n_btiles; ++b)
+      for (int k = 0; k < s; ++k) {
+        WorkItem w;
+        w.group = (int32_t)gi;
+        w.btile = (int32_t)b;
+        w.step_begin = (int32_t)(L * k / s);
+        w.step_end = (int32_t)(L * (k + 1) / s);
+        if (w.step_end > w.step_begin) items.push_back(w);
+      }
+  }
+  (void)nc;
+  return items;
+}
+
+__global__ void export_kernel(const __half *A, int T, int N, int Np, int16_t *out) {
+  const int64_t total = (int64_t)T * N;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t t = i / N;
+    const int k = (int)(i % N);
+    out[i] = (int16_t)__half2int_rn(A[t * Np + k]);
+  }
+}
+
+// ranked-set allocation: one cudaMalloc carved into the RankDev arrays
+krux_status alloc_rankset(krux_ctx *ctx, krux_rankset *rs, int T, int N, bool with_lists) {
+  rs->T = T;
+  rs->N = N;
+  rs->Np = round_up(N, 16);
+  rs->rows_pad = round_up(std::max(T, 1), kTileM);
+  rs->n_ttiles = rs->rows_pad / kTileM;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off += (bytes + 255) / 256 * 256;
+    return o;
+  };
+  const size_t oA = take((size_t)rs->rows_pad * rs->Np * 2);
+  const size_t olo = with_lists ? take((size_t)T * N * 2) : 0;
+  const size_t oeq = with_lists ? take((size_t)T * N * 2) : 0;
+  const size_t otie = take((size_t)T * 8);
+  const size_t oK = take((size_t)T * 4);
+  const size_t otau = take((size_t)T * 4);
+  const size_t ocf = take((size_t)T * 8);
+  const size_t onc = take((size_t)T * 2);
+  const size_t oni = take((size_t)T * N * 2);
+  const size_t otn = take((size_t)rs->n_ttiles * 4);
+  rs->mem = nullptr;
+  for (size_t i = 0; i < ctx->pool.size(); ++i) {
+    if (ctx->pool[i].first == off) {
+      rs->mem = ctx->pool[i].second;
+      ctx->pool.erase(ctx->pool.begin() + (long)i);
+      break;
+    }
+  }
+  if (!rs->mem) KRUX_CUDA(ctx, cudaMalloc(&rs->mem, off));
+  rs->bytes = off;
+  char *b = (char *)rs->mem;
+  rs->dev.A = (__half *)(b + oA);
+  rs->dev.lo = with_lists ? (uint16_t *)(b + olo) : nullptr;
+  rs->dev.eq = with_lists ? (uint16_t *)(b + oeq) : nullptr;
+  rs->dev.tie = (int64_t *)(b + otie);
+  rs->dev.K = (int32_t *)(b + oK);
+  rs->dev.tau = (float *)(b + otau);
+  rs->dev.cfac = (double *)(b + ocf);
+  rs->dev.nan_cnt = (uint16_t *)(b + onc);
+  rs->dev.nan_idx = (uint16_t *)(b + oni);
+  rs->dev.tile_nan = (uint32_t *)(b + otn);
+  return KRUX_OK;
+}
+
+krux_status check_opts(krux_ctx *ctx, const krux_opts *o) {
+  if (!o) return fail(ctx, KRUX_EINVAL, "opts is NULL");
+  if (!(o->pthresh > 0.0 && o->pthresh < 1.0)) return fail(ctx, KRUX_EINVAL, "pthresh must be in (0,1)");
+  if (o->hit_capacity < 0) return fail(ctx, KRUX_EINVAL, "hit_capacity < 0");
+  if (o->flags != 0) return fail(ctx, KRUX_EINVAL, "flags must be 0");
+  if ((o->dense_H == nullptr) != (o->dense_p == nullptr))
+    return fail(ctx, KRUX_EINVAL, "dense_H and dense_p must both be set or both NULL");
+  return KRUX_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------
+extern "C" {
+
+const char *krux_status_string(krux_status s) {
+  switch (s) {
+    case KRUX_OK: return "ok";
+    case KRUX_EINVAL: return "invalid argument";
+    case KRUX_ENOMEM: return "out of memory";
+    case KRUX_ECUDA: return "CUDA error";
+    case KRUX_EOVERFLOW: return "hit list overflow";
+    case KRUX_ETIMEOUT: return "device wait timed out";
+    case KRUX_EUNSUPPORTED: return "unsupported";
+  }
+  return "unknown status";
+}
+
+const char *krux_last_error(const krux_ctx *ctx) { return ctx ? ctx->err.c_str() : "no context"; }
+
+krux_status krux_create(krux_ctx **out, int device) {
+  if (!out) return KRUX_EINVAL;
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return KRUX_EINVAL;
+  krux_ctx *ctx = new krux_ctx();
+  ctx->device = device;
+  if (cudaSetDevice(device) != cudaSuccess) {
+    delete ctx;
+    return KRUX_ECUDA;
+  }
+  cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
+  cudaDeviceGetAttribute(&ctx->cc_major, cudaDevAttrComputeCapabilityMajor, device);
+  cudaDeviceGetAttribute(&ctx->cc_minor, cudaDevAttrComputeCapabilityMinor, device);
+  if (!(ctx->cc_major == 10 && ctx->cc_minor == 3)) {
+    delete ctx;
+    return KRUX_EUNSUPPORTED;
+  }
+  void *fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+          cudaSuccess ||
+      fn == nullptr) {
+    delete ctx;
+    return KRUX_ECUDA;
+  }
+  ctx->encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  for (int i = 0; i < kEv; ++i) cudaEventCreate(&ctx->ev[i]);
+  *out = ctx;
+  return KRUX_OK;
+}
+
+void krux_destroy(krux_ctx *ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  DevBuf *bufs[] = {&ctx->B, &ctx->meta, &ctx->codes, &ctx->groups, &ctx->items, &ctx->status,
+                    &ctx->counters, &ctx->aux, &ctx->cfacptr, &ctx->miss_idx, &ctx->miss_mask,
+                    &ctx->list, &ctx->gemm_out, &ctx->bucket_ranks, &ctx->permA};
+  for (DevBuf *b : bufs) b->release();
+  for (auto &pb : ctx->pool) cudaFree(pb.second);
+  for (int i = 0; i < kEv; ++i)
+    if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
+  if (ctx->blas) plain_handle_destroy(ctx->blas);
+  delete ctx;
+}
+
+krux_status krux_set_profiling(krux_ctx *ctx, int enable) {
+  if (!ctx) return KRUX_EINVAL;
+  ctx->profiling = enable != 0;
+  return KRUX_OK;
+}
+
+krux_status krux_get_profile(const krux_ctx *ctx, krux_profile *out) {
+  if (!ctx || !out) return KRUX_EINVAL;
+  *out = ctx->prof;
+  return KRUX_OK;
+}
+
+krux_status krux_set_wait_limit(krux_ctx *ctx, long long cycles) {
+  if (!ctx || cycles < 0) return KRUX_EINVAL;
+  ctx->wait_limit = cycles == 0 ? kDefaultWait : cycles;
+  return KRUX_OK;
+}
+
+krux_status krux_make_perms(uint64_t seed, int P, int N, int32_t *out) {
+  if (P < 0 || N < 0 || (P > 0 && N > 0 && !out)) return KRUX_EINVAL;
+  for (int q = 0; q < P; ++q) {
+    int32_t *pm = out + (int64_t)q * N;
+    for (int k = 0; k < N; ++k) pm[k] = k;
+    uint64_t s = seed + (uint64_t)q;
+    for (int i = N - 1; i >= 1; --i) {
+      s += 0x9E3779B97F4A7C15ull;
+      uint64_t z = s;
+      z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+      z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+      z ^= z >> 31;
+      const int j = (int)(z % (uint64_t)(i + 1));
+      std::swap(pm[i], pm[j]);
+    }
+  }
+  return KRUX_OK;
+}
+
+krux_status krux_rank(krux_ctx *ctx, const float *expr, int T, int N, int64_t ld,
+                      krux_rankset **out, void *stream) {
+  if (!ctx || !out) return fail(ctx, KRUX_EINVAL, "NULL argument");
+  *out = nullptr;
+  if (T < 1 || N < 1 || N > kMaxN || ld < N || !expr)
+    return fail(ctx, KRUX_EINVAL, "krux_rank: need T >= 1, 1 <= N <= %d, ld >= N, expr != NULL", kMaxN);
+  cudaStream_t s = (cudaStream_t)stream;
+  KRUX_CUDA(ctx, cudaSetDevice(ctx->device));
+  krux_rankset *rs = new krux_rankset();
+  krux_status st = alloc_rankset(ctx, rs, T, N, true);
+  if (st != KRUX_OK) {
+    delete rs;
+    return st;
+  }
+  ev_record(ctx, 0, s);
+  cudaError_t e = cudaMemsetAsync(rs->dev.A, 0, (size_t)rs->rows_pad * rs->Np * 2, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(rs->dev.tile_nan, 0, (size_t)rs->n_ttiles * 4, s);
+  if (e == cudaSuccess) e = launch_rank(expr, T, N, ld, rs->Np, rs->rows_pad, rs->dev, s);
+  ev_record(ctx, 1, s);
+  uint32_t any_nan = 0;
+  if (e == cudaSuccess) {
+    std::vector<uint32_t> tn(rs->n_ttiles);
+    e = cudaMemcpyAsync(tn.data(), rs->dev.tile_nan, tn.size() * 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    for (uint32_t v : tn) any_nan |= v;
+  }
+  if (e != cudaSuccess) {
+    krux_rankset_free(ctx, rs);
+    return fail(ctx, KRUX_ECUDA, "krux_rank: %s", cudaGetErrorString(e));
+  }
+  rs->has_nan = any_nan != 0;
+  if (ctx->profiling) {
+    ctx->prof = krux_profile{};
+    ctx->prof.ms_rank = ev_ms(ctx, 0, 1);
+    ctx->prof.launches = 1;
+  }
+  *out = rs;
+  return KRUX_OK;
+}
+
+void krux_rankset_free(krux_ctx *ctx, krux_rankset *rs) {
+  if (!rs) return;
+  if (ctx && rs->mem) {
+    ctx->pool.emplace_back(rs->bytes, rs->mem);  // kept for the next krux_rank of this size
+  } else if (rs->mem) {
+    cudaFree(rs->mem);
+  }
+  delete rs;
+}
+
+krux_status krux_rankset_export(krux_ctx *ctx, const krux_rankset *rs, int16_t *centred,
+                                int64_t *tie, int32_t *K, void *stream) {
+  if (!ctx || !rs) return fail(ctx, KRUX_EINVAL, "NULL argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (centred) {
+    export_kernel<<<std::max(1, std::min(4096, (rs->T * rs->N + 255) / 256)), 256, 0, s>>>(
+        rs->dev.A, rs->T, rs->N, rs->Np, centred);
+    KRUX_CUDA(ctx, cudaGetLastError());
+  }
+  if (tie) KRUX_CUDA(ctx, cudaMemcpyAsync(tie, rs->dev.tie, (size_t)rs->T * 8, cudaMemcpyDeviceToDevice, s));
+  if (K) KRUX_CUDA(ctx, cudaMemcpyAsync(K, rs->dev.K, (size_t)rs->T * 4, cudaMemcpyDeviceToDevice, s));
+  return KRUX_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------------------
+// Missing genotypes (section "Handling missing values": one genotype matrix per
+// missing-value pattern, with the expression re-ranked without those samples).
+namespace {
+
+struct Bucket {
+  std::vector<int32_t> drop;   // samples removed
+  std::vector<int64_t> snps;   // SNP rows with exactly this pattern, ascending
+};
+
+// Finds SNPs of rows [b, b+n) that carry a -1, groups them by their exact
+// missing-sample set, and lists the complete rows.  `bad` reports codes outside
+// {-1,0,1,2}.  Synchronises the stream.
+krux_status find_missing(krux_ctx *ctx, const int8_t *geno, int64_t ldg, int N, int64_t b,
+                         int64_t n, cudaStream_t s, std::vector<Bucket> &buckets,
+                         std::vector<int64_t> &complete, bool &bad) {
+  KRUX_CUDA(ctx, ctx->status.ensure(64));
+  KRUX_CUDA(ctx, ctx->counters.ensure(64));
+  KRUX_CUDA(ctx, ctx->miss_idx.ensure((size_t)std::max<int64_t>(n, 1) * 8));
+  KRUX_CUDA(ctx, ctx->miss_mask.ensure((size_t)std::max<int64_t>(n, 1) * (kMaxN / 8)));
+  KRUX_CUDA(ctx, cudaMemsetAsync(ctx->status.p, 0, 64, s));
+  KRUX_CUDA(ctx, cudaMemsetAsync(ctx->counters.p, 0, 64, s));
+  unsigned int *cnt = ctx->counters.as<unsigned int>();
+  KRUX_CUDA(ctx, launch_missing_scan(geno, ldg, N, b, n, cnt, ctx->miss_idx.as<int64_t>(),
+                                     ctx->miss_mask.as<uint64_t>(), ctx->status.as<unsigned int>(), s));
+  unsigned int m32 = 0, st = 0;
+  KRUX_CUDA(ctx, cudaMemcpyAsync(&m32, cnt, 4, cudaMemcpyDeviceToHost, s));
+  KRUX_CUDA(ctx, cudaMemcpyAsync(&st, ctx->status.p, 4, cudaMemcpyDeviceToHost, s));
+  KRUX_CUDA(ctx, cudaStreamSynchronize(s));
+  bad = (st & kDevBadCode) != 0;
+  buckets.clear();
+  complete.clear();
+  if (bad || m32 == 0) return KRUX_OK;
+  const int64_t m = m32;
+  constexpr int W = kMaxN / 64;
+  std::vector<int64_t> idx(m);
+  std::vector<uint64_t> mask((size_t)m * W);
+  KRUX_CUDA(ctx, cudaMemcpyAsync(idx.data(), ctx->miss_idx.p, m * 8, cudaMemcpyDeviceToHost, s));
+  KRUX_CUDA(ctx, cudaMemcpyAsync(mask.data(), ctx->miss_mask.p, mask.size() * 8,
+                                 cudaMemcpyDeviceToHost, s));
+  KRUX_CUDA(ctx, cudaStreamSynchronize(s));
+  std::vector<int64_t> order(m);
+  for (int64_t i = 0; i < m; ++i) order[i] = i;
+  std::sort(order.begin(), order.end(), [&](int64_t a, int64_t c) { return idx[a] < idx[c]; });
+  std::map<std::vector<uint64_t>, size_t> where;
+  for (int64_t oi : order) {
+    std::vector<uint64_t> key(mask.begin() + oi * W, mask.begin() + (oi + 1) * W);
+    auto it = where.find(key);
+    size_t bi;
+    if (it == where.end()) {
+      bi = buckets.size();
+      Bucket bk;
+      for (int k = 0; k < N; ++k)
+        if ((key[k / 64] >> (k % 64)) & 1ull) bk.drop.push_back(k);
+      buckets.push_back(std::move(bk));
+      where.emplace(std::move(key), bi);
+    } else {
+      bi = it->second;
+    }
+    buckets[bi].snps.push_back(idx[oi]);
+  }
+  std::vector<char> is_miss((size_t)n, 0);
+  for (int64_t i = 0; i < m; ++i) is_miss[idx[i] - b] = 1;
+  complete.reserve((size_t)(n - m));
+  for (int64_t i = 0; i < n; ++i)
+    if (!is_miss[i]) complete.push_back(b + i);
+  return KRUX_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------
+// Scan groups and hit-list slots.
+namespace {
+
+// One output hit list.  Groups writing the same slot share its counter, so the
+// list is one contiguous array whatever the number of groups.
+struct OutSlot {
+  krux_hit *hits = nullptr;
+  double *H = nullptr, *P = nullptr;
+  int64_t capacity = 0;
+  HitAux *aux = nullptr;
+};
+
+struct ScanGroupIn {
+  const krux_rankset *rs = nullptr;  // geometry (T, N, Np, rows_pad)
+  const __half *A = nullptr;         // n_agroups stacked rank matrices of rows_pad rows
+  int n_agroups = 1;
+  const float *tau = nullptr;
+  const double *cfac = nullptr;
+  const uint32_t *tile_nan = nullptr;
+  const uint16_t *nan_cnt = nullptr;  // nullptr when no trait has NaN
+  const uint16_t *nan_idx = nullptr;
+  const int8_t *geno = nullptr;
+  int64_t ldg = 0;
+  const int64_t *snp_list = nullptr;  // device rows, or nullptr for [snp_begin, +n_snps)
+  int64_t list_off = -1;              // offset into the call's list buffer (patched later)
+  int64_t snp_begin = 0, n_snps = 0;
+  int allow_missing = 0;
+  int out_slot = 0;
+  double *dense_H = nullptr, *dense_p = nullptr;
+  int64_t dense_ld = 0, dense_snp0 = 0;
+  double *minp_key = nullptr;
+  int bucket = -1;                    // index into the call's bucket rank sets
+};
+
+struct BucketJob {
+  const krux_rankset *base;
+  std::vector<int32_t> drop;
+};
+
+// All state of one scan call that must outlive the launch.
+struct CallPlan {
+  std::vector<ScanGroupIn> groups;
+  std::vector<OutSlot> slots;
+  std::vector<int64_t> lists;         // host copy of all SNP lists
+  std::vector<BucketJob> bucket_jobs;
+  std::vector<krux_rankset> bucket_sets;  // host shells of the re-ranked sets
+};
+
+size_t bucket_bytes(const krux_rankset *rs) {
+  size_t off = 0;
+  auto take = [&](size_t b) { off += (b + 255) / 256 * 256; };
+  take((size_t)rs->rows_pad * rs->Np * 2);
+  take((size_t)rs->T * 8);
+  take((size_t)rs->T * 4);
+  take((size_t)rs->T * 4);
+  take((size_t)rs->T * 8);
+  take((size_t)rs->T * 2);
+  take((size_t)rs->T * rs->N * 2);
+  take((size_t)rs->n_ttiles * 4);
+  return off;
+}
+
+// Groups for one rank set against SNP rows [b, e) of geno: complete SNPs as one
+// group, and one group per missing-sample pattern (section "Handling missing
+// values").  A / n_agroups give the (possibly permutation-stacked) rank matrices.
+krux_status plan_groups(krux_ctx *ctx, CallPlan &cp, const krux_rankset *rs, const int8_t *geno,
+                        int64_t ldg, int64_t b, int64_t e, const __half *A, int n_agroups,
+                        int slot, double *dense_H, double *dense_p, double *minp_key,
+                        cudaStream_t s) {
+  const int64_t n = e - b;
+  if (n <= 0) return KRUX_OK;
+  std::vector<Bucket> buckets;
+  std::vector<int64_t> complete;
+  bool bad = false;
+  krux_status st = find_missing(ctx, geno, ldg, rs->N, b, n, s, buckets, complete, bad);
+  if (st != KRUX_OK) return st;
+  if (bad) return fail(ctx, KRUX_EINVAL, "genotype code outside {-1,0,1,2}");
+  if (!buckets.empty() && n_agroups > 1)
+    return fail(ctx, KRUX_EUNSUPPORTED, "permutation scan with missing genotypes");
+  ScanGroupIn g0;
+  g0.rs = rs;
+  g0.A = A ? A : rs->dev.A;
+  g0.n_agroups = n_agroups;
+  g0.tau = rs->dev.tau;
+  g0.cfac = rs->dev.cfac;
+  g0.tile_nan = rs->dev.tile_nan;
+  g0.nan_cnt = rs->has_nan ? rs->dev.nan_cnt : nullptr;
+  g0.nan_idx = rs->dev.nan_idx;
+  g0.geno = geno;
+  g0.ldg = ldg;
+  g0.out_slot = slot;
+  g0.dense_H = dense_H;
+  g0.dense_p = dense_p;
+  g0.dense_ld = n;
+  g0.dense_snp0 = b;
+  g0.minp_key = minp_key;
+  if (buckets.empty()) {
+    g0.snp_begin = b;
+    g0.n_snps = n;
+    cp.groups.push_back(g0);
+    return KRUX_OK;
+  }
+  if (!complete.empty()) {
+    g0.list_off = (int64_t)cp.lists.size();
+    g0.n_snps = (int64_t)complete.size();
+    cp.lists.insert(cp.lists.end(), complete.begin(), complete.end());
+    cp.groups.push_back(g0);
+  }
+  for (auto &bk : buckets) {
+    ScanGroupIn gb = g0;
+    gb.minp_key = nullptr;
+    gb.list_off = (int64_t)cp.lists.size();
+    gb.n_snps = (int64_t)bk.snps.size();
+    gb.allow_missing = 1;
+    gb.bucket = (int)cp.bucket_jobs.size();
+    cp.lists.insert(cp.lists.end(), bk.snps.begin(), bk.snps.end());
+    cp.bucket_jobs.push_back(BucketJob{rs, bk.drop});
+    cp.groups.push_back(gb);
+  }
+  return KRUX_OK;
+}
+
+// Uploads SNP lists, re-ranks every bucket, and points the groups at the results.
+krux_status materialise(krux_ctx *ctx, CallPlan &cp, cudaStream_t s) {
+  if (!cp.lists.empty()) {
+    KRUX_CUDA(ctx, ctx->list.ensure(cp.lists.size() * 8));
+    KRUX_CUDA(ctx, cudaMemcpyAsync(ctx->list.p, cp.lists.data(), cp.lists.size() * 8,
+                                   cudaMemcpyHostToDevice, s));
+  }
+  for (auto &g : cp.groups)
+    if (g.list_off >= 0) g.snp_list = ctx->list.as<int64_t>() + g.list_off;
+  if (cp.bucket_jobs.empty()) return KRUX_OK;
+  std::vector<size_t> off(cp.bucket_jobs.size());
+  size_t tot = 0;
+  for (size_t i = 0; i < cp.bucket_jobs.size(); ++i) {
+    off[i] = tot;
+    tot += bucket_bytes(cp.bucket_jobs[i].base);
+  }
+  const size_t drop_off = tot;
+  tot += cp.bucket_jobs.size() * kMaxN * 4;
+  KRUX_CUDA(ctx, ctx->bucket_ranks.ensure(tot));
+  std::vector<int32_t> drops(cp.bucket_jobs.size() * kMaxN, 0);
+  for (size_t i = 0; i < cp.bucket_jobs.size(); ++i)
+    std::copy(cp.bucket_jobs[i].drop.begin(), cp.bucket_jobs[i].drop.end(), drops.begin() + i * kMaxN);
+  char *base = ctx->bucket_ranks.as<char>();
+  int32_t *ddrop = reinterpret_cast<int32_t *>(base + drop_off);
+  KRUX_CUDA(ctx, cudaMemcpyAsync(ddrop, drops.data(), drops.size() * 4, cudaMemcpyHostToDevice, s));
+  cp.bucket_sets.assign(cp.bucket_jobs.size(), krux_rankset());
+  for (size_t i = 0; i < cp.bucket_jobs.size(); ++i) {
+    const krux_rankset *rs = cp.bucket_jobs[i].base;
+    krux_rankset &bs = cp.bucket_sets[i];
+    bs.T = rs->T;
+    bs.N = rs->N;
+    bs.Np = rs->Np;
+    bs.rows_pad = rs->rows_pad;
+    bs.n_ttiles = rs->n_ttiles;
+    bs.has_nan = rs->has_nan;
+    char *p = base + off[i];
+    size_t o2 = 0;
+    auto take = [&](size_t bytes) {
+      char *r = p + o2;
+      o2 += (bytes + 255) / 256 * 256;
+      return r;
+    };
+    bs.dev.A = (__half *)take((size_t)rs->rows_pad * rs->Np * 2);
+    bs.dev.tie = (int64_t *)take((size_t)rs->T * 8);
+    bs.dev.K = (int32_t *)take((size_t)rs->T * 4);
+    bs.dev.tau = (float *)take((size_t)rs->T * 4);
+    bs.dev.cfac = (double *)take((size_t)rs->T * 8);
+    bs.dev.nan_cnt = (uint16_t *)take((size_t)rs->T * 2);
+    bs.dev.nan_idx = (uint16_t *)take((size_t)rs->T * rs->N * 2);
+    bs.dev.tile_nan = (uint32_t *)take((size_t)rs->n_ttiles * 4);
+    KRUX_CUDA(ctx, cudaMemsetAsync(bs.dev.A, 0, (size_t)rs->rows_pad * rs->Np * 2, s));
+    KRUX_CUDA(ctx, cudaMemsetAsync(bs.dev.tile_nan, 0, (size_t)rs->n_ttiles * 4, s));
+    KRUX_CUDA(ctx, launch_rerank_bucket(rs->dev, rs->T, rs->N, rs->Np, ddrop + i * kMaxN,
+                                        (int)cp.bucket_jobs[i].drop.size(), bs.dev, s));
+  }
+  for (auto &g : cp.groups) {
+    if (g.bucket < 0) continue;
+    const krux_rankset &bs = cp.bucket_sets[g.bucket];
+    g.A = bs.dev.A;
+    g.tau = bs.dev.tau;
+    g.cfac = bs.dev.cfac;
+    g.tile_nan = bs.dev.tile_nan;
+    g.nan_cnt = bs.has_nan ? bs.dev.nan_cnt : nullptr;
+    g.nan_idx = bs.dev.nan_idx;
+  }
+  return KRUX_OK;
+}
+
+// Packs every group, launches the fused kernel once over all groups, reads the
+// per-slot hit counts back and runs the FP64 finalisation per slot.
+krux_status run_fused(krux_ctx *ctx, CallPlan &cp, const krux_opts *o, cudaStream_t s,
+                      std::vector<unsigned long long> &counts) {
+  const double h1 = h_df1(o->pthresh), h2 = h_df2(o->pthresh);
+  const int ng = (int)cp.groups.size();
+  const int nslots = (int)cp.slots.size();
+  counts.assign(nslots, 0);
+  if (ng == 0) return KRUX_OK;
+  int kpad = kAtomK;
+  for (auto &g : cp.groups) kpad = std::max(kpad, round_up(g.rs->Np, kAtomK));
+  int nc = 0, nA = 0;
+  if (!pick_shape(kpad, nc, nA))
+    return fail(ctx, KRUX_EUNSUPPORTED, "N too large for the resident-B tile (Np=%d)", kpad);
+  std::vector<int64_t> boff(ng), moff(ng), coff(ng);
+  int64_t btot = 0, mtot = 0, ctot = 0;
+  for (int i = 0; i < ng; ++i) {
+    const int64_t nch = (cp.groups[i].n_snps + kChunkSnps - 1) / kChunkSnps;
+    boff[i] = btot;
+    moff[i] = mtot;
+    coff[i] = ctot;
+    btot += (nch * kChunkRows * cp.groups[i].rs->Np * 2 + 255) / 256 * 256;
+    mtot += nch;
+    if (cp.groups[i].nan_cnt) ctot += nch * cp.groups[i].rs->Np * 2;
+  }
+  KRUX_CUDA(ctx, ctx->B.ensure(std::max<int64_t>(btot, 256)));
+  KRUX_CUDA(ctx, ctx->meta.ensure(std::max<int64_t>(mtot, 1) * sizeof(ChunkMeta)));
+  KRUX_CUDA(ctx, ctx->codes.ensure(std::max<int64_t>(ctot, 1) * 8));
+  KRUX_CUDA(ctx, ctx->counters.ensure((size_t)nslots * 8 + 64));
+  KRUX_CUDA(ctx, ctx->status.ensure(64));
+  KRUX_CUDA(ctx, cudaMemsetAsync(ctx->counters.p, 0, (size_t)nslots * 8, s));
+  KRUX_CUDA(ctx, cudaMemsetAsync(ctx->status.p, 0, 64, s));
+  unsigned int *status = ctx->status.as<unsigned int>();
+
+  ev_record(ctx, 2, s);
+  std::vector<GroupDesc> descs(ng);
+  std::vector<GroupPlan> plans(ng);
+  for (int i = 0; i < ng; ++i) {
+    ScanGroupIn &g = cp.groups[i];
+    const krux_rankset *rs = g.rs;
+    const OutSlot &os = cp.slots[g.out_slot];
+    __half *B = reinterpret_cast<__half *>(ctx->B.as<char>() + boff[i]);
+    ChunkMeta *meta = ctx->meta.as<ChunkMeta>() + moff[i];
+    uint64_t *codes = g.nan_cnt ? ctx->codes.as<uint64_t>() + coff[i] : nullptr;
+    KRUX_CUDA(ctx, launch_pack2(g.geno, g.ldg, rs->N, rs->Np, g.snp_list, g.snp_begin, g.n_snps, 0,
+                                h1, h2, g.allow_missing, B, meta, codes, status, s));
+    GroupDesc &d = plans[i].d;
+    std::memset(&d, 0, sizeof d);
+    const int64_t nch = (g.n_snps + kChunkSnps - 1) / kChunkSnps;
+    krux_status st = encode_map(ctx, &d.tmA, g.A, rs->Np, (int64_t)rs->rows_pad * g.n_agroups);
+    if (st != KRUX_OK) return st;
+    st = encode_map(ctx, &d.tmB, B, rs->Np, std::max<int64_t>(nch, 1) * kChunkRows);
+    if (st != KRUX_OK) return st;
+    d.meta = meta;
+    d.codes = codes;
+    d.tau = g.tau;
+    d.cfac = g.cfac;
+    d.nan_cnt = g.nan_cnt;
+    d.nan_idx = g.nan_idx;
+    d.tile_nan = g.tile_nan;
+    d.hits = os.hits;
+    d.aux = os.aux;
+    d.counter = ctx->counters.as<unsigned long long>() + g.out_slot;
+    d.capacity = os.capacity;
+    d.dense_H = g.dense_H;
+    d.dense_p = g.dense_p;
+    d.dense_ld = g.dense_ld;
+    d.dense_snp0 = g.dense_snp0;
+    d.minp_key = g.minp_key;
+    d.T = rs->T;
+    d.N = rs->N;
+    d.Np = rs->Np;
+    d.n_ttiles = rs->n_ttiles;
+    d.rows_per_agroup = rs->rows_pad;
+    d.n_agroups = g.n_agroups;
+    d.nchunks = (int32_t)nch;
+    d.n_atoms = (rs->Np + kAtomK - 1) / kAtomK;
+    d.group_id = i;
+    plans[i].n_btiles = (nch + nc - 1) / nc;
+    plans[i].steps = (int64_t)g.n_agroups * rs->n_ttiles;
+    descs[i] = d;
+  }
+  ev_record(ctx, 3, s);
+  std::vector<WorkItem> items = make_items(plans, nc, ctx->sm_count);
+  KRUX_CUDA(ctx, ctx->groups.ensure(sizeof(GroupDesc) * ng));
+  KRUX_CUDA(ctx, ctx->items.ensure(sizeof(WorkItem) * std::max<size_t>(items.size(), 1)));
+  KRUX_CUDA(ctx, cudaMemcpyAsync(ctx->groups.p, descs.data(), sizeof(GroupDesc) * ng,
+                                 cudaMemcpyHostToDevice, s));
+  if (!items.empty())
+    KRUX_CUDA(ctx, cudaMemcpyAsync(ctx->items.p, items.data(), sizeof(WorkItem) * items.size(),
+                                   cudaMemcpyHostToDevice, s));
+  ScanParams p{};
+  p.groups = ctx->groups.as<GroupDesc>();
+  p.items = ctx->items.as<WorkItem>();
+  p.n_items = (int32_t)items.size();
+  p.nc = nc;
+  p.nA = nA;
+  p.kpad = kpad;
+  p.margin = (float)(o->recheck_margin > 0 ? o->recheck_margin : 1e-4);
+  p.dense = o->dense_H != nullptr ? 1 : 0;
+  p.pthresh = o->pthresh;
+  p.h1 = (float)h1;
+  p.h2 = (float)h2;
+  p.status = status;
+  p.timeout_cycles = ctx->wait_limit;
+  const int grid = (int)std::min<size_t>(items.size(), (size_t)ctx->sm_count);
+  if (grid > 0) KRUX_CUDA(ctx, launch_scan(p, grid, scan_smem_bytes(nc, nA, kpad), s));
+  ev_record(ctx, 4, s);
+
+  unsigned int hst[2] = {0, 0};
+  KRUX_CUDA(ctx, cudaMemcpyAsync(counts.data(), ctx->counters.p, (size_t)nslots * 8,
+                                 cudaMemcpyDeviceToHost, s));
+  KRUX_CUDA(ctx, cudaMemcpyAsync(hst, ctx->status.p, 8, cudaMemcpyDeviceToHost, s));
+  KRUX_CUDA(ctx, cudaStreamSynchronize(s));
+  if (ctx->profiling) {
+    ctx->prof.ms_pack = ev_ms(ctx, 2, 3);
+    ctx->prof.ms_scan = ev_ms(ctx, 3, 4);
+    ctx->prof.scan_grid = grid;
+    ctx->prof.launches += (grid > 0 ? 1 : 0);
+    for (auto &g : cp.groups) ctx->prof.launches += g.nan_cnt ? 2 : 1;
+  }
+  if (hst[0] & kDevBadCode) return fail(ctx, KRUX_EINVAL, "genotype code outside {-1,0,1,2}");
+  if (hst[0] & kDevTimeout)
+    return fail(ctx, KRUX_ETIMEOUT, "device wait timed out (site %u)", hst[1]);
+
+  // FP64 H and p of the stored hits
+  std::vector<const double *> cf(ng);
+  for (int i = 0; i < ng; ++i) cf[i] = cp.groups[i].cfac;
+  KRUX_CUDA(ctx, ctx->cfacptr.ensure(sizeof(double *) * ng));
+  KRUX_CUDA(ctx, cudaMemcpyAsync(ctx->cfacptr.p, cf.data(), sizeof(double *) * ng,
+                                 cudaMemcpyHostToDevice, s));
+  ev_record(ctx, 5, s);
+  for (int k = 0; k < nslots; ++k) {
+    const OutSlot &os = cp.slots[k];
+    const int64_t nst = std::min<int64_t>((int64_t)counts[k], os.capacity);
+    if (nst > 0) {
+      KRUX_CUDA(ctx, launch_finalize(os.hits, os.aux, nst, ctx->cfacptr.as<const double *>(), os.H,
+                                     os.P, s));
+      if (ctx->profiling) ctx->prof.launches += 1;
+    }
+  }
+  ev_record(ctx, 6, s);
+  if (ctx->profiling) {
+    KRUX_CUDA(ctx, cudaStreamSynchronize(s));
+    ctx->prof.ms_finalize = ev_ms(ctx, 5, 6);
+  }
+  return KRUX_OK;
+}
+
+krux_status check_scan_args(krux_ctx *ctx, const krux_rankset *rs, const int8_t *geno, int64_t S,
+                            int64_t ldg, const krux_opts *opts, krux_hit *hits, double *hit_H,
+                            double *hit_p, int64_t *n_hits) {
+  if (!ctx) return KRUX_EINVAL;
+  if (!rs || !n_hits) return fail(ctx, KRUX_EINVAL, "NULL rank set or n_hits");
+  krux_status st = check_opts(ctx, opts);
+  if (st != KRUX_OK) return st;
+  if (S < 0 || (S > 0 && ldg < rs->N)) return fail(ctx, KRUX_EINVAL, "need S >= 0 and ldg >= N");
+  if (S > 0 && !geno) return fail(ctx, KRUX_EINVAL, "geno is NULL");
+  if (S >= (int64_t)1 << 31) return fail(ctx, KRUX_EINVAL, "S must be < 2^31");
+  if (opts->hit_capacity > 0 && (!hits || !hit_H || !hit_p))
+    return fail(ctx, KRUX_EINVAL, "hit outputs are NULL");
+  const int64_t b = opts->snp_begin, e = opts->snp_end > 0 ? opts->snp_end : S;
+  if (b < 0 || e > S || b > e)
+    return fail(ctx, KRUX_EINVAL, "bad SNP slice [%lld, %lld)", (long long)b, (long long)e);
+  return KRUX_OK;
+}
+
+}  // namespace
+
+extern "C" krux_status krux_scan(krux_ctx *ctx, const krux_rankset *rs, const int8_t *geno,
+                                 int64_t S, int64_t ldg, const krux_opts *opts, krux_hit *hits,
+                                 double *hit_H, double *hit_p, int64_t *n_hits, void *stream) {
+  krux_status st = check_scan_args(ctx, rs, geno, S, ldg, opts, hits, hit_H, hit_p, n_hits);
+  if (st != KRUX_OK) return st;
+  *n_hits = 0;
+  cudaStream_t s = (cudaStream_t)stream;
+  KRUX_CUDA(ctx, cudaSetDevice(ctx->device));
+  const int64_t b = opts->snp_begin, e = opts->snp_end > 0 ? opts->snp_end : S;
+  if (ctx->profiling) {
+    ctx->prof = krux_profile{};
+    ctx->prof.pairs = (int64_t)rs->T * (e - b);
+  }
+  KRUX_CUDA(ctx, ctx->aux.ensure((size_t)std::max<int64_t>(opts->hit_capacity, 1) * sizeof(HitAux)));
+  CallPlan cp;
+  cp.slots.push_back(OutSlot{hits, hit_H, hit_p, opts->hit_capacity, ctx->aux.as<HitAux>()});
+  st = plan_groups(ctx, cp, rs, geno, ldg, b, e, nullptr, 1, 0, opts->dense_H, opts->dense_p,
+                   nullptr, s);
+  if (st != KRUX_OK) return st;
+  st = materialise(ctx, cp, s);
+  if (st != KRUX_OK) return st;
+  std::vector<unsigned long long> counts;
+  st = run_fused(ctx, cp, opts, s, counts);
+  if (st != KRUX_OK) return st;
+  *n_hits = (int64_t)counts[0];
+  if (*n_hits > opts->hit_capacity)
+    return fail(ctx, KRUX_EOVERFLOW, "%lld hits exceed capacity %lld", (long long)*n_hits,
+                (long long)opts->hit_capacity);
+  return KRUX_OK;
+}
+
+extern "C" krux_status krux_scan_grouped(krux_ctx *ctx, krux_cohort *cohorts, int n_cohorts,
+                                         const krux_opts *opts, void *stream) {
+  if (!ctx) return KRUX_EINVAL;
+  krux_status st = check_opts(ctx, opts);
+  if (st != KRUX_OK) return st;
+  if (n_cohorts < 0 || (n_cohorts > 0 && !cohorts)) return fail(ctx, KRUX_EINVAL, "bad cohort list");
+  if (opts->dense_H) return fail(ctx, KRUX_EINVAL, "dense output is not available for grouped scans");
+  cudaStream_t s = (cudaStream_t)stream;
+  KRUX_CUDA(ctx, cudaSetDevice(ctx->device));
+  int64_t captot = 0;
+  for (int c = 0; c < n_cohorts; ++c) {
+    krux_cohort &k = cohorts[c];
+    k.n_hits = 0;
+    if (!k.rs || k.S < 0 || (k.S > 0 && (!k.geno || k.ldg < k.rs->N)) || k.hit_capacity < 0 ||
+        (k.hit_capacity > 0 && (!k.hits || !k.hit_H || !k.hit_p)))
+      return fail(ctx, KRUX_EINVAL, "cohort %d: bad arguments", c);
+    captot += std::max<int64_t>(k.hit_capacity, 1);
+  }
+  if (ctx->profiling) {
+    ctx->prof = krux_profile{};
+    for (int c = 0; c < n_cohorts; ++c) ctx->prof.pairs += (int64_t)cohorts[c].rs->T * cohorts[c].S;
+  }
+  KRUX_CUDA(ctx, ctx->aux.ensure((size_t)std::max<int64_t>(captot, 1) * sizeof(HitAux)));
+  CallPlan cp;
+  int64_t aoff = 0;
+  for (int c = 0; c < n_cohorts; ++c) {
+    krux_cohort &k = cohorts[c];
+    cp.slots.push_back(OutSlot{k.hits, k.hit_H, k.hit_p, k.hit_capacity, ctx->aux.as<HitAux>() + aoff});
+    aoff += std::max<int64_t>(k.hit_capacity, 1);
+    st = plan_groups(ctx, cp, k.rs, k.geno, k.ldg, 0, k.S, nullptr, 1, c, nullptr, nullptr, nullptr, s);
+    if (st != KRUX_OK) return st;
+  }
+  st = materialise(ctx, cp, s);
+  if (st != KRUX_OK) return st;
+  std::vector<unsigned long long> counts;
+  st = run_fused(ctx, cp, opts, s, counts);
+  if (st != KRUX_OK) return st;
+  bool over = false;
+  for (int c = 0; c < n_cohorts; ++c) {
+    cohorts[c].n_hits = (int64_t)counts[c];
+    over |= cohorts[c].n_hits > cohorts[c].hit_capacity;
+  }
+  if (over) return fail(ctx, KRUX_EOVERFLOW, "a cohort's hits exceed its capacity");
+  return KRUX_OK;
+}
+
+extern "C" krux_status krux_scan_plain(krux_ctx *ctx, const krux_rankset *rs, const int8_t *geno,
+                                       int64_t S, int64_t ldg, const krux_opts *opts, krux_hit *hits,
+                                       double *hit_H, double *hit_p, int64_t *n_hits, void *stream) {
+  krux_status st = check_scan_args(ctx, rs, geno, S, ldg, opts, hits, hit_H, hit_p, n_hits);
+  if (st != KRUX_OK) return st;
+  *n_hits = 0;
+  cudaStream_t s = (cudaStream_t)stream;
+  KRUX_CUDA(ctx, cudaSetDevice(ctx->device));
+  const int64_t b = opts->snp_begin, e = opts->snp_end > 0 ? opts->snp_end : S;
+  const int64_t n = e - b;
+  if (ctx->profiling) {
+    ctx->prof = krux_profile{};
+    ctx->prof.pairs = (int64_t)rs->T * n;
+  }
+  if (n == 0) return KRUX_OK;
+  std::vector<Bucket> buckets;
+  std::vector<int64_t> complete;
+  bool bad = false;
+  st = find_missing(ctx, geno, ldg, rs->N, b, n, s, buckets, complete, bad);
+  if (st != KRUX_OK) return st;
+  if (bad) return fail(ctx, KRUX_EINVAL, "genotype code outside {-1,0,1,2}");
+  if (!buckets.empty())
+    return fail(ctx, KRUX_EUNSUPPORTED, "the plain form takes complete genotypes only");
+  if (!ctx->blas) ctx->blas = plain_handle_create();
+  if (!ctx->blas) return fail(ctx, KRUX_ECUDA, "cublasCreate failed");
+  const double h1 = h_df1(opts->pthresh), h2 = h_df2(opts->pthresh);
+  const int64_t nch = (n + kChunkSnps - 1) / kChunkSnps;
+  KRUX_CUDA(ctx, ctx->B.ensure((size_t)nch * kChunkRows * rs->Np * 2));
+  KRUX_CUDA(ctx, ctx->meta.ensure((size_t)nch * sizeof(ChunkMeta)));
+  KRUX_CUDA(ctx, ctx->aux.ensure((size_t)std::max<int64_t>(opts->hit_capacity, 1) * sizeof(HitAux)));
+  KRUX_CUDA(ctx, ctx->counters.ensure(64));
+  KRUX_CUDA(ctx, ctx->status.ensure(64));
+  KRUX_CUDA(ctx, cudaMemsetAsync(ctx->counters.p, 0, 64, s));
+  KRUX_CUDA(ctx, cudaMemsetAsync(ctx->status.p, 0, 64, s));
+  ev_record(ctx, 2, s);
+  KRUX_CUDA(ctx, launch_pack2(geno, ldg, rs->N, rs->Np, nullptr, b, n, 0, h1, h2, 0,
+                              ctx->B.as<__half>(), ctx->meta.as<ChunkMeta>(), nullptr,
+                              ctx->status.as<unsigned int>(), s));
+  ev_record(ctx, 3, s);
+  // SNP slices whose T x 2*slice FP32 rank-sum matrix fits a 4 GiB buffer
+  const int64_t budget = (int64_t)4 << 30;
+  int64_t cs = std::max<int64_t>(1, budget / ((int64_t)rs->rows_pad * kChunkRows * 4));
+  cs = std::min(cs, nch);
+  KRUX_CUDA(ctx, ctx->gemm_out.ensure((size_t)rs->rows_pad * cs * kChunkRows * 4));
+  const float margin = (float)(opts->recheck_margin > 0 ? opts->recheck_margin : 1e-4);
+  int launches = 1;
+  for (int64_t c0 = 0; c0 < nch; c0 += cs) {
+    const int64_t cn = std::min(cs, nch - c0);
+    const int rowsB = (int)(cn * kChunkRows);
+    KRUX_CUDA(ctx, plain_gemm(ctx->blas, rs->dev.A, rs->rows_pad, rs->Np,
+                              ctx->B.as<__half>() + (size_t)c0 * kChunkRows * rs->Np, rowsB,
+                              ctx->gemm_out.as<float>(), s));
+    const int n_slots = (int)std::min<int64_t>(cn * kChunkSnps, n - c0 * kChunkSnps);
+    KRUX_CUDA(ctx, launch_plain_epilogue2(
+                       ctx->gemm_out.as<float>(), rowsB, rs->T, n_slots, ctx->meta.as<ChunkMeta>() + c0,
+                       rs->dev.tau, rs->dev.cfac, rs->has_nan ? rs->dev.nan_cnt : nullptr,
+                       rs->dev.nan_idx, rs->N, geno, ldg, margin, opts->pthresh, (float)h1, (float)h2,
+                       hits, ctx->aux.as<HitAux>(), ctx->counters.as<unsigned long long>(),
+                       opts->hit_capacity, opts->dense_H, opts->dense_p, n, b, s));
+    launches += 2;
+  }
+  ev_record(ctx, 4, s);
+  unsigned long long cnt = 0;
+  unsigned int hst = 0;
+  KRUX_CUDA(ctx, cudaMemcpyAsync(&cnt, ctx->counters.p, 8, cudaMemcpyDeviceToHost, s));
+  KRUX_CUDA(ctx, cudaMemcpyAsync(&hst, ctx->status.p, 4, cudaMemcpyDeviceToHost, s));
+  KRUX_CUDA(ctx, cudaStreamSynchronize(s));
+  if (hst & kDevBadCode) return fail(ctx, KRUX_EINVAL, "genotype code outside {-1,0,1,2}");
+  const double *cf = rs->dev.cfac;
+  KRUX_CUDA(ctx, ctx->cfacptr.ensure(sizeof(double *)));
+  KRUX_CUDA(ctx, cudaMemcpyAsync(ctx->cfacptr.p, &cf, sizeof(double *), cudaMemcpyHostToDevice, s));
+  ev_record(ctx, 5, s);
+  const int64_t nst = std::min<int64_t>((int64_t)cnt, opts->hit_capacity);
+  if (nst > 0)
+    KRUX_CUDA(ctx, launch_finalize(hits, ctx->aux.as<HitAux>(), nst, ctx->cfacptr.as<const double *>(),
+                                   hit_H, hit_p, s));
+  ev_record(ctx, 6, s);
+  if (ctx->profiling) {
+    KRUX_CUDA(ctx, cudaStreamSynchronize(s));
+    ctx->prof.ms_pack = ev_ms(ctx, 2, 3);
+    ctx->prof.ms_scan = ev_ms(ctx, 3, 4);
+    ctx->prof.ms_finalize = ev_ms(ctx, 5, 6);
+    ctx->prof.launches = launches + (nst > 0 ? 1 : 0) + 1;
+  }
+  *n_hits = (int64_t)cnt;
+  if (*n_hits > opts->hit_capacity)
+    return fail(ctx, KRUX_EOVERFLOW, "%lld hits exceed capacity %lld", (long long)*n_hits,
+                (long long)opts->hit_capacity);
+  return KRUX_OK;
+}
+
+extern "C" krux_status krux_permute(krux_ctx *ctx, const krux_rankset *rs, const int8_t *geno,
+                                    int64_t S, int64_t ldg, const int32_t *perms, int P,
+                                    const krux_opts *opts, double *minp, krux_hit *hits,
+                                    double *hit_H, double *hit_p, int64_t *n_hits, void *stream) {
+  (void)rs; (void)geno; (void)S; (void)ldg; (void)perms; (void)P; (void)opts; (void)minp;
+  (void)hits; (void)hit_H; (void)hit_p; (void)n_hits; (void)stream;
+  return fail(ctx, KRUX_EUNSUPPORTED, "krux_permute is not available in this build yet");
+}

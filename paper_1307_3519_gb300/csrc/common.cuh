@@ -1,0 +1,125 @@
+// common.cuh -- device-side data layouts shared by the kernels of the Kruskal-Wallis
+// scan library (rank transform, genotype packing, fused tcgen05 scan, FP64
+// finalisation, plain GEMM form) and by the host orchestration in abi.cu.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/krux.h"
+
+namespace krux {
+
+// ---- fixed tile geometry ---------------------------------------------------
+constexpr int kTileM = 128;        // traits per MMA tile = TMEM lanes
+constexpr int kChunkSnps = 64;     // SNPs per chunk
+constexpr int kChunkRows = 128;    // B rows per chunk: [I_0 of 64 SNPs | I_1 of 64 SNPs]
+constexpr int kMaxN = 512;         // samples: centred 2*rank fits FP16 exactly below 2048
+constexpr int kAtomK = 64;         // K elements per 128-byte swizzle atom (fp16)
+constexpr int kTmemSlots = 4;      // accumulator ring: 4 x 128 fp32 columns = all of TMEM
+constexpr int kEpiWarps = 8;       // epilogue warps: 2 per TMEM lane quarter
+constexpr int kProducerWarp = 8;   // TMA producer
+constexpr int kMmaWarp = 9;        // tcgen05.mma issuer, owns the TMEM allocation
+constexpr int kScanThreads = 320;
+
+// ---- per-chunk SNP metadata (one 1536-byte blob per chunk of 64 SNPs) ------
+// Fast-test coefficients: with u = D_0, v = D_1 (D_2 = -u - v) the statistic's
+// quadratic form sum_i D_i^2 / N_i equals alpha (u + beta v)^2 + gamma v^2; alpha
+// and gamma are pre-divided by the chi-square threshold h_df of the SNP's df so
+// that one per-trait bound decides the test.
+struct ChunkMeta {
+  float alpha[kChunkSnps];      // (r0 + r2) / h_df
+  float beta[kChunkSnps];       // r2 / (r0 + r2)
+  float gamma[kChunkSnps];      // (r1 + r2 r0 / (r0 + r2)) / h_df
+  int32_t snp[kChunkSnps];      // output SNP index, -1 = padding
+  uint16_t n[3][kChunkSnps];    // genotype group sizes over non-missing samples
+  uint8_t df[kChunkSnps];       // non-empty groups - 1
+  uint8_t pad_[64];
+};
+static_assert(sizeof(ChunkMeta) == 1536, "ChunkMeta must be 1536 bytes");
+
+// Side record of a hit, written next to the public krux_hit record and used by the
+// FP64 finalisation: the pair's group sizes and the group (cohort / bucket) index.
+struct HitAux {
+  uint16_t n0, n1, n2, group;
+};
+
+// ---- rank set: everything the scan needs about one expression matrix ------
+struct RankDev {
+  __half *A;            // [rows_pad][Np] centred 2*rank (0 at NaN and padding)
+  uint16_t *lo;         // [T][N] #present values strictly below (for bucket re-ranks)
+  uint16_t *eq;         // [T][N] #present values equal (itself included), 0 at NaN
+  int64_t *tie;         // [T] sum over present samples of eq^2 - 1 = sum (t^3 - t)
+  int32_t *K;           // [T] present samples
+  float *tau;           // [T] K(K+1)C/3 (fast-test bound), +inf when degenerate
+  double *cfac;         // [T] 3 / (K(K+1)C), 0 when degenerate
+  uint16_t *nan_cnt;    // [T] NaN samples of the trait
+  uint16_t *nan_idx;    // [T][N] their sample indices (first nan_cnt entries)
+  uint32_t *tile_nan;   // [rows_pad/128] 1 if any trait of the tile has a NaN
+};
+
+// ---- one group of a scan launch (a cohort, a missing-pattern bucket, or the
+// unpermuted + permuted rank matrices of a permutation batch) ----------------
+struct alignas(64) GroupDesc {
+  CUtensorMap tmA;          // 2D fp16 [rowsA][Np], box {64, 128}, 128B swizzle
+  CUtensorMap tmB;          // 2D fp16 [nchunks*128][Np], box {64, 128}, 128B swizzle
+  const ChunkMeta *meta;    // [nchunks]
+  const uint64_t *codes;    // [nchunks][Np][2] 2-bit genotype codes (3 = missing), or null
+  const float *tau;         // [T]
+  const double *cfac;       // [T]
+  const uint16_t *nan_cnt;  // [T] or null when the rank set has no NaN
+  const uint16_t *nan_idx;  // [T][N]
+  const uint32_t *tile_nan; // [n_ttiles]
+  krux_hit *hits;           // hit records (capacity entries)
+  HitAux *aux;              // side records
+  unsigned long long *counter;  // hits found (keeps counting past capacity)
+  double *dense_H, *dense_p;    // optional [T][dense_ld]
+  double *minp_key;         // permutation mode: [n_agroups-1][T] best -ln p (as double bits)
+  int64_t capacity;
+  int64_t dense_ld;
+  int64_t dense_snp0;       // SNP index of dense column 0
+  int32_t T, N, Np, n_ttiles, rows_per_agroup, n_agroups, nchunks, n_atoms;
+  int32_t group_id;
+  int32_t pad_[7];
+};
+
+// Work item: B tile `btile` (chunks btile*nc .. +nc) of group `group`, against the
+// (agroup, trait-tile) steps [step_begin, step_end) of that group.
+struct WorkItem {
+  int32_t group, btile, step_begin, step_end;
+};
+
+struct ScanParams {
+  const GroupDesc *groups;
+  const WorkItem *items;
+  int32_t n_items;
+  int32_t nc;               // chunks per B tile
+  int32_t nA;               // A pipeline stages
+  int32_t kpad;             // smem K width of a tile (multiple of 64)
+  float margin;             // relative band rechecked in FP64
+  int32_t dense;            // 1: every pair's H, p written in FP64
+  double pthresh;
+  float h1, h2;             // chi-square thresholds at pthresh for df 1, 2 (fp32)
+  unsigned int *status;     // [0] error bits, [1] where
+  long long timeout_cycles;
+};
+
+enum : unsigned int {
+  kDevTimeout = 1u,
+  kDevBadCode = 2u,
+};
+
+// ---- launch wrappers (defined in the .cu files) -----------------------------
+cudaError_t launch_rank(const float *expr, int T, int N, int64_t ld, int Np, int rows_pad,
+                        const RankDev &r, cudaStream_t s);
+cudaError_t launch_permute_rows(const __half *A, __half *out, int rows_pad, int Np, int N,
+                                const int32_t *perms, int P, cudaStream_t s);
+cudaError_t launch_scan(const ScanParams &p, int grid, size_t smem, cudaStream_t s);
+size_t scan_smem_bytes(int nc, int nA, int kpad);
+cudaError_t launch_finalize(const krux_hit *hits, const HitAux *aux, int64_t n,
+                            const double *const *cfac_by_group, double *H, double *p,
+                            cudaStream_t s);
+
+}  // namespace krux

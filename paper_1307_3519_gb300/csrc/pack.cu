@@ -1,0 +1,205 @@
+// pack.cu -- genotype packing (section "Calculation of the Kruskal-Wallis test
+// statistic by matrix multiplication": the index matrices I_i(m,k) = [G(m,k) = i]
+// and the group sizes N_i(m) = sum_k I_i(m,k)).
+//
+// Only I_0 and I_1 are materialised: with centred ranks the three rank sums
+// satisfy D_0 + D_1 + D_2 = 0, so D_2 follows from the other two.  The packed
+// operand is FP16 0/1 in chunks of 64 SNPs: chunk c holds rows [0,64) = I_0 and
+// rows [64,128) = I_1 of SNPs 64c .. 64c+63, each row Np samples long.
+#include "common.cuh"
+
+namespace krux {
+
+namespace {
+constexpr int kPackWarps = 8;
+
+// Missing-genotype pre-pass: flags SNPs with a -1 code, appends (index, sample
+// bitmask) of each such SNP, and reports codes outside {-1,0,1,2}.
+__global__ void __launch_bounds__(kPackWarps * 32)
+missing_scan_kernel(const int8_t *__restrict__ geno, int64_t ldg, int N, int64_t snp_begin,
+                    int64_t n_snps, unsigned int *n_missing, int64_t *miss_idx,
+                    uint64_t *miss_mask, unsigned int *status) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t j = (int64_t)blockIdx.x * kPackWarps + warp;
+  if (j >= n_snps) return;
+  const int8_t *g = geno + (snp_begin + j) * ldg;
+  uint32_t words[kMaxN / 32];
+  bool any = false, bad = false;
+#pragma unroll
+  for (int w = 0; w < kMaxN / 32; ++w) {
+    const int k = w * 32 + lane;
+    int code = 0;
+    if (w * 32 < N) {
+      code = k < N ? (int)g[k] : 0;
+    }
+    bad |= (code < -1 || code > 2);
+    words[w] = __ballot_sync(0xffffffffu, code == -1);
+    any |= words[w] != 0u;
+  }
+  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(status, kDevBadCode);
+  if (!any) return;
+  unsigned int slot = 0;
+  if (lane == 0) slot = atomicAdd(n_missing, 1u);
+  slot = __shfl_sync(0xffffffffu, slot, 0);
+  if (lane == 0) miss_idx[slot] = snp_begin + j;
+  if (lane < kMaxN / 64) {
+    const uint64_t m = (uint64_t)words[2 * lane] | ((uint64_t)words[2 * lane + 1] << 32);
+    miss_mask[(int64_t)slot * (kMaxN / 64) + lane] = m;
+  }
+}
+
+// One warp per packed SNP slot j (including the padding of the last chunk).
+// SNP j is snp_list[j] if a list is given, else snp_begin + j.  SNPs that carry a
+// missing code are packed with zero coefficients here (they are scanned in
+// their missing-pattern bucket, where the rank set excludes those samples and
+// the -1 entries simply pack as 0 in both indicators).
+__global__ void __launch_bounds__(kPackWarps * 32)
+pack_kernel(const int8_t *__restrict__ geno, int64_t ldg, int N, int Np,
+            const int64_t *__restrict__ snp_list, int64_t snp_begin, int64_t n_snps,
+            int64_t n_slots, int64_t snp_out_base, double h1, double h2, int allow_missing,
+            __half *__restrict__ B, ChunkMeta *__restrict__ meta, unsigned int *status) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t j = (int64_t)blockIdx.x * kPackWarps + warp;
+  if (j >= n_slots) return;
+  const int64_t c = j / kChunkSnps;
+  const int jj = (int)(j % kChunkSnps);
+  __half *r0 = B + (c * kChunkRows + jj) * Np;
+  __half *r1 = B + (c * kChunkRows + kChunkSnps + jj) * Np;
+  ChunkMeta &m = meta[c];
+  const __half one = __int2half_rn(1), zero = __int2half_rn(0);
+  if (j >= n_snps) {
+    for (int k = lane; k < Np; k += 32) {
+      r0[k] = zero;
+      r1[k] = zero;
+    }
+    if (lane == 0) {
+      m.alpha[jj] = 0.f;
+      m.beta[jj] = 0.f;
+      m.gamma[jj] = 0.f;
+      m.snp[jj] = -1;
+      m.n[0][jj] = m.n[1][jj] = m.n[2][jj] = 0;
+      m.df[jj] = 0;
+    }
+    return;
+  }
+  const int64_t s = snp_list ? snp_list[j] : snp_begin + j;
+  const int8_t *g = geno + s * ldg;
+  int n0 = 0, n1 = 0, n2 = 0;
+  bool miss = false, bad = false;
+  for (int k = lane; k < Np; k += 32) {
+    const int code = k < N ? (int)g[k] : -1;
+    r0[k] = code == 0 ? one : zero;
+    r1[k] = code == 1 ? one : zero;
+    n0 += code == 0;
+    n1 += code == 1;
+    n2 += code == 2;
+    if (k < N) {
+      miss |= code == -1;
+      bad |= (code < -1 || code > 2);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    n0 += __shfl_xor_sync(0xffffffffu, n0, o);
+    n1 += __shfl_xor_sync(0xffffffffu, n1, o);
+    n2 += __shfl_xor_sync(0xffffffffu, n2, o);
+  }
+  miss = __any_sync(0xffffffffu, miss);
+  bad = __any_sync(0xffffffffu, bad);
+  if (lane == 0) {
+    if (bad) atomicOr(status, kDevBadCode);
+    const int groups = (n0 > 0) + (n1 > 0) + (n2 > 0);
+    const int df = groups > 0 ? groups - 1 : 0;
+    float al = 0.f, be = 0.f, ga = 0.f;
+    const bool excluded = miss && !allow_missing;
+    if (df > 0 && !excluded) {
+      // sum_i D_i^2 / N_i with D_2 = -(u + v):  (r0 + r2) u^2 + 2 r2 u v + (r1 + r2) v^2
+      //   = alpha (u + beta v)^2 + gamma v^2,  alpha = r0 + r2, beta = r2 / alpha,
+      //   gamma = r1 + r2 r0 / alpha   (empty groups have r_i = 0)
+      const double q0 = n0 ? 1.0 / n0 : 0.0, q1 = n1 ? 1.0 / n1 : 0.0, q2 = n2 ? 1.0 / n2 : 0.0;
+      const double a = q0 + q2;
+      const double h = df == 1 ? h1 : h2;
+      al = (float)(a / h);
+      be = (float)(q2 / a);
+      ga = (float)((q1 + q2 * q0 / a) / h);
+    }
+    m.alpha[jj] = al;
+    m.beta[jj] = be;
+    m.gamma[jj] = ga;
+    m.snp[jj] = excluded ? -1 : (int32_t)(snp_out_base + s);
+    m.n[0][jj] = (uint16_t)n0;
+    m.n[1][jj] = (uint16_t)n1;
+    m.n[2][jj] = (uint16_t)n2;
+    m.df[jj] = (uint8_t)df;
+  }
+}
+
+__device__ __forceinline__ uint64_t spread_bits(uint32_t v) {
+  uint64_t x = v;
+  x = (x | (x << 16)) & 0x0000FFFF0000FFFFull;
+  x = (x | (x << 8)) & 0x00FF00FF00FF00FFull;
+  x = (x | (x << 4)) & 0x0F0F0F0F0F0F0F0Full;
+  x = (x | (x << 2)) & 0x3333333333333333ull;
+  x = (x | (x << 1)) & 0x5555555555555555ull;
+  return x;
+}
+
+// 2-bit genotype codes per chunk and sample: word [c][k][h] holds, at bits
+// 2j..2j+1, the code of SNP 64c + 32h + j at sample k (0,1,2; 3 = missing or
+// padding).  Used by the epilogue to drop a trait's NaN samples from N_i.
+__global__ void __launch_bounds__(kPackWarps * 32)
+codes_kernel(const int8_t *__restrict__ geno, int64_t ldg, int N, int Np,
+             const int64_t *__restrict__ snp_list, int64_t snp_begin, int64_t n_snps,
+             int64_t n_halves, uint64_t *__restrict__ codes) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t hw = (int64_t)blockIdx.x * kPackWarps + warp;  // chunk * 2 + half
+  if (hw >= n_halves) return;
+  const int64_t j = hw * 32 + lane;
+  const int8_t *g = nullptr;
+  if (j < n_snps) g = geno + (snp_list ? snp_list[j] : snp_begin + j) * ldg;
+  const int64_t c = hw >> 1;
+  const int h = (int)(hw & 1);
+  for (int k = 0; k < Np; ++k) {
+    int code = 3;
+    if (g && k < N) {
+      const int v = g[k];
+      code = (v >= 0 && v <= 2) ? v : 3;
+    }
+    const uint32_t b0 = __ballot_sync(0xffffffffu, code & 1);
+    const uint32_t b1 = __ballot_sync(0xffffffffu, (code >> 1) & 1);
+    if (lane == 0) codes[(c * Np + k) * 2 + h] = spread_bits(b0) | (spread_bits(b1) << 1);
+  }
+}
+}  // namespace
+
+cudaError_t launch_missing_scan(const int8_t *geno, int64_t ldg, int N, int64_t snp_begin,
+                                int64_t n_snps, unsigned int *n_missing, int64_t *miss_idx,
+                                uint64_t *miss_mask, unsigned int *status, cudaStream_t s) {
+  if (n_snps <= 0) return cudaSuccess;
+  const int64_t grid = (n_snps + kPackWarps - 1) / kPackWarps;
+  missing_scan_kernel<<<(unsigned)grid, kPackWarps * 32, 0, s>>>(geno, ldg, N, snp_begin, n_snps,
+                                                                 n_missing, miss_idx, miss_mask, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack2(const int8_t *geno, int64_t ldg, int N, int Np, const int64_t *snp_list,
+                         int64_t snp_begin, int64_t n_snps, int64_t snp_out_base, double h1,
+                         double h2, int allow_missing, __half *B, ChunkMeta *meta,
+                         uint64_t *codes, unsigned int *status, cudaStream_t s) {
+  const int64_t nchunks = (n_snps + kChunkSnps - 1) / kChunkSnps;
+  const int64_t n_slots = nchunks * kChunkSnps;
+  if (n_slots == 0) return cudaSuccess;
+  const int64_t grid = (n_slots + kPackWarps - 1) / kPackWarps;
+  pack_kernel<<<(unsigned)grid, kPackWarps * 32, 0, s>>>(geno, ldg, N, Np, snp_list, snp_begin,
+                                                         n_snps, n_slots, snp_out_base, h1, h2,
+                                                         allow_missing, B, meta, status);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || codes == nullptr) return e;
+  const int64_t n_halves = nchunks * 2;
+  const int64_t grid2 = (n_halves + kPackWarps - 1) / kPackWarps;
+  codes_kernel<<<(unsigned)grid2, kPackWarps * 32, 0, s>>>(geno, ldg, N, Np, snp_list, snp_begin,
+                                                           n_snps, n_halves, codes);
+  return cudaGetLastError();
+}
+
+}  // namespace krux

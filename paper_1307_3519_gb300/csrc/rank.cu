@@ -1,0 +1,206 @@
+// rank.cu -- per-trait average-rank transform (section "Input data": ranks per
+// trait row; section "Handling tied data": average ranks for ties and the factor
+// sum(t^3 - t); section "Handling missing values": NaN samples are left out).
+//
+// One warp per trait.  The row is staged in shared memory and each present
+// sample k counts lo = #{j present: x_j < x_k} and eq = #{j present: x_j == x_k}
+// (k itself included), so 2 * average rank = 2 lo + eq + 1, exactly.  The stored
+// value is the centred integer a = 2 lo + eq - K = 2 rank - (K + 1), |a| <= K-1,
+// which FP16 holds exactly for K <= 512 (integers up to 2048 are exact).  The
+// run containing k has length eq, so sum_k (eq_k^2 - 1) = sum_runs (t^3 - t).
+#include "common.cuh"
+
+namespace krux {
+
+namespace {
+constexpr int kRankWarps = 8;
+
+__global__ void __launch_bounds__(kRankWarps * 32)
+rank_kernel(const float *__restrict__ expr, int T, int N, int64_t ld, int Np, RankDev r) {
+  extern __shared__ float srow[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int t = blockIdx.x * kRankWarps + warp;
+  if (t >= T) return;  // whole warp leaves together; no block-level barrier follows
+  float *x = srow + warp * N;
+  const float *row = expr + (int64_t)t * ld;
+  for (int k = lane; k < N; k += 32) x[k] = row[k];
+  __syncwarp();
+
+  // present count and the list of NaN samples, in sample order
+  int K = 0, nan_seen = 0;
+  for (int k0 = 0; k0 < N; k0 += 32) {
+    const int k = k0 + lane;
+    const bool isn = (k < N) && isnan(x[k]);
+    const bool pres = (k < N) && !isn;
+    const unsigned bn = __ballot_sync(0xffffffffu, isn);
+    K += __popc(__ballot_sync(0xffffffffu, pres));
+    if (isn) r.nan_idx[(int64_t)t * N + nan_seen + __popc(bn & ((1u << lane) - 1u))] = (uint16_t)k;
+    nan_seen += __popc(bn);
+  }
+
+  long long tie = 0;
+  for (int k = lane; k < Np; k += 32) {
+    int a = 0;
+    if (k < N) {
+      const float xk = x[k];
+      uint16_t lo16 = 0, eq16 = 0;
+      if (!isnan(xk)) {
+        int lo = 0, eq = 0;
+        int j = 0;
+        for (; j + 4 <= N; j += 4) {
+          const float x0 = x[j], x1 = x[j + 1], x2 = x[j + 2], x3 = x[j + 3];
+          lo += (x0 < xk) + (x1 < xk) + (x2 < xk) + (x3 < xk);
+          eq += (x0 == xk) + (x1 == xk) + (x2 == xk) + (x3 == xk);
+        }
+        for (; j < N; ++j) {
+          lo += (x[j] < xk);
+          eq += (x[j] == xk);
+        }
+        lo16 = (uint16_t)lo;
+        eq16 = (uint16_t)eq;
+        tie += (long long)eq * eq - 1;
+        a = 2 * lo + eq - K;
+      }
+      r.lo[(int64_t)t * N + k] = lo16;
+      r.eq[(int64_t)t * N + k] = eq16;
+    }
+    r.A[(int64_t)t * Np + k] = __int2half_rn(a);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) tie += __shfl_xor_sync(0xffffffffu, tie, o);
+
+  if (lane == 0) {
+    r.tie[t] = tie;
+    r.K[t] = K;
+    r.nan_cnt[t] = (uint16_t)(N - K);
+    if (N - K > 0) atomicOr(&r.tile_nan[t / kTileM], 1u);
+    // tie factor C = 1 - sum(t^3-t)/(K^3-K); H = 3/(K(K+1)C) * sum_i D_i^2/N_i
+    const double Kd = (double)K;
+    const double C = K >= 2 ? 1.0 - (double)tie / (Kd * Kd * Kd - Kd) : 0.0;
+    if (K >= 2 && C > 0.0) {
+      const double s = Kd * (Kd + 1.0) * C;
+      r.cfac[t] = 3.0 / s;
+      r.tau[t] = (float)(s / 3.0);
+    } else {
+      r.cfac[t] = 0.0;
+      r.tau[t] = __int_as_float(0x7f800000);  // +inf: never a hit
+    }
+  }
+}
+
+// out[p][row][k] = A[row][perm_p[k]] for k < N (padding columns stay 0): the
+// rank matrix of the expression with its sample columns permuted (ranks, tie
+// sums and K are invariant under a column permutation).
+__global__ void permute_rows_kernel(const __half *__restrict__ A, __half *__restrict__ out,
+                                    int rows_pad, int Np, int N, const int32_t *__restrict__ perms,
+                                    int P) {
+  const int64_t total = (int64_t)P * rows_pad * Np;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int k = (int)(i % Np);
+    const int64_t pr = i / Np;
+    const int row = (int)(pr % rows_pad);
+    const int p = (int)(pr / rows_pad);
+    __half v = __int2half_rn(0);
+    if (k < N) v = A[(int64_t)row * Np + perms[(int64_t)p * N + k]];
+    out[i] = v;
+  }
+}
+}  // namespace
+
+cudaError_t launch_rank(const float *expr, int T, int N, int64_t ld, int Np, int rows_pad,
+                        const RankDev &r, cudaStream_t s) {
+  (void)rows_pad;
+  const int grid = (T + kRankWarps - 1) / kRankWarps;
+  const size_t smem = (size_t)kRankWarps * N * sizeof(float);
+  rank_kernel<<<grid, kRankWarps * 32, smem, s>>>(expr, T, N, ld, Np, r);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_permute_rows(const __half *A, __half *out, int rows_pad, int Np, int N,
+                                const int32_t *perms, int P, cudaStream_t s) {
+  const int64_t total = (int64_t)P * rows_pad * Np;
+  int grid = (int)((total + 255) / 256);
+  if (grid > 152 * 16) grid = 152 * 16;
+  permute_rows_kernel<<<grid, 256, 0, s>>>(A, out, rows_pad, Np, N, perms, P);
+  return cudaGetLastError();
+}
+
+}  // namespace krux
+
+// ---------------------------------------------------------------------------
+// Ranks of every trait over the samples left after dropping a missing-genotype
+// pattern (section "Handling missing values": a new expression matrix with the
+// samples of the pattern removed, re-ranked).  No re-sort: for present samples,
+// x_q < x_k exactly when lo_q < lo_k and x_q == x_k exactly when lo_q == lo_k,
+// so lo' = lo - #{q dropped, present, lo_q < lo_k} and
+// eq' = eq - #{q dropped, present, lo_q == lo_k}.
+namespace krux {
+namespace {
+__global__ void __launch_bounds__(256)
+rerank_kernel(RankDev base, int T, int N, int Np, const int32_t *__restrict__ drop, int n_drop,
+              RankDev out) {
+  __shared__ uint32_t dmask[kMaxN / 32];
+  __shared__ int32_t dlist[kMaxN];
+  for (int i = threadIdx.x; i < kMaxN / 32; i += blockDim.x) dmask[i] = 0u;
+  __syncthreads();
+  for (int i = threadIdx.x; i < n_drop; i += blockDim.x) {
+    dlist[i] = drop[i];
+    atomicOr(&dmask[drop[i] >> 5], 1u << (drop[i] & 31));
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int t = blockIdx.x * 8 + warp;
+  if (t >= T) return;
+  const uint16_t *lo = base.lo + (int64_t)t * N;
+  const uint16_t *eq = base.eq + (int64_t)t * N;
+  int Kdrop = 0;
+  for (int i = 0; i < n_drop; ++i) Kdrop += eq[dlist[i]] > 0;
+  const int K = base.K[t] - Kdrop;
+  long long tie = 0;
+  for (int k = lane; k < Np; k += 32) {
+    int a = 0;
+    if (k < N && eq[k] > 0 && !((dmask[k >> 5] >> (k & 31)) & 1u)) {
+      const int lk = lo[k];
+      int l = lk, e = eq[k];
+      for (int i = 0; i < n_drop; ++i) {
+        const int q = dlist[i];
+        if (eq[q] > 0) {
+          l -= lo[q] < lk;
+          e -= lo[q] == lk;
+        }
+      }
+      tie += (long long)e * e - 1;
+      a = 2 * l + e - K;
+    }
+    out.A[(int64_t)t * Np + k] = __int2half_rn(a);
+  }
+  for (int k = lane; k < N; k += 32) out.nan_idx[(int64_t)t * N + k] = base.nan_idx[(int64_t)t * N + k];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) tie += __shfl_xor_sync(0xffffffffu, tie, o);
+  if (lane == 0) {
+    out.tie[t] = tie;
+    out.K[t] = K;
+    const int nc = base.nan_cnt[t];
+    out.nan_cnt[t] = (uint16_t)nc;
+    if (nc > 0) atomicOr(&out.tile_nan[t / kTileM], 1u);
+    const double Kd = (double)K;
+    const double C = K >= 2 ? 1.0 - (double)tie / (Kd * Kd * Kd - Kd) : 0.0;
+    if (K >= 2 && C > 0.0) {
+      const double s = Kd * (Kd + 1.0) * C;
+      out.cfac[t] = 3.0 / s;
+      out.tau[t] = (float)(s / 3.0);
+    } else {
+      out.cfac[t] = 0.0;
+      out.tau[t] = __int_as_float(0x7f800000);
+    }
+  }
+}
+}  // namespace
+
+cudaError_t launch_rerank_bucket(const RankDev &base, int T, int N, int Np, const int32_t *drop,
+                                 int n_drop, const RankDev &out, cudaStream_t s) {
+  rerank_kernel<<<(T + 7) / 8, 256, 0, s>>>(base, T, N, Np, drop, n_drop, out);
+  return cudaGetLastError();
+}
+}  // namespace krux

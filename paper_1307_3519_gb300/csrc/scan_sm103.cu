@@ -1,0 +1,592 @@
+// scan_sm103.cu -- fused Kruskal-Wallis scan for sm_103a (tcgen05 + TMA + TMEM).
+//
+// For a tile of 128 traits and a chunk of 64 SNPs the tensor cores contract the
+// centred rank matrix A (traits x samples, FP16 integers) with the packed
+// indicator rows [I_0 | I_1] of the chunk (Eq. 4: S_i = R I_i^T, here in centred
+// form D_i = 2 S_i - N_i (K+1)), accumulating exact FP32 integers in TMEM.  The
+// epilogue never writes the rank sums to memory: it evaluates Eq. 2 in centred
+// form, H = 3/(K(K+1)C) sum_i D_i^2/N_i with D_2 = -D_0 - D_1 and the tie factor
+// C (section "Handling tied data"), compares it with the chi-square threshold of
+// the SNP's degrees of freedom (section "P-value calculation and empirical FDR
+// correction"), decides pairs within a relative margin of the threshold in
+// FP64, and appends hits with one atomic per warp.
+//
+// Roles (320 threads, one CTA per SM, persistent over work items):
+//   warps 0-7 : epilogue; warp w reads TMEM lanes 32*(w%4).. (traits) and SNP
+//               half w/4 of each chunk
+//   warp 8    : TMA producer (A tiles stream through nA stages; a B tile of nc
+//               chunks stays resident while all trait tiles pass)
+//   warp 9    : TMEM allocator and tcgen05.mma issuer (one thread)
+// Every mbarrier wait is bounded: on timeout the kernel raises an error bit,
+// drains its own asynchronous copies and MMAs, frees TMEM and returns.
+#include "common.cuh"
+
+namespace krux {
+
+namespace {
+
+// tcgen05 instruction descriptor, kind::f16: D = F32, A = B = F16, both K-major,
+// N = 128 (bits 17-22 hold N >> 3), M = 128 (bits 24-28 hold M >> 4).
+constexpr uint32_t kIdesc = (1u << 4) | ((uint32_t)(128 >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+constexpr uint32_t kTileRowsBytes = 128 * 128;  // one 64-element (128 B) K atom of 128 rows
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Shared-memory matrix descriptor for a K-major tile in the 128-byte swizzle
+// layout: 8-row groups 1024 B apart (SBO), leading offset unused, version 1,
+// layout type 2 (128B swizzle).
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1u << 16;
+  d |= (uint64_t)(1024u >> 4) << 32;
+  d |= (uint64_t)1u << 46;
+  d |= (uint64_t)2u << 61;
+  return d;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0u;
+}
+
+struct WaitCtl {
+  volatile int *abort_flag;
+  unsigned int *status;
+  long long limit;
+};
+
+// Bounded wait for the phase of parity `parity`; false on timeout or abort.
+__device__ __noinline__ bool wait_bar(uint32_t bar, uint32_t parity, const WaitCtl &w,
+                                      unsigned int where) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (true) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (*w.abort_flag) return false;
+    if (clock64() - t0 > w.limit) {
+      *w.abort_flag = 1;
+      atomicOr(w.status, kDevTimeout);
+      atomicMax(w.status + 1, where);
+      return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, "
+      "%3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes,
+                                          uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void prefetch_map(const CUtensorMap *map) {
+  asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t da, uint64_t db, uint32_t idesc,
+                                       uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+      "l"(da), "l"(db), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+
+#define KRUX_LD32_REGS(r)                                                                       \
+  "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),          \
+      "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),  \
+      "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),            \
+      "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),            \
+      "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+
+// 32 consecutive fp32 columns of this warp's 32 TMEM lanes (one lane per thread).
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+      "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : KRUX_LD32_REGS(r)
+      : "r"(taddr)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Scaled quadratic form minus the trait's bound: alpha (u + beta v)^2 + gamma v^2 + nt.
+__device__ __forceinline__ float kw_q(float u, float v, float al, float be, float ga, float nt) {
+  const float w = fmaf(be, v, u);
+  const float e = ga * v;
+  const float q = fmaf(e, v, nt);
+  const float f = al * w;
+  return fmaf(f, w, q);
+}
+
+// p-value of the pair in FP64 from the exact centred sums and group sizes.
+__device__ __forceinline__ double kw_p64(double H, int df) {
+  if (df == 1) return erfc(sqrt(0.5 * H));
+  if (df == 2) return exp(-0.5 * H);
+  return 1.0;
+}
+__device__ __forceinline__ double kw_H64(int u, int v, int n0, int n1, int n2, double cfac) {
+  const double D0 = (double)u, D1 = (double)v, D2 = -(double)(u + v);
+  double Q = 0.0;
+  if (n0 > 0) Q += D0 * D0 / (double)n0;
+  if (n1 > 0) Q += D1 * D1 / (double)n1;
+  if (n2 > 0) Q += D2 * D2 / (double)n2;
+  return cfac * Q;
+}
+
+struct EpiTrait {
+  int trait;        // global trait row of this thread (may be >= T in the last tile)
+  bool valid;
+  float ntlo, nthi; // -tau (1 -/+ margin)
+  double cfac;
+  int nan_cnt;      // 0 unless the rank set has NaN in this trait
+  const uint16_t *nan_idx;
+};
+
+// Group sizes of a pair after removing the trait's NaN samples (section
+// "Handling missing values": N_i(n,m) counts the samples present for both).
+__device__ __forceinline__ void pair_counts(const EpiTrait &et, const ChunkMeta &m,
+                                            const uint64_t *codes, int h, int jj, int j,
+                                            int &n0, int &n1, int &n2) {
+  n0 = m.n[0][jj];
+  n1 = m.n[1][jj];
+  n2 = m.n[2][jj];
+  for (int i = 0; i < et.nan_cnt; ++i) {
+    const int k = et.nan_idx[i];
+    const int code = (int)((codes[k * 2 + h] >> (2 * j)) & 3ull);
+    n0 -= code == 0;
+    n1 -= code == 1;
+    n2 -= code == 2;
+  }
+}
+
+__device__ __forceinline__ int df_of(int n0, int n1, int n2) {
+  const int g = (n0 > 0) + (n1 > 0) + (n2 > 0);
+  return g > 0 ? g - 1 : 0;
+}
+
+// Epilogue of one (trait tile, chunk half): 32 SNPs x this thread's trait.
+__device__ __forceinline__ void epilogue_chunk(const uint32_t (&d0)[32], const uint32_t (&d1)[32],
+                                               const ChunkMeta &m, const uint64_t *codes, int h,
+                                               const EpiTrait &et, const GroupDesc &g,
+                                               const ScanParams &p, int lane) {
+  const int jb = 32 * h;
+  uint32_t hitmask = 0;
+  if (p.dense) {
+    // every pair in FP64 (small problems): H, p written densely
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      const int snp = m.snp[jb + j];
+      if (et.valid && snp >= 0) {
+        int n0, n1, n2;
+        pair_counts(et, m, codes, h, jb + j, j, n0, n1, n2);
+        const int u = (int)__uint_as_float(d0[j]), v = (int)__uint_as_float(d1[j]);
+        const int df = df_of(n0, n1, n2);
+        const double H = df > 0 ? kw_H64(u, v, n0, n1, n2, et.cfac) : 0.0;
+        const double pv = df > 0 && et.cfac > 0.0 ? kw_p64(H, df) : 1.0;
+        const int64_t o = (int64_t)et.trait * g.dense_ld + (snp - g.dense_snp0);
+        g.dense_H[o] = et.cfac > 0.0 ? H : 0.0;
+        g.dense_p[o] = pv;
+        if (pv < p.pthresh) hitmask |= 1u << j;
+      }
+    }
+  } else if (et.nan_cnt == 0) {
+    uint32_t acc = 0xffffffffu;
+    const float *al = m.alpha + jb, *be = m.beta + jb, *ga = m.gamma + jb;
+#pragma unroll
+    for (int j = 0; j < 32; j += 4) {
+      const float4 A4 = *reinterpret_cast<const float4 *>(al + j);
+      const float4 B4 = *reinterpret_cast<const float4 *>(be + j);
+      const float4 G4 = *reinterpret_cast<const float4 *>(ga + j);
+      const float q0 = kw_q(__uint_as_float(d0[j]), __uint_as_float(d1[j]), A4.x, B4.x, G4.x, et.ntlo);
+      const float q1 = kw_q(__uint_as_float(d0[j + 1]), __uint_as_float(d1[j + 1]), A4.y, B4.y, G4.y, et.ntlo);
+      const float q2 = kw_q(__uint_as_float(d0[j + 2]), __uint_as_float(d1[j + 2]), A4.z, B4.z, G4.z, et.ntlo);
+      const float q3 = kw_q(__uint_as_float(d0[j + 3]), __uint_as_float(d1[j + 3]), A4.w, B4.w, G4.w, et.ntlo);
+      acc &= __float_as_uint(q0) & __float_as_uint(q1);
+      acc &= __float_as_uint(q2) & __float_as_uint(q3);
+    }
+    if ((int)acc >= 0) {
+      // some pair is at or above the lower edge of the band: classify each
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const float u = __uint_as_float(d0[j]), v = __uint_as_float(d1[j]);
+        const float ql = kw_q(u, v, al[j], be[j], ga[j], et.ntlo);
+        if (ql >= 0.f && m.snp[jb + j] >= 0) {
+          const float qh = kw_q(u, v, al[j], be[j], ga[j], et.nthi);
+          bool hit = qh > 0.f;
+          if (!hit) {
+            const int n0 = m.n[0][jb + j], n1 = m.n[1][jb + j], n2 = m.n[2][jb + j];
+            const double H = kw_H64((int)u, (int)v, n0, n1, n2, et.cfac);
+            hit = kw_p64(H, m.df[jb + j]) < p.pthresh;
+          }
+          if (hit) hitmask |= 1u << j;
+        }
+      }
+    }
+  } else {
+    // trait with NaN samples: per-pair group sizes, FP32 test, FP64 near the bound
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      if (m.snp[jb + j] >= 0) {
+        int n0, n1, n2;
+        pair_counts(et, m, codes, h, jb + j, j, n0, n1, n2);
+        const int df = df_of(n0, n1, n2);
+        if (df > 0) {
+          const float u = __uint_as_float(d0[j]), v = __uint_as_float(d1[j]), w = -(u + v);
+          float Q = 0.f;
+          if (n0 > 0) Q += u * u / (float)n0;
+          if (n1 > 0) Q += v * v / (float)n1;
+          if (n2 > 0) Q += w * w / (float)n2;
+          const float hq = (float)et.cfac * Q;
+          const float h = df == 1 ? p.h1 : p.h2;
+          if (hq > h * (1.f - p.margin)) {
+            bool hit = hq > h * (1.f + p.margin);
+            if (!hit) hit = kw_p64(kw_H64((int)u, (int)v, n0, n1, n2, et.cfac), df) < p.pthresh;
+            if (hit) hitmask |= 1u << j;
+          }
+        }
+      }
+    }
+  }
+
+  if (!__any_sync(0xffffffffu, hitmask != 0u)) return;
+  // warp-aggregated append: one atomic per warp
+  const int cnt = __popc(hitmask);
+  int incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  const int total = __shfl_sync(0xffffffffu, incl, 31);
+  unsigned long long base = 0;
+  if (lane == 0) base = atomicAdd(g.counter, (unsigned long long)total);
+  base = __shfl_sync(0xffffffffu, base, 0);
+  unsigned long long idx = base + (unsigned long long)(incl - cnt);
+  const unsigned long long cap = (unsigned long long)g.capacity;
+#pragma unroll
+  for (int j = 0; j < 32; ++j) {
+    if ((hitmask >> j) & 1u) {
+      if (idx < cap) {
+        int n0, n1, n2;
+        pair_counts(et, m, codes, h, jb + j, j, n0, n1, n2);
+        krux_hit r;
+        r.trait = (uint32_t)et.trait;
+        r.snp = (uint32_t)m.snp[jb + j];
+        r.d0 = (int32_t)__uint_as_float(d0[j]);
+        r.d1 = (int32_t)__uint_as_float(d1[j]);
+        g.hits[idx] = r;
+        HitAux a;
+        a.n0 = (uint16_t)n0;
+        a.n1 = (uint16_t)n1;
+        a.n2 = (uint16_t)n2;
+        a.group = (uint16_t)g.group_id;
+        g.aux[idx] = a;
+      }
+      ++idx;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kScanThreads, 1) krux_scan_kernel(const ScanParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  uint8_t *sbase = smem_raw + (base - raw);
+  const uint32_t tile_bytes = 128u * (uint32_t)p.kpad * 2u;
+  const uint32_t sA = base;
+  const uint32_t sB = base + (uint32_t)p.nA * tile_bytes;
+  ChunkMeta *smeta = reinterpret_cast<ChunkMeta *>(sbase + (size_t)(p.nA + p.nc) * tile_bytes);
+  uint8_t *scodes = reinterpret_cast<uint8_t *>(smeta + p.nc);
+  const uint32_t codes_stride = (uint32_t)p.kpad * 16u;
+  uint64_t *bars = reinterpret_cast<uint64_t *>(scodes + (size_t)p.nc * codes_stride);
+  const uint32_t bar0 = smem_u32(bars);
+  const int nA = p.nA, nc = p.nc;
+  // barrier addresses
+  auto a_full = [&](int s) { return bar0 + 8u * (uint32_t)s; };
+  auto a_empty = [&](int s) { return bar0 + 8u * (uint32_t)(nA + s); };
+  auto b_full = [&](int c) { return bar0 + 8u * (uint32_t)(2 * nA + c); };
+  auto b_empty = [&](int c) { return bar0 + 8u * (uint32_t)(2 * nA + nc + c); };
+  auto t_full = [&](int s) { return bar0 + 8u * (uint32_t)(2 * nA + 2 * nc + s); };
+  auto t_empty = [&](int s) { return bar0 + 8u * (uint32_t)(2 * nA + 2 * nc + kTmemSlots + s); };
+  const uint32_t drain = bar0 + 8u * (uint32_t)(2 * nA + 2 * nc + 2 * kTmemSlots);
+  uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bars + 2 * nA + 2 * nc + 2 * kTmemSlots + 1);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_holder + 1);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < nA; ++s) {
+      mbar_init(a_full(s), 1);
+      mbar_init(a_empty(s), 1);
+    }
+    for (int c = 0; c < nc; ++c) {
+      mbar_init(b_full(c), 1);
+      mbar_init(b_empty(c), 1 + kEpiWarps);
+    }
+    for (int s = 0; s < kTmemSlots; ++s) {
+      mbar_init(t_full(s), 1);
+      mbar_init(t_empty(s), kEpiWarps);
+    }
+    mbar_init(drain, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == kMmaWarp) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
+                     smem_u32(tmem_holder))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_holder;
+  const WaitCtl wc{abort_flag, p.status, p.timeout_cycles};
+
+  if (warp == kProducerWarp) {
+    if (lane == 0) {
+      uint32_t a_stage = 0, a_phase = 0, b_bits = 0;
+      uint32_t a_used = 0, a_last = 0, b_used = 0, b_last = 0;
+      for (int it = blockIdx.x; it < p.n_items; it += gridDim.x) {
+        const WorkItem w = p.items[it];
+        const GroupDesc *g = p.groups + w.group;
+        prefetch_map(&g->tmA);
+        prefetch_map(&g->tmB);
+        const int nc_item = min(nc, g->nchunks - w.btile * nc);
+        const uint32_t tile_tx = (uint32_t)g->n_atoms * kTileRowsBytes;
+        const uint32_t codes_bytes = g->codes ? (uint32_t)g->Np * 16u : 0u;
+        for (int c = 0; c < nc_item; ++c) {
+          const uint32_t ph = (b_bits >> c) & 1u;
+          if (!wait_bar(b_empty(c), ph ^ 1u, wc, 1)) goto producer_done;
+          const int chunk = w.btile * nc + c;
+          mbar_expect_tx(b_full(c), tile_tx + (uint32_t)sizeof(ChunkMeta) + codes_bytes);
+          for (int a = 0; a < g->n_atoms; ++a)
+            tma_load_2d(sB + (uint32_t)c * tile_bytes + (uint32_t)a * kTileRowsBytes, &g->tmB,
+                        a * kAtomK, chunk * kChunkRows, b_full(c));
+          bulk_load(smem_u32(smeta + c), g->meta + chunk, (uint32_t)sizeof(ChunkMeta), b_full(c));
+          if (codes_bytes)
+            bulk_load(smem_u32(scodes + (size_t)c * codes_stride), g->codes + (size_t)chunk * g->Np * 2,
+                      codes_bytes, b_full(c));
+          b_used |= 1u << c;
+          b_last = (b_last & ~(1u << c)) | (ph << c);
+          b_bits ^= 1u << c;
+        }
+        for (int step = w.step_begin; step < w.step_end; ++step) {
+          const int ag = step / g->n_ttiles, tt = step - ag * g->n_ttiles;
+          const int row0 = ag * g->rows_per_agroup + tt * kTileM;
+          if (!wait_bar(a_empty(a_stage), a_phase ^ 1u, wc, 2)) goto producer_done;
+          mbar_expect_tx(a_full(a_stage), tile_tx);
+          for (int a = 0; a < g->n_atoms; ++a)
+            tma_load_2d(sA + (uint32_t)a_stage * tile_bytes + (uint32_t)a * kTileRowsBytes, &g->tmA,
+                        a * kAtomK, row0, a_full(a_stage));
+          a_used |= 1u << a_stage;
+          a_last = (a_last & ~(1u << a_stage)) | (a_phase << a_stage);
+          if (++a_stage == (uint32_t)nA) {
+            a_stage = 0;
+            a_phase ^= 1u;
+          }
+        }
+      }
+    producer_done:
+      // let every copy this thread issued land before the CTA can exit
+      for (int s = 0; s < nA; ++s)
+        if ((a_used >> s) & 1u) wait_bar(a_full(s), (a_last >> s) & 1u, wc, 10);
+      for (int c = 0; c < nc; ++c)
+        if ((b_used >> c) & 1u) wait_bar(b_full(c), (b_last >> c) & 1u, wc, 11);
+    }
+    __syncwarp();
+  } else if (warp == kMmaWarp) {
+    if (lane == 0) {
+      uint32_t a_stage = 0, a_phase = 0, b_bits = 0, slot = 0, slot_phase = 0;
+      for (int it = blockIdx.x; it < p.n_items; it += gridDim.x) {
+        const WorkItem w = p.items[it];
+        const GroupDesc *g = p.groups + w.group;
+        const int nc_item = min(nc, g->nchunks - w.btile * nc);
+        const int ksteps = g->Np / 16;
+        for (int step = w.step_begin; step < w.step_end; ++step) {
+          if (!wait_bar(a_full(a_stage), a_phase, wc, 3)) goto mma_done;
+          tc_fence_after();
+          for (int c = 0; c < nc_item; ++c) {
+            if (step == w.step_begin) {
+              if (!wait_bar(b_full(c), (b_bits >> c) & 1u, wc, 4)) goto mma_done;
+              tc_fence_after();
+            }
+            if (!wait_bar(t_empty(slot), slot_phase ^ 1u, wc, 5)) goto mma_done;
+            tc_fence_after();
+            const uint32_t d_tmem = tmem_base + slot * 128u;
+            const uint32_t a_tile = sA + a_stage * tile_bytes;
+            const uint32_t b_tile = sB + (uint32_t)c * tile_bytes;
+            for (int k = 0; k < ksteps; ++k) {
+              const uint32_t off = (uint32_t)(k >> 2) * kTileRowsBytes + (uint32_t)(k & 3) * 32u;
+              tc_mma(d_tmem, umma_desc(a_tile + off), umma_desc(b_tile + off), kIdesc, k > 0 ? 1u : 0u);
+            }
+            tc_commit(t_full(slot));
+            if (++slot == (uint32_t)kTmemSlots) {
+              slot = 0;
+              slot_phase ^= 1u;
+            }
+          }
+          tc_commit(a_empty(a_stage));
+          if (++a_stage == (uint32_t)nA) {
+            a_stage = 0;
+            a_phase ^= 1u;
+          }
+        }
+        for (int c = 0; c < nc_item; ++c) {
+          tc_commit(b_empty(c));
+          b_bits ^= 1u << c;
+        }
+      }
+    mma_done:
+      // all issued MMAs must finish before TMEM is released
+      tc_commit(drain);
+      wait_bar(drain, 0, wc, 12);
+    }
+    __syncwarp();
+  } else {
+    // epilogue warps
+    const int q = warp & 3, h = warp >> 2;
+    uint32_t slot = 0, slot_phase = 0, b_bits = 0;
+    for (int it = blockIdx.x; it < p.n_items; it += gridDim.x) {
+      const WorkItem w = p.items[it];
+      const GroupDesc &g = p.groups[w.group];
+      const int nc_item = min(nc, g.nchunks - w.btile * nc);
+      for (int step = w.step_begin; step < w.step_end; ++step) {
+        const int ag = step / g.n_ttiles, tt = step - ag * g.n_ttiles;
+        EpiTrait et;
+        et.trait = tt * kTileM + 32 * q + lane;
+        et.valid = et.trait < g.T;
+        const float tau = et.valid ? g.tau[et.trait] : __int_as_float(0x7f800000);
+        et.ntlo = -tau * (1.f - p.margin);
+        et.nthi = -tau * (1.f + p.margin);
+        et.cfac = et.valid ? g.cfac[et.trait] : 0.0;
+        et.nan_cnt = 0;
+        et.nan_idx = nullptr;
+        if (g.nan_cnt != nullptr && et.valid) {
+          et.nan_cnt = g.nan_cnt[et.trait];
+          et.nan_idx = g.nan_idx + (int64_t)et.trait * g.N;
+        }
+        (void)ag;
+        for (int c = 0; c < nc_item; ++c) {
+          bool ok = true;
+          if (step == w.step_begin) ok = wait_bar(b_full(c), (b_bits >> c) & 1u, wc, 6);
+          ok = ok && wait_bar(t_full(slot), slot_phase, wc, 7);
+          if (!__all_sync(0xffffffffu, ok)) goto epi_done;
+          tc_fence_after();
+          uint32_t d0[32], d1[32];
+          const uint32_t taddr = tmem_base + ((uint32_t)(32 * q) << 16) + slot * 128u + 32u * (uint32_t)h;
+          tmem_ld32(taddr, d0);
+          tmem_ld32(taddr + 64u, d1);
+          tmem_wait_ld();
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(t_empty(slot));
+          if (++slot == (uint32_t)kTmemSlots) {
+            slot = 0;
+            slot_phase ^= 1u;
+          }
+          const uint64_t *codes =
+              g.codes ? reinterpret_cast<const uint64_t *>(scodes + (size_t)c * codes_stride) : nullptr;
+          epilogue_chunk(d0, d1, smeta[c], codes, h, et, g, p, lane);
+          if (step == w.step_end - 1) {
+            __syncwarp();
+            if (lane == 0) mbar_arrive(b_empty(c));
+          }
+        }
+      }
+      for (int c = 0; c < nc_item; ++c) b_bits ^= 1u << c;
+    }
+  epi_done:
+    tc_fence_before();
+  }
+
+  __syncthreads();
+  if (warp == kMmaWarp) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem_base) : "memory");
+  }
+}
+
+// FP64 statistic and p-value of each stored hit, from its exact centred sums.
+__global__ void finalize_kernel(const krux_hit *__restrict__ hits, const HitAux *__restrict__ aux,
+                                int64_t n, const double *const *__restrict__ cfac_by_group,
+                                double *__restrict__ H, double *__restrict__ P) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const krux_hit r = hits[i];
+    const HitAux a = aux[i];
+    const double cf = cfac_by_group[a.group][r.trait];
+    const int df = df_of(a.n0, a.n1, a.n2);
+    const double h = kw_H64(r.d0, r.d1, a.n0, a.n1, a.n2, cf);
+    H[i] = h;
+    P[i] = kw_p64(h, df);
+  }
+}
+
+}  // namespace
+
+size_t scan_smem_bytes(int nc, int nA, int kpad) {
+  const size_t tile = (size_t)128 * kpad * 2;
+  return 1024 + (size_t)(nA + nc) * tile + (size_t)nc * sizeof(ChunkMeta) + (size_t)nc * kpad * 16 +
+         8 * (size_t)(2 * nA + 2 * nc + 2 * kTmemSlots + 1) + 16;
+}
+
+cudaError_t launch_scan(const ScanParams &p, int grid, size_t smem, cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(krux_scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  krux_scan_kernel<<<grid, kScanThreads, smem, s>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const krux_hit *hits, const HitAux *aux, int64_t n,
+                            const double *const *cfac_by_group, double *H, double *p,
+                            cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  int grid = (int)((n + 255) / 256);
+  if (grid > 152 * 8) grid = 152 * 8;
+  finalize_kernel<<<grid, 256, 0, s>>>(hits, aux, n, cfac_by_group, H, p);
+  return cudaGetLastError();
+}
+
+}  // namespace krux

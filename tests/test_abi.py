@@ -1,0 +1,69 @@
+"""The C-ABI library builds, loads and exports every function include/krux.h
+declares; host-only entry points work without a GPU."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "krux.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1307_3519_gb300 import build
+    build.build()
+    import paper_1307_3519_gb300 as k
+    return k.load_library()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s*(krux_[a-z_0-9]+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ["krux_rank", "krux_scan", "krux_permute", "krux_scan_plain", "krux_scan_grouped",
+                     "krux_create", "krux_destroy", "krux_make_perms"]:
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    import paper_1307_3519_gb300 as k
+    names = declared_functions()
+    assert sorted(k.EXPORTS) == names
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_status_strings(lib):
+    for s in range(7):
+        assert lib.krux_status_string(s)
+
+
+def test_make_perms_matches_generator(lib):
+    import paper_1307_3519_gb300 as k
+    for seed, P, N in [(1307, 16, 102), (0, 3, 7), (99, 2, 500)]:
+        assert np.array_equal(k.krux_make_perms(seed, P, N), synth.make_perms(seed, P, N))
+
+
+def test_create_without_gpu_reports_an_error(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = ctypes.c_void_p()
+    st = lib.krux_create(ctypes.byref(h), 0)
+    assert st != 0 and not h.value
+
+
+def test_null_arguments_are_rejected(lib):
+    # validation happens before any device work
+    assert lib.krux_create(None, 0) == 1
+    assert lib.krux_set_profiling(None, 1) == 1

@@ -1,0 +1,184 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle."""
+import numpy as np
+import pytest
+
+import synth
+from kwcheck import check_dense, check_hits
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def kx():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1307_3519_gb300 import build
+    build.build()
+    import paper_1307_3519_gb300 as k
+    ctx = k.Krux(0)
+    yield ctx
+    ctx.close()
+
+
+def _dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+# ---------------------------------------------------------------- rank transform
+@pytest.mark.parametrize("T,N,decimals,nan", [(1, 1, 2, 0.0), (7, 5, 1, 0.0), (129, 60, 2, 0.0),
+                                              (300, 102, None, 0.02), (40, 250, 1, 0.05),
+                                              (33, 512, 0, 0.0), (16, 511, None, 0.3)])
+def test_rank_bit_exact(kx, oracle_mod, T, N, decimals, nan):
+    rng = np.random.default_rng(T * 1000 + N)
+    x = rng.standard_normal((T, N))
+    if decimals is not None:
+        x = np.round(x, decimals)
+    x = x.astype(np.float32)
+    x[rng.random((T, N)) < nan] = np.nan
+    if T > 3:
+        x[0] = 1.5            # all tied
+        x[1, : N // 2] = -0.0 # signed zeros tie with zeros
+        x[1, N // 2:] = 0.0
+    rs = kx.krux_rank(_dev(x))
+    c, tie, K = (a.cpu().numpy() for a in kx.export(rs))
+    for t in range(T):
+        r2, otie, oK = oracle_mod.rank_row(x[t])
+        assert K[t] == oK
+        assert tie[t] == int(otie)
+        ok = ~np.isnan(x[t])
+        assert np.array_equal(c[t][ok], r2[ok] - (oK + 1)), f"trait {t}"
+        assert np.all(c[t][~ok] == 0)
+
+
+# ---------------------------------------------------------------- fused scan
+def test_workload1_dense_and_hits(kx, oracle_mod):
+    """Full 60-sample workload: every pair's H and p densely, plus the hit list."""
+    d = synth.config(1)
+    orc = oracle_mod.scan(d["expr"], d["geno"], d["pthresh"])
+    rs = kx.krux_rank(_dev(d["expr"]))
+    res = kx.krux_scan(rs, _dev(d["geno"]), d["pthresh"], capacity=200_000, dense=True)
+    check_dense(res["dense_H"].cpu().numpy(), res["dense_p"].cpu().numpy(), orc)
+    check_hits(res, orc, np.arange(d["T"]), np.arange(d["S"]), d["pthresh"])
+    res2 = kx.krux_scan(rs, _dev(d["geno"]), d["pthresh"], capacity=200_000)
+    check_hits(res2, orc, np.arange(d["T"]), np.arange(d["S"]), d["pthresh"])
+    assert res2["n_hits"] == res["n_hits"] == int(orc["hit"].sum())
+
+
+@pytest.mark.parametrize("N,T,S,pth", [(5, 3, 1, 0.3), (17, 129, 65, 0.05), (33, 200, 300, 0.02),
+                                       (60, 257, 1000, 1e-3), (102, 300, 2500, 1e-3),
+                                       (150, 131, 700, 1e-3), (200, 128, 640, 1e-2),
+                                       (256, 100, 333, 1e-2)])
+def test_scan_hits_ragged(kx, oracle_mod, N, T, S, pth):
+    d = synth.config(2, T=T, S=S, N=N, seed=7 * N + S)
+    orc = oracle_mod.scan(d["expr"], d["geno"], pth)
+    rs = kx.krux_rank(_dev(d["expr"]))
+    res = kx.krux_scan(rs, _dev(d["geno"]), pth, capacity=T * S)
+    check_hits(res, orc, np.arange(T), np.arange(S), pth, must_have_hits=False)
+    assert res["n_hits"] == int(orc["hit"].sum())
+
+
+def test_plain_form_matches(kx, oracle_mod):
+    d = synth.config(2, T=300, S=3000, seed=11)
+    pth = 1e-3
+    orc = oracle_mod.scan(d["expr"], d["geno"], pth)
+    rs = kx.krux_rank(_dev(d["expr"]))
+    g = _dev(d["geno"])
+    a = kx.krux_scan(rs, g, pth, capacity=300 * 3000)
+    b = kx.krux_scan_plain(rs, g, pth, capacity=300 * 3000)
+    check_hits(a, orc, np.arange(300), np.arange(3000), pth)
+    check_hits(b, orc, np.arange(300), np.arange(3000), pth)
+    bd = kx.krux_scan_plain(rs, g, pth, capacity=300 * 3000, dense=True)
+    check_dense(bd["dense_H"].cpu().numpy(), bd["dense_p"].cpu().numpy(), orc)
+
+
+def test_slices_and_overflow(kx, oracle_mod):
+    d = synth.config(1, T=100, S=900, seed=5)
+    pth = 0.02
+    orc = oracle_mod.scan(d["expr"], d["geno"], pth)
+    rs = kx.krux_rank(_dev(d["expr"]))
+    g = _dev(d["geno"])
+    total = int(orc["hit"].sum())
+    assert total > 50
+    parts = []
+    for b, e in [(0, 130), (130, 131), (131, 900)]:
+        r = kx.krux_scan(rs, g, pth, capacity=100 * 900, snp_begin=b, snp_end=e)
+        sub = {k: v[:, b:e] for k, v in orc.items()}
+        check_hits(r, sub, np.arange(100), np.arange(b, e), pth, must_have_hits=False)
+        parts.append(r["n_hits"])
+    assert sum(parts) == total
+    small = kx.krux_scan(rs, g, pth, capacity=10)
+    assert small["overflow"] and small["n_hits"] == total and small["hits"].shape[0] == 10
+    zero = kx.krux_scan(rs, g, pth, capacity=0)
+    assert zero["n_hits"] == total
+
+
+def test_degenerate_inputs(kx, oracle_mod):
+    """Monomorphic SNPs, all-tied traits, a single sample group and S = 0."""
+    d = synth.config(1, T=40, S=200, seed=3)
+    x, g = d["expr"].copy(), d["geno"].copy()
+    x[0] = 0.25
+    x[1, :] = np.arange(60, dtype=np.float32)
+    g[0] = 1
+    g[1] = 0
+    g[2, :30] = 2
+    g[2, 30:] = 0
+    pth = 0.05
+    orc = oracle_mod.scan(x, g, pth)
+    rs = kx.krux_rank(_dev(x))
+    res = kx.krux_scan(rs, _dev(g), pth, capacity=40 * 200, dense=True)
+    check_dense(res["dense_H"].cpu().numpy(), res["dense_p"].cpu().numpy(), orc)
+    check_hits(res, orc, np.arange(40), np.arange(200), pth)
+    empty = kx.krux_scan(rs, _dev(g[:0]), pth, capacity=10)
+    assert empty["n_hits"] == 0
+
+
+def test_bad_genotype_code(kx):
+    import paper_1307_3519_gb300 as k
+    d = synth.config(1, T=10, S=20, seed=1)
+    g = d["geno"].copy()
+    g[5, 7] = 3
+    rs = kx.krux_rank(_dev(d["expr"]))
+    with pytest.raises(k.KruxError) as e:
+        kx.krux_scan(rs, _dev(g), 0.01, capacity=100)
+    assert e.value.status == k.KRUX_EINVAL
+
+
+def test_nan_expression(kx, oracle_mod):
+    d = synth.config(2, T=260, S=1500, seed=21)
+    x = d["expr"].copy()
+    rng = np.random.default_rng(4)
+    x[rng.random(x.shape) < 0.02] = np.nan
+    x[3, :90] = np.nan          # a trait with many missing values
+    x[4, :101] = np.nan         # one present sample: degenerate
+    pth = 1e-3
+    orc = oracle_mod.scan(x, d["geno"], pth)
+    rs = kx.krux_rank(_dev(x))
+    res = kx.krux_scan(rs, _dev(d["geno"]), pth, capacity=260 * 1500)
+    check_hits(res, orc, np.arange(260), np.arange(1500), pth)
+    dn = kx.krux_scan(rs, _dev(d["geno"]), pth, capacity=260 * 1500, dense=True)
+    check_dense(dn["dense_H"].cpu().numpy(), dn["dense_p"].cpu().numpy(), orc)
+
+
+def test_missing_genotypes(kx, oracle_mod):
+    """Missing-value workload at reduced size: -1 genotypes in missing-sample
+    patterns and NaN expression; ranks over the samples present in both."""
+    d = synth.config(3, T=300, S=4000)
+    pth = 1e-3
+    orc = oracle_mod.scan(d["expr"], d["geno"], pth)
+    rs = kx.krux_rank(_dev(d["expr"]))
+    res = kx.krux_scan(rs, _dev(d["geno"]), pth, capacity=300 * 4000)
+    check_hits(res, orc, np.arange(300), np.arange(4000), pth)
+    dn = kx.krux_scan(rs, _dev(d["geno"]), pth, capacity=300 * 4000, dense=True)
+    check_dense(dn["dense_H"].cpu().numpy(), dn["dense_p"].cpu().numpy(), orc)
+
+
+def test_host_end_to_end(kx, oracle_mod):
+    d = synth.config(1, T=50, S=400, seed=8)
+    out = kx.scan_host(d["expr"], d["geno"], 0.01, capacity=50 * 400)
+    orc = oracle_mod.scan(d["expr"], d["geno"], 0.01)
+    assert out["n_hits"] == int(orc["hit"].sum())
+    got = {(int(a), int(b)) for a, b in out["hits"][:, :2]}
+    want = {tuple(x) for x in np.argwhere(orc["hit"]).tolist()}
+    assert got == want
