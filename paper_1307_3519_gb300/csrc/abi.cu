@@ -23,8 +23,8 @@ cudaError_t launch_missing_scan(const int8_t *geno, int64_t ldg, int N, int64_t 
                                 uint64_t *miss_mask, unsigned int *status, cudaStream_t s);
 cudaError_t launch_pack2(const int8_t *geno, int64_t ldg, int N, int Np, const int64_t *snp_list,
                          int64_t snp_begin, int64_t n_snps, int64_t snp_out_base, double h1,
-                         double h2, int allow_missing, __half *B, ChunkMeta *meta,
-                         uint64_t *codes, unsigned int *status, cudaStream_t s);
+                         double h2, int allow_missing, int signed_df1, __half *B,
+                         ChunkMeta *meta, uint64_t *codes, unsigned int *status, cudaStream_t s);
 cudaError_t launch_rerank_bucket(const RankDev &base, int T, int N, int Np, const int32_t *drop,
                                  int n_drop, const RankDev &out, cudaStream_t s);
 cudaError_t launch_plain_epilogue2(const float *C, int64_t ldc, int T, int n_slots,
@@ -115,7 +115,7 @@ struct krux_ctx {
   PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   cudaEvent_t ev[kEv] = {};
   DevBuf B, meta, codes, groups, items, status, counters, aux, cfacptr, miss_idx, miss_mask,
-      list, gemm_out, bucket_ranks, permA;
+      list, gemm_out, bucket_ranks, permA, minpkey;
   void *blas = nullptr;
   std::vector<std::pair<size_t, void *>> pool;  // freed rank-set blocks, reused by size
 };
@@ -348,7 +348,7 @@ void krux_destroy(krux_ctx *ctx) {
   cudaSetDevice(ctx->device);
   DevBuf *bufs[] = {&ctx->B, &ctx->meta, &ctx->codes, &ctx->groups, &ctx->items, &ctx->status,
                     &ctx->counters, &ctx->aux, &ctx->cfacptr, &ctx->miss_idx, &ctx->miss_mask,
-                    &ctx->list, &ctx->gemm_out, &ctx->bucket_ranks, &ctx->permA};
+                    &ctx->list, &ctx->gemm_out, &ctx->bucket_ranks, &ctx->permA, &ctx->minpkey};
   for (DevBuf *b : bufs) b->release();
   for (auto &pb : ctx->pool) cudaFree(pb.second);
   for (int i = 0; i < kEv; ++i)
@@ -729,6 +729,8 @@ krux_status run_fused(krux_ctx *ctx, CallPlan &cp, const krux_opts *o, cudaStrea
   const double h1 = h_df1(o->pthresh), h2 = h_df2(o->pthresh);
   const int ng = (int)cp.groups.size();
   const int nslots = (int)cp.slots.size();
+  int signed_coef = 0;
+  for (auto &g : cp.groups) signed_coef |= g.minp_key != nullptr ? 1 : 0;
   counts.assign(nslots, 0);
   if (ng == 0) return KRUX_OK;
   int kpad = kAtomK;
@@ -767,7 +769,7 @@ krux_status run_fused(krux_ctx *ctx, CallPlan &cp, const krux_opts *o, cudaStrea
     ChunkMeta *meta = ctx->meta.as<ChunkMeta>() + moff[i];
     uint64_t *codes = g.nan_cnt ? ctx->codes.as<uint64_t>() + coff[i] : nullptr;
     KRUX_CUDA(ctx, launch_pack2(g.geno, g.ldg, rs->N, rs->Np, g.snp_list, g.snp_begin, g.n_snps, 0,
-                                h1, h2, g.allow_missing, B, meta, codes, status, s));
+                                h1, h2, g.allow_missing, signed_coef, B, meta, codes, status, s));
     GroupDesc &d = plans[i].d;
     std::memset(&d, 0, sizeof d);
     const int64_t nch = (g.n_snps + kChunkSnps - 1) / kChunkSnps;
@@ -827,6 +829,7 @@ krux_status run_fused(krux_ctx *ctx, CallPlan &cp, const krux_opts *o, cudaStrea
   p.h2 = (float)h2;
   p.status = status;
   p.timeout_cycles = ctx->wait_limit;
+  p.signed_coef = signed_coef;
   const int grid = (int)std::min<size_t>(items.size(), (size_t)ctx->sm_count);
   if (grid > 0) KRUX_CUDA(ctx, launch_scan(p, grid, scan_smem_bytes(nc, nA, kpad), s));
   ev_record(ctx, 4, s);
@@ -1003,7 +1006,7 @@ extern "C" krux_status krux_scan_plain(krux_ctx *ctx, const krux_rankset *rs, co
   KRUX_CUDA(ctx, cudaMemsetAsync(ctx->counters.p, 0, 64, s));
   KRUX_CUDA(ctx, cudaMemsetAsync(ctx->status.p, 0, 64, s));
   ev_record(ctx, 2, s);
-  KRUX_CUDA(ctx, launch_pack2(geno, ldg, rs->N, rs->Np, nullptr, b, n, 0, h1, h2, 0,
+  KRUX_CUDA(ctx, launch_pack2(geno, ldg, rs->N, rs->Np, nullptr, b, n, 0, h1, h2, 0, 0,
                               ctx->B.as<__half>(), ctx->meta.as<ChunkMeta>(), nullptr,
                               ctx->status.as<unsigned int>(), s));
   ev_record(ctx, 3, s);
@@ -1063,7 +1066,55 @@ extern "C" krux_status krux_permute(krux_ctx *ctx, const krux_rankset *rs, const
                                     int64_t S, int64_t ldg, const int32_t *perms, int P,
                                     const krux_opts *opts, double *minp, krux_hit *hits,
                                     double *hit_H, double *hit_p, int64_t *n_hits, void *stream) {
-  (void)rs; (void)geno; (void)S; (void)ldg; (void)perms; (void)P; (void)opts; (void)minp;
-  (void)hits; (void)hit_H; (void)hit_p; (void)n_hits; (void)stream;
-  return fail(ctx, KRUX_EUNSUPPORTED, "krux_permute is not available in this build yet");
+  krux_status st = check_scan_args(ctx, rs, geno, S, ldg, opts, hits, hit_H, hit_p, n_hits);
+  if (st != KRUX_OK) return st;
+  *n_hits = 0;
+  if (P < 1 || !perms || !minp) return fail(ctx, KRUX_EINVAL, "need P >= 1, perms and minp");
+  if (opts->dense_H) return fail(ctx, KRUX_EINVAL, "dense output is not available with permutations");
+  cudaStream_t s = (cudaStream_t)stream;
+  KRUX_CUDA(ctx, cudaSetDevice(ctx->device));
+  const int N = rs->N;
+  // every row must be a permutation of 0..N-1 (checked on the host before any gather)
+  std::vector<int32_t> hp((size_t)P * N);
+  KRUX_CUDA(ctx, cudaMemcpyAsync(hp.data(), perms, hp.size() * 4, cudaMemcpyDeviceToHost, s));
+  KRUX_CUDA(ctx, cudaStreamSynchronize(s));
+  for (int q = 0; q < P; ++q) {
+    std::vector<char> seen(N, 0);
+    for (int k = 0; k < N; ++k) {
+      const int32_t v = hp[(size_t)q * N + k];
+      if (v < 0 || v >= N || seen[v]) return fail(ctx, KRUX_EINVAL, "perms row %d is not a permutation", q);
+      seen[v] = 1;
+    }
+  }
+  const int64_t b = opts->snp_begin, e = opts->snp_end > 0 ? opts->snp_end : S;
+  if (ctx->profiling) {
+    ctx->prof = krux_profile{};
+    ctx->prof.pairs = (int64_t)rs->T * (e - b) * (1 + P);
+  }
+  const size_t one = (size_t)rs->rows_pad * rs->Np;
+  KRUX_CUDA(ctx, ctx->permA.ensure(one * 2 * (size_t)(1 + P)));
+  __half *stack = ctx->permA.as<__half>();
+  KRUX_CUDA(ctx, cudaMemcpyAsync(stack, rs->dev.A, one * 2, cudaMemcpyDeviceToDevice, s));
+  KRUX_CUDA(ctx, launch_permute_rows(rs->dev.A, stack + one, rs->rows_pad, rs->Np, N, perms, P, s));
+  KRUX_CUDA(ctx, ctx->minpkey.ensure((size_t)P * rs->T * 8));
+  KRUX_CUDA(ctx, cudaMemsetAsync(ctx->minpkey.p, 0, (size_t)P * rs->T * 8, s));
+  KRUX_CUDA(ctx, ctx->aux.ensure((size_t)std::max<int64_t>(opts->hit_capacity, 1) * sizeof(HitAux)));
+  CallPlan cp;
+  cp.slots.push_back(OutSlot{hits, hit_H, hit_p, opts->hit_capacity, ctx->aux.as<HitAux>()});
+  st = plan_groups(ctx, cp, rs, geno, ldg, b, e, stack, 1 + P, 0, nullptr, nullptr,
+                   ctx->minpkey.as<double>(), s);
+  if (st != KRUX_OK) return st;
+  st = materialise(ctx, cp, s);
+  if (st != KRUX_OK) return st;
+  std::vector<unsigned long long> counts;
+  st = run_fused(ctx, cp, opts, s, counts);
+  if (st != KRUX_OK) return st;
+  KRUX_CUDA(ctx, launch_minp_from_key(ctx->minpkey.as<double>(), minp, (int64_t)P * rs->T, s));
+  KRUX_CUDA(ctx, cudaStreamSynchronize(s));
+  if (ctx->profiling) ctx->prof.launches += 2;
+  *n_hits = (int64_t)counts[0];
+  if (*n_hits > opts->hit_capacity)
+    return fail(ctx, KRUX_EOVERFLOW, "%lld hits exceed capacity %lld", (long long)*n_hits,
+                (long long)opts->hit_capacity);
+  return KRUX_OK;
 }

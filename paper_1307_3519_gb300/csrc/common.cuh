@@ -104,6 +104,8 @@ struct ScanParams {
   float h1, h2;             // chi-square thresholds at pthresh for df 1, 2 (fp32)
   unsigned int *status;     // [0] error bits, [1] where
   long long timeout_cycles;
+  int32_t signed_coef;      // 1: df-1 SNPs carry negated alpha, gamma (permutation batches)
+  int32_t pad_;
 };
 
 enum : unsigned int {
@@ -118,6 +120,7 @@ cudaError_t launch_permute_rows(const __half *A, __half *out, int rows_pad, int 
                                 const int32_t *perms, int P, cudaStream_t s);
 cudaError_t launch_scan(const ScanParams &p, int grid, size_t smem, cudaStream_t s);
 size_t scan_smem_bytes(int nc, int nA, int kpad);
+cudaError_t launch_minp_from_key(const double *key, double *minp, int64_t n, cudaStream_t s);
 cudaError_t launch_finalize(const krux_hit *hits, const HitAux *aux, int64_t n,
                             const double *const *cfac_by_group, double *H, double *p,
                             cudaStream_t s);

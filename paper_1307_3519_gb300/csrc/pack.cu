@@ -57,7 +57,8 @@ __global__ void __launch_bounds__(kPackWarps * 32)
 pack_kernel(const int8_t *__restrict__ geno, int64_t ldg, int N, int Np,
             const int64_t *__restrict__ snp_list, int64_t snp_begin, int64_t n_snps,
             int64_t n_slots, int64_t snp_out_base, double h1, double h2, int allow_missing,
-            __half *__restrict__ B, ChunkMeta *__restrict__ meta, unsigned int *status) {
+            int signed_df1, __half *__restrict__ B, ChunkMeta *__restrict__ meta,
+            unsigned int *status) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t j = (int64_t)blockIdx.x * kPackWarps + warp;
   if (j >= n_slots) return;
@@ -119,9 +120,10 @@ pack_kernel(const int8_t *__restrict__ geno, int64_t ldg, int N, int Np,
       const double q0 = n0 ? 1.0 / n0 : 0.0, q1 = n1 ? 1.0 / n1 : 0.0, q2 = n2 ? 1.0 / n2 : 0.0;
       const double a = q0 + q2;
       const double h = df == 1 ? h1 : h2;
-      al = (float)(a / h);
+      const double sg = (signed_df1 && df == 1) ? -1.0 : 1.0;
+      al = (float)(sg * a / h);
       be = (float)(q2 / a);
-      ga = (float)((q1 + q2 * q0 / a) / h);
+      ga = (float)(sg * (q1 + q2 * q0 / a) / h);
     }
     m.alpha[jj] = al;
     m.beta[jj] = be;
@@ -184,15 +186,15 @@ cudaError_t launch_missing_scan(const int8_t *geno, int64_t ldg, int N, int64_t 
 
 cudaError_t launch_pack2(const int8_t *geno, int64_t ldg, int N, int Np, const int64_t *snp_list,
                          int64_t snp_begin, int64_t n_snps, int64_t snp_out_base, double h1,
-                         double h2, int allow_missing, __half *B, ChunkMeta *meta,
-                         uint64_t *codes, unsigned int *status, cudaStream_t s) {
+                         double h2, int allow_missing, int signed_df1, __half *B,
+                         ChunkMeta *meta, uint64_t *codes, unsigned int *status, cudaStream_t s) {
   const int64_t nchunks = (n_snps + kChunkSnps - 1) / kChunkSnps;
   const int64_t n_slots = nchunks * kChunkSnps;
   if (n_slots == 0) return cudaSuccess;
   const int64_t grid = (n_slots + kPackWarps - 1) / kPackWarps;
   pack_kernel<<<(unsigned)grid, kPackWarps * 32, 0, s>>>(geno, ldg, N, Np, snp_list, snp_begin,
                                                          n_snps, n_slots, snp_out_base, h1, h2,
-                                                         allow_missing, B, meta, status);
+                                                         allow_missing, signed_df1, B, meta, status);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || codes == nullptr) return e;
   const int64_t n_halves = nchunks * 2;

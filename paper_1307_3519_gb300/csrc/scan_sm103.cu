@@ -158,6 +158,32 @@ __device__ __forceinline__ float kw_q(float u, float v, float al, float be, floa
   return fmaf(f, w, q);
 }
 
+// Same quadratic form without the bound; with permutation batches the df-1 SNPs
+// carry negated alpha, gamma so the sign of the result tells the df apart.
+__device__ __forceinline__ float kw_s(float u, float v, float al, float be, float ga) {
+  const float w = fmaf(be, v, u);
+  const float e = ga * v;
+  const float t = e * v;
+  const float f = al * w;
+  return fmaf(f, w, t);
+}
+
+// -ln p for df = 1: -ln erfc(x) = x^2 - ln erfcx(x), x = sqrt(H/2) (no underflow).
+__device__ __forceinline__ float key1f(float H) {
+  const float x2 = 0.5f * H;
+  if (!(x2 > 0.f)) return 0.f;
+  return x2 - logf(erfcxf(sqrtf(x2)));
+}
+__device__ __forceinline__ double key64_of(double H, int df) {
+  if (df == 2) return 0.5 * H;
+  if (df == 1) {
+    const double x2 = 0.5 * H;
+    if (!(x2 > 0.0)) return 0.0;
+    return x2 - log(erfcx(sqrt(x2)));
+  }
+  return 0.0;
+}
+
 // p-value of the pair in FP64 from the exact centred sums and group sizes.
 __device__ __forceinline__ double kw_p64(double H, int df) {
   if (df == 1) return erfc(sqrt(0.5 * H));
@@ -227,6 +253,30 @@ __device__ __forceinline__ void epilogue_chunk(const uint32_t (&d0)[32], const u
         g.dense_H[o] = et.cfac > 0.0 ? H : 0.0;
         g.dense_p[o] = pv;
         if (pv < p.pthresh) hitmask |= 1u << j;
+      }
+    }
+  } else if (et.nan_cnt == 0 && p.signed_coef) {
+    // permutation batch, unpermuted group: |form| against the bound
+    uint32_t acc = 0xffffffffu;
+    const float *al = m.alpha + jb, *be = m.beta + jb, *ga = m.gamma + jb;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      const float q = fabsf(kw_s(__uint_as_float(d0[j]), __uint_as_float(d1[j]), al[j], be[j], ga[j])) + et.ntlo;
+      acc &= __float_as_uint(q);
+    }
+    if ((int)acc >= 0) {
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const float u = __uint_as_float(d0[j]), v = __uint_as_float(d1[j]);
+        const float sv = fabsf(kw_s(u, v, al[j], be[j], ga[j]));
+        if (sv + et.ntlo >= 0.f && m.snp[jb + j] >= 0) {
+          bool hit = sv + et.nthi > 0.f;
+          if (!hit) {
+            const double H = kw_H64((int)u, (int)v, m.n[0][jb + j], m.n[1][jb + j], m.n[2][jb + j], et.cfac);
+            hit = kw_p64(H, m.df[jb + j]) < p.pthresh;
+          }
+          if (hit) hitmask |= 1u << j;
+        }
       }
     }
   } else if (et.nan_cnt == 0) {
@@ -323,6 +373,73 @@ __device__ __forceinline__ void epilogue_chunk(const uint32_t (&d0)[32], const u
         g.aux[idx] = a;
       }
       ++idx;
+    }
+  }
+}
+
+// Running best -ln p of one (permutation, trait) over this thread's SNPs.
+struct MinpState {
+  double best;      // FP64 key of the best pair seen (or the global value at step start)
+  double start;     // value read at step start
+  float best_lo;    // FP32 filter bound: best * (1 - margin)
+  float c1, c2;     // H = c1 * |s| for df-1 SNPs; -ln p = c2 * s for df-2 SNPs
+};
+
+// Permuted group: track the minimum p (maximum -ln p) over 32 SNPs.
+__device__ __forceinline__ void epilogue_minp(const uint32_t (&d0)[32], const uint32_t (&d1)[32],
+                                              const ChunkMeta &m, const uint64_t *codes, int h,
+                                              const EpiTrait &et, const ScanParams &p,
+                                              MinpState &st) {
+  const int jb = 32 * h;
+  if (!et.valid) return;
+  if (et.nan_cnt > 0) {
+    // traits with NaN: exact per pair (group sizes differ per pair)
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      if (m.snp[jb + j] >= 0) {
+        int n0, n1, n2;
+        pair_counts(et, m, codes, h, jb + j, j, n0, n1, n2);
+        const int df = df_of(n0, n1, n2);
+        if (df > 0 && et.cfac > 0.0) {
+          const double key = key64_of(kw_H64((int)__uint_as_float(d0[j]), (int)__uint_as_float(d1[j]),
+                                             n0, n1, n2, et.cfac), df);
+          if (key > st.best) st.best = key;
+        }
+      }
+    }
+    st.best_lo = (float)st.best * (1.f - p.margin);
+    return;
+  }
+  const float *al = m.alpha + jb, *be = m.beta + jb, *ga = m.gamma + jb;
+  float smax = 0.f, smin = 0.f;
+#pragma unroll
+  for (int j = 0; j < 32; j += 4) {
+    const float4 A4 = *reinterpret_cast<const float4 *>(al + j);
+    const float4 B4 = *reinterpret_cast<const float4 *>(be + j);
+    const float4 G4 = *reinterpret_cast<const float4 *>(ga + j);
+    const float s0 = kw_s(__uint_as_float(d0[j]), __uint_as_float(d1[j]), A4.x, B4.x, G4.x);
+    const float s1 = kw_s(__uint_as_float(d0[j + 1]), __uint_as_float(d1[j + 1]), A4.y, B4.y, G4.y);
+    const float s2 = kw_s(__uint_as_float(d0[j + 2]), __uint_as_float(d1[j + 2]), A4.z, B4.z, G4.z);
+    const float s3 = kw_s(__uint_as_float(d0[j + 3]), __uint_as_float(d1[j + 3]), A4.w, B4.w, G4.w);
+    smax = fmaxf(smax, fmaxf(fmaxf(s0, s1), fmaxf(s2, s3)));
+    smin = fminf(smin, fminf(fminf(s0, s1), fminf(s2, s3)));
+  }
+  const float kg = fmaxf(smax * st.c2, key1f(-smin * st.c1));
+  if (kg > st.best_lo) {
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      const float u = __uint_as_float(d0[j]), v = __uint_as_float(d1[j]);
+      const float sv = kw_s(u, v, al[j], be[j], ga[j]);
+      const float kf = sv > 0.f ? sv * st.c2 : key1f(-sv * st.c1);
+      if (kf > st.best_lo && m.snp[jb + j] >= 0) {
+        const int df = m.df[jb + j];
+        const double key =
+            key64_of(kw_H64((int)u, (int)v, m.n[0][jb + j], m.n[1][jb + j], m.n[2][jb + j], et.cfac), df);
+        if (key > st.best) {
+          st.best = key;
+          st.best_lo = (float)key * (1.f - p.margin);
+        }
+      }
     }
   }
 }
@@ -506,7 +623,19 @@ __global__ void __launch_bounds__(kScanThreads, 1) krux_scan_kernel(const ScanPa
           et.nan_cnt = g.nan_cnt[et.trait];
           et.nan_idx = g.nan_idx + (int64_t)et.trait * g.N;
         }
-        (void)ag;
+        const bool minp_mode = g.minp_key != nullptr && ag > 0;
+        MinpState ms;
+        ms.best = 0.0;
+        ms.start = 0.0;
+        ms.c1 = (float)(et.cfac * (double)p.h1);
+        ms.c2 = (float)(et.cfac * (double)p.h2 * 0.5);
+        double *key_ptr = nullptr;
+        if (minp_mode && et.valid) {
+          key_ptr = g.minp_key + (int64_t)(ag - 1) * g.T + et.trait;
+          ms.start = __longlong_as_double((long long)__ldcg(reinterpret_cast<const unsigned long long *>(key_ptr)));
+          ms.best = ms.start;
+        }
+        ms.best_lo = (float)ms.best * (1.f - p.margin);
         for (int c = 0; c < nc_item; ++c) {
           bool ok = true;
           if (step == w.step_begin) ok = wait_bar(b_full(c), (b_bits >> c) & 1u, wc, 6);
@@ -527,12 +656,18 @@ __global__ void __launch_bounds__(kScanThreads, 1) krux_scan_kernel(const ScanPa
           }
           const uint64_t *codes =
               g.codes ? reinterpret_cast<const uint64_t *>(scodes + (size_t)c * codes_stride) : nullptr;
-          epilogue_chunk(d0, d1, smeta[c], codes, h, et, g, p, lane);
+          if (minp_mode)
+            epilogue_minp(d0, d1, smeta[c], codes, h, et, p, ms);
+          else
+            epilogue_chunk(d0, d1, smeta[c], codes, h, et, g, p, lane);
           if (step == w.step_end - 1) {
             __syncwarp();
             if (lane == 0) mbar_arrive(b_empty(c));
           }
         }
+        if (key_ptr != nullptr && ms.best > ms.start)
+          atomicMax(reinterpret_cast<unsigned long long *>(key_ptr),
+                    (unsigned long long)__double_as_longlong(ms.best));
       }
       for (int c = 0; c < nc_item; ++c) b_bits ^= 1u << c;
     }
@@ -563,7 +698,23 @@ __global__ void finalize_kernel(const krux_hit *__restrict__ hits, const HitAux 
   }
 }
 
+// minimum p of each (permutation, trait) from its best -ln p
+__global__ void minp_from_key_kernel(const double *__restrict__ key, double *__restrict__ minp,
+                                     int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    minp[i] = exp(-key[i]);
+}
+
 }  // namespace
+
+cudaError_t launch_minp_from_key(const double *key, double *minp, int64_t n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  int grid = (int)((n + 255) / 256);
+  if (grid > 4096) grid = 4096;
+  minp_from_key_kernel<<<grid, 256, 0, s>>>(key, minp, n);
+  return cudaGetLastError();
+}
 
 size_t scan_smem_bytes(int nc, int nA, int kpad) {
   const size_t tile = (size_t)128 * kpad * 2;
