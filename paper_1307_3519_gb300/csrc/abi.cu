@@ -115,7 +115,7 @@ struct krux_ctx {
   PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   cudaEvent_t ev[kEv] = {};
   DevBuf B, meta, codes, groups, items, status, counters, aux, cfacptr, miss_idx, miss_mask,
-      list, gemm_out, bucket_ranks, permA, minpkey;
+      list, gemm_out, bucket_ranks, permA, minpkey, seg;
   void *blas = nullptr;
   std::vector<std::pair<size_t, void *>> pool;  // freed rank-set blocks, reused by size
 };
@@ -348,7 +348,7 @@ void krux_destroy(krux_ctx *ctx) {
   cudaSetDevice(ctx->device);
   DevBuf *bufs[] = {&ctx->B, &ctx->meta, &ctx->codes, &ctx->groups, &ctx->items, &ctx->status,
                     &ctx->counters, &ctx->aux, &ctx->cfacptr, &ctx->miss_idx, &ctx->miss_mask,
-                    &ctx->list, &ctx->gemm_out, &ctx->bucket_ranks, &ctx->permA, &ctx->minpkey};
+                    &ctx->list, &ctx->gemm_out, &ctx->bucket_ranks, &ctx->permA, &ctx->minpkey, &ctx->seg};
   for (DevBuf *b : bufs) b->release();
   for (auto &pb : ctx->pool) cudaFree(pb.second);
   for (int i = 0; i < kEv; ++i)
@@ -485,6 +485,7 @@ krux_status find_missing(krux_ctx *ctx, const int8_t *geno, int64_t ldg, int N, 
   unsigned int *cnt = ctx->counters.as<unsigned int>();
   KRUX_CUDA(ctx, launch_missing_scan(geno, ldg, N, b, n, cnt, ctx->miss_idx.as<int64_t>(),
                                      ctx->miss_mask.as<uint64_t>(), ctx->status.as<unsigned int>(), s));
+  if (ctx->profiling) ctx->prof.launches += 1;
   unsigned int m32 = 0, st = 0;
   KRUX_CUDA(ctx, cudaMemcpyAsync(&m32, cnt, 4, cudaMemcpyDeviceToHost, s));
   KRUX_CUDA(ctx, cudaMemcpyAsync(&st, ctx->status.p, 4, cudaMemcpyDeviceToHost, s));
@@ -708,6 +709,7 @@ krux_status materialise(krux_ctx *ctx, CallPlan &cp, cudaStream_t s) {
     KRUX_CUDA(ctx, cudaMemsetAsync(bs.dev.tile_nan, 0, (size_t)rs->n_ttiles * 4, s));
     KRUX_CUDA(ctx, launch_rerank_bucket(rs->dev, rs->T, rs->N, rs->Np, ddrop + i * kMaxN,
                                         (int)cp.bucket_jobs[i].drop.size(), bs.dev, s));
+    if (ctx->profiling) ctx->prof.launches += 1;
   }
   for (auto &g : cp.groups) {
     if (g.bucket < 0) continue;
@@ -752,9 +754,9 @@ krux_status run_fused(krux_ctx *ctx, CallPlan &cp, const krux_opts *o, cudaStrea
   KRUX_CUDA(ctx, ctx->B.ensure(std::max<int64_t>(btot, 256)));
   KRUX_CUDA(ctx, ctx->meta.ensure(std::max<int64_t>(mtot, 1) * sizeof(ChunkMeta)));
   KRUX_CUDA(ctx, ctx->codes.ensure(std::max<int64_t>(ctot, 1) * 8));
-  KRUX_CUDA(ctx, ctx->counters.ensure((size_t)nslots * 8 + 64));
+  KRUX_CUDA(ctx, ctx->counters.ensure((size_t)nslots * 16 + 64));
   KRUX_CUDA(ctx, ctx->status.ensure(64));
-  KRUX_CUDA(ctx, cudaMemsetAsync(ctx->counters.p, 0, (size_t)nslots * 8, s));
+  KRUX_CUDA(ctx, cudaMemsetAsync(ctx->counters.p, 0, (size_t)nslots * 16, s));
   KRUX_CUDA(ctx, cudaMemsetAsync(ctx->status.p, 0, 64, s));
   unsigned int *status = ctx->status.as<unsigned int>();
 
@@ -831,11 +833,34 @@ krux_status run_fused(krux_ctx *ctx, CallPlan &cp, const krux_opts *o, cudaStrea
   p.timeout_cycles = ctx->wait_limit;
   p.signed_coef = signed_coef;
   const int grid = (int)std::min<size_t>(items.size(), (size_t)ctx->sm_count);
+  // Single hit list: stage hits per CTA (shared-memory counter, no global atomic
+  // per warp) and append the segments after the launch.
+  const bool staged = nslots == 1 && cp.slots[0].capacity > 0 && grid > 0;
+  if (staged) {
+    const int64_t cap = cp.slots[0].capacity;
+    const int seg_cap = (int)std::max<int64_t>(256, std::min<int64_t>(32768, 2 * cap / grid + 256));
+    const size_t rec = sizeof(krux_hit) + sizeof(HitAux);
+    KRUX_CUDA(ctx, ctx->seg.ensure((size_t)grid * seg_cap * rec + (size_t)grid * 4 + 256));
+    char *sb = ctx->seg.as<char>();
+    p.seg_cap = seg_cap;
+    p.seg_hits = reinterpret_cast<krux_hit *>(sb);
+    p.seg_aux = reinterpret_cast<HitAux *>(sb + (size_t)grid * seg_cap * sizeof(krux_hit));
+    p.seg_cnt = reinterpret_cast<unsigned int *>(sb + (size_t)grid * seg_cap * rec);
+  }
   if (grid > 0) KRUX_CUDA(ctx, launch_scan(p, grid, scan_smem_bytes(nc, nA, kpad), s));
+  unsigned long long *totals = ctx->counters.as<unsigned long long>() + nslots;
+  if (staged) {
+    KRUX_CUDA(ctx, launch_seg_compact(p.seg_hits, p.seg_aux, p.seg_cnt, grid, p.seg_cap,
+                                      ctx->counters.as<unsigned long long>(), cp.slots[0].hits,
+                                      cp.slots[0].aux, cp.slots[0].capacity, totals, s));
+  } else {
+    KRUX_CUDA(ctx, cudaMemcpyAsync(totals, ctx->counters.p, (size_t)nslots * 8,
+                                   cudaMemcpyDeviceToDevice, s));
+  }
   ev_record(ctx, 4, s);
 
   unsigned int hst[2] = {0, 0};
-  KRUX_CUDA(ctx, cudaMemcpyAsync(counts.data(), ctx->counters.p, (size_t)nslots * 8,
+  KRUX_CUDA(ctx, cudaMemcpyAsync(counts.data(), totals, (size_t)nslots * 8,
                                  cudaMemcpyDeviceToHost, s));
   KRUX_CUDA(ctx, cudaMemcpyAsync(hst, ctx->status.p, 8, cudaMemcpyDeviceToHost, s));
   KRUX_CUDA(ctx, cudaStreamSynchronize(s));
@@ -843,7 +868,7 @@ krux_status run_fused(krux_ctx *ctx, CallPlan &cp, const krux_opts *o, cudaStrea
     ctx->prof.ms_pack = ev_ms(ctx, 2, 3);
     ctx->prof.ms_scan = ev_ms(ctx, 3, 4);
     ctx->prof.scan_grid = grid;
-    ctx->prof.launches += (grid > 0 ? 1 : 0);
+    ctx->prof.launches += (grid > 0 ? 1 : 0) + (staged ? 1 : 0);
     for (auto &g : cp.groups) ctx->prof.launches += g.nan_cnt ? 2 : 1;
   }
   if (hst[0] & kDevBadCode) return fail(ctx, KRUX_EINVAL, "genotype code outside {-1,0,1,2}");

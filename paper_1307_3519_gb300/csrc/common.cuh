@@ -19,10 +19,11 @@ constexpr int kChunkRows = 128;    // B rows per chunk: [I_0 of 64 SNPs | I_1 of
 constexpr int kMaxN = 512;         // samples: centred 2*rank fits FP16 exactly below 2048
 constexpr int kAtomK = 64;         // K elements per 128-byte swizzle atom (fp16)
 constexpr int kTmemSlots = 4;      // accumulator ring: 4 x 128 fp32 columns = all of TMEM
-constexpr int kEpiWarps = 8;       // epilogue warps: 2 per TMEM lane quarter
-constexpr int kProducerWarp = 8;   // TMA producer
-constexpr int kMmaWarp = 9;        // tcgen05.mma issuer, owns the TMEM allocation
-constexpr int kScanThreads = 320;
+constexpr int kEpiWarps = 16;      // epilogue warps: 4 per TMEM lane quarter
+constexpr int kEpiSnps = 16;       // SNPs of a chunk each epilogue warp evaluates
+constexpr int kProducerWarp = 16;  // TMA producer
+constexpr int kMmaWarp = 17;       // tcgen05.mma issuer, owns the TMEM allocation
+constexpr int kScanThreads = 576;
 
 // ---- per-chunk SNP metadata (one 1536-byte blob per chunk of 64 SNPs) ------
 // Fast-test coefficients: with u = D_0, v = D_1 (D_2 = -u - v) the statistic's
@@ -105,7 +106,10 @@ struct ScanParams {
   unsigned int *status;     // [0] error bits, [1] where
   long long timeout_cycles;
   int32_t signed_coef;      // 1: df-1 SNPs carry negated alpha, gamma (permutation batches)
-  int32_t pad_;
+  int32_t seg_cap;          // records per CTA staging segment (0: hits go straight to the list)
+  krux_hit *seg_hits;       // [grid][seg_cap] staged hit records
+  HitAux *seg_aux;          // [grid][seg_cap]
+  unsigned int *seg_cnt;    // [grid] records staged by each CTA
 };
 
 enum : unsigned int {
@@ -120,6 +124,10 @@ cudaError_t launch_permute_rows(const __half *A, __half *out, int rows_pad, int 
                                 const int32_t *perms, int P, cudaStream_t s);
 cudaError_t launch_scan(const ScanParams &p, int grid, size_t smem, cudaStream_t s);
 size_t scan_smem_bytes(int nc, int nA, int kpad);
+cudaError_t launch_seg_compact(const krux_hit *seg_hits, const HitAux *seg_aux,
+                               const unsigned int *seg_cnt, int n_cta, int seg_cap,
+                               const unsigned long long *direct, krux_hit *out, HitAux *out_aux,
+                               int64_t capacity, unsigned long long *total, cudaStream_t s);
 cudaError_t launch_minp_from_key(const double *key, double *minp, int64_t n, cudaStream_t s);
 cudaError_t launch_finalize(const krux_hit *hits, const HitAux *aux, int64_t n,
                             const double *const *cfac_by_group, double *H, double *p,

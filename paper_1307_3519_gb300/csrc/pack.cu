@@ -27,14 +27,14 @@ missing_scan_kernel(const int8_t *__restrict__ geno, int64_t ldg, int N, int64_t
   bool any = false, bad = false;
 #pragma unroll
   for (int w = 0; w < kMaxN / 32; ++w) {
-    const int k = w * 32 + lane;
-    int code = 0;
-    if (w * 32 < N) {
-      code = k < N ? (int)g[k] : 0;
+    words[w] = 0u;
+    if (w * 32 < N) {  // warp-uniform
+      const int k = w * 32 + lane;
+      const int code = k < N ? (int)g[k] : 0;
+      bad |= (code < -1 || code > 2);
+      words[w] = __ballot_sync(0xffffffffu, code == -1);
+      any |= words[w] != 0u;
     }
-    bad |= (code < -1 || code > 2);
-    words[w] = __ballot_sync(0xffffffffu, code == -1);
-    any |= words[w] != 0u;
   }
   if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(status, kDevBadCode);
   if (!any) return;
@@ -56,7 +56,7 @@ missing_scan_kernel(const int8_t *__restrict__ geno, int64_t ldg, int N, int64_t
 __global__ void __launch_bounds__(kPackWarps * 32)
 pack_kernel(const int8_t *__restrict__ geno, int64_t ldg, int N, int Np,
             const int64_t *__restrict__ snp_list, int64_t snp_begin, int64_t n_snps,
-            int64_t n_slots, int64_t snp_out_base, double h1, double h2, int allow_missing,
+            int64_t n_slots, int64_t snp_out_base, float rh1, float rh2, int allow_missing,
             int signed_df1, __half *__restrict__ B, ChunkMeta *__restrict__ meta,
             unsigned int *status) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -116,14 +116,15 @@ pack_kernel(const int8_t *__restrict__ geno, int64_t ldg, int N, int Np,
     if (df > 0 && !excluded) {
       // sum_i D_i^2 / N_i with D_2 = -(u + v):  (r0 + r2) u^2 + 2 r2 u v + (r1 + r2) v^2
       //   = alpha (u + beta v)^2 + gamma v^2,  alpha = r0 + r2, beta = r2 / alpha,
-      //   gamma = r1 + r2 r0 / alpha   (empty groups have r_i = 0)
-      const double q0 = n0 ? 1.0 / n0 : 0.0, q1 = n1 ? 1.0 / n1 : 0.0, q2 = n2 ? 1.0 / n2 : 0.0;
-      const double a = q0 + q2;
-      const double h = df == 1 ? h1 : h2;
-      const double sg = (signed_df1 && df == 1) ? -1.0 : 1.0;
-      al = (float)(sg * a / h);
-      be = (float)(q2 / a);
-      ga = (float)(sg * (q1 + q2 * q0 / a) / h);
+      //   gamma = r1 + r2 r0 / alpha   (empty groups have r_i = 0).  FP32 is enough:
+      // these only feed the thresholded test, whose band is rechecked in FP64.
+      const float q0 = n0 ? 1.f / (float)n0 : 0.f, q1 = n1 ? 1.f / (float)n1 : 0.f,
+                  q2 = n2 ? 1.f / (float)n2 : 0.f;
+      const float a = q0 + q2;
+      const float rh = (df == 1 ? rh1 : rh2) * ((signed_df1 && df == 1) ? -1.f : 1.f);
+      al = a * rh;
+      be = q2 / a;
+      ga = (q1 + q2 * q0 / a) * rh;
     }
     m.alpha[jj] = al;
     m.beta[jj] = be;
@@ -193,7 +194,8 @@ cudaError_t launch_pack2(const int8_t *geno, int64_t ldg, int N, int Np, const i
   if (n_slots == 0) return cudaSuccess;
   const int64_t grid = (n_slots + kPackWarps - 1) / kPackWarps;
   pack_kernel<<<(unsigned)grid, kPackWarps * 32, 0, s>>>(geno, ldg, N, Np, snp_list, snp_begin,
-                                                         n_snps, n_slots, snp_out_base, h1, h2,
+                                                         n_snps, n_slots, snp_out_base,
+                                                         (float)(1.0 / h1), (float)(1.0 / h2),
                                                          allow_missing, signed_df1, B, meta, status);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || codes == nullptr) return e;

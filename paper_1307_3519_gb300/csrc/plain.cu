@@ -96,15 +96,26 @@ plain_epilogue_kernel(const float *__restrict__ C, int64_t ldc, int T, int n_slo
         hit = pv < pthresh;
       }
     } else if (snp >= 0 && df > 0 && cf > 0.0) {
-      float Q = 0.f;
-      const float w = -(uf + vf);
-      if (n0) Q += uf * uf / (float)n0;
-      if (n1) Q += vf * vf / (float)n1;
-      if (n2) Q += w * w / (float)n2;
-      const float hq = (float)cf * Q;
-      const float h = df == 1 ? h1 : h2;
-      if (hq > h * (1.f - margin)) {
-        hit = hq > h * (1.f + margin);
+      bool cand;
+      float hq = 0.f, hd = 1.f;
+      if (nn == 0) {
+        // alpha (u + beta v)^2 + gamma v^2 against tau (1 -/+ margin), as in the fused kernel
+        const float w = fmaf(m.beta[jj], vf, uf);
+        const float q = fmaf(m.alpha[jj] * w, w, m.gamma[jj] * vf * vf);
+        hq = q;
+        hd = tau[t];
+      } else {
+        const float w = -(uf + vf);
+        float Q = 0.f;
+        if (n0) Q += uf * uf / (float)n0;
+        if (n1) Q += vf * vf / (float)n1;
+        if (n2) Q += w * w / (float)n2;
+        hq = (float)cf * Q;
+        hd = df == 1 ? h1 : h2;
+      }
+      cand = hq >= hd * (1.f - margin);
+      if (cand) {
+        hit = hq > hd * (1.f + margin);
         if (!hit) {
           const double D0 = u, D1 = v, D2 = -(double)(u + v);
           double Qd = 0.0;
@@ -115,7 +126,6 @@ plain_epilogue_kernel(const float *__restrict__ C, int64_t ldc, int T, int n_slo
         }
       }
     }
-    (void)tau;
   }
   const unsigned ball = __ballot_sync(0xffffffffu, hit);
   if (ball == 0u) return;

@@ -11,12 +11,12 @@
 // correction"), decides pairs within a relative margin of the threshold in
 // FP64, and appends hits with one atomic per warp.
 //
-// Roles (320 threads, one CTA per SM, persistent over work items):
-//   warps 0-7 : epilogue; warp w reads TMEM lanes 32*(w%4).. (traits) and SNP
-//               half w/4 of each chunk
-//   warp 8    : TMA producer (A tiles stream through nA stages; a B tile of nc
+// Roles (576 threads, one CTA per SM, persistent over work items):
+//   warps 0-15: epilogue; warp w reads TMEM lanes 32*(w%4).. (traits) and the
+//               16 SNPs 16*(w/4).. of each 64-SNP chunk
+//   warp 16   : TMA producer (A tiles stream through nA stages; a B tile of nc
 //               chunks stays resident while all trait tiles pass)
-//   warp 9    : TMEM allocator and tcgen05.mma issuer (one thread)
+//   warp 17   : TMEM allocator and tcgen05.mma issuer (one thread)
 // Every mbarrier wait is bounded: on timeout the kernel raises an error bit,
 // drains its own asynchronous copies and MMAs, frees TMEM and returns.
 #include "common.cuh"
@@ -74,7 +74,7 @@ struct WaitCtl {
 };
 
 // Bounded wait for the phase of parity `parity`; false on timeout or abort.
-__device__ __noinline__ bool wait_bar(uint32_t bar, uint32_t parity, const WaitCtl &w,
+__device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, const WaitCtl &w,
                                       unsigned int where) {
   if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = clock64();
@@ -86,6 +86,21 @@ __device__ __noinline__ bool wait_bar(uint32_t bar, uint32_t parity, const WaitC
       atomicOr(w.status, kDevTimeout);
       atomicMax(w.status + 1, where);
       return false;
+    }
+  }
+}
+
+// Wait used while shutting down: ignores the abort flag (copies and MMAs already
+// issued must land before the CTA can release its shared memory and TMEM) and
+// gives up only after a fixed bound of about two seconds.
+__device__ __noinline__ void wait_drain(uint32_t bar, uint32_t parity, unsigned int *status,
+                                        unsigned int where) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > 4000000000LL) {
+      atomicOr(status, kDevTimeout);
+      atomicMax(status + 1, where);
+      return;
     }
   }
 }
@@ -129,19 +144,17 @@ __device__ __forceinline__ void tc_commit(uint32_t bar) {
                : "memory");
 }
 
-#define KRUX_LD32_REGS(r)                                                                       \
+#define KRUX_LD16_REGS(r)                                                                       \
   "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),          \
       "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),  \
-      "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),            \
-      "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),            \
-      "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      "=r"(r[14]), "=r"(r[15])
 
-// 32 consecutive fp32 columns of this warp's 32 TMEM lanes (one lane per thread).
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+// 16 consecutive fp32 columns of this warp's 32 TMEM lanes (one lane per thread).
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[kEpiSnps]) {
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
-      "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : KRUX_LD32_REGS(r)
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+      "%15}, [%16];"
+      : KRUX_LD16_REGS(r)
       : "r"(taddr)
       : "memory");
 }
@@ -210,15 +223,15 @@ struct EpiTrait {
 
 // Group sizes of a pair after removing the trait's NaN samples (section
 // "Handling missing values": N_i(n,m) counts the samples present for both).
-__device__ __forceinline__ void pair_counts(const EpiTrait &et, const ChunkMeta &m,
-                                            const uint64_t *codes, int h, int jj, int j,
+__device__ __forceinline__ void pair_counts(int nan_cnt, const uint16_t *nan_idx,
+                                            const ChunkMeta &m, const uint64_t *codes, int jj,
                                             int &n0, int &n1, int &n2) {
   n0 = m.n[0][jj];
   n1 = m.n[1][jj];
   n2 = m.n[2][jj];
-  for (int i = 0; i < et.nan_cnt; ++i) {
-    const int k = et.nan_idx[i];
-    const int code = (int)((codes[k * 2 + h] >> (2 * j)) & 3ull);
+  for (int i = 0; i < nan_cnt; ++i) {
+    const int k = nan_idx[i];
+    const int code = (int)((codes[k * 2 + (jj >> 5)] >> (2 * (jj & 31))) & 3ull);
     n0 -= code == 0;
     n1 -= code == 1;
     n2 -= code == 2;
@@ -230,114 +243,137 @@ __device__ __forceinline__ int df_of(int n0, int n1, int n2) {
   return g > 0 ? g - 1 : 0;
 }
 
-// Epilogue of one (trait tile, chunk half): 32 SNPs x this thread's trait.
-__device__ __forceinline__ void epilogue_chunk(const uint32_t (&d0)[32], const uint32_t (&d1)[32],
-                                               const ChunkMeta &m, const uint64_t *codes, int h,
-                                               const EpiTrait &et, const GroupDesc &g,
-                                               const ScanParams &p, int lane) {
-  const int jb = 32 * h;
+// ---- packed fp32x2 helpers (two SNPs per instruction) ----------------------
+__device__ __forceinline__ uint64_t pk2(uint32_t a, uint32_t b) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "r"(a), "r"(b));
+  return r;
+}
+__device__ __forceinline__ void upk2(uint64_t r, uint32_t &a, uint32_t &b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=r"(a), "=r"(b) : "l"(r));
+}
+__device__ __forceinline__ uint64_t ffma2(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ uint64_t fmul2(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t fadd2(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ float fmax3(float a, float b, float c) {
+  float r;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+__device__ __forceinline__ float fmin3(float a, float b, float c) {
+  float r;
+  asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+
+// Hot test of kEpiSnps SNPs: true when some pair may lie at or above the lower edge of
+// the band (q >= 0).  Two SNPs per packed instruction:
+//   w = u + beta v,  q = alpha w^2 + gamma v^2 - tau (1 - margin)
+// (with permutation batches the form is signed by df and |form| is tested).
+__device__ __forceinline__ bool hit_fast(const uint32_t (&d0)[kEpiSnps], const uint32_t (&d1)[kEpiSnps],
+                                         const ChunkMeta &m, int h, float ntlo, bool signed_coef) {
+  const uint64_t *al = reinterpret_cast<const uint64_t *>(m.alpha + kEpiSnps * h);
+  const uint64_t *be = reinterpret_cast<const uint64_t *>(m.beta + kEpiSnps * h);
+  const uint64_t *ga = reinterpret_cast<const uint64_t *>(m.gamma + kEpiSnps * h);
+  const uint64_t nt2 = pk2(__float_as_uint(ntlo), __float_as_uint(ntlo));
+  uint32_t acc = 0xffffffffu;
+#pragma unroll
+  for (int j = 0; j < kEpiSnps / 2; j += 2) {
+    const ulonglong2 A = *reinterpret_cast<const ulonglong2 *>(al + j);
+    const ulonglong2 B = *reinterpret_cast<const ulonglong2 *>(be + j);
+    const ulonglong2 G = *reinterpret_cast<const ulonglong2 *>(ga + j);
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      const int jj = 2 * (j + t);
+      const uint64_t u2 = pk2(d0[jj], d0[jj + 1]);
+      const uint64_t v2 = pk2(d1[jj], d1[jj + 1]);
+      const uint64_t a2 = t ? A.y : A.x, b2 = t ? B.y : B.x, g2 = t ? G.y : G.x;
+      const uint64_t w2 = ffma2(b2, v2, u2);
+      const uint64_t e2 = fmul2(g2, v2);
+      uint64_t q2;
+      if (!signed_coef) {
+        q2 = ffma2(e2, v2, nt2);
+        q2 = ffma2(fmul2(a2, w2), w2, q2);
+      } else {
+        q2 = ffma2(fmul2(a2, w2), w2, fmul2(e2, v2));
+        q2 = fadd2(q2 & 0x7fffffff7fffffffull, nt2);
+      }
+      uint32_t qa, qb;
+      upk2(q2, qa, qb);
+      acc &= qa & qb;
+    }
+  }
+  return (int)acc >= 0;
+}
+
+// Rare path of a hit-mode chunk half: dense FP64 output, traits with NaN,
+// classification of candidates (FP64 inside the band) and the warp-aggregated
+// append of hits.  Called by the whole warp; `dv` holds this lane's kEpiSnps D_0
+// then kEpiSnps D_1 values (a local copy, so the hot path keeps them in registers).
+__device__ __noinline__ void hit_slow(const uint32_t *dv, bool mine, const ChunkMeta &m,
+                                      const uint64_t *codes, int h, int trait, bool valid,
+                                      float ntlo, float nthi, double cfac, int nan_cnt,
+                                      const uint16_t *nan_idx, const GroupDesc &g,
+                                      const ScanParams &p, int lane) {
+  const int jb = kEpiSnps * h;
   uint32_t hitmask = 0;
-  if (p.dense) {
-    // every pair in FP64 (small problems): H, p written densely
-#pragma unroll
-    for (int j = 0; j < 32; ++j) {
+  if (mine && valid) {
+    const float *al = m.alpha + jb, *be = m.beta + jb, *ga = m.gamma + jb;
+    for (int j = 0; j < kEpiSnps; ++j) {
       const int snp = m.snp[jb + j];
-      if (et.valid && snp >= 0) {
+      if (snp < 0) continue;
+      const float u = __uint_as_float(dv[j]), v = __uint_as_float(dv[kEpiSnps + j]);
+      if (p.dense || nan_cnt > 0) {
         int n0, n1, n2;
-        pair_counts(et, m, codes, h, jb + j, j, n0, n1, n2);
-        const int u = (int)__uint_as_float(d0[j]), v = (int)__uint_as_float(d1[j]);
+        pair_counts(nan_cnt, nan_idx, m, codes, jb + j, n0, n1, n2);
         const int df = df_of(n0, n1, n2);
-        const double H = df > 0 ? kw_H64(u, v, n0, n1, n2, et.cfac) : 0.0;
-        const double pv = df > 0 && et.cfac > 0.0 ? kw_p64(H, df) : 1.0;
-        const int64_t o = (int64_t)et.trait * g.dense_ld + (snp - g.dense_snp0);
-        g.dense_H[o] = et.cfac > 0.0 ? H : 0.0;
-        g.dense_p[o] = pv;
-        if (pv < p.pthresh) hitmask |= 1u << j;
-      }
-    }
-  } else if (et.nan_cnt == 0 && p.signed_coef) {
-    // permutation batch, unpermuted group: |form| against the bound
-    uint32_t acc = 0xffffffffu;
-    const float *al = m.alpha + jb, *be = m.beta + jb, *ga = m.gamma + jb;
-#pragma unroll
-    for (int j = 0; j < 32; ++j) {
-      const float q = fabsf(kw_s(__uint_as_float(d0[j]), __uint_as_float(d1[j]), al[j], be[j], ga[j])) + et.ntlo;
-      acc &= __float_as_uint(q);
-    }
-    if ((int)acc >= 0) {
-#pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const float u = __uint_as_float(d0[j]), v = __uint_as_float(d1[j]);
-        const float sv = fabsf(kw_s(u, v, al[j], be[j], ga[j]));
-        if (sv + et.ntlo >= 0.f && m.snp[jb + j] >= 0) {
-          bool hit = sv + et.nthi > 0.f;
-          if (!hit) {
-            const double H = kw_H64((int)u, (int)v, m.n[0][jb + j], m.n[1][jb + j], m.n[2][jb + j], et.cfac);
-            hit = kw_p64(H, m.df[jb + j]) < p.pthresh;
-          }
-          if (hit) hitmask |= 1u << j;
-        }
-      }
-    }
-  } else if (et.nan_cnt == 0) {
-    uint32_t acc = 0xffffffffu;
-    const float *al = m.alpha + jb, *be = m.beta + jb, *ga = m.gamma + jb;
-#pragma unroll
-    for (int j = 0; j < 32; j += 4) {
-      const float4 A4 = *reinterpret_cast<const float4 *>(al + j);
-      const float4 B4 = *reinterpret_cast<const float4 *>(be + j);
-      const float4 G4 = *reinterpret_cast<const float4 *>(ga + j);
-      const float q0 = kw_q(__uint_as_float(d0[j]), __uint_as_float(d1[j]), A4.x, B4.x, G4.x, et.ntlo);
-      const float q1 = kw_q(__uint_as_float(d0[j + 1]), __uint_as_float(d1[j + 1]), A4.y, B4.y, G4.y, et.ntlo);
-      const float q2 = kw_q(__uint_as_float(d0[j + 2]), __uint_as_float(d1[j + 2]), A4.z, B4.z, G4.z, et.ntlo);
-      const float q3 = kw_q(__uint_as_float(d0[j + 3]), __uint_as_float(d1[j + 3]), A4.w, B4.w, G4.w, et.ntlo);
-      acc &= __float_as_uint(q0) & __float_as_uint(q1);
-      acc &= __float_as_uint(q2) & __float_as_uint(q3);
-    }
-    if ((int)acc >= 0) {
-      // some pair is at or above the lower edge of the band: classify each
-#pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const float u = __uint_as_float(d0[j]), v = __uint_as_float(d1[j]);
-        const float ql = kw_q(u, v, al[j], be[j], ga[j], et.ntlo);
-        if (ql >= 0.f && m.snp[jb + j] >= 0) {
-          const float qh = kw_q(u, v, al[j], be[j], ga[j], et.nthi);
-          bool hit = qh > 0.f;
-          if (!hit) {
-            const int n0 = m.n[0][jb + j], n1 = m.n[1][jb + j], n2 = m.n[2][jb + j];
-            const double H = kw_H64((int)u, (int)v, n0, n1, n2, et.cfac);
-            hit = kw_p64(H, m.df[jb + j]) < p.pthresh;
-          }
-          if (hit) hitmask |= 1u << j;
-        }
-      }
-    }
-  } else {
-    // trait with NaN samples: per-pair group sizes, FP32 test, FP64 near the bound
-#pragma unroll
-    for (int j = 0; j < 32; ++j) {
-      if (m.snp[jb + j] >= 0) {
-        int n0, n1, n2;
-        pair_counts(et, m, codes, h, jb + j, j, n0, n1, n2);
-        const int df = df_of(n0, n1, n2);
-        if (df > 0) {
-          const float u = __uint_as_float(d0[j]), v = __uint_as_float(d1[j]), w = -(u + v);
+        if (p.dense) {
+          const double H = (df > 0 && cfac > 0.0) ? kw_H64((int)u, (int)v, n0, n1, n2, cfac) : 0.0;
+          const double pv = (df > 0 && cfac > 0.0) ? kw_p64(H, df) : 1.0;
+          const int64_t o = (int64_t)trait * g.dense_ld + (snp - g.dense_snp0);
+          g.dense_H[o] = H;
+          g.dense_p[o] = pv;
+          if (pv < p.pthresh) hitmask |= 1u << j;
+        } else if (df > 0) {
+          const float w = -(u + v);
           float Q = 0.f;
           if (n0 > 0) Q += u * u / (float)n0;
           if (n1 > 0) Q += v * v / (float)n1;
           if (n2 > 0) Q += w * w / (float)n2;
-          const float hq = (float)et.cfac * Q;
-          const float h = df == 1 ? p.h1 : p.h2;
-          if (hq > h * (1.f - p.margin)) {
-            bool hit = hq > h * (1.f + p.margin);
-            if (!hit) hit = kw_p64(kw_H64((int)u, (int)v, n0, n1, n2, et.cfac), df) < p.pthresh;
+          const float hq = (float)cfac * Q;
+          const float hd = df == 1 ? p.h1 : p.h2;
+          if (hq > hd * (1.f - p.margin)) {
+            bool hit = hq > hd * (1.f + p.margin);
+            if (!hit) hit = kw_p64(kw_H64((int)u, (int)v, n0, n1, n2, cfac), df) < p.pthresh;
             if (hit) hitmask |= 1u << j;
           }
+        }
+      } else {
+        float sv = kw_s(u, v, al[j], be[j], ga[j]);
+        if (p.signed_coef) sv = fabsf(sv);
+        if (sv + ntlo >= 0.f) {
+          bool hit = sv + nthi > 0.f;
+          if (!hit) {
+            const double H = kw_H64((int)u, (int)v, m.n[0][jb + j], m.n[1][jb + j], m.n[2][jb + j], cfac);
+            hit = kw_p64(H, m.df[jb + j]) < p.pthresh;
+          }
+          if (hit) hitmask |= 1u << j;
         }
       }
     }
   }
-
   if (!__any_sync(0xffffffffu, hitmask != 0u)) return;
   // warp-aggregated append: one atomic per warp
   const int cnt = __popc(hitmask);
@@ -353,26 +389,86 @@ __device__ __forceinline__ void epilogue_chunk(const uint32_t (&d0)[32], const u
   base = __shfl_sync(0xffffffffu, base, 0);
   unsigned long long idx = base + (unsigned long long)(incl - cnt);
   const unsigned long long cap = (unsigned long long)g.capacity;
+  while (hitmask) {
+    const int j = __ffs(hitmask) - 1;
+    hitmask &= hitmask - 1u;
+    if (idx < cap) {
+      int n0, n1, n2;
+      pair_counts(nan_cnt, nan_idx, m, codes, jb + j, n0, n1, n2);
+      krux_hit r;
+      r.trait = (uint32_t)trait;
+      r.snp = (uint32_t)m.snp[jb + j];
+      r.d0 = (int32_t)__uint_as_float(dv[j]);
+      r.d1 = (int32_t)__uint_as_float(dv[kEpiSnps + j]);
+      g.hits[idx] = r;
+      HitAux a;
+      a.n0 = (uint16_t)n0;
+      a.n1 = (uint16_t)n1;
+      a.n2 = (uint16_t)n2;
+      a.group = (uint16_t)g.group_id;
+      g.aux[idx] = a;
+    }
+    ++idx;
+  }
+}
+
+// FP64 decision for a pair inside the band (rare): p < P_c from the exact sums.
+__device__ __noinline__ bool decide64(float u, float v, int n0, int n1, int n2, int df, double cfac,
+                                      double pthresh) {
+  return kw_p64(kw_H64((int)u, (int)v, n0, n1, n2, cfac), df) < pthresh;
+}
+
+// Warp-collective append of this lane's hits (bit j of `hitmask` = SNP jb + j).
+// Records first fill the CTA's staging segment through a shared-memory counter;
+// whatever does not fit goes straight to the caller's list through the global
+// counter.  A compaction pass appends the segments after the launch.
+__device__ __forceinline__ void emit_hits(uint32_t hitmask, const uint32_t (&d0)[kEpiSnps],
+                                          const uint32_t (&d1)[kEpiSnps], const ChunkMeta &m,
+                                          int jb, int trait, const GroupDesc &g,
+                                          const ScanParams &p, unsigned int *seg_n, int lane) {
+  const int cnt = __popc(hitmask);
+  int incl = cnt;
 #pragma unroll
-  for (int j = 0; j < 32; ++j) {
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  const unsigned int total = (unsigned int)__shfl_sync(0xffffffffu, incl, 31);
+  const unsigned int cap = (unsigned int)p.seg_cap;
+  unsigned int sbase = 0;
+  if (lane == 0 && cap > 0) sbase = atomicAdd(seg_n, total);
+  sbase = __shfl_sync(0xffffffffu, sbase, 0);
+  const unsigned int over_from = sbase > cap ? sbase : cap;  // first index beyond the segment
+  const unsigned int n_over = sbase + total > over_from ? sbase + total - over_from : 0u;
+  unsigned long long gbase = 0;
+  if (lane == 0 && n_over > 0) gbase = atomicAdd(g.counter, (unsigned long long)n_over);
+  gbase = __shfl_sync(0xffffffffu, gbase, 0);
+  unsigned int sidx = sbase + (unsigned int)(incl - cnt);
+  const size_t seg0 = (size_t)blockIdx.x * cap;
+#pragma unroll
+  for (int j = 0; j < kEpiSnps; ++j) {
     if ((hitmask >> j) & 1u) {
-      if (idx < cap) {
-        int n0, n1, n2;
-        pair_counts(et, m, codes, h, jb + j, j, n0, n1, n2);
-        krux_hit r;
-        r.trait = (uint32_t)et.trait;
-        r.snp = (uint32_t)m.snp[jb + j];
-        r.d0 = (int32_t)__uint_as_float(d0[j]);
-        r.d1 = (int32_t)__uint_as_float(d1[j]);
-        g.hits[idx] = r;
-        HitAux a;
-        a.n0 = (uint16_t)n0;
-        a.n1 = (uint16_t)n1;
-        a.n2 = (uint16_t)n2;
-        a.group = (uint16_t)g.group_id;
-        g.aux[idx] = a;
+      krux_hit r;
+      r.trait = (uint32_t)trait;
+      r.snp = (uint32_t)m.snp[jb + j];
+      r.d0 = (int32_t)__uint_as_float(d0[j]);
+      r.d1 = (int32_t)__uint_as_float(d1[j]);
+      HitAux a;
+      a.n0 = m.n[0][jb + j];
+      a.n1 = m.n[1][jb + j];
+      a.n2 = m.n[2][jb + j];
+      a.group = (uint16_t)g.group_id;
+      if (sidx < cap) {
+        p.seg_hits[seg0 + sidx] = r;
+        p.seg_aux[seg0 + sidx] = a;
+      } else {
+        const unsigned long long gi = gbase + (sidx - over_from);
+        if (gi < (unsigned long long)g.capacity) {
+          g.hits[gi] = r;
+          g.aux[gi] = a;
+        }
       }
-      ++idx;
+      ++sidx;
     }
   }
 }
@@ -385,63 +481,68 @@ struct MinpState {
   float c1, c2;     // H = c1 * |s| for df-1 SNPs; -ln p = c2 * s for df-2 SNPs
 };
 
-// Permuted group: track the minimum p (maximum -ln p) over 32 SNPs.
-__device__ __forceinline__ void epilogue_minp(const uint32_t (&d0)[32], const uint32_t (&d1)[32],
-                                              const ChunkMeta &m, const uint64_t *codes, int h,
-                                              const EpiTrait &et, const ScanParams &p,
-                                              MinpState &st) {
-  const int jb = 32 * h;
-  if (!et.valid) return;
-  if (et.nan_cnt > 0) {
-    // traits with NaN: exact per pair (group sizes differ per pair)
-#pragma unroll
-    for (int j = 0; j < 32; ++j) {
-      if (m.snp[jb + j] >= 0) {
-        int n0, n1, n2;
-        pair_counts(et, m, codes, h, jb + j, j, n0, n1, n2);
-        const int df = df_of(n0, n1, n2);
-        if (df > 0 && et.cfac > 0.0) {
-          const double key = key64_of(kw_H64((int)__uint_as_float(d0[j]), (int)__uint_as_float(d1[j]),
-                                             n0, n1, n2, et.cfac), df);
-          if (key > st.best) st.best = key;
-        }
-      }
-    }
-    st.best_lo = (float)st.best * (1.f - p.margin);
-    return;
-  }
-  const float *al = m.alpha + jb, *be = m.beta + jb, *ga = m.gamma + jb;
+// Hot filter of a permuted chunk half: largest df-2 form and most negative df-1
+// form over kEpiSnps SNPs, turned into an FP32 -ln p bound; true if some SNP may beat
+// the running best.
+__device__ __forceinline__ bool minp_fast(const uint32_t (&d0)[kEpiSnps], const uint32_t (&d1)[kEpiSnps],
+                                          const ChunkMeta &m, int h, const MinpState &st) {
+  const uint64_t *al = reinterpret_cast<const uint64_t *>(m.alpha + kEpiSnps * h);
+  const uint64_t *be = reinterpret_cast<const uint64_t *>(m.beta + kEpiSnps * h);
+  const uint64_t *ga = reinterpret_cast<const uint64_t *>(m.gamma + kEpiSnps * h);
   float smax = 0.f, smin = 0.f;
 #pragma unroll
-  for (int j = 0; j < 32; j += 4) {
-    const float4 A4 = *reinterpret_cast<const float4 *>(al + j);
-    const float4 B4 = *reinterpret_cast<const float4 *>(be + j);
-    const float4 G4 = *reinterpret_cast<const float4 *>(ga + j);
-    const float s0 = kw_s(__uint_as_float(d0[j]), __uint_as_float(d1[j]), A4.x, B4.x, G4.x);
-    const float s1 = kw_s(__uint_as_float(d0[j + 1]), __uint_as_float(d1[j + 1]), A4.y, B4.y, G4.y);
-    const float s2 = kw_s(__uint_as_float(d0[j + 2]), __uint_as_float(d1[j + 2]), A4.z, B4.z, G4.z);
-    const float s3 = kw_s(__uint_as_float(d0[j + 3]), __uint_as_float(d1[j + 3]), A4.w, B4.w, G4.w);
-    smax = fmaxf(smax, fmaxf(fmaxf(s0, s1), fmaxf(s2, s3)));
-    smin = fminf(smin, fminf(fminf(s0, s1), fminf(s2, s3)));
-  }
-  const float kg = fmaxf(smax * st.c2, key1f(-smin * st.c1));
-  if (kg > st.best_lo) {
+  for (int j = 0; j < kEpiSnps / 2; j += 2) {
+    const ulonglong2 A = *reinterpret_cast<const ulonglong2 *>(al + j);
+    const ulonglong2 B = *reinterpret_cast<const ulonglong2 *>(be + j);
+    const ulonglong2 G = *reinterpret_cast<const ulonglong2 *>(ga + j);
 #pragma unroll
-    for (int j = 0; j < 32; ++j) {
-      const float u = __uint_as_float(d0[j]), v = __uint_as_float(d1[j]);
-      const float sv = kw_s(u, v, al[j], be[j], ga[j]);
-      const float kf = sv > 0.f ? sv * st.c2 : key1f(-sv * st.c1);
-      if (kf > st.best_lo && m.snp[jb + j] >= 0) {
-        const int df = m.df[jb + j];
-        const double key =
-            key64_of(kw_H64((int)u, (int)v, m.n[0][jb + j], m.n[1][jb + j], m.n[2][jb + j], et.cfac), df);
-        if (key > st.best) {
-          st.best = key;
-          st.best_lo = (float)key * (1.f - p.margin);
-        }
-      }
+    for (int t = 0; t < 2; ++t) {
+      const int jj = 2 * (j + t);
+      const uint64_t u2 = pk2(d0[jj], d0[jj + 1]);
+      const uint64_t v2 = pk2(d1[jj], d1[jj + 1]);
+      const uint64_t a2 = t ? A.y : A.x, b2 = t ? B.y : B.x, g2 = t ? G.y : G.x;
+      const uint64_t w2 = ffma2(b2, v2, u2);
+      const uint64_t e2 = fmul2(g2, v2);
+      const uint64_t s2 = ffma2(fmul2(a2, w2), w2, fmul2(e2, v2));
+      uint32_t sa, sb;
+      upk2(s2, sa, sb);
+      smax = fmax3(smax, __uint_as_float(sa), __uint_as_float(sb));
+      smin = fmin3(smin, __uint_as_float(sa), __uint_as_float(sb));
     }
   }
+  return fmaxf(smax * st.c2, key1f(-smin * st.c1)) > st.best_lo;
+}
+
+// Rare path of a permuted chunk half: FP64 -ln p of every SNP that may beat
+// the running best; returns the new best.
+__device__ __noinline__ double minp_slow(const uint32_t *dv, const ChunkMeta &m,
+                                         const uint64_t *codes, int h, double cfac, int nan_cnt,
+                                         const uint16_t *nan_idx, double best, float best_lo,
+                                         float c1, float c2) {
+  const int jb = kEpiSnps * h;
+  const float *al = m.alpha + jb, *be = m.beta + jb, *ga = m.gamma + jb;
+  for (int j = 0; j < kEpiSnps; ++j) {
+    if (m.snp[jb + j] < 0) continue;
+    const float u = __uint_as_float(dv[j]), v = __uint_as_float(dv[kEpiSnps + j]);
+    double key = -1.0;
+    if (nan_cnt > 0) {
+      int n0, n1, n2;
+      pair_counts(nan_cnt, nan_idx, m, codes, jb + j, n0, n1, n2);
+      const int df = df_of(n0, n1, n2);
+      if (df > 0 && cfac > 0.0) key = key64_of(kw_H64((int)u, (int)v, n0, n1, n2, cfac), df);
+    } else {
+      const float sv = kw_s(u, v, al[j], be[j], ga[j]);
+      const float kf = sv > 0.f ? sv * c2 : key1f(-sv * c1);
+      if (kf > best_lo)
+        key = key64_of(kw_H64((int)u, (int)v, m.n[0][jb + j], m.n[1][jb + j], m.n[2][jb + j], cfac),
+                       m.df[jb + j]);
+    }
+    if (key > best) {
+      best = key;
+      best_lo = (float)key * 0.9999f;
+    }
+  }
+  return best;
 }
 
 __global__ void __launch_bounds__(kScanThreads, 1) krux_scan_kernel(const ScanParams p) {
@@ -469,6 +570,7 @@ __global__ void __launch_bounds__(kScanThreads, 1) krux_scan_kernel(const ScanPa
   const uint32_t drain = bar0 + 8u * (uint32_t)(2 * nA + 2 * nc + 2 * kTmemSlots);
   uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bars + 2 * nA + 2 * nc + 2 * kTmemSlots + 1);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_holder + 1);
+  unsigned int *seg_n = tmem_holder + 2;  // hits staged by this CTA
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < nA; ++s) {
@@ -485,6 +587,7 @@ __global__ void __launch_bounds__(kScanThreads, 1) krux_scan_kernel(const ScanPa
     }
     mbar_init(drain, 1);
     *abort_flag = 0;
+    *seg_n = 0u;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
@@ -547,9 +650,9 @@ __global__ void __launch_bounds__(kScanThreads, 1) krux_scan_kernel(const ScanPa
     producer_done:
       // let every copy this thread issued land before the CTA can exit
       for (int s = 0; s < nA; ++s)
-        if ((a_used >> s) & 1u) wait_bar(a_full(s), (a_last >> s) & 1u, wc, 10);
+        if ((a_used >> s) & 1u) wait_drain(a_full(s), (a_last >> s) & 1u, p.status, 10);
       for (int c = 0; c < nc; ++c)
-        if ((b_used >> c) & 1u) wait_bar(b_full(c), (b_last >> c) & 1u, wc, 11);
+        if ((b_used >> c) & 1u) wait_drain(b_full(c), (b_last >> c) & 1u, p.status, 11);
     }
     __syncwarp();
   } else if (warp == kMmaWarp) {
@@ -597,12 +700,12 @@ __global__ void __launch_bounds__(kScanThreads, 1) krux_scan_kernel(const ScanPa
     mma_done:
       // all issued MMAs must finish before TMEM is released
       tc_commit(drain);
-      wait_bar(drain, 0, wc, 12);
+      wait_drain(drain, 0, p.status, 12);
     }
     __syncwarp();
   } else {
     // epilogue warps
-    const int q = warp & 3, h = warp >> 2;
+    const int q = warp & 3, h = warp >> 2;  // lane quarter, SNP group of the chunk
     uint32_t slot = 0, slot_phase = 0, b_bits = 0;
     for (int it = blockIdx.x; it < p.n_items; it += gridDim.x) {
       const WorkItem w = p.items[it];
@@ -627,10 +730,12 @@ __global__ void __launch_bounds__(kScanThreads, 1) krux_scan_kernel(const ScanPa
         MinpState ms;
         ms.best = 0.0;
         ms.start = 0.0;
-        ms.c1 = (float)(et.cfac * (double)p.h1);
-        ms.c2 = (float)(et.cfac * (double)p.h2 * 0.5);
+        ms.c1 = 0.f;
+        ms.c2 = 0.f;
         double *key_ptr = nullptr;
         if (minp_mode && et.valid) {
+          ms.c1 = (float)(et.cfac * (double)p.h1);
+          ms.c2 = (float)(et.cfac * (double)p.h2 * 0.5);
           key_ptr = g.minp_key + (int64_t)(ag - 1) * g.T + et.trait;
           ms.start = __longlong_as_double((long long)__ldcg(reinterpret_cast<const unsigned long long *>(key_ptr)));
           ms.best = ms.start;
@@ -642,10 +747,11 @@ __global__ void __launch_bounds__(kScanThreads, 1) krux_scan_kernel(const ScanPa
           ok = ok && wait_bar(t_full(slot), slot_phase, wc, 7);
           if (!__all_sync(0xffffffffu, ok)) goto epi_done;
           tc_fence_after();
-          uint32_t d0[32], d1[32];
-          const uint32_t taddr = tmem_base + ((uint32_t)(32 * q) << 16) + slot * 128u + 32u * (uint32_t)h;
-          tmem_ld32(taddr, d0);
-          tmem_ld32(taddr + 64u, d1);
+          uint32_t d0[kEpiSnps], d1[kEpiSnps];
+          const uint32_t taddr =
+              tmem_base + ((uint32_t)(32 * q) << 16) + slot * 128u + (uint32_t)(kEpiSnps * h);
+          tmem_ld16(taddr, d0);
+          tmem_ld16(taddr + 64u, d1);
           tmem_wait_ld();
           tc_fence_before();
           __syncwarp();
@@ -656,10 +762,55 @@ __global__ void __launch_bounds__(kScanThreads, 1) krux_scan_kernel(const ScanPa
           }
           const uint64_t *codes =
               g.codes ? reinterpret_cast<const uint64_t *>(scodes + (size_t)c * codes_stride) : nullptr;
+          const ChunkMeta &mc = smeta[c];
+          bool need;
           if (minp_mode)
-            epilogue_minp(d0, d1, smeta[c], codes, h, et, p, ms);
+            need = et.valid && (et.nan_cnt > 0 || minp_fast(d0, d1, mc, h, ms));
           else
-            epilogue_chunk(d0, d1, smeta[c], codes, h, et, g, p, lane);
+            need = p.dense || et.nan_cnt > 0 || hit_fast(d0, d1, mc, h, et.ntlo, p.signed_coef != 0);
+          if (__any_sync(0xffffffffu, need)) {
+            if (minp_mode || __any_sync(0xffffffffu, p.dense || et.nan_cnt > 0)) {
+              // rare paths work on a local copy of the accumulators
+              uint32_t dv[2 * kEpiSnps];
+#pragma unroll
+              for (int j = 0; j < kEpiSnps; ++j) {
+                dv[j] = d0[j];
+                dv[kEpiSnps + j] = d1[j];
+              }
+              if (minp_mode) {
+                if (need) {
+                  ms.best = minp_slow(dv, mc, codes, h, et.cfac, et.nan_cnt, et.nan_idx, ms.best,
+                                      ms.best_lo, ms.c1, ms.c2);
+                  ms.best_lo = (float)ms.best * (1.f - p.margin);
+                }
+              } else {
+                hit_slow(dv, need, mc, codes, h, et.trait, et.valid, et.ntlo, et.nthi, et.cfac,
+                         et.nan_cnt, et.nan_idx, g, p, lane);
+              }
+            } else {
+              // classify the candidates in registers: above the band -> hit, inside -> FP64
+              uint32_t hm = 0;
+              const int jb = kEpiSnps * h;
+              if (need && et.valid) {
+                const float *al = mc.alpha + jb, *be = mc.beta + jb, *ga = mc.gamma + jb;
+#pragma unroll
+                for (int j = 0; j < kEpiSnps; ++j) {
+                  const float u = __uint_as_float(d0[j]), v = __uint_as_float(d1[j]);
+                  float sv = kw_s(u, v, al[j], be[j], ga[j]);
+                  if (p.signed_coef) sv = fabsf(sv);
+                  if (sv + et.ntlo >= 0.f && mc.snp[jb + j] >= 0) {
+                    bool hit = sv + et.nthi > 0.f;
+                    if (!hit)
+                      hit = decide64(u, v, mc.n[0][jb + j], mc.n[1][jb + j], mc.n[2][jb + j],
+                                     mc.df[jb + j], et.cfac, p.pthresh);
+                    if (hit) hm |= 1u << j;
+                  }
+                }
+              }
+              if (__any_sync(0xffffffffu, hm != 0u))
+                emit_hits(hm, d0, d1, mc, jb, et.trait, g, p, seg_n, lane);
+            }
+          }
           if (step == w.step_end - 1) {
             __syncwarp();
             if (lane == 0) mbar_arrive(b_empty(c));
@@ -676,9 +827,44 @@ __global__ void __launch_bounds__(kScanThreads, 1) krux_scan_kernel(const ScanPa
   }
 
   __syncthreads();
+  if (threadIdx.x == 0 && p.seg_cap > 0)
+    p.seg_cnt[blockIdx.x] = min(*seg_n, (unsigned int)p.seg_cap);
   if (warp == kMmaWarp) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem_base) : "memory");
+  }
+}
+
+// Appends every CTA's staged hits after the directly appended ones: block b
+// copies its segment to offset direct + sum_{c<b} seg_cnt[c] (entries past the
+// capacity are dropped); block 0 also writes the exact total.
+__global__ void seg_compact_kernel(const krux_hit *__restrict__ seg_hits,
+                                   const HitAux *__restrict__ seg_aux,
+                                   const unsigned int *__restrict__ seg_cnt, int seg_cap,
+                                   const unsigned long long *__restrict__ direct,
+                                   krux_hit *__restrict__ out, HitAux *__restrict__ out_aux,
+                                   int64_t capacity, unsigned long long *total) {
+  __shared__ unsigned long long off;
+  const int b = blockIdx.x;
+  if (threadIdx.x == 0) {
+    unsigned long long o = *direct;
+    for (int c = 0; c < b; ++c) o += seg_cnt[c];
+    off = o;
+    if (b == 0) {
+      unsigned long long t = *direct;
+      for (int c = 0; c < (int)gridDim.x; ++c) t += seg_cnt[c];
+      *total = t;
+    }
+  }
+  __syncthreads();
+  const unsigned int n = seg_cnt[b];
+  const size_t s0 = (size_t)b * seg_cap;
+  for (unsigned int i = threadIdx.x; i < n; i += blockDim.x) {
+    const unsigned long long o = off + i;
+    if (o < (unsigned long long)capacity) {
+      out[o] = seg_hits[s0 + i];
+      out_aux[o] = seg_aux[s0 + i];
+    }
   }
 }
 
@@ -707,6 +893,16 @@ __global__ void minp_from_key_kernel(const double *__restrict__ key, double *__r
 }
 
 }  // namespace
+
+cudaError_t launch_seg_compact(const krux_hit *seg_hits, const HitAux *seg_aux,
+                               const unsigned int *seg_cnt, int n_cta, int seg_cap,
+                               const unsigned long long *direct, krux_hit *out, HitAux *out_aux,
+                               int64_t capacity, unsigned long long *total, cudaStream_t s) {
+  if (n_cta <= 0) return cudaSuccess;
+  seg_compact_kernel<<<n_cta, 256, 0, s>>>(seg_hits, seg_aux, seg_cnt, seg_cap, direct, out, out_aux,
+                                           capacity, total);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_minp_from_key(const double *key, double *minp, int64_t n, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;

@@ -1,0 +1,95 @@
+"""Batched forms through the C ABI: permutation null (per-permutation, per-trait
+minimum p), several cohorts of uneven sample counts in one launch, and the
+bounded device-side wait."""
+import numpy as np
+import pytest
+
+import synth
+from kwcheck import check_hits
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def kx():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1307_3519_gb300 import build
+    build.build()
+    import paper_1307_3519_gb300 as k
+    ctx = k.Krux(0)
+    yield ctx
+    ctx.close()
+
+
+def _dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.mark.parametrize("T,S,P,N", [(200, 3000, 4, 102), (131, 700, 3, 60), (64, 1000, 2, 150)])
+def test_permutation_minp(kx, oracle_mod, T, S, P, N):
+    d = synth.config(4, T=T, S=S, N=N, seed=T + S)
+    perms = synth.make_perms(1307, P, N)
+    pth = 1e-3
+    rs = kx.krux_rank(_dev(d["expr"]))
+    res = kx.krux_permute(rs, _dev(d["geno"]), _dev(perms), pth, capacity=T * S)
+    want = oracle_mod.perm_minp(d["expr"], d["geno"], perms)
+    got = res["minp"].cpu().numpy()
+    assert got.shape == want.shape
+    assert np.all(np.abs(got - want) <= 1e-6 * want), \
+        f"max rel err {np.max(np.abs(got - want) / want)}"
+    orc = oracle_mod.scan(d["expr"], d["geno"], pth)
+    check_hits(res, orc, np.arange(T), np.arange(S), pth, must_have_hits=False)
+    assert res["n_hits"] == int(orc["hit"].sum())
+
+
+def test_permutation_rejects_bad_rows(kx):
+    import paper_1307_3519_gb300 as k
+    d = synth.config(4, T=10, S=50, seed=1)
+    perms = synth.make_perms(3, 2, d["N"])
+    perms[1, 0] = perms[1, 1]
+    rs = kx.krux_rank(_dev(d["expr"]))
+    with pytest.raises(k.KruxError) as e:
+        kx.krux_permute(rs, _dev(d["geno"]), _dev(perms), 1e-3, capacity=10)
+    assert e.value.status == k.KRUX_EINVAL
+
+
+def test_grouped_cohorts(kx, oracle_mod):
+    """Cohorts of uneven sample counts in one persistent launch, each against its
+    own genotypes (the multi-cohort workload at reduced T and S)."""
+    Ns = [48, 75, 102, 150, 200]
+    rng = np.random.default_rng(5)
+    cohorts, data = [], []
+    for n_c in Ns:
+        g, _ = synth.hwe_genotypes(rng, 700, n_c, 0.05, 0.5)
+        e = synth.expression_lognormal(rng, 150, n_c)
+        data.append((e, g))
+        cohorts.append(dict(rs=kx.krux_rank(_dev(e)), geno=_dev(g), capacity=150 * 700))
+    pth = 1e-2
+    out = kx.krux_scan_grouped(cohorts, pth)
+    for (e, g), res in zip(data, out):
+        orc = oracle_mod.scan(e, g, pth)
+        check_hits(res, orc, np.arange(150), np.arange(700), pth)
+        assert res["n_hits"] == int(orc["hit"].sum())
+
+
+def test_bounded_wait_reports_timeout_and_context_survives(kx, oracle_mod):
+    """With a one-cycle wait limit the first wait that has to spin gives up: the
+    kernel drains its copies, frees TMEM and the call returns KRUX_ETIMEOUT.  The
+    context stays usable and the next call with the default limit is correct."""
+    import paper_1307_3519_gb300 as k
+    d = synth.config(1, T=300, S=4000, seed=12)
+    rs = kx.krux_rank(_dev(d["expr"]))
+    g = _dev(d["geno"])
+    kx.set_wait_limit(1)
+    try:
+        with pytest.raises(k.KruxError) as e:
+            kx.krux_scan(rs, g, 1e-3, capacity=300 * 4000)
+        assert e.value.status == k.KRUX_ETIMEOUT
+    finally:
+        kx.set_wait_limit(0)
+    res = kx.krux_scan(rs, g, 1e-3, capacity=300 * 4000)
+    orc = oracle_mod.scan(d["expr"], d["geno"], 1e-3)
+    check_hits(res, orc, np.arange(300), np.arange(4000), 1e-3)
