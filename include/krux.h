@@ -166,6 +166,13 @@ krux_status krux_make_perms(uint64_t seed, int P, int N, int32_t *out);
 krux_status krux_set_profiling(krux_ctx *ctx, int enable);
 krux_status krux_get_profile(const krux_ctx *ctx, krux_profile *out);
 
+/* Tile-shape control for the autotuner and tests: layout 0 = 128-byte swizzled
+ * K atoms of 64 samples, 1 = 32-byte swizzled atoms of 16 samples, -1 = automatic;
+ * nc = SNP chunks (64 SNPs each) kept resident, nA = rank-tile pipeline stages
+ * (0, 0 = automatic).  A shape that does not fit shared memory makes the next
+ * scan return KRUX_EINVAL. */
+krux_status krux_set_tuning(krux_ctx *ctx, int layout, int nc, int nA);
+
 /* Test hook: device-side waits give up after `cycles` SM clock cycles (0 = the
  * default of about two seconds). */
 krux_status krux_set_wait_limit(krux_ctx *ctx, long long cycles);

@@ -26,7 +26,7 @@ STATUS_NAMES = ["KRUX_OK", "KRUX_EINVAL", "KRUX_ENOMEM", "KRUX_ECUDA", "KRUX_EOV
 EXPORTS = ["krux_create", "krux_destroy", "krux_status_string", "krux_last_error", "krux_rank",
            "krux_rankset_free", "krux_rankset_export", "krux_scan", "krux_scan_plain",
            "krux_permute", "krux_scan_grouped", "krux_make_perms", "krux_set_profiling",
-           "krux_get_profile", "krux_set_wait_limit"]
+           "krux_get_profile", "krux_set_wait_limit", "krux_set_tuning"]
 
 
 class KruxError(RuntimeError):
@@ -86,6 +86,7 @@ def load_library(path=LIB_PATH):
         "krux_set_profiling": ([P, I], I),
         "krux_get_profile": ([P, ctypes.POINTER(Profile)], I),
         "krux_set_wait_limit": ([P, ctypes.c_longlong], I),
+        "krux_set_tuning": ([P, I, I, I], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -172,6 +173,11 @@ class Krux:
         p = Profile()
         self._check(self.lib.krux_get_profile(self.handle, ctypes.byref(p)), "get_profile")
         return {f: getattr(p, f) for f, _ in Profile._fields_}
+
+    def set_tuning(self, layout=-1, nc=0, nA=0):
+        """Tile shape: layout (0: 64-sample atoms, 1: 16-sample atoms, -1 auto), nc
+        resident SNP chunks and nA rank-tile stages (0, 0 = automatic)."""
+        self._check(self.lib.krux_set_tuning(self.handle, layout, nc, nA), "set_tuning")
 
     def set_wait_limit(self, cycles):
         self._check(self.lib.krux_set_wait_limit(self.handle, int(cycles)), "set_wait_limit")

@@ -112,6 +112,7 @@ struct krux_ctx {
   bool profiling = false;
   krux_profile prof{};
   long long wait_limit = kDefaultWait;
+  int tune_layout = -1, tune_nc = 0, tune_nA = 0;  // 0 / -1 = automatic
   PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   cudaEvent_t ev[kEv] = {};
   DevBuf B, meta, codes, groups, items, status, counters, aux, cfacptr, miss_idx, miss_mask,
@@ -153,15 +154,18 @@ float ev_ms(krux_ctx *ctx, int a, int b) {
   return 0.f;
 }
 
-krux_status encode_map(krux_ctx *ctx, CUtensorMap *map, const void *base, int Np, int64_t rows) {
+int layout_atom(int layout) { return layout ? 16 : kAtomK; }
+
+krux_status encode_map(krux_ctx *ctx, CUtensorMap *map, const void *base, int Np, int64_t rows,
+                       int layout) {
   cuuint64_t dims[2] = {(cuuint64_t)Np, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)Np * 2};
-  cuuint32_t box[2] = {(cuuint32_t)kAtomK, (cuuint32_t)kTileM};
+  cuuint32_t box[2] = {(cuuint32_t)layout_atom(layout), (cuuint32_t)kTileM};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = ctx->encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<void *>(base), dims,
                            strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                           CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                           layout ? CU_TENSOR_MAP_SWIZZLE_32B : CU_TENSOR_MAP_SWIZZLE_128B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return fail(ctx, KRUX_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
   return KRUX_OK;
 }
@@ -171,7 +175,7 @@ krux_status encode_map(krux_ctx *ctx, CUtensorMap *map, const void *base, int Np
 bool pick_shape(int kpad, int &nc, int &nA) {
   const size_t limit = 232448;
   for (int c = 4; c >= 1; --c) {
-    for (int a = 4; a >= 2; --a) {
+    for (int a = 6; a >= 2; --a) {
       if (scan_smem_bytes(c, a, kpad) <= limit) {
         nc = c;
         nA = a;
@@ -366,6 +370,16 @@ krux_status krux_set_profiling(krux_ctx *ctx, int enable) {
 krux_status krux_get_profile(const krux_ctx *ctx, krux_profile *out) {
   if (!ctx || !out) return KRUX_EINVAL;
   *out = ctx->prof;
+  return KRUX_OK;
+}
+
+krux_status krux_set_tuning(krux_ctx *ctx, int layout, int nc, int nA) {
+  if (!ctx || layout < -1 || layout > 1 || nc < 0 || nA < 0 || nc > kTmemSlots || nA > 8 ||
+      ((nc == 0) != (nA == 0)))
+    return KRUX_EINVAL;
+  ctx->tune_layout = layout;
+  ctx->tune_nc = nc;
+  ctx->tune_nA = nA;
   return KRUX_OK;
 }
 
@@ -735,11 +749,19 @@ krux_status run_fused(krux_ctx *ctx, CallPlan &cp, const krux_opts *o, cudaStrea
   for (auto &g : cp.groups) signed_coef |= g.minp_key != nullptr ? 1 : 0;
   counts.assign(nslots, 0);
   if (ng == 0) return KRUX_OK;
-  int kpad = kAtomK;
-  for (auto &g : cp.groups) kpad = std::max(kpad, round_up(g.rs->Np, kAtomK));
+  const int layout = ctx->tune_layout >= 0 ? ctx->tune_layout : 1;
+  const int atom = layout_atom(layout);
+  int kpad = atom;
+  for (auto &g : cp.groups) kpad = std::max(kpad, round_up(g.rs->Np, atom));
   int nc = 0, nA = 0;
   if (!pick_shape(kpad, nc, nA))
     return fail(ctx, KRUX_EUNSUPPORTED, "N too large for the resident-B tile (Np=%d)", kpad);
+  if (ctx->tune_nc > 0 && ctx->tune_nA > 0) {
+    if (ctx->tune_nc > kTmemSlots || scan_smem_bytes(ctx->tune_nc, ctx->tune_nA, kpad) > 232448)
+      return fail(ctx, KRUX_EINVAL, "tuning shape nc=%d nA=%d does not fit", ctx->tune_nc, ctx->tune_nA);
+    nc = ctx->tune_nc;
+    nA = ctx->tune_nA;
+  }
   std::vector<int64_t> boff(ng), moff(ng), coff(ng);
   int64_t btot = 0, mtot = 0, ctot = 0;
   for (int i = 0; i < ng; ++i) {
@@ -775,9 +797,10 @@ krux_status run_fused(krux_ctx *ctx, CallPlan &cp, const krux_opts *o, cudaStrea
     GroupDesc &d = plans[i].d;
     std::memset(&d, 0, sizeof d);
     const int64_t nch = (g.n_snps + kChunkSnps - 1) / kChunkSnps;
-    krux_status st = encode_map(ctx, &d.tmA, g.A, rs->Np, (int64_t)rs->rows_pad * g.n_agroups);
+    krux_status st =
+        encode_map(ctx, &d.tmA, g.A, rs->Np, (int64_t)rs->rows_pad * g.n_agroups, layout);
     if (st != KRUX_OK) return st;
-    st = encode_map(ctx, &d.tmB, B, rs->Np, std::max<int64_t>(nch, 1) * kChunkRows);
+    st = encode_map(ctx, &d.tmB, B, rs->Np, std::max<int64_t>(nch, 1) * kChunkRows, layout);
     if (st != KRUX_OK) return st;
     d.meta = meta;
     d.codes = codes;
@@ -802,7 +825,7 @@ krux_status run_fused(krux_ctx *ctx, CallPlan &cp, const krux_opts *o, cudaStrea
     d.rows_per_agroup = rs->rows_pad;
     d.n_agroups = g.n_agroups;
     d.nchunks = (int32_t)nch;
-    d.n_atoms = (rs->Np + kAtomK - 1) / kAtomK;
+    d.n_atoms = (rs->Np + atom - 1) / atom;
     d.group_id = i;
     plans[i].n_btiles = (nch + nc - 1) / nc;
     plans[i].steps = (int64_t)g.n_agroups * rs->n_ttiles;
@@ -824,6 +847,7 @@ krux_status run_fused(krux_ctx *ctx, CallPlan &cp, const krux_opts *o, cudaStrea
   p.nc = nc;
   p.nA = nA;
   p.kpad = kpad;
+  p.layout = layout;
   p.margin = (float)(o->recheck_margin > 0 ? o->recheck_margin : 1e-4);
   p.dense = o->dense_H != nullptr ? 1 : 0;
   p.pthresh = o->pthresh;

@@ -64,8 +64,8 @@ struct RankDev {
 // ---- one group of a scan launch (a cohort, a missing-pattern bucket, or the
 // unpermuted + permuted rank matrices of a permutation batch) ----------------
 struct alignas(64) GroupDesc {
-  CUtensorMap tmA;          // 2D fp16 [rowsA][Np], box {64, 128}, 128B swizzle
-  CUtensorMap tmB;          // 2D fp16 [nchunks*128][Np], box {64, 128}, 128B swizzle
+  CUtensorMap tmA;          // 2D fp16 [rowsA][Np], box {atom K, 128}, swizzled
+  CUtensorMap tmB;          // 2D fp16 [nchunks*128][Np], box {atom K, 128}, swizzled
   const ChunkMeta *meta;    // [nchunks]
   const uint64_t *codes;    // [nchunks][Np][2] 2-bit genotype codes (3 = missing), or null
   const float *tau;         // [T]
@@ -98,7 +98,8 @@ struct ScanParams {
   int32_t n_items;
   int32_t nc;               // chunks per B tile
   int32_t nA;               // A pipeline stages
-  int32_t kpad;             // smem K width of a tile (multiple of 64)
+  int32_t kpad;             // smem K width of a tile (multiple of the layout's K atom)
+  int32_t layout;           // 0: 128-byte swizzle, 64-element atoms; 1: 32-byte swizzle, 16-element atoms
   float margin;             // relative band rechecked in FP64
   int32_t dense;            // 1: every pair's H, p written in FP64
   double pthresh;

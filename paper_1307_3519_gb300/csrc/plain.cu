@@ -77,9 +77,10 @@ plain_epilogue_kernel(const float *__restrict__ C, int64_t ldc, int T, int n_slo
     }
     const int groups = (n0 > 0) + (n1 > 0) + (n2 > 0);
     const int df = groups > 0 ? groups - 1 : 0;
-    const double cf = cfac[t];
+    const float tf = tau[t];  // K(K+1)C/3, +inf for degenerate traits; 1/tf = 3/(K(K+1)C)
     if (dense_H) {
       if (snp >= 0) {
+        const double cf = cfac[t];
         double H = 0.0;
         if (df > 0 && cf > 0.0) {
           const double D0 = u, D1 = v, D2 = -(double)(u + v);
@@ -95,26 +96,23 @@ plain_epilogue_kernel(const float *__restrict__ C, int64_t ldc, int T, int n_slo
         dense_p[o] = pv;
         hit = pv < pthresh;
       }
-    } else if (snp >= 0 && df > 0 && cf > 0.0) {
-      bool cand;
-      float hq = 0.f, hd = 1.f;
+    } else if (snp >= 0 && df > 0 && tf < __int_as_float(0x7f800000)) {
+      float hq, hd;
       if (nn == 0) {
         // alpha (u + beta v)^2 + gamma v^2 against tau (1 -/+ margin), as in the fused kernel
         const float w = fmaf(m.beta[jj], vf, uf);
-        const float q = fmaf(m.alpha[jj] * w, w, m.gamma[jj] * vf * vf);
-        hq = q;
-        hd = tau[t];
+        hq = fmaf(m.alpha[jj] * w, w, m.gamma[jj] * vf * vf);
+        hd = tf;
       } else {
         const float w = -(uf + vf);
         float Q = 0.f;
         if (n0) Q += uf * uf / (float)n0;
         if (n1) Q += vf * vf / (float)n1;
         if (n2) Q += w * w / (float)n2;
-        hq = (float)cf * Q;
+        hq = Q / tf;
         hd = df == 1 ? h1 : h2;
       }
-      cand = hq >= hd * (1.f - margin);
-      if (cand) {
+      if (hq >= hd * (1.f - margin)) {
         hit = hq > hd * (1.f + margin);
         if (!hit) {
           const double D0 = u, D1 = v, D2 = -(double)(u + v);
@@ -122,7 +120,7 @@ plain_epilogue_kernel(const float *__restrict__ C, int64_t ldc, int T, int n_slo
           if (n0) Qd += D0 * D0 / n0;
           if (n1) Qd += D1 * D1 / n1;
           if (n2) Qd += D2 * D2 / n2;
-          hit = p64_of(cf * Qd, df) < pthresh;
+          hit = p64_of(cfac[t] * Qd, df) < pthresh;
         }
       }
     }

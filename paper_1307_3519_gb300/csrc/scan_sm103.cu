@@ -28,21 +28,31 @@ namespace {
 // tcgen05 instruction descriptor, kind::f16: D = F32, A = B = F16, both K-major,
 // N = 128 (bits 17-22 hold N >> 3), M = 128 (bits 24-28 hold M >> 4).
 constexpr uint32_t kIdesc = (1u << 4) | ((uint32_t)(128 >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
-constexpr uint32_t kTileRowsBytes = 128 * 128;  // one 64-element (128 B) K atom of 128 rows
+// Two K-major shared-memory layouts: 128-byte swizzle with 64-element K atoms
+// (K padded to a multiple of 64, zero-filled by TMA), or 32-byte swizzle with
+// 16-element atoms (K padded to a multiple of 16 only).  An atom block holds 128
+// rows.
+__device__ __forceinline__ uint32_t atom_k(int layout) { return layout ? 16u : 64u; }
+__device__ __forceinline__ uint32_t atom_bytes(int layout) { return layout ? 4096u : 16384u; }
+// byte offset of K step k (16 elements) inside a tile
+__device__ __forceinline__ uint32_t kstep_off(int layout, int k) {
+  return layout ? (uint32_t)k * 4096u : (uint32_t)(k >> 2) * 16384u + (uint32_t)(k & 3) * 32u;
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-// Shared-memory matrix descriptor for a K-major tile in the 128-byte swizzle
-// layout: 8-row groups 1024 B apart (SBO), leading offset unused, version 1,
-// layout type 2 (128B swizzle).
-__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr) {
+// Shared-memory matrix descriptor of a K-major swizzled tile: start address,
+// leading offset (unused for these layouts), 8-row group stride (SBO: 1024 B for
+// the 128-byte swizzle, 256 B for the 32-byte swizzle), version 1, layout type
+// (2 = 128-byte swizzle, 6 = 32-byte swizzle).
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, int layout) {
   uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
   d |= (uint64_t)1u << 16;
-  d |= (uint64_t)(1024u >> 4) << 32;
+  d |= (uint64_t)((layout ? 256u : 1024u) >> 4) << 32;
   d |= (uint64_t)1u << 46;
-  d |= (uint64_t)2u << 61;
+  d |= (uint64_t)(layout ? 6u : 2u) << 61;
   return d;
 }
 
@@ -613,7 +623,7 @@ __global__ void __launch_bounds__(kScanThreads, 1) krux_scan_kernel(const ScanPa
         prefetch_map(&g->tmA);
         prefetch_map(&g->tmB);
         const int nc_item = min(nc, g->nchunks - w.btile * nc);
-        const uint32_t tile_tx = (uint32_t)g->n_atoms * kTileRowsBytes;
+        const uint32_t tile_tx = (uint32_t)g->n_atoms * atom_bytes(p.layout);
         const uint32_t codes_bytes = g->codes ? (uint32_t)g->Np * 16u : 0u;
         for (int c = 0; c < nc_item; ++c) {
           const uint32_t ph = (b_bits >> c) & 1u;
@@ -621,8 +631,8 @@ __global__ void __launch_bounds__(kScanThreads, 1) krux_scan_kernel(const ScanPa
           const int chunk = w.btile * nc + c;
           mbar_expect_tx(b_full(c), tile_tx + (uint32_t)sizeof(ChunkMeta) + codes_bytes);
           for (int a = 0; a < g->n_atoms; ++a)
-            tma_load_2d(sB + (uint32_t)c * tile_bytes + (uint32_t)a * kTileRowsBytes, &g->tmB,
-                        a * kAtomK, chunk * kChunkRows, b_full(c));
+            tma_load_2d(sB + (uint32_t)c * tile_bytes + (uint32_t)a * atom_bytes(p.layout), &g->tmB,
+                        a * (int)atom_k(p.layout), chunk * kChunkRows, b_full(c));
           bulk_load(smem_u32(smeta + c), g->meta + chunk, (uint32_t)sizeof(ChunkMeta), b_full(c));
           if (codes_bytes)
             bulk_load(smem_u32(scodes + (size_t)c * codes_stride), g->codes + (size_t)chunk * g->Np * 2,
@@ -637,8 +647,8 @@ __global__ void __launch_bounds__(kScanThreads, 1) krux_scan_kernel(const ScanPa
           if (!wait_bar(a_empty(a_stage), a_phase ^ 1u, wc, 2)) goto producer_done;
           mbar_expect_tx(a_full(a_stage), tile_tx);
           for (int a = 0; a < g->n_atoms; ++a)
-            tma_load_2d(sA + (uint32_t)a_stage * tile_bytes + (uint32_t)a * kTileRowsBytes, &g->tmA,
-                        a * kAtomK, row0, a_full(a_stage));
+            tma_load_2d(sA + (uint32_t)a_stage * tile_bytes + (uint32_t)a * atom_bytes(p.layout),
+                        &g->tmA, a * (int)atom_k(p.layout), row0, a_full(a_stage));
           a_used |= 1u << a_stage;
           a_last = (a_last & ~(1u << a_stage)) | (a_phase << a_stage);
           if (++a_stage == (uint32_t)nA) {
@@ -677,8 +687,9 @@ __global__ void __launch_bounds__(kScanThreads, 1) krux_scan_kernel(const ScanPa
             const uint32_t a_tile = sA + a_stage * tile_bytes;
             const uint32_t b_tile = sB + (uint32_t)c * tile_bytes;
             for (int k = 0; k < ksteps; ++k) {
-              const uint32_t off = (uint32_t)(k >> 2) * kTileRowsBytes + (uint32_t)(k & 3) * 32u;
-              tc_mma(d_tmem, umma_desc(a_tile + off), umma_desc(b_tile + off), kIdesc, k > 0 ? 1u : 0u);
+              const uint32_t off = kstep_off(p.layout, k);
+              tc_mma(d_tmem, umma_desc(a_tile + off, p.layout), umma_desc(b_tile + off, p.layout), kIdesc,
+                     k > 0 ? 1u : 0u);
             }
             tc_commit(t_full(slot));
             if (++slot == (uint32_t)kTmemSlots) {
@@ -868,6 +879,10 @@ __global__ void seg_compact_kernel(const krux_hit *__restrict__ seg_hits,
   }
 }
 
+// 1/n in FP64 for n = 0..kMaxN (entry 0 unused): the finalisation multiplies
+// instead of dividing (FP64 division is slow on this part).
+__constant__ double c_rcp[kMaxN + 1];
+
 // FP64 statistic and p-value of each stored hit, from its exact centred sums.
 __global__ void finalize_kernel(const krux_hit *__restrict__ hits, const HitAux *__restrict__ aux,
                                 int64_t n, const double *const *__restrict__ cfac_by_group,
@@ -878,7 +893,11 @@ __global__ void finalize_kernel(const krux_hit *__restrict__ hits, const HitAux 
     const HitAux a = aux[i];
     const double cf = cfac_by_group[a.group][r.trait];
     const int df = df_of(a.n0, a.n1, a.n2);
-    const double h = kw_H64(r.d0, r.d1, a.n0, a.n1, a.n2, cf);
+    const double D0 = (double)r.d0, D1 = (double)r.d1, D2 = -(double)(r.d0 + r.d1);
+    double Q = D0 * D0 * c_rcp[a.n0];
+    Q = fma(D1 * D1, c_rcp[a.n1], Q);
+    Q = fma(D2 * D2, c_rcp[a.n2], Q);
+    const double h = cf * Q;
     H[i] = h;
     P[i] = kw_p64(h, df);
   }
@@ -930,6 +949,17 @@ cudaError_t launch_finalize(const krux_hit *hits, const HitAux *aux, int64_t n,
                             const double *const *cfac_by_group, double *H, double *p,
                             cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
+  static int table_device = -1;  // the table is uploaded once per device
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (table_device != dev) {
+    double t[kMaxN + 1];
+    t[0] = 0.0;  // empty groups have D_i = 0 and contribute nothing
+    for (int k = 1; k <= kMaxN; ++k) t[k] = 1.0 / (double)k;
+    cudaError_t e = cudaMemcpyToSymbol(c_rcp, t, sizeof t);
+    if (e != cudaSuccess) return e;
+    table_device = dev;
+  }
   int grid = (int)((n + 255) / 256);
   if (grid > 152 * 8) grid = 152 * 8;
   finalize_kernel<<<grid, 256, 0, s>>>(hits, aux, n, cfac_by_group, H, p);

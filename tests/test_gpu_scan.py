@@ -182,3 +182,26 @@ def test_host_end_to_end(kx, oracle_mod):
     got = {(int(a), int(b)) for a, b in out["hits"][:, :2]}
     want = {tuple(x) for x in np.argwhere(orc["hit"]).tolist()}
     assert got == want
+
+
+@pytest.mark.parametrize("layout,nc,nA", [(0, 0, 0), (1, 0, 0), (1, 2, 4), (0, 3, 3), (1, 1, 2), (1, 4, 2)])
+@pytest.mark.parametrize("N", [60, 102, 150])
+def test_tile_shapes(kx, oracle_mod, layout, nc, nA, N):
+    """Every shared-memory layout and pipeline shape the tuner may pick gives
+    the oracle's hit set and exact rank sums."""
+    import paper_1307_3519_gb300 as k
+    d = synth.config(2, T=270, S=1300, N=N, seed=N + 3 * nc + layout)
+    pth = 2e-3
+    orc = oracle_mod.scan(d["expr"], d["geno"], pth)
+    rs = kx.krux_rank(_dev(d["expr"]))
+    kx.set_tuning(layout, nc, nA)
+    try:
+        res = kx.krux_scan(rs, _dev(d["geno"]), pth, capacity=270 * 1300)
+    except k.KruxError as e:
+        kx.set_tuning(-1, 0, 0)
+        assert e.status == k.KRUX_EINVAL  # shape does not fit this N
+        return
+    finally:
+        kx.set_tuning(-1, 0, 0)
+    check_hits(res, orc, np.arange(270), np.arange(1300), pth, must_have_hits=False)
+    assert res["n_hits"] == int(orc["hit"].sum())
