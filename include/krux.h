@@ -166,6 +166,32 @@ krux_status krux_make_perms(uint64_t seed, int P, int N, int32_t *out);
 krux_status krux_set_profiling(krux_ctx *ctx, int enable);
 krux_status krux_get_profile(const krux_ctx *ctx, krux_profile *out);
 
+/* Fused scan for callers that cannot allocate device memory (no paper
+ * counterpart: this is a deployment variant of krux_scan).  Code running under
+ * an allocator that owns the whole device, plugins inside such processes, and
+ * latency-critical paths where an allocation may block or fail can call this
+ * instead: it needs no context and calls no cudaMalloc, cudaFree or allocating
+ * library routine.  All scratch memory comes from one fixed 16 MiB device array
+ * inside the library, which every GPU that loads the library keeps until the
+ * process exits.
+ *   expr, T, N, ld, geno, S, ldg, pthresh : as krux_rank / krux_scan, with
+ *          T <= 4096, N <= 256 and complete genotypes (a -1 code returns
+ *          KRUX_EUNSUPPORTED); any S (SNPs are processed in slices of 4096).
+ *   hits, hit_H, hit_p : device outputs of hit_capacity entries.  At most
+ *          262,144 hits are stored per call; *n_hits (host) is always the exact
+ *          count, and KRUX_EOVERFLOW is returned when it exceeds what was stored.
+ * Sizes beyond these limits return KRUX_EINVAL before any device work.  The
+ * first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current, so make it before any stream
+ * capture.  Every call on a device shares the array, and the previous call's
+ * contents stay in it (each call clears what must start at zero); calls that
+ * overlap on the GPU race, so issue them on one stream or serialise them.  The
+ * call synchronises `stream` before returning. */
+krux_status krux_scan_noalloc(const float *expr, int T, int N, int64_t ld, const int8_t *geno,
+                              int64_t S, int64_t ldg, double pthresh, krux_hit *hits,
+                              double *hit_H, double *hit_p, int64_t hit_capacity,
+                              int64_t *n_hits, void *stream);
+
 /* Tile-shape control for the autotuner and tests: layout 0 = 128-byte swizzled
  * K atoms of 64 samples, 1 = 32-byte swizzled atoms of 16 samples, -1 = automatic;
  * nc = SNP chunks (64 SNPs each) kept resident, nA = rank-tile pipeline stages

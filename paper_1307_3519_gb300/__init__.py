@@ -26,7 +26,7 @@ STATUS_NAMES = ["KRUX_OK", "KRUX_EINVAL", "KRUX_ENOMEM", "KRUX_ECUDA", "KRUX_EOV
 EXPORTS = ["krux_create", "krux_destroy", "krux_status_string", "krux_last_error", "krux_rank",
            "krux_rankset_free", "krux_rankset_export", "krux_scan", "krux_scan_plain",
            "krux_permute", "krux_scan_grouped", "krux_make_perms", "krux_set_profiling",
-           "krux_get_profile", "krux_set_wait_limit", "krux_set_tuning"]
+           "krux_get_profile", "krux_set_wait_limit", "krux_set_tuning", "krux_scan_noalloc"]
 
 
 class KruxError(RuntimeError):
@@ -87,6 +87,7 @@ def load_library(path=LIB_PATH):
         "krux_get_profile": ([P, ctypes.POINTER(Profile)], I),
         "krux_set_wait_limit": ([P, ctypes.c_longlong], I),
         "krux_set_tuning": ([P, I, I, I], I),
+        "krux_scan_noalloc": ([P, I, I, I64, P, I64, I64, D, P, P, P, I64, ctypes.POINTER(I64), P], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -104,6 +105,20 @@ def _stream(stream=None):
     import torch
     s = stream if stream is not None else torch.cuda.current_stream()
     return ctypes.c_void_p(s.cuda_stream)
+
+
+def krux_scan_noalloc(expr, geno, pthresh, hits, hit_H, hit_p, stream=None):
+    """Scan without any device allocation by the library (see include/krux.h):
+    expr cuda float32 [T, N], geno cuda int8 [S, N], outputs preallocated by the
+    caller (hits int32 [cap, 4], hit_H / hit_p float64 [cap]).  Returns
+    (status, exact hit count)."""
+    n = ctypes.c_int64()
+    st = load_library().krux_scan_noalloc(
+        ctypes.c_void_p(expr.data_ptr()), expr.shape[0], expr.shape[1], expr.stride(0),
+        ctypes.c_void_p(geno.data_ptr()), geno.shape[0], geno.stride(0), float(pthresh),
+        ctypes.c_void_p(hits.data_ptr()), ctypes.c_void_p(hit_H.data_ptr()),
+        ctypes.c_void_p(hit_p.data_ptr()), hits.shape[0], ctypes.byref(n), _stream(stream))
+    return st, n.value
 
 
 def krux_make_perms(seed, P, N):
