@@ -194,10 +194,18 @@ krux_status krux_scan_noalloc(const float *expr, int T, int N, int64_t ld, const
 
 /* Tile-shape control for the autotuner and tests: layout 0 = 128-byte swizzled
  * K atoms of 64 samples, 1 = 32-byte swizzled atoms of 16 samples, -1 = automatic;
- * nc = SNP chunks (64 SNPs each) kept resident, nA = rank-tile pipeline stages
- * (0, 0 = automatic).  A shape that does not fit shared memory makes the next
- * scan return KRUX_EINVAL. */
-krux_status krux_set_tuning(krux_ctx *ctx, int layout, int nc, int nA);
+ * nc = SNP chunks (64 SNPs each) kept resident, nA = rank-tile pipeline stages,
+ * ka = samples per rank stage (a multiple of 64; 0 = the whole K); nc = nA = 0
+ * (and ka = 0) = automatic.  A shape that does not fit shared memory makes the
+ * next scan return KRUX_EINVAL. */
+krux_status krux_set_tuning(krux_ctx *ctx, int layout, int nc, int nA, int ka);
+
+/* Test hook (no GPU needed): the pipeline shape a scan of one group of N samples
+ * would use, after the same shared-memory plan check every launch passes.
+ * out[7] = {samples per rank stage, rank stages, B region bytes, resident
+ * chunks, K blocks per step, B chunk stride, shared-memory bytes}.  Returns
+ * KRUX_OK, or KRUX_EUNSUPPORTED if no sound plan exists. */
+krux_status krux_debug_plan(int N, int with_nan, int layout, int nc, int nA, int ka, int32_t *out);
 
 /* Test hook: device-side waits give up after `cycles` SM clock cycles (0 = the
  * default of about two seconds). */

@@ -26,7 +26,7 @@ STATUS_NAMES = ["KRUX_OK", "KRUX_EINVAL", "KRUX_ENOMEM", "KRUX_ECUDA", "KRUX_EOV
 EXPORTS = ["krux_create", "krux_destroy", "krux_status_string", "krux_last_error", "krux_rank",
            "krux_rankset_free", "krux_rankset_export", "krux_scan", "krux_scan_plain",
            "krux_permute", "krux_scan_grouped", "krux_make_perms", "krux_set_profiling",
-           "krux_get_profile", "krux_set_wait_limit", "krux_set_tuning", "krux_scan_noalloc"]
+           "krux_get_profile", "krux_set_wait_limit", "krux_set_tuning", "krux_scan_noalloc", "krux_debug_plan"]
 
 
 class KruxError(RuntimeError):
@@ -86,7 +86,8 @@ def load_library(path=LIB_PATH):
         "krux_set_profiling": ([P, I], I),
         "krux_get_profile": ([P, ctypes.POINTER(Profile)], I),
         "krux_set_wait_limit": ([P, ctypes.c_longlong], I),
-        "krux_set_tuning": ([P, I, I, I], I),
+        "krux_set_tuning": ([P, I, I, I, I], I),
+        "krux_debug_plan": ([I, I, I, I, I, I, P], I),
         "krux_scan_noalloc": ([P, I, I, I64, P, I64, I64, D, P, P, P, I64, ctypes.POINTER(I64), P], I),
     }
     for name, (args, res) in sig.items():
@@ -119,6 +120,15 @@ def krux_scan_noalloc(expr, geno, pthresh, hits, hit_H, hit_p, stream=None):
         ctypes.c_void_p(hits.data_ptr()), ctypes.c_void_p(hit_H.data_ptr()),
         ctypes.c_void_p(hit_p.data_ptr()), hits.shape[0], ctypes.byref(n), _stream(stream))
     return st, n.value
+
+
+def krux_debug_plan(N, with_nan=False, layout=-1, nc=0, nA=0, ka=0):
+    """(status, dict) of the pipeline shape a scan of N samples would use."""
+    out = np.zeros(7, dtype=np.int32)
+    st = load_library().krux_debug_plan(N, int(with_nan), layout, nc, nA, ka,
+                                        out.ctypes.data_as(ctypes.c_void_p))
+    keys = ["ka", "nA", "b_region", "nc", "nkb", "b_stride", "smem"]
+    return st, dict(zip(keys, out.tolist()))
 
 
 def krux_make_perms(seed, P, N):
@@ -189,10 +199,11 @@ class Krux:
         self._check(self.lib.krux_get_profile(self.handle, ctypes.byref(p)), "get_profile")
         return {f: getattr(p, f) for f, _ in Profile._fields_}
 
-    def set_tuning(self, layout=-1, nc=0, nA=0):
+    def set_tuning(self, layout=-1, nc=0, nA=0, ka=0):
         """Tile shape: layout (0: 64-sample atoms, 1: 16-sample atoms, -1 auto), nc
-        resident SNP chunks and nA rank-tile stages (0, 0 = automatic)."""
-        self._check(self.lib.krux_set_tuning(self.handle, layout, nc, nA), "set_tuning")
+        resident SNP chunks, nA rank-tile stages, ka samples per rank stage (0 =
+        whole K); nc = nA = 0 = automatic."""
+        self._check(self.lib.krux_set_tuning(self.handle, layout, nc, nA, ka), "set_tuning")
 
     def set_wait_limit(self, cycles):
         self._check(self.lib.krux_set_wait_limit(self.handle, int(cycles)), "set_wait_limit")

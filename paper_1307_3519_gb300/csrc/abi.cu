@@ -112,7 +112,7 @@ struct krux_ctx {
   bool profiling = false;
   krux_profile prof{};
   long long wait_limit = kDefaultWait;
-  int tune_layout = -1, tune_nc = 0, tune_nA = 0;  // 0 / -1 = automatic
+  int tune_layout = -1, tune_nc = 0, tune_nA = 0, tune_ka = 0;  // 0 / -1 = automatic
   PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   cudaEvent_t ev[kEv] = {};
   DevBuf B, meta, codes, groups, items, status, counters, aux, cfacptr, miss_idx, miss_mask,
@@ -170,20 +170,96 @@ krux_status encode_map(krux_ctx *ctx, CUtensorMap *map, const void *base, int Np
   return KRUX_OK;
 }
 
-// Pipeline shape for a shared-memory K width: chunks kept resident (nc) and A
-// stages (nA) that fit the 227 KB of shared memory of one CTA.
-bool pick_shape(int kpad, int &nc, int &nA) {
-  const size_t limit = 232448;
-  for (int c = 4; c >= 1; --c) {
-    for (int a = 6; a >= 2; --a) {
-      if (scan_smem_bytes(c, a, kpad) <= limit) {
-        nc = c;
-        nA = a;
-        return true;
-      }
+// Pipeline shape of one launch.  The A (rank) stages hold ka samples of 128
+// traits: the whole K when that leaves room for at least three resident SNP
+// chunks of the widest group, else K blocks of 64 samples.  b_region is the
+// shared memory left for resident B chunks; each group keeps as many of its own
+// chunks as fit (at most the 4 TMEM accumulator slots, at most 2 when its K is
+// split into blocks, so that its accumulators stay double-buffered).
+struct LaunchShape {
+  int ka = 0, nA = 0, b_region = 0, force_nc = 0, no_pair = 0;
+};
+constexpr size_t kSmemLimit = 232448;
+
+size_t shape_overhead(int nA, int codes_k) {
+  return scan_smem_bytes2(kTmemSlots, nA, 0, 0, std::max(codes_k, 16));
+}
+
+bool pick_launch_shape(const krux_ctx *ctx, int kpad, int codes_k, LaunchShape &sh) {
+  const size_t chunk = (size_t)256 * kpad;
+  if (ctx->tune_nc > 0) {  // explicit shape (tests, autotuner)
+    sh.ka = ctx->tune_ka > 0 ? ctx->tune_ka : kpad;
+    sh.nA = ctx->tune_nA;
+    sh.b_region = (int)(chunk * ctx->tune_nc);
+    sh.force_nc = ctx->tune_nc;
+    if (sh.ka % 64 != 0 && sh.ka != kpad) return false;
+    return shape_overhead(sh.nA, codes_k) + (size_t)sh.nA * 256 * sh.ka + sh.b_region <= kSmemLimit;
+  }
+  for (int a = 3; a >= 2; --a) {  // whole K per stage
+    const size_t used = shape_overhead(a, codes_k) + (size_t)a * chunk;
+    if (used < kSmemLimit && (kSmemLimit - used) / chunk >= 3) {
+      sh.ka = kpad;
+      sh.nA = a;
+      sh.b_region = (int)(std::min<size_t>(kTmemSlots, (kSmemLimit - used) / chunk) * chunk);
+      return true;
     }
   }
-  return false;
+  int best_nc = 0;
+  for (int a = 4; a >= 2; --a) {  // K blocks of 64 samples
+    const size_t used = shape_overhead(a, codes_k) + (size_t)a * 256 * 64;
+    if (used >= kSmemLimit) continue;
+    // keep every region after B on a 1024-byte boundary (TMA and vector loads)
+    const size_t region = (kSmemLimit - used) / 1024 * 1024;
+    const int nc = (int)std::min<size_t>(2, region / chunk);
+    if (nc > best_nc) {
+      best_nc = nc;
+      sh.ka = 64;
+      sh.nA = a;
+      sh.b_region = (int)region;
+    }
+  }
+  return best_nc >= 1;
+}
+
+// Refuses a launch plan whose shared-memory regions or per-group shapes are not
+// aligned or do not fit: every TMA destination and vector load must stay
+// aligned and inside its region.  Returns an empty string when the plan is sound.
+std::string validate_plan(const ScanParams &p, const std::vector<GroupDesc> &g, size_t smem) {
+  char buf[256];
+  auto bad = [&](const char *what) {
+    snprintf(buf, sizeof buf, "internal launch plan check failed: %s", what);
+    return std::string(buf);
+  };
+  const int atom = p.layout ? 16 : 64;
+  if (smem > kSmemLimit) return bad("shared memory above the per-CTA limit");
+  if (p.nA < 1 || p.nc < 1 || p.nc > kTmemSlots) return bad("stage or chunk count");
+  if (p.a_tile_bytes % 1024 || p.b_region % 1024 || p.a_tile_bytes != 256 * p.ka) return bad("region alignment");
+  if (p.ka % atom || p.kpad % 16) return bad("K widths");
+  if ((size_t)p.nA * p.a_tile_bytes + (size_t)p.b_region + 1024 > smem) return bad("regions exceed the allocation");
+  for (const GroupDesc &d : g) {
+    if (d.nc < 1 || d.nc > p.nc) return bad("group chunk count");
+    if (d.b_stride % 4096 || (int64_t)d.nc * d.b_stride > p.b_region) return bad("group B chunks");
+    if (d.b_stride < 256 * d.n_atoms * atom) return bad("group B stride");
+    if ((int64_t)d.nkb * p.ka < (int64_t)d.n_atoms * atom || d.nkb < 1) return bad("group K blocks");
+    if (d.nkb > 1 && d.nc * 2 > kTmemSlots) return bad("TMEM slots for K blocks");
+    if (d.Np % 16 || d.Np > d.n_atoms * atom) return bad("group K width");
+    if (d.codes && d.Np > p.kpad) return bad("codes width");
+    if (d.pair && (p.layout != 1 || d.nc % 2 != 0)) return bad("chunk pairs");
+  }
+  return std::string();
+}
+
+// Per-group share of a launch shape.
+void group_shape(const LaunchShape &sh, int kpad_g, int atom, GroupDesc &d) {
+  d.b_stride = 256 * kpad_g;
+  const int atoms_per_block = sh.ka / atom;
+  d.nkb = (d.n_atoms + atoms_per_block - 1) / atoms_per_block;
+  int nc = (int)std::min<int64_t>(kTmemSlots, sh.b_region / d.b_stride);
+  if (d.nkb > 1) nc = std::min(nc, 2);
+  if (sh.force_nc > 0) nc = std::min(nc, sh.force_nc);
+  d.nc = std::max(nc, 1);
+  // N = 256 MMAs over chunk pairs (32-byte swizzle layout, even chunk count)
+  d.pair = (atom == 16 && d.nc >= 2 && d.nc % 2 == 0 && !sh.no_pair) ? 1 : 0;
 }
 
 struct GroupPlan {
@@ -256,9 +332,9 @@ krux_status alloc_rankset(krux_ctx *ctx, krux_rankset *rs, int T, int N, bool wi
   const size_t oeq = with_lists ? take((size_t)T * N * 2) : 0;
   const size_t otie = take((size_t)T * 8);
   const size_t oK = take((size_t)T * 4);
-  const size_t otau = take((size_t)T * 4);
-  const size_t ocf = take((size_t)T * 8);
-  const size_t onc = take((size_t)T * 2);
+  const size_t otau = take((size_t)rs->rows_pad * 4);
+  const size_t ocf = take((size_t)rs->rows_pad * 8);
+  const size_t onc = take((size_t)rs->rows_pad * 2);
   const size_t oni = take((size_t)T * N * 2);
   const size_t otn = take((size_t)rs->n_ttiles * 4);
   rs->mem = nullptr;
@@ -373,13 +449,14 @@ krux_status krux_get_profile(const krux_ctx *ctx, krux_profile *out) {
   return KRUX_OK;
 }
 
-krux_status krux_set_tuning(krux_ctx *ctx, int layout, int nc, int nA) {
+krux_status krux_set_tuning(krux_ctx *ctx, int layout, int nc, int nA, int ka) {
   if (!ctx || layout < -1 || layout > 1 || nc < 0 || nA < 0 || nc > kTmemSlots || nA > 8 ||
-      ((nc == 0) != (nA == 0)))
+      ((nc == 0) != (nA == 0)) || ka < 0 || ka % 64 != 0 || (ka > 0 && nc == 0))
     return KRUX_EINVAL;
   ctx->tune_layout = layout;
   ctx->tune_nc = nc;
   ctx->tune_nA = nA;
+  ctx->tune_ka = ka;
   return KRUX_OK;
 }
 
@@ -601,9 +678,9 @@ size_t bucket_bytes(const krux_rankset *rs) {
   take((size_t)rs->rows_pad * rs->Np * 2);
   take((size_t)rs->T * 8);
   take((size_t)rs->T * 4);
-  take((size_t)rs->T * 4);
-  take((size_t)rs->T * 8);
-  take((size_t)rs->T * 2);
+  take((size_t)rs->rows_pad * 4);
+  take((size_t)rs->rows_pad * 8);
+  take((size_t)rs->rows_pad * 2);
   take((size_t)rs->T * rs->N * 2);
   take((size_t)rs->n_ttiles * 4);
   return off;
@@ -714,9 +791,9 @@ krux_status materialise(krux_ctx *ctx, CallPlan &cp, cudaStream_t s) {
     bs.dev.A = (__half *)take((size_t)rs->rows_pad * rs->Np * 2);
     bs.dev.tie = (int64_t *)take((size_t)rs->T * 8);
     bs.dev.K = (int32_t *)take((size_t)rs->T * 4);
-    bs.dev.tau = (float *)take((size_t)rs->T * 4);
-    bs.dev.cfac = (double *)take((size_t)rs->T * 8);
-    bs.dev.nan_cnt = (uint16_t *)take((size_t)rs->T * 2);
+    bs.dev.tau = (float *)take((size_t)rs->rows_pad * 4);
+    bs.dev.cfac = (double *)take((size_t)rs->rows_pad * 8);
+    bs.dev.nan_cnt = (uint16_t *)take((size_t)rs->rows_pad * 2);
     bs.dev.nan_idx = (uint16_t *)take((size_t)rs->T * rs->N * 2);
     bs.dev.tile_nan = (uint32_t *)take((size_t)rs->n_ttiles * 4);
     KRUX_CUDA(ctx, cudaMemsetAsync(bs.dev.A, 0, (size_t)rs->rows_pad * rs->Np * 2, s));
@@ -751,17 +828,17 @@ krux_status run_fused(krux_ctx *ctx, CallPlan &cp, const krux_opts *o, cudaStrea
   if (ng == 0) return KRUX_OK;
   const int layout = ctx->tune_layout >= 0 ? ctx->tune_layout : 1;
   const int atom = layout_atom(layout);
-  int kpad = atom;
-  for (auto &g : cp.groups) kpad = std::max(kpad, round_up(g.rs->Np, atom));
-  int nc = 0, nA = 0;
-  if (!pick_shape(kpad, nc, nA))
-    return fail(ctx, KRUX_EUNSUPPORTED, "N too large for the resident-B tile (Np=%d)", kpad);
-  if (ctx->tune_nc > 0 && ctx->tune_nA > 0) {
-    if (ctx->tune_nc > kTmemSlots || scan_smem_bytes(ctx->tune_nc, ctx->tune_nA, kpad) > 232448)
-      return fail(ctx, KRUX_EINVAL, "tuning shape nc=%d nA=%d does not fit", ctx->tune_nc, ctx->tune_nA);
-    nc = ctx->tune_nc;
-    nA = ctx->tune_nA;
+  int kpad = atom, codes_k = 0;
+  for (auto &g : cp.groups) {
+    kpad = std::max(kpad, round_up(g.rs->Np, atom));
+    if (g.nan_cnt) codes_k = std::max(codes_k, g.rs->Np);
   }
+  LaunchShape sh;
+  if (!pick_launch_shape(ctx, kpad, codes_k, sh))
+    return fail(ctx, ctx->tune_nc > 0 ? KRUX_EINVAL : KRUX_EUNSUPPORTED,
+                "no pipeline shape fits shared memory (Np=%d, tuning nc=%d nA=%d ka=%d)", kpad,
+                ctx->tune_nc, ctx->tune_nA, ctx->tune_ka);
+  const int nA = sh.nA;
   std::vector<int64_t> boff(ng), moff(ng), coff(ng);
   int64_t btot = 0, mtot = 0, ctot = 0;
   for (int i = 0; i < ng; ++i) {
@@ -785,6 +862,7 @@ krux_status run_fused(krux_ctx *ctx, CallPlan &cp, const krux_opts *o, cudaStrea
   ev_record(ctx, 2, s);
   std::vector<GroupDesc> descs(ng);
   std::vector<GroupPlan> plans(ng);
+  int nc_max = 1;
   for (int i = 0; i < ng; ++i) {
     ScanGroupIn &g = cp.groups[i];
     const krux_rankset *rs = g.rs;
@@ -827,12 +905,14 @@ krux_status run_fused(krux_ctx *ctx, CallPlan &cp, const krux_opts *o, cudaStrea
     d.nchunks = (int32_t)nch;
     d.n_atoms = (rs->Np + atom - 1) / atom;
     d.group_id = i;
-    plans[i].n_btiles = (nch + nc - 1) / nc;
+    group_shape(sh, round_up(rs->Np, atom), atom, d);
+    nc_max = std::max(nc_max, d.nc);
+    plans[i].n_btiles = (nch + d.nc - 1) / d.nc;
     plans[i].steps = (int64_t)g.n_agroups * rs->n_ttiles;
     descs[i] = d;
   }
   ev_record(ctx, 3, s);
-  std::vector<WorkItem> items = make_items(plans, nc, ctx->sm_count);
+  std::vector<WorkItem> items = make_items(plans, nc_max, ctx->sm_count);
   KRUX_CUDA(ctx, ctx->groups.ensure(sizeof(GroupDesc) * ng));
   KRUX_CUDA(ctx, ctx->items.ensure(sizeof(WorkItem) * std::max<size_t>(items.size(), 1)));
   KRUX_CUDA(ctx, cudaMemcpyAsync(ctx->groups.p, descs.data(), sizeof(GroupDesc) * ng,
@@ -844,9 +924,12 @@ krux_status run_fused(krux_ctx *ctx, CallPlan &cp, const krux_opts *o, cudaStrea
   p.groups = ctx->groups.as<GroupDesc>();
   p.items = ctx->items.as<WorkItem>();
   p.n_items = (int32_t)items.size();
-  p.nc = nc;
+  p.nc = nc_max;
   p.nA = nA;
-  p.kpad = kpad;
+  p.kpad = std::max(codes_k, 16);
+  p.ka = sh.ka;
+  p.a_tile_bytes = 256 * sh.ka;
+  p.b_region = sh.b_region;
   p.layout = layout;
   p.margin = (float)(o->recheck_margin > 0 ? o->recheck_margin : 1e-4);
   p.dense = o->dense_H != nullptr ? 1 : 0;
@@ -871,7 +954,12 @@ krux_status run_fused(krux_ctx *ctx, CallPlan &cp, const krux_opts *o, cudaStrea
     p.seg_aux = reinterpret_cast<HitAux *>(sb + (size_t)grid * seg_cap * sizeof(krux_hit));
     p.seg_cnt = reinterpret_cast<unsigned int *>(sb + (size_t)grid * seg_cap * rec);
   }
-  if (grid > 0) KRUX_CUDA(ctx, launch_scan(p, grid, scan_smem_bytes(nc, nA, kpad), s));
+  const size_t smem = scan_smem_bytes2(nc_max, nA, (size_t)p.a_tile_bytes, (size_t)p.b_region, p.kpad);
+  {
+    const std::string why = validate_plan(p, descs, smem);
+    if (!why.empty()) return fail(ctx, KRUX_EUNSUPPORTED, "%s", why.c_str());
+  }
+  if (grid > 0) KRUX_CUDA(ctx, launch_scan(p, grid, smem, s));
   unsigned long long *totals = ctx->counters.as<unsigned long long>() + nslots;
   if (staged) {
     KRUX_CUDA(ctx, launch_seg_compact(p.seg_hits, p.seg_aux, p.seg_cnt, grid, p.seg_cap,
@@ -1145,8 +1233,8 @@ extern "C" krux_status krux_permute(krux_ctx *ctx, const krux_rankset *rs, const
   __half *stack = ctx->permA.as<__half>();
   KRUX_CUDA(ctx, cudaMemcpyAsync(stack, rs->dev.A, one * 2, cudaMemcpyDeviceToDevice, s));
   KRUX_CUDA(ctx, launch_permute_rows(rs->dev.A, stack + one, rs->rows_pad, rs->Np, N, perms, P, s));
-  KRUX_CUDA(ctx, ctx->minpkey.ensure((size_t)P * rs->T * 8));
-  KRUX_CUDA(ctx, cudaMemsetAsync(ctx->minpkey.p, 0, (size_t)P * rs->T * 8, s));
+  KRUX_CUDA(ctx, ctx->minpkey.ensure((size_t)P * rs->rows_pad * 8));
+  KRUX_CUDA(ctx, cudaMemsetAsync(ctx->minpkey.p, 0, (size_t)P * rs->rows_pad * 8, s));
   KRUX_CUDA(ctx, ctx->aux.ensure((size_t)std::max<int64_t>(opts->hit_capacity, 1) * sizeof(HitAux)));
   CallPlan cp;
   cp.slots.push_back(OutSlot{hits, hit_H, hit_p, opts->hit_capacity, ctx->aux.as<HitAux>()});
@@ -1158,7 +1246,7 @@ extern "C" krux_status krux_permute(krux_ctx *ctx, const krux_rankset *rs, const
   std::vector<unsigned long long> counts;
   st = run_fused(ctx, cp, opts, s, counts);
   if (st != KRUX_OK) return st;
-  KRUX_CUDA(ctx, launch_minp_from_key(ctx->minpkey.as<double>(), minp, (int64_t)P * rs->T, s));
+  KRUX_CUDA(ctx, launch_minp_from_key(ctx->minpkey.as<double>(), minp, P, rs->T, rs->rows_pad, s));
   KRUX_CUDA(ctx, cudaStreamSynchronize(s));
   if (ctx->profiling) ctx->prof.launches += 2;
   *n_hits = (int64_t)counts[0];
@@ -1166,4 +1254,46 @@ extern "C" krux_status krux_permute(krux_ctx *ctx, const krux_rankset *rs, const
     return fail(ctx, KRUX_EOVERFLOW, "%lld hits exceed capacity %lld", (long long)*n_hits,
                 (long long)opts->hit_capacity);
   return KRUX_OK;
+}
+
+// Test hook: the launch plan for one group of N samples (no GPU needed).
+extern "C" krux_status krux_debug_plan(int N, int with_nan, int layout, int nc, int nA, int ka,
+                                       int32_t *out) {
+  if (N < 1 || N > kMaxN || !out) return KRUX_EINVAL;
+  krux_ctx tmp;
+  tmp.tune_layout = layout;
+  tmp.tune_nc = nc;
+  tmp.tune_nA = nA;
+  tmp.tune_ka = ka;
+  const int lay = layout >= 0 ? layout : 1;
+  const int atom = layout_atom(lay);
+  const int Np = round_up(N, 16);
+  const int kpad = round_up(Np, atom);
+  const int codes_k = with_nan ? Np : 0;
+  LaunchShape sh;
+  if (!pick_launch_shape(&tmp, kpad, codes_k, sh)) return KRUX_EUNSUPPORTED;
+  GroupDesc d;
+  std::memset(&d, 0, sizeof d);
+  d.Np = Np;
+  d.n_atoms = (Np + atom - 1) / atom;
+  d.codes = with_nan ? reinterpret_cast<const uint64_t *>(16) : nullptr;
+  group_shape(sh, kpad, atom, d);
+  ScanParams p{};
+  p.nc = d.nc;
+  p.nA = sh.nA;
+  p.kpad = std::max(codes_k, 16);
+  p.ka = sh.ka;
+  p.a_tile_bytes = 256 * sh.ka;
+  p.b_region = sh.b_region;
+  p.layout = lay;
+  const size_t smem = scan_smem_bytes2(p.nc, p.nA, (size_t)p.a_tile_bytes, (size_t)p.b_region, p.kpad);
+  out[0] = sh.ka;
+  out[1] = sh.nA;
+  out[2] = sh.b_region;
+  out[3] = d.nc;
+  out[4] = d.nkb;
+  out[5] = d.b_stride;
+  out[6] = (int32_t)smem;
+  const std::string why = validate_plan(p, std::vector<GroupDesc>{d}, smem);
+  return why.empty() ? KRUX_OK : KRUX_EUNSUPPORTED;
 }

@@ -24,6 +24,11 @@ constexpr int kEpiSnps = 16;       // SNPs of a chunk each epilogue warp evaluat
 constexpr int kProducerWarp = 16;  // TMA producer
 constexpr int kMmaWarp = 17;       // tcgen05.mma issuer, owns the TMEM allocation
 constexpr int kScanThreads = 576;
+// Per-step trait constants staged in shared memory by the producer (one entry per
+// 128-trait tile step): tau f32 [128] @0, 3/(K(K+1)C) f64 [128] @512, starting
+// -ln p key f64 [128] @1536 (permutation batches), NaN count u16 [128] @2560.
+constexpr int kTcDepth = 4;
+constexpr int kTcBytes = 2816;
 
 // ---- per-chunk SNP metadata (one 1536-byte blob per chunk of 64 SNPs) ------
 // Fast-test coefficients: with u = D_0, v = D_1 (D_2 = -u - v) the statistic's
@@ -54,9 +59,9 @@ struct RankDev {
   uint16_t *eq;         // [T][N] #present values equal (itself included), 0 at NaN
   int64_t *tie;         // [T] sum over present samples of eq^2 - 1 = sum (t^3 - t)
   int32_t *K;           // [T] present samples
-  float *tau;           // [T] K(K+1)C/3 (fast-test bound), +inf when degenerate
-  double *cfac;         // [T] 3 / (K(K+1)C), 0 when degenerate
-  uint16_t *nan_cnt;    // [T] NaN samples of the trait
+  float *tau;           // [rows_pad] K(K+1)C/3 (fast-test bound), +inf when degenerate or padding
+  double *cfac;         // [rows_pad] 3 / (K(K+1)C), 0 when degenerate or padding
+  uint16_t *nan_cnt;    // [rows_pad] NaN samples of the trait (0 for padding)
   uint16_t *nan_idx;    // [T][N] their sample indices (first nan_cnt entries)
   uint32_t *tile_nan;   // [rows_pad/128] 1 if any trait of the tile has a NaN
 };
@@ -77,13 +82,17 @@ struct alignas(64) GroupDesc {
   HitAux *aux;              // side records
   unsigned long long *counter;  // hits found (keeps counting past capacity)
   double *dense_H, *dense_p;    // optional [T][dense_ld]
-  double *minp_key;         // permutation mode: [n_agroups-1][T] best -ln p (as double bits)
+  double *minp_key;         // permutation mode: [n_agroups-1][rows_per_agroup] best -ln p (as double bits)
   int64_t capacity;
   int64_t dense_ld;
   int64_t dense_snp0;       // SNP index of dense column 0
   int32_t T, N, Np, n_ttiles, rows_per_agroup, n_agroups, nchunks, n_atoms;
   int32_t group_id;
-  int32_t pad_[7];
+  int32_t nc;               // SNP chunks of one B tile (resident together)
+  int32_t b_stride;         // shared-memory bytes of one resident B chunk
+  int32_t nkb;              // rank-tile K blocks per step (1 = the whole K at once)
+  int32_t pair;             // 1: chunks 2j, 2j+1 interleaved per K atom, one N = 256 MMA per pair
+  int32_t pad_[3];
 };
 
 // Work item: B tile `btile` (chunks btile*nc .. +nc) of group `group`, against the
@@ -96,9 +105,12 @@ struct ScanParams {
   const GroupDesc *groups;
   const WorkItem *items;
   int32_t n_items;
-  int32_t nc;               // chunks per B tile
+  int32_t nc;               // most chunks any group keeps resident (<= kTmemSlots)
   int32_t nA;               // A pipeline stages
-  int32_t kpad;             // smem K width of a tile (multiple of the layout's K atom)
+  int32_t kpad;             // widest K of the groups (codes rows are kpad * 16 bytes)
+  int32_t ka;               // samples per A stage (a K block; multiple of the layout's atom)
+  int32_t a_tile_bytes;     // 128 * ka * 2
+  int32_t b_region;         // shared-memory bytes for the resident B chunks
   int32_t layout;           // 0: 128-byte swizzle, 64-element atoms; 1: 32-byte swizzle, 16-element atoms
   float margin;             // relative band rechecked in FP64
   int32_t dense;            // 1: every pair's H, p written in FP64
@@ -125,11 +137,15 @@ cudaError_t launch_permute_rows(const __half *A, __half *out, int rows_pad, int 
                                 const int32_t *perms, int P, cudaStream_t s);
 cudaError_t launch_scan(const ScanParams &p, int grid, size_t smem, cudaStream_t s);
 size_t scan_smem_bytes(int nc, int nA, int kpad);
+size_t scan_smem_bytes2(int nc, int nA, size_t a_tile_bytes, size_t b_region, int codes_k);
 cudaError_t launch_seg_compact(const krux_hit *seg_hits, const HitAux *seg_aux,
                                const unsigned int *seg_cnt, int n_cta, int seg_cap,
                                const unsigned long long *direct, krux_hit *out, HitAux *out_aux,
                                int64_t capacity, unsigned long long *total, cudaStream_t s);
-cudaError_t launch_minp_from_key(const double *key, double *minp, int64_t n, cudaStream_t s);
+cudaError_t launch_minp_from_key(const double *key, double *minp, int P, int T, int ld,
+                                 cudaStream_t s);
+cudaError_t launch_pad_traits(int T, int rows_pad, float *tau, double *cfac, uint16_t *nan_cnt,
+                              cudaStream_t s);
 cudaError_t launch_finalize(const krux_hit *hits, const HitAux *aux, int64_t n,
                             const double *const *cfac_by_group, double *H, double *p,
                             cudaStream_t s);

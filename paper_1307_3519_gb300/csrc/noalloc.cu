@@ -241,6 +241,9 @@ extern "C" krux_status krux_scan_noalloc(const float *expr, int T, int N, int64_
     g.nchunks = (int32_t)nch;
     g.n_atoms = Np / 16;
     g.group_id = 0;
+    g.nc = nc;
+    g.b_stride = 256 * Np;
+    g.nkb = 1;
     // work items: one B tile of nc chunks against all trait tiles, split to fill the SMs
     WorkItem items[kNaMaxItems];
     const int64_t nbt = (nch + nc - 1) / nc;
@@ -261,6 +264,9 @@ extern "C" krux_status krux_scan_noalloc(const float *expr, int T, int N, int64_
     p.nc = nc;
     p.nA = nA;
     p.kpad = Np;
+    p.ka = Np;
+    p.a_tile_bytes = 256 * Np;
+    p.b_region = nc * 256 * Np;
     p.layout = 1;
     p.margin = 1e-4f;
     p.dense = 0;

@@ -108,13 +108,30 @@ __global__ void permute_rows_kernel(const __half *__restrict__ A, __half *__rest
 }
 }  // namespace
 
+// Per-trait constants of the padding rows of the last 128-trait tile: never a hit.
+__global__ void pad_traits_kernel(int T, int rows_pad, float *tau, double *cfac, uint16_t *nan_cnt) {
+  const int t = T + blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= rows_pad) return;
+  tau[t] = __int_as_float(0x7f800000);
+  cfac[t] = 0.0;
+  nan_cnt[t] = 0;
+}
+
+cudaError_t launch_pad_traits(int T, int rows_pad, float *tau, double *cfac, uint16_t *nan_cnt,
+                              cudaStream_t s) {
+  if (rows_pad <= T) return cudaSuccess;
+  pad_traits_kernel<<<1, 128, 0, s>>>(T, rows_pad, tau, cfac, nan_cnt);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_rank(const float *expr, int T, int N, int64_t ld, int Np, int rows_pad,
                         const RankDev &r, cudaStream_t s) {
-  (void)rows_pad;
   const int grid = (T + kRankWarps - 1) / kRankWarps;
   const size_t smem = (size_t)kRankWarps * N * sizeof(float);
   rank_kernel<<<grid, kRankWarps * 32, smem, s>>>(expr, T, N, ld, Np, r);
-  return cudaGetLastError();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_pad_traits(T, rows_pad, r.tau, r.cfac, r.nan_cnt, s);
 }
 
 cudaError_t launch_permute_rows(const __half *A, __half *out, int rows_pad, int Np, int N,
@@ -201,6 +218,9 @@ rerank_kernel(RankDev base, int T, int N, int Np, const int32_t *__restrict__ dr
 cudaError_t launch_rerank_bucket(const RankDev &base, int T, int N, int Np, const int32_t *drop,
                                  int n_drop, const RankDev &out, cudaStream_t s) {
   rerank_kernel<<<(T + 7) / 8, 256, 0, s>>>(base, T, N, Np, drop, n_drop, out);
-  return cudaGetLastError();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int rows_pad = (T + kTileM - 1) / kTileM * kTileM;
+  return launch_pad_traits(T, rows_pad, out.tau, out.cfac, out.nan_cnt, s);
 }
 }  // namespace krux

@@ -28,6 +28,9 @@ namespace {
 // tcgen05 instruction descriptor, kind::f16: D = F32, A = B = F16, both K-major,
 // N = 128 (bits 17-22 hold N >> 3), M = 128 (bits 24-28 hold M >> 4).
 constexpr uint32_t kIdesc = (1u << 4) | ((uint32_t)(128 >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+// Same with N = 256: one MMA over a pair of chunks whose B rows are interleaved
+// per K atom (256 rows of 32 B), writing two adjacent 128-column accumulators.
+constexpr uint32_t kIdesc256 = (1u << 4) | ((uint32_t)(256 >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
 // Two K-major shared-memory layouts: 128-byte swizzle with 64-element K atoms
 // (K padded to a multiple of 64, zero-filled by TMA), or 32-byte swizzle with
 // 16-element atoms (K padded to a multiple of 16 only).  An atom block holds 128
@@ -561,13 +564,15 @@ __global__ void __launch_bounds__(kScanThreads, 1) krux_scan_kernel(const ScanPa
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
   uint8_t *sbase = smem_raw + (base - raw);
-  const uint32_t tile_bytes = 128u * (uint32_t)p.kpad * 2u;
+  const uint32_t a_tile_bytes = (uint32_t)p.a_tile_bytes;
   const uint32_t sA = base;
-  const uint32_t sB = base + (uint32_t)p.nA * tile_bytes;
-  ChunkMeta *smeta = reinterpret_cast<ChunkMeta *>(sbase + (size_t)(p.nA + p.nc) * tile_bytes);
+  const uint32_t sB = base + (uint32_t)p.nA * a_tile_bytes;
+  ChunkMeta *smeta =
+      reinterpret_cast<ChunkMeta *>(sbase + (size_t)p.nA * a_tile_bytes + (size_t)p.b_region);
   uint8_t *scodes = reinterpret_cast<uint8_t *>(smeta + p.nc);
   const uint32_t codes_stride = (uint32_t)p.kpad * 16u;
-  uint64_t *bars = reinterpret_cast<uint64_t *>(scodes + (size_t)p.nc * codes_stride);
+  uint8_t *stc = scodes + (size_t)p.nc * codes_stride;  // trait-constant ring
+  uint64_t *bars = reinterpret_cast<uint64_t *>(stc + (size_t)kTcDepth * kTcBytes);
   const uint32_t bar0 = smem_u32(bars);
   const int nA = p.nA, nc = p.nc;
   // barrier addresses
@@ -578,7 +583,12 @@ __global__ void __launch_bounds__(kScanThreads, 1) krux_scan_kernel(const ScanPa
   auto t_full = [&](int s) { return bar0 + 8u * (uint32_t)(2 * nA + 2 * nc + s); };
   auto t_empty = [&](int s) { return bar0 + 8u * (uint32_t)(2 * nA + 2 * nc + kTmemSlots + s); };
   const uint32_t drain = bar0 + 8u * (uint32_t)(2 * nA + 2 * nc + 2 * kTmemSlots);
-  uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bars + 2 * nA + 2 * nc + 2 * kTmemSlots + 1);
+  auto tc_full = [&](int e) { return bar0 + 8u * (uint32_t)(2 * nA + 2 * nc + 2 * kTmemSlots + 1 + e); };
+  auto tc_empty = [&](int e) {
+    return bar0 + 8u * (uint32_t)(2 * nA + 2 * nc + 2 * kTmemSlots + 1 + kTcDepth + e);
+  };
+  uint32_t *tmem_holder =
+      reinterpret_cast<uint32_t *>(bars + 2 * nA + 2 * nc + 2 * kTmemSlots + 1 + 2 * kTcDepth);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_holder + 1);
   unsigned int *seg_n = tmem_holder + 2;  // hits staged by this CTA
 
@@ -596,6 +606,10 @@ __global__ void __launch_bounds__(kScanThreads, 1) krux_scan_kernel(const ScanPa
       mbar_init(t_empty(s), kEpiWarps);
     }
     mbar_init(drain, 1);
+    for (int e = 0; e < kTcDepth; ++e) {
+      mbar_init(tc_full(e), 1);
+      mbar_init(tc_empty(e), kEpiWarps);
+    }
     *abort_flag = 0;
     *seg_n = 0u;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -617,22 +631,30 @@ __global__ void __launch_bounds__(kScanThreads, 1) krux_scan_kernel(const ScanPa
     if (lane == 0) {
       uint32_t a_stage = 0, a_phase = 0, b_bits = 0;
       uint32_t a_used = 0, a_last = 0, b_used = 0, b_last = 0;
+      uint32_t tc_e = 0, tc_phase = 0, tc_used = 0, tc_last = 0;
       for (int it = blockIdx.x; it < p.n_items; it += gridDim.x) {
         const WorkItem w = p.items[it];
         const GroupDesc *g = p.groups + w.group;
         prefetch_map(&g->tmA);
         prefetch_map(&g->tmB);
-        const int nc_item = min(nc, g->nchunks - w.btile * nc);
-        const uint32_t tile_tx = (uint32_t)g->n_atoms * atom_bytes(p.layout);
+        const int ncg = g->nc;
+        const int nc_item = min(ncg, g->nchunks - w.btile * ncg);
+        const uint32_t b_stride = (uint32_t)g->b_stride;
+        const uint32_t abytes = atom_bytes(p.layout);
+        const int ak = (int)atom_k(p.layout);
+        const uint32_t b_tx = (uint32_t)g->n_atoms * abytes;
         const uint32_t codes_bytes = g->codes ? (uint32_t)g->Np * 16u : 0u;
         for (int c = 0; c < nc_item; ++c) {
           const uint32_t ph = (b_bits >> c) & 1u;
           if (!wait_bar(b_empty(c), ph ^ 1u, wc, 1)) goto producer_done;
-          const int chunk = w.btile * nc + c;
-          mbar_expect_tx(b_full(c), tile_tx + (uint32_t)sizeof(ChunkMeta) + codes_bytes);
+          const int chunk = w.btile * ncg + c;
+          mbar_expect_tx(b_full(c), b_tx + (uint32_t)sizeof(ChunkMeta) + codes_bytes);
+          // paired groups interleave chunks 2j, 2j+1 per K atom: [atom][chunk of pair][128 rows]
+          const uint32_t bbase = g->pair ? sB + (uint32_t)(c >> 1) * 2u * b_stride + (uint32_t)(c & 1) * abytes
+                                         : sB + (uint32_t)c * b_stride;
+          const uint32_t astep = g->pair ? 2u * abytes : abytes;
           for (int a = 0; a < g->n_atoms; ++a)
-            tma_load_2d(sB + (uint32_t)c * tile_bytes + (uint32_t)a * atom_bytes(p.layout), &g->tmB,
-                        a * (int)atom_k(p.layout), chunk * kChunkRows, b_full(c));
+            tma_load_2d(bbase + (uint32_t)a * astep, &g->tmB, a * ak, chunk * kChunkRows, b_full(c));
           bulk_load(smem_u32(smeta + c), g->meta + chunk, (uint32_t)sizeof(ChunkMeta), b_full(c));
           if (codes_bytes)
             bulk_load(smem_u32(scodes + (size_t)c * codes_stride), g->codes + (size_t)chunk * g->Np * 2,
@@ -641,19 +663,46 @@ __global__ void __launch_bounds__(kScanThreads, 1) krux_scan_kernel(const ScanPa
           b_last = (b_last & ~(1u << c)) | (ph << c);
           b_bits ^= 1u << c;
         }
+        const int atoms_per_block = p.ka / ak;
         for (int step = w.step_begin; step < w.step_end; ++step) {
           const int ag = step / g->n_ttiles, tt = step - ag * g->n_ttiles;
           const int row0 = ag * g->rows_per_agroup + tt * kTileM;
-          if (!wait_bar(a_empty(a_stage), a_phase ^ 1u, wc, 2)) goto producer_done;
-          mbar_expect_tx(a_full(a_stage), tile_tx);
-          for (int a = 0; a < g->n_atoms; ++a)
-            tma_load_2d(sA + (uint32_t)a_stage * tile_bytes + (uint32_t)a * atom_bytes(p.layout),
-                        &g->tmA, a * (int)atom_k(p.layout), row0, a_full(a_stage));
-          a_used |= 1u << a_stage;
-          a_last = (a_last & ~(1u << a_stage)) | (a_phase << a_stage);
-          if (++a_stage == (uint32_t)nA) {
-            a_stage = 0;
-            a_phase ^= 1u;
+          // the rank tile of this step, in K blocks of p.ka samples
+          for (int kb = 0; kb < g->nkb; ++kb) {
+            if (!wait_bar(a_empty(a_stage), a_phase ^ 1u, wc, 2)) goto producer_done;
+            const int a0 = kb * atoms_per_block;
+            const int na = min(atoms_per_block, g->n_atoms - a0);
+            mbar_expect_tx(a_full(a_stage), (uint32_t)na * abytes);
+            for (int a = 0; a < na; ++a)
+              tma_load_2d(sA + (uint32_t)a_stage * a_tile_bytes + (uint32_t)a * abytes, &g->tmA,
+                          (a0 + a) * ak, row0, a_full(a_stage));
+            a_used |= 1u << a_stage;
+            a_last = (a_last & ~(1u << a_stage)) | (a_phase << a_stage);
+            if (++a_stage == (uint32_t)nA) {
+              a_stage = 0;
+              a_phase ^= 1u;
+            }
+          }
+          // this step's per-trait constants into the ring (padded to whole tiles)
+          if (!wait_bar(tc_empty(tc_e), tc_phase ^ 1u, wc, 8)) goto producer_done;
+          {
+            const bool with_key = g->minp_key != nullptr && ag > 0;
+            const uint32_t tx = 512u + 1024u + (g->nan_cnt ? 256u : 0u) + (with_key ? 1024u : 0u);
+            const uint32_t dst = smem_u32(stc + (size_t)tc_e * kTcBytes);
+            const int64_t r0 = (int64_t)tt * kTileM;
+            mbar_expect_tx(tc_full(tc_e), tx);
+            bulk_load(dst, g->tau + r0, 512u, tc_full(tc_e));
+            bulk_load(dst + 512u, g->cfac + r0, 1024u, tc_full(tc_e));
+            if (with_key)
+              bulk_load(dst + 1536u, g->minp_key + (int64_t)(ag - 1) * g->rows_per_agroup + r0, 1024u,
+                        tc_full(tc_e));
+            if (g->nan_cnt) bulk_load(dst + 2560u, g->nan_cnt + r0, 256u, tc_full(tc_e));
+            tc_used |= 1u << tc_e;
+            tc_last = (tc_last & ~(1u << tc_e)) | (tc_phase << tc_e);
+            if (++tc_e == (uint32_t)kTcDepth) {
+              tc_e = 0;
+              tc_phase ^= 1u;
+            }
           }
         }
       }
@@ -663,6 +712,8 @@ __global__ void __launch_bounds__(kScanThreads, 1) krux_scan_kernel(const ScanPa
         if ((a_used >> s) & 1u) wait_drain(a_full(s), (a_last >> s) & 1u, p.status, 10);
       for (int c = 0; c < nc; ++c)
         if ((b_used >> c) & 1u) wait_drain(b_full(c), (b_last >> c) & 1u, p.status, 11);
+      for (int e = 0; e < kTcDepth; ++e)
+        if ((tc_used >> e) & 1u) wait_drain(tc_full(e), (tc_last >> e) & 1u, p.status, 13);
     }
     __syncwarp();
   } else if (warp == kMmaWarp) {
@@ -671,36 +722,85 @@ __global__ void __launch_bounds__(kScanThreads, 1) krux_scan_kernel(const ScanPa
       for (int it = blockIdx.x; it < p.n_items; it += gridDim.x) {
         const WorkItem w = p.items[it];
         const GroupDesc *g = p.groups + w.group;
-        const int nc_item = min(nc, g->nchunks - w.btile * nc);
+        const int ncg = g->nc;
+        const int nc_item = min(ncg, g->nchunks - w.btile * ncg);
+        const uint32_t b_stride = (uint32_t)g->b_stride;
         const int ksteps = g->Np / 16;
+        const int kpb = p.ka / 16;  // K steps per block
         for (int step = w.step_begin; step < w.step_end; ++step) {
-          if (!wait_bar(a_full(a_stage), a_phase, wc, 3)) goto mma_done;
-          tc_fence_after();
-          for (int c = 0; c < nc_item; ++c) {
-            if (step == w.step_begin) {
-              if (!wait_bar(b_full(c), (b_bits >> c) & 1u, wc, 4)) goto mma_done;
-              tc_fence_after();
-            }
-            if (!wait_bar(t_empty(slot), slot_phase ^ 1u, wc, 5)) goto mma_done;
+          if (g->pair && (slot & 1u)) {
+            // paired accumulators start on an even slot: retire this one unused
+            if (!wait_bar(t_empty(slot), slot_phase ^ 1u, wc, 14)) goto mma_done;
             tc_fence_after();
-            const uint32_t d_tmem = tmem_base + slot * 128u;
-            const uint32_t a_tile = sA + a_stage * tile_bytes;
-            const uint32_t b_tile = sB + (uint32_t)c * tile_bytes;
-            for (int k = 0; k < ksteps; ++k) {
-              const uint32_t off = kstep_off(p.layout, k);
-              tc_mma(d_tmem, umma_desc(a_tile + off, p.layout), umma_desc(b_tile + off, p.layout), kIdesc,
-                     k > 0 ? 1u : 0u);
-            }
             tc_commit(t_full(slot));
             if (++slot == (uint32_t)kTmemSlots) {
               slot = 0;
               slot_phase ^= 1u;
             }
           }
-          tc_commit(a_empty(a_stage));
-          if (++a_stage == (uint32_t)nA) {
-            a_stage = 0;
-            a_phase ^= 1u;
+          for (int kb = 0; kb < g->nkb; ++kb) {
+            if (!wait_bar(a_full(a_stage), a_phase, wc, 3)) goto mma_done;
+            tc_fence_after();
+            const int k0 = kb * kpb;
+            const int nk = min(kpb, ksteps - k0);
+            const uint32_t a_tile = sA + a_stage * a_tile_bytes;
+            for (int c = 0; c < nc_item;) {
+              const bool two = g->pair && c + 1 < nc_item;
+              uint32_t sc = slot + (uint32_t)c, ph = slot_phase;
+              if (sc >= (uint32_t)kTmemSlots) {
+                sc -= kTmemSlots;
+                ph ^= 1u;
+              }
+              if (kb == 0) {
+                for (int j = 0; j < (two ? 2 : 1); ++j) {
+                  const uint32_t sj = sc + (uint32_t)j;  // sc is even when two: sj stays in range
+                  if (step == w.step_begin) {
+                    if (!wait_bar(b_full(c + j), (b_bits >> (c + j)) & 1u, wc, 4)) goto mma_done;
+                  }
+                  if (!wait_bar(t_empty(sj), ph ^ 1u, wc, 5)) goto mma_done;
+                }
+                tc_fence_after();
+              }
+              const uint32_t d_tmem = tmem_base + sc * 128u;
+              // descriptors are built once per chunk and K block; a K step only moves
+              // the start address field (bits 0-13, address >> 4), which never carries
+              if (p.layout) {
+                const uint32_t b_tile = g->pair ? sB + (uint32_t)(c >> 1) * 2u * b_stride
+                                                : sB + (uint32_t)c * b_stride;
+                const uint32_t bstep = g->pair ? 8192u : 4096u;
+                const uint32_t idesc = two ? kIdesc256 : kIdesc;
+                uint64_t da = umma_desc(a_tile, 1), db = umma_desc(b_tile + (uint32_t)k0 * bstep, 1);
+                tc_mma(d_tmem, da, db, idesc, kb > 0 ? 1u : 0u);
+                for (int k = 1; k < nk; ++k) {
+                  da += 4096u >> 4;
+                  db += bstep >> 4;
+                  tc_mma(d_tmem, da, db, idesc, 1u);
+                }
+              } else {
+                const uint32_t b_tile = sB + (uint32_t)c * b_stride;
+                const uint64_t da = umma_desc(a_tile, 0), db = umma_desc(b_tile, 0);
+                for (int k = 0; k < nk; ++k) {
+                  const uint64_t oa = (uint64_t)(kstep_off(0, k) >> 4);
+                  const uint64_t ob = (uint64_t)(kstep_off(0, k0 + k) >> 4);
+                  tc_mma(d_tmem, da + oa, db + ob, kIdesc, (kb > 0 || k > 0) ? 1u : 0u);
+                }
+              }
+              if (kb == g->nkb - 1) {
+                tc_commit(t_full(sc));
+                if (two) tc_commit(t_full(sc + 1u));
+              }
+              c += two ? 2 : 1;
+            }
+            tc_commit(a_empty(a_stage));
+            if (++a_stage == (uint32_t)nA) {
+              a_stage = 0;
+              a_phase ^= 1u;
+            }
+          }
+          slot += (uint32_t)nc_item;
+          if (slot >= (uint32_t)kTmemSlots) {
+            slot -= kTmemSlots;
+            slot_phase ^= 1u;
           }
         }
         for (int c = 0; c < nc_item; ++c) {
@@ -717,41 +817,56 @@ __global__ void __launch_bounds__(kScanThreads, 1) krux_scan_kernel(const ScanPa
   } else {
     // epilogue warps
     const int q = warp & 3, h = warp >> 2;  // lane quarter, SNP group of the chunk
-    uint32_t slot = 0, slot_phase = 0, b_bits = 0;
+    uint32_t slot = 0, slot_phase = 0, b_bits = 0, tc_e = 0, tc_phase = 0;
     for (int it = blockIdx.x; it < p.n_items; it += gridDim.x) {
       const WorkItem w = p.items[it];
       const GroupDesc &g = p.groups[w.group];
-      const int nc_item = min(nc, g.nchunks - w.btile * nc);
+      const int nc_item = min(g.nc, g.nchunks - w.btile * g.nc);
+      const int g_ntt = g.n_ttiles, g_T = g.T, g_N = g.N;
+      const bool g_has_nan = g.nan_cnt != nullptr;
       for (int step = w.step_begin; step < w.step_end; ++step) {
-        const int ag = step / g.n_ttiles, tt = step - ag * g.n_ttiles;
+        const int ag = step / g_ntt, tt = step - ag * g_ntt;
+        if (g.pair && (slot & 1u)) {
+          // the MMA warp retired this slot unused (paired accumulators start even)
+          if (!__all_sync(0xffffffffu, wait_bar(t_full(slot), slot_phase, wc, 15))) goto epi_done;
+          __syncwarp();
+          if (lane == 0) mbar_arrive(t_empty(slot));
+          if (++slot == (uint32_t)kTmemSlots) {
+            slot = 0;
+            slot_phase ^= 1u;
+          }
+        }
+        // this step's trait constants, staged by the producer
+        if (!__all_sync(0xffffffffu, wait_bar(tc_full(tc_e), tc_phase, wc, 9))) goto epi_done;
+        const uint8_t *tcp = stc + (size_t)tc_e * kTcBytes;
+        const int row = 32 * q + lane;
         EpiTrait et;
-        et.trait = tt * kTileM + 32 * q + lane;
-        et.valid = et.trait < g.T;
-        const float tau = et.valid ? g.tau[et.trait] : __int_as_float(0x7f800000);
+        et.trait = tt * kTileM + row;
+        et.valid = et.trait < g_T;
+        const float tau = reinterpret_cast<const float *>(tcp)[row];
         et.ntlo = -tau * (1.f - p.margin);
         et.nthi = -tau * (1.f + p.margin);
-        et.cfac = et.valid ? g.cfac[et.trait] : 0.0;
-        et.nan_cnt = 0;
-        et.nan_idx = nullptr;
-        if (g.nan_cnt != nullptr && et.valid) {
-          et.nan_cnt = g.nan_cnt[et.trait];
-          et.nan_idx = g.nan_idx + (int64_t)et.trait * g.N;
-        }
+        et.cfac = reinterpret_cast<const double *>(tcp + 512)[row];
+        et.nan_cnt = g_has_nan ? (int)reinterpret_cast<const uint16_t *>(tcp + 2560)[row] : 0;
+        et.nan_idx = g_has_nan && et.valid ? g.nan_idx + (int64_t)et.trait * g_N : nullptr;
         const bool minp_mode = g.minp_key != nullptr && ag > 0;
+        // min-p state: FP64 work only in permuted groups (FP64 issue is slow here)
         MinpState ms;
-        ms.best = 0.0;
-        ms.start = 0.0;
-        ms.c1 = 0.f;
-        ms.c2 = 0.f;
         double *key_ptr = nullptr;
-        if (minp_mode && et.valid) {
-          ms.c1 = (float)(et.cfac * (double)p.h1);
-          ms.c2 = (float)(et.cfac * (double)p.h2 * 0.5);
-          key_ptr = g.minp_key + (int64_t)(ag - 1) * g.T + et.trait;
-          ms.start = __longlong_as_double((long long)__ldcg(reinterpret_cast<const unsigned long long *>(key_ptr)));
-          ms.best = ms.start;
+        if (minp_mode) {
+          ms.best = 0.0;
+          ms.start = 0.0;
+          ms.c1 = 0.f;
+          ms.c2 = 0.f;
+          if (et.valid) {
+            ms.c1 = (float)(et.cfac * (double)p.h1);
+            ms.c2 = (float)(et.cfac * (double)p.h2 * 0.5);
+            key_ptr = g.minp_key + (int64_t)(ag - 1) * g.rows_per_agroup + et.trait;
+            ms.start = reinterpret_cast<const double *>(tcp + 1536)[row];
+            ms.best = ms.start;
+          }
+          ms.best_lo = (float)ms.best * (1.f - p.margin);
         }
-        ms.best_lo = (float)ms.best * (1.f - p.margin);
         for (int c = 0; c < nc_item; ++c) {
           bool ok = true;
           if (step == w.step_begin) ok = wait_bar(b_full(c), (b_bits >> c) & 1u, wc, 6);
@@ -827,9 +942,15 @@ __global__ void __launch_bounds__(kScanThreads, 1) krux_scan_kernel(const ScanPa
             if (lane == 0) mbar_arrive(b_empty(c));
           }
         }
-        if (key_ptr != nullptr && ms.best > ms.start)
+        if (minp_mode && key_ptr != nullptr && ms.best > ms.start)
           atomicMax(reinterpret_cast<unsigned long long *>(key_ptr),
                     (unsigned long long)__double_as_longlong(ms.best));
+        __syncwarp();
+        if (lane == 0) mbar_arrive(tc_empty(tc_e));
+        if (++tc_e == (uint32_t)kTcDepth) {
+          tc_e = 0;
+          tc_phase ^= 1u;
+        }
       }
       for (int c = 0; c < nc_item; ++c) b_bits ^= 1u << c;
     }
@@ -903,12 +1024,13 @@ __global__ void finalize_kernel(const krux_hit *__restrict__ hits, const HitAux 
   }
 }
 
-// minimum p of each (permutation, trait) from its best -ln p
+// minimum p of each (permutation, trait) from its best -ln p (key rows of ld entries)
 __global__ void minp_from_key_kernel(const double *__restrict__ key, double *__restrict__ minp,
-                                     int64_t n) {
+                                     int P, int T, int ld) {
+  const int64_t n = (int64_t)P * T;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
-    minp[i] = exp(-key[i]);
+    minp[i] = exp(-key[(i / T) * ld + i % T]);
 }
 
 }  // namespace
@@ -923,18 +1045,24 @@ cudaError_t launch_seg_compact(const krux_hit *seg_hits, const HitAux *seg_aux,
   return cudaGetLastError();
 }
 
-cudaError_t launch_minp_from_key(const double *key, double *minp, int64_t n, cudaStream_t s) {
+cudaError_t launch_minp_from_key(const double *key, double *minp, int P, int T, int ld,
+                                 cudaStream_t s) {
+  const int64_t n = (int64_t)P * T;
   if (n <= 0) return cudaSuccess;
   int grid = (int)((n + 255) / 256);
   if (grid > 4096) grid = 4096;
-  minp_from_key_kernel<<<grid, 256, 0, s>>>(key, minp, n);
+  minp_from_key_kernel<<<grid, 256, 0, s>>>(key, minp, P, T, ld);
   return cudaGetLastError();
 }
 
 size_t scan_smem_bytes(int nc, int nA, int kpad) {
-  const size_t tile = (size_t)128 * kpad * 2;
-  return 1024 + (size_t)(nA + nc) * tile + (size_t)nc * sizeof(ChunkMeta) + (size_t)nc * kpad * 16 +
-         8 * (size_t)(2 * nA + 2 * nc + 2 * kTmemSlots + 1) + 16;
+  return scan_smem_bytes2(nc, nA, (size_t)128 * kpad * 2, (size_t)nc * 128 * kpad * 2, kpad);
+}
+
+size_t scan_smem_bytes2(int nc, int nA, size_t a_tile_bytes, size_t b_region, int codes_k) {
+  return 1024 + (size_t)nA * a_tile_bytes + b_region + (size_t)nc * sizeof(ChunkMeta) +
+         (size_t)nc * codes_k * 16 + (size_t)kTcDepth * kTcBytes +
+         8 * (size_t)(2 * nA + 2 * nc + 2 * kTmemSlots + 1 + 2 * kTcDepth) + 16;
 }
 
 cudaError_t launch_scan(const ScanParams &p, int grid, size_t smem, cudaStream_t s) {

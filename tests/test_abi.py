@@ -67,3 +67,22 @@ def test_null_arguments_are_rejected(lib):
     # validation happens before any device work
     assert lib.krux_create(None, 0) == 1
     assert lib.krux_set_profiling(None, 1) == 1
+
+
+def test_every_launch_plan_is_sound(lib):
+    """The shared-memory plan of every sample count (and of the tuning shapes the
+    GPU tests use) passes the alignment / bounds check each launch runs, so no
+    launch can get a misaligned TMA destination or vector load."""
+    import paper_1307_3519_gb300 as k
+    for N in range(1, 513):
+        for nan in (False, True):
+            for layout in (-1, 0):
+                st, plan = k.krux_debug_plan(N, nan, layout)
+                assert st == 0, (N, nan, layout, plan)
+                assert plan["smem"] <= 232448 and plan["b_region"] % 1024 == 0
+                assert plan["nc"] * plan["b_stride"] <= plan["b_region"]
+    for N in (60, 102, 150):
+        for layout, nc, nA, ka in [(0, 3, 3, 0), (1, 1, 2, 0), (1, 4, 2, 0), (1, 2, 4, 64),
+                                   (0, 2, 3, 64), (1, 1, 4, 64), (1, 4, 3, 64)]:
+            st, plan = k.krux_debug_plan(N, False, layout, nc, nA, ka)
+            assert st in (0, 6)  # sound, or refused (never an unchecked plan)

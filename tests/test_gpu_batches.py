@@ -28,7 +28,8 @@ def _dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-@pytest.mark.parametrize("T,S,P,N", [(200, 3000, 4, 102), (131, 700, 3, 60), (64, 1000, 2, 150)])
+@pytest.mark.parametrize("T,S,P,N", [(200, 3000, 4, 102), (131, 700, 3, 60), (64, 1000, 2, 150),
+                                     (40, 300, 2, 300)])
 def test_permutation_minp(kx, oracle_mod, T, S, P, N):
     d = synth.config(4, T=T, S=S, N=N, seed=T + S)
     perms = synth.make_perms(1307, P, N)
@@ -59,7 +60,7 @@ def test_permutation_rejects_bad_rows(kx):
 def test_grouped_cohorts(kx, oracle_mod):
     """Cohorts of uneven sample counts in one persistent launch, each against its
     own genotypes (the multi-cohort workload at reduced T and S)."""
-    Ns = [48, 75, 102, 150, 200]
+    Ns = [48, 75, 102, 150, 200, 300, 500]
     rng = np.random.default_rng(5)
     cohorts, data = [], []
     for n_c in Ns:

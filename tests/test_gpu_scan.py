@@ -69,7 +69,8 @@ def test_workload1_dense_and_hits(kx, oracle_mod):
 @pytest.mark.parametrize("N,T,S,pth", [(5, 3, 1, 0.3), (17, 129, 65, 0.05), (33, 200, 300, 0.02),
                                        (60, 257, 1000, 1e-3), (102, 300, 2500, 1e-3),
                                        (150, 131, 700, 1e-3), (200, 128, 640, 1e-2),
-                                       (256, 100, 333, 1e-2)])
+                                       (256, 100, 333, 1e-2), (300, 129, 300, 1e-2),
+                                       (400, 64, 200, 1e-2), (512, 33, 150, 1e-2)])
 def test_scan_hits_ragged(kx, oracle_mod, N, T, S, pth):
     d = synth.config(2, T=T, S=S, N=N, seed=7 * N + S)
     orc = oracle_mod.scan(d["expr"], d["geno"], pth)
@@ -184,24 +185,27 @@ def test_host_end_to_end(kx, oracle_mod):
     assert got == want
 
 
-@pytest.mark.parametrize("layout,nc,nA", [(0, 0, 0), (1, 0, 0), (1, 2, 4), (0, 3, 3), (1, 1, 2), (1, 4, 2)])
+@pytest.mark.parametrize("layout,nc,nA,ka", [(0, 0, 0, 0), (1, 0, 0, 0), (1, 2, 4, 0), (0, 3, 3, 0),
+                                             (1, 1, 2, 0), (1, 4, 2, 0), (1, 2, 4, 64), (0, 2, 3, 64),
+                                             (1, 1, 4, 64), (1, 4, 3, 64)])
 @pytest.mark.parametrize("N", [60, 102, 150])
-def test_tile_shapes(kx, oracle_mod, layout, nc, nA, N):
-    """Every shared-memory layout and pipeline shape the tuner may pick gives
-    the oracle's hit set and exact rank sums."""
+def test_tile_shapes(kx, oracle_mod, layout, nc, nA, ka, N):
+    """Every shared-memory layout and pipeline shape the tuner may pick (whole-K
+    rank stages or K blocks of 64 samples) gives the oracle's hit set and exact
+    rank sums."""
     import paper_1307_3519_gb300 as k
     d = synth.config(2, T=270, S=1300, N=N, seed=N + 3 * nc + layout)
     pth = 2e-3
     orc = oracle_mod.scan(d["expr"], d["geno"], pth)
     rs = kx.krux_rank(_dev(d["expr"]))
-    kx.set_tuning(layout, nc, nA)
+    kx.set_tuning(layout, nc, nA, ka)
     try:
         res = kx.krux_scan(rs, _dev(d["geno"]), pth, capacity=270 * 1300)
     except k.KruxError as e:
-        kx.set_tuning(-1, 0, 0)
+        kx.set_tuning(-1, 0, 0, 0)
         assert e.status == k.KRUX_EINVAL  # shape does not fit this N
         return
     finally:
-        kx.set_tuning(-1, 0, 0)
+        kx.set_tuning(-1, 0, 0, 0)
     check_hits(res, orc, np.arange(270), np.arange(1300), pth, must_have_hits=False)
     assert res["n_hits"] == int(orc["hit"].sum())
