@@ -126,16 +126,27 @@ krux_status krux_scan_plain(krux_ctx *ctx, const krux_rankset *rs, const int8_t 
                             double *hit_H, double *hit_p, int64_t *n_hits, void *stream);
 
 /* Permutation null (section "P-value calculation and empirical FDR correction":
- * the scan repeated with the columns of the expression ranks permuted).
+ * the scan repeated, with the same P_c, with the columns of the expression ranks
+ * permuted).
  *   perms : device int32 [P][N], each row a permutation of 0..N-1; sample k of
  *           permutation q takes the expression of sample perms[q][k].
  *   minp  : device double [P][T]: per permutation and trait, the minimum p over
  *           the scanned SNPs.
+ *   fdr_hist : optional device uint64 [1 + P][fdr_bins] (NULL = off), zeroed and
+ *           filled by the call: row 0 counts the real data's stored hits, row q the
+ *           pairs of permutation q with p' < P_c, both by bin
+ *           b = floor((-log10 p - (-log10 P_c)) / fdr_bin_width), clamped to
+ *           [0, fdr_bins).  Summing bins b.. gives the count of pairs with
+ *           p <= P_c * 10^(-b * fdr_bin_width), from which the empirical FDR of
+ *           that threshold is the mean permuted count over the real count.
+ *           fdr_bins >= 1 and fdr_bin_width > 0 when fdr_hist is given.  Row 0 is
+ *           complete only when the hits fit the capacity (else KRUX_EOVERFLOW).
  * The unpermuted scan's hits are returned as in krux_scan. */
 krux_status krux_permute(krux_ctx *ctx, const krux_rankset *rs, const int8_t *geno, int64_t S,
                          int64_t ldg, const int32_t *perms, int P, const krux_opts *opts,
                          double *minp, krux_hit *hits, double *hit_H, double *hit_p,
-                         int64_t *n_hits, void *stream);
+                         int64_t *n_hits, uint64_t *fdr_hist, int fdr_bins,
+                         double fdr_bin_width, void *stream);
 
 /* One cohort of a grouped scan: its own rank set (any N <= 512), genotypes and
  * hit outputs; n_hits is written by krux_scan_grouped. */

@@ -155,3 +155,33 @@ def perm_minp(expr, geno, perms, traits=None, snps=None):
     if rc != 0:
         raise ValueError("genotype code outside {-1,0,1,2}")
     return out
+
+
+def fdr_from_pvalues(p_real, p_perm, pthresh, thresholds):
+    """Empirical FDR (section "P-value calculation and empirical FDR correction"):
+    for each threshold P <= P_c, the mean over the randomised data sets of the
+    number of pairs with P' <= P, divided by the number of real pairs with P' <= P.
+    Only pairs with p < P_c take part (the permuted scans use the same P_c).
+    p_real: 1-D p-values of the real data; p_perm: list of 1-D arrays, one per
+    permutation.  Returns (n_real [len(thresholds)], perm_counts [P, len], fdr),
+    fdr NaN where n_real is 0."""
+    thr = np.asarray(thresholds, dtype=np.float64)
+
+    def count(pv):
+        pv = np.asarray(pv, dtype=np.float64).ravel()
+        pv = pv[pv < pthresh]
+        return np.array([int(np.count_nonzero(pv <= P)) for P in thr], dtype=np.int64)
+
+    n_real = count(p_real)
+    perm_counts = np.stack([count(q) for q in p_perm]) if len(p_perm) else np.zeros((0, thr.size), np.int64)
+    mean = perm_counts.mean(axis=0) if len(p_perm) else np.full(thr.size, np.nan)
+    fdr = np.array([mean[i] / n_real[i] if n_real[i] > 0 else np.nan for i in range(thr.size)])
+    return n_real, perm_counts, fdr
+
+
+def fdr(expr, geno, perms, pthresh, thresholds, snps=None):
+    """Empirical FDR of the scan at each threshold: the real scan and one scan
+    per permutation row of ``perms`` (expression columns permuted), all traits."""
+    p_real = scan(expr, geno, pthresh, snps=snps)["p"]
+    p_perm = [scan(expr, geno, pthresh, snps=snps, perm=perms[q])["p"] for q in range(len(perms))]
+    return fdr_from_pvalues(p_real, p_perm, pthresh, thresholds)

@@ -80,7 +80,7 @@ def load_library(path=LIB_PATH):
         "krux_scan": ([P, P, P, I64, I64, ctypes.POINTER(Opts), P, P, P, ctypes.POINTER(I64), P], I),
         "krux_scan_plain": ([P, P, P, I64, I64, ctypes.POINTER(Opts), P, P, P, ctypes.POINTER(I64), P], I),
         "krux_permute": ([P, P, P, I64, I64, P, I, ctypes.POINTER(Opts), P, P, P, P,
-                          ctypes.POINTER(I64), P], I),
+                          ctypes.POINTER(I64), P, I, D, P], I),
         "krux_scan_grouped": ([P, ctypes.POINTER(Cohort), I, ctypes.POINTER(Opts), P], I),
         "krux_make_perms": ([ctypes.c_uint64, I, I, P], I),
         "krux_set_profiling": ([P, I], I),
@@ -277,11 +277,17 @@ class Krux:
         return self._scan(self.lib.krux_scan_plain, rs, geno, pthresh, capacity, snp_begin,
                           snp_end, dense, margin, stream)
 
-    def krux_permute(self, rs, geno, perms, pthresh, capacity, stream=None):
-        """Permutation null: returns dict(minp float64 [P, T], and the unpermuted hits)."""
+    def krux_permute(self, rs, geno, perms, pthresh, capacity, fdr_bins=0, fdr_bin_width=0.1,
+                     stream=None):
+        """Permutation null: returns dict(minp float64 [P, T], the unpermuted hits and,
+        with fdr_bins > 0, fdr_hist int64 [1 + P, fdr_bins] (row 0 the real data's
+        hits, row q the pairs of permutation q with p' < P_c, binned by
+        -log10 p in steps of fdr_bin_width from -log10 P_c))."""
         import torch
         S = geno.shape[0]
         P_ = perms.shape[0]
+        hist = (torch.empty((1 + P_, fdr_bins), dtype=torch.int64, device=self.device)
+                if fdr_bins > 0 else None)
         minp = torch.empty((P_, rs.T), dtype=torch.float64, device=self.device)
         hits = torch.empty((max(capacity, 1), 4), dtype=torch.int32, device=self.device)
         H = torch.empty(max(capacity, 1), dtype=torch.float64, device=self.device)
@@ -290,11 +296,12 @@ class Krux:
         n = ctypes.c_int64()
         st = self.lib.krux_permute(self.handle, rs.handle, _ptr(geno), S, geno.stride(0), _ptr(perms),
                                    P_, ctypes.byref(o), _ptr(minp), _ptr(hits), _ptr(H), _ptr(Pv),
-                                   ctypes.byref(n), _stream(stream))
+                                   ctypes.byref(n), _ptr(hist), fdr_bins, float(fdr_bin_width),
+                                   _stream(stream))
         st = self._check(st, "krux_permute")
         k = min(n.value, capacity)
         return dict(minp=minp, n_hits=n.value, overflow=st == KRUX_EOVERFLOW, hits=hits[:k],
-                    H=H[:k], p=Pv[:k])
+                    H=H[:k], p=Pv[:k], fdr_hist=hist)
 
     def krux_scan_grouped(self, cohorts, pthresh, stream=None):
         """cohorts: list of dict(rs, geno, capacity).  Returns a list of result dicts."""

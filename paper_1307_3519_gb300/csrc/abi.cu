@@ -116,7 +116,7 @@ struct krux_ctx {
   PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   cudaEvent_t ev[kEv] = {};
   DevBuf B, meta, codes, groups, items, status, counters, aux, cfacptr, miss_idx, miss_mask,
-      list, gemm_out, bucket_ranks, permA, minpkey, seg;
+      list, gemm_out, bucket_ranks, permA, minpkey, seg, permNan;
   void *blas = nullptr;
   std::vector<std::pair<size_t, void *>> pool;  // freed rank-set blocks, reused by size
 };
@@ -428,7 +428,8 @@ void krux_destroy(krux_ctx *ctx) {
   cudaSetDevice(ctx->device);
   DevBuf *bufs[] = {&ctx->B, &ctx->meta, &ctx->codes, &ctx->groups, &ctx->items, &ctx->status,
                     &ctx->counters, &ctx->aux, &ctx->cfacptr, &ctx->miss_idx, &ctx->miss_mask,
-                    &ctx->list, &ctx->gemm_out, &ctx->bucket_ranks, &ctx->permA, &ctx->minpkey, &ctx->seg};
+                    &ctx->list, &ctx->gemm_out, &ctx->bucket_ranks, &ctx->permA, &ctx->minpkey, &ctx->seg,
+                    &ctx->permNan};
   for (DevBuf *b : bufs) b->release();
   for (auto &pb : ctx->pool) cudaFree(pb.second);
   for (int i = 0; i < kEv; ++i)
@@ -645,6 +646,7 @@ struct ScanGroupIn {
   const uint32_t *tile_nan = nullptr;
   const uint16_t *nan_cnt = nullptr;  // nullptr when no trait has NaN
   const uint16_t *nan_idx = nullptr;
+  int64_t nan_ag_stride = 0;          // permuted groups: elements between agroups' NaN lists
   const int8_t *geno = nullptr;
   int64_t ldg = 0;
   const int64_t *snp_list = nullptr;  // device rows, or nullptr for [snp_begin, +n_snps)
@@ -670,6 +672,9 @@ struct CallPlan {
   std::vector<int64_t> lists;         // host copy of all SNP lists
   std::vector<BucketJob> bucket_jobs;
   std::vector<krux_rankset> bucket_sets;  // host shells of the re-ranked sets
+  unsigned long long *fdr_hist = nullptr;  // permutation calls: [1 + P][fdr_bins] or null
+  int fdr_bins = 0;
+  double fdr_l0 = 0.0, fdr_w = 1.0;
 };
 
 size_t bucket_bytes(const krux_rankset *rs) {
@@ -886,6 +891,7 @@ krux_status run_fused(krux_ctx *ctx, CallPlan &cp, const krux_opts *o, cudaStrea
     d.cfac = g.cfac;
     d.nan_cnt = g.nan_cnt;
     d.nan_idx = g.nan_idx;
+    d.nan_ag_stride = g.nan_ag_stride;
     d.tile_nan = g.tile_nan;
     d.hits = os.hits;
     d.aux = os.aux;
@@ -939,6 +945,10 @@ krux_status run_fused(krux_ctx *ctx, CallPlan &cp, const krux_opts *o, cudaStrea
   p.status = status;
   p.timeout_cycles = ctx->wait_limit;
   p.signed_coef = signed_coef;
+  p.fdr_hist = cp.fdr_hist;
+  p.fdr_bins = cp.fdr_bins;
+  p.fdr_l0 = cp.fdr_l0;
+  p.fdr_w = cp.fdr_w;
   const int grid = (int)std::min<size_t>(items.size(), (size_t)ctx->sm_count);
   // Single hit list: stage hits per CTA (shared-memory counter, no global atomic
   // per warp) and append the segments after the launch.
@@ -999,7 +1009,7 @@ krux_status run_fused(krux_ctx *ctx, CallPlan &cp, const krux_opts *o, cudaStrea
     const int64_t nst = std::min<int64_t>((int64_t)counts[k], os.capacity);
     if (nst > 0) {
       KRUX_CUDA(ctx, launch_finalize(os.hits, os.aux, nst, ctx->cfacptr.as<const double *>(), os.H,
-                                     os.P, s));
+                                     os.P, s, cp.fdr_hist, cp.fdr_bins, cp.fdr_l0, cp.fdr_w));
       if (ctx->profiling) ctx->prof.launches += 1;
     }
   }
@@ -1202,12 +1212,16 @@ extern "C" krux_status krux_scan_plain(krux_ctx *ctx, const krux_rankset *rs, co
 extern "C" krux_status krux_permute(krux_ctx *ctx, const krux_rankset *rs, const int8_t *geno,
                                     int64_t S, int64_t ldg, const int32_t *perms, int P,
                                     const krux_opts *opts, double *minp, krux_hit *hits,
-                                    double *hit_H, double *hit_p, int64_t *n_hits, void *stream) {
+                                    double *hit_H, double *hit_p, int64_t *n_hits,
+                                    uint64_t *fdr_hist, int fdr_bins, double fdr_bin_width,
+                                    void *stream) {
   krux_status st = check_scan_args(ctx, rs, geno, S, ldg, opts, hits, hit_H, hit_p, n_hits);
   if (st != KRUX_OK) return st;
   *n_hits = 0;
   if (P < 1 || !perms || !minp) return fail(ctx, KRUX_EINVAL, "need P >= 1, perms and minp");
   if (opts->dense_H) return fail(ctx, KRUX_EINVAL, "dense output is not available with permutations");
+  if (fdr_hist && (fdr_bins < 1 || !(fdr_bin_width > 0.0)))
+    return fail(ctx, KRUX_EINVAL, "FDR histogram needs fdr_bins >= 1 and fdr_bin_width > 0");
   cudaStream_t s = (cudaStream_t)stream;
   KRUX_CUDA(ctx, cudaSetDevice(ctx->device));
   const int N = rs->N;
@@ -1236,11 +1250,37 @@ extern "C" krux_status krux_permute(krux_ctx *ctx, const krux_rankset *rs, const
   KRUX_CUDA(ctx, ctx->minpkey.ensure((size_t)P * rs->rows_pad * 8));
   KRUX_CUDA(ctx, cudaMemsetAsync(ctx->minpkey.p, 0, (size_t)P * rs->rows_pad * 8, s));
   KRUX_CUDA(ctx, ctx->aux.ensure((size_t)std::max<int64_t>(opts->hit_capacity, 1) * sizeof(HitAux)));
+  if (fdr_hist)
+    KRUX_CUDA(ctx, cudaMemsetAsync(fdr_hist, 0, (size_t)(1 + P) * fdr_bins * 8, s));
   CallPlan cp;
   cp.slots.push_back(OutSlot{hits, hit_H, hit_p, opts->hit_capacity, ctx->aux.as<HitAux>()});
+  cp.fdr_hist = reinterpret_cast<unsigned long long *>(fdr_hist);
+  cp.fdr_bins = fdr_bins;
+  cp.fdr_l0 = -std::log10(opts->pthresh);
+  cp.fdr_w = fdr_bin_width;
   st = plan_groups(ctx, cp, rs, geno, ldg, b, e, stack, 1 + P, 0, nullptr, nullptr,
                    ctx->minpkey.as<double>(), s);
   if (st != KRUX_OK) return st;
+  if (rs->has_nan) {
+    // NaN samples of permutation q sit at inv_q(original position)
+    const size_t lst = (size_t)rs->T * N;
+    std::vector<int32_t> inv((size_t)P * N);
+    for (int q = 0; q < P; ++q)
+      for (int k = 0; k < N; ++k) inv[(size_t)q * N + hp[(size_t)q * N + k]] = k;
+    const size_t inv_off = (lst * 2 * (size_t)(1 + P) + 255) / 256 * 256;
+    KRUX_CUDA(ctx, ctx->permNan.ensure(inv_off + inv.size() * 4));
+    uint16_t *lists = ctx->permNan.as<uint16_t>();
+    int32_t *dinv = reinterpret_cast<int32_t *>(ctx->permNan.as<char>() + inv_off);
+    KRUX_CUDA(ctx, cudaMemcpyAsync(dinv, inv.data(), inv.size() * 4, cudaMemcpyHostToDevice, s));
+    KRUX_CUDA(ctx, cudaMemcpyAsync(lists, rs->dev.nan_idx, lst * 2, cudaMemcpyDeviceToDevice, s));
+    KRUX_CUDA(ctx, launch_permute_nan_idx(rs->dev.nan_cnt, rs->dev.nan_idx, rs->T, N, dinv, P,
+                                          lists + lst, s));
+    for (auto &g : cp.groups) {
+      g.nan_idx = lists;
+      g.nan_ag_stride = (int64_t)lst;
+    }
+    if (ctx->profiling) ctx->prof.launches += 1;
+  }
   st = materialise(ctx, cp, s);
   if (st != KRUX_OK) return st;
   std::vector<unsigned long long> counts;

@@ -92,7 +92,9 @@ struct alignas(64) GroupDesc {
   int32_t b_stride;         // shared-memory bytes of one resident B chunk
   int32_t nkb;              // rank-tile K blocks per step (1 = the whole K at once)
   int32_t pair;             // 1: chunks 2j, 2j+1 interleaved per K atom, one N = 256 MMA per pair
-  int32_t pad_[3];
+  int32_t pad_;
+  int64_t nan_ag_stride;    // elements between the NaN index lists of consecutive agroups
+                            // (permuted groups: NaN samples sit at permuted positions)
 };
 
 // Work item: B tile `btile` (chunks btile*nc .. +nc) of group `group`, against the
@@ -123,6 +125,11 @@ struct ScanParams {
   krux_hit *seg_hits;       // [grid][seg_cap] staged hit records
   HitAux *seg_aux;          // [grid][seg_cap]
   unsigned int *seg_cnt;    // [grid] records staged by each CTA
+  unsigned long long *fdr_hist;  // permutation batches: [1 + P][fdr_bins] counts of p < P_c by
+                                 // -log10 p bin (row 0 = real data, filled by the finalisation)
+  int32_t fdr_bins;
+  float fdr_pad_;
+  double fdr_l0, fdr_w;     // bin b = floor((-log10 p - fdr_l0) / fdr_w), clamped to [0, bins)
 };
 
 enum : unsigned int {
@@ -133,6 +140,10 @@ enum : unsigned int {
 // ---- launch wrappers (defined in the .cu files) -----------------------------
 cudaError_t launch_rank(const float *expr, int T, int N, int64_t ld, int Np, int rows_pad,
                         const RankDev &r, cudaStream_t s);
+// NaN sample lists of the permuted rank matrices: out[q][t][j] = inv[q][nan_idx[t][j]]
+// for j < nan_cnt[t] (sample k of permutation q takes the value of sample perm[q][k]).
+cudaError_t launch_permute_nan_idx(const uint16_t *nan_cnt, const uint16_t *nan_idx, int T, int N,
+                                   const int32_t *inv, int P, uint16_t *out, cudaStream_t s);
 cudaError_t launch_permute_rows(const __half *A, __half *out, int rows_pad, int Np, int N,
                                 const int32_t *perms, int P, cudaStream_t s);
 cudaError_t launch_scan(const ScanParams &p, int grid, size_t smem, cudaStream_t s);
@@ -148,6 +159,7 @@ cudaError_t launch_pad_traits(int T, int rows_pad, float *tau, double *cfac, uin
                               cudaStream_t s);
 cudaError_t launch_finalize(const krux_hit *hits, const HitAux *aux, int64_t n,
                             const double *const *cfac_by_group, double *H, double *p,
-                            cudaStream_t s);
+                            cudaStream_t s, unsigned long long *fdr_hist = nullptr, int fdr_bins = 0,
+                            double fdr_l0 = 0.0, double fdr_w = 1.0);
 
 }  // namespace krux

@@ -106,6 +106,20 @@ __global__ void permute_rows_kernel(const __half *__restrict__ A, __half *__rest
     out[i] = v;
   }
 }
+__global__ void permute_nan_idx_kernel(const uint16_t *__restrict__ nan_cnt,
+                                       const uint16_t *__restrict__ nan_idx, int T, int N,
+                                       const int32_t *__restrict__ inv, int P,
+                                       uint16_t *__restrict__ out) {
+  const int64_t total = (int64_t)P * T * N;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(i % N);
+    const int64_t qt = i / N;
+    const int t = (int)(qt % T);
+    const int q = (int)(qt / T);
+    if (j < nan_cnt[t]) out[i] = (uint16_t)inv[(int64_t)q * N + nan_idx[(int64_t)t * N + j]];
+  }
+}
 }  // namespace
 
 // Per-trait constants of the padding rows of the last 128-trait tile: never a hit.
@@ -132,6 +146,16 @@ cudaError_t launch_rank(const float *expr, int T, int N, int64_t ld, int Np, int
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return launch_pad_traits(T, rows_pad, r.tau, r.cfac, r.nan_cnt, s);
+}
+
+cudaError_t launch_permute_nan_idx(const uint16_t *nan_cnt, const uint16_t *nan_idx, int T, int N,
+                                   const int32_t *inv, int P, uint16_t *out, cudaStream_t s) {
+  const int64_t total = (int64_t)P * T * N;
+  if (total == 0) return cudaSuccess;
+  int grid = (int)((total + 255) / 256);
+  if (grid > 152 * 16) grid = 152 * 16;
+  permute_nan_idx_kernel<<<grid, 256, 0, s>>>(nan_cnt, nan_idx, T, N, inv, P, out);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_permute_rows(const __half *A, __half *out, int rows_pad, int Np, int N,

@@ -210,6 +210,15 @@ __device__ __forceinline__ double key64_of(double H, int df) {
   return 0.0;
 }
 
+// FDR histogram bin of a pair with -ln p = key: b = floor((-log10 p - l0) / w),
+// clamped to [0, bins).
+__device__ __forceinline__ int fdr_bin(double key, double l0, double w, int bins) {
+  const double x = (key * 0.43429448190325182765 - l0) / w;
+  if (!(x >= 1.0)) return 0;
+  if (x >= (double)(bins - 1)) return bins - 1;
+  return (int)x;
+}
+
 // p-value of the pair in FP64 from the exact centred sums and group sizes.
 __device__ __forceinline__ double kw_p64(double H, int df) {
   if (df == 1) return erfc(sqrt(0.5 * H));
@@ -496,9 +505,10 @@ struct MinpState {
 
 // Hot filter of a permuted chunk half: largest df-2 form and most negative df-1
 // form over kEpiSnps SNPs, turned into an FP32 -ln p bound; true if some SNP may beat
-// the running best.
+// the running best, or (FDR histogram on, tau_lo finite) may have p < P_c.
 __device__ __forceinline__ bool minp_fast(const uint32_t (&d0)[kEpiSnps], const uint32_t (&d1)[kEpiSnps],
-                                          const ChunkMeta &m, int h, const MinpState &st) {
+                                          const ChunkMeta &m, int h, const MinpState &st,
+                                          float tau_lo) {
   const uint64_t *al = reinterpret_cast<const uint64_t *>(m.alpha + kEpiSnps * h);
   const uint64_t *be = reinterpret_cast<const uint64_t *>(m.beta + kEpiSnps * h);
   const uint64_t *ga = reinterpret_cast<const uint64_t *>(m.gamma + kEpiSnps * h);
@@ -523,17 +533,20 @@ __device__ __forceinline__ bool minp_fast(const uint32_t (&d0)[kEpiSnps], const 
       smin = fmin3(smin, __uint_as_float(sa), __uint_as_float(sb));
     }
   }
-  return fmaxf(smax * st.c2, key1f(-smin * st.c1)) > st.best_lo;
+  return fmaxf(smax * st.c2, key1f(-smin * st.c1)) > st.best_lo || fmaxf(smax, -smin) >= tau_lo;
 }
 
-// Rare path of a permuted chunk half: FP64 -ln p of every SNP that may beat
-// the running best; returns the new best.
+// Rare path of a permuted chunk half: FP64 -ln p of every SNP that may beat the
+// running best (returned), and, with the FDR histogram on, the bin count of
+// every pair with p < P_c (row `row` of the histogram).
 __device__ __noinline__ double minp_slow(const uint32_t *dv, const ChunkMeta &m,
                                          const uint64_t *codes, int h, double cfac, int nan_cnt,
                                          const uint16_t *nan_idx, double best, float best_lo,
-                                         float c1, float c2) {
+                                         float c1, float c2, float tau_lo, const ScanParams &p,
+                                         int row) {
   const int jb = kEpiSnps * h;
   const float *al = m.alpha + jb, *be = m.beta + jb, *ga = m.gamma + jb;
+  const double key_c = -log(p.pthresh);  // -ln P_c
   for (int j = 0; j < kEpiSnps; ++j) {
     if (m.snp[jb + j] < 0) continue;
     const float u = __uint_as_float(dv[j]), v = __uint_as_float(dv[kEpiSnps + j]);
@@ -546,13 +559,16 @@ __device__ __noinline__ double minp_slow(const uint32_t *dv, const ChunkMeta &m,
     } else {
       const float sv = kw_s(u, v, al[j], be[j], ga[j]);
       const float kf = sv > 0.f ? sv * c2 : key1f(-sv * c1);
-      if (kf > best_lo)
+      if (kf > best_lo || fabsf(sv) >= tau_lo)
         key = key64_of(kw_H64((int)u, (int)v, m.n[0][jb + j], m.n[1][jb + j], m.n[2][jb + j], cfac),
                        m.df[jb + j]);
     }
+    if (p.fdr_hist != nullptr && key > key_c)
+      atomicAdd(p.fdr_hist + (int64_t)row * p.fdr_bins + fdr_bin(key, p.fdr_l0, p.fdr_w, p.fdr_bins),
+                1ull);
     if (key > best) {
       best = key;
-      best_lo = (float)key * 0.9999f;
+      best_lo = (float)key * (1.f - p.margin);
     }
   }
   return best;
@@ -848,8 +864,12 @@ __global__ void __launch_bounds__(kScanThreads, 1) krux_scan_kernel(const ScanPa
         et.nthi = -tau * (1.f + p.margin);
         et.cfac = reinterpret_cast<const double *>(tcp + 512)[row];
         et.nan_cnt = g_has_nan ? (int)reinterpret_cast<const uint16_t *>(tcp + 2560)[row] : 0;
-        et.nan_idx = g_has_nan && et.valid ? g.nan_idx + (int64_t)et.trait * g_N : nullptr;
+        et.nan_idx = g_has_nan && et.valid
+                         ? g.nan_idx + ag * g.nan_ag_stride + (int64_t)et.trait * g_N
+                         : nullptr;
         const bool minp_mode = g.minp_key != nullptr && ag > 0;
+        // with the FDR histogram on, permuted pairs at or above the band are counted
+        const float fdr_tau_lo = p.fdr_hist != nullptr ? -et.ntlo : __int_as_float(0x7f800000);
         // min-p state: FP64 work only in permuted groups (FP64 issue is slow here)
         MinpState ms;
         double *key_ptr = nullptr;
@@ -891,7 +911,7 @@ __global__ void __launch_bounds__(kScanThreads, 1) krux_scan_kernel(const ScanPa
           const ChunkMeta &mc = smeta[c];
           bool need;
           if (minp_mode)
-            need = et.valid && (et.nan_cnt > 0 || minp_fast(d0, d1, mc, h, ms));
+            need = et.valid && (et.nan_cnt > 0 || minp_fast(d0, d1, mc, h, ms, fdr_tau_lo));
           else
             need = p.dense || et.nan_cnt > 0 || hit_fast(d0, d1, mc, h, et.ntlo, p.signed_coef != 0);
           if (__any_sync(0xffffffffu, need)) {
@@ -906,7 +926,7 @@ __global__ void __launch_bounds__(kScanThreads, 1) krux_scan_kernel(const ScanPa
               if (minp_mode) {
                 if (need) {
                   ms.best = minp_slow(dv, mc, codes, h, et.cfac, et.nan_cnt, et.nan_idx, ms.best,
-                                      ms.best_lo, ms.c1, ms.c2);
+                                      ms.best_lo, ms.c1, ms.c2, fdr_tau_lo, p, ag);
                   ms.best_lo = (float)ms.best * (1.f - p.margin);
                 }
               } else {
@@ -1007,7 +1027,9 @@ __constant__ double c_rcp[kMaxN + 1];
 // FP64 statistic and p-value of each stored hit, from its exact centred sums.
 __global__ void finalize_kernel(const krux_hit *__restrict__ hits, const HitAux *__restrict__ aux,
                                 int64_t n, const double *const *__restrict__ cfac_by_group,
-                                double *__restrict__ H, double *__restrict__ P) {
+                                double *__restrict__ H, double *__restrict__ P,
+                                unsigned long long *fdr_hist, int fdr_bins, double fdr_l0,
+                                double fdr_w) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const krux_hit r = hits[i];
@@ -1021,6 +1043,8 @@ __global__ void finalize_kernel(const krux_hit *__restrict__ hits, const HitAux 
     const double h = cf * Q;
     H[i] = h;
     P[i] = kw_p64(h, df);
+    if (fdr_hist != nullptr)  // row 0: the real data's hits by -log10 p bin
+      atomicAdd(fdr_hist + fdr_bin(key64_of(h, df), fdr_l0, fdr_w, fdr_bins), 1ull);
   }
 }
 
@@ -1075,7 +1099,8 @@ cudaError_t launch_scan(const ScanParams &p, int grid, size_t smem, cudaStream_t
 
 cudaError_t launch_finalize(const krux_hit *hits, const HitAux *aux, int64_t n,
                             const double *const *cfac_by_group, double *H, double *p,
-                            cudaStream_t s) {
+                            cudaStream_t s, unsigned long long *fdr_hist, int fdr_bins,
+                            double fdr_l0, double fdr_w) {
   if (n <= 0) return cudaSuccess;
   static int table_device = -1;  // the table is uploaded once per device
   int dev = 0;
@@ -1090,7 +1115,8 @@ cudaError_t launch_finalize(const krux_hit *hits, const HitAux *aux, int64_t n,
   }
   int grid = (int)((n + 255) / 256);
   if (grid > 152 * 8) grid = 152 * 8;
-  finalize_kernel<<<grid, 256, 0, s>>>(hits, aux, n, cfac_by_group, H, p);
+  finalize_kernel<<<grid, 256, 0, s>>>(hits, aux, n, cfac_by_group, H, p, fdr_hist, fdr_bins, fdr_l0,
+                                       fdr_w);
   return cudaGetLastError();
 }
 

@@ -46,6 +46,25 @@ def test_permutation_minp(kx, oracle_mod, T, S, P, N):
     assert res["n_hits"] == int(orc["hit"].sum())
 
 
+def test_permutation_minp_with_nan_expression(kx, oracle_mod):
+    """NaN expression values move with the permuted columns: each permutation's
+    group sizes exclude the samples whose permuted value is NaN."""
+    T, S, P, N = 90, 800, 3, 80
+    d = synth.config(3, T=T, S=S, N=N, seed=91)
+    geno = np.where(d["geno"] < 0, 0, d["geno"]).astype(np.int8)
+    assert np.isnan(d["expr"]).any()
+    perms = synth.make_perms(17, P, N)
+    pth = 1e-3
+    rs = kx.krux_rank(_dev(d["expr"]))
+    res = kx.krux_permute(rs, _dev(geno), _dev(perms), pth, capacity=T * S)
+    want = oracle_mod.perm_minp(d["expr"], geno, perms)
+    got = res["minp"].cpu().numpy()
+    assert np.all(np.abs(got - want) <= 1e-6 * want), \
+        f"max rel err {np.max(np.abs(got - want) / want)}"
+    orc = oracle_mod.scan(d["expr"], geno, pth)
+    check_hits(res, orc, np.arange(T), np.arange(S), pth, must_have_hits=False)
+
+
 def test_permutation_rejects_bad_rows(kx):
     import paper_1307_3519_gb300 as k
     d = synth.config(4, T=10, S=50, seed=1)
@@ -94,3 +113,34 @@ def test_bounded_wait_reports_timeout_and_context_survives(kx, oracle_mod):
     res = kx.krux_scan(rs, g, 1e-3, capacity=300 * 4000)
     orc = oracle_mod.scan(d["expr"], d["geno"], 1e-3)
     check_hits(res, orc, np.arange(300), np.arange(4000), 1e-3)
+
+
+@pytest.mark.parametrize("T,S,P,N,nan", [(150, 2500, 3, 102, False), (70, 900, 2, 75, True)])
+def test_permutation_fdr_histogram(kx, oracle_mod, T, S, P, N, nan):
+    """Per-permutation counts of p' < P_c by -log10 p bin, and the real data's
+    row, against the oracle's p of every pair; the FDR curve from it equals the
+    definition evaluated by the oracle."""
+    from paper_1307_3519_gb300.fdr import fdr_curve
+    d = synth.config(3 if nan else 4, T=T, S=S, N=N, seed=T * 7 + S)
+    expr = d["expr"]
+    geno = np.where(d["geno"] < 0, 0, d["geno"]).astype(np.int8)  # complete genotypes
+    perms = synth.make_perms(11, P, N)
+    pth, w, bins = 1e-2, 0.2, 16
+    rs = kx.krux_rank(_dev(expr))
+    res = kx.krux_permute(rs, _dev(geno), _dev(perms), pth, capacity=T * S, fdr_bins=bins,
+                          fdr_bin_width=w)
+    got = res["fdr_hist"].cpu().numpy()
+    rows = [oracle_mod.scan(expr, geno, pth)["p"]]
+    rows += [oracle_mod.scan(expr, geno, pth, perm=perms[q])["p"] for q in range(P)]
+    l0 = -np.log10(pth)
+    for q, p in enumerate(rows):
+        p = p[p < pth]
+        x = (-np.log10(p) - l0) / w
+        want = np.bincount(np.clip(np.floor(x), 0, bins - 1).astype(np.int64), minlength=bins)
+        near = np.abs(x - np.round(x)) < 1e-9
+        assert np.sum(np.abs(got[q] - want)) <= 2 * int(near.sum()), (q, got[q], want)
+        assert got[q].sum() == p.size
+    c = fdr_curve(got, pth, w)
+    n_real, pc, fdr = oracle_mod.fdr_from_pvalues(rows[0], rows[1:], pth, c["threshold"])
+    assert np.array_equal(c["n_real"], n_real) and np.array_equal(c["mean_perm"] * P, pc.sum(axis=0))
+    assert np.allclose(c["fdr"], fdr, rtol=1e-12, atol=0, equal_nan=True)

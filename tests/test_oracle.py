@@ -12,6 +12,8 @@ import pytest
 import scipy.special as sps
 import scipy.stats as st
 
+import synth
+
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "kw_worked_examples.txt")
 
 
@@ -249,3 +251,45 @@ def test_permuted_scan_equals_scan_of_permuted_expression(oracle_mod):
 def test_bad_genotype_code_raises(oracle_mod):
     with pytest.raises(ValueError):
         oracle_mod.kw_pair(np.arange(4, dtype=np.float32), np.array([0, 1, 3, 2], np.int8))
+
+
+def _read_fdr_golden():
+    rows = {}
+    for line in open(os.path.join(os.path.dirname(GOLDEN), "fdr_worked_example.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        k, v = line.rstrip("\n").split("\t")
+        rows.setdefault(k, []).append(np.array([float(x) for x in v.split(",")]))
+    return rows
+
+
+def test_fdr_worked_example(oracle_mod):
+    g = _read_fdr_golden()
+    n_real, pc, fdr = oracle_mod.fdr_from_pvalues(g["real"][0], g["perm"], g["pthresh"][0][0],
+                                                  g["thresholds"][0])
+    assert np.array_equal(n_real, g["n_real"][0])
+    assert np.array_equal(pc, np.stack(g["perm_counts"]))
+    assert np.allclose(fdr, g["fdr"][0], equal_nan=True, rtol=0, atol=1e-15)
+
+
+def test_fdr_of_identity_permutations_is_one(oracle_mod):
+    """Randomised data identical to the real data: FDR = 1 wherever it is defined."""
+    d = synth.config(4, T=12, S=150, N=30, seed=77)
+    ident = np.tile(np.arange(d["N"], dtype=np.int32), (2, 1))
+    thr = 0.05 * 10.0 ** -np.arange(0, 3, 0.5)
+    n_real, pc, fdr = oracle_mod.fdr(d["expr"], d["geno"], ident, 0.05, thr)
+    assert n_real[0] > 0
+    assert np.array_equal(pc[0], n_real) and np.array_equal(pc[1], n_real)
+    assert np.all(fdr[n_real > 0] == 1.0)
+
+
+def test_fdr_counts_match_permuted_scans(oracle_mod):
+    """The permuted counts are those of a scan of the column-permuted expression."""
+    d = synth.config(4, T=10, S=120, N=40, seed=78)
+    perms = synth.make_perms(5, 2, d["N"])
+    thr = np.array([0.05, 0.01, 0.001])
+    _, pc, _ = oracle_mod.fdr(d["expr"], d["geno"], perms, 0.05, thr)
+    for q in range(2):
+        p = oracle_mod.scan(np.ascontiguousarray(d["expr"][:, perms[q]]), d["geno"], 0.05)["p"]
+        p = p[p < 0.05]
+        assert list(pc[q]) == [int((p <= t).sum()) for t in thr]
