@@ -11,6 +11,7 @@ host API with pinned host buffers, and the FP64 CPU oracle is timed on a
 bounded sample of the same workload on the host cores.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fused|reference]
+  python bench.py --scan-only [--traits T] [--snps S] [--data hwe|paper] [--reps R]
 
 With --impl reference only the oracle arm runs (the CPU reference program),
 on a bounded sample per step, and prints the same JSON line with
@@ -39,6 +40,19 @@ WORKLOAD = ("paper-scale fused scan: N=102 samples, T=20000 traits, S=500000 SNP
             "1-SD shifts on ~1% of pairs; hits at p<1e-5")
 
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one krux_scan_kernel
+# launch on the paper-scale workload, from one ncu capture, with the git blob hash of
+# the kernel source it was taken on: reported only while that source is unchanged.
+SCAN_TRAFFIC = None  # {"blob": "<sha1>", "bytes": <per launch>}
+
+
+def kernel_blob():
+    import hashlib
+    with open(os.path.join(ROOT, "paper_1307_3519_gb300", "csrc", "scan_sm103.cu"), "rb") as f:
+        data = f.read()
+    return hashlib.sha1(b"blob %d\0" % len(data) + data).hexdigest()
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -63,7 +77,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
         except OSError:
@@ -128,22 +142,24 @@ def barrier(world):
 
 def oracle_sample_rate(d, target_s=12.0, seed=0):
     """Oracle throughput (pairs/s) on a bounded sample of the workload sized for
-    about target_s seconds of CPU work."""
+    about target_s seconds of CPU work: whole trait rows (all SNPs), a multiple of
+    the oracle's thread count so that no thread idles."""
     import oracle
     rng = np.random.default_rng(seed)
     T, S = d["expr"].shape[0], d["geno"].shape[0]
-    probe_t = rng.choice(T, 2, replace=False)
-    probe_s = np.arange(0, S, max(1, S // 50000))
+    cores = oracle.num_threads()
+    probe_t = rng.choice(T, min(T, cores), replace=False)
+    probe_s = np.arange(0, S, max(1, S // 20000))
     t0 = time.perf_counter()
     oracle.scan(d["expr"], d["geno"], d["pthresh"], traits=probe_t, snps=probe_s)
     rate0 = probe_t.size * probe_s.size / (time.perf_counter() - t0)
-    n_pairs = rate0 * target_s
-    nt = int(max(1, min(T, n_pairs // S)))
+    nt = int(round(rate0 * target_s / S / cores)) * cores
+    nt = int(max(cores, min(T, nt)))
     traits = rng.choice(T, nt, replace=False)
     t0 = time.perf_counter()
     oracle.scan(d["expr"], d["geno"], d["pthresh"], traits=traits)
     dt = time.perf_counter() - t0
-    return nt * S / dt, dict(traits=nt, snps=S, seconds=dt, cores=oracle.num_threads())
+    return nt * S / dt, dict(traits=nt, snps=S, seconds=dt, cores=cores)
 
 
 def run_reference(args):
@@ -263,7 +279,9 @@ def run_fused(args):
     achieved = flops / (ms_scan / 1e3) / 1e12
     peak = float(pk["bf16_tflops"])  # FP16 dense rate equals the BF16 rate (nominal ratio 1)
     roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": None,
+            "frac": achieved / peak,
+            "traffic": (SCAN_TRAFFIC["bytes"] if SCAN_TRAFFIC and SCAN_TRAFFIC["blob"] == kernel_blob()
+                        else None),
             "kernel": "krux_scan_kernel", "peak_kind": f"{pk_kind} bf16 burst (fp16 = bf16 x 1.0)",
             "ms_per_launch": ms_scan, "flops_per_launch": flops}
 
@@ -315,14 +333,56 @@ def run_fused(args):
         dist.destroy_process_group()
 
 
+def run_scan_only(args):
+    """Profiling driver: the fused scan kernel alone, `reps` calls on one seeded
+    input (T traits x S SNPs x 102 samples), one text line per call.  data=hwe:
+    HWE genotypes (MAF 0.05-0.5) and log-normal expression, almost no hits;
+    data=paper: the paper-scale workload's generator at these sizes."""
+    import torch
+    from paper_1307_3519_gb300 import build as kbuild
+    kbuild.build()
+    import paper_1307_3519_gb300 as k
+    import synth
+    T, S = args.traits, args.snps
+    if args.data == "paper":
+        d = synth.config(2, T=T, S=S)
+        geno, expr, pth = d["geno"], d["expr"], d["pthresh"]
+    else:
+        rng = np.random.default_rng(1)
+        geno, _ = synth.hwe_genotypes(rng, S, 102, 0.05, 0.5)
+        expr = synth.expression_lognormal(rng, T, 102)
+        pth = 1e-5
+    kx = k.Krux(0)
+    kx.set_profiling(True)
+    rs = kx.krux_rank(torch.from_numpy(expr).cuda())
+    g = torch.from_numpy(geno).cuda()
+    for i in range(args.reps):
+        r = kx.krux_scan(rs, g, pth, capacity=min(50_000_000, T * S))
+        pr = kx.profile()
+        fl = 4.0 * 102 * T * S
+        print(f"scan-only data={args.data} T={T} S={S} call={i} hits={r['n_hits']} "
+              f"scan={pr['ms_scan']:.3f} ms ({fl / pr['ms_scan'] / 1e9:.1f} TFLOP/s algorithmic) "
+              f"pack={pr['ms_pack']:.3f} ms finalize={pr['ms_finalize']:.3f} ms grid={pr['scan_grid']}",
+              flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="fused", choices=["fused", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--scan-only", action="store_true",
+                    help="profiling driver: only the fused scan, --reps calls, text output")
+    ap.add_argument("--traits", type=int, default=20000)
+    ap.add_argument("--snps", type=int, default=100000)
+    ap.add_argument("--data", default="hwe", choices=["hwe", "paper"])
+    ap.add_argument("--reps", type=int, default=3)
     args = ap.parse_args()
+    if args.scan_only:
+        run_scan_only(args)
+        return
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

@@ -71,7 +71,7 @@ typedef struct {
 typedef struct {
   float ms_rank;        /* rank transform (krux_rank) */
   float ms_pack;        /* genotype packing */
-  float ms_scan;        /* fused tcgen05 scan kernel, or plain GEMM + epilogue */
+  float ms_scan;        /* fused tcgen05 scan kernel alone, or plain GEMM + epilogue */
   float ms_finalize;    /* FP64 H / p of the hit list */
   float ms_gemm;        /* plain form: library GEMM part of ms_scan */
   int32_t launches;     /* kernels the last call launched */

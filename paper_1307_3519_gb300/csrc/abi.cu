@@ -969,7 +969,9 @@ krux_status run_fused(krux_ctx *ctx, CallPlan &cp, const krux_opts *o, cudaStrea
     const std::string why = validate_plan(p, descs, smem);
     if (!why.empty()) return fail(ctx, KRUX_EUNSUPPORTED, "%s", why.c_str());
   }
+  ev_record(ctx, 7, s);  // the scan kernel alone: events 7 .. 4
   if (grid > 0) KRUX_CUDA(ctx, launch_scan(p, grid, smem, s));
+  ev_record(ctx, 4, s);
   unsigned long long *totals = ctx->counters.as<unsigned long long>() + nslots;
   if (staged) {
     KRUX_CUDA(ctx, launch_seg_compact(p.seg_hits, p.seg_aux, p.seg_cnt, grid, p.seg_cap,
@@ -979,7 +981,6 @@ krux_status run_fused(krux_ctx *ctx, CallPlan &cp, const krux_opts *o, cudaStrea
     KRUX_CUDA(ctx, cudaMemcpyAsync(totals, ctx->counters.p, (size_t)nslots * 8,
                                    cudaMemcpyDeviceToDevice, s));
   }
-  ev_record(ctx, 4, s);
 
   unsigned int hst[2] = {0, 0};
   KRUX_CUDA(ctx, cudaMemcpyAsync(counts.data(), totals, (size_t)nslots * 8,
@@ -988,7 +989,7 @@ krux_status run_fused(krux_ctx *ctx, CallPlan &cp, const krux_opts *o, cudaStrea
   KRUX_CUDA(ctx, cudaStreamSynchronize(s));
   if (ctx->profiling) {
     ctx->prof.ms_pack = ev_ms(ctx, 2, 3);
-    ctx->prof.ms_scan = ev_ms(ctx, 3, 4);
+    ctx->prof.ms_scan = ev_ms(ctx, 7, 4);
     ctx->prof.scan_grid = grid;
     ctx->prof.launches += (grid > 0 ? 1 : 0) + (staged ? 1 : 0);
     for (auto &g : cp.groups) ctx->prof.launches += g.nan_cnt ? 2 : 1;

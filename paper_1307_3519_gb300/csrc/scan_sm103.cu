@@ -440,22 +440,55 @@ __device__ __noinline__ bool decide64(float u, float v, int n0, int n1, int n2, 
   return kw_p64(kw_H64((int)u, (int)v, n0, n1, n2, cfac), df) < pthresh;
 }
 
-// Warp-collective append of this lane's hits (bit j of `hitmask` = SNP jb + j).
-// Records first fill the CTA's staging segment through a shared-memory counter;
-// whatever does not fit goes straight to the caller's list through the global
-// counter.  A compaction pass appends the segments after the launch.
-__device__ __forceinline__ void emit_hits(uint32_t hitmask, const uint32_t (&d0)[kEpiSnps],
-                                          const uint32_t (&d1)[kEpiSnps], const ChunkMeta &m,
-                                          int jb, int trait, const GroupDesc &g,
-                                          const ScanParams &p, unsigned int *seg_n, int lane) {
-  const int cnt = __popc(hitmask);
-  int incl = cnt;
+// Rare path of a hit-mode chunk half without dense output or NaN traits, called
+// by the whole warp.  Each lane classifies its candidates (two SNPs per packed
+// instruction: at or above the upper band edge -> hit, inside the band -> FP64),
+// then the warp appends the hits column by column, so that the lanes holding a
+// hit of SNP j write consecutive records.  Records first fill the CTA's staging
+// segment through one shared-memory atomic per warp; whatever does not fit goes
+// straight to the caller's list through the global counter.  A compaction pass
+// appends the segments after the launch.
+__device__ __noinline__ void hit_event(const uint32_t *dv, bool mine, const ChunkMeta &m, int h,
+                                       int trait, float ntlo, float nthi, double cfac,
+                                       const GroupDesc &g, const ScanParams &p,
+                                       unsigned int *seg_n, int lane) {
+  const int jb = kEpiSnps * h;
+  uint32_t hm = 0;
+  if (mine) {
+    const uint64_t *al = reinterpret_cast<const uint64_t *>(m.alpha + jb);
+    const uint64_t *be = reinterpret_cast<const uint64_t *>(m.beta + jb);
+    const uint64_t *ga = reinterpret_cast<const uint64_t *>(m.gamma + jb);
+    const uint64_t lo2c = pk2(__float_as_uint(ntlo), __float_as_uint(ntlo));
+    const uint64_t hi2c = pk2(__float_as_uint(nthi), __float_as_uint(nthi));
+    uint32_t below = 0, not_sure = 0;  // sign bits of s - tau(1 -/+ margin)
 #pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int y = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += y;
+    for (int j = 0; j < kEpiSnps; j += 2) {
+      const uint64_t u2 = pk2(dv[j], dv[j + 1]);
+      const uint64_t v2 = pk2(dv[kEpiSnps + j], dv[kEpiSnps + j + 1]);
+      const uint64_t w2 = ffma2(be[j / 2], v2, u2);
+      const uint64_t e2 = fmul2(ga[j / 2], v2);
+      uint64_t s2 = ffma2(fmul2(al[j / 2], w2), w2, fmul2(e2, v2));
+      if (p.signed_coef) s2 &= 0x7fffffff7fffffffull;
+      uint32_t la, lb, ha, hb;
+      upk2(fadd2(s2, lo2c), la, lb);
+      upk2(fadd2(s2, hi2c), ha, hb);
+      below |= ((la >> 31) | ((lb >> 31) << 1)) << j;
+      not_sure |= ((ha >> 31) | ((hb >> 31) << 1)) << j;
+    }
+    uint32_t cand = ~below & ((1u << kEpiSnps) - 1u);
+    while (cand) {
+      const int j = __ffs(cand) - 1;
+      cand &= cand - 1u;
+      if (m.snp[jb + j] < 0) continue;
+      bool hit = ((not_sure >> j) & 1u) == 0u;
+      if (!hit)
+        hit = decide64(__uint_as_float(dv[j]), __uint_as_float(dv[kEpiSnps + j]), m.n[0][jb + j],
+                       m.n[1][jb + j], m.n[2][jb + j], m.df[jb + j], cfac, p.pthresh);
+      if (hit) hm |= 1u << j;
+    }
   }
-  const unsigned int total = (unsigned int)__shfl_sync(0xffffffffu, incl, 31);
+  const unsigned int total = __reduce_add_sync(0xffffffffu, (unsigned int)__popc(hm));
+  if (total == 0u) return;
   const unsigned int cap = (unsigned int)p.seg_cap;
   unsigned int sbase = 0;
   if (lane == 0 && cap > 0) sbase = atomicAdd(seg_n, total);
@@ -465,33 +498,40 @@ __device__ __forceinline__ void emit_hits(uint32_t hitmask, const uint32_t (&d0)
   unsigned long long gbase = 0;
   if (lane == 0 && n_over > 0) gbase = atomicAdd(g.counter, (unsigned long long)n_over);
   gbase = __shfl_sync(0xffffffffu, gbase, 0);
-  unsigned int sidx = sbase + (unsigned int)(incl - cnt);
   const size_t seg0 = (size_t)blockIdx.x * cap;
-#pragma unroll
-  for (int j = 0; j < kEpiSnps; ++j) {
-    if ((hitmask >> j) & 1u) {
+  const uint32_t below_me = (1u << lane) - 1u;
+  const uint16_t gid = (uint16_t)g.group_id;
+  unsigned int run = sbase;  // index of the next record (same in every lane)
+  uint32_t cols = __reduce_or_sync(0xffffffffu, hm);
+  while (cols) {
+    const int j = __ffs(cols) - 1;
+    cols &= cols - 1u;
+    const bool mine_j = (hm >> j) & 1u;
+    const uint32_t bal = __ballot_sync(0xffffffffu, mine_j);
+    if (mine_j) {
+      const unsigned int idx = run + (unsigned int)__popc(bal & below_me);
       krux_hit r;
       r.trait = (uint32_t)trait;
       r.snp = (uint32_t)m.snp[jb + j];
-      r.d0 = (int32_t)__uint_as_float(d0[j]);
-      r.d1 = (int32_t)__uint_as_float(d1[j]);
-      HitAux a;
-      a.n0 = m.n[0][jb + j];
-      a.n1 = m.n[1][jb + j];
-      a.n2 = m.n[2][jb + j];
-      a.group = (uint16_t)g.group_id;
-      if (sidx < cap) {
-        p.seg_hits[seg0 + sidx] = r;
-        p.seg_aux[seg0 + sidx] = a;
+      r.d0 = (int32_t)__uint_as_float(dv[j]);
+      r.d1 = (int32_t)__uint_as_float(dv[kEpiSnps + j]);
+      HitAux x;
+      x.n0 = m.n[0][jb + j];
+      x.n1 = m.n[1][jb + j];
+      x.n2 = m.n[2][jb + j];
+      x.group = gid;
+      if (idx < cap) {
+        p.seg_hits[seg0 + idx] = r;
+        p.seg_aux[seg0 + idx] = x;
       } else {
-        const unsigned long long gi = gbase + (sidx - over_from);
+        const unsigned long long gi = gbase + (idx - over_from);
         if (gi < (unsigned long long)g.capacity) {
           g.hits[gi] = r;
-          g.aux[gi] = a;
+          g.aux[gi] = x;
         }
       }
-      ++sidx;
     }
+    run += (unsigned int)__popc(bal);
   }
 }
 
@@ -915,46 +955,25 @@ __global__ void __launch_bounds__(kScanThreads, 1) krux_scan_kernel(const ScanPa
           else
             need = p.dense || et.nan_cnt > 0 || hit_fast(d0, d1, mc, h, et.ntlo, p.signed_coef != 0);
           if (__any_sync(0xffffffffu, need)) {
-            if (minp_mode || __any_sync(0xffffffffu, p.dense || et.nan_cnt > 0)) {
-              // rare paths work on a local copy of the accumulators
-              uint32_t dv[2 * kEpiSnps];
+            // rare paths work on a local copy of the accumulators
+            uint32_t dv[2 * kEpiSnps];
 #pragma unroll
-              for (int j = 0; j < kEpiSnps; ++j) {
-                dv[j] = d0[j];
-                dv[kEpiSnps + j] = d1[j];
+            for (int j = 0; j < kEpiSnps; ++j) {
+              dv[j] = d0[j];
+              dv[kEpiSnps + j] = d1[j];
+            }
+            if (minp_mode) {
+              if (need) {
+                ms.best = minp_slow(dv, mc, codes, h, et.cfac, et.nan_cnt, et.nan_idx, ms.best,
+                                    ms.best_lo, ms.c1, ms.c2, fdr_tau_lo, p, ag);
+                ms.best_lo = (float)ms.best * (1.f - p.margin);
               }
-              if (minp_mode) {
-                if (need) {
-                  ms.best = minp_slow(dv, mc, codes, h, et.cfac, et.nan_cnt, et.nan_idx, ms.best,
-                                      ms.best_lo, ms.c1, ms.c2, fdr_tau_lo, p, ag);
-                  ms.best_lo = (float)ms.best * (1.f - p.margin);
-                }
-              } else {
-                hit_slow(dv, need, mc, codes, h, et.trait, et.valid, et.ntlo, et.nthi, et.cfac,
-                         et.nan_cnt, et.nan_idx, g, p, lane);
-              }
+            } else if (__any_sync(0xffffffffu, p.dense || et.nan_cnt > 0)) {
+              hit_slow(dv, need, mc, codes, h, et.trait, et.valid, et.ntlo, et.nthi, et.cfac,
+                       et.nan_cnt, et.nan_idx, g, p, lane);
             } else {
-              // classify the candidates in registers: above the band -> hit, inside -> FP64
-              uint32_t hm = 0;
-              const int jb = kEpiSnps * h;
-              if (need && et.valid) {
-                const float *al = mc.alpha + jb, *be = mc.beta + jb, *ga = mc.gamma + jb;
-#pragma unroll
-                for (int j = 0; j < kEpiSnps; ++j) {
-                  const float u = __uint_as_float(d0[j]), v = __uint_as_float(d1[j]);
-                  float sv = kw_s(u, v, al[j], be[j], ga[j]);
-                  if (p.signed_coef) sv = fabsf(sv);
-                  if (sv + et.ntlo >= 0.f && mc.snp[jb + j] >= 0) {
-                    bool hit = sv + et.nthi > 0.f;
-                    if (!hit)
-                      hit = decide64(u, v, mc.n[0][jb + j], mc.n[1][jb + j], mc.n[2][jb + j],
-                                     mc.df[jb + j], et.cfac, p.pthresh);
-                    if (hit) hm |= 1u << j;
-                  }
-                }
-              }
-              if (__any_sync(0xffffffffu, hm != 0u))
-                emit_hits(hm, d0, d1, mc, jb, et.trait, g, p, seg_n, lane);
+              hit_event(dv, need && et.valid, mc, h, et.trait, et.ntlo, et.nthi, et.cfac, g, p,
+                        seg_n, lane);
             }
           }
           if (step == w.step_end - 1) {
