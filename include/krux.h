@@ -106,7 +106,8 @@ krux_status krux_rankset_export(krux_ctx *ctx, const krux_rankset *rs, int16_t *
  *   geno : device int8 [S][ldg] row-major, codes 0/1/2, -1 = missing; any other
  *          code -> KRUX_EINVAL.  Same sample order and N as the rank set.
  *   hits, hit_H, hit_p : device outputs of opts->hit_capacity entries, in
- *          unspecified order.  SNP indices are rows of geno (slice offsets included).
+ *          unspecified order; hits must be 16-byte aligned (else KRUX_EINVAL).
+ *          SNP indices are rows of geno (slice offsets included).
  *   n_hits : host; receives the exact number of hits, also when it exceeds the
  *          capacity (then the first hit_capacity found are stored and the call
  *          returns KRUX_EOVERFLOW).

@@ -950,19 +950,20 @@ krux_status run_fused(krux_ctx *ctx, CallPlan &cp, const krux_opts *o, cudaStrea
   p.fdr_l0 = cp.fdr_l0;
   p.fdr_w = cp.fdr_w;
   const int grid = (int)std::min<size_t>(items.size(), (size_t)ctx->sm_count);
-  // Single hit list: stage hits per CTA (shared-memory counter, no global atomic
-  // per warp) and append the segments after the launch.
+  // Single hit list: every epilogue warp stages its hits in a segment of its own
+  // (no atomic per hit event) and the segments are appended after the launch.
   const bool staged = nslots == 1 && cp.slots[0].capacity > 0 && grid > 0;
+  const int n_seg = grid * kEpiWarps;
   if (staged) {
     const int64_t cap = cp.slots[0].capacity;
-    const int seg_cap = (int)std::max<int64_t>(256, std::min<int64_t>(32768, 2 * cap / grid + 256));
+    const int seg_cap = (int)std::max<int64_t>(64, std::min<int64_t>(4096, 2 * cap / n_seg + 64));
     const size_t rec = sizeof(krux_hit) + sizeof(HitAux);
-    KRUX_CUDA(ctx, ctx->seg.ensure((size_t)grid * seg_cap * rec + (size_t)grid * 4 + 256));
+    KRUX_CUDA(ctx, ctx->seg.ensure((size_t)n_seg * seg_cap * rec + (size_t)n_seg * 4 + 256));
     char *sb = ctx->seg.as<char>();
     p.seg_cap = seg_cap;
     p.seg_hits = reinterpret_cast<krux_hit *>(sb);
-    p.seg_aux = reinterpret_cast<HitAux *>(sb + (size_t)grid * seg_cap * sizeof(krux_hit));
-    p.seg_cnt = reinterpret_cast<unsigned int *>(sb + (size_t)grid * seg_cap * rec);
+    p.seg_aux = reinterpret_cast<HitAux *>(sb + (size_t)n_seg * seg_cap * sizeof(krux_hit));
+    p.seg_cnt = reinterpret_cast<unsigned int *>(sb + (size_t)n_seg * seg_cap * rec);
   }
   const size_t smem = scan_smem_bytes2(nc_max, nA, (size_t)p.a_tile_bytes, (size_t)p.b_region, p.kpad);
   {
@@ -974,7 +975,7 @@ krux_status run_fused(krux_ctx *ctx, CallPlan &cp, const krux_opts *o, cudaStrea
   ev_record(ctx, 4, s);
   unsigned long long *totals = ctx->counters.as<unsigned long long>() + nslots;
   if (staged) {
-    KRUX_CUDA(ctx, launch_seg_compact(p.seg_hits, p.seg_aux, p.seg_cnt, grid, p.seg_cap,
+    KRUX_CUDA(ctx, launch_seg_compact(p.seg_hits, p.seg_aux, p.seg_cnt, n_seg, p.seg_cap,
                                       ctx->counters.as<unsigned long long>(), cp.slots[0].hits,
                                       cp.slots[0].aux, cp.slots[0].capacity, totals, s));
   } else {
@@ -1034,6 +1035,7 @@ krux_status check_scan_args(krux_ctx *ctx, const krux_rankset *rs, const int8_t 
   if (S >= (int64_t)1 << 31) return fail(ctx, KRUX_EINVAL, "S must be < 2^31");
   if (opts->hit_capacity > 0 && (!hits || !hit_H || !hit_p))
     return fail(ctx, KRUX_EINVAL, "hit outputs are NULL");
+  if (((uintptr_t)hits & 15u) != 0) return fail(ctx, KRUX_EINVAL, "hits must be 16-byte aligned");
   const int64_t b = opts->snp_begin, e = opts->snp_end > 0 ? opts->snp_end : S;
   if (b < 0 || e > S || b > e)
     return fail(ctx, KRUX_EINVAL, "bad SNP slice [%lld, %lld)", (long long)b, (long long)e);
@@ -1087,7 +1089,7 @@ extern "C" krux_status krux_scan_grouped(krux_ctx *ctx, krux_cohort *cohorts, in
     krux_cohort &k = cohorts[c];
     k.n_hits = 0;
     if (!k.rs || k.S < 0 || (k.S > 0 && (!k.geno || k.ldg < k.rs->N)) || k.hit_capacity < 0 ||
-        (k.hit_capacity > 0 && (!k.hits || !k.hit_H || !k.hit_p)))
+        (k.hit_capacity > 0 && (!k.hits || !k.hit_H || !k.hit_p)) || ((uintptr_t)k.hits & 15u) != 0)
       return fail(ctx, KRUX_EINVAL, "cohort %d: bad arguments", c);
     captot += std::max<int64_t>(k.hit_capacity, 1);
   }

@@ -48,9 +48,39 @@ static_assert(sizeof(ChunkMeta) == 1536, "ChunkMeta must be 1536 bytes");
 
 // Side record of a hit, written next to the public krux_hit record and used by the
 // FP64 finalisation: the pair's group sizes and the group (cohort / bucket) index.
-struct HitAux {
+struct alignas(8) HitAux {
   uint16_t n0, n1, n2, group;
 };
+
+// Hit records move as one 16-byte and one 8-byte access (hit lists are 16-byte
+// aligned; the host rejects other pointers).  Stores are streaming (evict-first):
+// the records are not read again by the writing SM, and the scan kernel's small
+// L1 (most of the unified memory is shared memory) should keep its own lines.
+__device__ __forceinline__ void st_hit(krux_hit *dst, const krux_hit &r) {
+  __stcs(reinterpret_cast<uint4 *>(dst), make_uint4(r.trait, r.snp, (uint32_t)r.d0, (uint32_t)r.d1));
+}
+__device__ __forceinline__ void st_aux(HitAux *dst, const HitAux &a) {
+  __stcs(reinterpret_cast<uint2 *>(dst),
+         make_uint2((uint32_t)a.n0 | ((uint32_t)a.n1 << 16), (uint32_t)a.n2 | ((uint32_t)a.group << 16)));
+}
+__device__ __forceinline__ krux_hit ld_hit(const krux_hit *src) {
+  const uint4 v = *reinterpret_cast<const uint4 *>(src);
+  krux_hit r;
+  r.trait = v.x;
+  r.snp = v.y;
+  r.d0 = (int32_t)v.z;
+  r.d1 = (int32_t)v.w;
+  return r;
+}
+__device__ __forceinline__ HitAux ld_aux(const HitAux *src) {
+  const uint2 v = *reinterpret_cast<const uint2 *>(src);
+  HitAux a;
+  a.n0 = (uint16_t)(v.x & 0xffffu);
+  a.n1 = (uint16_t)(v.x >> 16);
+  a.n2 = (uint16_t)(v.y & 0xffffu);
+  a.group = (uint16_t)(v.y >> 16);
+  return a;
+}
 
 // ---- rank set: everything the scan needs about one expression matrix ------
 struct RankDev {
@@ -121,10 +151,11 @@ struct ScanParams {
   unsigned int *status;     // [0] error bits, [1] where
   long long timeout_cycles;
   int32_t signed_coef;      // 1: df-1 SNPs carry negated alpha, gamma (permutation batches)
-  int32_t seg_cap;          // records per CTA staging segment (0: hits go straight to the list)
-  krux_hit *seg_hits;       // [grid][seg_cap] staged hit records
-  HitAux *seg_aux;          // [grid][seg_cap]
-  unsigned int *seg_cnt;    // [grid] records staged by each CTA
+  int32_t seg_cap;          // records per staging segment (0: hits go straight to the list)
+  krux_hit *seg_hits;       // [grid][kEpiWarps][seg_cap] staged hit records, one segment per
+                            // epilogue warp
+  HitAux *seg_aux;          // [grid][kEpiWarps][seg_cap]
+  unsigned int *seg_cnt;    // [grid][kEpiWarps] records staged in each segment
   unsigned long long *fdr_hist;  // permutation batches: [1 + P][fdr_bins] counts of p < P_c by
                                  // -log10 p bin (row 0 = real data, filled by the finalisation)
   int32_t fdr_bins;
@@ -150,7 +181,7 @@ cudaError_t launch_scan(const ScanParams &p, int grid, size_t smem, cudaStream_t
 size_t scan_smem_bytes(int nc, int nA, int kpad);
 size_t scan_smem_bytes2(int nc, int nA, size_t a_tile_bytes, size_t b_region, int codes_k);
 cudaError_t launch_seg_compact(const krux_hit *seg_hits, const HitAux *seg_aux,
-                               const unsigned int *seg_cnt, int n_cta, int seg_cap,
+                               const unsigned int *seg_cnt, int n_seg, int seg_cap,
                                const unsigned long long *direct, krux_hit *out, HitAux *out_aux,
                                int64_t capacity, unsigned long long *total, cudaStream_t s);
 cudaError_t launch_minp_from_key(const double *key, double *minp, int P, int T, int ld,

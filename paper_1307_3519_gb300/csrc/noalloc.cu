@@ -156,7 +156,8 @@ extern "C" krux_status krux_scan_noalloc(const float *expr, int T, int N, int64_
   *n_hits = 0;
   if (!expr || T < 1 || T > kNaMaxT || N < 1 || N > kNaMaxN || ld < N || S < 0 ||
       (S > 0 && (!geno || ldg < N)) || S >= ((int64_t)1 << 31) || !(pthresh > 0.0 && pthresh < 1.0) ||
-      hit_capacity < 0 || (hit_capacity > 0 && (!hits || !hit_H || !hit_p)))
+      hit_capacity < 0 || (hit_capacity > 0 && (!hits || !hit_H || !hit_p)) ||
+      ((uintptr_t)hits & 15u) != 0)
     return KRUX_EINVAL;
   int dev = 0;
   NA_CUDA(cudaGetDevice(&dev));

@@ -138,13 +138,13 @@ plain_epilogue_kernel(const float *__restrict__ C, int64_t ldc, int T, int n_slo
       r.snp = (uint32_t)snp;
       r.d0 = u;
       r.d1 = v;
-      hits[idx] = r;
+      st_hit(hits + idx, r);
       HitAux a;
       a.n0 = (uint16_t)n0;
       a.n1 = (uint16_t)n1;
       a.n2 = (uint16_t)n2;
       a.group = 0;
-      aux[idx] = a;
+      st_aux(aux + idx, a);
     }
   }
 }

@@ -304,8 +304,9 @@ __device__ __forceinline__ float fmin3(float a, float b, float c) {
 // the band (q >= 0).  Two SNPs per packed instruction:
 //   w = u + beta v,  q = alpha w^2 + gamma v^2 - tau (1 - margin)
 // (with permutation batches the form is signed by df and |form| is tested).
+template <bool kSigned>
 __device__ __forceinline__ bool hit_fast(const uint32_t (&d0)[kEpiSnps], const uint32_t (&d1)[kEpiSnps],
-                                         const ChunkMeta &m, int h, float ntlo, bool signed_coef) {
+                                         const ChunkMeta &m, int h, float ntlo) {
   const uint64_t *al = reinterpret_cast<const uint64_t *>(m.alpha + kEpiSnps * h);
   const uint64_t *be = reinterpret_cast<const uint64_t *>(m.beta + kEpiSnps * h);
   const uint64_t *ga = reinterpret_cast<const uint64_t *>(m.gamma + kEpiSnps * h);
@@ -325,7 +326,7 @@ __device__ __forceinline__ bool hit_fast(const uint32_t (&d0)[kEpiSnps], const u
       const uint64_t w2 = ffma2(b2, v2, u2);
       const uint64_t e2 = fmul2(g2, v2);
       uint64_t q2;
-      if (!signed_coef) {
+      if (!kSigned) {
         q2 = ffma2(e2, v2, nt2);
         q2 = ffma2(fmul2(a2, w2), w2, q2);
       } else {
@@ -422,13 +423,13 @@ __device__ __noinline__ void hit_slow(const uint32_t *dv, bool mine, const Chunk
       r.snp = (uint32_t)m.snp[jb + j];
       r.d0 = (int32_t)__uint_as_float(dv[j]);
       r.d1 = (int32_t)__uint_as_float(dv[kEpiSnps + j]);
-      g.hits[idx] = r;
+      st_hit(g.hits + idx, r);
       HitAux a;
       a.n0 = (uint16_t)n0;
       a.n1 = (uint16_t)n1;
       a.n2 = (uint16_t)n2;
       a.group = (uint16_t)g.group_id;
-      g.aux[idx] = a;
+      st_aux(g.aux + idx, a);
     }
     ++idx;
   }
@@ -444,14 +445,15 @@ __device__ __noinline__ bool decide64(float u, float v, int n0, int n1, int n2, 
 // by the whole warp.  Each lane classifies its candidates (two SNPs per packed
 // instruction: at or above the upper band edge -> hit, inside the band -> FP64),
 // then the warp appends the hits column by column, so that the lanes holding a
-// hit of SNP j write consecutive records.  Records first fill the CTA's staging
-// segment through one shared-memory atomic per warp; whatever does not fit goes
-// straight to the caller's list through the global counter.  A compaction pass
-// appends the segments after the launch.
-__device__ __noinline__ void hit_event(const uint32_t *dv, bool mine, const ChunkMeta &m, int h,
-                                       int trait, float ntlo, float nthi, double cfac,
-                                       const GroupDesc &g, const ScanParams &p,
-                                       unsigned int *seg_n, int lane) {
+// hit of SNP j write consecutive records.  Records first fill this warp's own
+// staging segment (`wn` records already there; no atomic); whatever does not fit
+// goes straight to the caller's list through the global counter.  Returns the
+// number of hits found (the warp's segment counter advances by it).  A compaction
+// pass appends the segments after the launch.
+__device__ __noinline__ unsigned int hit_event(const uint32_t *dv, bool mine, const ChunkMeta &m,
+                                               int h, int trait, float ntlo, float nthi,
+                                               double cfac, const GroupDesc &g,
+                                               const ScanParams &p, unsigned int wn, int lane) {
   const int jb = kEpiSnps * h;
   uint32_t hm = 0;
   if (mine) {
@@ -488,17 +490,15 @@ __device__ __noinline__ void hit_event(const uint32_t *dv, bool mine, const Chun
     }
   }
   const unsigned int total = __reduce_add_sync(0xffffffffu, (unsigned int)__popc(hm));
-  if (total == 0u) return;
+  if (total == 0u) return 0u;
   const unsigned int cap = (unsigned int)p.seg_cap;
-  unsigned int sbase = 0;
-  if (lane == 0 && cap > 0) sbase = atomicAdd(seg_n, total);
-  sbase = __shfl_sync(0xffffffffu, sbase, 0);
+  const unsigned int sbase = wn;
   const unsigned int over_from = sbase > cap ? sbase : cap;  // first index beyond the segment
   const unsigned int n_over = sbase + total > over_from ? sbase + total - over_from : 0u;
   unsigned long long gbase = 0;
   if (lane == 0 && n_over > 0) gbase = atomicAdd(g.counter, (unsigned long long)n_over);
   gbase = __shfl_sync(0xffffffffu, gbase, 0);
-  const size_t seg0 = (size_t)blockIdx.x * cap;
+  const size_t seg0 = ((size_t)blockIdx.x * kEpiWarps + (threadIdx.x >> 5)) * cap;
   const uint32_t below_me = (1u << lane) - 1u;
   const uint16_t gid = (uint16_t)g.group_id;
   unsigned int run = sbase;  // index of the next record (same in every lane)
@@ -521,18 +521,19 @@ __device__ __noinline__ void hit_event(const uint32_t *dv, bool mine, const Chun
       x.n2 = m.n[2][jb + j];
       x.group = gid;
       if (idx < cap) {
-        p.seg_hits[seg0 + idx] = r;
-        p.seg_aux[seg0 + idx] = x;
+        st_hit(p.seg_hits + seg0 + idx, r);
+        st_aux(p.seg_aux + seg0 + idx, x);
       } else {
         const unsigned long long gi = gbase + (idx - over_from);
         if (gi < (unsigned long long)g.capacity) {
-          g.hits[gi] = r;
-          g.aux[gi] = x;
+          st_hit(g.hits + gi, r);
+          st_aux(g.aux + gi, x);
         }
       }
     }
     run += (unsigned int)__popc(bal);
   }
+  return total;
 }
 
 // Running best -ln p of one (permutation, trait) over this thread's SNPs.
@@ -646,7 +647,6 @@ __global__ void __launch_bounds__(kScanThreads, 1) krux_scan_kernel(const ScanPa
   uint32_t *tmem_holder =
       reinterpret_cast<uint32_t *>(bars + 2 * nA + 2 * nc + 2 * kTmemSlots + 1 + 2 * kTcDepth);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_holder + 1);
-  unsigned int *seg_n = tmem_holder + 2;  // hits staged by this CTA
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < nA; ++s) {
@@ -667,7 +667,6 @@ __global__ void __launch_bounds__(kScanThreads, 1) krux_scan_kernel(const ScanPa
       mbar_init(tc_empty(e), kEpiWarps);
     }
     *abort_flag = 0;
-    *seg_n = 0u;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
@@ -874,6 +873,7 @@ __global__ void __launch_bounds__(kScanThreads, 1) krux_scan_kernel(const ScanPa
     // epilogue warps
     const int q = warp & 3, h = warp >> 2;  // lane quarter, SNP group of the chunk
     uint32_t slot = 0, slot_phase = 0, b_bits = 0, tc_e = 0, tc_phase = 0;
+    unsigned int wn = 0;  // hits this warp has appended to its staging segment
     for (int it = blockIdx.x; it < p.n_items; it += gridDim.x) {
       const WorkItem w = p.items[it];
       const GroupDesc &g = p.groups[w.group];
@@ -953,7 +953,9 @@ __global__ void __launch_bounds__(kScanThreads, 1) krux_scan_kernel(const ScanPa
           if (minp_mode)
             need = et.valid && (et.nan_cnt > 0 || minp_fast(d0, d1, mc, h, ms, fdr_tau_lo));
           else
-            need = p.dense || et.nan_cnt > 0 || hit_fast(d0, d1, mc, h, et.ntlo, p.signed_coef != 0);
+            need = p.dense || et.nan_cnt > 0 ||
+                   (p.signed_coef ? hit_fast<true>(d0, d1, mc, h, et.ntlo)
+                                  : hit_fast<false>(d0, d1, mc, h, et.ntlo));
           if (__any_sync(0xffffffffu, need)) {
             // rare paths work on a local copy of the accumulators
             uint32_t dv[2 * kEpiSnps];
@@ -972,8 +974,8 @@ __global__ void __launch_bounds__(kScanThreads, 1) krux_scan_kernel(const ScanPa
               hit_slow(dv, need, mc, codes, h, et.trait, et.valid, et.ntlo, et.nthi, et.cfac,
                        et.nan_cnt, et.nan_idx, g, p, lane);
             } else {
-              hit_event(dv, need && et.valid, mc, h, et.trait, et.ntlo, et.nthi, et.cfac, g, p,
-                        seg_n, lane);
+              wn += hit_event(dv, need && et.valid, mc, h, et.trait, et.ntlo, et.nthi, et.cfac, g,
+                              p, wn, lane);
             }
           }
           if (step == w.step_end - 1) {
@@ -995,46 +997,57 @@ __global__ void __launch_bounds__(kScanThreads, 1) krux_scan_kernel(const ScanPa
     }
   epi_done:
     tc_fence_before();
+    if (lane == 0 && p.seg_cap > 0)
+      p.seg_cnt[blockIdx.x * kEpiWarps + warp] = min(wn, (unsigned int)p.seg_cap);
   }
 
   __syncthreads();
-  if (threadIdx.x == 0 && p.seg_cap > 0)
-    p.seg_cnt[blockIdx.x] = min(*seg_n, (unsigned int)p.seg_cap);
   if (warp == kMmaWarp) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem_base) : "memory");
   }
 }
 
-// Appends every CTA's staged hits after the directly appended ones: block b
-// copies its segment to offset direct + sum_{c<b} seg_cnt[c] (entries past the
-// capacity are dropped); block 0 also writes the exact total.
+// Appends every staging segment (one per epilogue warp of every CTA) after the
+// directly appended hits: block b copies segment b to offset
+// direct + sum_{c<b} seg_cnt[c] (entries past the capacity are dropped); block 0
+// also writes the exact total.
 __global__ void seg_compact_kernel(const krux_hit *__restrict__ seg_hits,
                                    const HitAux *__restrict__ seg_aux,
-                                   const unsigned int *__restrict__ seg_cnt, int seg_cap,
-                                   const unsigned long long *__restrict__ direct,
+                                   const unsigned int *__restrict__ seg_cnt, int n_seg,
+                                   int seg_cap, const unsigned long long *__restrict__ direct,
                                    krux_hit *__restrict__ out, HitAux *__restrict__ out_aux,
                                    int64_t capacity, unsigned long long *total) {
-  __shared__ unsigned long long off;
+  __shared__ unsigned long long part[2][8];
   const int b = blockIdx.x;
-  if (threadIdx.x == 0) {
-    unsigned long long o = *direct;
-    for (int c = 0; c < b; ++c) o += seg_cnt[c];
-    off = o;
-    if (b == 0) {
-      unsigned long long t = *direct;
-      for (int c = 0; c < (int)gridDim.x; ++c) t += seg_cnt[c];
-      *total = t;
-    }
+  unsigned long long before = 0, all = 0;
+  for (int c = threadIdx.x; c < n_seg; c += blockDim.x) {
+    const unsigned long long v = seg_cnt[c];
+    all += v;
+    if (c < b) before += v;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    before += __shfl_xor_sync(0xffffffffu, before, o);
+    all += __shfl_xor_sync(0xffffffffu, all, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    part[0][threadIdx.x >> 5] = before;
+    part[1][threadIdx.x >> 5] = all;
   }
   __syncthreads();
+  unsigned long long off = *direct, tot = *direct;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+    off += part[0][w];
+    tot += part[1][w];
+  }
+  if (b == 0 && threadIdx.x == 0) *total = tot;
   const unsigned int n = seg_cnt[b];
   const size_t s0 = (size_t)b * seg_cap;
   for (unsigned int i = threadIdx.x; i < n; i += blockDim.x) {
     const unsigned long long o = off + i;
     if (o < (unsigned long long)capacity) {
-      out[o] = seg_hits[s0 + i];
-      out_aux[o] = seg_aux[s0 + i];
+      st_hit(out + o, ld_hit(seg_hits + s0 + i));
+      st_aux(out_aux + o, ld_aux(seg_aux + s0 + i));
     }
   }
 }
@@ -1051,8 +1064,8 @@ __global__ void finalize_kernel(const krux_hit *__restrict__ hits, const HitAux 
                                 double fdr_w) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const krux_hit r = hits[i];
-    const HitAux a = aux[i];
+    const krux_hit r = ld_hit(hits + i);
+    const HitAux a = ld_aux(aux + i);
     const double cf = cfac_by_group[a.group][r.trait];
     const int df = df_of(a.n0, a.n1, a.n2);
     const double D0 = (double)r.d0, D1 = (double)r.d1, D2 = -(double)(r.d0 + r.d1);
@@ -1079,12 +1092,12 @@ __global__ void minp_from_key_kernel(const double *__restrict__ key, double *__r
 }  // namespace
 
 cudaError_t launch_seg_compact(const krux_hit *seg_hits, const HitAux *seg_aux,
-                               const unsigned int *seg_cnt, int n_cta, int seg_cap,
+                               const unsigned int *seg_cnt, int n_seg, int seg_cap,
                                const unsigned long long *direct, krux_hit *out, HitAux *out_aux,
                                int64_t capacity, unsigned long long *total, cudaStream_t s) {
-  if (n_cta <= 0) return cudaSuccess;
-  seg_compact_kernel<<<n_cta, 256, 0, s>>>(seg_hits, seg_aux, seg_cnt, seg_cap, direct, out, out_aux,
-                                           capacity, total);
+  if (n_seg <= 0) return cudaSuccess;
+  seg_compact_kernel<<<n_seg, 256, 0, s>>>(seg_hits, seg_aux, seg_cnt, n_seg, seg_cap, direct, out,
+                                           out_aux, capacity, total);
   return cudaGetLastError();
 }
 
