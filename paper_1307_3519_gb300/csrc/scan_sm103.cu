@@ -442,7 +442,8 @@ __device__ __noinline__ bool decide64(float u, float v, int n0, int n1, int n2, 
 }
 
 // Rare path of a hit-mode chunk half without dense output or NaN traits, called
-// by the whole warp.  Each lane classifies its candidates (two SNPs per packed
+// by the whole warp (inlined: a call costs more in register saves than the
+// extra code costs the hot loop).  Each lane classifies its candidates (two SNPs per packed
 // instruction: at or above the upper band edge -> hit, inside the band -> FP64),
 // then the warp appends the hits column by column, so that the lanes holding a
 // hit of SNP j write consecutive records.  Records first fill this warp's own
@@ -450,7 +451,7 @@ __device__ __noinline__ bool decide64(float u, float v, int n0, int n1, int n2, 
 // goes straight to the caller's list through the global counter.  Returns the
 // number of hits found (the warp's segment counter advances by it).  A compaction
 // pass appends the segments after the launch.
-__device__ __noinline__ unsigned int hit_event(const uint32_t *dv, bool mine, const ChunkMeta &m,
+__device__ __forceinline__ unsigned int hit_event(const uint32_t *dv, bool mine, const ChunkMeta &m,
                                                int h, int trait, float ntlo, float nthi,
                                                double cfac, const GroupDesc &g,
                                                const ScanParams &p, unsigned int wn, int lane) {
@@ -615,7 +616,7 @@ __device__ __noinline__ double minp_slow(const uint32_t *dv, const ChunkMeta &m,
   return best;
 }
 
-__global__ void __launch_bounds__(kScanThreads, 1) krux_scan_kernel(const ScanParams p) {
+__global__ void __launch_bounds__(kScanThreads, 1) krux_scan_kernel(const __grid_constant__ ScanParams p) {
   extern __shared__ uint8_t smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t raw = smem_u32(smem_raw);
