@@ -43,7 +43,10 @@ WORKLOAD = ("paper-scale fused scan: N=102 samples, T=20000 traits, S=500000 SNP
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one krux_scan_kernel
 # launch on the paper-scale workload, from one ncu capture, with the git blob hash of
 # the kernel source it was taken on: reported only while that source is unchanged.
-SCAN_TRAFFIC = None  # {"blob": "<sha1>", "bytes": <per launch>}
+# ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum on
+# "bench.py --scan-only --traits 20000 --snps 500000 --data paper": 242.51 MB read
+# + 78.04 MB written in one launch (1 pass, the full bench workload).
+SCAN_TRAFFIC = {"blob": "76fd062a3d396bc23619334d79b415df759f8c40", "bytes": 320.55e6}
 
 
 def kernel_blob():
