@@ -212,6 +212,58 @@ krux_status krux_scan_noalloc(const float *expr, int T, int N, int64_t ld, const
  * next scan return KRUX_EINVAL. */
 krux_status krux_set_tuning(krux_ctx *ctx, int layout, int nc, int nA, int ka);
 
+/* Autotuner (the tile shape is the project's own choice per sample width; the
+ * paper has no counterpart).  Times the fused scan of `rs` against the first
+ * min(S, 65536) SNPs of `geno` (device int8 [S][ldg]) at threshold pthresh for
+ * every launch shape that fits shared memory (both swizzle layouts, 1-4
+ * resident chunks, 2-4 rank stages, whole-K or 64-sample K blocks, and the
+ * automatic choice), three runs each, and keeps the fastest for the rank set's
+ * padded width Np: later scans whose widest group has that width use it, unless
+ * krux_set_tuning sets a shape.  shape_out (host int32[4], may be NULL) receives
+ * {layout, nc, nA, ka} of the winner (-1/0 entries = automatic).  Uses a
+ * temporary 40 MB device buffer; synchronises `stream`. */
+krux_status krux_autotune(krux_ctx *ctx, const krux_rankset *rs, const int8_t *geno, int64_t S,
+                          int64_t ldg, double pthresh, void *stream, int32_t *shape_out);
+
+/* CUDA graphs (the batched launch captured once and replayed; the paper has no
+ * counterpart).  krux_graph_scan / krux_graph_permute / krux_graph_grouped take
+ * the arguments of krux_scan / krux_permute / krux_scan_grouped (without
+ * n_hits and stream), plan the call once (the SNP groups, the launch shape, the
+ * work items) and capture its device work in a graph: for permutations the row
+ * gathers, then the packing of every group, the fused scan, the hit
+ * compaction, the FP64 finalisation (its hit count read on the device), the
+ * min-p conversion and the read-back of the hit counts into pinned host
+ * memory.  A replay (krux_graph_launch) reads the current contents of every
+ * buffer given at capture: new genotypes, ranks or permutations of the same
+ * shapes are scanned without any host work.  The graph owns a private
+ * workspace; the rank sets and all caller buffers must outlive it.
+ * Restrictions: complete genotypes at capture (a -1 code -> KRUX_EUNSUPPORTED);
+ * a -1 that appears in a replay is left out of the scan and reported by
+ * krux_graph_wait as KRUX_EUNSUPPORTED; a replayed permutation entry outside
+ * 0..N-1 reads as zeros and is reported as KRUX_EINVAL (replays check only the
+ * range of entries, not that a row is a permutation).
+ * *out receives the graph (free with krux_graph_destroy). */
+typedef struct krux_graph krux_graph;
+krux_status krux_graph_scan(krux_ctx *ctx, const krux_rankset *rs, const int8_t *geno, int64_t S,
+                            int64_t ldg, const krux_opts *opts, krux_hit *hits, double *hit_H,
+                            double *hit_p, krux_graph **out);
+krux_status krux_graph_permute(krux_ctx *ctx, const krux_rankset *rs, const int8_t *geno,
+                               int64_t S, int64_t ldg, const int32_t *perms, int P,
+                               const krux_opts *opts, double *minp, krux_hit *hits,
+                               double *hit_H, double *hit_p, uint64_t *fdr_hist, int fdr_bins,
+                               double fdr_bin_width, krux_graph **out);
+krux_status krux_graph_grouped(krux_ctx *ctx, const krux_cohort *cohorts, int n_cohorts,
+                               const krux_opts *opts, krux_graph **out);
+/* Enqueues one replay on `stream` (asynchronous). */
+krux_status krux_graph_launch(krux_graph *g, void *stream);
+/* Waits for the last replay and writes the exact hit count of each of its
+ * n_lists >= (number of hit lists: 1, or the cohort count) lists to n_hits
+ * (host).  Returns KRUX_OK, KRUX_EOVERFLOW (some list's count exceeds its
+ * capacity; the first `capacity` hits are stored), or a device-side error. */
+krux_status krux_graph_wait(krux_graph *g, int64_t *n_hits, int n_lists);
+const char *krux_graph_last_error(const krux_graph *g);
+void krux_graph_destroy(krux_graph *g);
+
 /* Test hook (no GPU needed): the pipeline shape a scan of one group of N samples
  * would use, after the same shared-memory plan check every launch passes.
  * out[7] = {samples per rank stage, rank stages, B region bytes, resident

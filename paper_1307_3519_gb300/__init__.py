@@ -26,7 +26,9 @@ STATUS_NAMES = ["KRUX_OK", "KRUX_EINVAL", "KRUX_ENOMEM", "KRUX_ECUDA", "KRUX_EOV
 EXPORTS = ["krux_create", "krux_destroy", "krux_status_string", "krux_last_error", "krux_rank",
            "krux_rankset_free", "krux_rankset_export", "krux_scan", "krux_scan_plain",
            "krux_permute", "krux_scan_grouped", "krux_make_perms", "krux_set_profiling",
-           "krux_get_profile", "krux_set_wait_limit", "krux_set_tuning", "krux_scan_noalloc", "krux_debug_plan"]
+           "krux_get_profile", "krux_set_wait_limit", "krux_set_tuning", "krux_scan_noalloc", "krux_debug_plan",
+           "krux_autotune", "krux_graph_scan", "krux_graph_permute", "krux_graph_grouped",
+           "krux_graph_launch", "krux_graph_wait", "krux_graph_last_error", "krux_graph_destroy"]
 
 
 class KruxError(RuntimeError):
@@ -89,6 +91,15 @@ def load_library(path=LIB_PATH):
         "krux_set_tuning": ([P, I, I, I, I], I),
         "krux_debug_plan": ([I, I, I, I, I, I, P], I),
         "krux_scan_noalloc": ([P, I, I, I64, P, I64, I64, D, P, P, P, I64, ctypes.POINTER(I64), P], I),
+        "krux_autotune": ([P, P, P, I64, I64, D, P, P], I),
+        "krux_graph_scan": ([P, P, P, I64, I64, ctypes.POINTER(Opts), P, P, P, ctypes.POINTER(P)], I),
+        "krux_graph_permute": ([P, P, P, I64, I64, P, I, ctypes.POINTER(Opts), P, P, P, P, P, I, D,
+                                ctypes.POINTER(P)], I),
+        "krux_graph_grouped": ([P, ctypes.POINTER(Cohort), I, ctypes.POINTER(Opts), ctypes.POINTER(P)], I),
+        "krux_graph_launch": ([P, P], I),
+        "krux_graph_wait": ([P, ctypes.POINTER(I64), I], I),
+        "krux_graph_last_error": ([P], ctypes.c_char_p),
+        "krux_graph_destroy": ([P], None),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -334,6 +345,82 @@ class Krux:
                             hits=hits[:k], H=H[:k], p=P[:k]))
         return out
 
+    # ---- autotuner and CUDA graphs ---------------------------------------------
+    def autotune(self, rs, geno, pthresh, stream=None):
+        """Times every launch shape on a sample of geno and keeps the fastest for
+        this rank set's width.  Returns (layout, nc, nA, ka) of the winner."""
+        shape = (ctypes.c_int32 * 4)()
+        st = self.lib.krux_autotune(self.handle, rs.handle, _ptr(geno), geno.shape[0], geno.stride(0),
+                                    float(pthresh), _stream(stream), shape)
+        self._check(st, "krux_autotune")
+        return tuple(shape)
+
+    def _outputs(self, capacity):
+        import torch
+        return (torch.empty((max(capacity, 1), 4), dtype=torch.int32, device=self.device),
+                torch.empty(max(capacity, 1), dtype=torch.float64, device=self.device),
+                torch.empty(max(capacity, 1), dtype=torch.float64, device=self.device))
+
+    def graph_scan(self, rs, geno, pthresh, capacity, dense=False):
+        """krux_scan captured as a CUDA graph; returns a Graph (launch / wait)."""
+        import torch
+        hits, H, P = self._outputs(capacity)
+        dn = None
+        if dense:
+            dn = (torch.empty((rs.T, geno.shape[0]), dtype=torch.float64, device=self.device),
+                  torch.empty((rs.T, geno.shape[0]), dtype=torch.float64, device=self.device))
+        o = self._opts(pthresh, capacity, dense=dn)
+        h = ctypes.c_void_p()
+        st = self.lib.krux_graph_scan(self.handle, rs.handle, _ptr(geno), geno.shape[0], geno.stride(0),
+                                      ctypes.byref(o), _ptr(hits), _ptr(H), _ptr(P), ctypes.byref(h))
+        self._check(st, "krux_graph_scan")
+        g = Graph(self, h, [(hits, H, P, capacity)], keep=(geno, rs))
+        if dn is not None:
+            g.dense = dn
+        return g
+
+    def graph_permute(self, rs, geno, perms, pthresh, capacity, fdr_bins=0, fdr_bin_width=0.1):
+        """krux_permute captured as a CUDA graph (minp, fdr_hist and the hits are
+        rewritten by every replay)."""
+        import torch
+        hits, H, P = self._outputs(capacity)
+        P_ = perms.shape[0]
+        minp = torch.empty((P_, rs.T), dtype=torch.float64, device=self.device)
+        hist = (torch.empty((1 + P_, fdr_bins), dtype=torch.int64, device=self.device)
+                if fdr_bins > 0 else None)
+        o = self._opts(pthresh, capacity)
+        h = ctypes.c_void_p()
+        st = self.lib.krux_graph_permute(self.handle, rs.handle, _ptr(geno), geno.shape[0],
+                                         geno.stride(0), _ptr(perms), P_, ctypes.byref(o), _ptr(minp),
+                                         _ptr(hits), _ptr(H), _ptr(P), _ptr(hist), fdr_bins,
+                                         float(fdr_bin_width), ctypes.byref(h))
+        self._check(st, "krux_graph_permute")
+        g = Graph(self, h, [(hits, H, P, capacity)], keep=(geno, perms, rs))
+        g.minp, g.fdr_hist = minp, hist
+        return g
+
+    def graph_grouped(self, cohorts, pthresh):
+        """krux_scan_grouped captured as a CUDA graph; cohorts as for krux_scan_grouped."""
+        arr = (Cohort * len(cohorts))()
+        outs = []
+        for i, c in enumerate(cohorts):
+            hits, H, P = self._outputs(c["capacity"])
+            outs.append((hits, H, P, c["capacity"]))
+            g = c["geno"]
+            arr[i].rs = c["rs"].handle
+            arr[i].geno = g.data_ptr()
+            arr[i].S = g.shape[0]
+            arr[i].ldg = g.stride(0)
+            arr[i].hits = hits.data_ptr()
+            arr[i].hit_H = H.data_ptr()
+            arr[i].hit_p = P.data_ptr()
+            arr[i].hit_capacity = c["capacity"]
+        o = self._opts(pthresh, 0)
+        h = ctypes.c_void_p()
+        st = self.lib.krux_graph_grouped(self.handle, arr, len(cohorts), ctypes.byref(o), ctypes.byref(h))
+        self._check(st, "krux_graph_grouped")
+        return Graph(self, h, outs, keep=tuple(cohorts))
+
     # ---- end to end from host arrays -------------------------------------------
     def scan_pinned(self, expr_h, geno_h, pthresh, capacity, stream=None):
         """End-to-end scan from pinned host tensors (float32 [T,N], int8 [S,N]):
@@ -363,3 +450,40 @@ class Krux:
                    p=r["p"].cpu().numpy())
         rs.free()
         return out
+
+
+class Graph:
+    """A captured scan (krux_graph_*): launch() enqueues a replay, wait() returns
+    one result dict per hit list (as krux_scan's).  Keeps the tensors it reads
+    and writes alive."""
+
+    def __init__(self, ctx, handle, outs, keep=()):
+        self.ctx, self.handle, self.outs, self.keep = ctx, handle, outs, keep
+        self.lib = ctx.lib
+
+    def launch(self, stream=None):
+        st = self.lib.krux_graph_launch(self.handle, _stream(stream))
+        if st != KRUX_OK:
+            raise KruxError(st, "krux_graph_launch: " + (self.lib.krux_graph_last_error(self.handle) or b"").decode())
+
+    def wait(self):
+        n = (ctypes.c_int64 * len(self.outs))()
+        st = self.lib.krux_graph_wait(self.handle, n, len(self.outs))
+        if st not in (KRUX_OK, KRUX_EOVERFLOW):
+            raise KruxError(st, "krux_graph_wait: " + (self.lib.krux_graph_last_error(self.handle) or b"").decode())
+        res = []
+        for (hits, H, P, cap), cnt in zip(self.outs, n):
+            k = min(cnt, cap)
+            res.append(dict(n_hits=cnt, overflow=cnt > cap, hits=hits[:k], H=H[:k], p=P[:k]))
+        return res
+
+    def close(self):
+        if self.handle:
+            self.lib.krux_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

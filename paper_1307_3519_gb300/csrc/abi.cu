@@ -5,6 +5,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -119,6 +120,7 @@ struct krux_ctx {
       list, gemm_out, bucket_ranks, permA, minpkey, seg, permNan;
   void *blas = nullptr;
   std::vector<std::pair<size_t, void *>> pool;  // freed rank-set blocks, reused by size
+  std::map<int, std::array<int, 4>> tuned;       // krux_autotune: K width -> layout, nc, nA, ka
 };
 
 namespace {
@@ -672,8 +674,18 @@ struct CallPlan {
   std::vector<int64_t> lists;         // host copy of all SNP lists
   std::vector<BucketJob> bucket_jobs;
   std::vector<krux_rankset> bucket_sets;  // host shells of the re-ranked sets
-  unsigned long long *fdr_hist = nullptr;  // permutation calls: [1 + P][fdr_bins] or null
-  int fdr_bins = 0;
+  struct PermJob {  // permutation batch: the stacked, permuted rank matrices
+    bool on = false;
+    const krux_rankset *rs = nullptr;
+    const int32_t *perms = nullptr;
+    int P = 0;
+    __half *stack = nullptr;     // [1 + P][rows_pad][Np]
+    double *minp = nullptr;      // caller's [P][T]
+    uint16_t *lists = nullptr;   // [1 + P][T][N] NaN sample lists (rank sets with NaN)
+    int32_t *inv = nullptr;      // [P][N] inverse permutations
+  } perm;
+  unsigned long long *fdr_hist = nullptr;  // permutation calls: [fdr_rows = 1 + P][fdr_bins] or null
+  int fdr_rows = 0, fdr_bins = 0;
   double fdr_l0 = 0.0, fdr_w = 1.0;
 };
 
@@ -820,18 +832,53 @@ krux_status materialise(krux_ctx *ctx, CallPlan &cp, cudaStream_t s) {
   return KRUX_OK;
 }
 
-// Packs every group, launches the fused kernel once over all groups, reads the
-// per-slot hit counts back and runs the FP64 finalisation per slot.
-krux_status run_fused(krux_ctx *ctx, CallPlan &cp, const krux_opts *o, cudaStream_t s,
-                      std::vector<unsigned long long> &counts) {
-  const double h1 = h_df1(o->pthresh), h2 = h_df2(o->pthresh);
-  const int ng = (int)cp.groups.size();
-  const int nslots = (int)cp.slots.size();
+// One fused launch, split in three phases so that the middle one can be captured
+// in a CUDA graph: prepare (host planning, buffer sizing, descriptor uploads; no
+// work queued that a replay would need), enqueue (stream work only: packing, the
+// scan, compaction, device-count-driven finalisation), finish (synchronise, read
+// the counts and the status word).
+struct FusedLaunch {
+  ScanParams p{};
+  int grid = 0;
+  size_t smem = 0;
+  bool staged = false;
+  int n_seg = 0;
+  int nslots = 0;
+  double h1 = 0.0, h2 = 0.0;
   int signed_coef = 0;
-  for (auto &g : cp.groups) signed_coef |= g.minp_key != nullptr ? 1 : 0;
-  counts.assign(nslots, 0);
+  std::vector<int64_t> boff, moff, coff;
+  int layout = 1;
+};
+
+krux_status prepare_fused(krux_ctx *ctx, CallPlan &cp, const krux_opts *o, FusedLaunch &fl,
+                          cudaStream_t s) {
+  fl.h1 = h_df1(o->pthresh);
+  fl.h2 = h_df2(o->pthresh);
+  const int ng = (int)cp.groups.size();
+  fl.nslots = (int)cp.slots.size();
+  fl.signed_coef = 0;
+  for (auto &g : cp.groups) fl.signed_coef |= g.minp_key != nullptr ? 1 : 0;
+  KRUX_CUDA(ctx, ctx->counters.ensure((size_t)fl.nslots * 16 + 64));
+  KRUX_CUDA(ctx, ctx->status.ensure(64));
   if (ng == 0) return KRUX_OK;
-  const int layout = ctx->tune_layout >= 0 ? ctx->tune_layout : 1;
+  int lay = -1, tnc = ctx->tune_nc, tnA = ctx->tune_nA, tka = ctx->tune_ka;
+  const int atom0 = layout_atom(ctx->tune_layout >= 0 ? ctx->tune_layout : 1);
+  int kpad0 = atom0;
+  for (auto &g : cp.groups) kpad0 = std::max(kpad0, round_up(g.rs->Np, atom0));
+  if (ctx->tune_layout >= 0 || ctx->tune_nc > 0) {
+    lay = ctx->tune_layout;
+  } else {
+    // a shape picked by krux_autotune for this width, if there is one
+    auto it = ctx->tuned.find(round_up(kpad0, 16));
+    if (it != ctx->tuned.end()) {
+      lay = it->second[0];
+      tnc = it->second[1];
+      tnA = it->second[2];
+      tka = it->second[3];
+    }
+  }
+  const int layout = lay >= 0 ? lay : 1;
+  fl.layout = layout;
   const int atom = layout_atom(layout);
   int kpad = atom, codes_k = 0;
   for (auto &g : cp.groups) {
@@ -839,18 +886,29 @@ krux_status run_fused(krux_ctx *ctx, CallPlan &cp, const krux_opts *o, cudaStrea
     if (g.nan_cnt) codes_k = std::max(codes_k, g.rs->Np);
   }
   LaunchShape sh;
-  if (!pick_launch_shape(ctx, kpad, codes_k, sh))
-    return fail(ctx, ctx->tune_nc > 0 ? KRUX_EINVAL : KRUX_EUNSUPPORTED,
-                "no pipeline shape fits shared memory (Np=%d, tuning nc=%d nA=%d ka=%d)", kpad,
-                ctx->tune_nc, ctx->tune_nA, ctx->tune_ka);
-  const int nA = sh.nA;
-  std::vector<int64_t> boff(ng), moff(ng), coff(ng);
+  {
+    const int s_nc = ctx->tune_nc, s_nA = ctx->tune_nA, s_ka = ctx->tune_ka;
+    ctx->tune_nc = tnc;
+    ctx->tune_nA = tnA;
+    ctx->tune_ka = tka;
+    const bool ok = pick_launch_shape(ctx, kpad, codes_k, sh);
+    ctx->tune_nc = s_nc;
+    ctx->tune_nA = s_nA;
+    ctx->tune_ka = s_ka;
+    if (!ok)
+      return fail(ctx, tnc > 0 ? KRUX_EINVAL : KRUX_EUNSUPPORTED,
+                  "no pipeline shape fits shared memory (Np=%d, tuning nc=%d nA=%d ka=%d)", kpad,
+                  tnc, tnA, tka);
+  }
+  fl.boff.assign(ng, 0);
+  fl.moff.assign(ng, 0);
+  fl.coff.assign(ng, 0);
   int64_t btot = 0, mtot = 0, ctot = 0;
   for (int i = 0; i < ng; ++i) {
     const int64_t nch = (cp.groups[i].n_snps + kChunkSnps - 1) / kChunkSnps;
-    boff[i] = btot;
-    moff[i] = mtot;
-    coff[i] = ctot;
+    fl.boff[i] = btot;
+    fl.moff[i] = mtot;
+    fl.coff[i] = ctot;
     btot += (nch * kChunkRows * cp.groups[i].rs->Np * 2 + 255) / 256 * 256;
     mtot += nch;
     if (cp.groups[i].nan_cnt) ctot += nch * cp.groups[i].rs->Np * 2;
@@ -858,13 +916,6 @@ krux_status run_fused(krux_ctx *ctx, CallPlan &cp, const krux_opts *o, cudaStrea
   KRUX_CUDA(ctx, ctx->B.ensure(std::max<int64_t>(btot, 256)));
   KRUX_CUDA(ctx, ctx->meta.ensure(std::max<int64_t>(mtot, 1) * sizeof(ChunkMeta)));
   KRUX_CUDA(ctx, ctx->codes.ensure(std::max<int64_t>(ctot, 1) * 8));
-  KRUX_CUDA(ctx, ctx->counters.ensure((size_t)nslots * 16 + 64));
-  KRUX_CUDA(ctx, ctx->status.ensure(64));
-  KRUX_CUDA(ctx, cudaMemsetAsync(ctx->counters.p, 0, (size_t)nslots * 16, s));
-  KRUX_CUDA(ctx, cudaMemsetAsync(ctx->status.p, 0, 64, s));
-  unsigned int *status = ctx->status.as<unsigned int>();
-
-  ev_record(ctx, 2, s);
   std::vector<GroupDesc> descs(ng);
   std::vector<GroupPlan> plans(ng);
   int nc_max = 1;
@@ -872,11 +923,7 @@ krux_status run_fused(krux_ctx *ctx, CallPlan &cp, const krux_opts *o, cudaStrea
     ScanGroupIn &g = cp.groups[i];
     const krux_rankset *rs = g.rs;
     const OutSlot &os = cp.slots[g.out_slot];
-    __half *B = reinterpret_cast<__half *>(ctx->B.as<char>() + boff[i]);
-    ChunkMeta *meta = ctx->meta.as<ChunkMeta>() + moff[i];
-    uint64_t *codes = g.nan_cnt ? ctx->codes.as<uint64_t>() + coff[i] : nullptr;
-    KRUX_CUDA(ctx, launch_pack2(g.geno, g.ldg, rs->N, rs->Np, g.snp_list, g.snp_begin, g.n_snps, 0,
-                                h1, h2, g.allow_missing, signed_coef, B, meta, codes, status, s));
+    __half *B = reinterpret_cast<__half *>(ctx->B.as<char>() + fl.boff[i]);
     GroupDesc &d = plans[i].d;
     std::memset(&d, 0, sizeof d);
     const int64_t nch = (g.n_snps + kChunkSnps - 1) / kChunkSnps;
@@ -885,8 +932,8 @@ krux_status run_fused(krux_ctx *ctx, CallPlan &cp, const krux_opts *o, cudaStrea
     if (st != KRUX_OK) return st;
     st = encode_map(ctx, &d.tmB, B, rs->Np, std::max<int64_t>(nch, 1) * kChunkRows, layout);
     if (st != KRUX_OK) return st;
-    d.meta = meta;
-    d.codes = codes;
+    d.meta = ctx->meta.as<ChunkMeta>() + fl.moff[i];
+    d.codes = g.nan_cnt ? ctx->codes.as<uint64_t>() + fl.coff[i] : nullptr;
     d.tau = g.tau;
     d.cfac = g.cfac;
     d.nan_cnt = g.nan_cnt;
@@ -917,21 +964,28 @@ krux_status run_fused(krux_ctx *ctx, CallPlan &cp, const krux_opts *o, cudaStrea
     plans[i].steps = (int64_t)g.n_agroups * rs->n_ttiles;
     descs[i] = d;
   }
-  ev_record(ctx, 3, s);
   std::vector<WorkItem> items = make_items(plans, nc_max, ctx->sm_count);
   KRUX_CUDA(ctx, ctx->groups.ensure(sizeof(GroupDesc) * ng));
   KRUX_CUDA(ctx, ctx->items.ensure(sizeof(WorkItem) * std::max<size_t>(items.size(), 1)));
+  // pageable uploads: staged before the calls return, so the host vectors may go
   KRUX_CUDA(ctx, cudaMemcpyAsync(ctx->groups.p, descs.data(), sizeof(GroupDesc) * ng,
                                  cudaMemcpyHostToDevice, s));
   if (!items.empty())
     KRUX_CUDA(ctx, cudaMemcpyAsync(ctx->items.p, items.data(), sizeof(WorkItem) * items.size(),
                                    cudaMemcpyHostToDevice, s));
-  ScanParams p{};
+  std::vector<const double *> cf(ng);
+  for (int i = 0; i < ng; ++i) cf[i] = cp.groups[i].cfac;
+  KRUX_CUDA(ctx, ctx->cfacptr.ensure(sizeof(double *) * ng));
+  KRUX_CUDA(ctx, cudaMemcpyAsync(ctx->cfacptr.p, cf.data(), sizeof(double *) * ng,
+                                 cudaMemcpyHostToDevice, s));
+  KRUX_CUDA(ctx, finalize_prepare());
+  ScanParams &p = fl.p;
+  p = ScanParams{};
   p.groups = ctx->groups.as<GroupDesc>();
   p.items = ctx->items.as<WorkItem>();
   p.n_items = (int32_t)items.size();
   p.nc = nc_max;
-  p.nA = nA;
+  p.nA = sh.nA;
   p.kpad = std::max(codes_k, 16);
   p.ka = sh.ka;
   p.a_tile_bytes = 256 * sh.ka;
@@ -940,87 +994,164 @@ krux_status run_fused(krux_ctx *ctx, CallPlan &cp, const krux_opts *o, cudaStrea
   p.margin = (float)(o->recheck_margin > 0 ? o->recheck_margin : 1e-4);
   p.dense = o->dense_H != nullptr ? 1 : 0;
   p.pthresh = o->pthresh;
-  p.h1 = (float)h1;
-  p.h2 = (float)h2;
-  p.status = status;
+  p.h1 = (float)fl.h1;
+  p.h2 = (float)fl.h2;
+  p.status = ctx->status.as<unsigned int>();
   p.timeout_cycles = ctx->wait_limit;
-  p.signed_coef = signed_coef;
+  p.signed_coef = fl.signed_coef;
   p.fdr_hist = cp.fdr_hist;
   p.fdr_bins = cp.fdr_bins;
   p.fdr_l0 = cp.fdr_l0;
   p.fdr_w = cp.fdr_w;
-  const int grid = (int)std::min<size_t>(items.size(), (size_t)ctx->sm_count);
+  fl.grid = (int)std::min<size_t>(items.size(), (size_t)ctx->sm_count);
   // Single hit list: every epilogue warp stages its hits in a segment of its own
   // (no atomic per hit event) and the segments are appended after the launch.
-  const bool staged = nslots == 1 && cp.slots[0].capacity > 0 && grid > 0;
-  const int n_seg = grid * kEpiWarps;
-  if (staged) {
+  fl.staged = fl.nslots == 1 && cp.slots[0].capacity > 0 && fl.grid > 0;
+  fl.n_seg = fl.grid * kEpiWarps;
+  if (fl.staged) {
     const int64_t cap = cp.slots[0].capacity;
-    const int seg_cap = (int)std::max<int64_t>(64, std::min<int64_t>(4096, 2 * cap / n_seg + 64));
+    const int seg_cap = (int)std::max<int64_t>(64, std::min<int64_t>(4096, 2 * cap / fl.n_seg + 64));
     const size_t rec = sizeof(krux_hit) + sizeof(HitAux);
-    KRUX_CUDA(ctx, ctx->seg.ensure((size_t)n_seg * seg_cap * rec + (size_t)n_seg * 4 + 256));
+    KRUX_CUDA(ctx, ctx->seg.ensure((size_t)fl.n_seg * seg_cap * rec + (size_t)fl.n_seg * 4 + 256));
     char *sb = ctx->seg.as<char>();
     p.seg_cap = seg_cap;
     p.seg_hits = reinterpret_cast<krux_hit *>(sb);
-    p.seg_aux = reinterpret_cast<HitAux *>(sb + (size_t)n_seg * seg_cap * sizeof(krux_hit));
-    p.seg_cnt = reinterpret_cast<unsigned int *>(sb + (size_t)n_seg * seg_cap * rec);
+    p.seg_aux = reinterpret_cast<HitAux *>(sb + (size_t)fl.n_seg * seg_cap * sizeof(krux_hit));
+    p.seg_cnt = reinterpret_cast<unsigned int *>(sb + (size_t)fl.n_seg * seg_cap * rec);
   }
-  const size_t smem = scan_smem_bytes2(nc_max, nA, (size_t)p.a_tile_bytes, (size_t)p.b_region, p.kpad);
-  {
-    const std::string why = validate_plan(p, descs, smem);
-    if (!why.empty()) return fail(ctx, KRUX_EUNSUPPORTED, "%s", why.c_str());
+  fl.smem = scan_smem_bytes2(nc_max, sh.nA, (size_t)p.a_tile_bytes, (size_t)p.b_region, p.kpad);
+  const std::string why = validate_plan(p, descs, fl.smem);
+  if (!why.empty()) return fail(ctx, KRUX_EUNSUPPORTED, "%s", why.c_str());
+  if (fl.grid > 0) KRUX_CUDA(ctx, scan_set_smem(fl.smem));
+  return KRUX_OK;
+}
+
+krux_status enqueue_fused(krux_ctx *ctx, CallPlan &cp, const FusedLaunch &fl, cudaStream_t s) {
+  const int ng = (int)cp.groups.size();
+  const int nslots = fl.nslots;
+  KRUX_CUDA(ctx, cudaMemsetAsync(ctx->counters.p, 0, (size_t)nslots * 16, s));
+  KRUX_CUDA(ctx, cudaMemsetAsync(ctx->status.p, 0, 64, s));
+  if (cp.fdr_hist)
+    KRUX_CUDA(ctx, cudaMemsetAsync(cp.fdr_hist, 0, (size_t)cp.fdr_rows * cp.fdr_bins * 8, s));
+  if (ng == 0) {  // nothing to scan: a permutation batch still reports min p = 1
+    if (cp.perm.on) {
+      KRUX_CUDA(ctx, cudaMemsetAsync(ctx->minpkey.p, 0,
+                                     (size_t)cp.perm.P * cp.perm.rs->rows_pad * 8, s));
+      KRUX_CUDA(ctx, launch_minp_from_key(ctx->minpkey.as<double>(), cp.perm.minp, cp.perm.P,
+                                          cp.perm.rs->T, cp.perm.rs->rows_pad, s));
+    }
+    return KRUX_OK;
   }
+  unsigned int *status = ctx->status.as<unsigned int>();
+  if (cp.perm.on) {
+    const CallPlan::PermJob &pj = cp.perm;
+    const krux_rankset *rs = pj.rs;
+    const size_t one = (size_t)rs->rows_pad * rs->Np;
+    KRUX_CUDA(ctx, cudaMemcpyAsync(pj.stack, rs->dev.A, one * 2, cudaMemcpyDeviceToDevice, s));
+    KRUX_CUDA(ctx, launch_permute_rows(rs->dev.A, pj.stack + one, rs->rows_pad, rs->Np, rs->N,
+                                       pj.perms, pj.P, status, s));
+    KRUX_CUDA(ctx, cudaMemsetAsync(ctx->minpkey.p, 0, (size_t)pj.P * rs->rows_pad * 8, s));
+    if (pj.lists) {
+      // NaN samples of permutation q sit at inv_q(original position)
+      const size_t lst = (size_t)rs->T * rs->N;
+      // zero first: entries a bad replayed row never writes stay valid sample indices
+      KRUX_CUDA(ctx, cudaMemsetAsync(pj.inv, 0, (size_t)pj.P * rs->N * 4, s));
+      KRUX_CUDA(ctx, launch_invert_perms(pj.perms, pj.P, rs->N, pj.inv, s));
+      KRUX_CUDA(ctx, cudaMemcpyAsync(pj.lists, rs->dev.nan_idx, lst * 2, cudaMemcpyDeviceToDevice, s));
+      KRUX_CUDA(ctx, launch_permute_nan_idx(rs->dev.nan_cnt, rs->dev.nan_idx, rs->T, rs->N, pj.inv,
+                                            pj.P, pj.lists + lst, s));
+    }
+  }
+  ev_record(ctx, 2, s);
+  for (int i = 0; i < ng; ++i) {
+    const ScanGroupIn &g = cp.groups[i];
+    const krux_rankset *rs = g.rs;
+    __half *B = reinterpret_cast<__half *>(ctx->B.as<char>() + fl.boff[i]);
+    ChunkMeta *meta = ctx->meta.as<ChunkMeta>() + fl.moff[i];
+    uint64_t *codes = g.nan_cnt ? ctx->codes.as<uint64_t>() + fl.coff[i] : nullptr;
+    KRUX_CUDA(ctx, launch_pack2(g.geno, g.ldg, rs->N, rs->Np, g.snp_list, g.snp_begin, g.n_snps, 0,
+                                fl.h1, fl.h2, g.allow_missing, fl.signed_coef, B, meta, codes,
+                                status, s));
+  }
+  ev_record(ctx, 3, s);
   ev_record(ctx, 7, s);  // the scan kernel alone: events 7 .. 4
-  if (grid > 0) KRUX_CUDA(ctx, launch_scan(p, grid, smem, s));
+  if (fl.grid > 0) KRUX_CUDA(ctx, launch_scan_only(fl.p, fl.grid, fl.smem, s));
   ev_record(ctx, 4, s);
   unsigned long long *totals = ctx->counters.as<unsigned long long>() + nslots;
-  if (staged) {
-    KRUX_CUDA(ctx, launch_seg_compact(p.seg_hits, p.seg_aux, p.seg_cnt, n_seg, p.seg_cap,
-                                      ctx->counters.as<unsigned long long>(), cp.slots[0].hits,
-                                      cp.slots[0].aux, cp.slots[0].capacity, totals, s));
+  if (fl.staged) {
+    KRUX_CUDA(ctx, launch_seg_compact(fl.p.seg_hits, fl.p.seg_aux, fl.p.seg_cnt, fl.n_seg,
+                                      fl.p.seg_cap, ctx->counters.as<unsigned long long>(),
+                                      cp.slots[0].hits, cp.slots[0].aux, cp.slots[0].capacity,
+                                      totals, s));
   } else {
     KRUX_CUDA(ctx, cudaMemcpyAsync(totals, ctx->counters.p, (size_t)nslots * 8,
                                    cudaMemcpyDeviceToDevice, s));
   }
-
-  unsigned int hst[2] = {0, 0};
-  KRUX_CUDA(ctx, cudaMemcpyAsync(counts.data(), totals, (size_t)nslots * 8,
-                                 cudaMemcpyDeviceToHost, s));
-  KRUX_CUDA(ctx, cudaMemcpyAsync(hst, ctx->status.p, 8, cudaMemcpyDeviceToHost, s));
-  KRUX_CUDA(ctx, cudaStreamSynchronize(s));
-  if (ctx->profiling) {
-    ctx->prof.ms_pack = ev_ms(ctx, 2, 3);
-    ctx->prof.ms_scan = ev_ms(ctx, 7, 4);
-    ctx->prof.scan_grid = grid;
-    ctx->prof.launches += (grid > 0 ? 1 : 0) + (staged ? 1 : 0);
-    for (auto &g : cp.groups) ctx->prof.launches += g.nan_cnt ? 2 : 1;
-  }
-  if (hst[0] & kDevBadCode) return fail(ctx, KRUX_EINVAL, "genotype code outside {-1,0,1,2}");
-  if (hst[0] & kDevTimeout)
-    return fail(ctx, KRUX_ETIMEOUT, "device wait timed out (site %u)", hst[1]);
-
-  // FP64 H and p of the stored hits
-  std::vector<const double *> cf(ng);
-  for (int i = 0; i < ng; ++i) cf[i] = cp.groups[i].cfac;
-  KRUX_CUDA(ctx, ctx->cfacptr.ensure(sizeof(double *) * ng));
-  KRUX_CUDA(ctx, cudaMemcpyAsync(ctx->cfacptr.p, cf.data(), sizeof(double *) * ng,
-                                 cudaMemcpyHostToDevice, s));
+  // FP64 H and p of the stored hits: each slot's count is read on the device
   ev_record(ctx, 5, s);
   for (int k = 0; k < nslots; ++k) {
     const OutSlot &os = cp.slots[k];
-    const int64_t nst = std::min<int64_t>((int64_t)counts[k], os.capacity);
-    if (nst > 0) {
-      KRUX_CUDA(ctx, launch_finalize(os.hits, os.aux, nst, ctx->cfacptr.as<const double *>(), os.H,
-                                     os.P, s, cp.fdr_hist, cp.fdr_bins, cp.fdr_l0, cp.fdr_w));
-      if (ctx->profiling) ctx->prof.launches += 1;
-    }
+    if (os.capacity <= 0) continue;
+    KRUX_CUDA(ctx, launch_finalize_dev(os.hits, os.aux, totals + k, os.capacity,
+                                       ctx->cfacptr.as<const double *>(), os.H, os.P,
+                                       ctx->sm_count, s, cp.fdr_hist, cp.fdr_bins, cp.fdr_l0,
+                                       cp.fdr_w));
   }
   ev_record(ctx, 6, s);
-  if (ctx->profiling) {
-    KRUX_CUDA(ctx, cudaStreamSynchronize(s));
-    ctx->prof.ms_finalize = ev_ms(ctx, 5, 6);
-  }
+  if (cp.perm.on)
+    KRUX_CUDA(ctx, launch_minp_from_key(ctx->minpkey.as<double>(), cp.perm.minp, cp.perm.P,
+                                        cp.perm.rs->T, cp.perm.rs->rows_pad, s));
   return KRUX_OK;
+}
+
+int fused_launches(const CallPlan &cp, const FusedLaunch &fl) {
+  int n = (fl.grid > 0 ? 1 : 0) + (fl.staged ? 1 : 0);
+  for (auto &g : cp.groups) n += g.nan_cnt ? 2 : 1;
+  for (auto &os : cp.slots) n += os.capacity > 0 ? 1 : 0;
+  if (cp.perm.on) n += 2 + (cp.perm.lists ? 2 : 0);
+  return n;
+}
+
+// Reads the status word back; KRUX_OK, or the device-side error.
+krux_status device_status(krux_ctx *ctx, const unsigned int *hst) {
+  if (hst[0] & kDevBadCode) return fail(ctx, KRUX_EINVAL, "genotype code outside {-1,0,1,2}");
+  if (hst[0] & kDevBadPerm) return fail(ctx, KRUX_EINVAL, "a permutation entry is outside 0..N-1");
+  if (hst[0] & kDevTimeout)
+    return fail(ctx, KRUX_ETIMEOUT, "device wait timed out (site %u)", hst[1]);
+  return KRUX_OK;
+}
+
+krux_status finish_fused(krux_ctx *ctx, CallPlan &cp, const FusedLaunch &fl, cudaStream_t s,
+                         std::vector<unsigned long long> &counts) {
+  const int nslots = fl.nslots;
+  counts.assign(nslots, 0);
+  unsigned int hst[2] = {0, 0};
+  if (!cp.groups.empty()) {
+    KRUX_CUDA(ctx, cudaMemcpyAsync(counts.data(), ctx->counters.as<unsigned long long>() + nslots,
+                                   (size_t)nslots * 8, cudaMemcpyDeviceToHost, s));
+    KRUX_CUDA(ctx, cudaMemcpyAsync(hst, ctx->status.p, 8, cudaMemcpyDeviceToHost, s));
+  }
+  KRUX_CUDA(ctx, cudaStreamSynchronize(s));
+  if (ctx->profiling && !cp.groups.empty()) {
+    ctx->prof.ms_pack = ev_ms(ctx, 2, 3);
+    ctx->prof.ms_scan = ev_ms(ctx, 7, 4);
+    ctx->prof.ms_finalize = ev_ms(ctx, 5, 6);
+    ctx->prof.scan_grid = fl.grid;
+    ctx->prof.launches += fused_launches(cp, fl);
+  }
+  return device_status(ctx, hst);
+}
+
+// Packs every group, launches the fused kernel once over all groups, finalises
+// every slot's hits in FP64 and reads the per-slot hit counts back.
+krux_status run_fused(krux_ctx *ctx, CallPlan &cp, const krux_opts *o, cudaStream_t s,
+                      std::vector<unsigned long long> &counts) {
+  FusedLaunch fl;
+  krux_status st = prepare_fused(ctx, cp, o, fl, s);
+  if (st != KRUX_OK) return st;
+  st = enqueue_fused(ctx, cp, fl, s);
+  if (st != KRUX_OK) return st;
+  return finish_fused(ctx, cp, fl, s, counts);
 }
 
 krux_status check_scan_args(krux_ctx *ctx, const krux_rankset *rs, const int8_t *geno, int64_t S,
@@ -1212,6 +1343,47 @@ extern "C" krux_status krux_scan_plain(krux_ctx *ctx, const krux_rankset *rs, co
   return KRUX_OK;
 }
 
+// Plans a permutation batch: the 1 + P stacked rank matrices as one group (the
+// stacking itself is queued by enqueue_fused).
+static krux_status plan_permute(krux_ctx *ctx, CallPlan &cp, const krux_rankset *rs, const int8_t *geno,
+                         int64_t S, int64_t ldg, const int32_t *perms, int P,
+                         const krux_opts *opts, double *minp, krux_hit *hits, double *hit_H,
+                         double *hit_p, uint64_t *fdr_hist, int fdr_bins, double fdr_bin_width,
+                         cudaStream_t s) {
+  const int64_t b = opts->snp_begin, e = opts->snp_end > 0 ? opts->snp_end : S;
+  const size_t one = (size_t)rs->rows_pad * rs->Np;
+  KRUX_CUDA(ctx, ctx->permA.ensure(one * 2 * (size_t)(1 + P)));
+  KRUX_CUDA(ctx, ctx->minpkey.ensure((size_t)P * rs->rows_pad * 8));
+  KRUX_CUDA(ctx, ctx->aux.ensure((size_t)std::max<int64_t>(opts->hit_capacity, 1) * sizeof(HitAux)));
+  cp.slots.push_back(OutSlot{hits, hit_H, hit_p, opts->hit_capacity, ctx->aux.as<HitAux>()});
+  cp.fdr_hist = reinterpret_cast<unsigned long long *>(fdr_hist);
+  cp.fdr_rows = 1 + P;
+  cp.fdr_bins = fdr_bins;
+  cp.fdr_l0 = -std::log10(opts->pthresh);
+  cp.fdr_w = fdr_bin_width;
+  cp.perm.on = true;
+  cp.perm.rs = rs;
+  cp.perm.perms = perms;
+  cp.perm.P = P;
+  cp.perm.stack = ctx->permA.as<__half>();
+  cp.perm.minp = minp;
+  krux_status st = plan_groups(ctx, cp, rs, geno, ldg, b, e, cp.perm.stack, 1 + P, 0, nullptr,
+                               nullptr, ctx->minpkey.as<double>(), s);
+  if (st != KRUX_OK) return st;
+  if (rs->has_nan) {
+    const size_t lst = (size_t)rs->T * rs->N;
+    const size_t inv_off = (lst * 2 * (size_t)(1 + P) + 255) / 256 * 256;
+    KRUX_CUDA(ctx, ctx->permNan.ensure(inv_off + (size_t)P * rs->N * 4));
+    cp.perm.lists = ctx->permNan.as<uint16_t>();
+    cp.perm.inv = reinterpret_cast<int32_t *>(ctx->permNan.as<char>() + inv_off);
+    for (auto &g : cp.groups) {
+      g.nan_idx = cp.perm.lists;
+      g.nan_ag_stride = (int64_t)lst;
+    }
+  }
+  return materialise(ctx, cp, s);
+}
+
 extern "C" krux_status krux_permute(krux_ctx *ctx, const krux_rankset *rs, const int8_t *geno,
                                     int64_t S, int64_t ldg, const int32_t *perms, int P,
                                     const krux_opts *opts, double *minp, krux_hit *hits,
@@ -1245,57 +1417,351 @@ extern "C" krux_status krux_permute(krux_ctx *ctx, const krux_rankset *rs, const
     ctx->prof = krux_profile{};
     ctx->prof.pairs = (int64_t)rs->T * (e - b) * (1 + P);
   }
-  const size_t one = (size_t)rs->rows_pad * rs->Np;
-  KRUX_CUDA(ctx, ctx->permA.ensure(one * 2 * (size_t)(1 + P)));
-  __half *stack = ctx->permA.as<__half>();
-  KRUX_CUDA(ctx, cudaMemcpyAsync(stack, rs->dev.A, one * 2, cudaMemcpyDeviceToDevice, s));
-  KRUX_CUDA(ctx, launch_permute_rows(rs->dev.A, stack + one, rs->rows_pad, rs->Np, N, perms, P, s));
-  KRUX_CUDA(ctx, ctx->minpkey.ensure((size_t)P * rs->rows_pad * 8));
-  KRUX_CUDA(ctx, cudaMemsetAsync(ctx->minpkey.p, 0, (size_t)P * rs->rows_pad * 8, s));
-  KRUX_CUDA(ctx, ctx->aux.ensure((size_t)std::max<int64_t>(opts->hit_capacity, 1) * sizeof(HitAux)));
-  if (fdr_hist)
-    KRUX_CUDA(ctx, cudaMemsetAsync(fdr_hist, 0, (size_t)(1 + P) * fdr_bins * 8, s));
   CallPlan cp;
-  cp.slots.push_back(OutSlot{hits, hit_H, hit_p, opts->hit_capacity, ctx->aux.as<HitAux>()});
-  cp.fdr_hist = reinterpret_cast<unsigned long long *>(fdr_hist);
-  cp.fdr_bins = fdr_bins;
-  cp.fdr_l0 = -std::log10(opts->pthresh);
-  cp.fdr_w = fdr_bin_width;
-  st = plan_groups(ctx, cp, rs, geno, ldg, b, e, stack, 1 + P, 0, nullptr, nullptr,
-                   ctx->minpkey.as<double>(), s);
-  if (st != KRUX_OK) return st;
-  if (rs->has_nan) {
-    // NaN samples of permutation q sit at inv_q(original position)
-    const size_t lst = (size_t)rs->T * N;
-    std::vector<int32_t> inv((size_t)P * N);
-    for (int q = 0; q < P; ++q)
-      for (int k = 0; k < N; ++k) inv[(size_t)q * N + hp[(size_t)q * N + k]] = k;
-    const size_t inv_off = (lst * 2 * (size_t)(1 + P) + 255) / 256 * 256;
-    KRUX_CUDA(ctx, ctx->permNan.ensure(inv_off + inv.size() * 4));
-    uint16_t *lists = ctx->permNan.as<uint16_t>();
-    int32_t *dinv = reinterpret_cast<int32_t *>(ctx->permNan.as<char>() + inv_off);
-    KRUX_CUDA(ctx, cudaMemcpyAsync(dinv, inv.data(), inv.size() * 4, cudaMemcpyHostToDevice, s));
-    KRUX_CUDA(ctx, cudaMemcpyAsync(lists, rs->dev.nan_idx, lst * 2, cudaMemcpyDeviceToDevice, s));
-    KRUX_CUDA(ctx, launch_permute_nan_idx(rs->dev.nan_cnt, rs->dev.nan_idx, rs->T, N, dinv, P,
-                                          lists + lst, s));
-    for (auto &g : cp.groups) {
-      g.nan_idx = lists;
-      g.nan_ag_stride = (int64_t)lst;
-    }
-    if (ctx->profiling) ctx->prof.launches += 1;
-  }
-  st = materialise(ctx, cp, s);
+  st = plan_permute(ctx, cp, rs, geno, S, ldg, perms, P, opts, minp, hits, hit_H, hit_p, fdr_hist,
+                    fdr_bins, fdr_bin_width, s);
   if (st != KRUX_OK) return st;
   std::vector<unsigned long long> counts;
   st = run_fused(ctx, cp, opts, s, counts);
   if (st != KRUX_OK) return st;
-  KRUX_CUDA(ctx, launch_minp_from_key(ctx->minpkey.as<double>(), minp, P, rs->T, rs->rows_pad, s));
-  KRUX_CUDA(ctx, cudaStreamSynchronize(s));
-  if (ctx->profiling) ctx->prof.launches += 2;
   *n_hits = (int64_t)counts[0];
   if (*n_hits > opts->hit_capacity)
     return fail(ctx, KRUX_EOVERFLOW, "%lld hits exceed capacity %lld", (long long)*n_hits,
                 (long long)opts->hit_capacity);
+  return KRUX_OK;
+}
+
+// ---------------------------------------------------------------------------
+// CUDA graphs: one call's stream work (permutation stacking, packing, the fused
+// scan, compaction, FP64 finalisation, min-p conversion) captured once and
+// replayed.  The graph owns a private workspace (its own context buffers), so
+// later calls on the caller's context cannot move memory the graph uses.
+struct krux_graph {
+  krux_ctx *w = nullptr;           // private workspace context
+  CallPlan cp;
+  FusedLaunch fl;
+  krux_opts opts{};
+  cudaStream_t cs = nullptr;       // capture stream
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  unsigned long long *host = nullptr;  // pinned: [nslots] totals, then 2 status words
+  cudaStream_t last = nullptr;     // stream of the last launch
+  bool launched = false;
+};
+
+namespace {
+
+krux_ctx *workspace_clone(const krux_ctx *src) {
+  krux_ctx *w = new krux_ctx();
+  w->device = src->device;
+  w->sm_count = src->sm_count;
+  w->cc_major = src->cc_major;
+  w->cc_minor = src->cc_minor;
+  w->wait_limit = src->wait_limit;
+  w->tune_layout = src->tune_layout;
+  w->tune_nc = src->tune_nc;
+  w->tune_nA = src->tune_nA;
+  w->tune_ka = src->tune_ka;
+  w->tuned = src->tuned;
+  w->encode = src->encode;
+  w->profiling = false;
+  return w;
+}
+
+void graph_free(krux_graph *g) {
+  if (!g) return;
+  if (g->w) cudaSetDevice(g->w->device);
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  if (g->cs) cudaStreamDestroy(g->cs);
+  if (g->host) cudaFreeHost(g->host);
+  if (g->w) krux_destroy(g->w);
+  delete g;
+}
+
+// Copies the workspace's error text to the caller's context and frees the graph.
+krux_status graph_fail(krux_ctx *ctx, krux_graph *g, krux_status st) {
+  if (g && g->w && !g->w->err.empty()) ctx->err = g->w->err;
+  graph_free(g);
+  return st;
+}
+
+// Prepares, then captures enqueue_fused plus the read-back of the counts into
+// pinned host memory.
+krux_status graph_capture(krux_ctx *ctx, krux_graph *g) {
+  krux_ctx *w = g->w;
+  if (!g->cp.bucket_jobs.empty() || !g->cp.lists.empty())
+    return fail(ctx, KRUX_EUNSUPPORTED, "graphs take complete genotypes (no -1 codes)");
+  krux_status st = prepare_fused(w, g->cp, &g->opts, g->fl, g->cs);
+  if (st != KRUX_OK) return st;
+  const int nslots = g->fl.nslots;
+  KRUX_CUDA(w, cudaHostAlloc(reinterpret_cast<void **>(&g->host), (size_t)(nslots + 1) * 8,
+                             cudaHostAllocDefault));
+  std::memset(g->host, 0, (size_t)(nslots + 1) * 8);
+  KRUX_CUDA(w, cudaStreamSynchronize(g->cs));
+  KRUX_CUDA(w, cudaStreamBeginCapture(g->cs, cudaStreamCaptureModeThreadLocal));
+  st = enqueue_fused(w, g->cp, g->fl, g->cs);
+  if (st == KRUX_OK && cudaMemcpyAsync(g->host, w->counters.as<unsigned long long>() + nslots,
+                                       (size_t)nslots * 8, cudaMemcpyDeviceToHost, g->cs) != cudaSuccess)
+    st = fail(w, KRUX_ECUDA, "capture of the count read-back failed");
+  if (st == KRUX_OK && cudaMemcpyAsync(g->host + nslots, w->status.p, 8, cudaMemcpyDeviceToHost,
+                                       g->cs) != cudaSuccess)
+    st = fail(w, KRUX_ECUDA, "capture of the status read-back failed");
+  cudaGraph_t graph = nullptr;
+  const cudaError_t ec = cudaStreamEndCapture(g->cs, &graph);
+  if (st != KRUX_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+  }
+  if (ec != cudaSuccess)
+    return fail(w, KRUX_ECUDA, "cudaStreamEndCapture: %s", cudaGetErrorString(ec));
+  g->graph = graph;
+  KRUX_CUDA(w, cudaGraphInstantiate(&g->exec, g->graph, 0));
+  return KRUX_OK;
+}
+
+krux_status graph_begin(krux_ctx *ctx, krux_graph **out, krux_graph *&g) {
+  *out = nullptr;
+  KRUX_CUDA(ctx, cudaSetDevice(ctx->device));
+  g = new krux_graph();
+  g->w = workspace_clone(ctx);
+  if (cudaStreamCreateWithFlags(&g->cs, cudaStreamNonBlocking) != cudaSuccess) {
+    graph_free(g);
+    g = nullptr;
+    return fail(ctx, KRUX_ECUDA, "cudaStreamCreateWithFlags failed");
+  }
+  return KRUX_OK;
+}
+
+}  // namespace
+
+extern "C" krux_status krux_graph_scan(krux_ctx *ctx, const krux_rankset *rs, const int8_t *geno,
+                                       int64_t S, int64_t ldg, const krux_opts *opts,
+                                       krux_hit *hits, double *hit_H, double *hit_p,
+                                       krux_graph **out) {
+  if (!out) return KRUX_EINVAL;
+  int64_t dummy = 0;
+  krux_status st = check_scan_args(ctx, rs, geno, S, ldg, opts, hits, hit_H, hit_p, &dummy);
+  if (st != KRUX_OK) return st;
+  krux_graph *g = nullptr;
+  st = graph_begin(ctx, out, g);
+  if (st != KRUX_OK) return st;
+  g->opts = *opts;
+  krux_ctx *w = g->w;
+  const int64_t b = opts->snp_begin, e = opts->snp_end > 0 ? opts->snp_end : S;
+  if (w->aux.ensure((size_t)std::max<int64_t>(opts->hit_capacity, 1) * sizeof(HitAux)) != cudaSuccess)
+    return graph_fail(ctx, g, fail(ctx, KRUX_ENOMEM, "graph workspace"));
+  g->cp.slots.push_back(OutSlot{hits, hit_H, hit_p, opts->hit_capacity, w->aux.as<HitAux>()});
+  st = plan_groups(w, g->cp, rs, geno, ldg, b, e, nullptr, 1, 0, opts->dense_H, opts->dense_p,
+                   nullptr, g->cs);
+  if (st == KRUX_OK) st = materialise(w, g->cp, g->cs);
+  if (st == KRUX_OK) st = graph_capture(ctx, g);
+  if (st != KRUX_OK) return graph_fail(ctx, g, st);
+  *out = g;
+  return KRUX_OK;
+}
+
+extern "C" krux_status krux_graph_permute(krux_ctx *ctx, const krux_rankset *rs,
+                                          const int8_t *geno, int64_t S, int64_t ldg,
+                                          const int32_t *perms, int P, const krux_opts *opts,
+                                          double *minp, krux_hit *hits, double *hit_H,
+                                          double *hit_p, uint64_t *fdr_hist, int fdr_bins,
+                                          double fdr_bin_width, krux_graph **out) {
+  if (!out) return KRUX_EINVAL;
+  int64_t dummy = 0;
+  krux_status st = check_scan_args(ctx, rs, geno, S, ldg, opts, hits, hit_H, hit_p, &dummy);
+  if (st != KRUX_OK) return st;
+  if (P < 1 || !perms || !minp) return fail(ctx, KRUX_EINVAL, "need P >= 1, perms and minp");
+  if (opts->dense_H) return fail(ctx, KRUX_EINVAL, "dense output is not available with permutations");
+  if (fdr_hist && (fdr_bins < 1 || !(fdr_bin_width > 0.0)))
+    return fail(ctx, KRUX_EINVAL, "FDR histogram needs fdr_bins >= 1 and fdr_bin_width > 0");
+  krux_graph *g = nullptr;
+  st = graph_begin(ctx, out, g);
+  if (st != KRUX_OK) return st;
+  g->opts = *opts;
+  st = plan_permute(g->w, g->cp, rs, geno, S, ldg, perms, P, opts, minp, hits, hit_H, hit_p,
+                    fdr_hist, fdr_bins, fdr_bin_width, g->cs);
+  if (st == KRUX_OK) st = graph_capture(ctx, g);
+  if (st != KRUX_OK) return graph_fail(ctx, g, st);
+  *out = g;
+  return KRUX_OK;
+}
+
+extern "C" krux_status krux_graph_grouped(krux_ctx *ctx, const krux_cohort *cohorts, int n_cohorts,
+                                          const krux_opts *opts, krux_graph **out) {
+  if (!ctx || !out) return KRUX_EINVAL;
+  krux_status st = check_opts(ctx, opts);
+  if (st != KRUX_OK) return st;
+  if (n_cohorts < 1 || !cohorts) return fail(ctx, KRUX_EINVAL, "bad cohort list");
+  if (opts->dense_H) return fail(ctx, KRUX_EINVAL, "dense output is not available for grouped scans");
+  int64_t captot = 0;
+  for (int c = 0; c < n_cohorts; ++c) {
+    const krux_cohort &k = cohorts[c];
+    if (!k.rs || k.S < 0 || (k.S > 0 && (!k.geno || k.ldg < k.rs->N)) || k.hit_capacity < 0 ||
+        (k.hit_capacity > 0 && (!k.hits || !k.hit_H || !k.hit_p)) || ((uintptr_t)k.hits & 15u) != 0)
+      return fail(ctx, KRUX_EINVAL, "cohort %d: bad arguments", c);
+    captot += std::max<int64_t>(k.hit_capacity, 1);
+  }
+  krux_graph *g = nullptr;
+  st = graph_begin(ctx, out, g);
+  if (st != KRUX_OK) return st;
+  g->opts = *opts;
+  krux_ctx *w = g->w;
+  if (w->aux.ensure((size_t)std::max<int64_t>(captot, 1) * sizeof(HitAux)) != cudaSuccess)
+    return graph_fail(ctx, g, fail(ctx, KRUX_ENOMEM, "graph workspace"));
+  int64_t aoff = 0;
+  for (int c = 0; c < n_cohorts && st == KRUX_OK; ++c) {
+    const krux_cohort &k = cohorts[c];
+    g->cp.slots.push_back(
+        OutSlot{k.hits, k.hit_H, k.hit_p, k.hit_capacity, w->aux.as<HitAux>() + aoff});
+    aoff += std::max<int64_t>(k.hit_capacity, 1);
+    st = plan_groups(w, g->cp, k.rs, k.geno, k.ldg, 0, k.S, nullptr, 1, c, nullptr, nullptr,
+                     nullptr, g->cs);
+  }
+  if (st == KRUX_OK) st = materialise(w, g->cp, g->cs);
+  if (st == KRUX_OK) st = graph_capture(ctx, g);
+  if (st != KRUX_OK) return graph_fail(ctx, g, st);
+  *out = g;
+  return KRUX_OK;
+}
+
+extern "C" krux_status krux_graph_launch(krux_graph *g, void *stream) {
+  if (!g || !g->exec) return KRUX_EINVAL;
+  if (cudaSetDevice(g->w->device) != cudaSuccess) return KRUX_ECUDA;
+  const cudaError_t e = cudaGraphLaunch(g->exec, (cudaStream_t)stream);
+  if (e != cudaSuccess) return fail(g->w, KRUX_ECUDA, "cudaGraphLaunch: %s", cudaGetErrorString(e));
+  g->last = (cudaStream_t)stream;
+  g->launched = true;
+  return KRUX_OK;
+}
+
+extern "C" krux_status krux_graph_wait(krux_graph *g, int64_t *n_hits, int n_lists) {
+  if (!g || !g->launched) return KRUX_EINVAL;
+  const int nslots = g->fl.nslots;
+  if (n_lists < nslots || (nslots > 0 && !n_hits)) return KRUX_EINVAL;
+  if (cudaSetDevice(g->w->device) != cudaSuccess) return KRUX_ECUDA;
+  const cudaError_t e = cudaStreamSynchronize(g->last);
+  if (e != cudaSuccess) return fail(g->w, KRUX_ECUDA, "%s", cudaGetErrorString(e));
+  unsigned int hst[2];
+  std::memcpy(hst, g->host + nslots, 8);
+  bool over = false;
+  for (int k = 0; k < nslots; ++k) {
+    n_hits[k] = (int64_t)g->host[k];
+    over |= n_hits[k] > g->cp.slots[k].capacity;
+  }
+  const krux_status st = device_status(g->w, hst);
+  if (st != KRUX_OK) return st;
+  if (hst[0] & kDevMissing)
+    return fail(g->w, KRUX_EUNSUPPORTED, "a -1 genotype code appeared in a graph replay");
+  if (over) return fail(g->w, KRUX_EOVERFLOW, "hits exceed a list's capacity");
+  return KRUX_OK;
+}
+
+extern "C" const char *krux_graph_last_error(const krux_graph *g) {
+  return g && g->w ? g->w->err.c_str() : "";
+}
+
+extern "C" void krux_graph_destroy(krux_graph *g) { graph_free(g); }
+
+// ---------------------------------------------------------------------------
+// Autotuner: times the fused scan of this rank set over a sample of the SNPs
+// (the first 65,536) for every launch shape that fits, and keeps the fastest for
+// the rank set's K width; later launches of that width use it unless a shape is
+// set explicitly with krux_set_tuning.
+extern "C" krux_status krux_autotune(krux_ctx *ctx, const krux_rankset *rs, const int8_t *geno,
+                                     int64_t S, int64_t ldg, double pthresh, void *stream,
+                                     int32_t *shape_out) {
+  if (!ctx) return KRUX_EINVAL;
+  if (!rs || !geno || S < 1 || ldg < rs->N || !(pthresh > 0.0 && pthresh < 1.0))
+    return fail(ctx, KRUX_EINVAL, "autotune needs a rank set, genotypes and 0 < P_c < 1");
+  KRUX_CUDA(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t n = std::min<int64_t>(S, 65536);
+  const int64_t cap = 1 << 20;
+  DevBuf out;
+  KRUX_CUDA(ctx, out.ensure((size_t)cap * (sizeof(krux_hit) + 16)));
+  krux_hit *hits = out.as<krux_hit>();
+  double *H = reinterpret_cast<double *>(out.as<char>() + (size_t)cap * sizeof(krux_hit));
+  double *P = H + cap;
+  krux_opts o{};
+  o.pthresh = pthresh;
+  o.hit_capacity = cap;
+  o.snp_end = n;
+  struct Cand { int layout, nc, nA, ka; };
+  std::vector<Cand> cands = {{-1, 0, 0, 0}};
+  for (int layout : {1, 0})
+    for (int nc : {4, 3, 2, 1})
+      for (int nA : {2, 3, 4})
+        for (int ka : {0, 64}) cands.push_back(Cand{layout, nc, nA, ka});
+  const int s_layout = ctx->tune_layout, s_nc = ctx->tune_nc, s_nA = ctx->tune_nA,
+            s_ka = ctx->tune_ka;
+  const bool s_prof = ctx->profiling;
+  const auto saved_tuned = ctx->tuned;
+  ctx->tuned.erase(rs->Np);
+  ctx->profiling = false;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best_ms = 0.f;
+  Cand best{-1, 0, 0, 0};
+  bool any = false;
+  krux_status result = KRUX_OK;
+  for (const Cand &c : cands) {
+    ctx->tune_layout = c.layout;
+    ctx->tune_nc = c.nc;
+    ctx->tune_nA = c.nA;
+    ctx->tune_ka = c.ka;
+    float ms = 0.f;
+    bool ok = true;
+    for (int rep = 0; rep < 3 && ok; ++rep) {
+      int64_t nh = 0;
+      cudaEventRecord(e0, s);
+      const krux_status st = krux_scan(ctx, rs, geno, S, ldg, &o, hits, H, P, &nh, stream);
+      cudaEventRecord(e1, s);
+      if (st == KRUX_ECUDA || st == KRUX_ETIMEOUT) {
+        result = st;  // a real failure: stop tuning
+        ok = false;
+        break;
+      }
+      if (st != KRUX_OK && st != KRUX_EOVERFLOW) {
+        ok = false;  // this shape does not fit
+        break;
+      }
+      cudaEventSynchronize(e1);
+      float t = 0.f;
+      cudaEventElapsedTime(&t, e0, e1);
+      if (rep == 1 || (rep == 2 && t < ms)) ms = t;  // best of the two timed runs
+    }
+    if (result != KRUX_OK) break;
+    if (ok && (!any || ms < best_ms)) {
+      any = true;
+      best_ms = ms;
+      best = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->tune_layout = s_layout;
+  ctx->tune_nc = s_nc;
+  ctx->tune_nA = s_nA;
+  ctx->tune_ka = s_ka;
+  ctx->profiling = s_prof;
+  out.release();
+  if (result != KRUX_OK) {
+    ctx->tuned = saved_tuned;
+    return result;
+  }
+  if (!any) {
+    ctx->tuned = saved_tuned;
+    return fail(ctx, KRUX_EUNSUPPORTED, "no launch shape ran");
+  }
+  ctx->tuned[rs->Np] = {best.layout, best.nc, best.nA, best.ka};
+  if (shape_out) {
+    shape_out[0] = best.layout;
+    shape_out[1] = best.nc;
+    shape_out[2] = best.nA;
+    shape_out[3] = best.ka;
+  }
   return KRUX_OK;
 }
 

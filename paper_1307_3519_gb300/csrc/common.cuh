@@ -166,6 +166,8 @@ struct ScanParams {
 enum : unsigned int {
   kDevTimeout = 1u,
   kDevBadCode = 2u,
+  kDevBadPerm = 4u,     // a permutation entry outside 0..N-1 (its row is gathered as zeros)
+  kDevMissing = 8u,     // a -1 code in a group packed as complete (graph replays)
 };
 
 // ---- launch wrappers (defined in the .cu files) -----------------------------
@@ -175,8 +177,11 @@ cudaError_t launch_rank(const float *expr, int T, int N, int64_t ld, int Np, int
 // for j < nan_cnt[t] (sample k of permutation q takes the value of sample perm[q][k]).
 cudaError_t launch_permute_nan_idx(const uint16_t *nan_cnt, const uint16_t *nan_idx, int T, int N,
                                    const int32_t *inv, int P, uint16_t *out, cudaStream_t s);
+// inv[q][perms[q][k]] = k for every in-range entry.
+cudaError_t launch_invert_perms(const int32_t *perms, int P, int N, int32_t *inv, cudaStream_t s);
+// status (may be null) gets kDevBadPerm for an entry outside 0..N-1.
 cudaError_t launch_permute_rows(const __half *A, __half *out, int rows_pad, int Np, int N,
-                                const int32_t *perms, int P, cudaStream_t s);
+                                const int32_t *perms, int P, unsigned int *status, cudaStream_t s);
 cudaError_t launch_scan(const ScanParams &p, int grid, size_t smem, cudaStream_t s);
 size_t scan_smem_bytes(int nc, int nA, int kpad);
 size_t scan_smem_bytes2(int nc, int nA, size_t a_tile_bytes, size_t b_region, int codes_k);
@@ -188,6 +193,17 @@ cudaError_t launch_minp_from_key(const double *key, double *minp, int P, int T, 
                                  cudaStream_t s);
 cudaError_t launch_pad_traits(int T, int rows_pad, float *tau, double *cfac, uint16_t *nan_cnt,
                               cudaStream_t s);
+// Uploads the 1/n table the finalisation uses (once per device; not during a
+// graph capture).
+cudaError_t finalize_prepare();
+// Finalisation of min(*count, capacity) hits, the count read on the device.
+cudaError_t launch_finalize_dev(const krux_hit *hits, const HitAux *aux,
+                                const unsigned long long *count, int64_t capacity,
+                                const double *const *cfac_by_group, double *H, double *p,
+                                int sm_count, cudaStream_t s, unsigned long long *fdr_hist,
+                                int fdr_bins, double fdr_l0, double fdr_w);
+cudaError_t scan_set_smem(size_t smem);
+cudaError_t launch_scan_only(const ScanParams &p, int grid, size_t smem, cudaStream_t s);
 cudaError_t launch_finalize(const krux_hit *hits, const HitAux *aux, int64_t n,
                             const double *const *cfac_by_group, double *H, double *p,
                             cudaStream_t s, unsigned long long *fdr_hist = nullptr, int fdr_bins = 0,

@@ -109,6 +109,7 @@ pack_kernel(const int8_t *__restrict__ geno, int64_t ldg, int N, int Np,
   bad = __any_sync(0xffffffffu, bad);
   if (lane == 0) {
     if (bad) atomicOr(status, kDevBadCode);
+    if (miss && !allow_missing) atomicOr(status, kDevMissing);
     const int groups = (n0 > 0) + (n1 > 0) + (n2 > 0);
     const int df = groups > 0 ? groups - 1 : 0;
     float al = 0.f, be = 0.f, ga = 0.f;

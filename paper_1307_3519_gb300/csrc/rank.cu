@@ -93,7 +93,7 @@ rank_kernel(const float *__restrict__ expr, int T, int N, int64_t ld, int Np, Ra
 // sums and K are invariant under a column permutation).
 __global__ void permute_rows_kernel(const __half *__restrict__ A, __half *__restrict__ out,
                                     int rows_pad, int Np, int N, const int32_t *__restrict__ perms,
-                                    int P) {
+                                    int P, unsigned int *status) {
   const int64_t total = (int64_t)P * rows_pad * Np;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -102,10 +102,29 @@ __global__ void permute_rows_kernel(const __half *__restrict__ A, __half *__rest
     const int row = (int)(pr % rows_pad);
     const int p = (int)(pr / rows_pad);
     __half v = __int2half_rn(0);
-    if (k < N) v = A[(int64_t)row * Np + perms[(int64_t)p * N + k]];
+    if (k < N) {
+      const int32_t src = perms[(int64_t)p * N + k];
+      if (src >= 0 && src < N)
+        v = A[(int64_t)row * Np + src];
+      else if (status != nullptr)
+        atomicOr(status, kDevBadPerm);
+    }
     out[i] = v;
   }
 }
+// inv[q][perms[q][k]] = k (entries outside 0..N-1 are skipped; the row gather
+// reports them).
+__global__ void invert_perms_kernel(const int32_t *__restrict__ perms, int P, int N,
+                                    int32_t *__restrict__ inv) {
+  const int64_t total = (int64_t)P * N;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int q = (int)(i / N), k = (int)(i % N);
+    const int32_t v = perms[i];
+    if (v >= 0 && v < N) inv[(int64_t)q * N + v] = k;
+  }
+}
+
 __global__ void permute_nan_idx_kernel(const uint16_t *__restrict__ nan_cnt,
                                        const uint16_t *__restrict__ nan_idx, int T, int N,
                                        const int32_t *__restrict__ inv, int P,
@@ -148,6 +167,15 @@ cudaError_t launch_rank(const float *expr, int T, int N, int64_t ld, int Np, int
   return launch_pad_traits(T, rows_pad, r.tau, r.cfac, r.nan_cnt, s);
 }
 
+cudaError_t launch_invert_perms(const int32_t *perms, int P, int N, int32_t *inv, cudaStream_t s) {
+  const int64_t total = (int64_t)P * N;
+  if (total == 0) return cudaSuccess;
+  int grid = (int)((total + 255) / 256);
+  if (grid > 152 * 4) grid = 152 * 4;
+  invert_perms_kernel<<<grid, 256, 0, s>>>(perms, P, N, inv);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_permute_nan_idx(const uint16_t *nan_cnt, const uint16_t *nan_idx, int T, int N,
                                    const int32_t *inv, int P, uint16_t *out, cudaStream_t s) {
   const int64_t total = (int64_t)P * T * N;
@@ -159,11 +187,11 @@ cudaError_t launch_permute_nan_idx(const uint16_t *nan_cnt, const uint16_t *nan_
 }
 
 cudaError_t launch_permute_rows(const __half *A, __half *out, int rows_pad, int Np, int N,
-                                const int32_t *perms, int P, cudaStream_t s) {
+                                const int32_t *perms, int P, unsigned int *status, cudaStream_t s) {
   const int64_t total = (int64_t)P * rows_pad * Np;
   int grid = (int)((total + 255) / 256);
   if (grid > 152 * 16) grid = 152 * 16;
-  permute_rows_kernel<<<grid, 256, 0, s>>>(A, out, rows_pad, Np, N, perms, P);
+  permute_rows_kernel<<<grid, 256, 0, s>>>(A, out, rows_pad, Np, N, perms, P, status);
   return cudaGetLastError();
 }
 

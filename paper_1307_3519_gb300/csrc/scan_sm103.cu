@@ -1058,27 +1058,51 @@ __global__ void seg_compact_kernel(const krux_hit *__restrict__ seg_hits,
 __constant__ double c_rcp[kMaxN + 1];
 
 // FP64 statistic and p-value of each stored hit, from its exact centred sums.
+__device__ __forceinline__ void finalize_one(const krux_hit *__restrict__ hits,
+                                             const HitAux *__restrict__ aux, int64_t i,
+                                             const double *const *__restrict__ cfac_by_group,
+                                             double *__restrict__ H, double *__restrict__ P,
+                                             unsigned long long *fdr_hist, int fdr_bins,
+                                             double fdr_l0, double fdr_w) {
+  const krux_hit r = ld_hit(hits + i);
+  const HitAux a = ld_aux(aux + i);
+  const double cf = cfac_by_group[a.group][r.trait];
+  const int df = df_of(a.n0, a.n1, a.n2);
+  const double D0 = (double)r.d0, D1 = (double)r.d1, D2 = -(double)(r.d0 + r.d1);
+  double Q = D0 * D0 * c_rcp[a.n0];
+  Q = fma(D1 * D1, c_rcp[a.n1], Q);
+  Q = fma(D2 * D2, c_rcp[a.n2], Q);
+  const double h = cf * Q;
+  H[i] = h;
+  P[i] = kw_p64(h, df);
+  if (fdr_hist != nullptr)  // row 0: the real data's hits by -log10 p bin
+    atomicAdd(fdr_hist + fdr_bin(key64_of(h, df), fdr_l0, fdr_w, fdr_bins), 1ull);
+}
+
 __global__ void finalize_kernel(const krux_hit *__restrict__ hits, const HitAux *__restrict__ aux,
                                 int64_t n, const double *const *__restrict__ cfac_by_group,
                                 double *__restrict__ H, double *__restrict__ P,
                                 unsigned long long *fdr_hist, int fdr_bins, double fdr_l0,
                                 double fdr_w) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const krux_hit r = ld_hit(hits + i);
-    const HitAux a = ld_aux(aux + i);
-    const double cf = cfac_by_group[a.group][r.trait];
-    const int df = df_of(a.n0, a.n1, a.n2);
-    const double D0 = (double)r.d0, D1 = (double)r.d1, D2 = -(double)(r.d0 + r.d1);
-    double Q = D0 * D0 * c_rcp[a.n0];
-    Q = fma(D1 * D1, c_rcp[a.n1], Q);
-    Q = fma(D2 * D2, c_rcp[a.n2], Q);
-    const double h = cf * Q;
-    H[i] = h;
-    P[i] = kw_p64(h, df);
-    if (fdr_hist != nullptr)  // row 0: the real data's hits by -log10 p bin
-      atomicAdd(fdr_hist + fdr_bin(key64_of(h, df), fdr_l0, fdr_w, fdr_bins), 1ull);
-  }
+       i += (int64_t)gridDim.x * blockDim.x)
+    finalize_one(hits, aux, i, cfac_by_group, H, P, fdr_hist, fdr_bins, fdr_l0, fdr_w);
+}
+
+// The same over min(*count, capacity) hits, the count read on the device (no host
+// round trip between the scan and the finalisation; capturable in a graph).
+__global__ void finalize_dev_kernel(const krux_hit *__restrict__ hits,
+                                    const HitAux *__restrict__ aux,
+                                    const unsigned long long *__restrict__ count, int64_t capacity,
+                                    const double *const *__restrict__ cfac_by_group,
+                                    double *__restrict__ H, double *__restrict__ P,
+                                    unsigned long long *fdr_hist, int fdr_bins, double fdr_l0,
+                                    double fdr_w) {
+  const unsigned long long c = *count;
+  const int64_t n = c < (unsigned long long)capacity ? (int64_t)c : capacity;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    finalize_one(hits, aux, i, cfac_by_group, H, P, fdr_hist, fdr_bins, fdr_l0, fdr_w);
 }
 
 // minimum p of each (permutation, trait) from its best -ln p (key rows of ld entries)
@@ -1122,12 +1146,35 @@ size_t scan_smem_bytes2(int nc, int nA, size_t a_tile_bytes, size_t b_region, in
          8 * (size_t)(2 * nA + 2 * nc + 2 * kTmemSlots + 1 + 2 * kTcDepth) + 16;
 }
 
-cudaError_t launch_scan(const ScanParams &p, int grid, size_t smem, cudaStream_t s) {
-  cudaError_t e = cudaFuncSetAttribute(krux_scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
-  if (e != cudaSuccess) return e;
+cudaError_t scan_set_smem(size_t smem) {
+  return cudaFuncSetAttribute(krux_scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)smem);
+}
+
+cudaError_t launch_scan_only(const ScanParams &p, int grid, size_t smem, cudaStream_t s) {
   krux_scan_kernel<<<grid, kScanThreads, smem, s>>>(p);
   return cudaGetLastError();
+}
+
+cudaError_t launch_scan(const ScanParams &p, int grid, size_t smem, cudaStream_t s) {
+  cudaError_t e = scan_set_smem(smem);
+  if (e != cudaSuccess) return e;
+  return launch_scan_only(p, grid, smem, s);
+}
+
+cudaError_t finalize_prepare() {
+  static unsigned long long uploaded = 0;  // bit d: the table is on device d
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 64 && ((uploaded >> dev) & 1ull)) return cudaSuccess;
+  double t[kMaxN + 1];
+  t[0] = 0.0;  // empty groups have D_i = 0 and contribute nothing
+  for (int k = 1; k <= kMaxN; ++k) t[k] = 1.0 / (double)k;
+  e = cudaMemcpyToSymbol(c_rcp, t, sizeof t);
+  if (e != cudaSuccess) return e;
+  if (dev < 64) uploaded |= 1ull << dev;
+  return cudaSuccess;
 }
 
 cudaError_t launch_finalize(const krux_hit *hits, const HitAux *aux, int64_t n,
@@ -1135,21 +1182,26 @@ cudaError_t launch_finalize(const krux_hit *hits, const HitAux *aux, int64_t n,
                             cudaStream_t s, unsigned long long *fdr_hist, int fdr_bins,
                             double fdr_l0, double fdr_w) {
   if (n <= 0) return cudaSuccess;
-  static int table_device = -1;  // the table is uploaded once per device
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (table_device != dev) {
-    double t[kMaxN + 1];
-    t[0] = 0.0;  // empty groups have D_i = 0 and contribute nothing
-    for (int k = 1; k <= kMaxN; ++k) t[k] = 1.0 / (double)k;
-    cudaError_t e = cudaMemcpyToSymbol(c_rcp, t, sizeof t);
-    if (e != cudaSuccess) return e;
-    table_device = dev;
-  }
+  cudaError_t e = finalize_prepare();
+  if (e != cudaSuccess) return e;
   int grid = (int)((n + 255) / 256);
   if (grid > 152 * 8) grid = 152 * 8;
   finalize_kernel<<<grid, 256, 0, s>>>(hits, aux, n, cfac_by_group, H, p, fdr_hist, fdr_bins, fdr_l0,
                                        fdr_w);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finalize_dev(const krux_hit *hits, const HitAux *aux,
+                                const unsigned long long *count, int64_t capacity,
+                                const double *const *cfac_by_group, double *H, double *p,
+                                int sm_count, cudaStream_t s, unsigned long long *fdr_hist,
+                                int fdr_bins, double fdr_l0, double fdr_w) {
+  if (capacity <= 0) return cudaSuccess;
+  int grid = sm_count * 4;
+  const int64_t need = (capacity + 255) / 256;
+  if (need < grid) grid = (int)need;
+  finalize_dev_kernel<<<grid, 256, 0, s>>>(hits, aux, count, capacity, cfac_by_group, H, p,
+                                           fdr_hist, fdr_bins, fdr_l0, fdr_w);
   return cudaGetLastError();
 }
 

@@ -86,3 +86,19 @@ def test_every_launch_plan_is_sound(lib):
                                    (0, 2, 3, 64), (1, 1, 4, 64), (1, 4, 3, 64)]:
             st, plan = k.krux_debug_plan(N, False, layout, nc, nA, ka)
             assert st in (0, 6)  # sound, or refused (never an unchecked plan)
+
+
+def test_every_autotune_candidate_is_sound_or_refused(lib):
+    """The shapes krux_autotune tries: each one either passes the plan check or
+    is refused before any launch."""
+    import paper_1307_3519_gb300 as k
+    for N in (16, 48, 60, 75, 102, 150, 200, 256, 300, 400, 500, 512):
+        for nan in (False, True):
+            for layout in (1, 0):
+                for nc in (4, 3, 2, 1):
+                    for nA in (2, 3, 4):
+                        for ka in (0, 64):
+                            st, plan = k.krux_debug_plan(N, nan, layout, nc, nA, ka)
+                            assert st in (0, 1, 6), (N, nan, layout, nc, nA, ka, st)
+                            if st == 0:
+                                assert plan["smem"] <= 232448 and plan["b_region"] % 1024 == 0
