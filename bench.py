@@ -223,6 +223,9 @@ def run_fused(args):
     H = torch.empty(cap, dtype=torch.float64, device=dev)
     P = torch.empty(cap, dtype=torch.float64, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    # launch shape: the autotuner's choice for this width, timed on this workload's SNPs
+    rs_tune = kx.krux_rank(expr)
+    tile_shape = kx.autotune(rs_tune, geno, pth)
     kx.set_profiling(True)
 
     import ctypes
@@ -276,6 +279,28 @@ def run_fused(args):
     ptimes, pscan, _, pprofs, pn = timed(lib.krux_scan_plain, psteps, 1)
     pvalue = pairs * psteps / (sum(ptimes) / 1e3)
 
+    # the same scan as a CUDA-graph replay (packing, scan, compaction, finalisation;
+    # the ranks of the step before stay in place)
+    graph = kx.graph_scan(rs_tune, geno, pth, cap)
+    for _ in range(args.warmup):
+        graph.launch(stream)
+    graph.wait()
+    gtimes = []
+    gev0, gev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    gsteps = max(1, min(args.steps, 10))
+    for _ in range(gsteps):
+        flush.zero_()
+        gev0.record(stream)
+        graph.launch(stream)
+        gev1.record(stream)
+        gev1.synchronize()
+        gtimes.append(gev0.elapsed_time(gev1))
+    g_hits = graph.wait()[0]["n_hits"]
+    graph.close()
+    graph_line = {"value": pairs / (float(np.mean(gtimes)) / 1e3), "unit": "pairs/s",
+                  "ms_per_step": float(np.mean(gtimes)), "steps": gsteps, "hits": g_hits,
+                  "what": "pack + fused scan + compaction + FP64 finalisation, one graph replay"}
+
     pk, pk_kind = peaks()
     flops = 4.0 * N * pairs  # algorithmic: two indicator columns x N samples x multiply-add
     ms_scan = float(np.mean(scan_ms))
@@ -322,9 +347,11 @@ def run_fused(args):
                 "data": "synthetic",
                 "config": {"workload": WORKLOAD, "T": T, "S": S, "N": N, "pthresh": pth,
                            "hit_capacity": cap, "l2": "flushed (256 MB write) between steps",
+                           "tile_shape": dict(zip(("layout", "nc", "nA", "ka"), tile_shape)),
                            "parallelism": f"snp-shards x{world}"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": c, "hits": n_hits,
+                "graph": graph_line,
                 "plain": {"value": pvalue, "unit": "pairs/s", "ms_per_step": float(np.mean(ptimes)),
                           "steps": psteps, "fused_speedup": value / world / pvalue, "hits": pn},
                 "breakdown_ms": {k2: float(np.mean([p[1][k2] for p in profs]))
@@ -347,6 +374,7 @@ def run_scan_only(args):
     import paper_1307_3519_gb300 as k
     import synth
     T, S = args.traits, args.snps
+    # the autotuner runs first (as in the benchmark) unless --no-autotune
     if args.data == "paper":
         d = synth.config(2, T=T, S=S)
         geno, expr, pth = d["geno"], d["expr"], d["pthresh"]
@@ -356,9 +384,11 @@ def run_scan_only(args):
         expr = synth.expression_lognormal(rng, T, 102)
         pth = 1e-5
     kx = k.Krux(0)
-    kx.set_profiling(True)
     rs = kx.krux_rank(torch.from_numpy(expr).cuda())
     g = torch.from_numpy(geno).cuda()
+    if not args.no_autotune:  # the launch shape the benchmark uses
+        print(f"scan-only autotuned shape (layout, nc, nA, ka) = {kx.autotune(rs, g, pth)}", flush=True)
+    kx.set_profiling(True)
     for i in range(args.reps):
         r = kx.krux_scan(rs, g, pth, capacity=min(50_000_000, T * S))
         pr = kx.profile()
@@ -382,6 +412,8 @@ def main():
     ap.add_argument("--snps", type=int, default=100000)
     ap.add_argument("--data", default="hwe", choices=["hwe", "paper"])
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="scan-only: the automatic launch shape instead of the autotuner's")
     args = ap.parse_args()
     if args.scan_only:
         run_scan_only(args)
