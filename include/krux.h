@@ -149,6 +149,22 @@ krux_status krux_permute(krux_ctx *ctx, const krux_rankset *rs, const int8_t *ge
                          int64_t *n_hits, uint64_t *fdr_hist, int fdr_bins,
                          double fdr_bin_width, void *stream);
 
+/* cis scan (the paper's cis-eQTL analysis keeps marker-trait pairs within 1 Mbp
+ * of each other): as krux_scan, but only pairs with
+ * |snp_pos[snp] - trait_pos[trait]| <= window are tested and reported, and the
+ * work is pruned to them: every SNP tile meets only the trait tiles its window
+ * reaches.
+ *   snp_pos   : device int64 [S], a global coordinate per SNP row (for several
+ *               chromosomes, e.g. chromosome * 2^40 + base position), nondecreasing;
+ *   trait_pos : device int64 [T], the coordinate of each trait's gene, same scale,
+ *               nondecreasing (sort the traits before ranking);
+ *   window    : >= 0, same units.
+ * Unsorted coordinates, window < 0 or dense output -> KRUX_EINVAL. */
+krux_status krux_scan_cis(krux_ctx *ctx, const krux_rankset *rs, const int8_t *geno, int64_t S,
+                          int64_t ldg, const int64_t *snp_pos, const int64_t *trait_pos,
+                          int64_t window, const krux_opts *opts, krux_hit *hits, double *hit_H,
+                          double *hit_p, int64_t *n_hits, void *stream);
+
 /* One cohort of a grouped scan: its own rank set (any N <= 512), genotypes and
  * hit outputs; n_hits is written by krux_scan_grouped. */
 typedef struct {

@@ -185,3 +185,14 @@ def fdr(expr, geno, perms, pthresh, thresholds, snps=None):
     p_real = scan(expr, geno, pthresh, snps=snps)["p"]
     p_perm = [scan(expr, geno, pthresh, snps=snps, perm=perms[q])["p"] for q in range(len(perms))]
     return fdr_from_pvalues(p_real, p_perm, pthresh, thresholds)
+
+
+def scan_cis(expr, geno, pthresh, snp_pos, trait_pos, window):
+    """cis scan (the paper's cis-eQTL analysis: marker-trait pairs within a fixed
+    distance): the full scan with every pair outside |snp_pos - trait_pos| <=
+    window marked as not a hit.  Returns the dense result dict of ``scan``."""
+    r = scan(expr, geno, pthresh)
+    d = np.abs(np.asarray(trait_pos, dtype=np.int64)[:, None] - np.asarray(snp_pos, dtype=np.int64)[None, :])
+    r["in_window"] = d <= window
+    r["hit"] = r["hit"] & r["in_window"]
+    return r

@@ -28,7 +28,8 @@ EXPORTS = ["krux_create", "krux_destroy", "krux_status_string", "krux_last_error
            "krux_permute", "krux_scan_grouped", "krux_make_perms", "krux_set_profiling",
            "krux_get_profile", "krux_set_wait_limit", "krux_set_tuning", "krux_scan_noalloc", "krux_debug_plan",
            "krux_autotune", "krux_graph_scan", "krux_graph_permute", "krux_graph_grouped",
-           "krux_graph_launch", "krux_graph_wait", "krux_graph_last_error", "krux_graph_destroy"]
+           "krux_graph_launch", "krux_graph_wait", "krux_graph_last_error", "krux_graph_destroy",
+           "krux_scan_cis"]
 
 
 class KruxError(RuntimeError):
@@ -92,6 +93,8 @@ def load_library(path=LIB_PATH):
         "krux_debug_plan": ([I, I, I, I, I, I, P], I),
         "krux_scan_noalloc": ([P, I, I, I64, P, I64, I64, D, P, P, P, I64, ctypes.POINTER(I64), P], I),
         "krux_autotune": ([P, P, P, I64, I64, D, P, P], I),
+        "krux_scan_cis": ([P, P, P, I64, I64, P, P, I64, ctypes.POINTER(Opts), P, P, P,
+                           ctypes.POINTER(I64), P], I),
         "krux_graph_scan": ([P, P, P, I64, I64, ctypes.POINTER(Opts), P, P, P, ctypes.POINTER(P)], I),
         "krux_graph_permute": ([P, P, P, I64, I64, P, I, ctypes.POINTER(Opts), P, P, P, P, P, I, D,
                                 ctypes.POINTER(P)], I),
@@ -281,6 +284,19 @@ class Krux:
         d0, d1), H, p float64 [k], and dense_H / dense_p [T, S] if dense)."""
         return self._scan(self.lib.krux_scan, rs, geno, pthresh, capacity, snp_begin, snp_end,
                           dense, margin, stream)
+
+    def krux_scan_cis(self, rs, geno, snp_pos, trait_pos, window, pthresh, capacity, stream=None):
+        """cis scan: only pairs with |snp_pos - trait_pos| <= window (int64 device
+        coordinates, nondecreasing).  Returns the result dict of krux_scan."""
+        hits, H, P = self._outputs(capacity)
+        o = self._opts(pthresh, capacity)
+        n = ctypes.c_int64()
+        st = self.lib.krux_scan_cis(self.handle, rs.handle, _ptr(geno), geno.shape[0], geno.stride(0),
+                                    _ptr(snp_pos), _ptr(trait_pos), int(window), ctypes.byref(o),
+                                    _ptr(hits), _ptr(H), _ptr(P), ctypes.byref(n), _stream(stream))
+        st = self._check(st, "krux_scan_cis")
+        k = min(n.value, capacity)
+        return dict(n_hits=n.value, overflow=st == KRUX_EOVERFLOW, hits=hits[:k], H=H[:k], p=P[:k])
 
     def krux_scan_plain(self, rs, geno, pthresh, capacity, snp_begin=0, snp_end=0, dense=False,
                         margin=0.0, stream=None):

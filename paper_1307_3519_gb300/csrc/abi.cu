@@ -684,6 +684,12 @@ struct CallPlan {
     uint16_t *lists = nullptr;   // [1 + P][T][N] NaN sample lists (rank sets with NaN)
     int32_t *inv = nullptr;      // [P][N] inverse permutations
   } perm;
+  struct Cis {  // cis scans: SNP and trait coordinates (host copies) and the window
+    bool on = false;
+    const int64_t *snp_pos = nullptr, *trait_pos = nullptr;  // device
+    std::vector<int64_t> h_snp, h_trait;                      // host copies
+    int64_t window = -1;
+  } cis;
   unsigned long long *fdr_hist = nullptr;  // permutation calls: [fdr_rows = 1 + P][fdr_bins] or null
   int fdr_rows = 0, fdr_bins = 0;
   double fdr_l0 = 0.0, fdr_w = 1.0;
@@ -832,6 +838,40 @@ krux_status materialise(krux_ctx *ctx, CallPlan &cp, cudaStream_t s) {
   return KRUX_OK;
 }
 
+// cis scans: for every B tile, only the trait tiles whose traits can lie within
+// the window of one of the tile's SNPs (SNP and trait coordinates are
+// nondecreasing, so that is one contiguous range of trait tiles); B tiles with
+// none are skipped.
+std::vector<WorkItem> make_items_cis(const CallPlan &cp, const std::vector<GroupPlan> &gp) {
+  std::vector<WorkItem> items;
+  const std::vector<int64_t> &tp = cp.cis.h_trait;
+  const int64_t W = cp.cis.window;
+  for (size_t gi = 0; gi < gp.size(); ++gi) {
+    const ScanGroupIn &g = cp.groups[gi];
+    const GroupDesc &d = gp[gi].d;
+    auto snp_at = [&](int64_t i) {
+      return g.list_off >= 0 ? cp.lists[(size_t)(g.list_off + i)] : g.snp_begin + i;
+    };
+    for (int64_t b = 0; b < gp[gi].n_btiles; ++b) {
+      const int64_t first = b * d.nc * kChunkSnps;
+      const int64_t last = std::min<int64_t>((b + 1) * d.nc * kChunkSnps, g.n_snps) - 1;
+      if (first > last) continue;
+      const int64_t lo = cp.cis.h_snp[(size_t)snp_at(first)] - W;
+      const int64_t hi = cp.cis.h_snp[(size_t)snp_at(last)] + W;
+      const int64_t t0 = std::lower_bound(tp.begin(), tp.end(), lo) - tp.begin();
+      const int64_t t1 = std::upper_bound(tp.begin(), tp.end(), hi) - tp.begin();
+      if (t0 >= t1) continue;
+      WorkItem w;
+      w.group = (int32_t)gi;
+      w.btile = (int32_t)b;
+      w.step_begin = (int32_t)(t0 / kTileM);
+      w.step_end = (int32_t)((t1 - 1) / kTileM + 1);
+      items.push_back(w);
+    }
+  }
+  return items;
+}
+
 // One fused launch, split in three phases so that the middle one can be captured
 // in a CUDA graph: prepare (host planning, buffer sizing, descriptor uploads; no
 // work queued that a replay would need), enqueue (stream work only: packing, the
@@ -964,7 +1004,8 @@ krux_status prepare_fused(krux_ctx *ctx, CallPlan &cp, const krux_opts *o, Fused
     plans[i].steps = (int64_t)g.n_agroups * rs->n_ttiles;
     descs[i] = d;
   }
-  std::vector<WorkItem> items = make_items(plans, nc_max, ctx->sm_count);
+  std::vector<WorkItem> items =
+      cp.cis.on ? make_items_cis(cp, plans) : make_items(plans, nc_max, ctx->sm_count);
   KRUX_CUDA(ctx, ctx->groups.ensure(sizeof(GroupDesc) * ng));
   KRUX_CUDA(ctx, ctx->items.ensure(sizeof(WorkItem) * std::max<size_t>(items.size(), 1)));
   // pageable uploads: staged before the calls return, so the host vectors may go
@@ -1003,6 +1044,11 @@ krux_status prepare_fused(krux_ctx *ctx, CallPlan &cp, const krux_opts *o, Fused
   p.fdr_bins = cp.fdr_bins;
   p.fdr_l0 = cp.fdr_l0;
   p.fdr_w = cp.fdr_w;
+  if (cp.cis.on) {
+    p.cis_snp_pos = cp.cis.snp_pos;
+    p.cis_trait_pos = cp.cis.trait_pos;
+    p.cis_window = cp.cis.window;
+  }
   fl.grid = (int)std::min<size_t>(items.size(), (size_t)ctx->sm_count);
   // Single hit list: every epilogue warp stages its hits in a segment of its own
   // (no atomic per hit event) and the segments are appended after the launch.
@@ -1193,6 +1239,57 @@ extern "C" krux_status krux_scan(krux_ctx *ctx, const krux_rankset *rs, const in
   cp.slots.push_back(OutSlot{hits, hit_H, hit_p, opts->hit_capacity, ctx->aux.as<HitAux>()});
   st = plan_groups(ctx, cp, rs, geno, ldg, b, e, nullptr, 1, 0, opts->dense_H, opts->dense_p,
                    nullptr, s);
+  if (st != KRUX_OK) return st;
+  st = materialise(ctx, cp, s);
+  if (st != KRUX_OK) return st;
+  std::vector<unsigned long long> counts;
+  st = run_fused(ctx, cp, opts, s, counts);
+  if (st != KRUX_OK) return st;
+  *n_hits = (int64_t)counts[0];
+  if (*n_hits > opts->hit_capacity)
+    return fail(ctx, KRUX_EOVERFLOW, "%lld hits exceed capacity %lld", (long long)*n_hits,
+                (long long)opts->hit_capacity);
+  return KRUX_OK;
+}
+
+extern "C" krux_status krux_scan_cis(krux_ctx *ctx, const krux_rankset *rs, const int8_t *geno,
+                                     int64_t S, int64_t ldg, const int64_t *snp_pos,
+                                     const int64_t *trait_pos, int64_t window,
+                                     const krux_opts *opts, krux_hit *hits, double *hit_H,
+                                     double *hit_p, int64_t *n_hits, void *stream) {
+  krux_status st = check_scan_args(ctx, rs, geno, S, ldg, opts, hits, hit_H, hit_p, n_hits);
+  if (st != KRUX_OK) return st;
+  *n_hits = 0;
+  if (opts->dense_H || opts->dense_p)
+    return fail(ctx, KRUX_EINVAL, "dense output is not available with a cis window");
+  if (window < 0 || (S > 0 && !snp_pos) || !trait_pos)
+    return fail(ctx, KRUX_EINVAL, "cis scan needs window >= 0 and both coordinate arrays");
+  cudaStream_t s = (cudaStream_t)stream;
+  KRUX_CUDA(ctx, cudaSetDevice(ctx->device));
+  CallPlan cp;
+  cp.cis.on = true;
+  cp.cis.snp_pos = snp_pos;
+  cp.cis.trait_pos = trait_pos;
+  cp.cis.window = window;
+  cp.cis.h_snp.resize((size_t)S);
+  cp.cis.h_trait.resize((size_t)rs->T);
+  if (S > 0)
+    KRUX_CUDA(ctx, cudaMemcpyAsync(cp.cis.h_snp.data(), snp_pos, (size_t)S * 8,
+                                   cudaMemcpyDeviceToHost, s));
+  KRUX_CUDA(ctx, cudaMemcpyAsync(cp.cis.h_trait.data(), trait_pos, (size_t)rs->T * 8,
+                                 cudaMemcpyDeviceToHost, s));
+  KRUX_CUDA(ctx, cudaStreamSynchronize(s));
+  if (!std::is_sorted(cp.cis.h_snp.begin(), cp.cis.h_snp.end()) ||
+      !std::is_sorted(cp.cis.h_trait.begin(), cp.cis.h_trait.end()))
+    return fail(ctx, KRUX_EINVAL, "cis coordinates must be nondecreasing");
+  const int64_t b = opts->snp_begin, e = opts->snp_end > 0 ? opts->snp_end : S;
+  if (ctx->profiling) {
+    ctx->prof = krux_profile{};
+    ctx->prof.pairs = (int64_t)rs->T * (e - b);
+  }
+  KRUX_CUDA(ctx, ctx->aux.ensure((size_t)std::max<int64_t>(opts->hit_capacity, 1) * sizeof(HitAux)));
+  cp.slots.push_back(OutSlot{hits, hit_H, hit_p, opts->hit_capacity, ctx->aux.as<HitAux>()});
+  st = plan_groups(ctx, cp, rs, geno, ldg, b, e, nullptr, 1, 0, nullptr, nullptr, nullptr, s);
   if (st != KRUX_OK) return st;
   st = materialise(ctx, cp, s);
   if (st != KRUX_OK) return st;

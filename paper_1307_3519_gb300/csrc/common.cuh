@@ -161,6 +161,10 @@ struct ScanParams {
   int32_t fdr_bins;
   float fdr_pad_;
   double fdr_l0, fdr_w;     // bin b = floor((-log10 p - fdr_l0) / fdr_w), clamped to [0, bins)
+  // cis mode (cis_window >= 0): a pair is reported only if |snp_pos - trait_pos| <= window
+  const int64_t *cis_snp_pos;    // [S] global coordinate of every SNP row
+  const int64_t *cis_trait_pos;  // [T] global coordinate of every trait (its gene)
+  int64_t cis_window = -1;       // -1: off
 };
 
 enum : unsigned int {

@@ -210,6 +210,13 @@ __device__ __forceinline__ double key64_of(double H, int df) {
   return 0.0;
 }
 
+// cis mode: only pairs whose SNP and trait lie within the window are reported.
+__device__ __forceinline__ bool in_cis_window(const ScanParams &p, int snp, int trait) {
+  if (p.cis_window < 0) return true;
+  const long long d = (long long)(p.cis_snp_pos[snp] - p.cis_trait_pos[trait]);
+  return d <= p.cis_window && -d <= p.cis_window;
+}
+
 // FDR histogram bin of a pair with -ln p = key: b = floor((-log10 p - l0) / w),
 // clamped to [0, bins).
 __device__ __forceinline__ int fdr_bin(double key, double l0, double w, int bins) {
@@ -356,7 +363,7 @@ __device__ __noinline__ void hit_slow(const uint32_t *dv, bool mine, const Chunk
     const float *al = m.alpha + jb, *be = m.beta + jb, *ga = m.gamma + jb;
     for (int j = 0; j < kEpiSnps; ++j) {
       const int snp = m.snp[jb + j];
-      if (snp < 0) continue;
+      if (snp < 0 || !in_cis_window(p, snp, trait)) continue;
       const float u = __uint_as_float(dv[j]), v = __uint_as_float(dv[kEpiSnps + j]);
       if (p.dense || nan_cnt > 0) {
         int n0, n1, n2;
@@ -482,7 +489,7 @@ __device__ __forceinline__ unsigned int hit_event(const uint32_t *dv, bool mine,
     while (cand) {
       const int j = __ffs(cand) - 1;
       cand &= cand - 1u;
-      if (m.snp[jb + j] < 0) continue;
+      if (m.snp[jb + j] < 0 || !in_cis_window(p, m.snp[jb + j], trait)) continue;
       bool hit = ((not_sure >> j) & 1u) == 0u;
       if (!hit)
         hit = decide64(__uint_as_float(dv[j]), __uint_as_float(dv[kEpiSnps + j]), m.n[0][jb + j],

@@ -230,3 +230,20 @@ def config(c, T=None, S=None, N=None, seed=None):
             cohorts.append(dict(expr=e, geno=g, N=n_c))
         return dict(cohorts=cohorts, pthresh=1e-5, T=T, S=S)
     raise ValueError(f"unknown workload {c}")
+
+
+def genome_positions(rng, S, T, n_chrom=22, chrom_len=150_000_000):
+    """Synthetic map for cis scans: SNP rows spread in order over ``n_chrom``
+    chromosomes of ``chrom_len`` bases (sorted uniform positions), and one gene
+    position per trait (uniform over the genome, sorted).  Coordinates are global:
+    chromosome * 2^40 + base position, int64, nondecreasing.  Returns
+    (snp_pos [S], trait_pos [T])."""
+    rng = _rng(rng)
+    per = np.full(n_chrom, S // n_chrom, dtype=np.int64)
+    per[: S % n_chrom] += 1
+    snp = np.concatenate([(np.int64(c) << 40) + np.sort(rng.integers(0, chrom_len, size=int(k)))
+                          for c, k in enumerate(per)]).astype(np.int64)
+    chrom = np.sort(rng.integers(0, n_chrom, size=T)).astype(np.int64)
+    gene = (chrom << 40) + rng.integers(0, chrom_len, size=T)
+    order = np.lexsort((gene & ((1 << 40) - 1), chrom))
+    return snp, gene[order].astype(np.int64)

@@ -209,3 +209,32 @@ def test_tile_shapes(kx, oracle_mod, layout, nc, nA, ka, N):
         kx.set_tuning(-1, 0, 0, 0)
     check_hits(res, orc, np.arange(270), np.arange(1300), pth, must_have_hits=False)
     assert res["n_hits"] == int(orc["hit"].sum())
+
+
+@pytest.mark.parametrize("window", [0, 200_000, 1_000_000, 1 << 50])
+def test_cis_scan(kx, oracle_mod, window):
+    """cis scan: the hits of the full scan within the window, nothing else; the
+    work is pruned to the trait tiles the window reaches."""
+    import synth as sy
+    T, S = 300, 4000
+    d = sy.config(2, T=T, S=S, seed=71)
+    snp_pos, trait_pos = sy.genome_positions(np.random.default_rng(72), S, T, n_chrom=2,
+                                             chrom_len=4_000_000)
+    rs = kx.krux_rank(_dev(d["expr"]))
+    g = _dev(d["geno"])
+    res = kx.krux_scan_cis(rs, g, _dev(snp_pos), _dev(trait_pos), window, 1e-4, capacity=T * S)
+    orc = oracle_mod.scan_cis(d["expr"], d["geno"], 1e-4, snp_pos, trait_pos, window)
+    check_hits(res, orc, np.arange(T), np.arange(S), 1e-4, must_have_hits=False)
+    assert res["n_hits"] == int(orc["hit"].sum())
+
+
+def test_cis_scan_rejects_unsorted_coordinates(kx):
+    import paper_1307_3519_gb300 as k
+    import synth as sy
+    d = sy.config(1, T=20, S=100, seed=73)
+    snp_pos, trait_pos = sy.genome_positions(np.random.default_rng(74), 100, 20)
+    snp_pos[3] = snp_pos[4] + 5  # no longer nondecreasing
+    rs = kx.krux_rank(_dev(d["expr"]))
+    with pytest.raises(k.KruxError) as e:
+        kx.krux_scan_cis(rs, _dev(d["geno"]), _dev(snp_pos), _dev(trait_pos), 1000, 1e-3, capacity=10)
+    assert e.value.status == k.KRUX_EINVAL

@@ -293,3 +293,19 @@ def test_fdr_counts_match_permuted_scans(oracle_mod):
         p = oracle_mod.scan(np.ascontiguousarray(d["expr"][:, perms[q]]), d["geno"], 0.05)["p"]
         p = p[p < 0.05]
         assert list(pc[q]) == [int((p <= t).sum()) for t in thr]
+
+
+def test_cis_window_mask(oracle_mod):
+    """Pairs kept by the cis filter: |snp_pos - trait_pos| <= window, worked by hand."""
+    rng = np.random.default_rng(3)
+    expr = rng.standard_normal((3, 12)).astype(np.float32)
+    geno = rng.integers(0, 3, size=(4, 12)).astype(np.int8)
+    snp_pos = np.array([0, 10, 20, (1 << 40)], dtype=np.int64)
+    trait_pos = np.array([5, 15, (1 << 40) + 3], dtype=np.int64)
+    r = oracle_mod.scan_cis(expr, geno, 0.5, snp_pos, trait_pos, 5)
+    want = np.array([[1, 1, 0, 0], [0, 1, 1, 0], [0, 0, 0, 1]], dtype=bool)
+    assert np.array_equal(r["in_window"], want)
+    full = oracle_mod.scan(expr, geno, 0.5)
+    assert np.array_equal(r["hit"], full["hit"] & want)
+    wide = oracle_mod.scan_cis(expr, geno, 0.5, snp_pos, trait_pos, 1 << 62)
+    assert np.array_equal(wide["hit"], full["hit"])
