@@ -24,8 +24,8 @@ _lib = None
 class _Pair(ctypes.Structure):
     _fields_ = [("H", ctypes.c_double), ("H_alt", ctypes.c_double),
                 ("p", ctypes.c_double), ("tie", ctypes.c_double),
-                ("rank2", ctypes.c_int64 * 3), ("d", ctypes.c_int64 * 3),
-                ("n", ctypes.c_int32 * 3), ("K", ctypes.c_int32),
+                ("rank2", ctypes.c_int64 * 5), ("d", ctypes.c_int64 * 5),
+                ("n", ctypes.c_int32 * 5), ("K", ctypes.c_int32),
                 ("df", ctypes.c_int32), ("hit", ctypes.c_int32)]
 
 
@@ -49,6 +49,15 @@ def _load():
         P = ctypes.c_void_p
         lib.oracle_pair.argtypes = [P, P, ctypes.c_int, ctypes.c_double, ctypes.POINTER(_Pair)]
         lib.oracle_pair.restype = ctypes.c_int
+        lib.oracle_pair_l.argtypes = [P, P, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                      ctypes.POINTER(_Pair)]
+        lib.oracle_pair_l.restype = ctypes.c_int
+        lib.oracle_chi2_upper.argtypes = [ctypes.c_double, ctypes.c_int]
+        lib.oracle_chi2_upper.restype = ctypes.c_double
+        lib.oracle_scan_l.argtypes = [P, ctypes.c_int64, P, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                                      P, ctypes.c_int64, P, ctypes.c_int64, P,
+                                      ctypes.c_double, P, P, P, P, P, P, P, P]
+        lib.oracle_scan_l.restype = ctypes.c_int
         lib.oracle_rank_row.argtypes = [P, ctypes.c_int, P, ctypes.POINTER(ctypes.c_double)]
         lib.oracle_rank_row.restype = ctypes.c_int32
         lib.oracle_scan.argtypes = [P, ctypes.c_int64, P, ctypes.c_int64, ctypes.c_int,
@@ -73,19 +82,27 @@ def num_threads():
     return int(_load().oracle_num_threads())
 
 
-def kw_pair(x, g, pthresh=0.05):
-    """Kruskal-Wallis test of one trait against one SNP.  Returns a dict with
-    H, H_alt, p, df, K, tie, n (3), rank2 (3) = 2*rank sums, d (3) = centred
-    sums 2*S_i - N_i*(K+1), hit."""
+def kw_pair(x, g, pthresh=0.05, max_code=2):
+    """Kruskal-Wallis test of one trait against one marker with codes
+    0..max_code (max_code <= 4; -1 = missing).  Returns a dict with H, H_alt, p,
+    df, K, tie, n (max_code+1), rank2 (max_code+1) = 2*rank sums, d
+    (max_code+1) = centred sums 2*S_i - N_i*(K+1), hit."""
     x = np.ascontiguousarray(x, dtype=np.float32)
     g = np.ascontiguousarray(g, dtype=np.int8)
     assert x.shape == g.shape and x.ndim == 1
     r = _Pair()
-    rc = _load().oracle_pair(_ptr(x), _ptr(g), x.size, float(pthresh), ctypes.byref(r))
+    rc = _load().oracle_pair_l(_ptr(x), _ptr(g), x.size, int(max_code), float(pthresh),
+                               ctypes.byref(r))
     if rc != 0:
-        raise ValueError("genotype code outside {-1,0,1,2}")
+        raise ValueError(f"genotype code outside {{-1, 0..{max_code}}}")
+    k = max_code + 1
     return dict(H=r.H, H_alt=r.H_alt, p=r.p, df=r.df, K=r.K, tie=r.tie,
-                n=list(r.n), rank2=list(r.rank2), d=list(r.d), hit=bool(r.hit))
+                n=list(r.n)[:k], rank2=list(r.rank2)[:k], d=list(r.d)[:k], hit=bool(r.hit))
+
+
+def chi2_upper(H, df):
+    """Upper tail of the chi-square law with df degrees of freedom at H."""
+    return float(_load().oracle_chi2_upper(float(H), int(df)))
 
 
 def rank_row(x):
@@ -97,10 +114,10 @@ def rank_row(x):
     return r2, tie.value, int(K)
 
 
-def scan(expr, geno, pthresh, traits=None, snps=None, perm=None):
-    """Dense per-pair results over traits x snps (defaults: all).  Returns a dict
-    of arrays shaped (len(traits), len(snps)): H, p, df, K, hit, H_alt, and
-    d / n shaped (..., 3)."""
+def scan(expr, geno, pthresh, traits=None, snps=None, perm=None, max_code=2):
+    """Dense per-pair results over traits x snps (defaults: all); genotype codes
+    0..max_code.  Returns a dict of arrays shaped (len(traits), len(snps)): H, p,
+    df, K, hit, H_alt, and d / n shaped (..., max_code + 1)."""
     expr = np.ascontiguousarray(expr, dtype=np.float32)
     geno = np.ascontiguousarray(geno, dtype=np.int8)
     T, N = expr.shape
@@ -109,18 +126,19 @@ def scan(expr, geno, pthresh, traits=None, snps=None, perm=None):
     traits = np.arange(T, dtype=np.int64) if traits is None else np.ascontiguousarray(traits, dtype=np.int64)
     snps = np.arange(S, dtype=np.int64) if snps is None else np.ascontiguousarray(snps, dtype=np.int64)
     nt, ns = traits.size, snps.size
+    ng = max_code + 1
     out = dict(H=np.empty((nt, ns)), p=np.empty((nt, ns)),
-               df=np.empty((nt, ns), np.int32), d=np.empty((nt, ns, 3), np.int64),
-               n=np.empty((nt, ns, 3), np.int32), K=np.empty((nt, ns), np.int32),
+               df=np.empty((nt, ns), np.int32), d=np.empty((nt, ns, ng), np.int64),
+               n=np.empty((nt, ns, ng), np.int32), K=np.empty((nt, ns), np.int32),
                hit=np.empty((nt, ns), np.uint8), H_alt=np.empty((nt, ns)))
     pp = None if perm is None else np.ascontiguousarray(perm, dtype=np.int32)
-    rc = _load().oracle_scan(_ptr(expr), N, _ptr(geno), N, N, _ptr(traits), nt,
-                             _ptr(snps), ns, _ptr(pp), float(pthresh),
-                             _ptr(out["H"]), _ptr(out["p"]), _ptr(out["df"]),
-                             _ptr(out["d"]), _ptr(out["n"]), _ptr(out["K"]),
-                             _ptr(out["hit"]), _ptr(out["H_alt"]))
+    rc = _load().oracle_scan_l(_ptr(expr), N, _ptr(geno), N, N, int(max_code), _ptr(traits), nt,
+                               _ptr(snps), ns, _ptr(pp), float(pthresh),
+                               _ptr(out["H"]), _ptr(out["p"]), _ptr(out["df"]),
+                               _ptr(out["d"]), _ptr(out["n"]), _ptr(out["K"]),
+                               _ptr(out["hit"]), _ptr(out["H_alt"]))
     if rc != 0:
-        raise ValueError("genotype code outside {-1,0,1,2}")
+        raise ValueError(f"genotype code outside {{-1, 0..{max_code}}}")
     out["hit"] = out["hit"].astype(bool)
     return out
 

@@ -18,13 +18,17 @@
  *      average of the 1-based positions it occupies (section "Input data":
  *      ranks per trait; ties get average ranks); accumulate sum(t^3 - t) over
  *      the runs (section "Handling tied data");
- *   3. rank sums S_i and counts N_i of each genotype group i = 0,1,2 (Eq. 4);
+ *   3. rank sums S_i and counts N_i of each genotype group i = 0..l (Eq. 4;
+ *      section "Input data": markers take values 0..l, l = 2 for biallelic
+ *      markers, and any number of alleles is allowed);
  *   4. S = 12/(K(K+1)) * sum_{i: N_i>0} S_i^2/N_i - 3(K+1) (Eq. 2; empty groups
  *      contribute nothing, the paper's NaN -> 0 rule);
  *   5. divide by 1 - sum(t^3-t)/(K^3-K) (section "Handling tied data");
  *   6. df = (number of non-empty groups) - 1; p = upper chi-square tail with df
- *      degrees of freedom (section "P-value calculation"): df = 1 gives
- *      erfc(sqrt(H/2)), df = 2 gives exp(-H/2);
+ *      degrees of freedom (section "P-value calculation"), from the closed
+ *      forms of the regularised upper incomplete gamma function Q(df/2, H/2)
+ *      for integer and half-integer shapes (df = 1: erfc(sqrt(H/2)); df = 2:
+ *      exp(-H/2));
  *   7. the pair is a hit iff p < P_c.
  * Degenerate pairs (df = 0, K < 2, or all values tied so the tie factor is 0)
  * get H = 0, p = 1 and are never hits.
@@ -45,9 +49,9 @@ typedef struct {
   double H_alt;    /* same statistic from the variance-ratio textbook form    */
   double p;        /* chi-square upper tail                                    */
   double tie;      /* sum over tie runs of t^3 - t                             */
-  int64_t rank2[3];/* twice the rank sum of each genotype group: 2*S_i        */
-  int64_t d[3];    /* centred sums 2*S_i - N_i*(K+1)                           */
-  int32_t n[3];    /* group sizes N_i                                          */
+  int64_t rank2[5];/* twice the rank sum of each genotype group: 2*S_i        */
+  int64_t d[5];    /* centred sums 2*S_i - N_i*(K+1)                           */
+  int32_t n[5];    /* group sizes N_i                                          */
   int32_t K;       /* samples used                                            */
   int32_t df;      /* degrees of freedom                                      */
   int32_t hit;     /* p < P_c                                                 */
@@ -96,26 +100,49 @@ static int32_t rank_row(const float *x, const unsigned char *use, int n,
   return K;
 }
 
-/* Upper tail of the chi-square law with df = 1 or 2 degrees of freedom. */
+/* Upper tail of the chi-square law with df degrees of freedom at H:
+ * Q(df/2, x), x = H/2, the regularised upper incomplete gamma function.  For an
+ * integer shape m (df = 2m):      Q(m, x)     = e^-x sum_{k<m} x^k / k!;
+ * for a half-integer shape (df = 2m+1): Q(m+1/2, x) = erfc(sqrt x)
+ *                                     + e^-x sum_{k=1..m} x^(k-1/2) / Gamma(k+1/2),
+ * with Gamma(k+1/2) = Gamma(k-1/2) * (k-1/2) and Gamma(1/2) = sqrt(pi). */
 static double chi2_upper(double H, int df) {
-  if (df == 1) return erfc(sqrt(0.5 * H));
-  if (df == 2) return exp(-0.5 * H);
-  return 1.0;
+  if (df <= 0) return 1.0;
+  const double x = 0.5 * H;
+  if (df % 2 == 0) {
+    double term = 1.0, sum = 0.0;
+    for (int k = 0; k < df / 2; ++k) {
+      if (k > 0) term *= x / (double)k;
+      sum += term;
+    }
+    return exp(-x) * sum;
+  }
+  if (!(x > 0.0)) return 1.0;
+  double q = erfc(sqrt(x));
+  double g = sqrt(3.14159265358979323846); /* Gamma(1/2) = sqrt(pi) */
+  double xp = 1.0 / sqrt(x);   /* x^(-1/2) */
+  for (int k = 1; k <= df / 2; ++k) {
+    g *= (double)k - 0.5;           /* Gamma(k + 1/2) */
+    xp *= x;                         /* x^(k - 1/2) */
+    q += exp(-x) * xp / g;
+  }
+  return q;
 }
 
 /* One (trait, SNP) pair.  x: expression of the trait over n samples (NaN =
- * missing); g: genotype codes of the SNP (0,1,2; -1 = missing).  Returns 0, or
- * -1 if a genotype code is outside {-1,0,1,2}. */
-int oracle_pair(const float *x, const int8_t *g, int n, double pthresh,
-                oracle_pair_t *out) {
+ * missing); g: genotype codes of the SNP (0..lmax; -1 = missing), lmax <= 4.
+ * Returns 0, or -1 if a genotype code is outside {-1, 0..lmax}. */
+int oracle_pair_l(const float *x, const int8_t *g, int n, int lmax, double pthresh,
+                  oracle_pair_t *out) {
   memset(out, 0, sizeof(*out));
   unsigned char *use = (unsigned char *)malloc((size_t)n + 1);
   int64_t *r2 = (int64_t *)malloc(sizeof(int64_t) * ((size_t)n + 1));
   keyed_t *work = (keyed_t *)malloc(sizeof(keyed_t) * ((size_t)n + 1));
   int rc = 0;
+  if (lmax < 1 || lmax > 4) rc = -1;
   for (int k = 0; k < n; ++k) {
-    if (g[k] < -1 || g[k] > 2) rc = -1;
-    use[k] = (g[k] >= 0 && g[k] <= 2 && !isnan(x[k])) ? 1 : 0;
+    if (g[k] < -1 || g[k] > lmax) rc = -1;
+    use[k] = (g[k] >= 0 && g[k] <= lmax && !isnan(x[k])) ? 1 : 0;
   }
   if (rc != 0) goto done;
 
@@ -129,7 +156,7 @@ int oracle_pair(const float *x, const int8_t *g, int n, double pthresh,
     out->n[g[k]] += 1;
   }
   int groups = 0;
-  for (int i = 0; i < 3; ++i) {
+  for (int i = 0; i <= lmax; ++i) {
     out->d[i] = out->rank2[i] - (int64_t)out->n[i] * (int64_t)(K + 1);
     if (out->n[i] > 0) ++groups;
   }
@@ -146,7 +173,7 @@ int oracle_pair(const float *x, const int8_t *g, int n, double pthresh,
   }
   /* Eq. 2 with rank sums S_i = rank2_i / 2, empty groups skipped */
   double acc = 0.0;
-  for (int i = 0; i < 3; ++i) {
+  for (int i = 0; i <= lmax; ++i) {
     if (out->n[i] == 0) continue;
     double Si = 0.5 * (double)out->rank2[i];
     acc += Si * Si / (double)out->n[i];
@@ -159,7 +186,7 @@ int oracle_pair(const float *x, const int8_t *g, int n, double pthresh,
    * which includes the tie correction by construction. */
   double mean = 0.5 * (Kd + 1.0);
   double num = 0.0, den = 0.0;
-  for (int i = 0; i < 3; ++i) {
+  for (int i = 0; i <= lmax; ++i) {
     if (out->n[i] == 0) continue;
     double mi = 0.5 * (double)out->rank2[i] / (double)out->n[i];
     num += (double)out->n[i] * (mi - mean) * (mi - mean);
@@ -181,6 +208,14 @@ done:
   return rc;
 }
 
+/* Biallelic form (codes 0, 1, 2). */
+int oracle_pair(const float *x, const int8_t *g, int n, double pthresh, oracle_pair_t *out) {
+  return oracle_pair_l(x, g, n, 2, pthresh, out);
+}
+
+/* Upper chi-square tail, exported for the pins. */
+double oracle_chi2_upper(double H, int df) { return chi2_upper(H, df); }
+
 /* Ranks of one expression row over its non-NaN samples: 2*average rank (0 for
  * NaN), the tie sum and K (section "Input data", "Handling missing values",
  * "Handling tied data"). */
@@ -201,11 +236,12 @@ int32_t oracle_rank_row(const float *x, int n, int64_t *rank2, double *tie) {
  * pair takes expression value x[perm[k]] (section "P-value calculation and
  * empirical FDR correction": the columns of the expression ranks are
  * permuted).  Returns 0 or -1 (bad genotype code). */
-int oracle_scan(const float *expr, int64_t ldx, const int8_t *geno, int64_t ldg,
-                int N, const int64_t *traits, int64_t nt, const int64_t *snps,
-                int64_t ns, const int32_t *perm, double pthresh, double *H,
-                double *p, int32_t *df, int64_t *d, int32_t *nk, int32_t *K,
-                uint8_t *hit, double *H_alt) {
+int oracle_scan_l(const float *expr, int64_t ldx, const int8_t *geno, int64_t ldg,
+                  int N, int lmax, const int64_t *traits, int64_t nt, const int64_t *snps,
+                  int64_t ns, const int32_t *perm, double pthresh, double *H,
+                  double *p, int32_t *df, int64_t *d, int32_t *nk, int32_t *K,
+                  uint8_t *hit, double *H_alt) {
+  const int ng = lmax + 1;
   int bad = 0;
 #pragma omp parallel for schedule(dynamic, 1) reduction(| : bad)
   for (int64_t a = 0; a < nt; ++a) {
@@ -214,13 +250,13 @@ int oracle_scan(const float *expr, int64_t ldx, const int8_t *geno, int64_t ldg,
     for (int k = 0; k < N; ++k) x[k] = perm ? row[perm[k]] : row[k];
     for (int64_t b = 0; b < ns; ++b) {
       oracle_pair_t r;
-      if (oracle_pair(x, geno + snps[b] * ldg, N, pthresh, &r) != 0) bad |= 1;
+      if (oracle_pair_l(x, geno + snps[b] * ldg, N, lmax, pthresh, &r) != 0) bad |= 1;
       int64_t o = a * ns + b;
       if (H) H[o] = r.H;
       if (p) p[o] = r.p;
       if (df) df[o] = r.df;
-      if (d) for (int i = 0; i < 3; ++i) d[3 * o + i] = r.d[i];
-      if (nk) for (int i = 0; i < 3; ++i) nk[3 * o + i] = r.n[i];
+      if (d) for (int i = 0; i < ng; ++i) d[ng * o + i] = r.d[i];
+      if (nk) for (int i = 0; i < ng; ++i) nk[ng * o + i] = r.n[i];
       if (K) K[o] = r.K;
       if (hit) hit[o] = (uint8_t)r.hit;
       if (H_alt) H_alt[o] = r.H_alt;
@@ -228,6 +264,16 @@ int oracle_scan(const float *expr, int64_t ldx, const int8_t *geno, int64_t ldg,
     free(x);
   }
   return bad ? -1 : 0;
+}
+
+/* Biallelic dense scan (codes 0, 1, 2). */
+int oracle_scan(const float *expr, int64_t ldx, const int8_t *geno, int64_t ldg,
+                int N, const int64_t *traits, int64_t nt, const int64_t *snps,
+                int64_t ns, const int32_t *perm, double pthresh, double *H,
+                double *p, int32_t *df, int64_t *d, int32_t *nk, int32_t *K,
+                uint8_t *hit, double *H_alt) {
+  return oracle_scan_l(expr, ldx, geno, ldg, N, 2, traits, nt, snps, ns, perm, pthresh, H, p, df,
+                       d, nk, K, hit, H_alt);
 }
 
 /* Permutation null: for each permutation q and trait a, the minimum p over

@@ -31,14 +31,14 @@ def _load_golden():
 
 
 def _mp_tail(H, df):
+    """Upper chi-square tail at an exact rational H, 40 digits (mpmath's
+    regularised upper incomplete gamma)."""
     import mpmath as mp
     mp.mp.dps = 40
     h = mp.mpf(H.numerator) / H.denominator
     if df == 0 or h == 0:
         return 1.0
-    if df == 1:
-        return float(mp.erfc(mp.sqrt(h / 2)))
-    return float(mp.exp(-h / 2))
+    return float(mp.gammainc(mp.mpf(df) / 2, h / 2, mp.inf, regularized=True))
 
 
 @pytest.mark.parametrize("case", range(8))
@@ -309,3 +309,80 @@ def test_cis_window_mask(oracle_mod):
     assert np.array_equal(r["hit"], full["hit"] & want)
     wide = oracle_mod.scan_cis(expr, geno, 0.5, snp_pos, trait_pos, 1 << 62)
     assert np.array_equal(wide["hit"], full["hit"])
+
+
+
+def _load_multi():
+    rows = []
+    with open(os.path.join(os.path.dirname(GOLDEN), "kw_multiallelic_examples.txt")) as f:
+        for line in f:
+            if not line.strip() or line.startswith("#"):
+                continue
+            vals, codes, mc, frac, df, d = line.rstrip("\n").split("\t")
+            rows.append((np.array([float(v) for v in vals.split(",")], dtype=np.float32),
+                         np.array([int(c) for c in codes.split(",")], dtype=np.int8), int(mc),
+                         Fraction(frac), int(df), [int(v) for v in d.split(",")]))
+    return rows
+
+
+@pytest.mark.parametrize("case", range(4))
+def test_multiallelic_worked_examples(oracle_mod, case):
+    x, g, mc, H, df, d = _load_multi()[case]
+    r = oracle_mod.kw_pair(x, g, max_code=mc)
+    assert r["df"] == df and r["d"] == d
+    assert r["H"] == pytest.approx(float(H), rel=1e-13, abs=1e-13)
+    assert r["p"] == pytest.approx(_mp_tail(H, df), rel=1e-12)
+
+
+@pytest.mark.parametrize("df", range(1, 9))
+def test_chi2_tail_all_df(oracle_mod, df):
+    """Closed forms of Q(df/2, H/2) against scipy's chi2.sf and gammaincc."""
+    for H in [1e-6, 0.3, 1.0, 4.7, 12.0, 31.5, 80.0, 300.0]:
+        want = st.chi2.sf(H, df)
+        assert oracle_mod.chi2_upper(H, df) == pytest.approx(want, rel=1e-11, abs=1e-300)
+        assert oracle_mod.chi2_upper(H, df) == pytest.approx(sps.gammaincc(df / 2, H / 2), rel=1e-11,
+                                                             abs=1e-300)
+
+
+@pytest.mark.parametrize("mc", [3, 4])
+def test_multiallelic_matches_scipy(oracle_mod, mc):
+    rng = np.random.default_rng(100 + mc)
+    checked = 0
+    for j in range(60):
+        n = int(rng.integers(8, 90))
+        x = np.round(rng.standard_normal(n), j % 3).astype(np.float32)
+        g = rng.integers(0, mc + 1, n).astype(np.int8)
+        if j % 2:
+            x[rng.random(n) < 0.1] = np.nan
+            g[rng.random(n) < 0.1] = -1
+        use = (g >= 0) & ~np.isnan(x)
+        groups = [x[use & (g == k)].astype(np.float64) for k in range(mc + 1)]
+        groups = [a for a in groups if a.size]
+        if len(groups) < 2 or np.unique(np.concatenate(groups)).size < 2:
+            continue
+        s = st.kruskal(*groups)
+        r = oracle_mod.kw_pair(x, g, max_code=mc)
+        assert r["df"] == len(groups) - 1
+        assert r["H"] == pytest.approx(s.statistic, rel=1e-9)
+        assert r["p"] == pytest.approx(s.pvalue, rel=1e-9)
+        assert r["H_alt"] == pytest.approx(r["H"], rel=1e-11, abs=1e-11)
+        checked += 1
+    assert checked > 40
+
+
+def test_multiallelic_exhaustive_permutation_mean(oracle_mod):
+    """Four groups, N = 7 with ties: over all 7! relabellings the mean H is k - 1 = 3."""
+    x = np.array([1, 2, 2, 3, 5, 5, 8], dtype=np.float32)
+    g = np.array([0, 0, 1, 1, 2, 3, 3], dtype=np.int8)
+    perms = np.array(list(itertools.permutations(range(7))), dtype=np.int64)
+    r = oracle_mod.scan(x[None, :], g[perms].astype(np.int8), 0.05, max_code=3)
+    assert np.all(r["df"][0] == 3)
+    assert r["H"][0].mean() == pytest.approx(3.0, rel=1e-12)
+
+
+def test_biallelic_data_gives_the_same_results_as_multiallelic_mode(oracle_mod):
+    d = synth.config(1, T=6, S=40, seed=5)
+    a = oracle_mod.scan(d["expr"], d["geno"], 1e-3)
+    b = oracle_mod.scan(d["expr"], d["geno"], 1e-3, max_code=4)
+    assert np.array_equal(a["H"], b["H"]) and np.array_equal(a["p"], b["p"])
+    assert np.array_equal(a["d"], b["d"][..., :3]) and np.all(b["d"][..., 3:] == 0)

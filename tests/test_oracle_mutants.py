@@ -23,7 +23,11 @@ MUTANTS = {
     "rank_off_by_one": ("(int64_t)(i + j + 2)", "(int64_t)(i + j + 1)"),
     "tie_sum_t2": ("ts += t * t * t - t;", "ts += t * t - t;"),
     "df_not_minus_one": ("out->df = groups > 0 ? groups - 1 : 0;", "out->df = groups;"),
-    "tails_swapped": ("if (df == 1) return erfc(sqrt(0.5 * H));", "if (df == 1) return exp(-0.5 * H);"),
+    "tails_swapped": ("if (df % 2 == 0) {", "if (df % 2 == 1) {"),
+    "odd_tail_sum_dropped": ("q += exp(-x) * xp / g;", "q += 0.0 * xp / g;"),
+    "even_tail_one_term": ("for (int k = 0; k < df / 2; ++k) {", "for (int k = 0; k < 1; ++k) {"),
+    "groups_past_two_ignored": ("  int groups = 0;\n  for (int i = 0; i <= lmax; ++i) {",
+                                "  int groups = 0;\n  for (int i = 0; i < 3 && i <= lmax; ++i) {"),
     "nan_not_dropped": ("!isnan(x[k])) ? 1 : 0;", "1) ? 1 : 0;"),
     "descending_ranks": ("if (x->v < y->v) return -1;\n  if (x->v > y->v) return 1;",
                          "if (x->v > y->v) return -1;\n  if (x->v < y->v) return 1;"),
@@ -35,8 +39,8 @@ MUTANTS = {
 class _Pair(ctypes.Structure):
     _fields_ = [("H", ctypes.c_double), ("H_alt", ctypes.c_double),
                 ("p", ctypes.c_double), ("tie", ctypes.c_double),
-                ("rank2", ctypes.c_int64 * 3), ("d", ctypes.c_int64 * 3),
-                ("n", ctypes.c_int32 * 3), ("K", ctypes.c_int32),
+                ("rank2", ctypes.c_int64 * 5), ("d", ctypes.c_int64 * 5),
+                ("n", ctypes.c_int32 * 5), ("K", ctypes.c_int32),
                 ("df", ctypes.c_int32), ("hit", ctypes.c_int32)]
 
 
@@ -49,14 +53,17 @@ def _compile(src_text, tmp_path, name):
     lib.oracle_pair.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_double,
                                 ctypes.POINTER(_Pair)]
     lib.oracle_pair.restype = ctypes.c_int
+    lib.oracle_pair_l.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                  ctypes.c_double, ctypes.POINTER(_Pair)]
+    lib.oracle_pair_l.restype = ctypes.c_int
     return lib
 
 
-def _pair(lib, x, g, pthresh=0.05):
+def _pair(lib, x, g, pthresh=0.05, max_code=2):
     x = np.ascontiguousarray(x, np.float32)
     g = np.ascontiguousarray(g, np.int8)
     r = _Pair()
-    lib.oracle_pair(x.ctypes.data, g.ctypes.data, x.size, pthresh, ctypes.byref(r))
+    lib.oracle_pair_l(x.ctypes.data, g.ctypes.data, x.size, max_code, pthresh, ctypes.byref(r))
     return r
 
 
@@ -64,7 +71,7 @@ def _pins_fail(lib):
     """Returns the name of the first failing pin, or None."""
     for i, (x, g, H, df, d) in enumerate(_load_golden()):
         r = _pair(lib, x, g)
-        if r.df != df or list(r.d) != d:
+        if r.df != df or list(r.d)[:3] != d:
             return f"golden{i}:df/d"
         if not np.isclose(r.H, float(H), rtol=1e-12, atol=1e-12):
             return f"golden{i}:H"
@@ -74,23 +81,24 @@ def _pins_fail(lib):
         if bool(_pair(lib, x, g, 0.3).hit) != hit_expected:
             return f"golden{i}:hit"
     rng = np.random.default_rng(77)
-    for j in range(30):
+    for j in range(45):
+        mc = 2 if j < 30 else 3 + (j % 2)  # the last cases: markers with 4 or 5 groups
         n = int(rng.integers(6, 80))
         x = np.round(rng.standard_normal(n), j % 3).astype(np.float32)
-        g = rng.integers(0, 3, n).astype(np.int8)
+        g = rng.integers(0, mc + 1, n).astype(np.int8)
         if j % 2:
             x[rng.random(n) < 0.1] = np.nan
             g[rng.random(n) < 0.1] = -1
         use = (g >= 0) & ~np.isnan(x)
-        groups = [x[use & (g == k)].astype(np.float64) for k in range(3)]
+        groups = [x[use & (g == k)].astype(np.float64) for k in range(mc + 1)]
         groups = [a for a in groups if a.size]
         if len(groups) < 2:
             continue
         s = st.kruskal(*groups)
-        r = _pair(lib, x, g, pthresh=s.pvalue * 1.5)
+        r = _pair(lib, x, g, pthresh=s.pvalue * 1.5, max_code=mc)
         if not (np.isclose(r.H, s.statistic, rtol=1e-9) and np.isclose(r.p, s.pvalue, rtol=1e-9)):
             return f"scipy{j}"
-        if not r.hit or _pair(lib, x, g, pthresh=s.pvalue * 0.5).hit:
+        if not r.hit or _pair(lib, x, g, pthresh=s.pvalue * 0.5, max_code=mc).hit:
             return f"hit{j}"
     return None
 
