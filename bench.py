@@ -367,7 +367,9 @@ def run_scan_only(args):
     """Profiling driver: the fused scan kernel alone, `reps` calls on one seeded
     input (T traits x S SNPs x 102 samples), one text line per call.  data=hwe:
     HWE genotypes (MAF 0.05-0.5) and log-normal expression, almost no hits;
-    data=paper: the paper-scale workload's generator at these sizes."""
+    data=paper: the paper-scale workload's generator at these sizes; data=multi:
+    markers with 2..5 genotype groups (codes 0..4; 4N flop per pair counted as for
+    biallelic markers, the contraction itself does 8N)."""
     import torch
     from paper_1307_3519_gb300 import build as kbuild
     kbuild.build()
@@ -375,9 +377,15 @@ def run_scan_only(args):
     import synth
     T, S = args.traits, args.snps
     # the autotuner runs first (as in the benchmark) unless --no-autotune
+    multi = args.data == "multi"
     if args.data == "paper":
         d = synth.config(2, T=T, S=S)
         geno, expr, pth = d["geno"], d["expr"], d["pthresh"]
+    elif multi:  # markers with 2..5 genotype groups (codes 0..4)
+        rng = np.random.default_rng(3)
+        geno = synth.multiallelic_genotypes(rng, S, 102)
+        expr = synth.expression_lognormal(rng, T, 102)
+        pth = 1e-5
     else:
         rng = np.random.default_rng(1)
         geno, _ = synth.hwe_genotypes(rng, S, 102, 0.05, 0.5)
@@ -387,10 +395,12 @@ def run_scan_only(args):
     rs = kx.krux_rank(torch.from_numpy(expr).cuda())
     g = torch.from_numpy(geno).cuda()
     if not args.no_autotune:  # the launch shape the benchmark uses
-        print(f"scan-only autotuned shape (layout, nc, nA, ka) = {kx.autotune(rs, g, pth)}", flush=True)
+        if not multi:  # the autotuner times the biallelic form
+            print(f"scan-only autotuned shape (layout, nc, nA, ka) = {kx.autotune(rs, g, pth)}",
+                  flush=True)
     kx.set_profiling(True)
     for i in range(args.reps):
-        r = kx.krux_scan(rs, g, pth, capacity=min(50_000_000, T * S))
+        r = kx.krux_scan(rs, g, pth, capacity=min(50_000_000, T * S), multiallelic=multi)
         pr = kx.profile()
         fl = 4.0 * 102 * T * S
         print(f"scan-only data={args.data} T={T} S={S} call={i} hits={r['n_hits']} "
@@ -410,7 +420,7 @@ def main():
                     help="profiling driver: only the fused scan, --reps calls, text output")
     ap.add_argument("--traits", type=int, default=20000)
     ap.add_argument("--snps", type=int, default=100000)
-    ap.add_argument("--data", default="hwe", choices=["hwe", "paper"])
+    ap.add_argument("--data", default="hwe", choices=["hwe", "paper", "multi"])
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--no-autotune", action="store_true",
                     help="scan-only: the automatic launch shape instead of the autotuner's")

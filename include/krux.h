@@ -52,6 +52,18 @@ typedef struct {
   int32_t d1;
 } krux_hit;
 
+/* krux_opts.flags bits.
+ * KRUX_FLAG_MULTIALLELIC: genotype codes 0..4 (section "Input data": markers take
+ *   values 0..l with any number of alleles, also varying between markers; here
+ *   l <= 4, so up to five genotype groups and df up to 4; the chi-square tail of
+ *   df 3 and 4 is computed in closed form).  Without it codes must be in
+ *   {-1, 0, 1, 2}.  The flag works with krux_scan, krux_scan_cis,
+ *   krux_scan_grouped and their graphs, on complete expression (no NaN) without
+ *   dense output; permutation batches and the plain form take biallelic markers
+ *   only (KRUX_EUNSUPPORTED).  Biallelic data scanned with the flag give the same
+ *   hits, H and p. */
+#define KRUX_FLAG_MULTIALLELIC 1
+
 /* Scan options (section "P-value calculation and empirical FDR correction": the
  * threshold P_c; section "Data slicing": a slice of markers starting at a given
  * marker). */
@@ -63,7 +75,7 @@ typedef struct {
   double *dense_H;         /* optional device [T][snp_end-snp_begin] FP64 H of every pair, NULL = off */
   double *dense_p;         /* optional device, same layout, FP64 p of every pair */
   double recheck_margin;   /* relative band around the threshold decided in FP64; <= 0 -> 1e-4 */
-  int32_t flags;           /* reserved, must be 0 */
+  int32_t flags;           /* KRUX_FLAG_* bits, 0 = none */
   int32_t reserved_;
 } krux_opts;
 

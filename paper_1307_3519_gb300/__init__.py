@@ -19,6 +19,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libkrux.so")
 
 KRUX_OK, KRUX_EINVAL, KRUX_ENOMEM, KRUX_ECUDA, KRUX_EOVERFLOW, KRUX_ETIMEOUT, KRUX_EUNSUPPORTED = range(7)
+KRUX_FLAG_MULTIALLELIC = 1  # genotype codes 0..4
 STATUS_NAMES = ["KRUX_OK", "KRUX_EINVAL", "KRUX_ENOMEM", "KRUX_ECUDA", "KRUX_EOVERFLOW",
                 "KRUX_ETIMEOUT", "KRUX_EUNSUPPORTED"]
 
@@ -243,7 +244,7 @@ class Krux:
                                                  _stream(stream)), "krux_rankset_export")
         return c, tie, K
 
-    def _opts(self, pthresh, capacity, snp_begin=0, snp_end=0, dense=None, margin=0.0):
+    def _opts(self, pthresh, capacity, snp_begin=0, snp_end=0, dense=None, margin=0.0, flags=0):
         o = Opts()
         o.pthresh = pthresh
         o.hit_capacity = capacity
@@ -252,10 +253,11 @@ class Krux:
         o.dense_H = dense[0].data_ptr() if dense is not None else None
         o.dense_p = dense[1].data_ptr() if dense is not None else None
         o.recheck_margin = margin
-        o.flags = 0
+        o.flags = flags
         return o
 
-    def _scan(self, fn, rs, geno, pthresh, capacity, snp_begin, snp_end, dense, margin, stream):
+    def _scan(self, fn, rs, geno, pthresh, capacity, snp_begin, snp_end, dense, margin, stream,
+              flags=0):
         import torch
         assert geno.is_cuda and geno.dtype == torch.int8 and geno.dim() == 2 and geno.stride(1) == 1
         S = geno.shape[0]
@@ -267,7 +269,7 @@ class Krux:
         if dense:
             dn = (torch.empty((rs.T, e - snp_begin), dtype=torch.float64, device=self.device),
                   torch.empty((rs.T, e - snp_begin), dtype=torch.float64, device=self.device))
-        o = self._opts(pthresh, capacity, snp_begin, snp_end, dn, margin)
+        o = self._opts(pthresh, capacity, snp_begin, snp_end, dn, margin, flags)
         n = ctypes.c_int64()
         st = fn(self.handle, rs.handle, _ptr(geno), S, geno.stride(0), ctypes.byref(o), _ptr(hits),
                 _ptr(H), _ptr(P), ctypes.byref(n), _stream(stream))
@@ -279,17 +281,19 @@ class Krux:
         return out
 
     def krux_scan(self, rs, geno, pthresh, capacity, snp_begin=0, snp_end=0, dense=False,
-                  margin=0.0, stream=None):
+                  margin=0.0, stream=None, multiallelic=False):
         """Fused scan.  Returns dict(n_hits, overflow, hits int32 [k,4] (trait, snp,
-        d0, d1), H, p float64 [k], and dense_H / dense_p [T, S] if dense)."""
+        d0, d1), H, p float64 [k], and dense_H / dense_p [T, S] if dense).
+        multiallelic: genotype codes 0..4 (KRUX_FLAG_MULTIALLELIC)."""
         return self._scan(self.lib.krux_scan, rs, geno, pthresh, capacity, snp_begin, snp_end,
-                          dense, margin, stream)
+                          dense, margin, stream, KRUX_FLAG_MULTIALLELIC if multiallelic else 0)
 
-    def krux_scan_cis(self, rs, geno, snp_pos, trait_pos, window, pthresh, capacity, stream=None):
+    def krux_scan_cis(self, rs, geno, snp_pos, trait_pos, window, pthresh, capacity, stream=None,
+                      multiallelic=False):
         """cis scan: only pairs with |snp_pos - trait_pos| <= window (int64 device
         coordinates, nondecreasing).  Returns the result dict of krux_scan."""
         hits, H, P = self._outputs(capacity)
-        o = self._opts(pthresh, capacity)
+        o = self._opts(pthresh, capacity, flags=KRUX_FLAG_MULTIALLELIC if multiallelic else 0)
         n = ctypes.c_int64()
         st = self.lib.krux_scan_cis(self.handle, rs.handle, _ptr(geno), geno.shape[0], geno.stride(0),
                                     _ptr(snp_pos), _ptr(trait_pos), int(window), ctypes.byref(o),
@@ -330,7 +334,7 @@ class Krux:
         return dict(minp=minp, n_hits=n.value, overflow=st == KRUX_EOVERFLOW, hits=hits[:k],
                     H=H[:k], p=Pv[:k], fdr_hist=hist)
 
-    def krux_scan_grouped(self, cohorts, pthresh, stream=None):
+    def krux_scan_grouped(self, cohorts, pthresh, stream=None, multiallelic=False):
         """cohorts: list of dict(rs, geno, capacity).  Returns a list of result dicts."""
         import torch
         arr = (Cohort * len(cohorts))()
@@ -350,7 +354,7 @@ class Krux:
             arr[i].hit_H = H.data_ptr()
             arr[i].hit_p = P.data_ptr()
             arr[i].hit_capacity = cap
-        o = self._opts(pthresh, 0)
+        o = self._opts(pthresh, 0, flags=KRUX_FLAG_MULTIALLELIC if multiallelic else 0)
         st = self.lib.krux_scan_grouped(self.handle, arr, len(cohorts), ctypes.byref(o), _stream(stream))
         self._check(st, "krux_scan_grouped")
         out = []
@@ -377,7 +381,7 @@ class Krux:
                 torch.empty(max(capacity, 1), dtype=torch.float64, device=self.device),
                 torch.empty(max(capacity, 1), dtype=torch.float64, device=self.device))
 
-    def graph_scan(self, rs, geno, pthresh, capacity, dense=False):
+    def graph_scan(self, rs, geno, pthresh, capacity, dense=False, multiallelic=False):
         """krux_scan captured as a CUDA graph; returns a Graph (launch / wait)."""
         import torch
         hits, H, P = self._outputs(capacity)
@@ -385,7 +389,8 @@ class Krux:
         if dense:
             dn = (torch.empty((rs.T, geno.shape[0]), dtype=torch.float64, device=self.device),
                   torch.empty((rs.T, geno.shape[0]), dtype=torch.float64, device=self.device))
-        o = self._opts(pthresh, capacity, dense=dn)
+        o = self._opts(pthresh, capacity, dense=dn,
+                       flags=KRUX_FLAG_MULTIALLELIC if multiallelic else 0)
         h = ctypes.c_void_p()
         st = self.lib.krux_graph_scan(self.handle, rs.handle, _ptr(geno), geno.shape[0], geno.stride(0),
                                       ctypes.byref(o), _ptr(hits), _ptr(H), _ptr(P), ctypes.byref(h))
@@ -415,7 +420,7 @@ class Krux:
         g.minp, g.fdr_hist = minp, hist
         return g
 
-    def graph_grouped(self, cohorts, pthresh):
+    def graph_grouped(self, cohorts, pthresh, multiallelic=False):
         """krux_scan_grouped captured as a CUDA graph; cohorts as for krux_scan_grouped."""
         arr = (Cohort * len(cohorts))()
         outs = []
@@ -431,7 +436,7 @@ class Krux:
             arr[i].hit_H = H.data_ptr()
             arr[i].hit_p = P.data_ptr()
             arr[i].hit_capacity = c["capacity"]
-        o = self._opts(pthresh, 0)
+        o = self._opts(pthresh, 0, flags=KRUX_FLAG_MULTIALLELIC if multiallelic else 0)
         h = ctypes.c_void_p()
         st = self.lib.krux_graph_grouped(self.handle, arr, len(cohorts), ctypes.byref(o), ctypes.byref(h))
         self._check(st, "krux_graph_grouped")

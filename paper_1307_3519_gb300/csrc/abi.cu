@@ -20,8 +20,13 @@ using namespace krux;
 
 namespace krux {
 cudaError_t launch_missing_scan(const int8_t *geno, int64_t ldg, int N, int64_t snp_begin,
-                                int64_t n_snps, unsigned int *n_missing, int64_t *miss_idx,
-                                uint64_t *miss_mask, unsigned int *status, cudaStream_t s);
+                                int64_t n_snps, int max_code, unsigned int *n_missing,
+                                int64_t *miss_idx, uint64_t *miss_mask, unsigned int *status,
+                                cudaStream_t s);
+cudaError_t launch_pack_multi(const int8_t *geno, int64_t ldg, int N, int Np,
+                              const int64_t *snp_list, int64_t snp_begin, int64_t n_snps,
+                              const double *h, int allow_missing, __half *B, ChunkMetaM *meta,
+                              unsigned int *status, cudaStream_t s);
 cudaError_t launch_pack2(const int8_t *geno, int64_t ldg, int N, int Np, const int64_t *snp_list,
                          int64_t snp_begin, int64_t n_snps, int64_t snp_out_base, double h1,
                          double h2, int allow_missing, int signed_df1, __half *B,
@@ -95,6 +100,30 @@ double h_df1(double p) {
 }
 double h_df2(double p) { return -2.0 * std::log(p); }
 
+// Upper chi-square tail for df = 1..4 from the closed forms of Q(df/2, h/2).
+double chi2_tail_host(double h, int df) {
+  const double x = 0.5 * h;
+  if (!(x > 0.0)) return 1.0;
+  switch (df) {
+    case 1: return std::erfc(std::sqrt(x));
+    case 2: return std::exp(-x);
+    case 3: return std::erfc(std::sqrt(x)) + 2.0 * std::sqrt(x / M_PI) * std::exp(-x);
+    default: return std::exp(-x) * (1.0 + x);
+  }
+}
+
+// Threshold h_d with P(chi2_d > h_d) = p, d = 1..4 (d = 1, 2 in closed form).
+double h_dfk(double p, int df) {
+  if (df == 1) return h_df1(p);
+  if (df == 2) return h_df2(p);
+  double lo = 0.0, hi = 4000.0;  // the tail is decreasing in h
+  for (int i = 0; i < 300; ++i) {
+    const double mid = 0.5 * (lo + hi);
+    if (chi2_tail_host(mid, df) > p) lo = mid; else hi = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
 }  // namespace
 
 struct krux_rankset {
@@ -117,7 +146,7 @@ struct krux_ctx {
   PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   cudaEvent_t ev[kEv] = {};
   DevBuf B, meta, codes, groups, items, status, counters, aux, cfacptr, miss_idx, miss_mask,
-      list, gemm_out, bucket_ranks, permA, minpkey, seg, permNan;
+      list, gemm_out, bucket_ranks, permA, minpkey, seg, permNan, aux2;
   void *blas = nullptr;
   std::vector<std::pair<size_t, void *>> pool;  // freed rank-set blocks, reused by size
   std::map<int, std::array<int, 4>> tuned;       // krux_autotune: K width -> layout, nc, nA, ka
@@ -367,7 +396,9 @@ krux_status check_opts(krux_ctx *ctx, const krux_opts *o) {
   if (!o) return fail(ctx, KRUX_EINVAL, "opts is NULL");
   if (!(o->pthresh > 0.0 && o->pthresh < 1.0)) return fail(ctx, KRUX_EINVAL, "pthresh must be in (0,1)");
   if (o->hit_capacity < 0) return fail(ctx, KRUX_EINVAL, "hit_capacity < 0");
-  if (o->flags != 0) return fail(ctx, KRUX_EINVAL, "flags must be 0");
+  if ((o->flags & ~KRUX_FLAG_MULTIALLELIC) != 0) return fail(ctx, KRUX_EINVAL, "unknown flags");
+  if ((o->flags & KRUX_FLAG_MULTIALLELIC) && o->dense_H)
+    return fail(ctx, KRUX_EINVAL, "dense output is not available for markers with codes 0..4");
   if ((o->dense_H == nullptr) != (o->dense_p == nullptr))
     return fail(ctx, KRUX_EINVAL, "dense_H and dense_p must both be set or both NULL");
   return KRUX_OK;
@@ -431,7 +462,7 @@ void krux_destroy(krux_ctx *ctx) {
   DevBuf *bufs[] = {&ctx->B, &ctx->meta, &ctx->codes, &ctx->groups, &ctx->items, &ctx->status,
                     &ctx->counters, &ctx->aux, &ctx->cfacptr, &ctx->miss_idx, &ctx->miss_mask,
                     &ctx->list, &ctx->gemm_out, &ctx->bucket_ranks, &ctx->permA, &ctx->minpkey, &ctx->seg,
-                    &ctx->permNan};
+                    &ctx->permNan, &ctx->aux2};
   for (DevBuf *b : bufs) b->release();
   for (auto &pb : ctx->pool) cudaFree(pb.second);
   for (int i = 0; i < kEv; ++i)
@@ -569,7 +600,7 @@ struct Bucket {
 // {-1,0,1,2}.  Synchronises the stream.
 krux_status find_missing(krux_ctx *ctx, const int8_t *geno, int64_t ldg, int N, int64_t b,
                          int64_t n, cudaStream_t s, std::vector<Bucket> &buckets,
-                         std::vector<int64_t> &complete, bool &bad) {
+                         std::vector<int64_t> &complete, bool &bad, int max_code) {
   KRUX_CUDA(ctx, ctx->status.ensure(64));
   KRUX_CUDA(ctx, ctx->counters.ensure(64));
   KRUX_CUDA(ctx, ctx->miss_idx.ensure((size_t)std::max<int64_t>(n, 1) * 8));
@@ -577,7 +608,7 @@ krux_status find_missing(krux_ctx *ctx, const int8_t *geno, int64_t ldg, int N, 
   KRUX_CUDA(ctx, cudaMemsetAsync(ctx->status.p, 0, 64, s));
   KRUX_CUDA(ctx, cudaMemsetAsync(ctx->counters.p, 0, 64, s));
   unsigned int *cnt = ctx->counters.as<unsigned int>();
-  KRUX_CUDA(ctx, launch_missing_scan(geno, ldg, N, b, n, cnt, ctx->miss_idx.as<int64_t>(),
+  KRUX_CUDA(ctx, launch_missing_scan(geno, ldg, N, b, n, max_code, cnt, ctx->miss_idx.as<int64_t>(),
                                      ctx->miss_mask.as<uint64_t>(), ctx->status.as<unsigned int>(), s));
   if (ctx->profiling) ctx->prof.launches += 1;
   unsigned int m32 = 0, st = 0;
@@ -637,6 +668,7 @@ struct OutSlot {
   double *H = nullptr, *P = nullptr;
   int64_t capacity = 0;
   HitAux *aux = nullptr;
+  HitAux2 *aux2 = nullptr;  // markers with more than three groups (set by prepare_fused)
 };
 
 struct ScanGroupIn {
@@ -684,6 +716,7 @@ struct CallPlan {
     uint16_t *lists = nullptr;   // [1 + P][T][N] NaN sample lists (rank sets with NaN)
     int32_t *inv = nullptr;      // [P][N] inverse permutations
   } perm;
+  bool multi = false;  // markers with codes 0..4 (chunks of kChunkSnpsM SNPs)
   struct Cis {  // cis scans: SNP and trait coordinates (host copies) and the window
     bool on = false;
     const int64_t *snp_pos = nullptr, *trait_pos = nullptr;  // device
@@ -721,9 +754,14 @@ krux_status plan_groups(krux_ctx *ctx, CallPlan &cp, const krux_rankset *rs, con
   std::vector<Bucket> buckets;
   std::vector<int64_t> complete;
   bool bad = false;
-  krux_status st = find_missing(ctx, geno, ldg, rs->N, b, n, s, buckets, complete, bad);
+  krux_status st =
+      find_missing(ctx, geno, ldg, rs->N, b, n, s, buckets, complete, bad, cp.multi ? kMaxCodeM : 2);
   if (st != KRUX_OK) return st;
-  if (bad) return fail(ctx, KRUX_EINVAL, "genotype code outside {-1,0,1,2}");
+  if (bad)
+    return fail(ctx, KRUX_EINVAL, cp.multi ? "genotype code outside {-1, 0..4}"
+                                           : "genotype code outside {-1,0,1,2}");
+  if (cp.multi && rs->has_nan)
+    return fail(ctx, KRUX_EUNSUPPORTED, "markers with more than three groups need complete expression");
   if (!buckets.empty() && n_agroups > 1)
     return fail(ctx, KRUX_EUNSUPPORTED, "permutation scan with missing genotypes");
   ScanGroupIn g0;
@@ -853,8 +891,9 @@ std::vector<WorkItem> make_items_cis(const CallPlan &cp, const std::vector<Group
       return g.list_off >= 0 ? cp.lists[(size_t)(g.list_off + i)] : g.snp_begin + i;
     };
     for (int64_t b = 0; b < gp[gi].n_btiles; ++b) {
-      const int64_t first = b * d.nc * kChunkSnps;
-      const int64_t last = std::min<int64_t>((b + 1) * d.nc * kChunkSnps, g.n_snps) - 1;
+      const int64_t csn = cp.multi ? kChunkSnpsM : kChunkSnps;
+      const int64_t first = b * d.nc * csn;
+      const int64_t last = std::min<int64_t>((b + 1) * d.nc * csn, g.n_snps) - 1;
       if (first > last) continue;
       const int64_t lo = cp.cis.h_snp[(size_t)snp_at(first)] - W;
       const int64_t hi = cp.cis.h_snp[(size_t)snp_at(last)] + W;
@@ -888,6 +927,7 @@ struct FusedLaunch {
   int signed_coef = 0;
   std::vector<int64_t> boff, moff, coff;
   int layout = 1;
+  double hm[4] = {0.0, 0.0, 0.0, 0.0};  // markers with codes 0..4: h_d for d = 1..4
 };
 
 krux_status prepare_fused(krux_ctx *ctx, CallPlan &cp, const krux_opts *o, FusedLaunch &fl,
@@ -945,7 +985,8 @@ krux_status prepare_fused(krux_ctx *ctx, CallPlan &cp, const krux_opts *o, Fused
   fl.coff.assign(ng, 0);
   int64_t btot = 0, mtot = 0, ctot = 0;
   for (int i = 0; i < ng; ++i) {
-    const int64_t nch = (cp.groups[i].n_snps + kChunkSnps - 1) / kChunkSnps;
+    const int64_t csn = cp.multi ? kChunkSnpsM : kChunkSnps;
+    const int64_t nch = (cp.groups[i].n_snps + csn - 1) / csn;
     fl.boff[i] = btot;
     fl.moff[i] = mtot;
     fl.coff[i] = ctot;
@@ -954,6 +995,15 @@ krux_status prepare_fused(krux_ctx *ctx, CallPlan &cp, const krux_opts *o, Fused
     if (cp.groups[i].nan_cnt) ctot += nch * cp.groups[i].rs->Np * 2;
   }
   KRUX_CUDA(ctx, ctx->B.ensure(std::max<int64_t>(btot, 256)));
+  if (cp.multi) {  // second side records, at the same offsets as the first
+    const HitAux *base = ctx->aux.as<HitAux>();
+    int64_t total = 1;
+    for (auto &os : cp.slots)
+      total = std::max<int64_t>(total, (int64_t)(os.aux - base) + std::max<int64_t>(os.capacity, 1));
+    KRUX_CUDA(ctx, ctx->aux2.ensure((size_t)total * sizeof(HitAux2)));
+    for (auto &os : cp.slots) os.aux2 = ctx->aux2.as<HitAux2>() + (os.aux - base);
+    for (int d = 1; d <= 4; ++d) fl.hm[d - 1] = h_dfk(o->pthresh, d);
+  }
   KRUX_CUDA(ctx, ctx->meta.ensure(std::max<int64_t>(mtot, 1) * sizeof(ChunkMeta)));
   KRUX_CUDA(ctx, ctx->codes.ensure(std::max<int64_t>(ctot, 1) * 8));
   std::vector<GroupDesc> descs(ng);
@@ -966,7 +1016,8 @@ krux_status prepare_fused(krux_ctx *ctx, CallPlan &cp, const krux_opts *o, Fused
     __half *B = reinterpret_cast<__half *>(ctx->B.as<char>() + fl.boff[i]);
     GroupDesc &d = plans[i].d;
     std::memset(&d, 0, sizeof d);
-    const int64_t nch = (g.n_snps + kChunkSnps - 1) / kChunkSnps;
+    const int64_t csn = cp.multi ? kChunkSnpsM : kChunkSnps;
+    const int64_t nch = (g.n_snps + csn - 1) / csn;
     krux_status st =
         encode_map(ctx, &d.tmA, g.A, rs->Np, (int64_t)rs->rows_pad * g.n_agroups, layout);
     if (st != KRUX_OK) return st;
@@ -982,6 +1033,7 @@ krux_status prepare_fused(krux_ctx *ctx, CallPlan &cp, const krux_opts *o, Fused
     d.tile_nan = g.tile_nan;
     d.hits = os.hits;
     d.aux = os.aux;
+    d.aux2 = os.aux2;
     d.counter = ctx->counters.as<unsigned long long>() + g.out_slot;
     d.capacity = os.capacity;
     d.dense_H = g.dense_H;
@@ -1044,6 +1096,7 @@ krux_status prepare_fused(krux_ctx *ctx, CallPlan &cp, const krux_opts *o, Fused
   p.fdr_bins = cp.fdr_bins;
   p.fdr_l0 = cp.fdr_l0;
   p.fdr_w = cp.fdr_w;
+  p.multi = cp.multi ? 1 : 0;
   if (cp.cis.on) {
     p.cis_snp_pos = cp.cis.snp_pos;
     p.cis_trait_pos = cp.cis.trait_pos;
@@ -1058,12 +1111,15 @@ krux_status prepare_fused(krux_ctx *ctx, CallPlan &cp, const krux_opts *o, Fused
     const int64_t cap = cp.slots[0].capacity;
     const int seg_cap = (int)std::max<int64_t>(64, std::min<int64_t>(4096, 2 * cap / fl.n_seg + 64));
     const size_t rec = sizeof(krux_hit) + sizeof(HitAux);
-    KRUX_CUDA(ctx, ctx->seg.ensure((size_t)fl.n_seg * seg_cap * rec + (size_t)fl.n_seg * 4 + 256));
+    const size_t a2off = ((size_t)fl.n_seg * seg_cap * rec + (size_t)fl.n_seg * 4 + 255) / 256 * 256;
+    const size_t a2 = cp.multi ? (size_t)fl.n_seg * seg_cap * sizeof(HitAux2) : 0;
+    KRUX_CUDA(ctx, ctx->seg.ensure(a2off + a2 + 256));
     char *sb = ctx->seg.as<char>();
     p.seg_cap = seg_cap;
     p.seg_hits = reinterpret_cast<krux_hit *>(sb);
     p.seg_aux = reinterpret_cast<HitAux *>(sb + (size_t)fl.n_seg * seg_cap * sizeof(krux_hit));
     p.seg_cnt = reinterpret_cast<unsigned int *>(sb + (size_t)fl.n_seg * seg_cap * rec);
+    if (cp.multi) p.seg_aux2 = reinterpret_cast<HitAux2 *>(sb + a2off);
   }
   fl.smem = scan_smem_bytes2(nc_max, sh.nA, (size_t)p.a_tile_bytes, (size_t)p.b_region, p.kpad);
   const std::string why = validate_plan(p, descs, fl.smem);
@@ -1115,9 +1171,14 @@ krux_status enqueue_fused(krux_ctx *ctx, CallPlan &cp, const FusedLaunch &fl, cu
     __half *B = reinterpret_cast<__half *>(ctx->B.as<char>() + fl.boff[i]);
     ChunkMeta *meta = ctx->meta.as<ChunkMeta>() + fl.moff[i];
     uint64_t *codes = g.nan_cnt ? ctx->codes.as<uint64_t>() + fl.coff[i] : nullptr;
-    KRUX_CUDA(ctx, launch_pack2(g.geno, g.ldg, rs->N, rs->Np, g.snp_list, g.snp_begin, g.n_snps, 0,
-                                fl.h1, fl.h2, g.allow_missing, fl.signed_coef, B, meta, codes,
-                                status, s));
+    if (cp.multi)
+      KRUX_CUDA(ctx, launch_pack_multi(g.geno, g.ldg, rs->N, rs->Np, g.snp_list, g.snp_begin,
+                                       g.n_snps, fl.hm, g.allow_missing, B,
+                                       reinterpret_cast<ChunkMetaM *>(meta), status, s));
+    else
+      KRUX_CUDA(ctx, launch_pack2(g.geno, g.ldg, rs->N, rs->Np, g.snp_list, g.snp_begin, g.n_snps,
+                                  0, fl.h1, fl.h2, g.allow_missing, fl.signed_coef, B, meta, codes,
+                                  status, s));
   }
   ev_record(ctx, 3, s);
   ev_record(ctx, 7, s);  // the scan kernel alone: events 7 .. 4
@@ -1125,9 +1186,10 @@ krux_status enqueue_fused(krux_ctx *ctx, CallPlan &cp, const FusedLaunch &fl, cu
   ev_record(ctx, 4, s);
   unsigned long long *totals = ctx->counters.as<unsigned long long>() + nslots;
   if (fl.staged) {
-    KRUX_CUDA(ctx, launch_seg_compact(fl.p.seg_hits, fl.p.seg_aux, fl.p.seg_cnt, fl.n_seg,
-                                      fl.p.seg_cap, ctx->counters.as<unsigned long long>(),
-                                      cp.slots[0].hits, cp.slots[0].aux, cp.slots[0].capacity,
+    KRUX_CUDA(ctx, launch_seg_compact(fl.p.seg_hits, fl.p.seg_aux, fl.p.seg_aux2, fl.p.seg_cnt,
+                                      fl.n_seg, fl.p.seg_cap,
+                                      ctx->counters.as<unsigned long long>(), cp.slots[0].hits,
+                                      cp.slots[0].aux, cp.slots[0].aux2, cp.slots[0].capacity,
                                       totals, s));
   } else {
     KRUX_CUDA(ctx, cudaMemcpyAsync(totals, ctx->counters.p, (size_t)nslots * 8,
@@ -1138,7 +1200,7 @@ krux_status enqueue_fused(krux_ctx *ctx, CallPlan &cp, const FusedLaunch &fl, cu
   for (int k = 0; k < nslots; ++k) {
     const OutSlot &os = cp.slots[k];
     if (os.capacity <= 0) continue;
-    KRUX_CUDA(ctx, launch_finalize_dev(os.hits, os.aux, totals + k, os.capacity,
+    KRUX_CUDA(ctx, launch_finalize_dev(os.hits, os.aux, os.aux2, totals + k, os.capacity,
                                        ctx->cfacptr.as<const double *>(), os.H, os.P,
                                        ctx->sm_count, s, cp.fdr_hist, cp.fdr_bins, cp.fdr_l0,
                                        cp.fdr_w));
@@ -1236,6 +1298,7 @@ extern "C" krux_status krux_scan(krux_ctx *ctx, const krux_rankset *rs, const in
   }
   KRUX_CUDA(ctx, ctx->aux.ensure((size_t)std::max<int64_t>(opts->hit_capacity, 1) * sizeof(HitAux)));
   CallPlan cp;
+  cp.multi = (opts->flags & KRUX_FLAG_MULTIALLELIC) != 0;
   cp.slots.push_back(OutSlot{hits, hit_H, hit_p, opts->hit_capacity, ctx->aux.as<HitAux>()});
   st = plan_groups(ctx, cp, rs, geno, ldg, b, e, nullptr, 1, 0, opts->dense_H, opts->dense_p,
                    nullptr, s);
@@ -1267,6 +1330,7 @@ extern "C" krux_status krux_scan_cis(krux_ctx *ctx, const krux_rankset *rs, cons
   cudaStream_t s = (cudaStream_t)stream;
   KRUX_CUDA(ctx, cudaSetDevice(ctx->device));
   CallPlan cp;
+  cp.multi = (opts->flags & KRUX_FLAG_MULTIALLELIC) != 0;
   cp.cis.on = true;
   cp.cis.snp_pos = snp_pos;
   cp.cis.trait_pos = trait_pos;
@@ -1327,6 +1391,7 @@ extern "C" krux_status krux_scan_grouped(krux_ctx *ctx, krux_cohort *cohorts, in
   }
   KRUX_CUDA(ctx, ctx->aux.ensure((size_t)std::max<int64_t>(captot, 1) * sizeof(HitAux)));
   CallPlan cp;
+  cp.multi = (opts->flags & KRUX_FLAG_MULTIALLELIC) != 0;
   int64_t aoff = 0;
   for (int c = 0; c < n_cohorts; ++c) {
     krux_cohort &k = cohorts[c];
@@ -1354,6 +1419,8 @@ extern "C" krux_status krux_scan_plain(krux_ctx *ctx, const krux_rankset *rs, co
                                        double *hit_H, double *hit_p, int64_t *n_hits, void *stream) {
   krux_status st = check_scan_args(ctx, rs, geno, S, ldg, opts, hits, hit_H, hit_p, n_hits);
   if (st != KRUX_OK) return st;
+  if (opts->flags & KRUX_FLAG_MULTIALLELIC)
+    return fail(ctx, KRUX_EUNSUPPORTED, "this form takes biallelic markers (codes 0, 1, 2) only");
   *n_hits = 0;
   cudaStream_t s = (cudaStream_t)stream;
   KRUX_CUDA(ctx, cudaSetDevice(ctx->device));
@@ -1367,7 +1434,7 @@ extern "C" krux_status krux_scan_plain(krux_ctx *ctx, const krux_rankset *rs, co
   std::vector<Bucket> buckets;
   std::vector<int64_t> complete;
   bool bad = false;
-  st = find_missing(ctx, geno, ldg, rs->N, b, n, s, buckets, complete, bad);
+  st = find_missing(ctx, geno, ldg, rs->N, b, n, s, buckets, complete, bad, 2);
   if (st != KRUX_OK) return st;
   if (bad) return fail(ctx, KRUX_EINVAL, "genotype code outside {-1,0,1,2}");
   if (!buckets.empty())
@@ -1489,6 +1556,8 @@ extern "C" krux_status krux_permute(krux_ctx *ctx, const krux_rankset *rs, const
                                     void *stream) {
   krux_status st = check_scan_args(ctx, rs, geno, S, ldg, opts, hits, hit_H, hit_p, n_hits);
   if (st != KRUX_OK) return st;
+  if (opts->flags & KRUX_FLAG_MULTIALLELIC)
+    return fail(ctx, KRUX_EUNSUPPORTED, "this form takes biallelic markers (codes 0, 1, 2) only");
   *n_hits = 0;
   if (P < 1 || !perms || !minp) return fail(ctx, KRUX_EINVAL, "need P >= 1, perms and minp");
   if (opts->dense_H) return fail(ctx, KRUX_EINVAL, "dense output is not available with permutations");
@@ -1644,6 +1713,7 @@ extern "C" krux_status krux_graph_scan(krux_ctx *ctx, const krux_rankset *rs, co
   st = graph_begin(ctx, out, g);
   if (st != KRUX_OK) return st;
   g->opts = *opts;
+  g->cp.multi = (opts->flags & KRUX_FLAG_MULTIALLELIC) != 0;
   krux_ctx *w = g->w;
   const int64_t b = opts->snp_begin, e = opts->snp_end > 0 ? opts->snp_end : S;
   if (w->aux.ensure((size_t)std::max<int64_t>(opts->hit_capacity, 1) * sizeof(HitAux)) != cudaSuccess)
@@ -1668,6 +1738,8 @@ extern "C" krux_status krux_graph_permute(krux_ctx *ctx, const krux_rankset *rs,
   int64_t dummy = 0;
   krux_status st = check_scan_args(ctx, rs, geno, S, ldg, opts, hits, hit_H, hit_p, &dummy);
   if (st != KRUX_OK) return st;
+  if (opts->flags & KRUX_FLAG_MULTIALLELIC)
+    return fail(ctx, KRUX_EUNSUPPORTED, "this form takes biallelic markers (codes 0, 1, 2) only");
   if (P < 1 || !perms || !minp) return fail(ctx, KRUX_EINVAL, "need P >= 1, perms and minp");
   if (opts->dense_H) return fail(ctx, KRUX_EINVAL, "dense output is not available with permutations");
   if (fdr_hist && (fdr_bins < 1 || !(fdr_bin_width > 0.0)))
@@ -1703,6 +1775,7 @@ extern "C" krux_status krux_graph_grouped(krux_ctx *ctx, const krux_cohort *coho
   st = graph_begin(ctx, out, g);
   if (st != KRUX_OK) return st;
   g->opts = *opts;
+  g->cp.multi = (opts->flags & KRUX_FLAG_MULTIALLELIC) != 0;
   krux_ctx *w = g->w;
   if (w->aux.ensure((size_t)std::max<int64_t>(captot, 1) * sizeof(HitAux)) != cudaSuccess)
     return graph_fail(ctx, g, fail(ctx, KRUX_ENOMEM, "graph workspace"));

@@ -46,10 +46,34 @@ struct ChunkMeta {
 };
 static_assert(sizeof(ChunkMeta) == 1536, "ChunkMeta must be 1536 bytes");
 
+// ---- markers with up to five genotype groups (section "Input data": values
+// 0..l, any number of alleles, also varying between markers) ------------------
+// A chunk holds 32 SNPs: rows [32i, 32i + 32) = I_i (i = 0..3) of SNPs 32c ..
+// 32c + 31; group 4 is implicit (D_4 = -(D_0 + D_1 + D_2 + D_3), because the
+// centred ranks of the present samples sum to zero).
+constexpr int kMaxCodeM = 4;      // largest genotype code
+constexpr int kChunkSnpsM = 32;   // SNPs per chunk
+constexpr int kEpiSnpsM = 8;      // SNPs of a chunk each epilogue warp evaluates
+struct ChunkMetaM {               // the same shared-memory slot as ChunkMeta
+  float coef[kMaxCodeM + 1][kChunkSnpsM];    // (1 / N_i) / h_df, 0 for empty groups
+  int32_t snp[kChunkSnpsM];                  // output SNP index, -1 = padding / left out
+  uint16_t n[kMaxCodeM + 1][kChunkSnpsM];    // group sizes over non-missing samples
+  uint8_t df[kChunkSnpsM];                   // non-empty groups - 1
+  uint8_t pad_[1536 - 640 - 128 - 320 - 32];
+};
+static_assert(sizeof(ChunkMetaM) == sizeof(ChunkMeta), "ChunkMetaM must fill a ChunkMeta slot");
+
 // Side record of a hit, written next to the public krux_hit record and used by the
 // FP64 finalisation: the pair's group sizes and the group (cohort / bucket) index.
 struct alignas(8) HitAux {
   uint16_t n0, n1, n2, group;
+};
+
+// Second side record of a hit on a marker with more than three groups: the
+// sizes of groups 3 and 4 and the centred sums D_2, D_3 (D_4 follows).
+struct alignas(16) HitAux2 {
+  uint16_t n3, n4, pad0_, pad1_;
+  int32_t d2, d3;
 };
 
 // Hit records move as one 16-byte and one 8-byte access (hit lists are 16-byte
@@ -110,6 +134,7 @@ struct alignas(64) GroupDesc {
   const uint32_t *tile_nan; // [n_ttiles]
   krux_hit *hits;           // hit records (capacity entries)
   HitAux *aux;              // side records
+  HitAux2 *aux2;            // second side records (markers with more than three groups)
   unsigned long long *counter;  // hits found (keeps counting past capacity)
   double *dense_H, *dense_p;    // optional [T][dense_ld]
   double *minp_key;         // permutation mode: [n_agroups-1][rows_per_agroup] best -ln p (as double bits)
@@ -165,6 +190,9 @@ struct ScanParams {
   const int64_t *cis_snp_pos;    // [S] global coordinate of every SNP row
   const int64_t *cis_trait_pos;  // [T] global coordinate of every trait (its gene)
   int64_t cis_window = -1;       // -1: off
+  // markers with up to five groups (chunks of kChunkSnpsM SNPs, ChunkMetaM):
+  int32_t multi = 0;
+  HitAux2 *seg_aux2 = nullptr;   // [grid][kEpiWarps][seg_cap]
 };
 
 enum : unsigned int {
@@ -190,9 +218,10 @@ cudaError_t launch_scan(const ScanParams &p, int grid, size_t smem, cudaStream_t
 size_t scan_smem_bytes(int nc, int nA, int kpad);
 size_t scan_smem_bytes2(int nc, int nA, size_t a_tile_bytes, size_t b_region, int codes_k);
 cudaError_t launch_seg_compact(const krux_hit *seg_hits, const HitAux *seg_aux,
-                               const unsigned int *seg_cnt, int n_seg, int seg_cap,
-                               const unsigned long long *direct, krux_hit *out, HitAux *out_aux,
-                               int64_t capacity, unsigned long long *total, cudaStream_t s);
+                               const HitAux2 *seg_aux2, const unsigned int *seg_cnt, int n_seg,
+                               int seg_cap, const unsigned long long *direct, krux_hit *out,
+                               HitAux *out_aux, HitAux2 *out_aux2, int64_t capacity,
+                               unsigned long long *total, cudaStream_t s);
 cudaError_t launch_minp_from_key(const double *key, double *minp, int P, int T, int ld,
                                  cudaStream_t s);
 cudaError_t launch_pad_traits(int T, int rows_pad, float *tau, double *cfac, uint16_t *nan_cnt,
@@ -200,8 +229,9 @@ cudaError_t launch_pad_traits(int T, int rows_pad, float *tau, double *cfac, uin
 // Uploads the 1/n table the finalisation uses (once per device; not during a
 // graph capture).
 cudaError_t finalize_prepare();
-// Finalisation of min(*count, capacity) hits, the count read on the device.
-cudaError_t launch_finalize_dev(const krux_hit *hits, const HitAux *aux,
+// Finalisation of min(*count, capacity) hits, the count read on the device;
+// aux2 is non-null for markers with more than three groups.
+cudaError_t launch_finalize_dev(const krux_hit *hits, const HitAux *aux, const HitAux2 *aux2,
                                 const unsigned long long *count, int64_t capacity,
                                 const double *const *cfac_by_group, double *H, double *p,
                                 int sm_count, cudaStream_t s, unsigned long long *fdr_hist,

@@ -14,10 +14,10 @@ namespace {
 constexpr int kPackWarps = 8;
 
 // Missing-genotype pre-pass: flags SNPs with a -1 code, appends (index, sample
-// bitmask) of each such SNP, and reports codes outside {-1,0,1,2}.
+// bitmask) of each such SNP, and reports codes outside {-1, 0..max_code}.
 __global__ void __launch_bounds__(kPackWarps * 32)
 missing_scan_kernel(const int8_t *__restrict__ geno, int64_t ldg, int N, int64_t snp_begin,
-                    int64_t n_snps, unsigned int *n_missing, int64_t *miss_idx,
+                    int64_t n_snps, int max_code, unsigned int *n_missing, int64_t *miss_idx,
                     uint64_t *miss_mask, unsigned int *status) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t j = (int64_t)blockIdx.x * kPackWarps + warp;
@@ -31,7 +31,7 @@ missing_scan_kernel(const int8_t *__restrict__ geno, int64_t ldg, int N, int64_t
     if (w * 32 < N) {  // warp-uniform
       const int k = w * 32 + lane;
       const int code = k < N ? (int)g[k] : 0;
-      bad |= (code < -1 || code > 2);
+      bad |= (code < -1 || code > max_code);
       words[w] = __ballot_sync(0xffffffffu, code == -1);
       any |= words[w] != 0u;
     }
@@ -174,15 +174,88 @@ codes_kernel(const int8_t *__restrict__ geno, int64_t ldg, int N, int Np,
     if (lane == 0) codes[(c * Np + k) * 2 + h] = spread_bits(b0) | (spread_bits(b1) << 1);
   }
 }
+// Markers with codes 0..4: one warp per packed SNP slot j of a 32-SNP chunk;
+// rows 32i + jj (i = 0..3) of chunk j / 32 get I_i, the metadata the group
+// sizes and coefficients (1 / N_i) / h_df (group 4's weighs (D_0+..+D_3)^2).
+__global__ void __launch_bounds__(kPackWarps * 32)
+pack_multi_kernel(const int8_t *__restrict__ geno, int64_t ldg, int N, int Np,
+                  const int64_t *__restrict__ snp_list, int64_t snp_begin, int64_t n_snps,
+                  int64_t n_slots, float rh1, float rh2, float rh3, float rh4, int allow_missing,
+                  __half *__restrict__ B, ChunkMetaM *__restrict__ meta, unsigned int *status) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t j = (int64_t)blockIdx.x * kPackWarps + warp;
+  if (j >= n_slots) return;
+  const int64_t c = j / kChunkSnpsM;
+  const int jj = (int)(j % kChunkSnpsM);
+  __half *rows[kMaxCodeM];
+#pragma unroll
+  for (int i = 0; i < kMaxCodeM; ++i) rows[i] = B + (c * kChunkRows + kChunkSnpsM * i + jj) * Np;
+  ChunkMetaM &m = meta[c];
+  const __half one = __int2half_rn(1), zero = __int2half_rn(0);
+  const int64_t s = j < n_snps ? (snp_list ? snp_list[j] : snp_begin + j) : -1;
+  const int8_t *g = s >= 0 ? geno + s * ldg : nullptr;
+  int cnt[kMaxCodeM + 1] = {0, 0, 0, 0, 0};
+  bool miss = false, bad = false;
+  for (int k = lane; k < Np; k += 32) {
+    const int code = (g != nullptr && k < N) ? (int)g[k] : -1;
+#pragma unroll
+    for (int i = 0; i < kMaxCodeM; ++i) rows[i][k] = code == i ? one : zero;
+#pragma unroll
+    for (int i = 0; i <= kMaxCodeM; ++i) cnt[i] += code == i;
+    if (g != nullptr && k < N) {
+      miss |= code == -1;
+      bad |= (code < -1 || code > kMaxCodeM);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i <= kMaxCodeM; ++i)
+    for (int o = 16; o > 0; o >>= 1) cnt[i] += __shfl_xor_sync(0xffffffffu, cnt[i], o);
+  miss = __any_sync(0xffffffffu, miss);
+  bad = __any_sync(0xffffffffu, bad);
+  if (lane == 0) {
+    if (bad) atomicOr(status, kDevBadCode);
+    if (miss && !allow_missing) atomicOr(status, kDevMissing);
+    int groups = 0;
+#pragma unroll
+    for (int i = 0; i <= kMaxCodeM; ++i) groups += cnt[i] > 0;
+    const int df = groups > 0 ? groups - 1 : 0;
+    const bool excluded = g == nullptr || (miss && !allow_missing);
+    const float rh = df == 1 ? rh1 : df == 2 ? rh2 : df == 3 ? rh3 : rh4;
+#pragma unroll
+    for (int i = 0; i <= kMaxCodeM; ++i) {
+      m.coef[i][jj] = (df > 0 && !excluded && cnt[i] > 0) ? rh / (float)cnt[i] : 0.f;
+      m.n[i][jj] = (uint16_t)cnt[i];
+    }
+    m.snp[jj] = excluded ? -1 : (int32_t)s;
+    m.df[jj] = (uint8_t)df;
+  }
+}
 }  // namespace
 
+cudaError_t launch_pack_multi(const int8_t *geno, int64_t ldg, int N, int Np,
+                              const int64_t *snp_list, int64_t snp_begin, int64_t n_snps,
+                              const double *h, int allow_missing, __half *B, ChunkMetaM *meta,
+                              unsigned int *status, cudaStream_t s) {
+  const int64_t nchunks = (n_snps + kChunkSnpsM - 1) / kChunkSnpsM;
+  const int64_t n_slots = nchunks * kChunkSnpsM;
+  if (n_slots == 0) return cudaSuccess;
+  const int64_t grid = (n_slots + kPackWarps - 1) / kPackWarps;
+  pack_multi_kernel<<<(unsigned)grid, kPackWarps * 32, 0, s>>>(
+      geno, ldg, N, Np, snp_list, snp_begin, n_snps, n_slots, (float)(1.0 / h[0]),
+      (float)(1.0 / h[1]), (float)(1.0 / h[2]), (float)(1.0 / h[3]), allow_missing, B, meta,
+      status);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_missing_scan(const int8_t *geno, int64_t ldg, int N, int64_t snp_begin,
-                                int64_t n_snps, unsigned int *n_missing, int64_t *miss_idx,
-                                uint64_t *miss_mask, unsigned int *status, cudaStream_t s) {
+                                int64_t n_snps, int max_code, unsigned int *n_missing,
+                                int64_t *miss_idx, uint64_t *miss_mask, unsigned int *status,
+                                cudaStream_t s) {
   if (n_snps <= 0) return cudaSuccess;
   const int64_t grid = (n_snps + kPackWarps - 1) / kPackWarps;
   missing_scan_kernel<<<(unsigned)grid, kPackWarps * 32, 0, s>>>(geno, ldg, N, snp_begin, n_snps,
-                                                                 n_missing, miss_idx, miss_mask, status);
+                                                                 max_code, n_missing, miss_idx,
+                                                                 miss_mask, status);
   return cudaGetLastError();
 }
 

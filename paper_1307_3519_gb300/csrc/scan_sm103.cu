@@ -171,6 +171,14 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[kEpiSnps
       : "r"(taddr)
       : "memory");
 }
+// 8 consecutive fp32 columns of this warp's 32 TMEM lanes.
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[kEpiSnpsM]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                 "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr)
+               : "memory");
+}
 __device__ __forceinline__ void tmem_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
@@ -224,6 +232,18 @@ __device__ __forceinline__ int fdr_bin(double key, double l0, double w, int bins
   if (!(x >= 1.0)) return 0;
   if (x >= (double)(bins - 1)) return bins - 1;
   return (int)x;
+}
+
+// Upper chi-square tail with df = 1..4 degrees of freedom, Q(df/2, H/2) for
+// integer and half-integer shape: df 1: erfc(sqrt x); df 2: e^-x;
+// df 3: erfc(sqrt x) + 2 sqrt(x / pi) e^-x; df 4: e^-x (1 + x); x = H/2.
+__device__ __forceinline__ double chi2_tail64(double H, int df) {
+  if (df <= 0 || !(H > 0.0)) return 1.0;
+  const double x = 0.5 * H;
+  if (df == 1) return erfc(sqrt(x));
+  if (df == 2) return exp(-x);
+  if (df == 3) return erfc(sqrt(x)) + 1.12837916709551257390 * sqrt(x) * exp(-x);
+  return exp(-x) * (1.0 + x);
 }
 
 // p-value of the pair in FP64 from the exact centred sums and group sizes.
@@ -544,6 +564,133 @@ __device__ __forceinline__ unsigned int hit_event(const uint32_t *dv, bool mine,
   return total;
 }
 
+// ---- markers with up to five groups ---------------------------------------
+// Hot test of a warp's kEpiSnpsM SNPs of a 32-SNP chunk: true when some pair may
+// lie at or above the lower band edge, Q/h_df = sum_i c_i D_i^2 + c_4 (sum_i D_i)^2
+// >= tau (1 - margin), two SNPs per packed instruction.
+__device__ __forceinline__ bool hit_fast_m(const uint32_t (&d)[kMaxCodeM][kEpiSnpsM],
+                                           const ChunkMetaM &m, int h, float ntlo) {
+  const int jb = kEpiSnpsM * h;
+  const uint64_t nt2 = pk2(__float_as_uint(ntlo), __float_as_uint(ntlo));
+  uint32_t acc = 0xffffffffu;
+#pragma unroll
+  for (int j = 0; j < kEpiSnpsM; j += 2) {
+    uint64_t u[kMaxCodeM];
+#pragma unroll
+    for (int i = 0; i < kMaxCodeM; ++i) u[i] = pk2(d[i][j], d[i][j + 1]);
+    const uint64_t s2 = fadd2(fadd2(u[0], u[1]), fadd2(u[2], u[3]));
+    uint64_t q = nt2;
+#pragma unroll
+    for (int i = 0; i < kMaxCodeM; ++i) {
+      const uint64_t c2 = *reinterpret_cast<const uint64_t *>(m.coef[i] + jb + j);
+      q = ffma2(fmul2(c2, u[i]), u[i], q);
+    }
+    const uint64_t c4 = *reinterpret_cast<const uint64_t *>(m.coef[kMaxCodeM] + jb + j);
+    q = ffma2(fmul2(c4, s2), s2, q);
+    uint32_t qa, qb;
+    upk2(q, qa, qb);
+    acc &= qa & qb;
+  }
+  return (int)acc >= 0;
+}
+
+// FP64 decision for a pair inside the band: p < P_c from the exact sums.
+__device__ __noinline__ bool decide64_m(const int *D, const ChunkMetaM &m, int jj, double cfac,
+                                        double pthresh) {
+  double Q = 0.0, S = 0.0;
+  for (int i = 0; i < kMaxCodeM; ++i) {
+    S += (double)D[i];
+    if (m.n[i][jj] > 0) Q += (double)D[i] * (double)D[i] / (double)m.n[i][jj];
+  }
+  if (m.n[kMaxCodeM][jj] > 0) Q += S * S / (double)m.n[kMaxCodeM][jj];
+  return chi2_tail64(cfac * Q, m.df[jj]) < pthresh;
+}
+
+// Rare path of a chunk of markers with up to five groups, called by the whole
+// warp: classification of this lane's candidates and the warp's column-wise
+// append into its staging segment (or the list), as hit_event does.  dv holds
+// D_i of SNP j at dv[kEpiSnpsM * i + j] (i = 0..3).
+__device__ __noinline__ unsigned int hit_event_m(const uint32_t *dv, bool mine, const ChunkMetaM &m,
+                                                 int h, int trait, float ntlo, float nthi,
+                                                 double cfac, const GroupDesc &g,
+                                                 const ScanParams &p, unsigned int wn, int lane) {
+  const int jb = kEpiSnpsM * h;
+  uint32_t hm = 0;
+  if (mine) {
+    for (int j = 0; j < kEpiSnpsM; ++j) {
+      const int jj = jb + j;
+      if (m.snp[jj] < 0 || !in_cis_window(p, m.snp[jj], trait)) continue;
+      float S = 0.f, q = 0.f;
+      int D[kMaxCodeM];
+      for (int i = 0; i < kMaxCodeM; ++i) {
+        const float v = __uint_as_float(dv[kEpiSnpsM * i + j]);
+        D[i] = (int)v;
+        S += v;
+        q = fmaf(m.coef[i][jj] * v, v, q);
+      }
+      q = fmaf(m.coef[kMaxCodeM][jj] * S, S, q);
+      if (q + ntlo >= 0.f) {
+        bool hit = q + nthi > 0.f;
+        if (!hit) hit = decide64_m(D, m, jj, cfac, p.pthresh);
+        if (hit) hm |= 1u << j;
+      }
+    }
+  }
+  const unsigned int total = __reduce_add_sync(0xffffffffu, (unsigned int)__popc(hm));
+  if (total == 0u) return 0u;
+  const unsigned int cap = (unsigned int)p.seg_cap;
+  const unsigned int sbase = wn;
+  const unsigned int over_from = sbase > cap ? sbase : cap;
+  const unsigned int n_over = sbase + total > over_from ? sbase + total - over_from : 0u;
+  unsigned long long gbase = 0;
+  if (lane == 0 && n_over > 0) gbase = atomicAdd(g.counter, (unsigned long long)n_over);
+  gbase = __shfl_sync(0xffffffffu, gbase, 0);
+  const size_t seg0 = ((size_t)blockIdx.x * kEpiWarps + (threadIdx.x >> 5)) * cap;
+  const uint32_t below_me = (1u << lane) - 1u;
+  unsigned int run = sbase;
+  uint32_t cols = __reduce_or_sync(0xffffffffu, hm);
+  while (cols) {
+    const int j = __ffs(cols) - 1;
+    cols &= cols - 1u;
+    const bool mine_j = (hm >> j) & 1u;
+    const uint32_t bal = __ballot_sync(0xffffffffu, mine_j);
+    if (mine_j) {
+      const int jj = jb + j;
+      const unsigned int idx = run + (unsigned int)__popc(bal & below_me);
+      krux_hit r;
+      r.trait = (uint32_t)trait;
+      r.snp = (uint32_t)m.snp[jj];
+      r.d0 = (int32_t)__uint_as_float(dv[j]);
+      r.d1 = (int32_t)__uint_as_float(dv[kEpiSnpsM + j]);
+      HitAux x;
+      x.n0 = m.n[0][jj];
+      x.n1 = m.n[1][jj];
+      x.n2 = m.n[2][jj];
+      x.group = (uint16_t)g.group_id;
+      HitAux2 y;
+      y.n3 = m.n[3][jj];
+      y.n4 = m.n[4][jj];
+      y.pad0_ = y.pad1_ = 0;
+      y.d2 = (int32_t)__uint_as_float(dv[2 * kEpiSnpsM + j]);
+      y.d3 = (int32_t)__uint_as_float(dv[3 * kEpiSnpsM + j]);
+      if (idx < cap) {
+        st_hit(p.seg_hits + seg0 + idx, r);
+        st_aux(p.seg_aux + seg0 + idx, x);
+        p.seg_aux2[seg0 + idx] = y;
+      } else {
+        const unsigned long long gi = gbase + (idx - over_from);
+        if (gi < (unsigned long long)g.capacity) {
+          st_hit(g.hits + gi, r);
+          st_aux(g.aux + gi, x);
+          g.aux2[gi] = y;
+        }
+      }
+    }
+    run += (unsigned int)__popc(bal);
+  }
+  return total;
+}
+
 // Running best -ln p of one (permutation, trait) over this thread's SNPs.
 struct MinpState {
   double best;      // FP64 key of the best pair seen (or the global value at step start)
@@ -623,6 +770,9 @@ __device__ __noinline__ double minp_slow(const uint32_t *dv, const ChunkMeta &m,
   return best;
 }
 
+// kMulti: markers with up to five genotype groups (32-SNP chunks, ChunkMetaM);
+// the producer and MMA warps are the same in both forms.
+template <bool kMulti>
 __global__ void __launch_bounds__(kScanThreads, 1) krux_scan_kernel(const __grid_constant__ ScanParams p) {
   extern __shared__ uint8_t smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -941,49 +1091,78 @@ __global__ void __launch_bounds__(kScanThreads, 1) krux_scan_kernel(const __grid
           ok = ok && wait_bar(t_full(slot), slot_phase, wc, 7);
           if (!__all_sync(0xffffffffu, ok)) goto epi_done;
           tc_fence_after();
-          uint32_t d0[kEpiSnps], d1[kEpiSnps];
-          const uint32_t taddr =
-              tmem_base + ((uint32_t)(32 * q) << 16) + slot * 128u + (uint32_t)(kEpiSnps * h);
-          tmem_ld16(taddr, d0);
-          tmem_ld16(taddr + 64u, d1);
-          tmem_wait_ld();
-          tc_fence_before();
-          __syncwarp();
-          if (lane == 0) mbar_arrive(t_empty(slot));
-          if (++slot == (uint32_t)kTmemSlots) {
-            slot = 0;
-            slot_phase ^= 1u;
-          }
-          const uint64_t *codes =
-              g.codes ? reinterpret_cast<const uint64_t *>(scodes + (size_t)c * codes_stride) : nullptr;
-          const ChunkMeta &mc = smeta[c];
-          bool need;
-          if (minp_mode)
-            need = et.valid && (et.nan_cnt > 0 || minp_fast(d0, d1, mc, h, ms, fdr_tau_lo));
-          else
-            need = p.dense || et.nan_cnt > 0 ||
-                   (p.signed_coef ? hit_fast<true>(d0, d1, mc, h, et.ntlo)
-                                  : hit_fast<false>(d0, d1, mc, h, et.ntlo));
-          if (__any_sync(0xffffffffu, need)) {
-            // rare paths work on a local copy of the accumulators
-            uint32_t dv[2 * kEpiSnps];
+          if constexpr (kMulti) {
+            // markers with up to five groups: this warp's 8 SNPs of a 32-SNP chunk,
+            // D_i of SNP j in column 32 i + j (i = 0..3)
+            uint32_t dd[kMaxCodeM][kEpiSnpsM];
+            const uint32_t tb =
+                tmem_base + ((uint32_t)(32 * q) << 16) + slot * 128u + (uint32_t)(kEpiSnpsM * h);
 #pragma unroll
-            for (int j = 0; j < kEpiSnps; ++j) {
-              dv[j] = d0[j];
-              dv[kEpiSnps + j] = d1[j];
+            for (int i = 0; i < kMaxCodeM; ++i) tmem_ld8(tb + (uint32_t)(kChunkSnpsM * i), dd[i]);
+            tmem_wait_ld();
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(t_empty(slot));
+            if (++slot == (uint32_t)kTmemSlots) {
+              slot = 0;
+              slot_phase ^= 1u;
             }
-            if (minp_mode) {
-              if (need) {
-                ms.best = minp_slow(dv, mc, codes, h, et.cfac, et.nan_cnt, et.nan_idx, ms.best,
-                                    ms.best_lo, ms.c1, ms.c2, fdr_tau_lo, p, ag);
-                ms.best_lo = (float)ms.best * (1.f - p.margin);
+            const ChunkMetaM &mm = *reinterpret_cast<const ChunkMetaM *>(&smeta[c]);
+            const bool need = hit_fast_m(dd, mm, h, et.ntlo);
+            if (__any_sync(0xffffffffu, need)) {
+              uint32_t dv[kMaxCodeM * kEpiSnpsM];
+#pragma unroll
+              for (int i = 0; i < kMaxCodeM; ++i)
+#pragma unroll
+                for (int j = 0; j < kEpiSnpsM; ++j) dv[kEpiSnpsM * i + j] = dd[i][j];
+              wn += hit_event_m(dv, need && et.valid, mm, h, et.trait, et.ntlo, et.nthi, et.cfac,
+                                g, p, wn, lane);
+            }
+          } else {
+            uint32_t d0[kEpiSnps], d1[kEpiSnps];
+            const uint32_t taddr =
+                tmem_base + ((uint32_t)(32 * q) << 16) + slot * 128u + (uint32_t)(kEpiSnps * h);
+            tmem_ld16(taddr, d0);
+            tmem_ld16(taddr + 64u, d1);
+            tmem_wait_ld();
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(t_empty(slot));
+            if (++slot == (uint32_t)kTmemSlots) {
+              slot = 0;
+              slot_phase ^= 1u;
+            }
+            const uint64_t *codes =
+                g.codes ? reinterpret_cast<const uint64_t *>(scodes + (size_t)c * codes_stride) : nullptr;
+            const ChunkMeta &mc = smeta[c];
+            bool need;
+            if (minp_mode)
+              need = et.valid && (et.nan_cnt > 0 || minp_fast(d0, d1, mc, h, ms, fdr_tau_lo));
+            else
+              need = p.dense || et.nan_cnt > 0 ||
+                     (p.signed_coef ? hit_fast<true>(d0, d1, mc, h, et.ntlo)
+                                    : hit_fast<false>(d0, d1, mc, h, et.ntlo));
+            if (__any_sync(0xffffffffu, need)) {
+              // rare paths work on a local copy of the accumulators
+              uint32_t dv[2 * kEpiSnps];
+  #pragma unroll
+              for (int j = 0; j < kEpiSnps; ++j) {
+                dv[j] = d0[j];
+                dv[kEpiSnps + j] = d1[j];
               }
-            } else if (__any_sync(0xffffffffu, p.dense || et.nan_cnt > 0)) {
-              hit_slow(dv, need, mc, codes, h, et.trait, et.valid, et.ntlo, et.nthi, et.cfac,
-                       et.nan_cnt, et.nan_idx, g, p, lane);
-            } else {
-              wn += hit_event(dv, need && et.valid, mc, h, et.trait, et.ntlo, et.nthi, et.cfac, g,
-                              p, wn, lane);
+              if (minp_mode) {
+                if (need) {
+                  ms.best = minp_slow(dv, mc, codes, h, et.cfac, et.nan_cnt, et.nan_idx, ms.best,
+                                      ms.best_lo, ms.c1, ms.c2, fdr_tau_lo, p, ag);
+                  ms.best_lo = (float)ms.best * (1.f - p.margin);
+                }
+              } else if (__any_sync(0xffffffffu, p.dense || et.nan_cnt > 0)) {
+                hit_slow(dv, need, mc, codes, h, et.trait, et.valid, et.ntlo, et.nthi, et.cfac,
+                         et.nan_cnt, et.nan_idx, g, p, lane);
+              } else {
+                wn += hit_event(dv, need && et.valid, mc, h, et.trait, et.ntlo, et.nthi, et.cfac, g,
+                                p, wn, lane);
+              }
             }
           }
           if (step == w.step_end - 1) {
@@ -1022,10 +1201,12 @@ __global__ void __launch_bounds__(kScanThreads, 1) krux_scan_kernel(const __grid
 // also writes the exact total.
 __global__ void seg_compact_kernel(const krux_hit *__restrict__ seg_hits,
                                    const HitAux *__restrict__ seg_aux,
+                                   const HitAux2 *__restrict__ seg_aux2,
                                    const unsigned int *__restrict__ seg_cnt, int n_seg,
                                    int seg_cap, const unsigned long long *__restrict__ direct,
                                    krux_hit *__restrict__ out, HitAux *__restrict__ out_aux,
-                                   int64_t capacity, unsigned long long *total) {
+                                   HitAux2 *__restrict__ out_aux2, int64_t capacity,
+                                   unsigned long long *total) {
   __shared__ unsigned long long part[2][8];
   const int b = blockIdx.x;
   unsigned long long before = 0, all = 0;
@@ -1056,6 +1237,7 @@ __global__ void seg_compact_kernel(const krux_hit *__restrict__ seg_hits,
     if (o < (unsigned long long)capacity) {
       st_hit(out + o, ld_hit(seg_hits + s0 + i));
       st_aux(out_aux + o, ld_aux(seg_aux + s0 + i));
+      if (out_aux2 != nullptr) out_aux2[o] = seg_aux2[s0 + i];
     }
   }
 }
@@ -1066,7 +1248,8 @@ __constant__ double c_rcp[kMaxN + 1];
 
 // FP64 statistic and p-value of each stored hit, from its exact centred sums.
 __device__ __forceinline__ void finalize_one(const krux_hit *__restrict__ hits,
-                                             const HitAux *__restrict__ aux, int64_t i,
+                                             const HitAux *__restrict__ aux,
+                                             const HitAux2 *__restrict__ aux2, int64_t i,
                                              const double *const *__restrict__ cfac_by_group,
                                              double *__restrict__ H, double *__restrict__ P,
                                              unsigned long long *fdr_hist, int fdr_bins,
@@ -1074,14 +1257,30 @@ __device__ __forceinline__ void finalize_one(const krux_hit *__restrict__ hits,
   const krux_hit r = ld_hit(hits + i);
   const HitAux a = ld_aux(aux + i);
   const double cf = cfac_by_group[a.group][r.trait];
-  const int df = df_of(a.n0, a.n1, a.n2);
-  const double D0 = (double)r.d0, D1 = (double)r.d1, D2 = -(double)(r.d0 + r.d1);
-  double Q = D0 * D0 * c_rcp[a.n0];
-  Q = fma(D1 * D1, c_rcp[a.n1], Q);
-  Q = fma(D2 * D2, c_rcp[a.n2], Q);
+  int df;
+  double Q;
+  if (aux2 == nullptr) {
+    df = df_of(a.n0, a.n1, a.n2);
+    const double D0 = (double)r.d0, D1 = (double)r.d1, D2 = -(double)(r.d0 + r.d1);
+    Q = D0 * D0 * c_rcp[a.n0];
+    Q = fma(D1 * D1, c_rcp[a.n1], Q);
+    Q = fma(D2 * D2, c_rcp[a.n2], Q);
+  } else {  // five groups: D_4 = -(D_0 + D_1 + D_2 + D_3)
+    const HitAux2 b = aux2[i];
+    const int n[5] = {a.n0, a.n1, a.n2, b.n3, b.n4};
+    const double D[5] = {(double)r.d0, (double)r.d1, (double)b.d2, (double)b.d3,
+                         -((double)r.d0 + (double)r.d1 + (double)b.d2 + (double)b.d3)};
+    int groups = 0;
+    Q = 0.0;
+    for (int k = 0; k < 5; ++k) {
+      groups += n[k] > 0;
+      Q = fma(D[k] * D[k], c_rcp[n[k]], Q);
+    }
+    df = groups > 0 ? groups - 1 : 0;
+  }
   const double h = cf * Q;
   H[i] = h;
-  P[i] = kw_p64(h, df);
+  P[i] = aux2 == nullptr ? kw_p64(h, df) : chi2_tail64(h, df);
   if (fdr_hist != nullptr)  // row 0: the real data's hits by -log10 p bin
     atomicAdd(fdr_hist + fdr_bin(key64_of(h, df), fdr_l0, fdr_w, fdr_bins), 1ull);
 }
@@ -1093,13 +1292,14 @@ __global__ void finalize_kernel(const krux_hit *__restrict__ hits, const HitAux 
                                 double fdr_w) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
-    finalize_one(hits, aux, i, cfac_by_group, H, P, fdr_hist, fdr_bins, fdr_l0, fdr_w);
+    finalize_one(hits, aux, nullptr, i, cfac_by_group, H, P, fdr_hist, fdr_bins, fdr_l0, fdr_w);
 }
 
 // The same over min(*count, capacity) hits, the count read on the device (no host
 // round trip between the scan and the finalisation; capturable in a graph).
 __global__ void finalize_dev_kernel(const krux_hit *__restrict__ hits,
                                     const HitAux *__restrict__ aux,
+                                    const HitAux2 *__restrict__ aux2,
                                     const unsigned long long *__restrict__ count, int64_t capacity,
                                     const double *const *__restrict__ cfac_by_group,
                                     double *__restrict__ H, double *__restrict__ P,
@@ -1109,7 +1309,7 @@ __global__ void finalize_dev_kernel(const krux_hit *__restrict__ hits,
   const int64_t n = c < (unsigned long long)capacity ? (int64_t)c : capacity;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
-    finalize_one(hits, aux, i, cfac_by_group, H, P, fdr_hist, fdr_bins, fdr_l0, fdr_w);
+    finalize_one(hits, aux, aux2, i, cfac_by_group, H, P, fdr_hist, fdr_bins, fdr_l0, fdr_w);
 }
 
 // minimum p of each (permutation, trait) from its best -ln p (key rows of ld entries)
@@ -1124,12 +1324,13 @@ __global__ void minp_from_key_kernel(const double *__restrict__ key, double *__r
 }  // namespace
 
 cudaError_t launch_seg_compact(const krux_hit *seg_hits, const HitAux *seg_aux,
-                               const unsigned int *seg_cnt, int n_seg, int seg_cap,
-                               const unsigned long long *direct, krux_hit *out, HitAux *out_aux,
-                               int64_t capacity, unsigned long long *total, cudaStream_t s) {
+                               const HitAux2 *seg_aux2, const unsigned int *seg_cnt, int n_seg,
+                               int seg_cap, const unsigned long long *direct, krux_hit *out,
+                               HitAux *out_aux, HitAux2 *out_aux2, int64_t capacity,
+                               unsigned long long *total, cudaStream_t s) {
   if (n_seg <= 0) return cudaSuccess;
-  seg_compact_kernel<<<n_seg, 256, 0, s>>>(seg_hits, seg_aux, seg_cnt, n_seg, seg_cap, direct, out,
-                                           out_aux, capacity, total);
+  seg_compact_kernel<<<n_seg, 256, 0, s>>>(seg_hits, seg_aux, seg_aux2, seg_cnt, n_seg, seg_cap,
+                                           direct, out, out_aux, out_aux2, capacity, total);
   return cudaGetLastError();
 }
 
@@ -1154,12 +1355,18 @@ size_t scan_smem_bytes2(int nc, int nA, size_t a_tile_bytes, size_t b_region, in
 }
 
 cudaError_t scan_set_smem(size_t smem) {
-  return cudaFuncSetAttribute(krux_scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(krux_scan_kernel<false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(krux_scan_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)smem);
 }
 
 cudaError_t launch_scan_only(const ScanParams &p, int grid, size_t smem, cudaStream_t s) {
-  krux_scan_kernel<<<grid, kScanThreads, smem, s>>>(p);
+  if (p.multi)
+    krux_scan_kernel<true><<<grid, kScanThreads, smem, s>>>(p);
+  else
+    krux_scan_kernel<false><<<grid, kScanThreads, smem, s>>>(p);
   return cudaGetLastError();
 }
 
@@ -1198,7 +1405,7 @@ cudaError_t launch_finalize(const krux_hit *hits, const HitAux *aux, int64_t n,
   return cudaGetLastError();
 }
 
-cudaError_t launch_finalize_dev(const krux_hit *hits, const HitAux *aux,
+cudaError_t launch_finalize_dev(const krux_hit *hits, const HitAux *aux, const HitAux2 *aux2,
                                 const unsigned long long *count, int64_t capacity,
                                 const double *const *cfac_by_group, double *H, double *p,
                                 int sm_count, cudaStream_t s, unsigned long long *fdr_hist,
@@ -1207,7 +1414,7 @@ cudaError_t launch_finalize_dev(const krux_hit *hits, const HitAux *aux,
   int grid = sm_count * 4;
   const int64_t need = (capacity + 255) / 256;
   if (need < grid) grid = (int)need;
-  finalize_dev_kernel<<<grid, 256, 0, s>>>(hits, aux, count, capacity, cfac_by_group, H, p,
+  finalize_dev_kernel<<<grid, 256, 0, s>>>(hits, aux, aux2, count, capacity, cfac_by_group, H, p,
                                            fdr_hist, fdr_bins, fdr_l0, fdr_w);
   return cudaGetLastError();
 }

@@ -247,3 +247,16 @@ def genome_positions(rng, S, T, n_chrom=22, chrom_len=150_000_000):
     gene = (chrom << 40) + rng.integers(0, chrom_len, size=T)
     order = np.lexsort((gene & ((1 << 40) - 1), chrom))
     return snp, gene[order].astype(np.int64)
+
+
+def multiallelic_genotypes(rng, S, N, max_code=4, alpha=1.5):
+    """Markers with a varying number of alleles (section "Input data": values
+    0..l, also varying between markers): marker m uses codes 0..k_m with k_m
+    uniform in 1..max_code and code frequencies ~ Dirichlet(alpha); int8 S x N."""
+    rng = _rng(rng)
+    k = rng.integers(1, max_code + 1, size=S)
+    geno = np.empty((S, N), dtype=np.int8)
+    for m in range(S):
+        f = rng.dirichlet(np.full(k[m] + 1, alpha))
+        geno[m] = rng.choice(k[m] + 1, size=N, p=f).astype(np.int8)
+    return geno
