@@ -43,10 +43,10 @@ WORKLOAD = ("paper-scale fused scan: N=102 samples, T=20000 traits, S=500000 SNP
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one krux_scan_kernel
 # launch on the paper-scale workload, from one ncu capture, with the git blob hash of
 # the kernel source it was taken on: reported only while that source is unchanged.
-# ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum on
-# "bench.py --scan-only --traits 20000 --snps 500000 --data paper": 242.51 MB read
-# + 78.04 MB written in one launch (1 pass, the full bench workload).
-SCAN_TRAFFIC = {"blob": "76fd062a3d396bc23619334d79b415df759f8c40", "bytes": 320.55e6}
+# ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum on "bench.py --scan-only
+# --traits 20000 --snps 500000 --data paper --tile 1,3,2,0" (the benchmark's workload
+# and autotuned shape): 242.06 MB read + 79.62 MB written in one launch (1 pass).
+SCAN_TRAFFIC = {"blob": "5963b4c9547275e87a00de11c92f628cbcdfb485", "bytes": 321.68e6}
 
 
 def kernel_blob():
@@ -394,7 +394,9 @@ def run_scan_only(args):
     kx = k.Krux(0)
     rs = kx.krux_rank(torch.from_numpy(expr).cuda())
     g = torch.from_numpy(geno).cuda()
-    if not args.no_autotune:  # the launch shape the benchmark uses
+    if args.tile:  # an explicit launch shape (e.g. the one the benchmark's autotuner chose)
+        kx.set_tuning(*[int(v) for v in args.tile.split(",")])
+    elif not args.no_autotune:  # the launch shape the benchmark uses
         if not multi:  # the autotuner times the biallelic form
             print(f"scan-only autotuned shape (layout, nc, nA, ka) = {kx.autotune(rs, g, pth)}",
                   flush=True)
@@ -422,6 +424,8 @@ def main():
     ap.add_argument("--snps", type=int, default=100000)
     ap.add_argument("--data", default="hwe", choices=["hwe", "paper", "multi"])
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--tile", default="",
+                    help="scan-only: launch shape layout,nc,nA,ka instead of the autotuner's")
     ap.add_argument("--no-autotune", action="store_true",
                     help="scan-only: the automatic launch shape instead of the autotuner's")
     args = ap.parse_args()
