@@ -214,3 +214,60 @@ def scan_cis(expr, geno, pthresh, snp_pos, trait_pos, window):
     r["in_window"] = d <= window
     r["hit"] = r["hit"] & r["in_window"]
     return r
+
+
+def parametric_pair(x, g, model):
+    """Parametric statistics of one trait against one biallelic marker (the
+    paper's comparison: matrix-eQTL's ANOVA and linear models), FP64 from the
+    definitions over the samples with a genotype (codes 0,1,2).
+    model 'anova': one-way ANOVA over the non-empty genotype groups,
+      F = (SS_between / (g - 1)) / (SS_within / (K - g)), p = upper F(g-1, K-g) tail;
+    model 'linear': least-squares regression of x on the dosage (the code),
+      t = r sqrt((K - 2) / (1 - r^2)), p = two-sided Student t(K - 2) tail.
+    Returns (stat, p); degenerate pairs (one group, constant dosage or x) give
+    (0, 1).  The tails are scipy.stats' (a library step)."""
+    import scipy.stats as sst
+    x = np.asarray(x, dtype=np.float64)
+    g = np.asarray(g)
+    use = g >= 0
+    x, g = x[use], g[use].astype(np.float64)
+    K = x.size
+    if model == "anova":
+        levels = [c for c in (0, 1, 2) if np.any(g == c)]
+        k = len(levels)
+        if k < 2 or K <= k:
+            return 0.0, 1.0
+        m = x.mean()
+        ssb = sum(np.sum(g == c) * (x[g == c].mean() - m) ** 2 for c in levels)
+        ssw = sum(np.sum((x[g == c] - x[g == c].mean()) ** 2) for c in levels)
+        if ssw == 0.0:
+            return (np.inf, 0.0) if ssb > 0 else (0.0, 1.0)
+        F = (ssb / (k - 1)) / (ssw / (K - k))
+        return float(F), float(sst.f.sf(F, k - 1, K - k))
+    if model == "linear":
+        if K < 3:
+            return 0.0, 1.0
+        dg, dx = g - g.mean(), x - x.mean()
+        sgg, sxx, sxg = np.sum(dg * dg), np.sum(dx * dx), np.sum(dx * dg)
+        if sgg == 0.0 or sxx == 0.0:
+            return 0.0, 1.0
+        r = sxg / np.sqrt(sgg * sxx)
+        if abs(r) >= 1.0:
+            return (np.inf if r > 0 else -np.inf), 0.0
+        t = r * np.sqrt((K - 2) / (1.0 - r * r))
+        return float(t), float(2.0 * sst.t.sf(abs(t), K - 2))
+    raise ValueError("model must be 'anova' or 'linear'")
+
+
+def parametric_scan(expr, geno, pthresh, model, traits=None, snps=None):
+    """parametric_pair over traits x snps: dict of (nt, ns) arrays stat, p, hit."""
+    expr = np.asarray(expr)
+    geno = np.asarray(geno)
+    traits = np.arange(expr.shape[0]) if traits is None else np.asarray(traits)
+    snps = np.arange(geno.shape[0]) if snps is None else np.asarray(snps)
+    stat = np.empty((traits.size, snps.size))
+    p = np.empty((traits.size, snps.size))
+    for a, t in enumerate(traits):
+        for b, s in enumerate(snps):
+            stat[a, b], p[a, b] = parametric_pair(expr[t], geno[s], model)
+    return dict(stat=stat, p=p, hit=p < pthresh)

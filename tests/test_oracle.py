@@ -386,3 +386,72 @@ def test_biallelic_data_gives_the_same_results_as_multiallelic_mode(oracle_mod):
     b = oracle_mod.scan(d["expr"], d["geno"], 1e-3, max_code=4)
     assert np.array_equal(a["H"], b["H"]) and np.array_equal(a["p"], b["p"])
     assert np.array_equal(a["d"], b["d"][..., :3]) and np.all(b["d"][..., 3:] == 0)
+
+
+def _load_param():
+    rows = []
+    with open(os.path.join(os.path.dirname(GOLDEN), "parametric_worked_examples.txt")) as f:
+        for line in f:
+            if not line.strip() or line.startswith("#"):
+                continue
+            vals, codes, model, frac, d1, d2 = line.rstrip("\n").split("\t")
+            rows.append((np.array([float(v) for v in vals.split(",")]),
+                         np.array([int(c) for c in codes.split(",")], dtype=np.int8), model,
+                         Fraction(frac), int(d1), int(d2)))
+    return rows
+
+
+@pytest.mark.parametrize("case", range(4))
+def test_parametric_worked_examples(oracle_mod, case):
+    x, g, model, val, d1, d2 = _load_param()[case]
+    stat, p = oracle_mod.parametric_pair(x, g, model)
+    if model == "anova":
+        assert stat == pytest.approx(float(val), rel=1e-13)
+        assert p == pytest.approx(st.f.sf(float(val), d1, d2), rel=1e-12)
+    else:
+        assert stat * stat == pytest.approx(float(val), rel=1e-13)
+        # the two-sided t tail equals the F(1, K-2) tail of t^2
+        assert p == pytest.approx(st.f.sf(float(val), 1, d2), rel=1e-10)
+
+
+def test_parametric_matches_scipy_routines(oracle_mod):
+    """ANOVA against scipy's f_oneway, linear against scipy's linregress."""
+    rng = np.random.default_rng(91)
+    n_checked = 0
+    for j in range(40):
+        n = int(rng.integers(8, 120))
+        x = rng.standard_normal(n) + 3.0 * (j % 5)
+        g = rng.integers(0, 3, n).astype(np.int8)
+        if j % 3 == 0:
+            g[rng.random(n) < 0.1] = -1
+        use = g >= 0
+        groups = [x[use & (g == c)] for c in range(3) if np.any(use & (g == c))]
+        if len(groups) < 2:
+            continue
+        F, pF = oracle_mod.parametric_pair(x, g, "anova")
+        ref = st.f_oneway(*groups)
+        assert F == pytest.approx(ref.statistic, rel=1e-10) and pF == pytest.approx(ref.pvalue, rel=1e-9)
+        t, pt = oracle_mod.parametric_pair(x, g, "linear")
+        lr = st.linregress(g[use].astype(float), x[use])
+        assert pt == pytest.approx(lr.pvalue, rel=1e-9)
+        assert t == pytest.approx(lr.slope / lr.stderr, rel=1e-9)
+        n_checked += 1
+    assert n_checked > 30
+
+
+def test_parametric_invariances(oracle_mod):
+    """Both statistics are invariant under x -> a x + b (a > 0); the linear t flips
+    sign with the dosage direction; ANOVA ignores group labels."""
+    rng = np.random.default_rng(92)
+    x = rng.standard_normal(50)
+    g = rng.integers(0, 3, 50).astype(np.int8)
+    for model in ("anova", "linear"):
+        s0, p0 = oracle_mod.parametric_pair(x, g, model)
+        s1, p1 = oracle_mod.parametric_pair(7.0 * x - 300.0, g, model)
+        assert s1 == pytest.approx(s0, rel=1e-9) and p1 == pytest.approx(p0, rel=1e-9)
+    t0, _ = oracle_mod.parametric_pair(x, g, "linear")
+    t1, _ = oracle_mod.parametric_pair(x, (2 - g).astype(np.int8), "linear")
+    assert t1 == pytest.approx(-t0, rel=1e-12)
+    F0, _ = oracle_mod.parametric_pair(x, g, "anova")
+    F1, _ = oracle_mod.parametric_pair(x, np.array([1, 2, 0], np.int8)[g], "anova")
+    assert F1 == pytest.approx(F0, rel=1e-12)
