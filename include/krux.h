@@ -177,6 +177,34 @@ krux_status krux_scan_cis(krux_ctx *ctx, const krux_rankset *rs, const int8_t *g
                           int64_t window, const krux_opts *opts, krux_hit *hits, double *hit_H,
                           double *hit_p, int64_t *n_hits, void *stream);
 
+/* Parametric statistics on the same tiles (the paper compares kruX with the
+ * linear and ANOVA models of matrix-eQTL on the same data): the contraction of
+ * the scan with the centred ranks replaced by standardised values
+ * (x - mean) / sd per trait, then
+ *   model 0: one-way ANOVA over the genotype groups, F with (groups - 1,
+ *            N - groups) df, p = upper F tail;
+ *   model 1: least-squares regression on the dosage (the code 0/1/2), t with
+ *            N - 2 df, p = two-sided t tail.
+ * The fused test runs on FP16 values with a wide band; every pair in it is
+ * recomputed in FP64 from `expr` and kept iff p < P_c, so the hit set and the
+ * FP64 statistic and p are those of the definitions.
+ *   expr : device float32 [T][ld], no NaN (-> KRUX_EINVAL); 4 <= N <= 512.
+ *   geno : device int8 [S][ldg], codes 0, 1, 2 (a -1 -> KRUX_EUNSUPPORTED).
+ *   hits : records with d0 = d1 = 0; hit_stat receives F (model 0) or t
+ *          (model 1), hit_p its p-value; 16-byte aligned hits as in krux_scan.
+ * opts: pthresh, hit_capacity and the SNP slice are used; flags must be 0 and
+ * dense output is not available.  n_hits is exact; if the band's work list
+ * (hit_capacity + 2^20 entries) overflows the call returns KRUX_EOVERFLOW with
+ * n_hits an upper bound. */
+krux_status krux_scan_parametric(krux_ctx *ctx, const float *expr, int T, int N, int64_t ld,
+                                 const int8_t *geno, int64_t S, int64_t ldg, int model,
+                                 const krux_opts *opts, krux_hit *hits, double *hit_stat,
+                                 double *hit_p, int64_t *n_hits, void *stream);
+
+/* Test hook (host only): the FP64 tails the parametric finalisation uses.
+ * kind 0: P(F(d1, d2) > x); kind 1: P(|T(d1)| > x); kind 2: I_x(d1, d2). */
+double krux_debug_tail(int kind, double x, double d1, double d2);
+
 /* One cohort of a grouped scan: its own rank set (any N <= 512), genotypes and
  * hit outputs; n_hits is written by krux_scan_grouped. */
 typedef struct {

@@ -30,7 +30,7 @@ EXPORTS = ["krux_create", "krux_destroy", "krux_status_string", "krux_last_error
            "krux_get_profile", "krux_set_wait_limit", "krux_set_tuning", "krux_scan_noalloc", "krux_debug_plan",
            "krux_autotune", "krux_graph_scan", "krux_graph_permute", "krux_graph_grouped",
            "krux_graph_launch", "krux_graph_wait", "krux_graph_last_error", "krux_graph_destroy",
-           "krux_scan_cis"]
+           "krux_scan_cis", "krux_scan_parametric", "krux_debug_tail"]
 
 
 class KruxError(RuntimeError):
@@ -94,6 +94,9 @@ def load_library(path=LIB_PATH):
         "krux_debug_plan": ([I, I, I, I, I, I, P], I),
         "krux_scan_noalloc": ([P, I, I, I64, P, I64, I64, D, P, P, P, I64, ctypes.POINTER(I64), P], I),
         "krux_autotune": ([P, P, P, I64, I64, D, P, P], I),
+        "krux_scan_parametric": ([P, P, I, I, I64, P, I64, I64, I, ctypes.POINTER(Opts), P, P, P,
+                                  ctypes.POINTER(I64), P], I),
+        "krux_debug_tail": ([I, D, D, D], D),
         "krux_scan_cis": ([P, P, P, I64, I64, P, P, I64, ctypes.POINTER(Opts), P, P, P,
                            ctypes.POINTER(I64), P], I),
         "krux_graph_scan": ([P, P, P, I64, I64, ctypes.POINTER(Opts), P, P, P, ctypes.POINTER(P)], I),
@@ -302,6 +305,23 @@ class Krux:
         k = min(n.value, capacity)
         return dict(n_hits=n.value, overflow=st == KRUX_EOVERFLOW, hits=hits[:k], H=H[:k], p=P[:k])
 
+    def krux_scan_parametric(self, expr, geno, model, pthresh, capacity, stream=None):
+        """Parametric comparison statistics (model 'anova' or 'linear') on the same
+        tiles; returns dict(n_hits, overflow, hits (d0 = d1 = 0), stat, p)."""
+        import torch
+        assert expr.is_cuda and expr.dtype == torch.float32 and expr.stride(1) == 1
+        m = {"anova": 0, "linear": 1}[model]
+        hits, H, P = self._outputs(capacity)
+        o = self._opts(pthresh, capacity)
+        n = ctypes.c_int64()
+        st = self.lib.krux_scan_parametric(self.handle, _ptr(expr), expr.shape[0], expr.shape[1],
+                                           expr.stride(0), _ptr(geno), geno.shape[0], geno.stride(0),
+                                           m, ctypes.byref(o), _ptr(hits), _ptr(H), _ptr(P),
+                                           ctypes.byref(n), _stream(stream))
+        st = self._check(st, "krux_scan_parametric")
+        k = min(n.value, capacity)
+        return dict(n_hits=n.value, overflow=st == KRUX_EOVERFLOW, hits=hits[:k], stat=H[:k], p=P[:k])
+
     def krux_scan_plain(self, rs, geno, pthresh, capacity, snp_begin=0, snp_end=0, dense=False,
                         margin=0.0, stream=None):
         """Plain two-pass form (library GEMM, then a separate epilogue)."""
@@ -508,3 +528,9 @@ class Graph:
             self.close()
         except Exception:
             pass
+
+
+def krux_debug_tail(kind, x, d1, d2=0.0):
+    """The parametric finalisation's FP64 tails on the host (kind 0: F upper tail,
+    1: two-sided t tail, 2: regularised incomplete beta I_x(d1, d2))."""
+    return float(load_library().krux_debug_tail(int(kind), float(x), float(d1), float(d2)))

@@ -23,6 +23,24 @@ cudaError_t launch_missing_scan(const int8_t *geno, int64_t ldg, int N, int64_t 
                                 int64_t n_snps, int max_code, unsigned int *n_missing,
                                 int64_t *miss_idx, uint64_t *miss_mask, unsigned int *status,
                                 cudaStream_t s);
+cudaError_t launch_pack_linear(const int8_t *geno, int64_t ldg, int N, int Np, int64_t snp_begin,
+                               int64_t n_snps, double rl, __half *B, ChunkMeta *meta,
+                               unsigned int *status, cudaStream_t s);
+cudaError_t launch_standardize(const float *expr, int T, int N, int64_t ld, int Np, __half *A,
+                               double *mean, double *sd, float *tau, double *cfac,
+                               uint16_t *nan_cnt, unsigned int *status, cudaStream_t s);
+cudaError_t launch_finalize_param(const krux_hit *hits, const unsigned long long *count,
+                                  int64_t capacity, const float *expr, int64_t ld,
+                                  const int8_t *geno, int64_t ldg, int N, const double *mean,
+                                  int model, double *stat, double *P, int sm_count,
+                                  cudaStream_t s);
+cudaError_t launch_filter_param(const krux_hit *hits, const unsigned long long *count,
+                                int64_t capacity, const double *stat, const double *P,
+                                double pthresh, krux_hit *out, double *out_stat, double *out_p,
+                                int64_t out_capacity, unsigned long long *n_out, int sm_count,
+                                cudaStream_t s);
+double param_f_crit(double pthresh, double d1, double d2);
+double param_t_crit(double pthresh, double nu);
 cudaError_t launch_pack_multi(const int8_t *geno, int64_t ldg, int N, int Np,
                               const int64_t *snp_list, int64_t snp_begin, int64_t n_snps,
                               const double *h, int allow_missing, __half *B, ChunkMetaM *meta,
@@ -146,7 +164,7 @@ struct krux_ctx {
   PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   cudaEvent_t ev[kEv] = {};
   DevBuf B, meta, codes, groups, items, status, counters, aux, cfacptr, miss_idx, miss_mask,
-      list, gemm_out, bucket_ranks, permA, minpkey, seg, permNan, aux2;
+      list, gemm_out, bucket_ranks, permA, minpkey, seg, permNan, aux2, param, paramOut;
   void *blas = nullptr;
   std::vector<std::pair<size_t, void *>> pool;  // freed rank-set blocks, reused by size
   std::map<int, std::array<int, 4>> tuned;       // krux_autotune: K width -> layout, nc, nA, ka
@@ -462,7 +480,7 @@ void krux_destroy(krux_ctx *ctx) {
   DevBuf *bufs[] = {&ctx->B, &ctx->meta, &ctx->codes, &ctx->groups, &ctx->items, &ctx->status,
                     &ctx->counters, &ctx->aux, &ctx->cfacptr, &ctx->miss_idx, &ctx->miss_mask,
                     &ctx->list, &ctx->gemm_out, &ctx->bucket_ranks, &ctx->permA, &ctx->minpkey, &ctx->seg,
-                    &ctx->permNan, &ctx->aux2};
+                    &ctx->permNan, &ctx->aux2, &ctx->param, &ctx->paramOut};
   for (DevBuf *b : bufs) b->release();
   for (auto &pb : ctx->pool) cudaFree(pb.second);
   for (int i = 0; i < kEv; ++i)
@@ -717,6 +735,17 @@ struct CallPlan {
     int32_t *inv = nullptr;      // [P][N] inverse permutations
   } perm;
   bool multi = false;  // markers with codes 0..4 (chunks of kChunkSnpsM SNPs)
+  struct Param {  // parametric comparison: fused test bounds and the FP64 decision
+    int model = -1;                 // -1 off, 0 ANOVA, 1 dosage regression
+    double h1 = 0.0, h2 = 0.0;      // ANOVA bounds tau_1, tau_2 on sum_i S_i^2 / N_i
+    double rl = 0.0;                // regression: 1 / ((K - 1) r_c^2)
+    const float *expr = nullptr;    // the caller's values, for the FP64 recomputation
+    int64_t ld = 0;
+    const double *mean = nullptr;   // per-trait mean the recomputation centres on
+    krux_hit *out = nullptr;        // the caller's lists
+    double *out_stat = nullptr, *out_p = nullptr;
+    int64_t out_capacity = 0;
+  } param;
   struct Cis {  // cis scans: SNP and trait coordinates (host copies) and the window
     bool on = false;
     const int64_t *snp_pos = nullptr, *trait_pos = nullptr;  // device
@@ -932,8 +961,8 @@ struct FusedLaunch {
 
 krux_status prepare_fused(krux_ctx *ctx, CallPlan &cp, const krux_opts *o, FusedLaunch &fl,
                           cudaStream_t s) {
-  fl.h1 = h_df1(o->pthresh);
-  fl.h2 = h_df2(o->pthresh);
+  fl.h1 = cp.param.model == 0 ? cp.param.h1 : h_df1(o->pthresh);
+  fl.h2 = cp.param.model == 0 ? cp.param.h2 : h_df2(o->pthresh);
   const int ng = (int)cp.groups.size();
   fl.nslots = (int)cp.slots.size();
   fl.signed_coef = 0;
@@ -1085,6 +1114,11 @@ krux_status prepare_fused(krux_ctx *ctx, CallPlan &cp, const krux_opts *o, Fused
   p.b_region = sh.b_region;
   p.layout = layout;
   p.margin = (float)(o->recheck_margin > 0 ? o->recheck_margin : 1e-4);
+  if (cp.param.model >= 0) {
+    // FP16 standardised values: a wide band, every pair in it decided in FP64
+    p.margin = 0.03f;
+    p.provisional = 1;
+  }
   p.dense = o->dense_H != nullptr ? 1 : 0;
   p.pthresh = o->pthresh;
   p.h1 = (float)fl.h1;
@@ -1131,7 +1165,7 @@ krux_status prepare_fused(krux_ctx *ctx, CallPlan &cp, const krux_opts *o, Fused
 krux_status enqueue_fused(krux_ctx *ctx, CallPlan &cp, const FusedLaunch &fl, cudaStream_t s) {
   const int ng = (int)cp.groups.size();
   const int nslots = fl.nslots;
-  KRUX_CUDA(ctx, cudaMemsetAsync(ctx->counters.p, 0, (size_t)nslots * 16, s));
+  KRUX_CUDA(ctx, cudaMemsetAsync(ctx->counters.p, 0, (size_t)nslots * 16 + 8, s));
   KRUX_CUDA(ctx, cudaMemsetAsync(ctx->status.p, 0, 64, s));
   if (cp.fdr_hist)
     KRUX_CUDA(ctx, cudaMemsetAsync(cp.fdr_hist, 0, (size_t)cp.fdr_rows * cp.fdr_bins * 8, s));
@@ -1171,7 +1205,10 @@ krux_status enqueue_fused(krux_ctx *ctx, CallPlan &cp, const FusedLaunch &fl, cu
     __half *B = reinterpret_cast<__half *>(ctx->B.as<char>() + fl.boff[i]);
     ChunkMeta *meta = ctx->meta.as<ChunkMeta>() + fl.moff[i];
     uint64_t *codes = g.nan_cnt ? ctx->codes.as<uint64_t>() + fl.coff[i] : nullptr;
-    if (cp.multi)
+    if (cp.param.model == 1)
+      KRUX_CUDA(ctx, launch_pack_linear(g.geno, g.ldg, rs->N, rs->Np, g.snp_begin, g.n_snps,
+                                        cp.param.rl, B, meta, status, s));
+    else if (cp.multi)
       KRUX_CUDA(ctx, launch_pack_multi(g.geno, g.ldg, rs->N, rs->Np, g.snp_list, g.snp_begin,
                                        g.n_snps, fl.hm, g.allow_missing, B,
                                        reinterpret_cast<ChunkMetaM *>(meta), status, s));
@@ -1197,7 +1234,19 @@ krux_status enqueue_fused(krux_ctx *ctx, CallPlan &cp, const FusedLaunch &fl, cu
   }
   // FP64 H and p of the stored hits: each slot's count is read on the device
   ev_record(ctx, 5, s);
-  for (int k = 0; k < nslots; ++k) {
+  if (cp.param.model >= 0) {  // FP64 decision of the provisional hits, then the filter
+    const OutSlot &os = cp.slots[0];
+    const ScanGroupIn &g = cp.groups[0];
+    KRUX_CUDA(ctx, launch_finalize_param(os.hits, totals, os.capacity, cp.param.expr, cp.param.ld,
+                                         g.geno, g.ldg, g.rs->N, cp.param.mean, cp.param.model,
+                                         os.H, os.P, ctx->sm_count, s));
+    KRUX_CUDA(ctx, launch_filter_param(os.hits, totals, os.capacity, os.H, os.P, fl.p.pthresh,
+                                       cp.param.out, cp.param.out_stat, cp.param.out_p,
+                                       cp.param.out_capacity,
+                                       ctx->counters.as<unsigned long long>() + 2 * nslots,
+                                       ctx->sm_count, s));
+  }
+  for (int k = 0; k < nslots && cp.param.model < 0; ++k) {
     const OutSlot &os = cp.slots[k];
     if (os.capacity <= 0) continue;
     KRUX_CUDA(ctx, launch_finalize_dev(os.hits, os.aux, os.aux2, totals + k, os.capacity,
@@ -1215,7 +1264,8 @@ krux_status enqueue_fused(krux_ctx *ctx, CallPlan &cp, const FusedLaunch &fl, cu
 int fused_launches(const CallPlan &cp, const FusedLaunch &fl) {
   int n = (fl.grid > 0 ? 1 : 0) + (fl.staged ? 1 : 0);
   for (auto &g : cp.groups) n += g.nan_cnt ? 2 : 1;
-  for (auto &os : cp.slots) n += os.capacity > 0 ? 1 : 0;
+  for (auto &os : cp.slots) n += (os.capacity > 0 && cp.param.model < 0) ? 1 : 0;
+  if (cp.param.model >= 0) n += 2;
   if (cp.perm.on) n += 2 + (cp.perm.lists ? 2 : 0);
   return n;
 }
@@ -1361,6 +1411,132 @@ extern "C" krux_status krux_scan_cis(krux_ctx *ctx, const krux_rankset *rs, cons
   st = run_fused(ctx, cp, opts, s, counts);
   if (st != KRUX_OK) return st;
   *n_hits = (int64_t)counts[0];
+  if (*n_hits > opts->hit_capacity)
+    return fail(ctx, KRUX_EOVERFLOW, "%lld hits exceed capacity %lld", (long long)*n_hits,
+                (long long)opts->hit_capacity);
+  return KRUX_OK;
+}
+
+extern "C" krux_status krux_scan_parametric(krux_ctx *ctx, const float *expr, int T, int N,
+                                            int64_t ld, const int8_t *geno, int64_t S,
+                                            int64_t ldg, int model, const krux_opts *opts,
+                                            krux_hit *hits, double *hit_stat, double *hit_p,
+                                            int64_t *n_hits, void *stream) {
+  if (!ctx) return KRUX_EINVAL;
+  if (!n_hits) return fail(ctx, KRUX_EINVAL, "n_hits is NULL");
+  *n_hits = 0;
+  krux_status st = check_opts(ctx, opts);
+  if (st != KRUX_OK) return st;
+  if (opts->flags != 0 || opts->dense_H)
+    return fail(ctx, KRUX_EINVAL, "parametric scans take no flags and no dense output");
+  if (model != 0 && model != 1) return fail(ctx, KRUX_EINVAL, "model must be 0 (ANOVA) or 1 (linear)");
+  if (!expr || T < 1 || N < 4 || N > kMaxN || ld < N)
+    return fail(ctx, KRUX_EINVAL, "need expr, T >= 1, 4 <= N <= %d and ld >= N", kMaxN);
+  if (S < 0 || (S > 0 && (!geno || ldg < N)) || S >= ((int64_t)1 << 31))
+    return fail(ctx, KRUX_EINVAL, "bad genotype matrix");
+  if (opts->hit_capacity > 0 && (!hits || !hit_stat || !hit_p))
+    return fail(ctx, KRUX_EINVAL, "hit outputs are NULL");
+  if (((uintptr_t)hits & 15u) != 0) return fail(ctx, KRUX_EINVAL, "hits must be 16-byte aligned");
+  cudaStream_t s = (cudaStream_t)stream;
+  KRUX_CUDA(ctx, cudaSetDevice(ctx->device));
+  const int64_t b = opts->snp_begin, e = opts->snp_end > 0 ? opts->snp_end : S;
+  if (b < 0 || e > S || b > e) return fail(ctx, KRUX_EINVAL, "bad SNP slice");
+  if (ctx->profiling) {
+    ctx->prof = krux_profile{};
+    ctx->prof.pairs = (int64_t)T * (e - b);
+  }
+  // the standardised values in the layout of a rank set
+  krux_rankset rs;
+  rs.T = T;
+  rs.N = N;
+  rs.Np = round_up(N, 16);
+  rs.rows_pad = round_up(T, kTileM);
+  rs.n_ttiles = rs.rows_pad / kTileM;
+  rs.has_nan = false;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off += (bytes + 255) / 256 * 256;
+    return o;
+  };
+  const size_t oA = take((size_t)rs.rows_pad * rs.Np * 2), oTau = take((size_t)rs.rows_pad * 4),
+               oCf = take((size_t)rs.rows_pad * 8), oNc = take((size_t)rs.rows_pad * 2),
+               oNi = take((size_t)T * N * 2), oTile = take((size_t)rs.n_ttiles * 4),
+               oMean = take((size_t)T * 8), oSd = take((size_t)T * 8);
+  KRUX_CUDA(ctx, ctx->param.ensure(off));
+  char *pb = ctx->param.as<char>();
+  KRUX_CUDA(ctx, cudaMemsetAsync(pb, 0, off, s));
+  rs.dev = RankDev{};
+  rs.dev.A = reinterpret_cast<__half *>(pb + oA);
+  rs.dev.tau = reinterpret_cast<float *>(pb + oTau);
+  rs.dev.cfac = reinterpret_cast<double *>(pb + oCf);
+  rs.dev.nan_cnt = reinterpret_cast<uint16_t *>(pb + oNc);
+  rs.dev.nan_idx = reinterpret_cast<uint16_t *>(pb + oNi);
+  rs.dev.tile_nan = reinterpret_cast<uint32_t *>(pb + oTile);
+  double *mean = reinterpret_cast<double *>(pb + oMean);
+  double *sd = reinterpret_cast<double *>(pb + oSd);
+  KRUX_CUDA(ctx, ctx->status.ensure(64));
+  KRUX_CUDA(ctx, cudaMemsetAsync(ctx->status.p, 0, 64, s));
+  ev_record(ctx, 0, s);
+  KRUX_CUDA(ctx, launch_standardize(expr, T, N, ld, rs.Np, rs.dev.A, mean, sd, rs.dev.tau,
+                                    rs.dev.cfac, rs.dev.nan_cnt, ctx->status.as<unsigned int>(), s));
+  KRUX_CUDA(ctx, launch_pad_traits(T, rs.rows_pad, rs.dev.tau, rs.dev.cfac, rs.dev.nan_cnt, s));
+  ev_record(ctx, 1, s);
+  unsigned int hst = 0;
+  KRUX_CUDA(ctx, cudaMemcpyAsync(&hst, ctx->status.p, 4, cudaMemcpyDeviceToHost, s));
+  KRUX_CUDA(ctx, cudaStreamSynchronize(s));
+  if (hst & kDevBadCode) return fail(ctx, KRUX_EINVAL, "parametric scans take expression without NaN");
+  // bounds of the fused test
+  CallPlan cp;
+  cp.param.model = model;
+  const double K = (double)N;
+  if (model == 0) {
+    for (int df = 1; df <= 2; ++df) {
+      const double fc = param_f_crit(opts->pthresh, df, K - 1.0 - df);
+      const double tau = (K - 1.0) * fc * df / (K - 1.0 - df + fc * df);
+      (df == 1 ? cp.param.h1 : cp.param.h2) = tau;
+    }
+  } else {
+    const double tc = param_t_crit(opts->pthresh, K - 2.0);
+    const double rc2 = tc * tc / (K - 2.0 + tc * tc);
+    cp.param.rl = 1.0 / ((K - 1.0) * rc2);
+  }
+  cp.param.expr = expr;
+  cp.param.ld = ld;
+  cp.param.mean = mean;
+  cp.param.out = hits;
+  cp.param.out_stat = hit_stat;
+  cp.param.out_p = hit_p;
+  cp.param.out_capacity = opts->hit_capacity;
+  // provisional hits: the caller's capacity plus room for the band
+  const int64_t prov = opts->hit_capacity + ((int64_t)1 << 20);
+  KRUX_CUDA(ctx, ctx->paramOut.ensure((size_t)prov * (16 + 8 + 8)));
+  krux_hit *ph = ctx->paramOut.as<krux_hit>();
+  double *pstat = reinterpret_cast<double *>(ctx->paramOut.as<char>() + (size_t)prov * 16);
+  double *pp = pstat + prov;
+  KRUX_CUDA(ctx, ctx->aux.ensure((size_t)prov * sizeof(HitAux)));
+  cp.slots.push_back(OutSlot{ph, pstat, pp, prov, ctx->aux.as<HitAux>()});
+  st = plan_groups(ctx, cp, &rs, geno, ldg, b, e, nullptr, 1, 0, nullptr, nullptr, nullptr, s);
+  if (st != KRUX_OK) return st;
+  if (!cp.bucket_jobs.empty())
+    return fail(ctx, KRUX_EUNSUPPORTED, "parametric scans take complete genotypes (no -1 codes)");
+  st = materialise(ctx, cp, s);
+  if (st != KRUX_OK) return st;
+  std::vector<unsigned long long> counts;
+  st = run_fused(ctx, cp, opts, s, counts);
+  if (st != KRUX_OK) return st;
+  unsigned long long n_final = 0;
+  KRUX_CUDA(ctx, cudaMemcpyAsync(&n_final, ctx->counters.as<unsigned long long>() + 2, 8,
+                                 cudaMemcpyDeviceToHost, s));
+  KRUX_CUDA(ctx, cudaStreamSynchronize(s));
+  if (ctx->profiling) ctx->prof.ms_rank = ev_ms(ctx, 0, 1);
+  if ((int64_t)counts[0] > prov) {
+    *n_hits = (int64_t)counts[0];
+    return fail(ctx, KRUX_EOVERFLOW,
+                "%lld provisional hits exceed the work list; n_hits is an upper bound",
+                (long long)counts[0]);
+  }
+  *n_hits = (int64_t)n_final;
   if (*n_hits > opts->hit_capacity)
     return fail(ctx, KRUX_EOVERFLOW, "%lld hits exceed capacity %lld", (long long)*n_hits,
                 (long long)opts->hit_capacity);

@@ -193,6 +193,9 @@ struct ScanParams {
   // markers with up to five groups (chunks of kChunkSnpsM SNPs, ChunkMetaM):
   int32_t multi = 0;
   HitAux2 *seg_aux2 = nullptr;   // [grid][kEpiWarps][seg_cap]
+  // parametric comparison: every pair at or above the lower band edge is kept as
+  // a provisional hit (decided later in FP64 from the FP32 values)
+  int32_t provisional = 0;
 };
 
 enum : unsigned int {

@@ -58,7 +58,7 @@ pack_kernel(const int8_t *__restrict__ geno, int64_t ldg, int N, int Np,
             const int64_t *__restrict__ snp_list, int64_t snp_begin, int64_t n_snps,
             int64_t n_slots, int64_t snp_out_base, float rh1, float rh2, int allow_missing,
             int signed_df1, __half *__restrict__ B, ChunkMeta *__restrict__ meta,
-            unsigned int *status) {
+            unsigned int *status, int linear, float rl) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t j = (int64_t)blockIdx.x * kPackWarps + warp;
   if (j >= n_slots) return;
@@ -114,7 +114,17 @@ pack_kernel(const int8_t *__restrict__ geno, int64_t ldg, int N, int Np,
     const int df = groups > 0 ? groups - 1 : 0;
     float al = 0.f, be = 0.f, ga = 0.f;
     const bool excluded = miss && !allow_missing;
-    if (df > 0 && !excluded) {
+    if (linear) {
+      // dosage regression (parametric comparison): rl (2 S_0 + S_1)^2 / S_gg,
+      // S_gg = sum over samples of (g - mean g)^2
+      const int K = n0 + n1 + n2;
+      const float gs = (float)n1 + 2.f * (float)n2;
+      const float sgg = K > 0 ? (float)n1 + 4.f * (float)n2 - gs * gs / (float)K : 0.f;
+      if (df > 0 && !excluded && sgg > 0.5f / (float)(K > 0 ? K : 1)) {
+        al = 4.f * rl / sgg;
+        be = 0.5f;
+      }
+    } else if (df > 0 && !excluded) {
       // sum_i D_i^2 / N_i with D_2 = -(u + v):  (r0 + r2) u^2 + 2 r2 u v + (r1 + r2) v^2
       //   = alpha (u + beta v)^2 + gamma v^2,  alpha = r0 + r2, beta = r2 / alpha,
       //   gamma = r1 + r2 r0 / alpha   (empty groups have r_i = 0).  FP32 is enough:
@@ -247,6 +257,21 @@ cudaError_t launch_pack_multi(const int8_t *geno, int64_t ldg, int N, int Np,
   return cudaGetLastError();
 }
 
+// Packing for the dosage regression of the parametric comparison: the same
+// indicators, coefficients rl (2 S_0 + S_1)^2 / S_gg (rl = 1 / ((K-1) r_c^2)).
+cudaError_t launch_pack_linear(const int8_t *geno, int64_t ldg, int N, int Np, int64_t snp_begin,
+                               int64_t n_snps, double rl, __half *B, ChunkMeta *meta,
+                               unsigned int *status, cudaStream_t s) {
+  const int64_t nchunks = (n_snps + kChunkSnps - 1) / kChunkSnps;
+  const int64_t n_slots = nchunks * kChunkSnps;
+  if (n_slots == 0) return cudaSuccess;
+  const int64_t grid = (n_slots + kPackWarps - 1) / kPackWarps;
+  pack_kernel<<<(unsigned)grid, kPackWarps * 32, 0, s>>>(geno, ldg, N, Np, nullptr, snp_begin, n_snps,
+                                                         n_slots, 0, 0.f, 0.f, 0, 0, B, meta, status,
+                                                         1, (float)rl);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_missing_scan(const int8_t *geno, int64_t ldg, int N, int64_t snp_begin,
                                 int64_t n_snps, int max_code, unsigned int *n_missing,
                                 int64_t *miss_idx, uint64_t *miss_mask, unsigned int *status,
@@ -270,7 +295,8 @@ cudaError_t launch_pack2(const int8_t *geno, int64_t ldg, int N, int Np, const i
   pack_kernel<<<(unsigned)grid, kPackWarps * 32, 0, s>>>(geno, ldg, N, Np, snp_list, snp_begin,
                                                          n_snps, n_slots, snp_out_base,
                                                          (float)(1.0 / h1), (float)(1.0 / h2),
-                                                         allow_missing, signed_df1, B, meta, status);
+                                                         allow_missing, signed_df1, B, meta, status,
+                                                         0, 0.f);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || codes == nullptr) return e;
   const int64_t n_halves = nchunks * 2;

@@ -510,7 +510,7 @@ __device__ __forceinline__ unsigned int hit_event(const uint32_t *dv, bool mine,
       const int j = __ffs(cand) - 1;
       cand &= cand - 1u;
       if (m.snp[jb + j] < 0 || !in_cis_window(p, m.snp[jb + j], trait)) continue;
-      bool hit = ((not_sure >> j) & 1u) == 0u;
+      bool hit = p.provisional != 0 || ((not_sure >> j) & 1u) == 0u;
       if (!hit)
         hit = decide64(__uint_as_float(dv[j]), __uint_as_float(dv[kEpiSnps + j]), m.n[0][jb + j],
                        m.n[1][jb + j], m.n[2][jb + j], m.df[jb + j], cfac, p.pthresh);

@@ -102,3 +102,21 @@ def test_every_autotune_candidate_is_sound_or_refused(lib):
                             assert st in (0, 1, 6), (N, nan, layout, nc, nA, ka, st)
                             if st == 0:
                                 assert plan["smem"] <= 232448 and plan["b_region"] % 1024 == 0
+
+
+def test_parametric_tails_match_scipy(lib):
+    """The FP64 F / t tails of the parametric finalisation (continued fraction of
+    the incomplete beta function), evaluated on the host, against scipy."""
+    import paper_1307_3519_gb300 as k
+    import scipy.special as sps
+    import scipy.stats as st
+    for d1, d2 in [(1, 10), (1, 100), (2, 3), (2, 99), (1, 498), (2, 300)]:
+        for f in [0.01, 0.5, 1.0, 3.0, 7.5, 15.0, 30.0, 80.0]:
+            want = st.f.sf(f, d1, d2)
+            assert k.krux_debug_tail(0, f, d1, d2) == pytest.approx(want, rel=1e-10, abs=1e-300)
+    for nu in [2, 5, 30, 100, 498]:
+        for t in [0.1, 1.0, 2.5, 4.0, 6.0, 9.0, 15.0]:
+            want = 2.0 * st.t.sf(t, nu)
+            assert k.krux_debug_tail(1, t, nu) == pytest.approx(want, rel=1e-10, abs=1e-300)
+    for a, b, x in [(0.5, 0.5, 0.3), (50.0, 0.5, 0.9), (3.0, 7.0, 0.2), (120.0, 1.0, 0.99)]:
+        assert k.krux_debug_tail(2, x, a, b) == pytest.approx(sps.betainc(a, b, x), rel=1e-11)
