@@ -411,6 +411,83 @@ def run_scan_only(args):
               flush=True)
 
 
+def run_row_timings(args):
+    """Timing driver for the other entry points on their workloads (text lines,
+    not the benchmark's JSON): whole calls timed with CUDA events on the current
+    stream, inputs resident, best of `reps` after one warm-up call."""
+    import torch
+    from paper_1307_3519_gb300 import build as kbuild
+    kbuild.build()
+    import paper_1307_3519_gb300 as k
+    import synth
+    kx = k.Krux(0)
+    st = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(name, pairs, fn):
+        out = fn()  # warm-up
+        best = None
+        for _ in range(args.reps):
+            ev0.record(st)
+            out = fn()
+            ev1.record(st)
+            ev1.synchronize()
+            t = ev0.elapsed_time(ev1)
+            best = t if best is None else min(best, t)
+        hits = out if isinstance(out, int) else -1
+        print(f"row {name}: {pairs:.4g} pairs in {best:.3f} ms = {pairs / best * 1e3:.4g} pairs/s "
+              f"(hits {hits})", flush=True)
+
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    want = set(args.rows.split(","))
+    if "missing" in want:  # missing genotype patterns and NaN expression
+        d = synth.config(3)
+        rs, g = kx.krux_rank(dev(d["expr"])), dev(d["geno"])
+        timed("missing-values 5000x100000x102", d["T"] * d["S"],
+              lambda: kx.krux_scan(rs, g, d["pthresh"], capacity=10_000_000)["n_hits"])
+    if "permute" in want:  # 16 permutations and the FDR histogram
+        d = synth.config(4)
+        rs, g, pm = kx.krux_rank(dev(d["expr"])), dev(d["geno"]), dev(d["perms"])
+        timed("permutations 20000x200000x102, P=16, FDR bins", 17 * d["T"] * d["S"],
+              lambda: kx.krux_permute(rs, g, pm, d["pthresh"], capacity=50_000_000, fdr_bins=40,
+                                      fdr_bin_width=0.1)["n_hits"])
+    if "cis" in want:  # 1 Mbp window on a 22-chromosome map
+        d = synth.config(2)
+        rs, g = kx.krux_rank(dev(d["expr"])), dev(d["geno"])
+        sp, tp = synth.genome_positions(np.random.default_rng(7), d["S"], d["T"])
+        sp, tp = dev(sp), dev(tp)
+        timed("cis 1 Mbp, 20000x500000x102 (pairs of the full product)", d["T"] * d["S"],
+              lambda: kx.krux_scan_cis(rs, g, sp, tp, 1_000_000, d["pthresh"],
+                                       capacity=50_000_000)["n_hits"])
+    if "multi" in want:  # markers with 2..5 genotype groups
+        rng = np.random.default_rng(3)
+        T, S = 20000, 100000
+        rs = kx.krux_rank(dev(synth.expression_lognormal(rng, T, 102)))
+        g = dev(synth.multiallelic_genotypes(rng, S, 102))
+        timed("multi-allelic 20000x100000x102", T * S,
+              lambda: kx.krux_scan(rs, g, 1e-5, capacity=10_000_000, multiallelic=True)["n_hits"])
+    for model in ("anova", "linear"):
+        if "param-" + model in want:
+            d = synth.config(2, S=100000)
+            e, g = dev(d["expr"]), dev(d["geno"])
+            timed(f"parametric {model} 20000x100000x102", d["T"] * d["S"],
+                  lambda: kx.krux_scan_parametric(e, g, model, 1e-5, capacity=10_000_000)["n_hits"])
+    if "cohorts" in want:  # 8 cohorts of uneven N in one grouped launch, direct and graph
+        d = synth.config(5)
+        cohorts = [dict(rs=kx.krux_rank(dev(c["expr"])), geno=dev(c["geno"]), capacity=5_000_000)
+                   for c in d["cohorts"]]
+        pairs = sum(c["rs"].T * c["geno"].shape[0] for c in cohorts)
+        timed("8 cohorts N=48..500, 15000x300000 each", pairs,
+              lambda: sum(r["n_hits"] for r in kx.krux_scan_grouped(cohorts, d["pthresh"])))
+        graph = kx.graph_grouped(cohorts, d["pthresh"])
+
+        def replay():
+            graph.launch(st)
+            return sum(r["n_hits"] for r in graph.wait())
+        timed("8 cohorts, CUDA-graph replay", pairs, replay)
+        graph.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -424,11 +501,17 @@ def main():
     ap.add_argument("--snps", type=int, default=100000)
     ap.add_argument("--data", default="hwe", choices=["hwe", "paper", "multi"])
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--rows", default="",
+                    help="timing driver: comma list of missing,permute,cis,multi,param-anova,"
+                         "param-linear,cohorts")
     ap.add_argument("--tile", default="",
                     help="scan-only: launch shape layout,nc,nA,ka instead of the autotuner's")
     ap.add_argument("--no-autotune", action="store_true",
                     help="scan-only: the automatic launch shape instead of the autotuner's")
     args = ap.parse_args()
+    if args.rows:
+        run_row_timings(args)
+        return
     if args.scan_only:
         run_scan_only(args)
         return
