@@ -315,17 +315,18 @@ struct GroupPlan {
   GroupDesc d;
   int64_t n_btiles = 0;
   int64_t steps = 0;
+  int64_t step_lo = 0;  // first step scanned (a min-p seed pass skips the unpermuted agroup)
 };
 
 std::vector<WorkItem> make_items(const std::vector<GroupPlan> &gp, int nc, int grid) {
   int64_t nb = 0, maxL = 1;
   for (auto &g : gp) {
     nb += g.n_btiles;
-    maxL = std::max(maxL, g.steps);
+    maxL = std::max(maxL, g.steps - g.step_lo);
   }
   int best_split = 1;
   double best = 1e300;
-  for (int s = 1; s <= 16 && s <= maxL; ++s) {
+  for (int s = 1; s <= 32 && s <= maxL; ++s) {
     const int64_t items = nb * s;
     const int64_t waves = (items + grid - 1) / grid;
     const double cost = (double)waves * ((double)maxL / s + 2.0);
@@ -337,15 +338,15 @@ std::vector<WorkItem> make_items(const std::vector<GroupPlan> &gp, int nc, int g
   std::vector<WorkItem> items;
   for (size_t gi = 0; gi < gp.size(); ++gi) {
     const auto &g = gp[gi];
-    const int64_t L = g.steps;
+    const int64_t L = g.steps - g.step_lo;
     const int s = (int)std::min<int64_t>(best_split, L);
     for (int64_t b = 0; b < g.n_btiles; ++b)
       for (int k = 0; k < s; ++k) {
         WorkItem w;
         w.group = (int32_t)gi;
         w.btile = (int32_t)b;
-        w.step_begin = (int32_t)(L * k / s);
-        w.step_end = (int32_t)(L * (k + 1) / s);
+        w.step_begin = (int32_t)(g.step_lo + L * k / s);
+        w.step_end = (int32_t)(g.step_lo + L * (k + 1) / s);
         if (w.step_end > w.step_begin) items.push_back(w);
       }
   }
@@ -733,6 +734,8 @@ struct CallPlan {
     double *minp = nullptr;      // caller's [P][T]
     uint16_t *lists = nullptr;   // [1 + P][T][N] NaN sample lists (rank sets with NaN)
     int32_t *inv = nullptr;      // [P][N] inverse permutations
+    bool pre_done = false;       // the stacking was queued already (before a seed pass)
+    bool seed = false;           // min-p seed pass: permuted agroups only, no hits, no FDR
   } perm;
   bool multi = false;  // markers with codes 0..4 (chunks of kChunkSnpsM SNPs)
   struct Param {  // parametric comparison: fused test bounds and the FP64 decision
@@ -1083,6 +1086,7 @@ krux_status prepare_fused(krux_ctx *ctx, CallPlan &cp, const krux_opts *o, Fused
     nc_max = std::max(nc_max, d.nc);
     plans[i].n_btiles = (nch + d.nc - 1) / d.nc;
     plans[i].steps = (int64_t)g.n_agroups * rs->n_ttiles;
+    if (cp.perm.seed) plans[i].step_lo = rs->n_ttiles;
     descs[i] = d;
   }
   std::vector<WorkItem> items =
@@ -1131,6 +1135,7 @@ krux_status prepare_fused(krux_ctx *ctx, CallPlan &cp, const krux_opts *o, Fused
   p.fdr_l0 = cp.fdr_l0;
   p.fdr_w = cp.fdr_w;
   p.multi = cp.multi ? 1 : 0;
+  for (auto &g : cp.groups) p.perm |= g.minp_key != nullptr ? 1 : 0;
   if (cp.cis.on) {
     p.cis_snp_pos = cp.cis.snp_pos;
     p.cis_trait_pos = cp.cis.trait_pos;
@@ -1166,7 +1171,8 @@ krux_status enqueue_fused(krux_ctx *ctx, CallPlan &cp, const FusedLaunch &fl, cu
   const int ng = (int)cp.groups.size();
   const int nslots = fl.nslots;
   KRUX_CUDA(ctx, cudaMemsetAsync(ctx->counters.p, 0, (size_t)nslots * 16 + 8, s));
-  KRUX_CUDA(ctx, cudaMemsetAsync(ctx->status.p, 0, 64, s));
+  if (!cp.perm.pre_done)  // else the seed pass before this launch cleared it
+    KRUX_CUDA(ctx, cudaMemsetAsync(ctx->status.p, 0, 64, s));
   if (cp.fdr_hist)
     KRUX_CUDA(ctx, cudaMemsetAsync(cp.fdr_hist, 0, (size_t)cp.fdr_rows * cp.fdr_bins * 8, s));
   if (ng == 0) {  // nothing to scan: a permutation batch still reports min p = 1
@@ -1179,7 +1185,7 @@ krux_status enqueue_fused(krux_ctx *ctx, CallPlan &cp, const FusedLaunch &fl, cu
     return KRUX_OK;
   }
   unsigned int *status = ctx->status.as<unsigned int>();
-  if (cp.perm.on) {
+  if (cp.perm.on && !cp.perm.pre_done) {
     const CallPlan::PermJob &pj = cp.perm;
     const krux_rankset *rs = pj.rs;
     const size_t one = (size_t)rs->rows_pad * rs->Np;
@@ -1255,7 +1261,7 @@ krux_status enqueue_fused(krux_ctx *ctx, CallPlan &cp, const FusedLaunch &fl, cu
                                        cp.fdr_w));
   }
   ev_record(ctx, 6, s);
-  if (cp.perm.on)
+  if (cp.perm.on && !cp.perm.seed)
     KRUX_CUDA(ctx, launch_minp_from_key(ctx->minpkey.as<double>(), cp.perm.minp, cp.perm.P,
                                         cp.perm.rs->T, cp.perm.rs->rows_pad, s));
   return KRUX_OK;
@@ -1763,6 +1769,26 @@ extern "C" krux_status krux_permute(krux_ctx *ctx, const krux_rankset *rs, const
   st = plan_permute(ctx, cp, rs, geno, S, ldg, perms, P, opts, minp, hits, hit_H, hit_p, fdr_hist,
                     fdr_bins, fdr_bin_width, s);
   if (st != KRUX_OK) return st;
+  // Seed pass: the permuted agroups against the first kSeedSnps SNPs, so that
+  // the main launch starts from running minima over thousands of SNPs instead of
+  // none (without it the first wave of CTAs refines nearly every chunk in FP64).
+  constexpr int64_t kSeedSnps = 8192;
+  if (cp.groups.size() == 1 && cp.groups[0].n_snps > 8 * kSeedSnps) {
+    CallPlan seed = cp;
+    seed.groups[0].n_snps = kSeedSnps;
+    seed.slots[0].capacity = 0;
+    seed.fdr_hist = nullptr;
+    seed.perm.seed = true;
+    FusedLaunch fs;
+    st = prepare_fused(ctx, seed, opts, fs, s);
+    if (st != KRUX_OK) return st;
+    st = enqueue_fused(ctx, seed, fs, s);
+    if (st != KRUX_OK) return st;
+    if (ctx->profiling) ctx->prof.launches += fused_launches(seed, fs);
+    // the main launch's planning may reallocate buffers the seed pass still reads
+    KRUX_CUDA(ctx, cudaStreamSynchronize(s));
+    cp.perm.pre_done = true;
+  }
   std::vector<unsigned long long> counts;
   st = run_fused(ctx, cp, opts, s, counts);
   if (st != KRUX_OK) return st;

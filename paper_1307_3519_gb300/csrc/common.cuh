@@ -196,6 +196,8 @@ struct ScanParams {
   // parametric comparison: every pair at or above the lower band edge is kept as
   // a provisional hit (decided later in FP64 from the FP32 values)
   int32_t provisional = 0;
+  // permutation mode: some groups carry a min-p key (GroupDesc::minp_key)
+  int32_t perm = 0;
 };
 
 enum : unsigned int {

@@ -691,13 +691,32 @@ __device__ __noinline__ unsigned int hit_event_m(const uint32_t *dv, bool mine, 
   return total;
 }
 
-// Running best -ln p of one (permutation, trait) over this thread's SNPs.
+// Hot filter bounds of one (permutation, trait): the running best -ln p turned
+// into bounds on the form, |s| of df-1 SNPs and s of df-2 SNPs.
 struct MinpState {
-  double best;      // FP64 key of the best pair seen (or the global value at step start)
-  double start;     // value read at step start
-  float best_lo;    // FP32 filter bound: best * (1 - margin)
-  float c1, c2;     // H = c1 * |s| for df-1 SNPs; -ln p = c2 * s for df-2 SNPs
+  float s1_lo, s2_lo;
 };
+
+// Bounds of the hot filter from the running best key: with key_lo = key (1 -
+// margin), a df-2 SNP may beat it iff c2 s > key_lo, a df-1 SNP iff
+// -ln erfc(sqrt(c1 |s| / 2)) > key_lo, i.e. c1 |s| > 2 erfcinv(exp(-key_lo))^2 (no
+// transcendental left per chunk).  Past p ~ 1e-35 a lower bound of the inverse is
+// used (the filter stays conservative).
+__device__ __noinline__ MinpState minp_bounds(float key, float c1, float c2, float margin) {
+  const float inf = __int_as_float(0x7f800000);
+  const float klo = key * (1.f - margin);
+  MinpState ms;
+  ms.s2_lo = c2 > 0.f ? klo / c2 : inf;
+  float h1 = 0.f;
+  if (klo > 80.f) {
+    h1 = 2.f * (klo - 0.5f * logf(3.14159265f * klo) - 1.f);
+  } else if (klo > 0.f) {
+    const float x = erfcinvf(expf(-klo));
+    h1 = 2.f * x * x * (1.f - 1e-5f);
+  }
+  ms.s1_lo = c1 > 0.f ? h1 / c1 : inf;
+  return ms;
+}
 
 // Hot filter of a permuted chunk half: largest df-2 form and most negative df-1
 // form over kEpiSnps SNPs, turned into an FP32 -ln p bound; true if some SNP may beat
@@ -729,50 +748,116 @@ __device__ __forceinline__ bool minp_fast(const uint32_t (&d0)[kEpiSnps], const 
       smin = fmin3(smin, __uint_as_float(sa), __uint_as_float(sb));
     }
   }
-  return fmaxf(smax * st.c2, key1f(-smin * st.c1)) > st.best_lo || fmaxf(smax, -smin) >= tau_lo;
+  return smax > st.s2_lo || -smin > st.s1_lo || fmaxf(smax, -smin) >= tau_lo;
 }
 
-// Rare path of a permuted chunk half: FP64 -ln p of every SNP that may beat the
-// running best (returned), and, with the FDR histogram on, the bin count of
-// every pair with p < P_c (row `row` of the histogram).
-__device__ __noinline__ double minp_slow(const uint32_t *dv, const ChunkMeta &m,
-                                         const uint64_t *codes, int h, double cfac, int nan_cnt,
-                                         const uint16_t *nan_idx, double best, float best_lo,
-                                         float c1, float c2, float tau_lo, const ScanParams &p,
-                                         int row) {
+// The leading pair of one (permutation, trait) in a step: its FP32 key and the
+// data to recompute it in FP64 (done once, at the end of the step, unless a
+// near tie asked for it earlier).  Lives in local memory: touched only by the
+// rare paths.
+struct MinpLead {
+  float key32;    // FP32 -ln p of the leader (the global value at step start if none)
+  float u, v;     // its centred sums
+  int n0, n1, n2, df;
+  double key64;   // FP64 -ln p once refined
+  int valid, refined;
+  double start;   // the global value at step start
+  float c1, c2;   // H = c1 |s| for df-1 SNPs; -ln p = c2 s for df-2 SNPs
+};
+
+// FP64 -ln p of a pair from its exact sums (0 for degenerate pairs).
+__device__ __noinline__ double lead_key64(float u, float v, int n0, int n1, int n2, int df,
+                                          double cfac) {
+  if (df <= 0 || !(cfac > 0.0)) return 0.0;
+  return key64_of(kw_H64((int)u, (int)v, n0, n1, n2, cfac), df);
+}
+
+// Rare path of a permuted chunk half: FP32 -ln p of the SNPs, leader update with
+// an FP64 decision only between near ties (FP32 keys within the recheck margin),
+// and, with the FDR histogram on, the FP64 bin count of every pair with p < P_c
+// (row `row` of the histogram).  start = the global best at step start.  Returns
+// the leader's FP32 key (the filter's new bound).
+__device__ __noinline__ float minp_slow(const uint32_t *dv, const ChunkMeta &m,
+                                        const uint64_t *codes, int h, double cfac, int nan_cnt,
+                                        const uint16_t *nan_idx, MinpLead *L, MinpState ms,
+                                        float tau_lo, const ScanParams &p, int row) {
+  const float c1 = L->c1, c2 = L->c2;
+  const double start = L->start;
   const int jb = kEpiSnps * h;
   const float *al = m.alpha + jb, *be = m.beta + jb, *ga = m.gamma + jb;
   const double key_c = -log(p.pthresh);  // -ln P_c
+  const float tie = p.margin;
   for (int j = 0; j < kEpiSnps; ++j) {
     if (m.snp[jb + j] < 0) continue;
     const float u = __uint_as_float(dv[j]), v = __uint_as_float(dv[kEpiSnps + j]);
+    int n0 = m.n[0][jb + j], n1 = m.n[1][jb + j], n2 = m.n[2][jb + j], df = m.df[jb + j];
+    float kf;
+    bool exact = false;  // this pair's FP64 key is needed now
     double key = -1.0;
     if (nan_cnt > 0) {
-      int n0, n1, n2;
       pair_counts(nan_cnt, nan_idx, m, codes, jb + j, n0, n1, n2);
-      const int df = df_of(n0, n1, n2);
-      if (df > 0 && cfac > 0.0) key = key64_of(kw_H64((int)u, (int)v, n0, n1, n2, cfac), df);
+      df = df_of(n0, n1, n2);
+      key = lead_key64(u, v, n0, n1, n2, df, cfac);
+      kf = (float)key;
+      exact = true;
     } else {
       const float sv = kw_s(u, v, al[j], be[j], ga[j]);
-      const float kf = sv > 0.f ? sv * c2 : key1f(-sv * c1);
-      if (kf > best_lo || fabsf(sv) >= tau_lo)
-        key = key64_of(kw_H64((int)u, (int)v, m.n[0][jb + j], m.n[1][jb + j], m.n[2][jb + j], cfac),
-                       m.df[jb + j]);
+      // the hot filter's test, per SNP: below both bounds the pair can neither lead
+      // nor reach the band
+      if (!(sv > ms.s2_lo || -sv > ms.s1_lo || fabsf(sv) >= tau_lo)) continue;
+      kf = sv > 0.f ? sv * c2 : key1f(-sv * c1);
+      if (fabsf(sv) >= tau_lo && p.fdr_hist != nullptr) {
+        key = lead_key64(u, v, n0, n1, n2, df, cfac);
+        exact = true;
+      }
     }
     if (p.fdr_hist != nullptr && key > key_c)
       atomicAdd(p.fdr_hist + (int64_t)row * p.fdr_bins + fdr_bin(key, p.fdr_l0, p.fdr_w, p.fdr_bins),
                 1ull);
-    if (key > best) {
-      best = key;
-      best_lo = (float)key * (1.f - p.margin);
+    if (kf > L->key32 * (1.f + tie) && !exact) {  // a clear new leader: FP64 later
+      L->key32 = kf;
+      L->u = u;
+      L->v = v;
+      L->n0 = n0;
+      L->n1 = n1;
+      L->n2 = n2;
+      L->df = df;
+      L->valid = 1;
+      L->refined = 0;
+    } else if (kf >= L->key32 * (1.f - tie)) {  // near the leader (or exact): decide in FP64
+      if (!exact) key = lead_key64(u, v, n0, n1, n2, df, cfac);
+      double lead = start;
+      if (L->valid) {
+        if (!L->refined) {
+          L->key64 = lead_key64(L->u, L->v, L->n0, L->n1, L->n2, L->df, cfac);
+          L->refined = 1;
+        }
+        lead = L->key64;
+      }
+      if (key > lead) {
+        L->key32 = fmaxf(kf, L->key32);
+        L->u = u;
+        L->v = v;
+        L->n0 = n0;
+        L->n1 = n1;
+        L->n2 = n2;
+        L->df = df;
+        L->key64 = key;
+        L->valid = 1;
+        L->refined = 1;
+      }
     }
   }
-  return best;
+  return L->key32;
 }
 
-// kMulti: markers with up to five genotype groups (32-SNP chunks, ChunkMetaM);
-// the producer and MMA warps are the same in both forms.
-template <bool kMulti>
+// Kernel forms: the plain scan, markers with up to five genotype groups (32-SNP
+// chunks, ChunkMetaM), and the permutation scan (groups with a min-p key); the
+// producer and MMA warps are the same in all three.  Separate forms keep the
+// state of one out of the registers of the others.
+enum ScanForm { kFormScan = 0, kFormMulti = 1, kFormPerm = 2 };
+
+template <int kForm>
 __global__ void __launch_bounds__(kScanThreads, 1) krux_scan_kernel(const __grid_constant__ ScanParams p) {
   extern __shared__ uint8_t smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1065,25 +1150,27 @@ __global__ void __launch_bounds__(kScanThreads, 1) krux_scan_kernel(const __grid
         et.nan_idx = g_has_nan && et.valid
                          ? g.nan_idx + ag * g.nan_ag_stride + (int64_t)et.trait * g_N
                          : nullptr;
-        const bool minp_mode = g.minp_key != nullptr && ag > 0;
+        const bool minp_mode = kForm == kFormPerm && g.minp_key != nullptr && ag > 0;
         // with the FDR histogram on, permuted pairs at or above the band are counted
         const float fdr_tau_lo = p.fdr_hist != nullptr ? -et.ntlo : __int_as_float(0x7f800000);
         // min-p state: FP64 work only in permuted groups (FP64 issue is slow here)
         MinpState ms;
+        MinpLead lead;
         double *key_ptr = nullptr;
         if (minp_mode) {
-          ms.best = 0.0;
-          ms.start = 0.0;
-          ms.c1 = 0.f;
-          ms.c2 = 0.f;
+          lead.start = 0.0;
+          lead.c1 = 0.f;
+          lead.c2 = 0.f;
           if (et.valid) {
-            ms.c1 = (float)(et.cfac * (double)p.h1);
-            ms.c2 = (float)(et.cfac * (double)p.h2 * 0.5);
+            lead.c1 = (float)et.cfac * p.h1;  // FP32: these only scale the filter
+            lead.c2 = (float)et.cfac * p.h2 * 0.5f;
             key_ptr = g.minp_key + (int64_t)(ag - 1) * g.rows_per_agroup + et.trait;
-            ms.start = reinterpret_cast<const double *>(tcp + 1536)[row];
-            ms.best = ms.start;
+            lead.start = reinterpret_cast<const double *>(tcp + 1536)[row];
           }
-          ms.best_lo = (float)ms.best * (1.f - p.margin);
+          lead.key32 = (float)lead.start;
+          lead.valid = 0;
+          lead.refined = 0;
+          ms = minp_bounds(lead.key32, lead.c1, lead.c2, p.margin);
         }
         for (int c = 0; c < nc_item; ++c) {
           bool ok = true;
@@ -1091,7 +1178,7 @@ __global__ void __launch_bounds__(kScanThreads, 1) krux_scan_kernel(const __grid
           ok = ok && wait_bar(t_full(slot), slot_phase, wc, 7);
           if (!__all_sync(0xffffffffu, ok)) goto epi_done;
           tc_fence_after();
-          if constexpr (kMulti) {
+          if constexpr (kForm == kFormMulti) {
             // markers with up to five groups: this warp's 8 SNPs of a 32-SNP chunk,
             // D_i of SNP j in column 32 i + j (i = 0..3)
             uint32_t dd[kMaxCodeM][kEpiSnpsM];
@@ -1152,9 +1239,9 @@ __global__ void __launch_bounds__(kScanThreads, 1) krux_scan_kernel(const __grid
               }
               if (minp_mode) {
                 if (need) {
-                  ms.best = minp_slow(dv, mc, codes, h, et.cfac, et.nan_cnt, et.nan_idx, ms.best,
-                                      ms.best_lo, ms.c1, ms.c2, fdr_tau_lo, p, ag);
-                  ms.best_lo = (float)ms.best * (1.f - p.margin);
+                  const float k32 = minp_slow(dv, mc, codes, h, et.cfac, et.nan_cnt, et.nan_idx,
+                                              &lead, ms, fdr_tau_lo, p, ag);
+                  ms = minp_bounds(k32, lead.c1, lead.c2, p.margin);
                 }
               } else if (__any_sync(0xffffffffu, p.dense || et.nan_cnt > 0)) {
                 hit_slow(dv, need, mc, codes, h, et.trait, et.valid, et.ntlo, et.nthi, et.cfac,
@@ -1170,9 +1257,14 @@ __global__ void __launch_bounds__(kScanThreads, 1) krux_scan_kernel(const __grid
             if (lane == 0) mbar_arrive(b_empty(c));
           }
         }
-        if (minp_mode && key_ptr != nullptr && ms.best > ms.start)
-          atomicMax(reinterpret_cast<unsigned long long *>(key_ptr),
-                    (unsigned long long)__double_as_longlong(ms.best));
+        if (minp_mode && key_ptr != nullptr && lead.valid) {
+          const double k64 = lead.refined ? lead.key64
+                                          : lead_key64(lead.u, lead.v, lead.n0, lead.n1, lead.n2,
+                                                       lead.df, et.cfac);
+          if (k64 > lead.start)
+            atomicMax(reinterpret_cast<unsigned long long *>(key_ptr),
+                      (unsigned long long)__double_as_longlong(k64));
+        }
         __syncwarp();
         if (lane == 0) mbar_arrive(tc_empty(tc_e));
         if (++tc_e == (uint32_t)kTcDepth) {
@@ -1355,18 +1447,23 @@ size_t scan_smem_bytes2(int nc, int nA, size_t a_tile_bytes, size_t b_region, in
 }
 
 cudaError_t scan_set_smem(size_t smem) {
-  cudaError_t e = cudaFuncSetAttribute(krux_scan_kernel<false>,
+  cudaError_t e = cudaFuncSetAttribute(krux_scan_kernel<kFormScan>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(krux_scan_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)smem);
+  e = cudaFuncSetAttribute(krux_scan_kernel<kFormMulti>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(krux_scan_kernel<kFormPerm>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
 cudaError_t launch_scan_only(const ScanParams &p, int grid, size_t smem, cudaStream_t s) {
   if (p.multi)
-    krux_scan_kernel<true><<<grid, kScanThreads, smem, s>>>(p);
+    krux_scan_kernel<kFormMulti><<<grid, kScanThreads, smem, s>>>(p);
+  else if (p.perm)
+    krux_scan_kernel<kFormPerm><<<grid, kScanThreads, smem, s>>>(p);
   else
-    krux_scan_kernel<false><<<grid, kScanThreads, smem, s>>>(p);
+    krux_scan_kernel<kFormScan><<<grid, kScanThreads, smem, s>>>(p);
   return cudaGetLastError();
 }
 
