@@ -751,18 +751,26 @@ __device__ __forceinline__ bool minp_fast(const uint32_t (&d0)[kEpiSnps], const 
   return smax > st.s2_lo || -smin > st.s1_lo || fmaxf(smax, -smin) >= tau_lo;
 }
 
-// The leading pair of one (permutation, trait) in a step: its FP32 key and the
-// data to recompute it in FP64 (done once, at the end of the step, unless a
-// near tie asked for it earlier).  Lives in local memory: touched only by the
-// rare paths.
+// Class leader of one (permutation, trait) in a step: the pair with the largest
+// form value among its df-1 SNPs (value |s|) or among its df-2 SNPs (value s).
+// Within a class -ln p grows with the value (-ln p = c2 s for df 2, a function of
+// c1 |s| that increases for df 1), so tracking the value needs no transcendental;
+// the FP64 key is computed once, at the end of the step, or earlier on a near tie.
+struct MinpCand {
+  float s;        // FP32 value (0: no leader yet)
+  float u, v;     // centred sums
+  int n01;        // n0 | n1 << 16
+  int n2df;       // n2 | df << 16
+  double k64;     // FP64 -ln p once computed, else -1
+};
+
+// Leader state of one (permutation, trait) in a step.  Lives in local memory:
+// touched only by the rare paths and at step boundaries.
 struct MinpLead {
-  float key32;    // FP32 -ln p of the leader (the global value at step start if none)
-  float u, v;     // its centred sums
-  int n0, n1, n2, df;
-  double key64;   // FP64 -ln p once refined
-  int valid, refined;
-  double start;   // the global value at step start
-  float c1, c2;   // H = c1 |s| for df-1 SNPs; -ln p = c2 s for df-2 SNPs
+  MinpCand cls[2];  // [0]: df-1 SNPs, [1]: df-2 SNPs
+  double exact;     // best FP64 key of the pairs decided exactly (traits with NaN), else -1
+  double start;     // the global value at step start
+  float c1, c2;     // H = c1 |s| for df-1 SNPs; -ln p = c2 s for df-2 SNPs
 };
 
 // FP64 -ln p of a pair from its exact sums (0 for degenerate pairs).
@@ -772,83 +780,92 @@ __device__ __noinline__ double lead_key64(float u, float v, int n0, int n1, int 
   return key64_of(kw_H64((int)u, (int)v, n0, n1, n2, cfac), df);
 }
 
-// Rare path of a permuted chunk half: FP32 -ln p of the SNPs, leader update with
-// an FP64 decision only between near ties (FP32 keys within the recheck margin),
-// and, with the FDR histogram on, the FP64 bin count of every pair with p < P_c
-// (row `row` of the histogram).  start = the global best at step start.  Returns
-// the leader's FP32 key (the filter's new bound).
-__device__ __noinline__ float minp_slow(const uint32_t *dv, const ChunkMeta &m,
-                                        const uint64_t *codes, int h, double cfac, int nan_cnt,
-                                        const uint16_t *nan_idx, MinpLead *L, MinpState ms,
-                                        float tau_lo, const ScanParams &p, int row) {
-  const float c1 = L->c1, c2 = L->c2;
-  const double start = L->start;
+__device__ __forceinline__ double cand_key64(MinpCand &C, double cfac) {
+  if (C.k64 < 0.0)
+    C.k64 = lead_key64(C.u, C.v, C.n01 & 0xffff, C.n01 >> 16, C.n2df & 0xffff, C.n2df >> 16, cfac);
+  return C.k64;
+}
+
+// Rare path of a permuted chunk half (trait without NaN): every SNP past the hot
+// filter's bounds is offered to its class leader.  A clearly larger value (by more
+// than the recheck margin) takes the lead without FP64; a near tie is decided on
+// the FP64 keys.  The bound of the class then rises to the leader's value less the
+// margin, so that only pairs that may beat the leader pass again.  With the FDR
+// histogram on, every pair at or above the band gets its FP64 key and, if p < P_c,
+// a count in row `row` of the histogram.
+__device__ __noinline__ MinpState minp_event(const uint32_t *dv, const ChunkMeta &m, int h,
+                                             double cfac, MinpLead *L, MinpState ms, float tau_lo,
+                                             const ScanParams &p, int row) {
   const int jb = kEpiSnps * h;
   const float *al = m.alpha + jb, *be = m.beta + jb, *ga = m.gamma + jb;
-  const double key_c = -log(p.pthresh);  // -ln P_c
   const float tie = p.margin;
   for (int j = 0; j < kEpiSnps; ++j) {
     if (m.snp[jb + j] < 0) continue;
     const float u = __uint_as_float(dv[j]), v = __uint_as_float(dv[kEpiSnps + j]);
-    int n0 = m.n[0][jb + j], n1 = m.n[1][jb + j], n2 = m.n[2][jb + j], df = m.df[jb + j];
-    float kf;
-    bool exact = false;  // this pair's FP64 key is needed now
+    const float sv = kw_s(u, v, al[j], be[j], ga[j]);
+    const bool lead = sv > ms.s2_lo || -sv > ms.s1_lo;
+    const bool band = p.fdr_hist != nullptr && fabsf(sv) >= tau_lo;
+    if (!lead && !band) continue;
+    const int n0 = m.n[0][jb + j], n1 = m.n[1][jb + j], n2 = m.n[2][jb + j], df = m.df[jb + j];
     double key = -1.0;
-    if (nan_cnt > 0) {
-      pair_counts(nan_cnt, nan_idx, m, codes, jb + j, n0, n1, n2);
-      df = df_of(n0, n1, n2);
+    if (band) {
       key = lead_key64(u, v, n0, n1, n2, df, cfac);
-      kf = (float)key;
-      exact = true;
-    } else {
-      const float sv = kw_s(u, v, al[j], be[j], ga[j]);
-      // the hot filter's test, per SNP: below both bounds the pair can neither lead
-      // nor reach the band
-      if (!(sv > ms.s2_lo || -sv > ms.s1_lo || fabsf(sv) >= tau_lo)) continue;
-      kf = sv > 0.f ? sv * c2 : key1f(-sv * c1);
-      if (fabsf(sv) >= tau_lo && p.fdr_hist != nullptr) {
-        key = lead_key64(u, v, n0, n1, n2, df, cfac);
-        exact = true;
-      }
+      if (key > -log(p.pthresh))
+        atomicAdd(p.fdr_hist + (int64_t)row * p.fdr_bins +
+                      fdr_bin(key, p.fdr_l0, p.fdr_w, p.fdr_bins),
+                  1ull);
     }
-    if (p.fdr_hist != nullptr && key > key_c)
+    if (!lead) continue;
+    const int k = sv > 0.f ? 1 : 0;
+    const float a = fabsf(sv);
+    MinpCand &C = L->cls[k];
+    bool take = a > C.s * (1.f + tie);
+    if (!take && a >= C.s * (1.f - tie)) {  // near tie with the leader: FP64
+      if (key < 0.0) key = lead_key64(u, v, n0, n1, n2, df, cfac);
+      take = key > cand_key64(C, cfac);
+    }
+    if (take) {
+      C.s = fmaxf(a, C.s);
+      C.u = u;
+      C.v = v;
+      C.n01 = n0 | (n1 << 16);
+      C.n2df = n2 | (df << 16);
+      C.k64 = key;
+    }
+    if (k) ms.s2_lo = fmaxf(ms.s2_lo, C.s * (1.f - tie));
+    else ms.s1_lo = fmaxf(ms.s1_lo, C.s * (1.f - tie));
+  }
+  return ms;
+}
+
+// Rare path of a permuted chunk half for a trait with NaN: the group sizes of each
+// pair come from the genotype codes of its present samples, every pair is decided
+// on its FP64 key (max into L->exact) and, with the FDR histogram on, counted.
+__device__ __noinline__ void minp_event_nan(const uint32_t *dv, const ChunkMeta &m,
+                                            const uint64_t *codes, int h, double cfac,
+                                            int nan_cnt, const uint16_t *nan_idx, MinpLead *L,
+                                            const ScanParams &p, int row) {
+  const int jb = kEpiSnps * h;
+  for (int j = 0; j < kEpiSnps; ++j) {
+    if (m.snp[jb + j] < 0) continue;
+    const float u = __uint_as_float(dv[j]), v = __uint_as_float(dv[kEpiSnps + j]);
+    int n0, n1, n2;
+    pair_counts(nan_cnt, nan_idx, m, codes, jb + j, n0, n1, n2);
+    const double key = lead_key64(u, v, n0, n1, n2, df_of(n0, n1, n2), cfac);
+    if (p.fdr_hist != nullptr && key > -log(p.pthresh))
       atomicAdd(p.fdr_hist + (int64_t)row * p.fdr_bins + fdr_bin(key, p.fdr_l0, p.fdr_w, p.fdr_bins),
                 1ull);
-    if (kf > L->key32 * (1.f + tie) && !exact) {  // a clear new leader: FP64 later
-      L->key32 = kf;
-      L->u = u;
-      L->v = v;
-      L->n0 = n0;
-      L->n1 = n1;
-      L->n2 = n2;
-      L->df = df;
-      L->valid = 1;
-      L->refined = 0;
-    } else if (kf >= L->key32 * (1.f - tie)) {  // near the leader (or exact): decide in FP64
-      if (!exact) key = lead_key64(u, v, n0, n1, n2, df, cfac);
-      double lead = start;
-      if (L->valid) {
-        if (!L->refined) {
-          L->key64 = lead_key64(L->u, L->v, L->n0, L->n1, L->n2, L->df, cfac);
-          L->refined = 1;
-        }
-        lead = L->key64;
-      }
-      if (key > lead) {
-        L->key32 = fmaxf(kf, L->key32);
-        L->u = u;
-        L->v = v;
-        L->n0 = n0;
-        L->n1 = n1;
-        L->n2 = n2;
-        L->df = df;
-        L->key64 = key;
-        L->valid = 1;
-        L->refined = 1;
-      }
-    }
+    L->exact = fmax(L->exact, key);
   }
-  return L->key32;
+}
+
+// End of a step: the best FP64 key of the step's leaders, if it beats the global
+// value read at step start.
+__device__ __noinline__ double minp_step_best(MinpLead *L, double cfac) {
+  double best = L->exact;
+  for (int k = 0; k < 2; ++k)
+    if (L->cls[k].s > 0.f) best = fmax(best, cand_key64(L->cls[k], cfac));
+  return best;
 }
 
 // Kernel forms: the plain scan, markers with up to five genotype groups (32-SNP
@@ -1167,10 +1184,12 @@ __global__ void __launch_bounds__(kScanThreads, 1) krux_scan_kernel(const __grid
             key_ptr = g.minp_key + (int64_t)(ag - 1) * g.rows_per_agroup + et.trait;
             lead.start = reinterpret_cast<const double *>(tcp + 1536)[row];
           }
-          lead.key32 = (float)lead.start;
-          lead.valid = 0;
-          lead.refined = 0;
-          ms = minp_bounds(lead.key32, lead.c1, lead.c2, p.margin);
+          for (int k = 0; k < 2; ++k) {
+            lead.cls[k].s = 0.f;
+            lead.cls[k].k64 = -1.0;
+          }
+          lead.exact = -1.0;
+          ms = minp_bounds((float)lead.start, lead.c1, lead.c2, p.margin);
         }
         for (int c = 0; c < nc_item; ++c) {
           bool ok = true;
@@ -1239,9 +1258,10 @@ __global__ void __launch_bounds__(kScanThreads, 1) krux_scan_kernel(const __grid
               }
               if (minp_mode) {
                 if (need) {
-                  const float k32 = minp_slow(dv, mc, codes, h, et.cfac, et.nan_cnt, et.nan_idx,
-                                              &lead, ms, fdr_tau_lo, p, ag);
-                  ms = minp_bounds(k32, lead.c1, lead.c2, p.margin);
+                  if (et.nan_cnt > 0)
+                    minp_event_nan(dv, mc, codes, h, et.cfac, et.nan_cnt, et.nan_idx, &lead, p, ag);
+                  else
+                    ms = minp_event(dv, mc, h, et.cfac, &lead, ms, fdr_tau_lo, p, ag);
                 }
               } else if (__any_sync(0xffffffffu, p.dense || et.nan_cnt > 0)) {
                 hit_slow(dv, need, mc, codes, h, et.trait, et.valid, et.ntlo, et.nthi, et.cfac,
@@ -1257,10 +1277,8 @@ __global__ void __launch_bounds__(kScanThreads, 1) krux_scan_kernel(const __grid
             if (lane == 0) mbar_arrive(b_empty(c));
           }
         }
-        if (minp_mode && key_ptr != nullptr && lead.valid) {
-          const double k64 = lead.refined ? lead.key64
-                                          : lead_key64(lead.u, lead.v, lead.n0, lead.n1, lead.n2,
-                                                       lead.df, et.cfac);
+        if (minp_mode && key_ptr != nullptr) {
+          const double k64 = minp_step_best(&lead, et.cfac);
           if (k64 > lead.start)
             atomicMax(reinterpret_cast<unsigned long long *>(key_ptr),
                       (unsigned long long)__double_as_longlong(k64));
