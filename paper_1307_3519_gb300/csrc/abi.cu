@@ -1136,6 +1136,7 @@ krux_status prepare_fused(krux_ctx *ctx, CallPlan &cp, const krux_opts *o, Fused
   p.fdr_w = cp.fdr_w;
   p.multi = cp.multi ? 1 : 0;
   for (auto &g : cp.groups) p.perm |= g.minp_key != nullptr ? 1 : 0;
+  p.seed_bound = cp.perm.seed ? 1 : 0;
   if (cp.cis.on) {
     p.cis_snp_pos = cp.cis.snp_pos;
     p.cis_trait_pos = cp.cis.trait_pos;
@@ -1772,8 +1773,8 @@ extern "C" krux_status krux_permute(krux_ctx *ctx, const krux_rankset *rs, const
   // Seed pass: the permuted agroups against the first kSeedSnps SNPs, so that
   // the main launch starts from running minima over thousands of SNPs instead of
   // none (without it the first wave of CTAs refines nearly every chunk in FP64).
-  constexpr int64_t kSeedSnps = 8192;
-  if (cp.groups.size() == 1 && cp.groups[0].n_snps > 8 * kSeedSnps) {
+  constexpr int64_t kSeedSnps = 16384;
+  if (cp.groups.size() == 1 && cp.groups[0].n_snps > 4 * kSeedSnps) {
     CallPlan seed = cp;
     seed.groups[0].n_snps = kSeedSnps;
     seed.slots[0].capacity = 0;

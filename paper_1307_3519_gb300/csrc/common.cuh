@@ -198,6 +198,9 @@ struct ScanParams {
   int32_t provisional = 0;
   // permutation mode: some groups carry a min-p key (GroupDesc::minp_key)
   int32_t perm = 0;
+  // seed pass of a permutation batch: the permuted groups write, per (permutation,
+  // trait), a lower bound of the best -ln p over the scanned SNPs (no pair is decided)
+  int32_t seed_bound = 0;
 };
 
 enum : unsigned int {

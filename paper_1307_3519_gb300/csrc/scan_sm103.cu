@@ -718,12 +718,11 @@ __device__ __noinline__ MinpState minp_bounds(float key, float c1, float c2, flo
   return ms;
 }
 
-// Hot filter of a permuted chunk half: largest df-2 form and most negative df-1
-// form over kEpiSnps SNPs, turned into an FP32 -ln p bound; true if some SNP may beat
-// the running best, or (FDR histogram on, tau_lo finite) may have p < P_c.
-__device__ __forceinline__ bool minp_fast(const uint32_t (&d0)[kEpiSnps], const uint32_t (&d1)[kEpiSnps],
-                                          const ChunkMeta &m, int h, const MinpState &st,
-                                          float tau_lo) {
+// Largest df-2 form value (smax >= 0) and most negative df-1 form value
+// (smin <= 0) of a permuted chunk half.
+__device__ __forceinline__ void minp_range(const uint32_t (&d0)[kEpiSnps],
+                                           const uint32_t (&d1)[kEpiSnps], const ChunkMeta &m,
+                                           int h, float &smax_out, float &smin_out) {
   const uint64_t *al = reinterpret_cast<const uint64_t *>(m.alpha + kEpiSnps * h);
   const uint64_t *be = reinterpret_cast<const uint64_t *>(m.beta + kEpiSnps * h);
   const uint64_t *ga = reinterpret_cast<const uint64_t *>(m.gamma + kEpiSnps * h);
@@ -748,7 +747,26 @@ __device__ __forceinline__ bool minp_fast(const uint32_t (&d0)[kEpiSnps], const 
       smin = fmin3(smin, __uint_as_float(sa), __uint_as_float(sb));
     }
   }
+  smax_out = smax;
+  smin_out = smin;
+}
+
+// Hot filter of a permuted chunk half: true if some SNP may beat the running best,
+// or (FDR histogram on, tau_lo finite) may have p < P_c.
+__device__ __forceinline__ bool minp_fast(const uint32_t (&d0)[kEpiSnps], const uint32_t (&d1)[kEpiSnps],
+                                          const ChunkMeta &m, int h, const MinpState &st,
+                                          float tau_lo) {
+  float smax, smin;
+  minp_range(d0, d1, m, h, smax, smin);
   return smax > st.s2_lo || -smin > st.s1_lo || fmaxf(smax, -smin) >= tau_lo;
+}
+
+// Seed bound of a step: FP32 -ln p of the largest values seen (ms holds them in
+// seed mode), less twice the recheck margin so that it stays below the FP64 key of
+// the pair that attains it.
+__device__ __noinline__ double minp_seed_key(MinpState ms, float c1, float c2, float margin) {
+  const float k = fmaxf(ms.s2_lo * c2, key1f(ms.s1_lo * c1));
+  return (double)(k * (1.f - 2.f * margin));
 }
 
 // Class leader of one (permutation, trait) in a step: the pair with the largest
@@ -1168,6 +1186,7 @@ __global__ void __launch_bounds__(kScanThreads, 1) krux_scan_kernel(const __grid
                          ? g.nan_idx + ag * g.nan_ag_stride + (int64_t)et.trait * g_N
                          : nullptr;
         const bool minp_mode = kForm == kFormPerm && g.minp_key != nullptr && ag > 0;
+        const bool seed_pass = kForm == kFormPerm && p.seed_bound != 0;
         // with the FDR histogram on, permuted pairs at or above the band are counted
         const float fdr_tau_lo = p.fdr_hist != nullptr ? -et.ntlo : __int_as_float(0x7f800000);
         // min-p state: FP64 work only in permuted groups (FP64 issue is slow here)
@@ -1190,6 +1209,10 @@ __global__ void __launch_bounds__(kScanThreads, 1) krux_scan_kernel(const __grid
           }
           lead.exact = -1.0;
           ms = minp_bounds((float)lead.start, lead.c1, lead.c2, p.margin);
+          if (seed_pass) {  // ms tracks the largest values instead
+            ms.s1_lo = 0.f;
+            ms.s2_lo = 0.f;
+          }
         }
         for (int c = 0; c < nc_item; ++c) {
           bool ok = true;
@@ -1242,7 +1265,14 @@ __global__ void __launch_bounds__(kScanThreads, 1) krux_scan_kernel(const __grid
                 g.codes ? reinterpret_cast<const uint64_t *>(scodes + (size_t)c * codes_stride) : nullptr;
             const ChunkMeta &mc = smeta[c];
             bool need;
-            if (minp_mode)
+            if (minp_mode && seed_pass) {
+              // seed pass: only the range of the values (traits with NaN sit out)
+              float smax, smin;
+              minp_range(d0, d1, mc, h, smax, smin);
+              ms.s2_lo = fmaxf(ms.s2_lo, smax);
+              ms.s1_lo = fmaxf(ms.s1_lo, -smin);
+              need = false;
+            } else if (minp_mode)
               need = et.valid && (et.nan_cnt > 0 || minp_fast(d0, d1, mc, h, ms, fdr_tau_lo));
             else
               need = p.dense || et.nan_cnt > 0 ||
@@ -1278,7 +1308,9 @@ __global__ void __launch_bounds__(kScanThreads, 1) krux_scan_kernel(const __grid
           }
         }
         if (minp_mode && key_ptr != nullptr) {
-          const double k64 = minp_step_best(&lead, et.cfac);
+          const double k64 = !seed_pass         ? minp_step_best(&lead, et.cfac)
+                             : et.nan_cnt == 0 ? minp_seed_key(ms, lead.c1, lead.c2, p.margin)
+                                               : -1.0;
           if (k64 > lead.start)
             atomicMax(reinterpret_cast<unsigned long long *>(key_ptr),
                       (unsigned long long)__double_as_longlong(k64));
@@ -1535,3 +1567,4 @@ cudaError_t launch_finalize_dev(const krux_hit *hits, const HitAux *aux, const H
 }
 
 }  // namespace krux
+
