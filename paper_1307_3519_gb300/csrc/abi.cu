@@ -49,8 +49,11 @@ cudaError_t launch_pack2(const int8_t *geno, int64_t ldg, int N, int Np, const i
                          int64_t snp_begin, int64_t n_snps, int64_t snp_out_base, double h1,
                          double h2, int allow_missing, int signed_df1, __half *B,
                          ChunkMeta *meta, uint64_t *codes, unsigned int *status, cudaStream_t s);
-cudaError_t launch_rerank_bucket(const RankDev &base, int T, int N, int Np, const int32_t *drop,
-                                 int n_drop, const RankDev &out, cudaStream_t s);
+cudaError_t launch_pack_batch(const PackJob *jobs, int n_jobs, int64_t total_slots,
+                              int64_t total_halves, double h1, double h2, int signed_df1,
+                              unsigned int *status, cudaStream_t s);
+cudaError_t launch_rerank_buckets(const RerankJob *jobs, const int32_t *drops, int n_jobs,
+                                  int max_rows_pad, cudaStream_t s);
 cudaError_t launch_plain_epilogue2(const float *C, int64_t ldc, int T, int n_slots,
                                    const ChunkMeta *meta, const float *tau, const double *cfac,
                                    const uint16_t *nan_cnt, const uint16_t *nan_idx, int N,
@@ -164,7 +167,7 @@ struct krux_ctx {
   PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   cudaEvent_t ev[kEv] = {};
   DevBuf B, meta, codes, groups, items, status, counters, aux, cfacptr, miss_idx, miss_mask,
-      list, gemm_out, bucket_ranks, permA, minpkey, seg, permNan, aux2, param, paramOut;
+      list, gemm_out, bucket_ranks, permA, minpkey, seg, permNan, aux2, param, paramOut, packjobs;
   void *blas = nullptr;
   std::vector<std::pair<size_t, void *>> pool;  // freed rank-set blocks, reused by size
   std::map<int, std::array<int, 4>> tuned;       // krux_autotune: K width -> layout, nc, nA, ka
@@ -481,7 +484,7 @@ void krux_destroy(krux_ctx *ctx) {
   DevBuf *bufs[] = {&ctx->B, &ctx->meta, &ctx->codes, &ctx->groups, &ctx->items, &ctx->status,
                     &ctx->counters, &ctx->aux, &ctx->cfacptr, &ctx->miss_idx, &ctx->miss_mask,
                     &ctx->list, &ctx->gemm_out, &ctx->bucket_ranks, &ctx->permA, &ctx->minpkey, &ctx->seg,
-                    &ctx->permNan, &ctx->aux2, &ctx->param, &ctx->paramOut};
+                    &ctx->permNan, &ctx->aux2, &ctx->param, &ctx->paramOut, &ctx->packjobs};
   for (DevBuf *b : bufs) b->release();
   for (auto &pb : ctx->pool) cudaFree(pb.second);
   for (int i = 0; i < kEv; ++i)
@@ -760,6 +763,7 @@ struct CallPlan {
   double fdr_l0 = 0.0, fdr_w = 1.0;
 };
 
+// Device bytes of one bucket's re-ranked set (A, tie sums, K, tau, cfac).
 size_t bucket_bytes(const krux_rankset *rs) {
   size_t off = 0;
   auto take = [&](size_t b) { off += (b + 255) / 256 * 256; };
@@ -768,9 +772,6 @@ size_t bucket_bytes(const krux_rankset *rs) {
   take((size_t)rs->T * 4);
   take((size_t)rs->rows_pad * 4);
   take((size_t)rs->rows_pad * 8);
-  take((size_t)rs->rows_pad * 2);
-  take((size_t)rs->T * rs->N * 2);
-  take((size_t)rs->n_ttiles * 4);
   return off;
 }
 
@@ -849,23 +850,30 @@ krux_status materialise(krux_ctx *ctx, CallPlan &cp, cudaStream_t s) {
   for (auto &g : cp.groups)
     if (g.list_off >= 0) g.snp_list = ctx->list.as<int64_t>() + g.list_off;
   if (cp.bucket_jobs.empty()) return KRUX_OK;
-  std::vector<size_t> off(cp.bucket_jobs.size());
+  const size_t nb = cp.bucket_jobs.size();
+  std::vector<size_t> off(nb);
   size_t tot = 0;
-  for (size_t i = 0; i < cp.bucket_jobs.size(); ++i) {
+  for (size_t i = 0; i < nb; ++i) {
     off[i] = tot;
     tot += bucket_bytes(cp.bucket_jobs[i].base);
   }
+  std::vector<int32_t> drops;
+  std::vector<RerankJob> jobs(nb);
+  for (size_t i = 0; i < nb; ++i) {
+    jobs[i].drop_off = (int32_t)drops.size();
+    jobs[i].n_drop = (int32_t)cp.bucket_jobs[i].drop.size();
+    drops.insert(drops.end(), cp.bucket_jobs[i].drop.begin(), cp.bucket_jobs[i].drop.end());
+  }
+  if (drops.empty()) drops.push_back(0);
+  const size_t jobs_off = tot;
+  tot += (nb * sizeof(RerankJob) + 255) / 256 * 256;
   const size_t drop_off = tot;
-  tot += cp.bucket_jobs.size() * kMaxN * 4;
+  tot += drops.size() * 4;
   KRUX_CUDA(ctx, ctx->bucket_ranks.ensure(tot));
-  std::vector<int32_t> drops(cp.bucket_jobs.size() * kMaxN, 0);
-  for (size_t i = 0; i < cp.bucket_jobs.size(); ++i)
-    std::copy(cp.bucket_jobs[i].drop.begin(), cp.bucket_jobs[i].drop.end(), drops.begin() + i * kMaxN);
   char *base = ctx->bucket_ranks.as<char>();
-  int32_t *ddrop = reinterpret_cast<int32_t *>(base + drop_off);
-  KRUX_CUDA(ctx, cudaMemcpyAsync(ddrop, drops.data(), drops.size() * 4, cudaMemcpyHostToDevice, s));
-  cp.bucket_sets.assign(cp.bucket_jobs.size(), krux_rankset());
-  for (size_t i = 0; i < cp.bucket_jobs.size(); ++i) {
+  cp.bucket_sets.assign(nb, krux_rankset());
+  int max_rows = 0;
+  for (size_t i = 0; i < nb; ++i) {
     const krux_rankset *rs = cp.bucket_jobs[i].base;
     krux_rankset &bs = cp.bucket_sets[i];
     bs.T = rs->T;
@@ -886,15 +894,30 @@ krux_status materialise(krux_ctx *ctx, CallPlan &cp, cudaStream_t s) {
     bs.dev.K = (int32_t *)take((size_t)rs->T * 4);
     bs.dev.tau = (float *)take((size_t)rs->rows_pad * 4);
     bs.dev.cfac = (double *)take((size_t)rs->rows_pad * 8);
-    bs.dev.nan_cnt = (uint16_t *)take((size_t)rs->rows_pad * 2);
-    bs.dev.nan_idx = (uint16_t *)take((size_t)rs->T * rs->N * 2);
-    bs.dev.tile_nan = (uint32_t *)take((size_t)rs->n_ttiles * 4);
-    KRUX_CUDA(ctx, cudaMemsetAsync(bs.dev.A, 0, (size_t)rs->rows_pad * rs->Np * 2, s));
-    KRUX_CUDA(ctx, cudaMemsetAsync(bs.dev.tile_nan, 0, (size_t)rs->n_ttiles * 4, s));
-    KRUX_CUDA(ctx, launch_rerank_bucket(rs->dev, rs->T, rs->N, rs->Np, ddrop + i * kMaxN,
-                                        (int)cp.bucket_jobs[i].drop.size(), bs.dev, s));
-    if (ctx->profiling) ctx->prof.launches += 1;
+    // dropping samples with a missing genotype leaves the NaN samples as they are
+    bs.dev.nan_cnt = rs->dev.nan_cnt;
+    bs.dev.nan_idx = rs->dev.nan_idx;
+    bs.dev.tile_nan = rs->dev.tile_nan;
+    RerankJob &j = jobs[i];
+    j.base = rs->dev;
+    j.A = bs.dev.A;
+    j.tie = bs.dev.tie;
+    j.K = bs.dev.K;
+    j.tau = bs.dev.tau;
+    j.cfac = bs.dev.cfac;
+    j.T = rs->T;
+    j.N = rs->N;
+    j.Np = rs->Np;
+    j.rows_pad = rs->rows_pad;
+    max_rows = std::max(max_rows, rs->rows_pad);
   }
+  // pageable uploads: staged before the calls return, so the host vectors may go
+  RerankJob *djobs = reinterpret_cast<RerankJob *>(base + jobs_off);
+  int32_t *ddrop = reinterpret_cast<int32_t *>(base + drop_off);
+  KRUX_CUDA(ctx, cudaMemcpyAsync(djobs, jobs.data(), nb * sizeof(RerankJob), cudaMemcpyHostToDevice, s));
+  KRUX_CUDA(ctx, cudaMemcpyAsync(ddrop, drops.data(), drops.size() * 4, cudaMemcpyHostToDevice, s));
+  KRUX_CUDA(ctx, launch_rerank_buckets(djobs, ddrop, (int)nb, max_rows, s));
+  if (ctx->profiling) ctx->prof.launches += 1;
   for (auto &g : cp.groups) {
     if (g.bucket < 0) continue;
     const krux_rankset &bs = cp.bucket_sets[g.bucket];
@@ -960,6 +983,10 @@ struct FusedLaunch {
   std::vector<int64_t> boff, moff, coff;
   int layout = 1;
   double hm[4] = {0.0, 0.0, 0.0, 0.0};  // markers with codes 0..4: h_d for d = 1..4
+  // biallelic rank-sum groups: all packed by one launch (job table on the device)
+  bool batched_pack = false;
+  int n_pack_jobs = 0;
+  int64_t pack_slots = 0, pack_halves = 0;
 };
 
 krux_status prepare_fused(krux_ctx *ctx, CallPlan &cp, const krux_opts *o, FusedLaunch &fl,
@@ -1099,6 +1126,38 @@ krux_status prepare_fused(krux_ctx *ctx, CallPlan &cp, const krux_opts *o, Fused
   if (!items.empty())
     KRUX_CUDA(ctx, cudaMemcpyAsync(ctx->items.p, items.data(), sizeof(WorkItem) * items.size(),
                                    cudaMemcpyHostToDevice, s));
+  fl.batched_pack = !cp.multi && cp.param.model != 1;
+  if (fl.batched_pack) {
+    std::vector<PackJob> jobs(ng);
+    int64_t slots = 0, halves = 0;
+    for (int i = 0; i < ng; ++i) {
+      const ScanGroupIn &g = cp.groups[i];
+      PackJob &j = jobs[i];
+      std::memset(&j, 0, sizeof j);
+      const int64_t nch = (g.n_snps + kChunkSnps - 1) / kChunkSnps;
+      j.geno = g.geno;
+      j.ldg = g.ldg;
+      j.snp_list = g.snp_list;
+      j.snp_begin = g.snp_begin;
+      j.n_snps = g.n_snps;
+      j.slot0 = slots;
+      j.half0 = halves;
+      j.B = reinterpret_cast<__half *>(ctx->B.as<char>() + fl.boff[i]);
+      j.meta = ctx->meta.as<ChunkMeta>() + fl.moff[i];
+      j.codes = g.nan_cnt ? ctx->codes.as<uint64_t>() + fl.coff[i] : nullptr;
+      j.N = g.rs->N;
+      j.Np = g.rs->Np;
+      j.allow_missing = g.allow_missing;
+      slots += nch * kChunkSnps;
+      if (j.codes) halves += nch * 2;
+    }
+    fl.n_pack_jobs = ng;
+    fl.pack_slots = slots;
+    fl.pack_halves = halves;
+    KRUX_CUDA(ctx, ctx->packjobs.ensure(sizeof(PackJob) * ng));
+    KRUX_CUDA(ctx, cudaMemcpyAsync(ctx->packjobs.p, jobs.data(), sizeof(PackJob) * ng,
+                                   cudaMemcpyHostToDevice, s));
+  }
   std::vector<const double *> cf(ng);
   for (int i = 0; i < ng; ++i) cf[i] = cp.groups[i].cfac;
   KRUX_CUDA(ctx, ctx->cfacptr.ensure(sizeof(double *) * ng));
@@ -1137,6 +1196,7 @@ krux_status prepare_fused(krux_ctx *ctx, CallPlan &cp, const krux_opts *o, Fused
   p.multi = cp.multi ? 1 : 0;
   for (auto &g : cp.groups) p.perm |= g.minp_key != nullptr ? 1 : 0;
   p.seed_bound = cp.perm.seed ? 1 : 0;
+  for (auto &g : cp.groups) p.has_nan |= g.nan_cnt != nullptr ? 1 : 0;
   if (cp.cis.on) {
     p.cis_snp_pos = cp.cis.snp_pos;
     p.cis_trait_pos = cp.cis.trait_pos;
@@ -1206,7 +1266,10 @@ krux_status enqueue_fused(krux_ctx *ctx, CallPlan &cp, const FusedLaunch &fl, cu
     }
   }
   ev_record(ctx, 2, s);
-  for (int i = 0; i < ng; ++i) {
+  if (fl.batched_pack)
+    KRUX_CUDA(ctx, launch_pack_batch(ctx->packjobs.as<PackJob>(), fl.n_pack_jobs, fl.pack_slots,
+                                     fl.pack_halves, fl.h1, fl.h2, fl.signed_coef, status, s));
+  for (int i = 0; i < ng && !fl.batched_pack; ++i) {
     const ScanGroupIn &g = cp.groups[i];
     const krux_rankset *rs = g.rs;
     __half *B = reinterpret_cast<__half *>(ctx->B.as<char>() + fl.boff[i]);
@@ -1270,7 +1333,10 @@ krux_status enqueue_fused(krux_ctx *ctx, CallPlan &cp, const FusedLaunch &fl, cu
 
 int fused_launches(const CallPlan &cp, const FusedLaunch &fl) {
   int n = (fl.grid > 0 ? 1 : 0) + (fl.staged ? 1 : 0);
-  for (auto &g : cp.groups) n += g.nan_cnt ? 2 : 1;
+  if (fl.batched_pack)
+    n += (fl.pack_slots > 0 ? 1 : 0) + (fl.pack_halves > 0 ? 1 : 0);
+  else
+    for (auto &g : cp.groups) n += g.nan_cnt ? 2 : 1;
   for (auto &os : cp.slots) n += (os.capacity > 0 && cp.param.model < 0) ? 1 : 0;
   if (cp.param.model >= 0) n += 2;
   if (cp.perm.on) n += 2 + (cp.perm.lists ? 2 : 0);

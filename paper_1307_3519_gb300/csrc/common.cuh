@@ -120,6 +120,35 @@ struct RankDev {
   uint32_t *tile_nan;   // [rows_pad/128] 1 if any trait of the tile has a NaN
 };
 
+// One missing-pattern bucket of a scan call: the base rank set's ranks re-derived
+// without the samples of the pattern (outputs per bucket; the NaN lists, counts
+// and tile flags are the base set's own).
+struct RerankJob {
+  RankDev base;             // lo, eq, K and nan_cnt are read
+  __half *A;                // [rows_pad][Np] (padding rows written as 0)
+  int64_t *tie;             // [T]
+  int32_t *K;               // [T]
+  float *tau;               // [rows_pad]
+  double *cfac;             // [rows_pad]
+  int32_t T, N, Np, rows_pad;
+  int32_t drop_off, n_drop; // the pattern's samples: drops[drop_off .. + n_drop)
+};
+
+// One SNP set of a batched packing launch (one scan group): slots
+// [slot0, slot0 + 64 * nchunks) and, when the group needs genotype codes, chunk
+// halves [half0, half0 + 2 * nchunks) of the flattened launch.
+struct PackJob {
+  const int8_t *geno;
+  int64_t ldg;
+  const int64_t *snp_list;  // device rows, or null for [snp_begin, snp_begin + n_snps)
+  int64_t snp_begin, n_snps;
+  int64_t slot0, half0;
+  __half *B;
+  ChunkMeta *meta;
+  uint64_t *codes;          // null: no codes (and no halves)
+  int32_t N, Np, allow_missing, pad_;
+};
+
 // ---- one group of a scan launch (a cohort, a missing-pattern bucket, or the
 // unpermuted + permuted rank matrices of a permutation batch) ----------------
 struct alignas(64) GroupDesc {
@@ -201,6 +230,8 @@ struct ScanParams {
   // seed pass of a permutation batch: the permuted groups write, per (permutation,
   // trait), a lower bound of the best -ln p over the scanned SNPs (no pair is decided)
   int32_t seed_bound = 0;
+  // some group's rank set has NaN (its traits get the exact-size hot test)
+  int32_t has_nan = 0;
 };
 
 enum : unsigned int {

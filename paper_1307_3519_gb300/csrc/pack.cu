@@ -48,20 +48,18 @@ missing_scan_kernel(const int8_t *__restrict__ geno, int64_t ldg, int N, int64_t
   }
 }
 
-// One warp per packed SNP slot j (including the padding of the last chunk).
-// SNP j is snp_list[j] if a list is given, else snp_begin + j.  SNPs that carry a
-// missing code are packed with zero coefficients here (they are scanned in
-// their missing-pattern bucket, where the rank set excludes those samples and
-// the -1 entries simply pack as 0 in both indicators).
-__global__ void __launch_bounds__(kPackWarps * 32)
-pack_kernel(const int8_t *__restrict__ geno, int64_t ldg, int N, int Np,
-            const int64_t *__restrict__ snp_list, int64_t snp_begin, int64_t n_snps,
-            int64_t n_slots, int64_t snp_out_base, float rh1, float rh2, int allow_missing,
-            int signed_df1, __half *__restrict__ B, ChunkMeta *__restrict__ meta,
-            unsigned int *status, int linear, float rl) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t j = (int64_t)blockIdx.x * kPackWarps + warp;
-  if (j >= n_slots) return;
+// Packs SNP slot j (one warp; j may be the padding of the last chunk).  SNP j is
+// snp_list[j] if a list is given, else snp_begin + j.  SNPs that carry a missing
+// code are packed with zero coefficients here (they are scanned in their
+// missing-pattern bucket, where the rank set excludes those samples and the -1
+// entries simply pack as 0 in both indicators).
+__device__ __forceinline__ void pack_slot(const int8_t *__restrict__ geno, int64_t ldg, int N,
+                                          int Np, const int64_t *__restrict__ snp_list,
+                                          int64_t snp_begin, int64_t n_snps, int64_t j,
+                                          int64_t snp_out_base, float rh1, float rh2,
+                                          int allow_missing, int signed_df1,
+                                          __half *__restrict__ B, ChunkMeta *__restrict__ meta,
+                                          unsigned int *status, int linear, float rl, int lane) {
   const int64_t c = j / kChunkSnps;
   const int jj = (int)(j % kChunkSnps);
   __half *r0 = B + (c * kChunkRows + jj) * Np;
@@ -148,6 +146,43 @@ pack_kernel(const int8_t *__restrict__ geno, int64_t ldg, int N, int Np,
   }
 }
 
+// One warp per packed SNP slot of one SNP set.
+__global__ void __launch_bounds__(kPackWarps * 32)
+pack_kernel(const int8_t *__restrict__ geno, int64_t ldg, int N, int Np,
+            const int64_t *__restrict__ snp_list, int64_t snp_begin, int64_t n_snps,
+            int64_t n_slots, int64_t snp_out_base, float rh1, float rh2, int allow_missing,
+            int signed_df1, __half *__restrict__ B, ChunkMeta *__restrict__ meta,
+            unsigned int *status, int linear, float rl) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t j = (int64_t)blockIdx.x * kPackWarps + warp;
+  if (j >= n_slots) return;
+  pack_slot(geno, ldg, N, Np, snp_list, snp_begin, n_snps, j, snp_out_base, rh1, rh2,
+            allow_missing, signed_df1, B, meta, status, linear, rl, lane);
+}
+
+// Last job whose first flattened unit is at or below x (x below the total).
+__device__ __forceinline__ int find_job(const PackJob *__restrict__ jobs, int n_jobs, int64_t x,
+                                        bool halves) {
+  int lo = 0, hi = n_jobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if ((halves ? jobs[mid].half0 : jobs[mid].slot0) <= x) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// All SNP sets of a call in one launch: one warp per flattened slot.
+__global__ void __launch_bounds__(kPackWarps * 32)
+pack_batch_kernel(const PackJob *__restrict__ jobs, int n_jobs, int64_t total_slots, float rh1,
+                  float rh2, int signed_df1, unsigned int *status) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t x = (int64_t)blockIdx.x * kPackWarps + warp;
+  if (x >= total_slots) return;
+  const PackJob &J = jobs[find_job(jobs, n_jobs, x, false)];
+  pack_slot(J.geno, J.ldg, J.N, J.Np, J.snp_list, J.snp_begin, J.n_snps, x - J.slot0, 0, rh1, rh2,
+            J.allow_missing, signed_df1, J.B, J.meta, status, 0, 0.f, lane);
+}
+
 __device__ __forceinline__ uint64_t spread_bits(uint32_t v) {
   uint64_t x = v;
   x = (x | (x << 16)) & 0x0000FFFF0000FFFFull;
@@ -160,14 +195,12 @@ __device__ __forceinline__ uint64_t spread_bits(uint32_t v) {
 
 // 2-bit genotype codes per chunk and sample: word [c][k][h] holds, at bits
 // 2j..2j+1, the code of SNP 64c + 32h + j at sample k (0,1,2; 3 = missing or
-// padding).  Used by the epilogue to drop a trait's NaN samples from N_i.
-__global__ void __launch_bounds__(kPackWarps * 32)
-codes_kernel(const int8_t *__restrict__ geno, int64_t ldg, int N, int Np,
-             const int64_t *__restrict__ snp_list, int64_t snp_begin, int64_t n_snps,
-             int64_t n_halves, uint64_t *__restrict__ codes) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t hw = (int64_t)blockIdx.x * kPackWarps + warp;  // chunk * 2 + half
-  if (hw >= n_halves) return;
+// padding).  Used by the epilogue to drop a trait's NaN samples from N_i.  One
+// warp per chunk half hw = 2c + h.
+__device__ __forceinline__ void codes_half(const int8_t *__restrict__ geno, int64_t ldg, int N,
+                                           int Np, const int64_t *__restrict__ snp_list,
+                                           int64_t snp_begin, int64_t n_snps, int64_t hw,
+                                           uint64_t *__restrict__ codes, int lane) {
   const int64_t j = hw * 32 + lane;
   const int8_t *g = nullptr;
   if (j < n_snps) g = geno + (snp_list ? snp_list[j] : snp_begin + j) * ldg;
@@ -184,6 +217,29 @@ codes_kernel(const int8_t *__restrict__ geno, int64_t ldg, int N, int Np,
     if (lane == 0) codes[(c * Np + k) * 2 + h] = spread_bits(b0) | (spread_bits(b1) << 1);
   }
 }
+
+__global__ void __launch_bounds__(kPackWarps * 32)
+codes_kernel(const int8_t *__restrict__ geno, int64_t ldg, int N, int Np,
+             const int64_t *__restrict__ snp_list, int64_t snp_begin, int64_t n_snps,
+             int64_t n_halves, uint64_t *__restrict__ codes) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t hw = (int64_t)blockIdx.x * kPackWarps + warp;  // chunk * 2 + half
+  if (hw >= n_halves) return;
+  codes_half(geno, ldg, N, Np, snp_list, snp_begin, n_snps, hw, codes, lane);
+}
+
+// The same for all SNP sets of a call that have codes (one warp per flattened half).
+__global__ void __launch_bounds__(kPackWarps * 32)
+codes_batch_kernel(const PackJob *__restrict__ jobs, int n_jobs, int64_t total_halves) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t x = (int64_t)blockIdx.x * kPackWarps + warp;
+  if (x >= total_halves) return;
+  const PackJob &J = jobs[find_job(jobs, n_jobs, x, true)];
+  if (J.codes == nullptr) return;  // (such jobs span no halves)
+  codes_half(J.geno, J.ldg, J.N, J.Np, J.snp_list, J.snp_begin, J.n_snps, x - J.half0, J.codes,
+             lane);
+}
+
 // Markers with codes 0..4: one warp per packed SNP slot j of a 32-SNP chunk;
 // rows 32i + jj (i = 0..3) of chunk j / 32 get I_i, the metadata the group
 // sizes and coefficients (1 / N_i) / h_df (group 4's weighs (D_0+..+D_3)^2).
@@ -304,6 +360,25 @@ cudaError_t launch_pack2(const int8_t *geno, int64_t ldg, int N, int Np, const i
   codes_kernel<<<(unsigned)grid2, kPackWarps * 32, 0, s>>>(geno, ldg, N, Np, snp_list, snp_begin,
                                                            n_snps, n_halves, codes);
   return cudaGetLastError();
+}
+
+cudaError_t launch_pack_batch(const PackJob *jobs, int n_jobs, int64_t total_slots,
+                              int64_t total_halves, double h1, double h2, int signed_df1,
+                              unsigned int *status, cudaStream_t s) {
+  if (n_jobs <= 0) return cudaSuccess;
+  if (total_slots > 0) {
+    const int64_t grid = (total_slots + kPackWarps - 1) / kPackWarps;
+    pack_batch_kernel<<<(unsigned)grid, kPackWarps * 32, 0, s>>>(
+        jobs, n_jobs, total_slots, (float)(1.0 / h1), (float)(1.0 / h2), signed_df1, status);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (total_halves > 0) {
+    const int64_t grid = (total_halves + kPackWarps - 1) / kPackWarps;
+    codes_batch_kernel<<<(unsigned)grid, kPackWarps * 32, 0, s>>>(jobs, n_jobs, total_halves);
+    return cudaGetLastError();
+  }
+  return cudaSuccess;
 }
 
 }  // namespace krux

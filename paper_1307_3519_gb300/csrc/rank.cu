@@ -203,29 +203,40 @@ cudaError_t launch_permute_rows(const __half *A, __half *out, int rows_pad, int 
 // samples of the pattern removed, re-ranked).  No re-sort: for present samples,
 // x_q < x_k exactly when lo_q < lo_k and x_q == x_k exactly when lo_q == lo_k,
 // so lo' = lo - #{q dropped, present, lo_q < lo_k} and
-// eq' = eq - #{q dropped, present, lo_q == lo_k}.
+// eq' = eq - #{q dropped, present, lo_q == lo_k}.  One launch re-ranks every
+// bucket of a call (grid.y = bucket).
 namespace krux {
 namespace {
 __global__ void __launch_bounds__(256)
-rerank_kernel(RankDev base, int T, int N, int Np, const int32_t *__restrict__ drop, int n_drop,
-              RankDev out) {
+rerank_kernel(const RerankJob *__restrict__ jobs, const int32_t *__restrict__ drops) {
+  const RerankJob &J = jobs[blockIdx.y];
+  const int N = J.N, Np = J.Np, T = J.T, n_drop = J.n_drop;
   __shared__ uint32_t dmask[kMaxN / 32];
   __shared__ int32_t dlist[kMaxN];
   for (int i = threadIdx.x; i < kMaxN / 32; i += blockDim.x) dmask[i] = 0u;
   __syncthreads();
   for (int i = threadIdx.x; i < n_drop; i += blockDim.x) {
-    dlist[i] = drop[i];
-    atomicOr(&dmask[drop[i] >> 5], 1u << (drop[i] & 31));
+    const int q = drops[J.drop_off + i];
+    dlist[i] = q;
+    atomicOr(&dmask[q >> 5], 1u << (q & 31));
   }
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int t = blockIdx.x * 8 + warp;
-  if (t >= T) return;
-  const uint16_t *lo = base.lo + (int64_t)t * N;
-  const uint16_t *eq = base.eq + (int64_t)t * N;
+  if (t >= J.rows_pad) return;
+  if (t >= T) {  // padding row: never a hit
+    for (int k = lane; k < Np; k += 32) J.A[(int64_t)t * Np + k] = __int2half_rn(0);
+    if (lane == 0) {
+      J.tau[t] = __int_as_float(0x7f800000);
+      J.cfac[t] = 0.0;
+    }
+    return;
+  }
+  const uint16_t *lo = J.base.lo + (int64_t)t * N;
+  const uint16_t *eq = J.base.eq + (int64_t)t * N;
   int Kdrop = 0;
   for (int i = 0; i < n_drop; ++i) Kdrop += eq[dlist[i]] > 0;
-  const int K = base.K[t] - Kdrop;
+  const int K = J.base.K[t] - Kdrop;
   long long tie = 0;
   for (int k = lane; k < Np; k += 32) {
     int a = 0;
@@ -242,37 +253,36 @@ rerank_kernel(RankDev base, int T, int N, int Np, const int32_t *__restrict__ dr
       tie += (long long)e * e - 1;
       a = 2 * l + e - K;
     }
-    out.A[(int64_t)t * Np + k] = __int2half_rn(a);
+    J.A[(int64_t)t * Np + k] = __int2half_rn(a);
   }
-  for (int k = lane; k < N; k += 32) out.nan_idx[(int64_t)t * N + k] = base.nan_idx[(int64_t)t * N + k];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) tie += __shfl_xor_sync(0xffffffffu, tie, o);
   if (lane == 0) {
-    out.tie[t] = tie;
-    out.K[t] = K;
-    const int nc = base.nan_cnt[t];
-    out.nan_cnt[t] = (uint16_t)nc;
-    if (nc > 0) atomicOr(&out.tile_nan[t / kTileM], 1u);
+    J.tie[t] = tie;
+    J.K[t] = K;
     const double Kd = (double)K;
     const double C = K >= 2 ? 1.0 - (double)tie / (Kd * Kd * Kd - Kd) : 0.0;
     if (K >= 2 && C > 0.0) {
       const double s = Kd * (Kd + 1.0) * C;
-      out.cfac[t] = 3.0 / s;
-      out.tau[t] = (float)(s / 3.0);
+      J.cfac[t] = 3.0 / s;
+      J.tau[t] = (float)(s / 3.0);
     } else {
-      out.cfac[t] = 0.0;
-      out.tau[t] = __int_as_float(0x7f800000);
+      J.cfac[t] = 0.0;
+      J.tau[t] = __int_as_float(0x7f800000);
     }
   }
 }
 }  // namespace
 
-cudaError_t launch_rerank_bucket(const RankDev &base, int T, int N, int Np, const int32_t *drop,
-                                 int n_drop, const RankDev &out, cudaStream_t s) {
-  rerank_kernel<<<(T + 7) / 8, 256, 0, s>>>(base, T, N, Np, drop, n_drop, out);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  const int rows_pad = (T + kTileM - 1) / kTileM * kTileM;
-  return launch_pad_traits(T, rows_pad, out.tau, out.cfac, out.nan_cnt, s);
+cudaError_t launch_rerank_buckets(const RerankJob *jobs, const int32_t *drops, int n_jobs,
+                                  int max_rows_pad, cudaStream_t s) {
+  for (int j0 = 0; j0 < n_jobs; j0 += 65535) {  // grid.y limit
+    const int nj = n_jobs - j0 < 65535 ? n_jobs - j0 : 65535;
+    rerank_kernel<<<dim3((unsigned)((max_rows_pad + 7) / 8), (unsigned)nj), 256, 0, s>>>(jobs + j0,
+                                                                                       drops);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 }  // namespace krux

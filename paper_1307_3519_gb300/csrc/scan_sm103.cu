@@ -368,6 +368,58 @@ __device__ __forceinline__ bool hit_fast(const uint32_t (&d0)[kEpiSnps], const u
   return (int)acc >= 0;
 }
 
+// Hot test of a chunk half for a trait with NaN samples (section "Handling missing
+// values": N_i(n,m) counts the samples present for both).  Each pair's group sizes
+// come from the genotype codes of the trait's c NaN samples: k_i = the NaN samples
+// with genotype i, summed over the samples in 2-bit fields (c <= 3; more take the
+// rare path at once), n_i' = n_i - k_i.  Then sum_i D_i^2 / n_i' in FP32 (an
+// emptied group has D_i = 0 and counts as n_i' = 1) against the bound of the
+// pair's own df (q1, q2: h_df (1 - margin) / cfac).  True if some pair may be a
+// hit; the rare path decides it exactly.
+__device__ __forceinline__ bool hit_fast_nan(const uint32_t (&d0)[kEpiSnps],
+                                             const uint32_t (&d1)[kEpiSnps], const ChunkMeta &m,
+                                             int h, const uint64_t *codes, int c,
+                                             const uint16_t *nan_idx, float q1, float q2) {
+  if (c > 3) return true;
+  uint32_t k0 = 0u, k1 = 0u, k2 = 0u;
+  for (int i = 0; i < c; ++i) {
+    const int k = nan_idx[i];
+    const uint32_t x = (uint32_t)(codes[k * 2 + (h >> 1)] >> (32 * (h & 1)));
+    const uint32_t lo = x & 0x55555555u, hi = (x >> 1) & 0x55555555u;
+    k0 += ~(lo | hi) & 0x55555555u;
+    k1 += lo & ~hi;
+    k2 += hi & ~lo;
+  }
+  const int jb = kEpiSnps * h;
+  const uint4 *p0 = reinterpret_cast<const uint4 *>(&m.n[0][jb]);
+  const uint4 *p1 = reinterpret_cast<const uint4 *>(&m.n[1][jb]);
+  const uint4 *p2 = reinterpret_cast<const uint4 *>(&m.n[2][jb]);
+  const float inf = __int_as_float(0x7f800000);
+  bool need = false;
+#pragma unroll
+  for (int hb = 0; hb < 2; ++hb) {  // SNPs 8 hb .. 8 hb + 7
+    const uint4 a0 = p0[hb], a1 = p1[hb], a2 = p2[hb];
+    const uint32_t w0[4] = {a0.x, a0.y, a0.z, a0.w}, w1[4] = {a1.x, a1.y, a1.z, a1.w},
+                   w2[4] = {a2.x, a2.y, a2.z, a2.w};
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int j = 8 * hb + t;
+      const int sh = (t & 1) * 16;
+      const int n0 = (int)((w0[t >> 1] >> sh) & 0xffffu) - (int)((k0 >> (2 * j)) & 3u);
+      const int n1 = (int)((w1[t >> 1] >> sh) & 0xffffu) - (int)((k1 >> (2 * j)) & 3u);
+      const int n2 = (int)((w2[t >> 1] >> sh) & 0xffffu) - (int)((k2 >> (2 * j)) & 3u);
+      const float u = __uint_as_float(d0[j]), v = __uint_as_float(d1[j]);
+      const float w = -(u + v);
+      const float Q = __fdividef(u * u, (float)max(n0, 1)) + __fdividef(v * v, (float)max(n1, 1)) +
+                      __fdividef(w * w, (float)max(n2, 1));
+      const int groups = (n0 > 0) + (n1 > 0) + (n2 > 0);
+      const float thr = groups == 3 ? q2 : (groups == 2 ? q1 : inf);
+      need |= Q >= thr;
+    }
+  }
+  return need;
+}
+
 // Rare path of a hit-mode chunk half: dense FP64 output, traits with NaN,
 // classification of candidates (FP64 inside the band) and the warp-aggregated
 // append of hits.  Called by the whole warp; `dv` holds this lane's kEpiSnps D_0
@@ -887,10 +939,11 @@ __device__ __noinline__ double minp_step_best(MinpLead *L, double cfac) {
 }
 
 // Kernel forms: the plain scan, markers with up to five genotype groups (32-SNP
-// chunks, ChunkMetaM), and the permutation scan (groups with a min-p key); the
-// producer and MMA warps are the same in all three.  Separate forms keep the
+// chunks, ChunkMetaM), the permutation scan (groups with a min-p key), and the
+// plain scan of rank sets with NaN (exact group sizes in the hot test); the
+// producer and MMA warps are the same in all four.  Separate forms keep the
 // state of one out of the registers of the others.
-enum ScanForm { kFormScan = 0, kFormMulti = 1, kFormPerm = 2 };
+enum ScanForm { kFormScan = 0, kFormMulti = 1, kFormPerm = 2, kFormNan = 3 };
 
 template <int kForm>
 __global__ void __launch_bounds__(kScanThreads, 1) krux_scan_kernel(const __grid_constant__ ScanParams p) {
@@ -1187,6 +1240,13 @@ __global__ void __launch_bounds__(kScanThreads, 1) krux_scan_kernel(const __grid
                          : nullptr;
         const bool minp_mode = kForm == kFormPerm && g.minp_key != nullptr && ag > 0;
         const bool seed_pass = kForm == kFormPerm && p.seed_bound != 0;
+        // traits with NaN (form kFormNan): the hot test's bounds on sum_i D_i^2 / n_i'
+        float nan_q1 = 0.f, nan_q2 = 0.f;
+        if (kForm == kFormNan) {
+          const float cf = (float)et.cfac;
+          nan_q1 = cf > 0.f ? p.h1 * (1.f - p.margin) / cf : __int_as_float(0x7f800000);
+          nan_q2 = cf > 0.f ? p.h2 * (1.f - p.margin) / cf : __int_as_float(0x7f800000);
+        }
         // with the FDR histogram on, permuted pairs at or above the band are counted
         const float fdr_tau_lo = p.fdr_hist != nullptr ? -et.ntlo : __int_as_float(0x7f800000);
         // min-p state: FP64 work only in permuted groups (FP64 issue is slow here)
@@ -1274,6 +1334,9 @@ __global__ void __launch_bounds__(kScanThreads, 1) krux_scan_kernel(const __grid
               need = false;
             } else if (minp_mode)
               need = et.valid && (et.nan_cnt > 0 || minp_fast(d0, d1, mc, h, ms, fdr_tau_lo));
+            else if (kForm == kFormNan && et.nan_cnt > 0)
+              need = p.dense || hit_fast_nan(d0, d1, mc, h, codes, et.nan_cnt, et.nan_idx,
+                                             nan_q1, nan_q2);
             else
               need = p.dense || et.nan_cnt > 0 ||
                      (p.signed_coef ? hit_fast<true>(d0, d1, mc, h, et.ntlo)
@@ -1503,6 +1566,9 @@ cudaError_t scan_set_smem(size_t smem) {
   e = cudaFuncSetAttribute(krux_scan_kernel<kFormMulti>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(krux_scan_kernel<kFormNan>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(krux_scan_kernel<kFormPerm>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
@@ -1512,6 +1578,8 @@ cudaError_t launch_scan_only(const ScanParams &p, int grid, size_t smem, cudaStr
     krux_scan_kernel<kFormMulti><<<grid, kScanThreads, smem, s>>>(p);
   else if (p.perm)
     krux_scan_kernel<kFormPerm><<<grid, kScanThreads, smem, s>>>(p);
+  else if (p.has_nan)
+    krux_scan_kernel<kFormNan><<<grid, kScanThreads, smem, s>>>(p);
   else
     krux_scan_kernel<kFormScan><<<grid, kScanThreads, smem, s>>>(p);
   return cudaGetLastError();
