@@ -12,6 +12,8 @@
 #include <cstring>
 #include <map>
 #include <string>
+#include <tuple>
+#include <unordered_map>
 #include <vector>
 
 #include "common.cuh"
@@ -652,22 +654,28 @@ krux_status find_missing(krux_ctx *ctx, const int8_t *geno, int64_t ldg, int N, 
   std::vector<int64_t> order(m);
   for (int64_t i = 0; i < m; ++i) order[i] = i;
   std::sort(order.begin(), order.end(), [&](int64_t a, int64_t c) { return idx[a] < idx[c]; });
-  std::map<std::vector<uint64_t>, size_t> where;
+  // buckets in order of their first SNP; a hash of the sample mask finds them
+  using Key = std::array<uint64_t, W>;
+  struct KeyHash {
+    size_t operator()(const Key &k) const {
+      uint64_t h = 0x9e3779b97f4a7c15ull;
+      for (uint64_t w : k) h = (h ^ w) * 0x100000001b3ull;
+      return (size_t)(h ^ (h >> 29));
+    }
+  };
+  std::unordered_map<Key, size_t, KeyHash> where;
+  where.reserve((size_t)m);
   for (int64_t oi : order) {
-    std::vector<uint64_t> key(mask.begin() + oi * W, mask.begin() + (oi + 1) * W);
-    auto it = where.find(key);
-    size_t bi;
-    if (it == where.end()) {
-      bi = buckets.size();
+    Key key;
+    std::copy(mask.begin() + oi * W, mask.begin() + (oi + 1) * W, key.begin());
+    auto ins = where.emplace(key, buckets.size());
+    if (ins.second) {
       Bucket bk;
       for (int k = 0; k < N; ++k)
         if ((key[k / 64] >> (k % 64)) & 1ull) bk.drop.push_back(k);
       buckets.push_back(std::move(bk));
-      where.emplace(std::move(key), bi);
-    } else {
-      bi = it->second;
     }
-    buckets[bi].snps.push_back(idx[oi]);
+    buckets[ins.first->second].snps.push_back(idx[oi]);
   }
   std::vector<char> is_miss((size_t)n, 0);
   for (int64_t i = 0; i < m; ++i) is_miss[idx[i] - b] = 1;
@@ -714,6 +722,10 @@ struct ScanGroupIn {
   int64_t dense_ld = 0, dense_snp0 = 0;
   double *minp_key = nullptr;
   int bucket = -1;                    // index into the call's bucket rank sets
+  // tensor map of A: groups whose rank matrices sit back to back in one buffer
+  // (missing-pattern buckets of one rank set) share it, each at row a_row0
+  const __half *a_map = nullptr;      // nullptr: a map of A's own rows
+  int64_t a_map_rows = 0, a_row0 = 0;
 };
 
 struct BucketJob {
@@ -763,11 +775,11 @@ struct CallPlan {
   double fdr_l0 = 0.0, fdr_w = 1.0;
 };
 
-// Device bytes of one bucket's re-ranked set (A, tie sums, K, tau, cfac).
+// Device bytes of one bucket's re-ranked set apart from A (tie sums, K, tau, cfac);
+// the A matrices of a call's buckets lie back to back before these.
 size_t bucket_bytes(const krux_rankset *rs) {
   size_t off = 0;
   auto take = [&](size_t b) { off += (b + 255) / 256 * 256; };
-  take((size_t)rs->rows_pad * rs->Np * 2);
   take((size_t)rs->T * 8);
   take((size_t)rs->T * 4);
   take((size_t)rs->rows_pad * 4);
@@ -851,8 +863,12 @@ krux_status materialise(krux_ctx *ctx, CallPlan &cp, cudaStream_t s) {
     if (g.list_off >= 0) g.snp_list = ctx->list.as<int64_t>() + g.list_off;
   if (cp.bucket_jobs.empty()) return KRUX_OK;
   const size_t nb = cp.bucket_jobs.size();
-  std::vector<size_t> off(nb);
+  std::vector<size_t> aoff(nb), off(nb);
   size_t tot = 0;
+  for (size_t i = 0; i < nb; ++i) {  // rows_pad * Np * 2 is a multiple of 256
+    aoff[i] = tot;
+    tot += (size_t)cp.bucket_jobs[i].base->rows_pad * cp.bucket_jobs[i].base->Np * 2;
+  }
   for (size_t i = 0; i < nb; ++i) {
     off[i] = tot;
     tot += bucket_bytes(cp.bucket_jobs[i].base);
@@ -889,7 +905,7 @@ krux_status materialise(krux_ctx *ctx, CallPlan &cp, cudaStream_t s) {
       o2 += (bytes + 255) / 256 * 256;
       return r;
     };
-    bs.dev.A = (__half *)take((size_t)rs->rows_pad * rs->Np * 2);
+    bs.dev.A = reinterpret_cast<__half *>(base + aoff[i]);
     bs.dev.tie = (int64_t *)take((size_t)rs->T * 8);
     bs.dev.K = (int32_t *)take((size_t)rs->T * 4);
     bs.dev.tau = (float *)take((size_t)rs->rows_pad * 4);
@@ -918,9 +934,19 @@ krux_status materialise(krux_ctx *ctx, CallPlan &cp, cudaStream_t s) {
   KRUX_CUDA(ctx, cudaMemcpyAsync(ddrop, drops.data(), drops.size() * 4, cudaMemcpyHostToDevice, s));
   KRUX_CUDA(ctx, launch_rerank_buckets(djobs, ddrop, (int)nb, max_rows, s));
   if (ctx->profiling) ctx->prof.launches += 1;
+  // runs of buckets of the same rank set: one A map each
+  std::vector<size_t> run(nb);
+  for (size_t i = 0; i < nb; ++i)
+    run[i] = (i > 0 && cp.bucket_jobs[i].base == cp.bucket_jobs[i - 1].base) ? run[i - 1] : i;
+  std::vector<int64_t> run_rows(nb, 0);
+  for (size_t i = 0; i < nb; ++i) run_rows[run[i]] += cp.bucket_jobs[i].base->rows_pad;
   for (auto &g : cp.groups) {
     if (g.bucket < 0) continue;
     const krux_rankset &bs = cp.bucket_sets[g.bucket];
+    const size_t r = run[(size_t)g.bucket];
+    g.a_map = reinterpret_cast<const __half *>(base + aoff[r]);
+    g.a_map_rows = run_rows[r];
+    g.a_row0 = (int64_t)((aoff[(size_t)g.bucket] - aoff[r]) / ((size_t)bs.Np * 2));
     g.A = bs.dev.A;
     g.tau = bs.dev.tau;
     g.cfac = bs.dev.cfac;
@@ -1068,6 +1094,20 @@ krux_status prepare_fused(krux_ctx *ctx, CallPlan &cp, const krux_opts *o, Fused
   std::vector<GroupDesc> descs(ng);
   std::vector<GroupPlan> plans(ng);
   int nc_max = 1;
+  // encoded maps by (base, width, rows): groups in one buffer share a map
+  std::map<std::tuple<const void *, int, int64_t>, CUtensorMap> maps;
+  auto map_of = [&](CUtensorMap *out, const void *base, int Np, int64_t rows) -> krux_status {
+    const auto key = std::make_tuple(base, Np, rows);
+    auto it = maps.find(key);
+    if (it == maps.end()) {
+      CUtensorMap m;
+      const krux_status st = encode_map(ctx, &m, base, Np, rows, layout);
+      if (st != KRUX_OK) return st;
+      it = maps.emplace(key, m).first;
+    }
+    *out = it->second;
+    return KRUX_OK;
+  };
   for (int i = 0; i < ng; ++i) {
     ScanGroupIn &g = cp.groups[i];
     const krux_rankset *rs = g.rs;
@@ -1077,10 +1117,21 @@ krux_status prepare_fused(krux_ctx *ctx, CallPlan &cp, const krux_opts *o, Fused
     std::memset(&d, 0, sizeof d);
     const int64_t csn = cp.multi ? kChunkSnpsM : kChunkSnps;
     const int64_t nch = (g.n_snps + csn - 1) / csn;
-    krux_status st =
-        encode_map(ctx, &d.tmA, g.A, rs->Np, (int64_t)rs->rows_pad * g.n_agroups, layout);
+    krux_status st;
+    if (g.a_map) {
+      st = map_of(&d.tmA, g.a_map, rs->Np, g.a_map_rows);
+      d.a_row0 = (int32_t)g.a_row0;
+    } else {
+      st = map_of(&d.tmA, g.A, rs->Np, (int64_t)rs->rows_pad * g.n_agroups);
+    }
     if (st != KRUX_OK) return st;
-    st = encode_map(ctx, &d.tmB, B, rs->Np, std::max<int64_t>(nch, 1) * kChunkRows, layout);
+    const int64_t pitch = (int64_t)rs->Np * 2;  // bytes per B row
+    if (fl.boff[i] % pitch == 0) {  // the whole B buffer as rows of this width
+      st = map_of(&d.tmB, ctx->B.p, rs->Np, std::max<int64_t>(btot / pitch, 1));
+      d.b_row0 = (int32_t)(fl.boff[i] / pitch);
+    } else {
+      st = map_of(&d.tmB, B, rs->Np, std::max<int64_t>(nch, 1) * kChunkRows);
+    }
     if (st != KRUX_OK) return st;
     d.meta = ctx->meta.as<ChunkMeta>() + fl.moff[i];
     d.codes = g.nan_cnt ? ctx->codes.as<uint64_t>() + fl.coff[i] : nullptr;

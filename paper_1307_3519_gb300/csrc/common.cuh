@@ -177,6 +177,7 @@ struct alignas(64) GroupDesc {
   int32_t nkb;              // rank-tile K blocks per step (1 = the whole K at once)
   int32_t pair;             // 1: chunks 2j, 2j+1 interleaved per K atom, one N = 256 MMA per pair
   int32_t pad_;
+  int32_t a_row0, b_row0;   // first row of this group's A / B in tmA / tmB (maps may be shared)
   int64_t nan_ag_stride;    // elements between the NaN index lists of consecutive agroups
                             // (permuted groups: NaN samples sit at permuted positions)
 };

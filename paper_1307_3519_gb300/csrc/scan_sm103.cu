@@ -1040,7 +1040,8 @@ __global__ void __launch_bounds__(kScanThreads, 1) krux_scan_kernel(const __grid
                                          : sB + (uint32_t)c * b_stride;
           const uint32_t astep = g->pair ? 2u * abytes : abytes;
           for (int a = 0; a < g->n_atoms; ++a)
-            tma_load_2d(bbase + (uint32_t)a * astep, &g->tmB, a * ak, chunk * kChunkRows, b_full(c));
+            tma_load_2d(bbase + (uint32_t)a * astep, &g->tmB, a * ak, g->b_row0 + chunk * kChunkRows,
+                        b_full(c));
           bulk_load(smem_u32(smeta + c), g->meta + chunk, (uint32_t)sizeof(ChunkMeta), b_full(c));
           if (codes_bytes)
             bulk_load(smem_u32(scodes + (size_t)c * codes_stride), g->codes + (size_t)chunk * g->Np * 2,
@@ -1052,7 +1053,7 @@ __global__ void __launch_bounds__(kScanThreads, 1) krux_scan_kernel(const __grid
         const int atoms_per_block = p.ka / ak;
         for (int step = w.step_begin; step < w.step_end; ++step) {
           const int ag = step / g->n_ttiles, tt = step - ag * g->n_ttiles;
-          const int row0 = ag * g->rows_per_agroup + tt * kTileM;
+          const int row0 = g->a_row0 + ag * g->rows_per_agroup + tt * kTileM;
           // the rank tile of this step, in K blocks of p.ka samples
           for (int kb = 0; kb < g->nkb; ++kb) {
             if (!wait_bar(a_empty(a_stage), a_phase ^ 1u, wc, 2)) goto producer_done;
