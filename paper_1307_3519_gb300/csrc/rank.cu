@@ -15,6 +15,22 @@ namespace krux {
 namespace {
 constexpr int kRankWarps = 8;
 
+// Tie factor C = 1 - sum(t^3-t)/(K^3-K) and the trait constants of the scan:
+// H = 3/(K(K+1)C) * sum_i D_i^2/N_i, so cfac = 3/(K(K+1)C) and the fast-test
+// bound tau = K(K+1)C/3; degenerate traits (K < 2 or C = 0) get cfac 0, tau +inf.
+__device__ __forceinline__ void trait_consts(int K, long long tie, float &tau, double &cfac) {
+  const double Kd = (double)K;
+  const double C = K >= 2 ? 1.0 - (double)tie / (Kd * Kd * Kd - Kd) : 0.0;
+  if (K >= 2 && C > 0.0) {
+    const double s = Kd * (Kd + 1.0) * C;
+    cfac = 3.0 / s;
+    tau = (float)(s / 3.0);
+  } else {
+    cfac = 0.0;
+    tau = __int_as_float(0x7f800000);  // +inf: never a hit
+  }
+}
+
 __global__ void __launch_bounds__(kRankWarps * 32)
 rank_kernel(const float *__restrict__ expr, int T, int N, int64_t ld, int Np, RankDev r) {
   extern __shared__ float srow[];
@@ -74,17 +90,7 @@ rank_kernel(const float *__restrict__ expr, int T, int N, int64_t ld, int Np, Ra
     r.K[t] = K;
     r.nan_cnt[t] = (uint16_t)(N - K);
     if (N - K > 0) atomicOr(&r.tile_nan[t / kTileM], 1u);
-    // tie factor C = 1 - sum(t^3-t)/(K^3-K); H = 3/(K(K+1)C) * sum_i D_i^2/N_i
-    const double Kd = (double)K;
-    const double C = K >= 2 ? 1.0 - (double)tie / (Kd * Kd * Kd - Kd) : 0.0;
-    if (K >= 2 && C > 0.0) {
-      const double s = Kd * (Kd + 1.0) * C;
-      r.cfac[t] = 3.0 / s;
-      r.tau[t] = (float)(s / 3.0);
-    } else {
-      r.cfac[t] = 0.0;
-      r.tau[t] = __int_as_float(0x7f800000);  // +inf: never a hit
-    }
+    trait_consts(K, tie, r.tau[t], r.cfac[t]);
   }
 }
 
@@ -224,12 +230,8 @@ rerank_kernel(const RerankJob *__restrict__ jobs, const int32_t *__restrict__ dr
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int t = blockIdx.x * 8 + warp;
   if (t >= J.rows_pad) return;
-  if (t >= T) {  // padding row: never a hit
+  if (t >= T) {  // padding row (its constants come from rerank_consts_kernel)
     for (int k = lane; k < Np; k += 32) J.A[(int64_t)t * Np + k] = __int2half_rn(0);
-    if (lane == 0) {
-      J.tau[t] = __int_as_float(0x7f800000);
-      J.cfac[t] = 0.0;
-    }
     return;
   }
   const uint16_t *lo = J.base.lo + (int64_t)t * N;
@@ -260,17 +262,20 @@ rerank_kernel(const RerankJob *__restrict__ jobs, const int32_t *__restrict__ dr
   if (lane == 0) {
     J.tie[t] = tie;
     J.K[t] = K;
-    const double Kd = (double)K;
-    const double C = K >= 2 ? 1.0 - (double)tie / (Kd * Kd * Kd - Kd) : 0.0;
-    if (K >= 2 && C > 0.0) {
-      const double s = Kd * (Kd + 1.0) * C;
-      J.cfac[t] = 3.0 / s;
-      J.tau[t] = (float)(s / 3.0);
-    } else {
-      J.cfac[t] = 0.0;
-      J.tau[t] = __int_as_float(0x7f800000);
-    }
   }
+}
+
+// The FP64 trait constants of every bucket, one thread per row (FP64 issue is
+// slow on this part, so it gets whole warps); padding rows get cfac 0, tau +inf.
+__global__ void __launch_bounds__(256) rerank_consts_kernel(const RerankJob *__restrict__ jobs) {
+  const RerankJob &J = jobs[blockIdx.y];
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= J.rows_pad) return;
+  float tau = __int_as_float(0x7f800000);
+  double cfac = 0.0;
+  if (t < J.T) trait_consts(J.K[t], J.tie[t], tau, cfac);
+  J.tau[t] = tau;
+  J.cfac[t] = cfac;
 }
 }  // namespace
 
@@ -280,7 +285,11 @@ cudaError_t launch_rerank_buckets(const RerankJob *jobs, const int32_t *drops, i
     const int nj = n_jobs - j0 < 65535 ? n_jobs - j0 : 65535;
     rerank_kernel<<<dim3((unsigned)((max_rows_pad + 7) / 8), (unsigned)nj), 256, 0, s>>>(jobs + j0,
                                                                                        drops);
-    const cudaError_t e = cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    rerank_consts_kernel<<<dim3((unsigned)((max_rows_pad + 255) / 256), (unsigned)nj), 256, 0, s>>>(
+        jobs + j0);
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;

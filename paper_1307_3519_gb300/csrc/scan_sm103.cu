@@ -368,27 +368,43 @@ __device__ __forceinline__ bool hit_fast(const uint32_t (&d0)[kEpiSnps], const u
   return (int)acc >= 0;
 }
 
+// Small non-negative integer (< 2^23) to float, exactly, without a conversion
+// instruction: the integer sits in the mantissa of 2^23.
+__device__ __forceinline__ float small_int_f(int x) {
+  return __int_as_float(0x4b000000 | x) - 8388608.f;
+}
+
 // Hot test of a chunk half for a trait with NaN samples (section "Handling missing
 // values": N_i(n,m) counts the samples present for both).  Each pair's group sizes
 // come from the genotype codes of the trait's c NaN samples: k_i = the NaN samples
-// with genotype i, summed over the samples in 2-bit fields (c <= 3; more take the
-// rare path at once), n_i' = n_i - k_i.  Then sum_i D_i^2 / n_i' in FP32 (an
-// emptied group has D_i = 0 and counts as n_i' = 1) against the bound of the
-// pair's own df (q1, q2: h_df (1 - margin) / cfac).  True if some pair may be a
-// hit; the rare path decides it exactly.
+// with genotype i, summed over the samples in 4-bit fields (c <= 15; more take the
+// rare path at once), n_i' = n_i - k_i.  The test sum_i D_i^2 / n_i' >= q_df is
+// taken without a division, as u^2 n1 n2 + v^2 n0 n2 + w^2 n0 n1 >= q_df n0 n1 n2
+// (an emptied group has D_i = 0 and counts as n_i' = 1; q_df of the pair's own df,
+// q1, q2 = h_df (1 - margin) / cfac).  True if some pair may be a hit; the rare
+// path decides it exactly.
 __device__ __forceinline__ bool hit_fast_nan(const uint32_t (&d0)[kEpiSnps],
                                              const uint32_t (&d1)[kEpiSnps], const ChunkMeta &m,
                                              int h, const uint64_t *codes, int c,
                                              const uint16_t *nan_idx, float q1, float q2) {
-  if (c > 3) return true;
-  uint32_t k0 = 0u, k1 = 0u, k2 = 0u;
+  if (c > 15) return true;
+  // k_i of SNPs 8 b .. 8 b + 7 in the 4-bit fields of kb[i][b]
+  uint32_t kb[3][2] = {{0u, 0u}, {0u, 0u}, {0u, 0u}};
   for (int i = 0; i < c; ++i) {
     const int k = nan_idx[i];
     const uint32_t x = (uint32_t)(codes[k * 2 + (h >> 1)] >> (32 * (h & 1)));
-    const uint32_t lo = x & 0x55555555u, hi = (x >> 1) & 0x55555555u;
-    k0 += ~(lo | hi) & 0x55555555u;
-    k1 += lo & ~hi;
-    k2 += hi & ~lo;
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      // the 8 two-bit codes of this half-word, each moved to a 4-bit field
+      uint32_t z = (x >> (16 * b)) & 0xffffu;
+      z = (z | (z << 8)) & 0x00ff00ffu;
+      z = (z | (z << 4)) & 0x0f0f0f0fu;
+      z = (z | (z << 2)) & 0x33333333u;
+      const uint32_t lo = z & 0x11111111u, hi = (z >> 1) & 0x11111111u;
+      kb[0][b] += ~(lo | hi) & 0x11111111u;
+      kb[1][b] += lo & ~hi;
+      kb[2][b] += hi & ~lo;
+    }
   }
   const int jb = kEpiSnps * h;
   const uint4 *p0 = reinterpret_cast<const uint4 *>(&m.n[0][jb]);
@@ -405,16 +421,18 @@ __device__ __forceinline__ bool hit_fast_nan(const uint32_t (&d0)[kEpiSnps],
     for (int t = 0; t < 8; ++t) {
       const int j = 8 * hb + t;
       const int sh = (t & 1) * 16;
-      const int n0 = (int)((w0[t >> 1] >> sh) & 0xffffu) - (int)((k0 >> (2 * j)) & 3u);
-      const int n1 = (int)((w1[t >> 1] >> sh) & 0xffffu) - (int)((k1 >> (2 * j)) & 3u);
-      const int n2 = (int)((w2[t >> 1] >> sh) & 0xffffu) - (int)((k2 >> (2 * j)) & 3u);
-      const float u = __uint_as_float(d0[j]), v = __uint_as_float(d1[j]);
-      const float w = -(u + v);
-      const float Q = __fdividef(u * u, (float)max(n0, 1)) + __fdividef(v * v, (float)max(n1, 1)) +
-                      __fdividef(w * w, (float)max(n2, 1));
+      const int n0 = (int)((w0[t >> 1] >> sh) & 0xffffu) - (int)((kb[0][hb] >> (4 * t)) & 15u);
+      const int n1 = (int)((w1[t >> 1] >> sh) & 0xffffu) - (int)((kb[1][hb] >> (4 * t)) & 15u);
+      const int n2 = (int)((w2[t >> 1] >> sh) & 0xffffu) - (int)((kb[2][hb] >> (4 * t)) & 15u);
       const int groups = (n0 > 0) + (n1 > 0) + (n2 > 0);
       const float thr = groups == 3 ? q2 : (groups == 2 ? q1 : inf);
-      need |= Q >= thr;
+      const float f0 = small_int_f(max(n0, 1)), f1 = small_int_f(max(n1, 1)),
+                  f2 = small_int_f(max(n2, 1));
+      const float u = __uint_as_float(d0[j]), v = __uint_as_float(d1[j]);
+      const float w = -(u + v);
+      const float f12 = f1 * f2;
+      const float num = fmaf(w * w, f0 * f1, fmaf(v * v, f0 * f2, u * u * f12));
+      need |= fmaf(-thr, f0 * f12, num) >= 0.f;
     }
   }
   return need;

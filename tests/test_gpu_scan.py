@@ -162,6 +162,28 @@ def test_nan_expression(kx, oracle_mod):
     check_dense(dn["dense_H"].cpu().numpy(), dn["dense_p"].cpu().numpy(), orc)
 
 
+@pytest.mark.parametrize("with_missing_geno", [False, True])
+def test_nan_counts_per_trait(kx, oracle_mod, with_missing_geno):
+    """Traits with 0..20 NaN samples (trait t has t mod 21): up to 15 per trait
+    the hot test works on each pair's exact group sizes, beyond that every pair
+    takes the rare path; with missing-genotype patterns the buckets' re-ranked
+    sets carry the same NaN lists.  The hit set must be the oracle's, so that a
+    hot test that drops a true hit fails here."""
+    d = synth.config(2, T=168, S=2100, seed=33)
+    x = d["expr"].copy()
+    g = d["geno"].copy()
+    rng = np.random.default_rng(9)
+    for t in range(x.shape[0]):
+        x[t, rng.choice(x.shape[1], t % 21, replace=False)] = np.nan
+    if with_missing_geno:
+        synth.add_missing_genotypes(rng, g, snp_frac=0.2, n_patterns=12, per_pattern=3)
+    pth = 2e-3
+    orc = oracle_mod.scan(x, g, pth)
+    rs = kx.krux_rank(_dev(x))
+    res = kx.krux_scan(rs, _dev(g), pth, capacity=168 * 2100)
+    check_hits(res, orc, np.arange(168), np.arange(2100), pth)
+
+
 def test_missing_genotypes(kx, oracle_mod):
     """Missing-value workload at reduced size: -1 genotypes in missing-sample
     patterns and NaN expression; ranks over the samples present in both."""
