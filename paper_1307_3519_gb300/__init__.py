@@ -471,8 +471,8 @@ class Krux:
         rs = self.krux_rank(e_d, stream)
         r = self.krux_scan(rs, g_d, pthresh, capacity, stream=stream)
         k = int(r["hits"].shape[0])
-        out = dict(n_hits=r["n_hits"], hits=r["hits"].cpu().numpy(), H=r["H"].cpu().numpy(),
-                   p=r["p"].cpu().numpy(), d2h_bytes=k * (16 + 8 + 8) + 8)
+        hits, H, P = _to_pinned_host(r["hits"], r["H"], r["p"])
+        out = dict(n_hits=r["n_hits"], hits=hits, H=H, p=P, d2h_bytes=k * (16 + 8 + 8) + 8)
         rs.free()
         return out
 
@@ -487,10 +487,24 @@ class Krux:
         g_d = g_h.to(self.device, non_blocking=True)
         rs = self.krux_rank(e_d, stream)
         r = self.krux_scan(rs, g_d, pthresh, capacity, stream=stream)
-        out = dict(n_hits=r["n_hits"], hits=r["hits"].cpu().numpy(), H=r["H"].cpu().numpy(),
-                   p=r["p"].cpu().numpy())
+        hits, H, P = _to_pinned_host(r["hits"], r["H"], r["p"])
+        out = dict(n_hits=r["n_hits"], hits=hits, H=H, p=P)
         rs.free()
         return out
+
+
+def _to_pinned_host(*tensors):
+    """Device tensors -> numpy arrays backed by pinned host memory (torch's caching
+    host allocator, so repeated calls reuse the blocks): the copies run at the
+    link's rate instead of through a pageable bounce buffer."""
+    import torch
+    outs = []
+    for t in tensors:
+        h = torch.empty(t.shape, dtype=t.dtype, pin_memory=True)
+        h.copy_(t, non_blocking=True)
+        outs.append(h)
+    torch.cuda.current_stream(tensors[0].device).synchronize()
+    return [h.numpy() for h in outs]
 
 
 class Graph:
