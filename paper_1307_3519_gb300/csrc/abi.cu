@@ -24,6 +24,7 @@ namespace krux {
 cudaError_t launch_missing_scan(const int8_t *geno, int64_t ldg, int N, int64_t snp_begin,
                                 int64_t n_snps, int max_code, unsigned int *n_missing,
                                 int64_t *miss_idx, uint64_t *miss_mask, unsigned int *status,
+                                uint32_t *flags,
                                 cudaStream_t s);
 cudaError_t launch_pack_linear(const int8_t *geno, int64_t ldg, int N, int Np, int64_t snp_begin,
                                int64_t n_snps, double rl, __half *B, ChunkMeta *meta,
@@ -628,13 +629,17 @@ krux_status find_missing(krux_ctx *ctx, const int8_t *geno, int64_t ldg, int N, 
   KRUX_CUDA(ctx, ctx->status.ensure(64));
   KRUX_CUDA(ctx, ctx->counters.ensure(64));
   KRUX_CUDA(ctx, ctx->miss_idx.ensure((size_t)std::max<int64_t>(n, 1) * 8));
-  KRUX_CUDA(ctx, ctx->miss_mask.ensure((size_t)std::max<int64_t>(n, 1) * (kMaxN / 8)));
+  // the masks, then one flag bit per SNP for the flat pre-pass
+  const size_t mask_bytes = (size_t)std::max<int64_t>(n, 1) * (kMaxN / 8);
+  KRUX_CUDA(ctx, ctx->miss_mask.ensure(mask_bytes + (size_t)(n + 31) / 32 * 4 + 256));
   KRUX_CUDA(ctx, cudaMemsetAsync(ctx->status.p, 0, 64, s));
   KRUX_CUDA(ctx, cudaMemsetAsync(ctx->counters.p, 0, 64, s));
   unsigned int *cnt = ctx->counters.as<unsigned int>();
+  uint32_t *flags = reinterpret_cast<uint32_t *>(ctx->miss_mask.as<char>() + mask_bytes);
   KRUX_CUDA(ctx, launch_missing_scan(geno, ldg, N, b, n, max_code, cnt, ctx->miss_idx.as<int64_t>(),
-                                     ctx->miss_mask.as<uint64_t>(), ctx->status.as<unsigned int>(), s));
-  if (ctx->profiling) ctx->prof.launches += 1;
+                                     ctx->miss_mask.as<uint64_t>(), ctx->status.as<unsigned int>(),
+                                     flags, s));
+  if (ctx->profiling) ctx->prof.launches += ldg == N ? 2 : 1;
   unsigned int m32 = 0, st = 0;
   KRUX_CUDA(ctx, cudaMemcpyAsync(&m32, cnt, 4, cudaMemcpyDeviceToHost, s));
   KRUX_CUDA(ctx, cudaMemcpyAsync(&st, ctx->status.p, 4, cudaMemcpyDeviceToHost, s));

@@ -48,6 +48,131 @@ missing_scan_kernel(const int8_t *__restrict__ geno, int64_t ldg, int N, int64_t
   }
 }
 
+// The same pre-pass for rows stored back to back (ldg == N), which is the usual
+// layout: the block is read as a flat byte array with 16-byte loads, every byte
+// checked four at a time; a -1 sets the bit of its SNP in `flags` (rare), a code
+// outside {-1, 0..max_code} sets kDevBadCode.  base = row 0 of the range, nbytes
+// = rows * N.
+__device__ __forceinline__ void missing_word(uint32_t x, int64_t o, int N, uint32_t mc4,
+                                             uint32_t *flags, bool &bad) {
+  uint32_t ff = __vcmpeq4(x, 0xffffffffu);
+  bad |= (__vcmpgtu4(x, mc4) & ~ff) != 0u;
+  while (ff != 0u) {
+    const int byte = (__ffs(ff) - 1) >> 3;
+    const int64_t snp = (o + byte) / N;
+    atomicOr(&flags[snp >> 5], 1u << (snp & 31));
+    ff &= ~(0xffu << (8 * byte));
+  }
+}
+
+__global__ void __launch_bounds__(256)
+missing_flag_kernel(const int8_t *__restrict__ base, int64_t nbytes, int N, int max_code,
+                    uint32_t *flags, unsigned int *status) {
+  const uint32_t mc4 = (uint32_t)max_code * 0x01010101u;
+  const int64_t head = std::min<int64_t>((16 - (int64_t)((uintptr_t)base & 15)) & 15, nbytes);
+  const int64_t words = (nbytes - head) / 16;
+  const int64_t tail0 = head + 16 * words;
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+  bool bad = false;
+  for (int64_t i = tid; i < words; i += nthreads) {
+    const uint4 v = *reinterpret_cast<const uint4 *>(base + head + 16 * i);
+    const int64_t o = head + 16 * i;
+    missing_word(v.x, o, N, mc4, flags, bad);
+    missing_word(v.y, o + 4, N, mc4, flags, bad);
+    missing_word(v.z, o + 8, N, mc4, flags, bad);
+    missing_word(v.w, o + 12, N, mc4, flags, bad);
+  }
+  // the unaligned head and the tail, one byte per thread
+  const int64_t extra = head + (nbytes - tail0);
+  if (tid < extra) {
+    const int64_t o = tid < head ? tid : tail0 + (tid - head);
+    const int code = base[o];
+    if (code == -1) {
+      const int64_t snp = o / N;
+      atomicOr(&flags[snp >> 5], 1u << (snp & 31));
+    }
+    bad |= code < -1 || code > max_code;
+  }
+  if (bad) atomicOr(status, kDevBadCode);
+}
+
+// The flagged SNPs (bit j of flags: SNP snp_begin + j) appended as (index, sample
+// bitmask), one warp per flag word.
+__global__ void __launch_bounds__(256)
+missing_collect_kernel(const int8_t *__restrict__ geno, int64_t ldg, int N, int64_t snp_begin,
+                       int64_t n_snps, const uint32_t *__restrict__ flags, unsigned int *n_missing,
+                       int64_t *miss_idx, uint64_t *miss_mask) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t w = (int64_t)blockIdx.x * 8 + warp;
+  if (w * 32 >= n_snps) return;
+  uint32_t bits = flags[w];
+  while (bits != 0u) {
+    const int bit = __ffs(bits) - 1;
+    bits &= bits - 1u;
+    const int64_t j = w * 32 + bit;
+    const int8_t *g = geno + (snp_begin + j) * ldg;
+    uint32_t words[kMaxN / 32];
+#pragma unroll
+    for (int q = 0; q < kMaxN / 32; ++q) {
+      words[q] = 0u;
+      if (q * 32 < N) {  // warp-uniform
+        const int k = q * 32 + lane;
+        words[q] = __ballot_sync(0xffffffffu, k < N && g[k] == -1);
+      }
+    }
+    unsigned int slot = 0;
+    if (lane == 0) slot = atomicAdd(n_missing, 1u);
+    slot = __shfl_sync(0xffffffffu, slot, 0);
+    if (lane == 0) miss_idx[slot] = snp_begin + j;
+    if (lane < kMaxN / 64) {
+      const uint64_t m = (uint64_t)words[2 * lane] | ((uint64_t)words[2 * lane + 1] << 32);
+      miss_mask[(int64_t)slot * (kMaxN / 64) + lane] = m;
+    }
+  }
+}
+
+// Metadata of SNP slot jj of a chunk: group sizes, df and the coefficients of the
+// hot test (zero for an excluded SNP: one with a missing code outside its bucket).
+__device__ __forceinline__ void write_meta(ChunkMeta &m, int jj, int n0, int n1, int n2,
+                                           bool excluded, int64_t snp_out, float rh1, float rh2,
+                                           int signed_df1, int linear, float rl) {
+  const int groups = (n0 > 0) + (n1 > 0) + (n2 > 0);
+  const int df = groups > 0 ? groups - 1 : 0;
+  float al = 0.f, be = 0.f, ga = 0.f;
+  if (linear) {
+    // dosage regression (parametric comparison): rl (2 S_0 + S_1)^2 / S_gg,
+    // S_gg = sum over samples of (g - mean g)^2
+    const int K = n0 + n1 + n2;
+    const float gs = (float)n1 + 2.f * (float)n2;
+    const float sgg = K > 0 ? (float)n1 + 4.f * (float)n2 - gs * gs / (float)K : 0.f;
+    if (df > 0 && !excluded && sgg > 0.5f / (float)(K > 0 ? K : 1)) {
+      al = 4.f * rl / sgg;
+      be = 0.5f;
+    }
+  } else if (df > 0 && !excluded) {
+    // sum_i D_i^2 / N_i with D_2 = -(u + v):  (r0 + r2) u^2 + 2 r2 u v + (r1 + r2) v^2
+    //   = alpha (u + beta v)^2 + gamma v^2,  alpha = r0 + r2, beta = r2 / alpha,
+    //   gamma = r1 + r2 r0 / alpha   (empty groups have r_i = 0).  FP32 is enough:
+    // these only feed the thresholded test, whose band is rechecked in FP64.
+    const float q0 = n0 ? 1.f / (float)n0 : 0.f, q1 = n1 ? 1.f / (float)n1 : 0.f,
+                q2 = n2 ? 1.f / (float)n2 : 0.f;
+    const float a = q0 + q2;
+    const float rh = (df == 1 ? rh1 : rh2) * ((signed_df1 && df == 1) ? -1.f : 1.f);
+    al = a * rh;
+    be = q2 / a;
+    ga = (q1 + q2 * q0 / a) * rh;
+  }
+  m.alpha[jj] = al;
+  m.beta[jj] = be;
+  m.gamma[jj] = ga;
+  m.snp[jj] = excluded ? -1 : (int32_t)snp_out;
+  m.n[0][jj] = (uint16_t)n0;
+  m.n[1][jj] = (uint16_t)n1;
+  m.n[2][jj] = (uint16_t)n2;
+  m.df[jj] = (uint8_t)df;
+}
+
 // Packs SNP slot j (one warp; j may be the padding of the last chunk).  SNP j is
 // snp_list[j] if a list is given, else snp_begin + j.  SNPs that carry a missing
 // code are packed with zero coefficients here (they are scanned in their
@@ -108,41 +233,8 @@ __device__ __forceinline__ void pack_slot(const int8_t *__restrict__ geno, int64
   if (lane == 0) {
     if (bad) atomicOr(status, kDevBadCode);
     if (miss && !allow_missing) atomicOr(status, kDevMissing);
-    const int groups = (n0 > 0) + (n1 > 0) + (n2 > 0);
-    const int df = groups > 0 ? groups - 1 : 0;
-    float al = 0.f, be = 0.f, ga = 0.f;
-    const bool excluded = miss && !allow_missing;
-    if (linear) {
-      // dosage regression (parametric comparison): rl (2 S_0 + S_1)^2 / S_gg,
-      // S_gg = sum over samples of (g - mean g)^2
-      const int K = n0 + n1 + n2;
-      const float gs = (float)n1 + 2.f * (float)n2;
-      const float sgg = K > 0 ? (float)n1 + 4.f * (float)n2 - gs * gs / (float)K : 0.f;
-      if (df > 0 && !excluded && sgg > 0.5f / (float)(K > 0 ? K : 1)) {
-        al = 4.f * rl / sgg;
-        be = 0.5f;
-      }
-    } else if (df > 0 && !excluded) {
-      // sum_i D_i^2 / N_i with D_2 = -(u + v):  (r0 + r2) u^2 + 2 r2 u v + (r1 + r2) v^2
-      //   = alpha (u + beta v)^2 + gamma v^2,  alpha = r0 + r2, beta = r2 / alpha,
-      //   gamma = r1 + r2 r0 / alpha   (empty groups have r_i = 0).  FP32 is enough:
-      // these only feed the thresholded test, whose band is rechecked in FP64.
-      const float q0 = n0 ? 1.f / (float)n0 : 0.f, q1 = n1 ? 1.f / (float)n1 : 0.f,
-                  q2 = n2 ? 1.f / (float)n2 : 0.f;
-      const float a = q0 + q2;
-      const float rh = (df == 1 ? rh1 : rh2) * ((signed_df1 && df == 1) ? -1.f : 1.f);
-      al = a * rh;
-      be = q2 / a;
-      ga = (q1 + q2 * q0 / a) * rh;
-    }
-    m.alpha[jj] = al;
-    m.beta[jj] = be;
-    m.gamma[jj] = ga;
-    m.snp[jj] = excluded ? -1 : (int32_t)(snp_out_base + s);
-    m.n[0][jj] = (uint16_t)n0;
-    m.n[1][jj] = (uint16_t)n1;
-    m.n[2][jj] = (uint16_t)n2;
-    m.df[jj] = (uint8_t)df;
+    write_meta(m, jj, n0, n1, n2, miss && !allow_missing, snp_out_base + s, rh1, rh2, signed_df1,
+               linear, rl);
   }
 }
 
@@ -171,16 +263,77 @@ __device__ __forceinline__ int find_job(const PackJob *__restrict__ jobs, int n_
   return lo;
 }
 
-// All SNP sets of a call in one launch: one warp per flattened slot.
+// All SNP sets of a call in one launch (rank-sum form): one warp per 32 flattened
+// slots (half a chunk; every job spans whole chunks).  Lane t writes samples
+// 4t .. 4t + 3 (+ 128 per pass) of both indicator rows of each slot with 8-byte
+// stores, the group sizes come from warp reductions, and lane i then writes the
+// metadata of slot i, so no lane does the per-SNP scalar work alone.
 __global__ void __launch_bounds__(kPackWarps * 32)
 pack_batch_kernel(const PackJob *__restrict__ jobs, int n_jobs, int64_t total_slots, float rh1,
                   float rh2, int signed_df1, unsigned int *status) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t x = (int64_t)blockIdx.x * kPackWarps + warp;
-  if (x >= total_slots) return;
-  const PackJob &J = jobs[find_job(jobs, n_jobs, x, false)];
-  pack_slot(J.geno, J.ldg, J.N, J.Np, J.snp_list, J.snp_begin, J.n_snps, x - J.slot0, 0, rh1, rh2,
-            J.allow_missing, signed_df1, J.B, J.meta, status, 0, 0.f, lane);
+  const int64_t x0 = ((int64_t)blockIdx.x * kPackWarps + warp) * 32;
+  if (x0 >= total_slots) return;
+  const PackJob &J = jobs[find_job(jobs, n_jobs, x0, false)];
+  const int64_t j0 = x0 - J.slot0;  // a multiple of 32
+  const int N = J.N, Np = J.Np;
+  const int64_t c = j0 / kChunkSnps;
+  const int jj0 = (int)(j0 % kChunkSnps);
+  const uint32_t one2 = 0x3c003c00u;  // two FP16 ones
+  int my_n0 = 0, my_n1 = 0, my_n2 = 0;
+  bool my_miss = false, any_bad = false;
+  int64_t my_s = 0;
+  for (int i = 0; i < 32; ++i) {
+    const int64_t j = j0 + i;
+    const bool valid = j < J.n_snps;
+    const int64_t s = valid ? (J.snp_list ? J.snp_list[j] : J.snp_begin + j) : 0;
+    const int8_t *g = J.geno + s * J.ldg;
+    __half *r0 = J.B + (c * kChunkRows + jj0 + i) * Np;
+    __half *r1 = J.B + (c * kChunkRows + kChunkSnps + jj0 + i) * Np;
+    int n0 = 0, n1 = 0, n2 = 0;
+    bool miss = false, bad = false;
+    for (int k0 = 4 * lane; k0 < Np; k0 += 128) {
+      uint32_t h0[2] = {0u, 0u}, h1[2] = {0u, 0u};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int k = k0 + q;
+        const int code = (valid && k < N) ? (int)g[k] : -1;
+        const uint32_t bit = (q & 1) ? 0xffff0000u : 0x0000ffffu;
+        if (code == 0) h0[q >> 1] |= one2 & bit;
+        if (code == 1) h1[q >> 1] |= one2 & bit;
+        n0 += code == 0;
+        n1 += code == 1;
+        n2 += code == 2;
+        if (valid && k < N) {
+          miss |= code == -1;
+          bad |= (code < -1 || code > 2);
+        }
+      }
+      *reinterpret_cast<uint2 *>(r0 + k0) = make_uint2(h0[0], h0[1]);
+      *reinterpret_cast<uint2 *>(r1 + k0) = make_uint2(h1[0], h1[1]);
+    }
+    n0 = (int)__reduce_add_sync(0xffffffffu, (unsigned)n0);
+    n1 = (int)__reduce_add_sync(0xffffffffu, (unsigned)n1);
+    n2 = (int)__reduce_add_sync(0xffffffffu, (unsigned)n2);
+    miss = __any_sync(0xffffffffu, miss);
+    any_bad |= bad;
+    if (lane == i) {
+      my_n0 = valid ? n0 : 0;
+      my_n1 = valid ? n1 : 0;
+      my_n2 = valid ? n2 : 0;
+      my_miss = miss;
+      my_s = valid ? s : -1;
+    }
+  }
+  if (__any_sync(0xffffffffu, any_bad) && lane == 0) atomicOr(status, kDevBadCode);
+  const bool excl = my_miss && !J.allow_missing;
+  if (__any_sync(0xffffffffu, excl) && lane == 0) atomicOr(status, kDevMissing);
+  ChunkMeta &m = J.meta[c];
+  if (my_s < 0) {  // padding slot of the last chunk
+    write_meta(m, jj0 + lane, 0, 0, 0, true, 0, rh1, rh2, signed_df1, 0, 0.f);
+  } else {
+    write_meta(m, jj0 + lane, my_n0, my_n1, my_n2, excl, my_s, rh1, rh2, signed_df1, 0, 0.f);
+  }
 }
 
 __device__ __forceinline__ uint64_t spread_bits(uint32_t v) {
@@ -331,8 +484,24 @@ cudaError_t launch_pack_linear(const int8_t *geno, int64_t ldg, int N, int Np, i
 cudaError_t launch_missing_scan(const int8_t *geno, int64_t ldg, int N, int64_t snp_begin,
                                 int64_t n_snps, int max_code, unsigned int *n_missing,
                                 int64_t *miss_idx, uint64_t *miss_mask, unsigned int *status,
-                                cudaStream_t s) {
+                                uint32_t *flags, cudaStream_t s) {
   if (n_snps <= 0) return cudaSuccess;
+  if (flags != nullptr && ldg == N) {  // rows back to back: the flat pre-pass
+    cudaError_t e = cudaMemsetAsync(flags, 0, (size_t)((n_snps + 31) / 32) * 4, s);
+    if (e != cudaSuccess) return e;
+    const int64_t nbytes = n_snps * (int64_t)N;
+    const int64_t words = nbytes / 16 + 32;
+    const int64_t blocks = std::min<int64_t>((words + 255) / 256, 152 * 16);
+    missing_flag_kernel<<<(unsigned)blocks, 256, 0, s>>>(geno + snp_begin * ldg, nbytes, N,
+                                                         max_code, flags, status);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int64_t fw = (n_snps + 31) / 32;
+    missing_collect_kernel<<<(unsigned)((fw + 7) / 8), 256, 0, s>>>(geno, ldg, N, snp_begin, n_snps,
+                                                                   flags, n_missing, miss_idx,
+                                                                   miss_mask);
+    return cudaGetLastError();
+  }
   const int64_t grid = (n_snps + kPackWarps - 1) / kPackWarps;
   missing_scan_kernel<<<(unsigned)grid, kPackWarps * 32, 0, s>>>(geno, ldg, N, snp_begin, n_snps,
                                                                  max_code, n_missing, miss_idx,
@@ -367,7 +536,8 @@ cudaError_t launch_pack_batch(const PackJob *jobs, int n_jobs, int64_t total_slo
                               unsigned int *status, cudaStream_t s) {
   if (n_jobs <= 0) return cudaSuccess;
   if (total_slots > 0) {
-    const int64_t grid = (total_slots + kPackWarps - 1) / kPackWarps;
+    const int64_t warps = (total_slots + 31) / 32;
+    const int64_t grid = (warps + kPackWarps - 1) / kPackWarps;
     pack_batch_kernel<<<(unsigned)grid, kPackWarps * 32, 0, s>>>(
         jobs, n_jobs, total_slots, (float)(1.0 / h1), (float)(1.0 / h2), signed_df1, status);
     const cudaError_t e = cudaGetLastError();
