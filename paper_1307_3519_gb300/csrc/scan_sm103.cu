@@ -821,16 +821,6 @@ __device__ __forceinline__ void minp_range(const uint32_t (&d0)[kEpiSnps],
   smin_out = smin;
 }
 
-// Hot filter of a permuted chunk half: true if some SNP may beat the running best,
-// or (FDR histogram on, tau_lo finite) may have p < P_c.
-__device__ __forceinline__ bool minp_fast(const uint32_t (&d0)[kEpiSnps], const uint32_t (&d1)[kEpiSnps],
-                                          const ChunkMeta &m, int h, const MinpState &st,
-                                          float tau_lo) {
-  float smax, smin;
-  minp_range(d0, d1, m, h, smax, smin);
-  return smax > st.s2_lo || -smin > st.s1_lo || fmaxf(smax, -smin) >= tau_lo;
-}
-
 // Seed bound of a step: FP32 -ln p of the largest values seen (ms holds them in
 // seed mode), less twice the recheck margin so that it stays below the FP64 key of
 // the pair that attains it.
@@ -978,7 +968,12 @@ __global__ void __launch_bounds__(kScanThreads, 1) krux_scan_kernel(const __grid
   uint8_t *scodes = reinterpret_cast<uint8_t *>(smeta + p.nc);
   const uint32_t codes_stride = (uint32_t)p.kpad * 16u;
   uint8_t *stc = scodes + (size_t)p.nc * codes_stride;  // trait-constant ring
-  uint64_t *bars = reinterpret_cast<uint64_t *>(stc + (size_t)kTcDepth * kTcBytes);
+  // permutation form: per trait row, the min-p filter bounds of the current step
+  // shared by the four warps that cover the row ((step tag << 32) | float bits;
+  // df-1 bounds, then df-2 bounds)
+  unsigned long long *sbound =
+      reinterpret_cast<unsigned long long *>(stc + (size_t)kTcDepth * kTcBytes);
+  uint64_t *bars = reinterpret_cast<uint64_t *>(sbound + 2 * kTileM);
   const uint32_t bar0 = smem_u32(bars);
   const int nA = p.nA, nc = p.nc;
   // barrier addresses
@@ -1025,6 +1020,7 @@ __global__ void __launch_bounds__(kScanThreads, 1) krux_scan_kernel(const __grid
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
+  for (int i = threadIdx.x; i < 2 * kTileM; i += blockDim.x) sbound[i] = 0ull;
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -1224,6 +1220,7 @@ __global__ void __launch_bounds__(kScanThreads, 1) krux_scan_kernel(const __grid
     const int q = warp & 3, h = warp >> 2;  // lane quarter, SNP group of the chunk
     uint32_t slot = 0, slot_phase = 0, b_bits = 0, tc_e = 0, tc_phase = 0;
     unsigned int wn = 0;  // hits this warp has appended to its staging segment
+    uint32_t step_tag = 0;  // steps begun by this warp (the same count in every epilogue warp)
     for (int it = blockIdx.x; it < p.n_items; it += gridDim.x) {
       const WorkItem w = p.items[it];
       const GroupDesc &g = p.groups[w.group];
@@ -1242,6 +1239,7 @@ __global__ void __launch_bounds__(kScanThreads, 1) krux_scan_kernel(const __grid
             slot_phase ^= 1u;
           }
         }
+        if constexpr (kForm == kFormPerm) ++step_tag;
         // this step's trait constants, staged by the producer
         if (!__all_sync(0xffffffffu, wait_bar(tc_full(tc_e), tc_phase, wc, 9))) goto epi_done;
         const uint8_t *tcp = stc + (size_t)tc_e * kTcBytes;
@@ -1351,8 +1349,26 @@ __global__ void __launch_bounds__(kScanThreads, 1) krux_scan_kernel(const __grid
               ms.s2_lo = fmaxf(ms.s2_lo, smax);
               ms.s1_lo = fmaxf(ms.s1_lo, -smin);
               need = false;
-            } else if (minp_mode)
-              need = et.valid && (et.nan_cnt > 0 || minp_fast(d0, d1, mc, h, ms, fdr_tau_lo));
+            } else if (minp_mode) {
+              if (!et.valid) {
+                need = false;
+              } else if (et.nan_cnt > 0) {
+                need = true;
+              } else {
+                float smax, smin;
+                minp_range(d0, d1, mc, h, smax, smin);
+                need = smax > ms.s2_lo || -smin > ms.s1_lo || fmaxf(smax, -smin) >= fdr_tau_lo;
+                if (need) {
+                  // the row's bounds from the other warps' leaders of this step first
+                  const unsigned long long b1 = sbound[row], b2 = sbound[kTileM + row];
+                  if ((uint32_t)(b1 >> 32) == step_tag)
+                    ms.s1_lo = fmaxf(ms.s1_lo, __uint_as_float((uint32_t)b1));
+                  if ((uint32_t)(b2 >> 32) == step_tag)
+                    ms.s2_lo = fmaxf(ms.s2_lo, __uint_as_float((uint32_t)b2));
+                  need = smax > ms.s2_lo || -smin > ms.s1_lo || fmaxf(smax, -smin) >= fdr_tau_lo;
+                }
+              }
+            }
             else if (kForm == kFormNan && et.nan_cnt > 0)
               need = p.dense || hit_fast_nan(d0, d1, mc, h, codes, et.nan_cnt, et.nan_idx,
                                              nan_q1, nan_q2);
@@ -1372,8 +1388,12 @@ __global__ void __launch_bounds__(kScanThreads, 1) krux_scan_kernel(const __grid
                 if (need) {
                   if (et.nan_cnt > 0)
                     minp_event_nan(dv, mc, codes, h, et.cfac, et.nan_cnt, et.nan_idx, &lead, p, ag);
-                  else
+                  else {
                     ms = minp_event(dv, mc, h, et.cfac, &lead, ms, fdr_tau_lo, p, ag);
+                    const unsigned long long tag = (unsigned long long)step_tag << 32;
+                    atomicMax(&sbound[row], tag | __float_as_uint(ms.s1_lo));
+                    atomicMax(&sbound[kTileM + row], tag | __float_as_uint(ms.s2_lo));
+                  }
                 }
               } else if (__any_sync(0xffffffffu, p.dense || et.nan_cnt > 0)) {
                 hit_slow(dv, need, mc, codes, h, et.trait, et.valid, et.ntlo, et.nthi, et.cfac,
@@ -1574,7 +1594,7 @@ size_t scan_smem_bytes(int nc, int nA, int kpad) {
 
 size_t scan_smem_bytes2(int nc, int nA, size_t a_tile_bytes, size_t b_region, int codes_k) {
   return 1024 + (size_t)nA * a_tile_bytes + b_region + (size_t)nc * sizeof(ChunkMeta) +
-         (size_t)nc * codes_k * 16 + (size_t)kTcDepth * kTcBytes +
+         (size_t)nc * codes_k * 16 + (size_t)kTcDepth * kTcBytes + 16 * (size_t)kTileM +
          8 * (size_t)(2 * nA + 2 * nc + 2 * kTmemSlots + 1 + 2 * kTcDepth) + 16;
 }
 
