@@ -898,7 +898,11 @@ __device__ __noinline__ MinpState minp_event(const uint32_t *dv, const ChunkMeta
     const float a = fabsf(sv);
     MinpCand &C = L->cls[k];
     bool take = a > C.s * (1.f + tie);
-    if (!take && a >= C.s * (1.f - tie)) {  // near tie with the leader: FP64
+    // near tie with the leader: FP64, unless the pair repeats the leader's sums and
+    // group sizes (copies of one SNP are common inside LD blocks) and so its key
+    const bool same = u == C.u && v == C.v && (n0 | (n1 << 16)) == C.n01 &&
+                      (n2 | (df << 16)) == C.n2df;
+    if (!take && !same && a >= C.s * (1.f - tie)) {
       if (key < 0.0) key = lead_key64(u, v, n0, n1, n2, df, cfac);
       take = key > cand_key64(C, cfac);
     }
@@ -1282,6 +1286,7 @@ __global__ void __launch_bounds__(kScanThreads, 1) krux_scan_kernel(const __grid
           }
           for (int k = 0; k < 2; ++k) {
             lead.cls[k].s = 0.f;
+            lead.cls[k].u = __int_as_float(0x7fc00000);  // NaN: equal to no pair
             lead.cls[k].k64 = -1.0;
           }
           lead.exact = -1.0;
