@@ -538,17 +538,133 @@ __device__ __noinline__ bool decide64(float u, float v, int n0, int n1, int n2, 
   return kw_p64(kw_H64((int)u, (int)v, n0, n1, n2, cfac), df) < pthresh;
 }
 
+
 // Rare path of a hit-mode chunk half without dense output or NaN traits, called
 // by the whole warp (inlined: a call costs more in register saves than the
 // extra code costs the hot loop).  Each lane classifies its candidates (two SNPs per packed
 // instruction: at or above the upper band edge -> hit, inside the band -> FP64),
-// then the warp appends the hits column by column, so that the lanes holding a
-// hit of SNP j write consecutive records.  Records first fill this warp's own
+// then the warp appends the hits in lane order with every lane writing records
+// (the source lane of record r is the first lane with inclusive count > r, found
+// by a binary search over shuffles; its SNP is the (r - excl)-th set bit of that
+// lane's mask and the sums come by shuffle), so the records of an event whose
+// hits sit in one lane still leave in whole vector stores.  Records first fill this warp's own
 // staging segment (`wn` records already there; no atomic); whatever does not fit
 // goes straight to the caller's list through the global counter.  Returns the
 // number of hits found (the warp's segment counter advances by it).  A compaction
 // pass appends the segments after the launch.
 __device__ __forceinline__ unsigned int hit_event(const uint32_t *dv, bool mine, const ChunkMeta &m,
+                                               int h, int trait, float ntlo, float nthi,
+                                               double cfac, const GroupDesc &g,
+                                               const ScanParams &p, unsigned int wn, int lane) {
+  const int jb = kEpiSnps * h;
+  uint32_t hm = 0;
+  if (mine) {
+    const uint64_t *al = reinterpret_cast<const uint64_t *>(m.alpha + jb);
+    const uint64_t *be = reinterpret_cast<const uint64_t *>(m.beta + jb);
+    const uint64_t *ga = reinterpret_cast<const uint64_t *>(m.gamma + jb);
+    const uint64_t lo2c = pk2(__float_as_uint(ntlo), __float_as_uint(ntlo));
+    const uint64_t hi2c = pk2(__float_as_uint(nthi), __float_as_uint(nthi));
+    uint32_t below = 0, not_sure = 0;  // sign bits of s - tau(1 -/+ margin)
+#pragma unroll
+    for (int j = 0; j < kEpiSnps; j += 2) {
+      const uint64_t u2 = pk2(dv[j], dv[j + 1]);
+      const uint64_t v2 = pk2(dv[kEpiSnps + j], dv[kEpiSnps + j + 1]);
+      const uint64_t w2 = ffma2(be[j / 2], v2, u2);
+      const uint64_t e2 = fmul2(ga[j / 2], v2);
+      uint64_t s2 = ffma2(fmul2(al[j / 2], w2), w2, fmul2(e2, v2));
+      if (p.signed_coef) s2 &= 0x7fffffff7fffffffull;
+      uint32_t la, lb, ha, hb;
+      upk2(fadd2(s2, lo2c), la, lb);
+      upk2(fadd2(s2, hi2c), ha, hb);
+      below |= ((la >> 31) | ((lb >> 31) << 1)) << j;
+      not_sure |= ((ha >> 31) | ((hb >> 31) << 1)) << j;
+    }
+    uint32_t cand = ~below & ((1u << kEpiSnps) - 1u);
+    while (cand) {
+      const int j = __ffs(cand) - 1;
+      cand &= cand - 1u;
+      if (m.snp[jb + j] < 0 || !in_cis_window(p, m.snp[jb + j], trait)) continue;
+      bool hit = p.provisional != 0 || ((not_sure >> j) & 1u) == 0u;
+      if (!hit)
+        hit = decide64(__uint_as_float(dv[j]), __uint_as_float(dv[kEpiSnps + j]), m.n[0][jb + j],
+                       m.n[1][jb + j], m.n[2][jb + j], m.df[jb + j], cfac, p.pthresh);
+      if (hit) hm |= 1u << j;
+    }
+  }
+  const unsigned int total = __reduce_add_sync(0xffffffffu, (unsigned int)__popc(hm));
+  if (total == 0u) return 0u;
+  const unsigned int cap = (unsigned int)p.seg_cap;
+  const unsigned int sbase = wn;
+  const unsigned int over_from = sbase > cap ? sbase : cap;  // first index beyond the segment
+  const unsigned int n_over = sbase + total > over_from ? sbase + total - over_from : 0u;
+  unsigned long long gbase = 0;
+  if (lane == 0 && n_over > 0) gbase = atomicAdd(g.counter, (unsigned long long)n_over);
+  gbase = __shfl_sync(0xffffffffu, gbase, 0);
+  const size_t seg0 = ((size_t)blockIdx.x * kEpiWarps + (threadIdx.x >> 5)) * cap;
+  const uint16_t gid = (uint16_t)g.group_id;
+  // lane l's hits take record indices [incl_l - cnt_l, incl_l) after sbase
+  const unsigned int cnt = (unsigned int)__popc(hm);
+  unsigned int incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  for (unsigned int r0 = 0; r0 < total; r0 += 32u) {
+    const unsigned int r = r0 + (unsigned int)lane;
+    int lo = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {  // first lane with incl > r
+      const unsigned int v = __shfl_sync(0xffffffffu, incl, lo + step - 1);
+      if (v <= r) lo += step;
+    }
+    const int src = lo < 31 ? lo : 31;
+    const unsigned int src_incl = __shfl_sync(0xffffffffu, incl, src);
+    const unsigned int src_cnt = __shfl_sync(0xffffffffu, cnt, src);
+    const uint32_t src_hm = __shfl_sync(0xffffffffu, hm, src);
+    const uint32_t src_trait = __shfl_sync(0xffffffffu, (uint32_t)trait, src);
+    const int j = (int)__fns(src_hm, 0u, (int)(r - (src_incl - src_cnt)) + 1);
+    uint32_t du = 0u, dw = 0u;
+#pragma unroll
+    for (int jj = 0; jj < kEpiSnps; ++jj) {
+      const uint32_t a = __shfl_sync(0xffffffffu, dv[jj], src);
+      const uint32_t b = __shfl_sync(0xffffffffu, dv[kEpiSnps + jj], src);
+      if (jj == j) {
+        du = a;
+        dw = b;
+      }
+    }
+    if (r < total) {
+      const unsigned int idx = sbase + r;
+      krux_hit rec;
+      rec.trait = src_trait;
+      rec.snp = (uint32_t)m.snp[jb + j];
+      rec.d0 = (int32_t)__uint_as_float(du);
+      rec.d1 = (int32_t)__uint_as_float(dw);
+      HitAux x;
+      x.n0 = m.n[0][jb + j];
+      x.n1 = m.n[1][jb + j];
+      x.n2 = m.n[2][jb + j];
+      x.group = gid;
+      if (idx < cap) {
+        st_hit(p.seg_hits + seg0 + idx, rec);
+        st_aux(p.seg_aux + seg0 + idx, x);
+      } else {
+        const unsigned long long gi = gbase + (idx - over_from);
+        if (gi < (unsigned long long)g.capacity) {
+          st_hit(g.hits + gi, rec);
+          st_aux(g.aux + gi, x);
+        }
+      }
+    }
+  }
+  return total;
+}
+
+// The same event with the records appended SNP column by SNP column (lanes with
+// a hit of the same SNP take consecutive records).  Smaller than the lane-order
+// append above; the permutation form uses it, where register room matters more.
+__device__ __forceinline__ unsigned int hit_event_cols(const uint32_t *dv, bool mine, const ChunkMeta &m,
                                                int h, int trait, float ntlo, float nthi,
                                                double cfac, const GroupDesc &g,
                                                const ScanParams &p, unsigned int wn, int lane) {
@@ -1404,8 +1520,12 @@ __global__ void __launch_bounds__(kScanThreads, 1) krux_scan_kernel(const __grid
                 hit_slow(dv, need, mc, codes, h, et.trait, et.valid, et.ntlo, et.nthi, et.cfac,
                          et.nan_cnt, et.nan_idx, g, p, lane);
               } else {
-                wn += hit_event(dv, need && et.valid, mc, h, et.trait, et.ntlo, et.nthi, et.cfac, g,
-                                p, wn, lane);
+                if constexpr (kForm == kFormPerm)
+                  wn += hit_event_cols(dv, need && et.valid, mc, h, et.trait, et.ntlo, et.nthi,
+                                       et.cfac, g, p, wn, lane);
+                else
+                  wn += hit_event(dv, need && et.valid, mc, h, et.trait, et.ntlo, et.nthi, et.cfac,
+                                  g, p, wn, lane);
               }
             }
           }
