@@ -580,6 +580,12 @@ __device__ __forceinline__ unsigned int hit_event(const uint32_t *dv, bool mine,
       not_sure |= ((ha >> 31) | ((hb >> 31) << 1)) << j;
     }
     uint32_t cand = ~below & ((1u << kEpiSnps) - 1u);
+    if (p.cis_window < 0) {
+      // padding and excluded SNPs carry zero coefficients and are never candidates:
+      // the clear hits need no loop, only the band goes on to FP64
+      hm = p.provisional != 0 ? cand : (cand & ~not_sure);
+      cand = p.provisional != 0 ? 0u : (cand & not_sure);
+    }
     while (cand) {
       const int j = __ffs(cand) - 1;
       cand &= cand - 1u;
