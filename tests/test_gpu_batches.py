@@ -95,6 +95,28 @@ def test_grouped_cohorts(kx, oracle_mod):
         assert res["n_hits"] == int(orc["hit"].sum())
 
 
+def test_grouped_cohorts_with_missing_values(kx, oracle_mod):
+    """Cohorts of different N in one launch, each with missing-genotype patterns and
+    NaN expression: the buckets of every cohort are re-ranked by one launch and
+    share one tensor map per cohort, groups of different width share the packed B
+    buffer, and the traits with NaN take the exact-size hot test."""
+    Ns = [60, 102, 150]
+    rng = np.random.default_rng(17)
+    cohorts, data = [], []
+    for n_c in Ns:
+        g, _ = synth.hwe_genotypes(rng, 900, n_c, 0.05, 0.5)
+        synth.add_missing_genotypes(rng, g, snp_frac=0.15, n_patterns=9, per_pattern=2)
+        e = synth.expression_lognormal(rng, 140, n_c)
+        synth.add_missing_expression(rng, e, 0.02)
+        data.append((e, g))
+        cohorts.append(dict(rs=kx.krux_rank(_dev(e)), geno=_dev(g), capacity=140 * 900))
+    pth = 1e-2
+    out = kx.krux_scan_grouped(cohorts, pth)
+    for (e, g), res in zip(data, out):
+        orc = oracle_mod.scan(e, g, pth)
+        check_hits(res, orc, np.arange(140), np.arange(900), pth)
+
+
 def test_bounded_wait_reports_timeout_and_context_survives(kx, oracle_mod):
     """With a one-cycle wait limit the first wait that has to spin gives up: the
     kernel drains its copies, frees TMEM and the call returns KRUX_ETIMEOUT.  The
