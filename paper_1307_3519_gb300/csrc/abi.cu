@@ -73,6 +73,33 @@ void plain_handle_destroy(void *h);
 
 namespace {
 
+// Pinned host staging buffer (grow-only): uploads from it run at the link's rate.
+// A call overwrites it only after the previous call's copies have completed
+// (every call synchronises its stream before returning).
+struct HostBuf {
+  void *p = nullptr;
+  size_t n = 0;
+  cudaError_t ensure(size_t bytes) {
+    if (bytes <= n) return cudaSuccess;
+    if (p) cudaFreeHost(p);
+    p = nullptr;
+    n = 0;
+    const size_t want = bytes + bytes / 4 + 4096;
+    cudaError_t e = cudaHostAlloc(&p, want, cudaHostAllocDefault);
+    if (e != cudaSuccess) {
+      p = nullptr;
+      return e;
+    }
+    n = want;
+    return cudaSuccess;
+  }
+  void release() {
+    if (p) cudaFreeHost(p);
+    p = nullptr;
+    n = 0;
+  }
+};
+
 struct DevBuf {
   void *p = nullptr;
   size_t n = 0;
@@ -171,6 +198,7 @@ struct krux_ctx {
   cudaEvent_t ev[kEv] = {};
   DevBuf B, meta, codes, groups, items, status, counters, aux, cfacptr, miss_idx, miss_mask,
       list, gemm_out, bucket_ranks, permA, minpkey, seg, permNan, aux2, param, paramOut, packjobs;
+  HostBuf list_host;  // staging of the SNP lists
   void *blas = nullptr;
   std::vector<std::pair<size_t, void *>> pool;  // freed rank-set blocks, reused by size
   std::map<int, std::array<int, 4>> tuned;       // krux_autotune: K width -> layout, nc, nA, ka
@@ -489,6 +517,7 @@ void krux_destroy(krux_ctx *ctx) {
                     &ctx->list, &ctx->gemm_out, &ctx->bucket_ranks, &ctx->permA, &ctx->minpkey, &ctx->seg,
                     &ctx->permNan, &ctx->aux2, &ctx->param, &ctx->paramOut, &ctx->packjobs};
   for (DevBuf *b : bufs) b->release();
+  ctx->list_host.release();
   for (auto &pb : ctx->pool) cudaFree(pb.second);
   for (int i = 0; i < kEv; ++i)
     if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
@@ -656,9 +685,17 @@ krux_status find_missing(krux_ctx *ctx, const int8_t *geno, int64_t ldg, int N, 
   KRUX_CUDA(ctx, cudaMemcpyAsync(mask.data(), ctx->miss_mask.p, mask.size() * 8,
                                  cudaMemcpyDeviceToHost, s));
   KRUX_CUDA(ctx, cudaStreamSynchronize(s));
-  std::vector<int64_t> order(m);
-  for (int64_t i = 0; i < m; ++i) order[i] = i;
-  std::sort(order.begin(), order.end(), [&](int64_t a, int64_t c) { return idx[a] < idx[c]; });
+  // the slots in SNP order (each SNP has at most one slot) and the complete rows,
+  // by one placement pass instead of a sort
+  std::vector<int32_t> slot_of((size_t)n, -1);
+  for (int64_t i = 0; i < m; ++i) slot_of[(size_t)(idx[i] - b)] = (int32_t)i;
+  std::vector<int64_t> order;
+  order.reserve((size_t)m);
+  complete.reserve((size_t)(n - m));
+  for (int64_t j = 0; j < n; ++j) {
+    if (slot_of[(size_t)j] >= 0) order.push_back(slot_of[(size_t)j]);
+    else complete.push_back(b + j);
+  }
   // buckets in order of their first SNP; a hash of the sample mask finds them
   using Key = std::array<uint64_t, W>;
   struct KeyHash {
@@ -682,11 +719,6 @@ krux_status find_missing(krux_ctx *ctx, const int8_t *geno, int64_t ldg, int N, 
     }
     buckets[ins.first->second].snps.push_back(idx[oi]);
   }
-  std::vector<char> is_miss((size_t)n, 0);
-  for (int64_t i = 0; i < m; ++i) is_miss[idx[i] - b] = 1;
-  complete.reserve((size_t)(n - m));
-  for (int64_t i = 0; i < n; ++i)
-    if (!is_miss[i]) complete.push_back(b + i);
   return KRUX_OK;
 }
 
@@ -861,7 +893,9 @@ krux_status plan_groups(krux_ctx *ctx, CallPlan &cp, const krux_rankset *rs, con
 krux_status materialise(krux_ctx *ctx, CallPlan &cp, cudaStream_t s) {
   if (!cp.lists.empty()) {
     KRUX_CUDA(ctx, ctx->list.ensure(cp.lists.size() * 8));
-    KRUX_CUDA(ctx, cudaMemcpyAsync(ctx->list.p, cp.lists.data(), cp.lists.size() * 8,
+    KRUX_CUDA(ctx, ctx->list_host.ensure(cp.lists.size() * 8));
+    std::memcpy(ctx->list_host.p, cp.lists.data(), cp.lists.size() * 8);
+    KRUX_CUDA(ctx, cudaMemcpyAsync(ctx->list.p, ctx->list_host.p, cp.lists.size() * 8,
                                    cudaMemcpyHostToDevice, s));
   }
   for (auto &g : cp.groups)
