@@ -607,7 +607,7 @@ krux_status krux_rank(krux_ctx *ctx, const float *expr, int T, int N, int64_t ld
   if (ctx->profiling) {
     ctx->prof = krux_profile{};
     ctx->prof.ms_rank = ev_ms(ctx, 0, 1);
-    ctx->prof.launches = 1;
+    ctx->prof.launches = 2;  // the rank transform and the padding-row constants
   }
   *out = rs;
   return KRUX_OK;
