@@ -62,9 +62,12 @@ KRUX_HD inline double ibeta(double a, double b, double x) {
   return 1.0 - std::exp(lfront) * ibeta_cf(b, a, 1.0 - x) / b;
 }
 
-// Upper tail of F(d1, d2) at f >= 0.
+// Upper tail of F(d1, d2) at f >= 0.  With two numerator degrees of freedom (three
+// genotype groups) I_x(d2/2, 1) = x^(d2/2), i.e. the tail is (1 + 2f/d2)^(-d2/2) in
+// closed form; other d1 take the continued fraction.
 KRUX_HD inline double f_tail(double f, double d1, double d2) {
   if (!(f > 0.0)) return 1.0;
+  if (d1 == 2.0) return std::exp(-0.5 * d2 * std::log1p(2.0 * f / d2));
   return ibeta(0.5 * d2, 0.5 * d1, d2 / (d2 + d1 * f));
 }
 

@@ -105,13 +105,14 @@ def test_every_autotune_candidate_is_sound_or_refused(lib):
 
 
 def test_parametric_tails_match_scipy(lib):
-    """The FP64 F / t tails of the parametric finalisation (continued fraction of
-    the incomplete beta function), evaluated on the host, against scipy."""
+    """The FP64 F / t tails of the parametric finalisation (closed form for two
+    numerator degrees of freedom, else the continued fraction of the incomplete
+    beta function), evaluated on the host, against scipy."""
     import paper_1307_3519_gb300 as k
     import scipy.special as sps
     import scipy.stats as st
-    for d1, d2 in [(1, 10), (1, 100), (2, 3), (2, 99), (1, 498), (2, 300)]:
-        for f in [0.01, 0.5, 1.0, 3.0, 7.5, 15.0, 30.0, 80.0]:
+    for d1, d2 in [(1, 10), (1, 100), (2, 3), (2, 99), (1, 498), (2, 300), (3, 99)]:
+        for f in [0.01, 0.5, 1.0, 3.0, 7.5, 15.0, 30.0, 80.0, 250.0]:
             want = st.f.sf(f, d1, d2)
             assert k.krux_debug_tail(0, f, d1, d2) == pytest.approx(want, rel=1e-10, abs=1e-300)
     for nu in [2, 5, 30, 100, 498]:
