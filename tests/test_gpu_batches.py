@@ -46,6 +46,20 @@ def test_permutation_minp(kx, oracle_mod, T, S, P, N):
     assert res["n_hits"] == int(orc["hit"].sum())
 
 
+def test_permutation_minp_with_seed_pass(kx, oracle_mod):
+    """Enough SNPs (70,000 > 4 x 16,384) for the seed pass that primes the minimum-p
+    keys with lower bounds before the main launch; every (permutation, trait)
+    minimum p against the oracle, on LD-block genotypes (many exact SNP copies)."""
+    d = synth.config(4, T=70, S=70000, seed=91)
+    perms = synth.make_perms(1307, 2, d["N"])
+    rs = kx.krux_rank(_dev(d["expr"]))
+    res = kx.krux_permute(rs, _dev(d["geno"]), _dev(perms), 1e-5, capacity=70 * 70000)
+    want = oracle_mod.perm_minp(d["expr"], d["geno"], perms)
+    got = res["minp"].cpu().numpy()
+    assert got.shape == want.shape
+    assert np.all(np.abs(got - want) <= 1e-6 * want), np.max(np.abs(got - want) / want)
+
+
 def test_permutation_minp_with_nan_expression(kx, oracle_mod):
     """NaN expression values move with the permuted columns: each permutation's
     group sizes exclude the samples whose permuted value is NaN."""
