@@ -46,11 +46,15 @@ def test_permutation_minp(kx, oracle_mod, T, S, P, N):
     assert res["n_hits"] == int(orc["hit"].sum())
 
 
-def test_permutation_minp_with_seed_pass(kx, oracle_mod):
+@pytest.mark.parametrize("nan", [0.0, 0.02])
+def test_permutation_minp_with_seed_pass(kx, oracle_mod, nan):
     """Enough SNPs (70,000 > 4 x 16,384) for the seed pass that primes the minimum-p
-    keys with lower bounds before the main launch; every (permutation, trait)
-    minimum p against the oracle, on LD-block genotypes (many exact SNP copies)."""
+    keys with lower bounds before the main launch (traits with NaN sit it out and
+    take the exact per-pair path); every (permutation, trait) minimum p against the
+    oracle, on LD-block genotypes (many exact SNP copies)."""
     d = synth.config(4, T=70, S=70000, seed=91)
+    if nan > 0:
+        synth.add_missing_expression(np.random.default_rng(5), d["expr"], nan)
     perms = synth.make_perms(1307, 2, d["N"])
     rs = kx.krux_rank(_dev(d["expr"]))
     res = kx.krux_permute(rs, _dev(d["geno"]), _dev(perms), 1e-5, capacity=70 * 70000)
