@@ -321,13 +321,14 @@ def run_fused(args):
     for _ in range(max(2, args.warmup)):  # warm-up (also fills the pinned-block cache)
         r = kx.scan_pinned(e_h, g_h, pth, cap)
     torch.cuda.synchronize()
+    barrier(world)
     t0 = time.perf_counter()
     d2h = 0
     for _ in range(esteps):
         r = kx.scan_pinned(e_h, g_h, pth, cap)
         d2h += r["d2h_bytes"]
-    e2e_s = time.perf_counter() - t0
-    e2e = {"value": pairs * esteps / e2e_s, "unit": "pairs/s",
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world)  # whole job: the slowest rank
+    e2e = {"value": pairs * world * esteps / e2e_s, "unit": "pairs/s",
            "h2d_bytes_per_step": int(e_h.numel() * 4 + g_h.numel()),
            "d2h_bytes_per_step": int(d2h // esteps)}
 
