@@ -333,7 +333,7 @@ def run_fused(args):
            "d2h_bytes_per_step": int(d2h // esteps)}
 
     cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:  # the oracle baseline: N = 1 only
         import oracle
         oracle.build()
         rate, info = oracle_sample_rate(d)
