@@ -280,16 +280,23 @@ pack_batch_kernel(const PackJob *__restrict__ jobs, int n_jobs, int64_t total_sl
   const int64_t c = j0 / kChunkSnps;
   const int jj0 = (int)(j0 % kChunkSnps);
   const uint32_t one2 = 0x3c003c00u;  // two FP16 ones
+  // the job's arrays through restrict pointers: the genotype reads of a slot may
+  // then be issued before the previous slot's stores
+  const int8_t *__restrict__ geno = J.geno;
+  const int64_t *__restrict__ snp_list = J.snp_list;
+  __half *__restrict__ Bj = J.B;
+  const int64_t ldg = J.ldg, n_snps = J.n_snps, snp_begin = J.snp_begin;
   int my_n0 = 0, my_n1 = 0, my_n2 = 0;
   bool my_miss = false, any_bad = false;
   int64_t my_s = 0;
+#pragma unroll 2
   for (int i = 0; i < 32; ++i) {
     const int64_t j = j0 + i;
-    const bool valid = j < J.n_snps;
-    const int64_t s = valid ? (J.snp_list ? J.snp_list[j] : J.snp_begin + j) : 0;
-    const int8_t *g = J.geno + s * J.ldg;
-    __half *r0 = J.B + (c * kChunkRows + jj0 + i) * Np;
-    __half *r1 = J.B + (c * kChunkRows + kChunkSnps + jj0 + i) * Np;
+    const bool valid = j < n_snps;
+    const int64_t s = valid ? (snp_list ? snp_list[j] : snp_begin + j) : 0;
+    const int8_t *g = geno + s * ldg;
+    __half *r0 = Bj + (c * kChunkRows + jj0 + i) * Np;
+    __half *r1 = Bj + (c * kChunkRows + kChunkSnps + jj0 + i) * Np;
     int n0 = 0, n1 = 0, n2 = 0;
     bool miss = false, bad = false;
     for (int k0 = 4 * lane; k0 < Np; k0 += 128) {
