@@ -90,7 +90,6 @@ rank_kernel(const float *__restrict__ expr, int T, int N, int64_t ld, int Np, Ra
     r.K[t] = K;
     r.nan_cnt[t] = (uint16_t)(N - K);
     if (N - K > 0) atomicOr(&r.tile_nan[t / kTileM], 1u);
-    trait_consts(K, tie, r.tau[t], r.cfac[t]);
   }
 }
 
@@ -156,6 +155,21 @@ __global__ void pad_traits_kernel(int T, int rows_pad, float *tau, double *cfac,
   nan_cnt[t] = 0;
 }
 
+// The FP64 trait constants of a rank set, one thread per row (FP64 issue is slow
+// on this part; done by one lane per trait in rank_kernel they cost most of its
+// time); padding rows get cfac 0, tau +inf and no NaN.
+__global__ void __launch_bounds__(256) rank_consts_kernel(int T, int rows_pad, RankDev r) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= rows_pad) return;
+  if (t < T) {
+    trait_consts(r.K[t], r.tie[t], r.tau[t], r.cfac[t]);
+  } else {
+    r.tau[t] = __int_as_float(0x7f800000);
+    r.cfac[t] = 0.0;
+    r.nan_cnt[t] = 0;
+  }
+}
+
 cudaError_t launch_pad_traits(int T, int rows_pad, float *tau, double *cfac, uint16_t *nan_cnt,
                               cudaStream_t s) {
   if (rows_pad <= T) return cudaSuccess;
@@ -170,7 +184,8 @@ cudaError_t launch_rank(const float *expr, int T, int N, int64_t ld, int Np, int
   rank_kernel<<<grid, kRankWarps * 32, smem, s>>>(expr, T, N, ld, Np, r);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  return launch_pad_traits(T, rows_pad, r.tau, r.cfac, r.nan_cnt, s);
+  rank_consts_kernel<<<(rows_pad + 255) / 256, 256, 0, s>>>(T, rows_pad, r);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_invert_perms(const int32_t *perms, int P, int N, int32_t *inv, cudaStream_t s) {
