@@ -11,7 +11,7 @@ host API with pinned host buffers, and the FP64 CPU oracle is timed on a
 bounded sample of the same workload on the host cores.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fused|reference]
-  python bench.py --scan-only [--traits T] [--snps S] [--data hwe|paper] [--reps R]
+  python bench.py --scan-only [--traits T] [--snps S] [--data hwe|paper] [--reps R] [--perms P]
 
 With --impl reference only the oracle arm runs (the CPU reference program),
 on a bounded sample per step, and prints the same JSON line with
@@ -44,8 +44,8 @@ WORKLOAD = ("paper-scale fused scan: N=102 samples, T=20000 traits, S=500000 SNP
 # launch on the paper-scale workload, from one ncu capture, with the git blob hash of
 # the kernel source it was taken on: reported only while that source is unchanged.
 # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum on "bench.py --scan-only
-# --traits 20000 --snps 500000 --data paper --tile 1,3,2,0" (the benchmark's workload
-# and autotuned shape): 242.06 MB read + 79.62 MB written in one launch (1 pass).
+# --traits 20000 --snps 500000 --data paper --tile 1,4,2,0" (the benchmark's workload
+# and autotuned shape): 241.27 MB read + 78.10 MB written in one launch (1 pass).
 SCAN_TRAFFIC = {"blob": "02a01e09e5245b5f6c2551f8441774ba6e351d26", "bytes": 319.37e6}
 
 
@@ -371,7 +371,8 @@ def run_scan_only(args):
     HWE genotypes (MAF 0.05-0.5) and log-normal expression, almost no hits;
     data=paper: the paper-scale workload's generator at these sizes; data=multi:
     markers with 2..5 genotype groups (codes 0..4; 4N flop per pair counted as for
-    biallelic markers, the contraction itself does 8N)."""
+    biallelic markers, the contraction itself does 8N).  --perms P: the permutation
+    form instead (krux_permute with P seeded permutations, (1 + P) T S pairs)."""
     import torch
     from paper_1307_3519_gb300 import build as kbuild
     kbuild.build()
@@ -403,6 +404,16 @@ def run_scan_only(args):
             print(f"scan-only autotuned shape (layout, nc, nA, ka) = {kx.autotune(rs, g, pth)}",
                   flush=True)
     kx.set_profiling(True)
+    if args.perms > 0:
+        perms = torch.from_numpy(synth.make_perms(1307, args.perms, 102)).cuda()
+        for i in range(args.reps):
+            r = kx.krux_permute(rs, g, perms, pth, capacity=min(50_000_000, T * S))
+            pr = kx.profile()
+            print(f"scan-only permute P={args.perms} data={args.data} T={T} S={S} call={i} "
+                  f"hits={r['n_hits']} scan={pr['ms_scan']:.3f} ms "
+                  f"({(1 + args.perms) * T * S / pr['ms_scan'] / 1e6:.4g} Gpairs/s) "
+                  f"launches={pr['launches']}", flush=True)
+        return
     for i in range(args.reps):
         r = kx.krux_scan(rs, g, pth, capacity=min(50_000_000, T * S), multiallelic=multi)
         pr = kx.profile()
@@ -503,6 +514,8 @@ def main():
     ap.add_argument("--snps", type=int, default=100000)
     ap.add_argument("--data", default="hwe", choices=["hwe", "paper", "multi"])
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--perms", type=int, default=0,
+                    help="scan-only: the permutation form with this many permutations")
     ap.add_argument("--rows", default="",
                     help="timing driver: comma list of missing,permute,cis,multi,param-anova,"
                          "param-linear,cohorts")
