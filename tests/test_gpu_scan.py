@@ -115,6 +115,32 @@ def test_slices_and_overflow(kx, oracle_mod):
     assert zero["n_hits"] == total
 
 
+def test_hits_past_the_staging_segments(kx, oracle_mod):
+    """Many hits per warp and a capacity of a third of them: each warp's staging
+    segment (sized from the capacity) holds about half of its hits, so the rest go
+    to the list through the global counter and the list ends up mixed.  The count
+    stays exact and every record kept must be an oracle hit with exact rank sums
+    and FP64 H and p."""
+    from kwcheck import gpu_hits_np, H_RTOL, H_ATOL, P_RTOL
+    d = synth.config(2, T=256, S=4000, seed=12)
+    pth = 0.05
+    orc = oracle_mod.scan(d["expr"], d["geno"], pth)
+    total = int(orc["hit"].sum())
+    assert total > 20000
+    rs = kx.krux_rank(_dev(d["expr"]))
+    cap = total // 3
+    res = kx.krux_scan(rs, _dev(d["geno"]), pth, capacity=cap)
+    assert res["overflow"] and res["n_hits"] == total and res["hits"].shape[0] == cap
+    h, H, p = gpu_hits_np(res)
+    t, snp = h[:, 0], h[:, 1]
+    assert len(set(zip(t.tolist(), snp.tolist()))) == cap, "duplicate records"
+    assert orc["hit"][t, snp].all(), "a record that is not a hit"
+    assert np.array_equal(h[:, 2], orc["d"][t, snp, 0]) and np.array_equal(h[:, 3], orc["d"][t, snp, 1])
+    oh, op = orc["H"][t, snp], orc["p"][t, snp]
+    assert np.all(np.abs(H - oh) <= H_RTOL * np.abs(oh) + H_ATOL)
+    assert np.all(np.abs(p - op) <= P_RTOL * op)
+
+
 def test_degenerate_inputs(kx, oracle_mod):
     """Monomorphic SNPs, all-tied traits, a single sample group and S = 0."""
     d = synth.config(1, T=40, S=200, seed=3)
