@@ -257,7 +257,10 @@ krux_status krux_get_profile(const krux_ctx *ctx, krux_profile *out);
  * capture.  Every call on a device shares the array, and the previous call's
  * contents stay in it (each call clears what must start at zero); calls that
  * overlap on the GPU race, so issue them on one stream or serialise them.  The
- * call synchronises `stream` before returning. */
+ * call synchronises `stream` before returning.  Its kernels give up a spinning
+ * wait after a fixed limit of 4x10^9 SM cycles (about two seconds) and then
+ * return KRUX_ETIMEOUT; krux_set_wait_limit, which sets a context's limit, has
+ * no effect here (this entry point has no context). */
 krux_status krux_scan_noalloc(const float *expr, int T, int N, int64_t ld, const int8_t *geno,
                               int64_t S, int64_t ldg, double pthresh, krux_hit *hits,
                               double *hit_H, double *hit_p, int64_t hit_capacity,

@@ -131,6 +131,21 @@ def krux_scan_noalloc(expr, geno, pthresh, hits, hit_H, hit_p, stream=None):
     expr cuda float32 [T, N], geno cuda int8 [S, N], outputs preallocated by the
     caller (hits int32 [cap, 4], hit_H / hit_p float64 [cap]).  Returns
     (status, exact hit count)."""
+    import torch
+    for name, t, dt in (("expr", expr, torch.float32), ("geno", geno, torch.int8),
+                        ("hits", hits, torch.int32), ("hit_H", hit_H, torch.float64),
+                        ("hit_p", hit_p, torch.float64)):
+        if t.dtype != dt or not t.is_cuda:
+            raise ValueError(f"krux_scan_noalloc: {name} must be a CUDA {dt} tensor")
+    if expr.dim() != 2 or geno.dim() != 2 or expr.stride(1) != 1 or geno.stride(1) != 1:
+        raise ValueError("krux_scan_noalloc: expr and geno must be 2-D with contiguous rows")
+    if hits.dim() != 2 or hits.shape[1] != 4 or not hits.is_contiguous():
+        raise ValueError("krux_scan_noalloc: hits must be a contiguous int32 [capacity, 4] tensor")
+    if hit_H.numel() < hits.shape[0] or hit_p.numel() < hits.shape[0] or \
+            not hit_H.is_contiguous() or not hit_p.is_contiguous():
+        raise ValueError("krux_scan_noalloc: hit_H and hit_p need hits.shape[0] contiguous entries")
+    if len({expr.device, geno.device, hits.device, hit_H.device, hit_p.device}) != 1:
+        raise ValueError("krux_scan_noalloc: all tensors must be on one device")
     n = ctypes.c_int64()
     st = load_library().krux_scan_noalloc(
         ctypes.c_void_p(expr.data_ptr()), expr.shape[0], expr.shape[1], expr.stride(0),

@@ -1292,6 +1292,15 @@ krux_status prepare_fused(krux_ctx *ctx, CallPlan &cp, const krux_opts *o, Fused
     p.cis_trait_pos = cp.cis.trait_pos;
     p.cis_window = cp.cis.window;
   }
+  // the plain scan form: 32-byte swizzle, every group's chunks paired and its K
+  // in one rank stage, complete data, no dense output, cis window, provisional
+  // hits, permutations or markers with more than three groups
+  {
+    bool fast = layout == 1 && !p.multi && !p.perm && !p.has_nan && !p.dense && !p.provisional &&
+                !p.signed_coef && p.cis_window < 0;
+    for (const GroupDesc &d : descs) fast = fast && d.pair == 1 && d.nkb == 1;
+    p.fast = fast ? 1 : 0;
+  }
   fl.grid = (int)std::min<size_t>(items.size(), (size_t)ctx->sm_count);
   // Single hit list: every epilogue warp stages its hits in a segment of its own
   // (no atomic per hit event) and the segments are appended after the launch.
@@ -1312,6 +1321,10 @@ krux_status prepare_fused(krux_ctx *ctx, CallPlan &cp, const krux_opts *o, Fused
     if (cp.multi) p.seg_aux2 = reinterpret_cast<HitAux2 *>(sb + a2off);
   }
   fl.smem = scan_smem_bytes2(nc_max, sh.nA, (size_t)p.a_tile_bytes, (size_t)p.b_region, p.kpad);
+  if (p.fast) {  // the plain scan form also holds its ring of hit-event buffers
+    if (fl.smem + kEvRegion <= kSmemLimit) fl.smem += kEvRegion;
+    else p.fast = 0;
+  }
   const std::string why = validate_plan(p, descs, fl.smem);
   if (!why.empty()) return fail(ctx, KRUX_EUNSUPPORTED, "%s", why.c_str());
   if (fl.grid > 0) KRUX_CUDA(ctx, scan_set_smem(fl.smem));

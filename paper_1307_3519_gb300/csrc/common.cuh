@@ -24,6 +24,49 @@ constexpr int kEpiSnps = 16;       // SNPs of a chunk each epilogue warp evaluat
 constexpr int kProducerWarp = 16;  // TMA producer
 constexpr int kMmaWarp = 17;       // tcgen05.mma issuer, owns the TMEM allocation
 constexpr int kScanThreads = 576;
+// The plain scan form (complete data, chunks paired into N = 256 MMAs): each of
+// its epilogue warps owns kFastSnps SNPs of one chunk of every accumulator pair
+// for one TMEM lane quarter (32 traits); after them come the producer, the MMA
+// issuer and two idle warps that complete their warpgroup, whose registers go to
+// the epilogue warps (setmaxnreg: both splits use all registers of the launch).
+constexpr int kFastSnps = 32;
+constexpr int kFastEpiWarps = 4 * (2 * kChunkSnps / kFastSnps);  // 16
+constexpr int kFastThreads = 32 * (kFastEpiWarps + 4);
+// the register file is split among the 4 schedulers: at most 16384 per scheduler
+constexpr int kFastRegsLaunch = (16384 / (32 * (kFastThreads / 128))) / 8 * 8;
+constexpr int kFastRegsLow = 56;
+constexpr int kFastRegsHigh =
+    (kFastRegsLaunch + 4 * (kFastRegsLaunch - kFastRegsLow) / kFastEpiWarps) / 8 * 8;
+static_assert(kFastEpiWarps == 16, "16 epilogue warps in the plain scan form");
+static_assert(kFastThreads * kFastRegsLaunch <= 65536, "launch registers");
+static_assert(4 * (kFastRegsLaunch - kFastRegsLow) >= kFastEpiWarps * (kFastRegsHigh - kFastRegsLaunch),
+              "the epilogue's extra registers must come from the producer warpgroup");
+
+// Hit events of the plain scan form are handed to the two idle warps of the
+// producer warpgroup through a ring of shared-memory entries: an epilogue warp
+// whose half-block (kEvSnps SNPs x 32 traits) has a candidate writes, for each
+// trait lane that found one, an entry with that trait's kEvSnps centred sums and
+// constants and the SNPs' metadata, and goes on; an event warp classifies the
+// entry's pairs (FP64 inside the band) and appends the hit records.
+constexpr int kEvSnps = kFastSnps / 2;  // 16
+constexpr int kEvEntries = 32;
+struct EvEntry {
+  float u[kEvSnps], v[kEvSnps];                 // D_0, D_1 of SNP j for this trait
+  float alpha[kEvSnps], beta[kEvSnps], gamma[kEvSnps];  // the SNPs' fast-test coefficients
+  int32_t snp[kEvSnps];                         // output SNP index
+  uint32_t n01[kEvSnps];                        // N_0 | N_1 << 16
+  uint32_t n2df[kEvSnps];                       // N_2 | df << 16
+  double cfac;                                  // 3 / (K(K+1)C) of the trait
+  float tau;                                    // its fast-test bound
+  int32_t trait;                                // its trait row
+  int32_t group;
+  int32_t pad_[3];
+};
+static_assert(sizeof(EvEntry) % 16 == 0, "event entries keep 16-byte alignment");
+// shared memory of the ring: alignment slack, entries, a full barrier and a
+// release count per entry, one 64-bit word (tickets claimed in the low 40 bits,
+// epilogue warps done above)
+constexpr size_t kEvRegion = 128 + kEvEntries * sizeof(EvEntry) + kEvEntries * 8 + kEvEntries * 4 + 8;
 // Per-step trait constants staged in shared memory by the producer (one entry per
 // 128-trait tile step): tau f32 [128] @0, 3/(K(K+1)C) f64 [128] @512, starting
 // -ln p key f64 [128] @1536 (permutation batches), NaN count u16 [128] @2560.
@@ -233,6 +276,9 @@ struct ScanParams {
   int32_t seed_bound = 0;
   // some group's rank set has NaN (its traits get the exact-size hot test)
   int32_t has_nan = 0;
+  // the plain scan form applies: 32-byte swizzle, every group's chunks paired, no
+  // NaN, no dense output, no cis window, no provisional hits, no permutations
+  int32_t fast = 0;
 };
 
 enum : unsigned int {

@@ -130,16 +130,6 @@ bool na_encode(const DeviceSetup &d, CUtensorMap *map, const void *base, int Np,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// Flags a -1 (missing) genotype code in SNP rows [b, b+n): this entry point
-// scans complete genotypes only.
-__global__ void na_missing_check(const int8_t *__restrict__ geno, int64_t ldg, int N, int64_t b,
-                                 int64_t n, unsigned int *flag) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n * N;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    if (geno[(b + i / N) * ldg + i % N] == -1) atomicOr(flag, 4u);
-  }
-}
-
 }  // namespace
 
 #define NA_CUDA(call)                                   \
@@ -215,8 +205,6 @@ extern "C" krux_status krux_scan_noalloc(const float *expr, int T, int N, int64_
   for (int64_t b = 0; b < S; b += kNaSlice) {
     const int64_t n = std::min<int64_t>(kNaSlice, S - b);
     const int64_t nch = (n + kChunkSnps - 1) / kChunkSnps;
-    na_missing_check<<<152, 256, 0, s>>>(geno, ldg, N, b, n, status);
-    NA_CUDA(cudaGetLastError());
     NA_CUDA(launch_pack2(geno, ldg, N, Np, nullptr, b, n, 0, h1, h2, 0, 0, B, meta, codes, status, s));
     GroupDesc g;
     std::memset(&g, 0, sizeof g);
@@ -278,6 +266,9 @@ extern "C" krux_status krux_scan_noalloc(const float *expr, int T, int N, int64_
     p.timeout_cycles = 4000000000LL;
     p.signed_coef = 0;
     p.seg_cap = 0;  // hits go straight to the caller's list
+    // the rank set may hold NaN: the kernel form with exact per-pair group sizes for
+    // traits with NaN (traits without NaN take the ordinary hot test there)
+    p.has_nan = 1;
     const int grid = std::min(ni, d->sm_count);
     NA_CUDA(launch_scan(p, grid, scan_smem_bytes(nc, nA, Np), s));
   }
@@ -286,9 +277,9 @@ extern "C" krux_status krux_scan_noalloc(const float *expr, int T, int N, int64_
   NA_CUDA(cudaMemcpyAsync(&cnt, counter, 8, cudaMemcpyDeviceToHost, s));
   NA_CUDA(cudaMemcpyAsync(hst, status, 8, cudaMemcpyDeviceToHost, s));
   NA_CUDA(cudaStreamSynchronize(s));
-  if (hst[0] & 2u) return KRUX_EINVAL;        // genotype code outside {-1,0,1,2}
-  if (hst[0] & 4u) return KRUX_EUNSUPPORTED;  // missing genotypes
-  if (hst[0] & 1u) return KRUX_ETIMEOUT;
+  if (hst[0] & kDevBadCode) return KRUX_EINVAL;        // genotype code outside {-1,0,1,2}
+  if (hst[0] & kDevMissing) return KRUX_EUNSUPPORTED;  // a -1 code (packed as complete data)
+  if (hst[0] & kDevTimeout) return KRUX_ETIMEOUT;
   const int64_t stored = std::min<int64_t>((int64_t)cnt, cap);
   if (stored > 0) {
     NA_CUDA(launch_finalize(hits, aux, stored, cfacptr, hit_H, hit_p, s));

@@ -19,6 +19,9 @@
 //   warp 17   : TMEM allocator and tcgen05.mma issuer (one thread)
 // Every mbarrier wait is bounded: on timeout the kernel raises an error bit,
 // drains its own asynchronous copies and MMAs, frees TMEM and returns.
+#include <atomic>
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace krux {
@@ -79,6 +82,22 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
       : "memory");
   return ok != 0u;
 }
+// The same with a suspend-time hint: a thread whose phase is not complete sleeps
+// (issuing nothing) until the phase completes or about `ns` nanoseconds pass.
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint32_t bar, uint32_t parity, uint32_t ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity), "r"(ns)
+      : "memory");
+  return ok != 0u;
+}
+// Suspend hint of the bounded waits (ns): long enough that a waiting thread
+// takes no issue slots from the working warps of its scheduler, short enough
+// that timeouts and aborts are still noticed promptly.
+constexpr uint32_t kWaitSleepNs = 200000u;
 
 struct WaitCtl {
   volatile int *abort_flag;
@@ -92,7 +111,7 @@ __device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, const Wa
   if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = clock64();
   while (true) {
-    if (mbar_try_wait(bar, parity)) return true;
+    if (mbar_try_wait_sleep(bar, parity, kWaitSleepNs)) return true;
     if (*w.abort_flag) return false;
     if (clock64() - t0 > w.limit) {
       *w.abort_flag = 1;
@@ -103,11 +122,34 @@ __device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, const Wa
   }
 }
 
+// The same bounded wait, reading its limit and status words from the kernel
+// parameters and the abort flag through its shared-memory address (keeps no
+// per-thread copies of them in registers).
+__device__ __forceinline__ bool wait_bar_p(uint32_t bar, uint32_t parity, const ScanParams &p,
+                                         uint32_t abort_addr, unsigned int where) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (true) {
+    if (mbar_try_wait_sleep(bar, parity, kWaitSleepNs)) return true;
+    int ab;
+    asm volatile("ld.volatile.shared.u32 %0, [%1];" : "=r"(ab) : "r"(abort_addr) : "memory");
+    if (ab) return false;
+    if (clock64() - t0 > p.timeout_cycles) {
+      asm volatile("st.volatile.shared.u32 [%0], %1;" ::"r"(abort_addr), "r"(1) : "memory");
+      atomicOr(p.status, kDevTimeout);
+      atomicMax(p.status + 1, where);
+      return false;
+    }
+  }
+}
+
 // Wait used while shutting down: ignores the abort flag (copies and MMAs already
 // issued must land before the CTA can release its shared memory and TMEM) and
 // gives up only after a fixed bound of about two seconds.
-__device__ __noinline__ void wait_drain(uint32_t bar, uint32_t parity, unsigned int *status,
-                                        unsigned int where) {
+// (inline: it is also reached by warps that have given registers away with
+// setmaxnreg, which must call no function compiled for more registers)
+__device__ __forceinline__ void wait_drain(uint32_t bar, uint32_t parity, unsigned int *status,
+                                           unsigned int where) {
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
     if (clock64() - t0 > 4000000000LL) {
@@ -537,6 +579,13 @@ __device__ __noinline__ bool decide64(float u, float v, int n0, int n1, int n2, 
                                       double pthresh) {
   return kw_p64(kw_H64((int)u, (int)v, n0, n1, n2, cfac), df) < pthresh;
 }
+// The same decision inline, for the event warps of the plain scan form: they run
+// with fewer registers than the kernel was compiled for (setmaxnreg) and must not
+// call a function compiled for the full count.
+__device__ __forceinline__ bool decide64_inl(float u, float v, int n0, int n1, int n2, int df,
+                                             double cfac, double pthresh) {
+  return kw_p64(kw_H64((int)u, (int)v, n0, n1, n2, cfac), df) < pthresh;
+}
 
 
 // Rare path of a hit-mode chunk half without dense output or NaN traits, called
@@ -754,6 +803,352 @@ __device__ __forceinline__ unsigned int hit_event_cols(const uint32_t *dv, bool 
     run += (unsigned int)__popc(bal);
   }
   return total;
+}
+
+// Hit event of the plain scan form, on the accumulator registers themselves
+// (static indexing only, so no local-memory copy): each lane classifies its
+// kEpiSnps pairs two at a time (at or above the upper band edge: hit; inside the
+// band: decided in FP64 from the exact sums, rare), then the warp appends the
+// records SNP column by SNP column, skipping columns without a hit in any lane
+// (lanes with a hit of the same SNP take consecutive records).  Records fill this
+// warp's staging segment (`wn` records already there); what does not fit goes
+// straight to the caller's list through the global counter.  Returns the number
+// of hits found.
+__device__ __forceinline__ unsigned int hit_event_reg(const uint32_t (&d0)[kEpiSnps],
+                                                      const uint32_t (&d1)[kEpiSnps],
+                                                      const ChunkMeta &m, int h, int trait,
+                                                      float ntlo, float nthi, double cfac,
+                                                      const GroupDesc &g, const ScanParams &p,
+                                                      unsigned int wn, int lane) {
+  const int jb = kEpiSnps * h;
+  const uint64_t *al = reinterpret_cast<const uint64_t *>(m.alpha + jb);
+  const uint64_t *be = reinterpret_cast<const uint64_t *>(m.beta + jb);
+  const uint64_t *ga = reinterpret_cast<const uint64_t *>(m.gamma + jb);
+  const uint64_t lo2c = pk2(__float_as_uint(ntlo), __float_as_uint(ntlo));
+  const uint64_t hi2c = pk2(__float_as_uint(nthi), __float_as_uint(nthi));
+  uint32_t below = 0, not_sure = 0;  // sign bits of s - tau(1 -/+ margin)
+#pragma unroll
+  for (int j = 0; j < kEpiSnps; j += 2) {
+    const uint64_t u2 = pk2(d0[j], d0[j + 1]);
+    const uint64_t v2 = pk2(d1[j], d1[j + 1]);
+    const uint64_t w2 = ffma2(be[j / 2], v2, u2);
+    const uint64_t e2 = fmul2(ga[j / 2], v2);
+    const uint64_t s2 = ffma2(fmul2(al[j / 2], w2), w2, fmul2(e2, v2));
+    uint32_t la, lb, ha, hb;
+    upk2(fadd2(s2, lo2c), la, lb);
+    upk2(fadd2(s2, hi2c), ha, hb);
+    below |= ((la >> 31) | ((lb >> 31) << 1)) << j;
+    not_sure |= ((ha >> 31) | ((hb >> 31) << 1)) << j;
+  }
+  // padding SNPs and degenerate traits carry zero coefficients / an infinite bound
+  // and are never candidates
+  const uint32_t cand = ~below & ((1u << kEpiSnps) - 1u);
+  uint32_t hm = cand & ~not_sure;
+  uint32_t band = cand & not_sure;
+  while (band) {  // inside the band: p < P_c decided in FP64 (rare)
+    const int j = __ffs(band) - 1;
+    band &= band - 1u;
+    float u = 0.f, v = 0.f;
+#pragma unroll
+    for (int jj = 0; jj < kEpiSnps; ++jj)
+      if (jj == j) {
+        u = __uint_as_float(d0[jj]);
+        v = __uint_as_float(d1[jj]);
+      }
+    if (decide64(u, v, m.n[0][jb + j], m.n[1][jb + j], m.n[2][jb + j], m.df[jb + j], cfac,
+                 p.pthresh))
+      hm |= 1u << j;
+  }
+  const unsigned int total = __reduce_add_sync(0xffffffffu, (unsigned int)__popc(hm));
+  if (total == 0u) return 0u;
+  const unsigned int cap = (unsigned int)p.seg_cap;
+  const unsigned int sbase = wn;
+  const unsigned int over_from = sbase > cap ? sbase : cap;  // first index beyond the segment
+  const unsigned int n_over = sbase + total > over_from ? sbase + total - over_from : 0u;
+  unsigned long long gbase = 0;
+  if (lane == 0 && n_over > 0) gbase = atomicAdd(g.counter, (unsigned long long)n_over);
+  gbase = __shfl_sync(0xffffffffu, gbase, 0);
+  const size_t seg0 = ((size_t)blockIdx.x * kEpiWarps + (threadIdx.x >> 5)) * cap;
+  const uint32_t below_me = (1u << lane) - 1u;
+  const uint16_t gid = (uint16_t)g.group_id;
+  const uint32_t cols = __reduce_or_sync(0xffffffffu, hm);
+  unsigned int run = sbase;  // index of the next record (same in every lane)
+#pragma unroll
+  for (int j = 0; j < kEpiSnps; ++j) {
+    if (((cols >> j) & 1u) == 0u) continue;  // warp-uniform
+    const bool mine = (hm >> j) & 1u;
+    const uint32_t bal = __ballot_sync(0xffffffffu, mine);
+    if (mine) {
+      const unsigned int idx = run + (unsigned int)__popc(bal & below_me);
+      krux_hit r;
+      r.trait = (uint32_t)trait;
+      r.snp = (uint32_t)m.snp[jb + j];
+      r.d0 = (int32_t)__uint_as_float(d0[j]);
+      r.d1 = (int32_t)__uint_as_float(d1[j]);
+      HitAux x;
+      x.n0 = m.n[0][jb + j];
+      x.n1 = m.n[1][jb + j];
+      x.n2 = m.n[2][jb + j];
+      x.group = gid;
+      if (idx < cap) {
+        st_hit(p.seg_hits + seg0 + idx, r);
+        st_aux(p.seg_aux + seg0 + idx, x);
+      } else {
+        const unsigned long long gi = gbase + (idx - over_from);
+        if (gi < (unsigned long long)g.capacity) {
+          st_hit(g.hits + gi, r);
+          st_aux(g.aux + gi, x);
+        }
+      }
+    }
+    run += (unsigned int)__popc(bal);
+  }
+  return total;
+}
+
+// ---- the plain scan form: one warp per chunk of an accumulator pair ----------
+// 32 consecutive fp32 columns of this warp's 32 TMEM lanes.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t *r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+      "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
+}
+
+// 16 consecutive fp32 columns of this warp's 32 TMEM lanes.
+__device__ __forceinline__ void tmem_ld16p(uint32_t taddr, uint32_t *r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+}
+// kFastSnps / 2 = 16 SNPs' D_0 and D_1 (columns c and 64 + c of the chunk) of this lane.
+__device__ __forceinline__ void tmem_ld_half(uint32_t taddr, uint32_t (&u)[kFastSnps / 2],
+                                             uint32_t (&v)[kFastSnps / 2]) {
+  tmem_ld16p(taddr, u);
+  tmem_ld16p(taddr + 64u, v);
+}
+
+// Hot test of kFastSnps SNPs of a chunk (from SNP `off`) for this lane's trait:
+// true when some pair may lie at or above the lower edge of the band (q >= 0),
+// two SNPs per packed instruction, w = u + beta v, q = alpha w^2 + gamma v^2 -
+// tau (1 - margin).  Blocks of 16 SNPs; two sign accumulators.
+template <int NS>
+__device__ __forceinline__ bool hit_fast_w(const uint32_t (&d0)[NS], const uint32_t (&d1)[NS],
+                                           const ChunkMeta &m, int off, float ntlo) {
+  const uint64_t nt2 = pk2(__float_as_uint(ntlo), __float_as_uint(ntlo));
+  uint32_t acc0 = 0xffffffffu, acc1 = 0xffffffffu;  // AND of the sign bits (two chains)
+#pragma unroll
+  for (int b = 0; b < NS / 16; ++b) {
+    const uint64_t *al = reinterpret_cast<const uint64_t *>(m.alpha + off + 16 * b);
+    const uint64_t *be = reinterpret_cast<const uint64_t *>(m.beta + off + 16 * b);
+    const uint64_t *ga = reinterpret_cast<const uint64_t *>(m.gamma + off + 16 * b);
+#pragma unroll
+    for (int j = 0; j < 8; j += 2) {
+      const ulonglong2 A = *reinterpret_cast<const ulonglong2 *>(al + j);
+      const ulonglong2 B = *reinterpret_cast<const ulonglong2 *>(be + j);
+      const ulonglong2 G = *reinterpret_cast<const ulonglong2 *>(ga + j);
+#pragma unroll
+      for (int t = 0; t < 2; ++t) {
+        const int jj = 16 * b + 2 * (j + t);
+        const uint64_t u2 = pk2(d0[jj], d0[jj + 1]);
+        const uint64_t v2 = pk2(d1[jj], d1[jj + 1]);
+        const uint64_t a2 = t ? A.y : A.x, b2 = t ? B.y : B.x, g2 = t ? G.y : G.x;
+        const uint64_t w2 = ffma2(b2, v2, u2);
+        const uint64_t e2 = fmul2(g2, v2);
+        uint64_t q2 = ffma2(e2, v2, nt2);
+        q2 = ffma2(fmul2(a2, w2), w2, q2);
+        uint32_t qa, qb;
+        upk2(q2, qa, qb);
+        if (t) acc1 &= qa & qb;
+        else acc0 &= qa & qb;
+      }
+    }
+    // compiler barrier: the next block's coefficient loads are not hoisted above
+    // this one (the accumulator registers stay live throughout)
+    if (b + 1 < NS / 16) asm volatile("" ::: "memory");
+  }
+  return (int)(acc0 & acc1) >= 0;
+}
+
+// ---- hit events of the plain scan form, handled by the event warps ---------
+// Several epilogue warps claim tickets at once, so one of them may claim an
+// entry's use k while uses k-1, k-2 are still pending: a phase-parity wait
+// cannot tell those apart.  A filler therefore waits on the entry's release count
+// (uses the event warp has finished) reaching k; the uses of an entry are then
+// filled in order, and its single consumer can wait on the full barrier by phase
+// parity.
+struct EvRing {
+  EvEntry *ent;
+  uint32_t bar0;                // ev_full[e] at bar0 + 8 e
+  unsigned int *released;       // [kEvEntries] uses of each entry the event warps have finished
+  unsigned long long *word;     // tickets claimed (low 40 bits), epilogue warps done (above)
+  __device__ __forceinline__ uint32_t full(int e) const { return bar0 + 8u * (uint32_t)e; }
+};
+constexpr unsigned long long kEvTicketMask = (1ull << 40) - 1ull;
+
+// Bounded wait of lane 0 until the entry of ticket t is free for its use t /
+// kEvEntries; false on timeout or abort.
+__device__ __forceinline__ bool ev_gate(const EvRing &ev, unsigned long long t, const ScanParams &p,
+                                        uint32_t abort_addr) {
+  const unsigned int k = (unsigned int)(t / kEvEntries);
+  const volatile unsigned int *rel = ev.released + (t % kEvEntries);
+  if (*rel >= k) return true;
+  const long long t0 = clock64();
+  while (*rel < k) {
+    __nanosleep(128);
+    int ab;
+    asm volatile("ld.volatile.shared.u32 %0, [%1];" : "=r"(ab) : "r"(abort_addr) : "memory");
+    if (ab) return false;
+    if (clock64() - t0 > p.timeout_cycles) {
+      asm volatile("st.volatile.shared.u32 [%0], %1;" ::"r"(abort_addr), "r"(1) : "memory");
+      atomicOr(p.status, kDevTimeout);
+      atomicMax(p.status + 1, 16u);
+      return false;
+    }
+  }
+  return true;
+}
+
+// An epilogue warp hands the traits of a half-block whose hot test found a
+// candidate to the event warps: one entry per such trait lane (tickets claimed
+// together), each with that lane's kEvSnps centred sums and constants and the
+// SNPs' metadata (written by lanes 0..kEvSnps-1).  False if a wait gave up.
+__device__ __forceinline__ bool ev_submit(const EvRing &ev, const uint32_t (&u)[kEvSnps],
+                                          const uint32_t (&v)[kEvSnps], bool need,
+                                          const ChunkMeta &m, int off, float tau, double cfac,
+                                          int trait, int group, const ScanParams &p,
+                                          uint32_t abort_addr, int lane) {
+  uint32_t lanes = __ballot_sync(0xffffffffu, need);
+  unsigned long long t = 0;
+  if (lane == 0) t = atomicAdd(ev.word, (unsigned long long)__popc(lanes)) & kEvTicketMask;
+  t = __shfl_sync(0xffffffffu, t, 0);
+  // this lane's SNP metadata (lanes 0..kEvSnps-1), written into every entry
+  const int jo = off + (lane & (kEvSnps - 1));
+  const float al = m.alpha[jo], be = m.beta[jo], ga = m.gamma[jo];
+  const int32_t sn = m.snp[jo];
+  const uint32_t n01 = (uint32_t)m.n[0][jo] | ((uint32_t)m.n[1][jo] << 16);
+  const uint32_t n2df = (uint32_t)m.n[2][jo] | ((uint32_t)m.df[jo] << 16);
+  while (lanes) {
+    const int L = __ffs((int)lanes) - 1;
+    lanes &= lanes - 1u;
+    int ok = 1;
+    if (lane == 0) {
+      ok = ev_gate(ev, t, p, abort_addr) ? 1 : 0;
+      __threadfence_block();  // the event warp's reads of the old contents come first
+    }
+    if (!__shfl_sync(0xffffffffu, ok, 0)) return false;
+    const int e = (int)(t % kEvEntries);
+    EvEntry &E = ev.ent[e];
+    if (lane < kEvSnps) {
+      E.alpha[lane] = al;
+      E.beta[lane] = be;
+      E.gamma[lane] = ga;
+      E.snp[lane] = sn;
+      E.n01[lane] = n01;
+      E.n2df[lane] = n2df;
+    }
+    if (lane == L) {
+#pragma unroll
+      for (int j = 0; j < kEvSnps; j += 4) {
+        *reinterpret_cast<uint4 *>(E.u + j) = make_uint4(u[j], u[j + 1], u[j + 2], u[j + 3]);
+        *reinterpret_cast<uint4 *>(E.v + j) = make_uint4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+      }
+      E.cfac = cfac;
+      E.tau = tau;
+      E.trait = trait;
+      E.group = group;
+    }
+    __threadfence_block();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(ev.full(e));
+    ++t;
+  }
+  return true;
+}
+
+// Group fields an event warp needs, cached across entries.
+struct EvGroup {
+  int index = -1;
+  krux_hit *hits;
+  HitAux *aux;
+  unsigned long long *counter;
+  int64_t capacity;
+  uint16_t gid;
+};
+
+// An event warp's work on one entry: lanes j < kEvSnps classify the pair (trait,
+// SNP j) in the same FP32 form as the hot test (at or above the upper band edge:
+// hit; inside the band: decided in FP64 from the exact sums) and the hits are
+// appended in SNP order, one record per lane, into this warp's staging region of
+// kEpiWarps / 2 segments of the CTA (`wn` records already there); what does not
+// fit goes to the group's list through its counter.  Returns the number of hits.
+__device__ __forceinline__ unsigned int ev_process(const EvEntry &E, EvGroup &G, const ScanParams &p,
+                                                   unsigned int wn, int lane, int ev_warp) {
+  const int j = lane & (kEvSnps - 1);
+  const bool act = lane < kEvSnps;
+  const float tau = E.tau;
+  const float u = E.u[j], v = E.v[j];
+  const float w = fmaf(E.beta[j], v, u);
+  const float s = fmaf(E.alpha[j] * w, w, (E.gamma[j] * v) * v);
+  const bool cand = act && s + -tau * (1.f - p.margin) >= 0.f;
+  bool hit = cand && s + -tau * (1.f + p.margin) >= 0.f;
+  const uint32_t n01 = E.n01[j], n2df = E.n2df[j];
+  if (__any_sync(0xffffffffu, cand && !hit)) {  // inside the band: FP64 (rare)
+    if (cand && !hit)
+      hit = decide64_inl(u, v, (int)(n01 & 0xffffu), (int)(n01 >> 16), (int)(n2df & 0xffffu),
+                         (int)(n2df >> 16), E.cfac, p.pthresh);
+  }
+  const uint32_t bal = __ballot_sync(0xffffffffu, hit);
+  const unsigned int n = (unsigned int)__popc(bal);
+  if (n == 0u) return 0u;
+  if (E.group != G.index) {
+    const GroupDesc &g = p.groups[E.group];
+    G.index = E.group;
+    G.hits = g.hits;
+    G.aux = g.aux;
+    G.counter = g.counter;
+    G.capacity = g.capacity;
+    G.gid = (uint16_t)g.group_id;
+  }
+  constexpr int kSegs = kEpiWarps / 2;  // staging segments per event warp
+  const unsigned int cap = (unsigned int)(kSegs * p.seg_cap);
+  const unsigned int over_from = wn > cap ? wn : cap;  // first index beyond the region
+  const unsigned int n_over = wn + n > over_from ? wn + n - over_from : 0u;
+  unsigned long long gbase = 0;
+  if (lane == 0 && n_over > 0) gbase = atomicAdd(G.counter, (unsigned long long)n_over);
+  gbase = __shfl_sync(0xffffffffu, gbase, 0);
+  if (hit) {
+    krux_hit rec;
+    rec.trait = (uint32_t)E.trait;
+    rec.snp = (uint32_t)E.snp[j];
+    rec.d0 = (int32_t)u;
+    rec.d1 = (int32_t)v;
+    HitAux x;
+    x.n0 = (uint16_t)(n01 & 0xffffu);
+    x.n1 = (uint16_t)(n01 >> 16);
+    x.n2 = (uint16_t)(n2df & 0xffffu);
+    x.group = G.gid;
+    const unsigned int idx = wn + (unsigned int)__popc(bal & ((1u << lane) - 1u));
+    if (idx < cap) {
+      const size_t seg0 = ((size_t)blockIdx.x * kEpiWarps + kSegs * ev_warp) * (size_t)p.seg_cap;
+      st_hit(p.seg_hits + seg0 + idx, rec);
+      st_aux(p.seg_aux + seg0 + idx, x);
+    } else {
+      const unsigned long long gi = gbase + (idx - over_from);
+      if (gi < (unsigned long long)G.capacity) {
+        st_hit(G.hits + gi, rec);
+        st_aux(G.aux + gi, x);
+      }
+    }
+  }
+  return n;
 }
 
 // ---- markers with up to five groups ---------------------------------------
@@ -1079,8 +1474,20 @@ __device__ __noinline__ double minp_step_best(MinpLead *L, double cfac) {
 // state of one out of the registers of the others.
 enum ScanForm { kFormScan = 0, kFormMulti = 1, kFormPerm = 2, kFormNan = 3 };
 
+// Warp roles of a kernel form: the epilogue warps first, then the producer and
+// the MMA issuer (the plain scan form also has two idle warps after them).
 template <int kForm>
-__global__ void __launch_bounds__(kScanThreads, 1) krux_scan_kernel(const __grid_constant__ ScanParams p) {
+struct ScanRoles {
+  static constexpr int kEpi = kForm == kFormScan ? kFastEpiWarps : kEpiWarps;
+  static constexpr int kProducer = kEpi;
+  static constexpr int kMma = kEpi + 1;
+  static constexpr int kThreads = kForm == kFormScan ? kFastThreads : kScanThreads;
+};
+
+template <int kForm>
+__global__ void __launch_bounds__(ScanRoles<kForm>::kThreads, 1)
+    krux_scan_kernel(const __grid_constant__ ScanParams p) {
+  using R = ScanRoles<kForm>;
   extern __shared__ uint8_t smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t raw = smem_u32(smem_raw);
@@ -1117,6 +1524,17 @@ __global__ void __launch_bounds__(kScanThreads, 1) krux_scan_kernel(const __grid
   uint32_t *tmem_holder =
       reinterpret_cast<uint32_t *>(bars + 2 * nA + 2 * nc + 2 * kTmemSlots + 1 + 2 * kTcDepth);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_holder + 1);
+  // plain scan form: the ring of hit-event buffers after everything else
+  EvRing ev;
+  {
+    uint8_t *evr = reinterpret_cast<uint8_t *>(
+        (reinterpret_cast<uintptr_t>(tmem_holder) + 16u + 127u) & ~(uintptr_t)127u);
+    ev.ent = reinterpret_cast<EvEntry *>(evr);
+    ev.bar0 = smem_u32(evr + kEvEntries * sizeof(EvEntry));
+    ev.released = reinterpret_cast<unsigned int *>(evr + kEvEntries * sizeof(EvEntry) + kEvEntries * 8);
+    ev.word = reinterpret_cast<unsigned long long *>(evr + kEvEntries * sizeof(EvEntry) +
+                                                     kEvEntries * 8 + kEvEntries * 4);
+  }
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < nA; ++s) {
@@ -1125,22 +1543,29 @@ __global__ void __launch_bounds__(kScanThreads, 1) krux_scan_kernel(const __grid
     }
     for (int c = 0; c < nc; ++c) {
       mbar_init(b_full(c), 1);
-      mbar_init(b_empty(c), 1 + kEpiWarps);
+      mbar_init(b_empty(c), 1 + R::kEpi);
     }
     for (int s = 0; s < kTmemSlots; ++s) {
       mbar_init(t_full(s), 1);
-      mbar_init(t_empty(s), kEpiWarps);
+      mbar_init(t_empty(s), R::kEpi);
     }
     mbar_init(drain, 1);
     for (int e = 0; e < kTcDepth; ++e) {
       mbar_init(tc_full(e), 1);
-      mbar_init(tc_empty(e), kEpiWarps);
+      mbar_init(tc_empty(e), R::kEpi);
     }
     *abort_flag = 0;
+    if constexpr (kForm == kFormScan) {
+      for (int e = 0; e < kEvEntries; ++e) {
+        mbar_init(ev.full(e), 1);
+        ev.released[e] = 0u;
+      }
+      *ev.word = 0ull;
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
-  if (warp == kMmaWarp) {
+  if (warp == R::kMma) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
                      smem_u32(tmem_holder))
                  : "memory");
@@ -1152,8 +1577,12 @@ __global__ void __launch_bounds__(kScanThreads, 1) krux_scan_kernel(const __grid
   tc_fence_after();
   const uint32_t tmem_base = *tmem_holder;
   const WaitCtl wc{abort_flag, p.status, p.timeout_cycles};
+  // plain scan form: the registers of the producer warpgroup (warps 8-11) go to
+  // the epilogue warps; each role's code sits under its own setmaxnreg
 
-  if (warp == kProducerWarp) {
+  if (warp == R::kProducer) {
+    if constexpr (kForm == kFormScan)
+      asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kFastRegsLow) : "memory");
     if (lane == 0) {
       uint32_t a_stage = 0, a_phase = 0, b_bits = 0;
       uint32_t a_used = 0, a_last = 0, b_used = 0, b_last = 0;
@@ -1243,7 +1672,66 @@ __global__ void __launch_bounds__(kScanThreads, 1) krux_scan_kernel(const __grid
         if ((tc_used >> e) & 1u) wait_drain(tc_full(e), (tc_last >> e) & 1u, p.status, 13);
     }
     __syncwarp();
-  } else if (warp == kMmaWarp) {
+  } else if (warp == R::kMma && kForm == kFormScan) {
+    // MMA issuer of the plain scan form: one N = 256 MMA chain per chunk pair (N =
+    // 128 for an odd last chunk) into accumulator pair `ps` (TMEM columns ps *
+    // 256 ..), released by the 8 epilogue warps as soon as they have loaded it
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kFastRegsLow) : "memory");
+    if (lane == 0) {
+      uint32_t a_stage = 0, a_phase = 0, b_bits = 0, ps = 0, ps_phase = 0;
+      for (int it = blockIdx.x; it < p.n_items; it += gridDim.x) {
+        const WorkItem w = p.items[it];
+        const GroupDesc *g = p.groups + w.group;
+        const int ncg = g->nc;
+        const int nc_item = min(ncg, g->nchunks - w.btile * ncg);
+        const uint32_t b_stride = (uint32_t)g->b_stride;
+        const int ksteps = g->Np / 16;
+        for (int step = w.step_begin; step < w.step_end; ++step) {
+          if (!wait_bar(a_full(a_stage), a_phase, wc, 3)) goto fast_mma_done;
+          tc_fence_after();
+          const uint32_t a_tile = sA + a_stage * a_tile_bytes;
+          for (int c = 0; c < nc_item; c += 2) {
+            const bool two = c + 1 < nc_item;
+            if (step == w.step_begin) {
+              if (!wait_bar(b_full(c), (b_bits >> c) & 1u, wc, 4)) goto fast_mma_done;
+              if (two && !wait_bar(b_full(c + 1), (b_bits >> (c + 1)) & 1u, wc, 4)) goto fast_mma_done;
+            }
+            if (!wait_bar(t_empty(ps), ps_phase ^ 1u, wc, 5)) goto fast_mma_done;
+            tc_fence_after();
+            // pair layout: [K atom][chunk of the pair][128 rows of 32 B]; a K step
+            // moves the start address field only (it never carries)
+            const uint32_t b_tile = sB + (uint32_t)(c >> 1) * 2u * b_stride;
+            uint64_t da = umma_desc(a_tile, 1), db = umma_desc(b_tile, 1);
+            const uint32_t d_tmem = tmem_base + ps * 256u;
+            const uint32_t idesc = two ? kIdesc256 : kIdesc;
+            tc_mma(d_tmem, da, db, idesc, 0u);
+            for (int k = 1; k < ksteps; ++k) {
+              da += 4096u >> 4;
+              db += 8192u >> 4;
+              tc_mma(d_tmem, da, db, idesc, 1u);
+            }
+            tc_commit(t_full(ps));
+            ps ^= 1u;
+            if (ps == 0u) ps_phase ^= 1u;
+          }
+          tc_commit(a_empty(a_stage));
+          if (++a_stage == (uint32_t)nA) {
+            a_stage = 0;
+            a_phase ^= 1u;
+          }
+        }
+        for (int c = 0; c < nc_item; ++c) {
+          tc_commit(b_empty(c));
+          b_bits ^= 1u << c;
+        }
+      }
+    fast_mma_done:
+      // all issued MMAs must finish before TMEM is released
+      tc_commit(drain);
+      wait_drain(drain, 0, p.status, 12);
+    }
+    __syncwarp();
+  } else if (warp == R::kMma) {
     if (lane == 0) {
       uint32_t a_stage = 0, a_phase = 0, b_bits = 0, slot = 0, slot_phase = 0;
       for (int it = blockIdx.x; it < p.n_items; it += gridDim.x) {
@@ -1341,6 +1829,144 @@ __global__ void __launch_bounds__(kScanThreads, 1) krux_scan_kernel(const __grid
       wait_drain(drain, 0, p.status, 12);
     }
     __syncwarp();
+  } else if constexpr (kForm == kFormScan) {
+    // epilogue warps of the plain scan form: warp 4k + q owns lane quarter q of
+    // kFastSnps SNPs of one chunk of every accumulator pair; it loads their D_0 and
+    // D_1 with one wait, releases the pair at once, then runs the hot test (and,
+    // when a lane has a candidate, the hit event) on the registers
+    if (warp >= R::kEpi) {  // the two event warps of the producer warpgroup
+      asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kFastRegsLow) : "memory");
+      const int e = warp - (R::kMma + 1);
+      unsigned int wn = 0;  // hits this event warp has appended to its staging region
+      EvGroup G;
+      for (unsigned long long t = (unsigned long long)e;; t += 2) {
+        const int b = (int)(t % kEvEntries);
+        const uint32_t ph = (uint32_t)((t / kEvEntries) & 1ull);
+        // lane 0 waits until ticket t is filled or no more tickets can come
+        int got = 0;
+        if (lane == 0) {
+          const long long t0 = clock64();
+          while (true) {
+            if (mbar_try_wait_sleep(ev.full(b), ph, 20000u)) {
+              got = 1;
+              break;
+            }
+            if (*abort_flag) break;
+            const unsigned long long wv = *reinterpret_cast<volatile unsigned long long *>(ev.word);
+            if ((wv >> 40) >= (unsigned long long)kFastEpiWarps && t >= (wv & kEvTicketMask)) break;
+            if (clock64() - t0 > p.timeout_cycles) {
+              *abort_flag = 1;
+              atomicOr(p.status, kDevTimeout);
+              atomicMax(p.status + 1, 17u);
+              break;
+            }
+          }
+        }
+        got = __shfl_sync(0xffffffffu, got, 0);
+        if (!got) break;
+        wn += ev_process(ev.ent[b], G, p, wn, lane, e);
+        __syncwarp();
+        if (lane == 0) {  // this use of the buffer is finished
+          __threadfence_block();
+          atomicAdd(ev.released + b, 1u);
+        }
+      }
+      if (lane == 0 && p.seg_cap > 0) {  // this event warp's staging segments
+        constexpr int kSegs = kEpiWarps / 2;
+        const unsigned int cap = (unsigned int)p.seg_cap;
+        for (int sgi = 0; sgi < kSegs; ++sgi) {
+          const unsigned int lo = cap * (unsigned int)sgi;
+          p.seg_cnt[blockIdx.x * kEpiWarps + kSegs * e + sgi] = wn > lo ? min(wn - lo, cap) : 0u;
+        }
+      }
+    } else {
+      asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kFastRegsHigh) : "memory");
+      constexpr int kPerChunk = kChunkSnps / kFastSnps;  // warps per chunk and lane quarter
+      const int q = warp & 3, k = warp >> 2;
+      const int h = k / kPerChunk;                     // chunk of the pair
+      const int off = kFastSnps * (k % kPerChunk);     // first SNP within the chunk
+      const int row = 32 * q + lane;
+      const uint32_t abort_addr = smem_u32(const_cast<const int *>(abort_flag));
+      const uint32_t lane_cols =
+          tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(128 * h + off);
+      uint32_t ps = 0, ps_phase = 0, b_bits = 0, tc_e = 0, tc_phase = 0;
+      unsigned int wn = 0;  // hits this warp has appended to its staging region
+      for (int it = blockIdx.x; it < p.n_items; it += gridDim.x) {
+        const WorkItem w = p.items[it];
+        const GroupDesc &g = p.groups[w.group];
+        const int g_nc = g.nc, g_ntt = g.n_ttiles;
+        const int nc_item = min(g_nc, g.nchunks - w.btile * g_nc);
+        int tt = w.step_begin % g_ntt;  // trait tile of the step
+        for (int step = w.step_begin; step < w.step_end; ++step) {
+          // this step's trait constants, staged by the producer (copied out at once)
+          if (!__all_sync(0xffffffffu, wait_bar_p(tc_full(tc_e), tc_phase, p, abort_addr, 9)))
+            goto epi_done_scan;
+          const uint8_t *tcp = stc + (size_t)tc_e * kTcBytes;
+          const float tau = reinterpret_cast<const float *>(tcp)[row];
+          const double cfac = reinterpret_cast<const double *>(tcp + 512)[row];
+          __syncwarp();
+          if (lane == 0) mbar_arrive(tc_empty(tc_e));
+          if (++tc_e == (uint32_t)kTcDepth) {
+            tc_e = 0;
+            tc_phase ^= 1u;
+          }
+          const float ntlo = -tau * (1.f - p.margin);
+          const float nthi = -tau * (1.f + p.margin);
+          const int trait = tt * kTileM + row;
+          const bool first = step == w.step_begin;
+          for (int c0 = 0; c0 < nc_item; c0 += 2) {
+            const int c = c0 + h;
+            const bool have = c < nc_item;  // an odd last chunk leaves warps 4-7 idle
+            bool ok = true;
+            if (first && have) ok = wait_bar_p(b_full(c), (b_bits >> c) & 1u, p, abort_addr, 6);
+            ok = ok && wait_bar_p(t_full(ps), ps_phase, p, abort_addr, 7);
+            if (!__all_sync(0xffffffffu, ok)) goto epi_done_scan;
+            tc_fence_after();
+            // two halves of this warp's SNPs: the second half is loaded while the
+            // first is tested, and the pair is released once it has landed
+            constexpr int kH = kFastSnps / 2;
+            uint32_t a0[kH], a1[kH], b0[kH], b1[kH];
+            const uint32_t taddr = lane_cols + ps * 256u;
+            const ChunkMeta &mc = smeta[have ? c : 0];
+            bool need_a = false, need_b = false;
+            if (have) {
+              tmem_ld_half(taddr, a0, a1);
+              tmem_wait_ld();
+              tmem_ld_half(taddr + (uint32_t)kH, b0, b1);
+              need_a = hit_fast_w<kH>(a0, a1, mc, off, ntlo);
+              tmem_wait_ld();
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(t_empty(ps));
+            ps ^= 1u;
+            if (ps == 0u) ps_phase ^= 1u;
+            if (have) {
+              need_b = hit_fast_w<kH>(b0, b1, mc, off + kH, ntlo);
+              if (__any_sync(0xffffffffu, need_a) &&
+                  !ev_submit(ev, a0, a1, need_a, mc, off, tau, cfac, trait, w.group, p, abort_addr,
+                             lane))
+                goto epi_done_scan;
+              if (__any_sync(0xffffffffu, need_b) &&
+                  !ev_submit(ev, b0, b1, need_b, mc, off + kH, tau, cfac, trait, w.group, p,
+                             abort_addr, lane))
+                goto epi_done_scan;
+            }
+          }
+          if (step == w.step_end - 1) {  // the chunks' metadata is no longer needed
+            __syncwarp();
+            if (lane == 0)
+              for (int c = 0; c < nc_item; ++c) mbar_arrive(b_empty(c));
+          }
+          if (++tt == g_ntt) tt = 0;
+        }
+        for (int c = 0; c < nc_item; ++c) b_bits ^= 1u << c;
+      }
+    epi_done_scan:
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) atomicAdd(ev.word, 1ull << 40);  // no more events from this warp
+    }
   } else {
     // epilogue warps
     const int q = warp & 3, h = warp >> 2;  // lane quarter, SNP group of the chunk
@@ -1564,7 +2190,7 @@ __global__ void __launch_bounds__(kScanThreads, 1) krux_scan_kernel(const __grid
   }
 
   __syncthreads();
-  if (warp == kMmaWarp) {
+  if (warp == R::kMma) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem_base) : "memory");
   }
@@ -1729,7 +2355,10 @@ size_t scan_smem_bytes2(int nc, int nA, size_t a_tile_bytes, size_t b_region, in
          8 * (size_t)(2 * nA + 2 * nc + 2 * kTmemSlots + 1 + 2 * kTcDepth) + 16;
 }
 
+bool fast_form_ok();
+
 cudaError_t scan_set_smem(size_t smem) {
+  (void)fast_form_ok();  // its one-time check happens here, before any graph capture
   cudaError_t e = cudaFuncSetAttribute(krux_scan_kernel<kFormScan>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -1748,11 +2377,31 @@ cudaError_t launch_scan_only(const ScanParams &p, int grid, size_t smem, cudaStr
     krux_scan_kernel<kFormMulti><<<grid, kScanThreads, smem, s>>>(p);
   else if (p.perm)
     krux_scan_kernel<kFormPerm><<<grid, kScanThreads, smem, s>>>(p);
-  else if (p.has_nan)
-    krux_scan_kernel<kFormNan><<<grid, kScanThreads, smem, s>>>(p);
+  else if (p.fast && fast_form_ok())
+    krux_scan_kernel<kFormScan><<<grid, kFastThreads, smem, s>>>(p);
   else
-    krux_scan_kernel<kFormScan><<<grid, kScanThreads, smem, s>>>(p);
+    // the general form: traits with NaN, dense output, cis window, provisional
+    // hits, unpaired chunks
+    krux_scan_kernel<kFormNan><<<grid, kScanThreads, smem, s>>>(p);
   return cudaGetLastError();
+}
+
+// The plain scan form moves registers between its warpgroups with setmaxnreg,
+// which is sound only if the kernel was built with exactly the launch register
+// count the split assumes (else an increase could wait for registers that were
+// never there): checked once, before its first launch.
+bool fast_form_ok() {
+  static std::atomic<int> ok{-1};
+  int v = ok.load(std::memory_order_acquire);
+  if (v < 0) {
+    cudaFuncAttributes a;
+    v = cudaFuncGetAttributes(&a, krux_scan_kernel<kFormScan>) == cudaSuccess &&
+                a.numRegs == kFastRegsLaunch && a.maxThreadsPerBlock >= kFastThreads
+            ? 1
+            : 0;
+    ok.store(v, std::memory_order_release);
+  }
+  return v == 1;
 }
 
 cudaError_t launch_scan(const ScanParams &p, int grid, size_t smem, cudaStream_t s) {
@@ -1762,17 +2411,19 @@ cudaError_t launch_scan(const ScanParams &p, int grid, size_t smem, cudaStream_t
 }
 
 cudaError_t finalize_prepare() {
-  static unsigned long long uploaded = 0;  // bit d: the table is on device d
+  // bit d: the table is on device d (callers on several host threads may race
+  // to upload it; the upload is idempotent, the mask update atomic)
+  static std::atomic<unsigned long long> uploaded{0};
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  if (dev < 64 && ((uploaded >> dev) & 1ull)) return cudaSuccess;
+  if (dev < 64 && ((uploaded.load(std::memory_order_acquire) >> dev) & 1ull)) return cudaSuccess;
   double t[kMaxN + 1];
   t[0] = 0.0;  // empty groups have D_i = 0 and contribute nothing
   for (int k = 1; k <= kMaxN; ++k) t[k] = 1.0 / (double)k;
   e = cudaMemcpyToSymbol(c_rcp, t, sizeof t);
   if (e != cudaSuccess) return e;
-  if (dev < 64) uploaded |= 1ull << dev;
+  if (dev < 64) uploaded.fetch_or(1ull << dev, std::memory_order_acq_rel);
   return cudaSuccess;
 }
 

@@ -76,3 +76,77 @@ def test_noalloc_rejects_sizes_beyond_its_limits():
     H = torch.empty(1, dtype=torch.float64, device="cuda")
     st, n = k.krux_scan_noalloc(e, g, 1e-3, out, H, H.clone())
     assert st == k.KRUX_EINVAL and n == 0
+
+
+def _noalloc_out(cap):
+    import torch
+    return (torch.empty((cap, 4), dtype=torch.int32, device="cuda"),
+            torch.empty(cap, dtype=torch.float64, device="cuda"),
+            torch.empty(cap, dtype=torch.float64, device="cuda"))
+
+
+def test_noalloc_at_its_largest_shape():
+    """T = 4096 traits and N = 256 samples (the documented maximum: the largest
+    scratch offsets, one resident SNP chunk per launch) against krux_scan."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_1307_3519_gb300 as k
+    x, g = _case(33, 4096, 300, 256, 0.0)
+    e, gd = torch.from_numpy(x).cuda(), torch.from_numpy(g).cuda()
+    kx = k.Krux(0)
+    rs = kx.krux_rank(e)
+    ref = kx.krux_scan(rs, gd, 1e-3, capacity=4096 * 300)
+    hits, H, P = _noalloc_out(20_000)
+    st, n = k.krux_scan_noalloc(e, gd, 1e-3, hits, H, P)
+    assert st == k.KRUX_OK and n == ref["n_hits"] and n > 0
+    a = _sorted(hits[:n], H[:n], P[:n])
+    b = _sorted(ref["hits"], ref["H"], ref["p"])
+    assert np.array_equal(a[0], b[0])
+    assert np.all(np.abs(a[1] - b[1]) <= 1e-6 * np.abs(b[1]) + 1e-10)
+    assert np.all(np.abs(a[2] - b[2]) <= 1e-6 * b[2])
+    kx.close()
+
+
+def test_noalloc_stored_hit_limit():
+    """More hits than the 262,144 records the entry point stores: KRUX_EOVERFLOW,
+    the exact total, and every stored record one of krux_scan's hits with the
+    same rank sums."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_1307_3519_gb300 as k
+    x, g = _case(34, 1024, 2000, 60, 0.0)
+    e, gd = torch.from_numpy(x).cuda(), torch.from_numpy(g).cuda()
+    kx = k.Krux(0)
+    rs = kx.krux_rank(e)
+    pth = 0.3
+    ref = kx.krux_scan(rs, gd, pth, capacity=1024 * 2000)
+    assert ref["n_hits"] > 262_144
+    hits, H, P = _noalloc_out(400_000)
+    st, n = k.krux_scan_noalloc(e, gd, pth, hits, H, P)
+    assert st == k.KRUX_EOVERFLOW and n == ref["n_hits"]
+    got = hits[:262_144].cpu().numpy().astype(np.int64)
+    want = ref["hits"].cpu().numpy().astype(np.int64)
+    key = lambda h: h[:, 0] * 10_000_000 + h[:, 1]
+    order = np.argsort(key(want))
+    pos = np.searchsorted(key(want)[order], key(got))
+    assert np.all(pos < want.shape[0])
+    match = want[order][pos]
+    assert np.array_equal(match, got)  # a real hit, same pair and rank sums
+    assert np.unique(key(got)).size == got.shape[0]  # no record twice
+    kx.close()
+
+
+def test_noalloc_rejects_missing_genotypes():
+    """One -1 code: the entry point scans complete genotypes only."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_1307_3519_gb300 as k
+    x, g = _case(35, 200, 500, 60, 0.0)
+    g[123, 7] = -1
+    e, gd = torch.from_numpy(x).cuda(), torch.from_numpy(g).cuda()
+    hits, H, P = _noalloc_out(1000)
+    st, n = k.krux_scan_noalloc(e, gd, 1e-3, hits, H, P)
+    assert st == k.KRUX_EUNSUPPORTED
