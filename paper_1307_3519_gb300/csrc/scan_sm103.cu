@@ -225,15 +225,6 @@ __device__ __forceinline__ void tmem_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// Scaled quadratic form minus the trait's bound: alpha (u + beta v)^2 + gamma v^2 + nt.
-__device__ __forceinline__ float kw_q(float u, float v, float al, float be, float ga, float nt) {
-  const float w = fmaf(be, v, u);
-  const float e = ga * v;
-  const float q = fmaf(e, v, nt);
-  const float f = al * w;
-  return fmaf(f, w, q);
-}
-
 // Same quadratic form without the bound; with permutation batches the df-1 SNPs
 // carry negated alpha, gamma so the sign of the result tells the df apart.
 __device__ __forceinline__ float kw_s(float u, float v, float al, float be, float ga) {
@@ -805,118 +796,7 @@ __device__ __forceinline__ unsigned int hit_event_cols(const uint32_t *dv, bool 
   return total;
 }
 
-// Hit event of the plain scan form, on the accumulator registers themselves
-// (static indexing only, so no local-memory copy): each lane classifies its
-// kEpiSnps pairs two at a time (at or above the upper band edge: hit; inside the
-// band: decided in FP64 from the exact sums, rare), then the warp appends the
-// records SNP column by SNP column, skipping columns without a hit in any lane
-// (lanes with a hit of the same SNP take consecutive records).  Records fill this
-// warp's staging segment (`wn` records already there); what does not fit goes
-// straight to the caller's list through the global counter.  Returns the number
-// of hits found.
-__device__ __forceinline__ unsigned int hit_event_reg(const uint32_t (&d0)[kEpiSnps],
-                                                      const uint32_t (&d1)[kEpiSnps],
-                                                      const ChunkMeta &m, int h, int trait,
-                                                      float ntlo, float nthi, double cfac,
-                                                      const GroupDesc &g, const ScanParams &p,
-                                                      unsigned int wn, int lane) {
-  const int jb = kEpiSnps * h;
-  const uint64_t *al = reinterpret_cast<const uint64_t *>(m.alpha + jb);
-  const uint64_t *be = reinterpret_cast<const uint64_t *>(m.beta + jb);
-  const uint64_t *ga = reinterpret_cast<const uint64_t *>(m.gamma + jb);
-  const uint64_t lo2c = pk2(__float_as_uint(ntlo), __float_as_uint(ntlo));
-  const uint64_t hi2c = pk2(__float_as_uint(nthi), __float_as_uint(nthi));
-  uint32_t below = 0, not_sure = 0;  // sign bits of s - tau(1 -/+ margin)
-#pragma unroll
-  for (int j = 0; j < kEpiSnps; j += 2) {
-    const uint64_t u2 = pk2(d0[j], d0[j + 1]);
-    const uint64_t v2 = pk2(d1[j], d1[j + 1]);
-    const uint64_t w2 = ffma2(be[j / 2], v2, u2);
-    const uint64_t e2 = fmul2(ga[j / 2], v2);
-    const uint64_t s2 = ffma2(fmul2(al[j / 2], w2), w2, fmul2(e2, v2));
-    uint32_t la, lb, ha, hb;
-    upk2(fadd2(s2, lo2c), la, lb);
-    upk2(fadd2(s2, hi2c), ha, hb);
-    below |= ((la >> 31) | ((lb >> 31) << 1)) << j;
-    not_sure |= ((ha >> 31) | ((hb >> 31) << 1)) << j;
-  }
-  // padding SNPs and degenerate traits carry zero coefficients / an infinite bound
-  // and are never candidates
-  const uint32_t cand = ~below & ((1u << kEpiSnps) - 1u);
-  uint32_t hm = cand & ~not_sure;
-  uint32_t band = cand & not_sure;
-  while (band) {  // inside the band: p < P_c decided in FP64 (rare)
-    const int j = __ffs(band) - 1;
-    band &= band - 1u;
-    float u = 0.f, v = 0.f;
-#pragma unroll
-    for (int jj = 0; jj < kEpiSnps; ++jj)
-      if (jj == j) {
-        u = __uint_as_float(d0[jj]);
-        v = __uint_as_float(d1[jj]);
-      }
-    if (decide64(u, v, m.n[0][jb + j], m.n[1][jb + j], m.n[2][jb + j], m.df[jb + j], cfac,
-                 p.pthresh))
-      hm |= 1u << j;
-  }
-  const unsigned int total = __reduce_add_sync(0xffffffffu, (unsigned int)__popc(hm));
-  if (total == 0u) return 0u;
-  const unsigned int cap = (unsigned int)p.seg_cap;
-  const unsigned int sbase = wn;
-  const unsigned int over_from = sbase > cap ? sbase : cap;  // first index beyond the segment
-  const unsigned int n_over = sbase + total > over_from ? sbase + total - over_from : 0u;
-  unsigned long long gbase = 0;
-  if (lane == 0 && n_over > 0) gbase = atomicAdd(g.counter, (unsigned long long)n_over);
-  gbase = __shfl_sync(0xffffffffu, gbase, 0);
-  const size_t seg0 = ((size_t)blockIdx.x * kEpiWarps + (threadIdx.x >> 5)) * cap;
-  const uint32_t below_me = (1u << lane) - 1u;
-  const uint16_t gid = (uint16_t)g.group_id;
-  const uint32_t cols = __reduce_or_sync(0xffffffffu, hm);
-  unsigned int run = sbase;  // index of the next record (same in every lane)
-#pragma unroll
-  for (int j = 0; j < kEpiSnps; ++j) {
-    if (((cols >> j) & 1u) == 0u) continue;  // warp-uniform
-    const bool mine = (hm >> j) & 1u;
-    const uint32_t bal = __ballot_sync(0xffffffffu, mine);
-    if (mine) {
-      const unsigned int idx = run + (unsigned int)__popc(bal & below_me);
-      krux_hit r;
-      r.trait = (uint32_t)trait;
-      r.snp = (uint32_t)m.snp[jb + j];
-      r.d0 = (int32_t)__uint_as_float(d0[j]);
-      r.d1 = (int32_t)__uint_as_float(d1[j]);
-      HitAux x;
-      x.n0 = m.n[0][jb + j];
-      x.n1 = m.n[1][jb + j];
-      x.n2 = m.n[2][jb + j];
-      x.group = gid;
-      if (idx < cap) {
-        st_hit(p.seg_hits + seg0 + idx, r);
-        st_aux(p.seg_aux + seg0 + idx, x);
-      } else {
-        const unsigned long long gi = gbase + (idx - over_from);
-        if (gi < (unsigned long long)g.capacity) {
-          st_hit(g.hits + gi, r);
-          st_aux(g.aux + gi, x);
-        }
-      }
-    }
-    run += (unsigned int)__popc(bal);
-  }
-  return total;
-}
-
 // ---- the plain scan form: one warp per chunk of an accumulator pair ----------
-// 32 consecutive fp32 columns of this warp's 32 TMEM lanes.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t *r) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
-      "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr)
-      : "memory");
-}
-
 // 16 consecutive fp32 columns of this warp's 32 TMEM lanes.
 __device__ __forceinline__ void tmem_ld16p(uint32_t taddr, uint32_t *r) {
   asm volatile(
@@ -1890,12 +1770,44 @@ __global__ void __launch_bounds__(ScanRoles<kForm>::kThreads, 1)
       const uint32_t lane_cols =
           tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(128 * h + off);
       uint32_t ps = 0, ps_phase = 0, b_bits = 0, tc_e = 0, tc_phase = 0;
-      unsigned int wn = 0;  // hits this warp has appended to its staging region
+      constexpr int kH = kFastSnps / 2;
+      // one accumulator pair: wait for it, load this warp's two halves (the second
+      // while the first is tested), release it, test the second half, hand any
+      // candidate half-block to the event warps; false if a wait gave up
+      auto pair_slot = [&](uint32_t ps, uint32_t phase, const ChunkMeta &mc, float tau,
+                           double cfac, float ntlo, int trait, int group) -> bool {
+        if (!__all_sync(0xffffffffu, wait_bar_p(t_full(ps), phase, p, abort_addr, 7))) return false;
+        tc_fence_after();
+        uint32_t a0[kH], a1[kH], b0[kH], b1[kH];
+        const uint32_t taddr = lane_cols + ps * 256u;
+        tmem_ld_half(taddr, a0, a1);
+        tmem_wait_ld();
+        tmem_ld_half(taddr + (uint32_t)kH, b0, b1);
+        const bool need_a = hit_fast_w<kH>(a0, a1, mc, off, ntlo);
+        tmem_wait_ld();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(t_empty(ps));
+        const bool need_b = hit_fast_w<kH>(b0, b1, mc, off + kH, ntlo);
+        if (__any_sync(0xffffffffu, need_a) &&
+            !ev_submit(ev, a0, a1, need_a, mc, off, tau, cfac, trait, group, p, abort_addr, lane))
+          return false;
+        if (__any_sync(0xffffffffu, need_b) &&
+            !ev_submit(ev, b0, b1, need_b, mc, off + kH, tau, cfac, trait, group, p, abort_addr, lane))
+          return false;
+        return true;
+      };
       for (int it = blockIdx.x; it < p.n_items; it += gridDim.x) {
         const WorkItem w = p.items[it];
         const GroupDesc &g = p.groups[w.group];
         const int g_nc = g.nc, g_ntt = g.n_ttiles;
         const int nc_item = min(g_nc, g.nchunks - w.btile * g_nc);
+        // this warp's chunks of the B tile (h and 2 + h) must have landed
+        {
+          bool ok = true;
+          for (int c = h; c < nc_item; c += 2) ok = ok && wait_bar_p(b_full(c), (b_bits >> c) & 1u, p, abort_addr, 6);
+          if (!__all_sync(0xffffffffu, ok)) goto epi_done_scan;
+        }
         int tt = w.step_begin % g_ntt;  // trait tile of the step
         for (int step = w.step_begin; step < w.step_end; ++step) {
           // this step's trait constants, staged by the producer (copied out at once)
@@ -1911,55 +1823,31 @@ __global__ void __launch_bounds__(ScanRoles<kForm>::kThreads, 1)
             tc_phase ^= 1u;
           }
           const float ntlo = -tau * (1.f - p.margin);
-          const float nthi = -tau * (1.f + p.margin);
           const int trait = tt * kTileM + row;
-          const bool first = step == w.step_begin;
-          for (int c0 = 0; c0 < nc_item; c0 += 2) {
-            const int c = c0 + h;
-            const bool have = c < nc_item;  // an odd last chunk leaves warps 4-7 idle
-            bool ok = true;
-            if (first && have) ok = wait_bar_p(b_full(c), (b_bits >> c) & 1u, p, abort_addr, 6);
-            ok = ok && wait_bar_p(t_full(ps), ps_phase, p, abort_addr, 7);
-            if (!__all_sync(0xffffffffu, ok)) goto epi_done_scan;
-            tc_fence_after();
-            // two halves of this warp's SNPs: the second half is loaded while the
-            // first is tested, and the pair is released once it has landed
-            constexpr int kH = kFastSnps / 2;
-            uint32_t a0[kH], a1[kH], b0[kH], b1[kH];
-            const uint32_t taddr = lane_cols + ps * 256u;
-            const ChunkMeta &mc = smeta[have ? c : 0];
-            bool need_a = false, need_b = false;
-            if (have) {
-              tmem_ld_half(taddr, a0, a1);
-              tmem_wait_ld();
-              tmem_ld_half(taddr + (uint32_t)kH, b0, b1);
-              need_a = hit_fast_w<kH>(a0, a1, mc, off, ntlo);
-              tmem_wait_ld();
+          {
+            for (int c0 = 0; c0 < nc_item; c0 += 2) {
+              const int c = c0 + h;
+              if (c < nc_item) {
+                if (!pair_slot(ps, ps_phase, smeta[c], tau, cfac, ntlo, trait, w.group))
+                  goto epi_done_scan;
+              } else {  // an odd last chunk leaves warps 8-15 idle: release only
+                if (!__all_sync(0xffffffffu, wait_bar_p(t_full(ps), ps_phase, p, abort_addr, 7)))
+                  goto epi_done_scan;
+                tc_fence_after();
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(t_empty(ps));
+              }
+              ps ^= 1u;
+              if (ps == 0u) ps_phase ^= 1u;
             }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(t_empty(ps));
-            ps ^= 1u;
-            if (ps == 0u) ps_phase ^= 1u;
-            if (have) {
-              need_b = hit_fast_w<kH>(b0, b1, mc, off + kH, ntlo);
-              if (__any_sync(0xffffffffu, need_a) &&
-                  !ev_submit(ev, a0, a1, need_a, mc, off, tau, cfac, trait, w.group, p, abort_addr,
-                             lane))
-                goto epi_done_scan;
-              if (__any_sync(0xffffffffu, need_b) &&
-                  !ev_submit(ev, b0, b1, need_b, mc, off + kH, tau, cfac, trait, w.group, p,
-                             abort_addr, lane))
-                goto epi_done_scan;
-            }
-          }
-          if (step == w.step_end - 1) {  // the chunks' metadata is no longer needed
-            __syncwarp();
-            if (lane == 0)
-              for (int c = 0; c < nc_item; ++c) mbar_arrive(b_empty(c));
           }
           if (++tt == g_ntt) tt = 0;
         }
+        // the chunks' metadata is no longer needed
+        __syncwarp();
+        if (lane == 0)
+          for (int c = 0; c < nc_item; ++c) mbar_arrive(b_empty(c));
         for (int c = 0; c < nc_item; ++c) b_bits ^= 1u << c;
       }
     epi_done_scan:
