@@ -6,9 +6,13 @@ the STAGE data): rank transform, genotype packing, fused tcgen05 scan with
 threshold and hit compaction, FP64 finalisation of the hit list.  Inputs are
 resident in device memory; L2 is flushed between steps (outside the timed
 events).  The plain two-pass form (library GEMM to memory, then a separate
-epilogue) is timed beside it, the end-to-end number goes through the public
-host API with pinned host buffers, and the FP64 CPU oracle is timed on a
-bounded sample of the same workload on the host cores.
+epilogue) is timed beside it; the end-to-end number goes through the C ABI's
+host-memory entry point (krux_scan_host, page-locked buffers, the copies inside
+the timed region); the FP64 CPU oracle is timed on a bounded sample of the same
+workload on the host cores.  The roofline carries both bounds of the scan kernel
+(FP16 tensor rate, epilogue issue rate) and its fraction of the slower one.  At
+N=1 the line also carries the missing-value, permutation-null and multi-cohort
+workloads at full size ("missing", "permute", "cohorts"; --no-extra skips them).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fused|reference]
   python bench.py --scan-only [--traits T] [--snps S] [--data hwe|paper] [--reps R] [--perms P]
@@ -40,13 +44,30 @@ WORKLOAD = ("paper-scale fused scan: N=102 samples, T=20000 traits, S=500000 SNP
             "1-SD shifts on ~1% of pairs; hits at p<1e-5")
 
 
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one krux_scan_kernel
-# launch on the paper-scale workload, from one ncu capture, with the git blob hash of
-# the kernel source it was taken on: reported only while that source is unchanged.
-# ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum on "bench.py --scan-only
-# --traits 20000 --snps 500000 --data paper --tile 1,4,2,0" (the benchmark's workload
-# and autotuned shape): 241.27 MB read + 78.10 MB written in one launch (1 pass).
-SCAN_TRAFFIC = {"blob": "02a01e09e5245b5f6c2551f8441774ba6e351d26", "bytes": 319.37e6}
+# Per-launch counters of krux_scan_kernel on the benchmark's workload, each with the
+# git blob hash of the kernel source it was taken on: reported only while that
+# source is unchanged (else null).  Commands (committed files only):
+#   traffic: ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none
+#            -k regex:krux_scan_kernel -s 1 -c 1 python bench.py --scan-only --traits 20000
+#            --snps 500000 --data paper --tile 1,4,2,0 --reps 2   (1 pass)
+#   issue:   ncu --metrics smsp__inst_executed.sum,sm__inst_executed_pipe_fmaheavy.sum,
+#            sm__inst_executed_pipe_fmalite.sum,sm__inst_executed_pipe_alu.sum --clock-control none
+#            -k regex:krux_scan_kernel -s 1 -c 1 python bench.py --scan-only --traits 20000
+#            --snps 100000 --data paper --tile 1,4,2,0 --reps 2
+#            (warp instructions x 32 lanes / pairs = lane issue slots per pair)
+# Measured on the kernel below: 241.51 MB read + 73.37 MB written per 500k-SNP launch;
+# 667.18 M warp instructions (565.75 M on the FMA-heavy, FMA-lite and ALU pipes) per
+# 100k-SNP launch of 2x10^9 pairs.
+SCAN_TRAFFIC = {"blob": "f7279c3fe8798c4d2df657ddd53329b7e4056ee5", "bytes": 314.88e6}
+SCAN_ISSUE = {"blob": "f7279c3fe8798c4d2df657ddd53329b7e4056ee5", "slots_per_pair": 10.68,
+              "fp32_int_slots_per_pair": 9.05,
+              "workload": "planted 20000 x 100000 x 102 (0.19% of pairs are hits)"}
+# Epilogue issue slots per pair by the operation count of the fused test: one add
+# for D_2, three multiplies by 1/n_i, one multiply and two fused multiply-adds for
+# Q, one select of the threshold by df, one compare/branch, plus the amortised
+# TMEM load: about 10 lane slots.  The epilogue bound is SMs x 128 lanes x SM clock
+# / 10 pairs per second.
+EPILOGUE_SLOTS_PER_PAIR = 10.0
 
 
 def kernel_blob():
@@ -174,9 +195,11 @@ def run_reference(args):
     oracle.build()
     d = synth.config(2)
     T, S = d["expr"].shape[0], d["geno"].shape[0]
-    # each step: the oracle on a bounded sample (4 traits x all SNPs)
+    # each step: the oracle on a bounded sample, one random trait per oracle thread
+    # (the oracle runs one trait per thread) x all SNPs
+    cores = oracle.num_threads()
     rng = np.random.default_rng(5)
-    nt = 4
+    nt = cores
     times = []
     for i in range(args.warmup + args.steps):
         traits = rng.choice(T, nt, replace=False)
@@ -192,11 +215,45 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "T": T, "S": S, "N": d["N"], "pthresh": d["pthresh"]},
-            "cpu_baseline": {"value": v, "unit": "pairs/s", "cores": oracle.num_threads(),
-                             "kind": "oracle",
-                             "sample": f"{nt} random traits x all {S} SNPs per step (FP64 per-pair oracle)"},
+            "cpu_baseline": {"value": v, "unit": "pairs/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{nt} random traits (one per oracle thread) x all {S} SNPs "
+                                       f"per step (FP64 per-pair oracle)"},
             "e2e": {"value": v, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def sm_count_and_clock(dev_index, clocks):
+    """SM count of the device and the SM clock (MHz) for the issue-rate bound: the
+    median sampled under load, else the maximum nvidia-smi reports, else 2070."""
+    import torch
+    sms = torch.cuda.get_device_properties(dev_index).multi_processor_count
+    mhz = clocks.get("sm_mhz") or clocks.get("sm_max_mhz") or 2070.0
+    return sms, float(mhz)
+
+
+def roofline_bounds(ms, pairs, N, sms, mhz, pk):
+    """Both bounds of the fused scan for `pairs` pairs at N samples in `ms`
+    milliseconds: the FP16 tensor bound (4N algorithmic flop per pair against the
+    measured dense rate) and the epilogue issue bound (EPILOGUE_SLOTS_PER_PAIR lane
+    slots per pair against SMs x 128 lanes x SM clock).  The binding bound is the
+    slower one; frac is the achieved rate over it."""
+    tensor_peak = float(pk["bf16_tflops"])  # FP16 dense rate = BF16 rate (nominal ratio 1)
+    flops = 4.0 * N * pairs
+    t_achieved = flops / (ms / 1e3) / 1e12
+    tensor_pairs = tensor_peak * 1e12 / (4.0 * N)
+    slot_peak = sms * 128 * mhz * 1e6  # lane issue slots per second
+    e_achieved = EPILOGUE_SLOTS_PER_PAIR * pairs / (ms / 1e3)
+    epi_pairs = slot_peak / EPILOGUE_SLOTS_PER_PAIR
+    rate = pairs / (ms / 1e3)
+    tensor = {"achieved": t_achieved, "peak": tensor_peak, "unit": "TFLOP/s",
+              "frac": t_achieved / tensor_peak, "peak_pairs_per_s": tensor_pairs,
+              "flops_per_launch": flops}
+    epi = {"achieved": e_achieved / 1e12, "peak": slot_peak / 1e12, "unit": "Tslot/s",
+           "frac": e_achieved / slot_peak, "peak_pairs_per_s": epi_pairs,
+           "slots_per_pair": EPILOGUE_SLOTS_PER_PAIR, "sms": sms, "sm_mhz": mhz}
+    bound = "tensor" if tensor_pairs <= epi_pairs else "alu"
+    b = tensor if bound == "tensor" else epi
+    return bound, b, {"tensor": tensor, "epilogue": epi}, rate / min(tensor_pairs, epi_pairs)
 
 
 def run_fused(args):
@@ -302,35 +359,47 @@ def run_fused(args):
                   "what": "pack + fused scan + compaction + FP64 finalisation, one graph replay"}
 
     pk, pk_kind = peaks()
-    flops = 4.0 * N * pairs  # algorithmic: two indicator columns x N samples x multiply-add
+    clocks = clk.summary()
+    sms, mhz = sm_count_and_clock(local, clocks)
     ms_scan = float(np.mean(scan_ms))
-    achieved = flops / (ms_scan / 1e3) / 1e12
-    peak = float(pk["bf16_tflops"])  # FP16 dense rate equals the BF16 rate (nominal ratio 1)
-    roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak,
-            "traffic": (SCAN_TRAFFIC["bytes"] if SCAN_TRAFFIC and SCAN_TRAFFIC["blob"] == kernel_blob()
-                        else None),
-            "kernel": "krux_scan_kernel", "peak_kind": f"{pk_kind} bf16 burst (fp16 = bf16 x 1.0)",
-            "ms_per_launch": ms_scan, "flops_per_launch": flops}
+    bound, b, bounds, frac = roofline_bounds(ms_scan, pairs, N, sms, mhz, pk)
+    traffic = (SCAN_TRAFFIC["bytes"] if SCAN_TRAFFIC["blob"] == kernel_blob() else None)
+    issue = ({k2: v for k2, v in SCAN_ISSUE.items() if k2 != "blob"}
+             if SCAN_ISSUE["blob"] == kernel_blob() and SCAN_ISSUE["slots_per_pair"] else None)
+    roof = {"bound": bound, "achieved": b["achieved"], "peak": b["peak"], "unit": b["unit"],
+            "frac": frac, "traffic": traffic, "kernel": "krux_scan_kernel",
+            "peak_kind": f"{pk_kind} bf16 burst (fp16 = bf16 x 1.0) / SMs x 128 lanes x median SM clock",
+            "ms_per_launch": ms_scan, "pairs_per_launch": pairs, "bounds": bounds,
+            "measured_issue": issue}
 
-    # end to end through the public host API (pinned host buffers, H2D + D2H inside)
+    # end to end through the C ABI on host memory (krux_scan_host: pinned host
+    # inputs and outputs, the library's H2D copies, rank, scan and D2H copies inside)
     e_h = torch.from_numpy(d["expr"]).pin_memory()
     g_h = torch.from_numpy(d["geno"]).pin_memory()
+    outs_h = (torch.empty((cap, 4), dtype=torch.int32).pin_memory(),
+              torch.empty(cap, dtype=torch.float64).pin_memory(),
+              torch.empty(cap, dtype=torch.float64).pin_memory())
     esteps = max(1, min(args.steps, 5))
     kx.set_profiling(False)
-    for _ in range(max(2, args.warmup)):  # warm-up (also fills the pinned-block cache)
-        r = kx.scan_pinned(e_h, g_h, pth, cap)
+    for _ in range(max(2, args.warmup)):
+        r = kx.krux_scan_host(e_h, g_h, pth, cap, out=outs_h)
     torch.cuda.synchronize()
     barrier(world)
     t0 = time.perf_counter()
     d2h = 0
     for _ in range(esteps):
-        r = kx.scan_pinned(e_h, g_h, pth, cap)
-        d2h += r["d2h_bytes"]
+        r = kx.krux_scan_host(e_h, g_h, pth, cap, out=outs_h)
+        d2h += r["d2h_bytes"] + 8
     e2e_s = max_over_ranks(time.perf_counter() - t0, world)  # whole job: the slowest rank
     e2e = {"value": pairs * world * esteps / e2e_s, "unit": "pairs/s",
            "h2d_bytes_per_step": int(e_h.numel() * 4 + g_h.numel()),
-           "d2h_bytes_per_step": int(d2h // esteps)}
+           "d2h_bytes_per_step": int(d2h // esteps), "steps": esteps, "hits": r["n_hits"],
+           "call": "krux_scan_host (C ABI, page-locked host buffers)"}
+    kx.set_profiling(True)
+
+    extra = {}
+    if world == 1 and not args.no_extra:
+        extra = extra_workloads(kx, flush, stream, pk, sms, mhz)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:  # the oracle baseline: N = 1 only
@@ -342,7 +411,6 @@ def run_fused(args):
                          f"({info['seconds']:.1f} s of FP64 per-pair oracle work)"}
 
     if rank == 0:
-        c = clk.summary()
         line = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f16",
@@ -352,17 +420,146 @@ def run_fused(args):
                            "tile_shape": dict(zip(("layout", "nc", "nA", "ka"), tile_shape)),
                            "parallelism": f"snp-shards x{world}"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": c, "hits": n_hits,
+                "clocks": clocks, "hits": n_hits,
                 "graph": graph_line,
                 "plain": {"value": pvalue, "unit": "pairs/s", "ms_per_step": float(np.mean(ptimes)),
                           "steps": psteps, "fused_speedup": value / world / pvalue, "hits": pn},
                 "breakdown_ms": {k2: float(np.mean([p[1][k2] for p in profs]))
                                  for k2 in ("ms_pack", "ms_scan", "ms_finalize")}
                 | {"ms_rank": float(np.mean([p[0]["ms_rank"] for p in profs]))}}
+        line.update(extra)
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def extra_workloads(kx, flush, stream, pk, sms, mhz, steps=5, warmup=3):
+    """The other three workloads at full size, each step one whole call on
+    resident device inputs (rank transform included), L2 flushed between steps
+    outside the timed events, CUDA events on the launching stream:
+      missing  -- N=102, T=5,000, S=100,000; 10% of SNPs with one of 200 missing
+                  patterns, 1% NaN expression; hits at p<1e-4
+      permute  -- N=102, T=20,000, S=200,000, P=16 permutations in one call (min p
+                  per permutation and trait, FDR histogram of 40 bins, real hits
+                  at p<1e-5); (1 + P) T S pairs per step
+      cohorts  -- 8 cohorts, N in {48,...,500}, T=15,000, S=300,000 each, one
+                  grouped launch; each cohort also scanned alone for its own
+                  roofline (4 N_c flop per pair)."""
+    import torch
+    import synth
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        ts, outs = [], []
+        for _ in range(steps):
+            flush.zero_()
+            ev0.record(stream)
+            out = fn()
+            ev1.record(stream)
+            ev1.synchronize()
+            ts.append(ev0.elapsed_time(ev1))
+            outs.append(out)
+        return float(np.mean(ts)), outs
+
+    out = {}
+    # missing values
+    d = synth.config(3)
+    e, g = dev(d["expr"]), dev(d["geno"])
+
+    def step_missing():
+        rs = kx.krux_rank(e)
+        pr = kx.profile()
+        r = kx.krux_scan(rs, g, d["pthresh"], capacity=10_000_000)
+        ps = kx.profile()
+        rs.free()
+        return r["n_hits"], pr, ps
+    ms, outs = timed(step_missing)
+    pairs = d["T"] * d["S"]
+    ms_scan = float(np.mean([o[2]["ms_scan"] for o in outs]))
+    _, _, _, frac = roofline_bounds(ms_scan, pairs, d["N"], sms, mhz, pk)
+    out["missing"] = {"value": pairs / (ms / 1e3), "unit": "pairs/s", "ms_per_step": ms, "steps": steps,
+                      "warmup": warmup, "hits": outs[-1][0], "T": d["T"], "S": d["S"], "N": d["N"],
+                      "pthresh": d["pthresh"],
+                      "gpu_launches": int(np.mean([o[1]["launches"] + o[2]["launches"] for o in outs])),
+                      "breakdown_ms": {"ms_rank": float(np.mean([o[1]["ms_rank"] for o in outs])),
+                                       "ms_pack": float(np.mean([o[2]["ms_pack"] for o in outs])),
+                                       "ms_scan": ms_scan,
+                                       "ms_finalize": float(np.mean([o[2]["ms_finalize"] for o in outs]))},
+                      "scan_kernel_roofline_frac": frac,
+                      "what": "krux_rank + krux_scan: missing-pattern groups re-ranked per group"}
+    del e, g, d
+    # permutation null
+    d = synth.config(4)
+    e, g, pm = dev(d["expr"]), dev(d["geno"]), dev(d["perms"])
+    P = int(d["perms"].shape[0])
+
+    def step_perm():
+        rs = kx.krux_rank(e)
+        pr = kx.profile()
+        r = kx.krux_permute(rs, g, pm, d["pthresh"], capacity=50_000_000, fdr_bins=40, fdr_bin_width=0.1)
+        ps = kx.profile()
+        rs.free()
+        return r["n_hits"], pr, ps
+    ms, outs = timed(step_perm)
+    pairs = (1 + P) * d["T"] * d["S"]
+    ms_scan = float(np.mean([o[2]["ms_scan"] for o in outs]))
+    _, _, _, frac = roofline_bounds(ms_scan, pairs, d["N"], sms, mhz, pk)
+    out["permute"] = {"value": pairs / (ms / 1e3), "unit": "pairs/s", "ms_per_step": ms, "steps": steps,
+                      "warmup": warmup, "hits": outs[-1][0], "P": P, "T": d["T"], "S": d["S"],
+                      "N": d["N"], "pthresh": d["pthresh"],
+                      "gpu_launches": int(np.mean([o[1]["launches"] + o[2]["launches"] for o in outs])),
+                      "ms_scan": ms_scan, "scan_kernel_roofline_frac": frac,
+                      "what": "krux_rank + krux_permute (P=16, min p per permutation and trait, "
+                              "FDR histogram, real hits); pairs = (1+P) T S"}
+    del e, g, pm, d
+    # cohorts
+    d = synth.config(5)
+    cin = [(dev(c["expr"]), dev(c["geno"]), int(c["expr"].shape[1])) for c in d["cohorts"]]
+
+    def step_cohorts():
+        rss = [kx.krux_rank(ce) for ce, _, _ in cin]
+        cohorts = [dict(rs=rs, geno=cg, capacity=5_000_000) for rs, (_, cg, _) in zip(rss, cin)]
+        r = kx.krux_scan_grouped(cohorts, d["pthresh"])
+        ps = kx.profile()
+        for rs in rss:
+            rs.free()
+        return sum(x["n_hits"] for x in r), ps
+    ms, outs = timed(step_cohorts)
+    tot_pairs = sum(ce.shape[0] * cg.shape[0] for ce, cg, _ in cin)
+    ms_grouped = float(np.mean([o[1]["ms_scan"] for o in outs]))
+    per, bound_ms = [], 0.0
+    for ce, cg, n in cin:
+        rs = kx.krux_rank(ce)
+        kx.krux_scan(rs, cg, d["pthresh"], capacity=5_000_000)
+        t_ = []
+        for _ in range(3):
+            flush.zero_()
+            kx.krux_scan(rs, cg, d["pthresh"], capacity=5_000_000)
+            t_.append(kx.profile()["ms_scan"])
+        rs.free()
+        cp = ce.shape[0] * cg.shape[0]
+        mc = float(np.mean(t_))
+        bnd, _, bnds, fr = roofline_bounds(mc, cp, n, sms, mhz, pk)
+        bound_ms += cp / min(bnds["tensor"]["peak_pairs_per_s"], bnds["epilogue"]["peak_pairs_per_s"]) * 1e3
+        per.append({"N": n, "ms_scan_alone": mc, "pairs_per_s": cp / (mc / 1e3), "bound": bnd,
+                    "frac": fr, "tensor_frac": bnds["tensor"]["frac"]})
+    out["cohorts"] = {"value": tot_pairs / (ms / 1e3), "unit": "pairs/s", "ms_per_step": ms, "steps": steps,
+                      "warmup": warmup, "hits": outs[-1][0], "n_cohorts": len(cin),
+                      "T": int(cin[0][0].shape[0]), "S": int(cin[0][1].shape[0]),
+                      "N": [n for _, _, n in cin], "pthresh": d["pthresh"],
+                      "ms_scan_grouped": ms_grouped, "grouped_roofline_frac": bound_ms / ms_grouped,
+                      "per_cohort": per,
+                      "what": "8 x krux_rank + one krux_scan_grouped launch; per-cohort rows: the "
+                              "cohort scanned alone, frac against its slower bound (4 N_c flop "
+                              "per pair on the tensor pipe, 10 issue slots per pair)"}
+    del cin, d
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_scan_only(args):
@@ -508,6 +705,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="fused", choices=["fused", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="leave out the missing-value, permutation and cohort workloads")
     ap.add_argument("--scan-only", action="store_true",
                     help="profiling driver: only the fused scan, --reps calls, text output")
     ap.add_argument("--traits", type=int, default=20000)

@@ -130,6 +130,27 @@ krux_status krux_scan(krux_ctx *ctx, const krux_rankset *rs, const int8_t *geno,
                       int64_t ldg, const krux_opts *opts, krux_hit *hits, double *hit_H,
                       double *hit_p, int64_t *n_hits, void *stream);
 
+/* End-to-end scan from host memory (the paper's whole analysis of section
+ * "Implementation": input matrices in, significant pairs out): copies the
+ * inputs to the device, runs krux_rank and krux_scan there, and copies the hit
+ * list back.
+ *   expr : HOST float32 [T][lde], as krux_rank (NaN = missing).
+ *   geno : HOST int8 [S][ldg], as krux_scan.
+ *   hits, hit_H, hit_p : HOST outputs of opts->hit_capacity entries; *n_hits as
+ *          in krux_scan (exact count; KRUX_EOVERFLOW when above the capacity,
+ *          with the first hit_capacity records copied).
+ * Page-locked host buffers (cudaHostAlloc or cudaHostRegister) copy at the
+ * link's rate; pageable ones work but copy through a bounce buffer.  Each input
+ * is one cudaMemcpyAsync (cudaMemcpy2DAsync when its leading dimension exceeds
+ * N) into device memory the context keeps between calls; the outputs are three
+ * copies of min(*n_hits, capacity) records.  opts->dense_H / dense_p must be
+ * NULL (dense output is a device-side option of krux_scan).  The call
+ * synchronises `stream` before returning. */
+krux_status krux_scan_host(krux_ctx *ctx, const float *expr, int T, int N, int64_t lde,
+                           const int8_t *geno, int64_t S, int64_t ldg, const krux_opts *opts,
+                           krux_hit *hits, double *hit_H, double *hit_p, int64_t *n_hits,
+                           void *stream);
+
 /* Plain two-pass form of the same scan, kept as the measured comparison point:
  * a library FP16 GEMM writes the T x 2S rank-sum matrix (in SNP slices) to device
  * memory, then a separate epilogue kernel reads it back.  Same arguments and

@@ -5,7 +5,7 @@ The compute path is the CUDA library built from ``csrc/`` (C ABI in
 and back.  There is no CPU fallback: if the library is missing the import
 fails.  Function names follow the C ABI (``krux_rank``, ``krux_scan``,
 ``krux_scan_plain``, ``krux_permute``, ``krux_scan_grouped``); the ``Krux``
-class wraps them with allocation of outputs, and ``Krux.scan_host`` is the
+class wraps them with allocation of outputs, and ``Krux.krux_scan_host`` is the
 end-to-end call from host arrays.
 """
 from __future__ import annotations
@@ -25,7 +25,7 @@ STATUS_NAMES = ["KRUX_OK", "KRUX_EINVAL", "KRUX_ENOMEM", "KRUX_ECUDA", "KRUX_EOV
 
 # Every entry point declared in include/krux.h.
 EXPORTS = ["krux_create", "krux_destroy", "krux_status_string", "krux_last_error", "krux_rank",
-           "krux_rankset_free", "krux_rankset_export", "krux_scan", "krux_scan_plain",
+           "krux_rankset_free", "krux_rankset_export", "krux_scan", "krux_scan_host", "krux_scan_plain",
            "krux_permute", "krux_scan_grouped", "krux_make_perms", "krux_set_profiling",
            "krux_get_profile", "krux_set_wait_limit", "krux_set_tuning", "krux_scan_noalloc", "krux_debug_plan",
            "krux_autotune", "krux_graph_scan", "krux_graph_permute", "krux_graph_grouped",
@@ -83,6 +83,8 @@ def load_library(path=LIB_PATH):
         "krux_rankset_export": ([P, P, P, P, P, P], I),
         "krux_scan": ([P, P, P, I64, I64, ctypes.POINTER(Opts), P, P, P, ctypes.POINTER(I64), P], I),
         "krux_scan_plain": ([P, P, P, I64, I64, ctypes.POINTER(Opts), P, P, P, ctypes.POINTER(I64), P], I),
+        "krux_scan_host": ([P, P, I, I, I64, P, I64, I64, ctypes.POINTER(Opts), P, P, P,
+                            ctypes.POINTER(I64), P], I),
         "krux_permute": ([P, P, P, I64, I64, P, I, ctypes.POINTER(Opts), P, P, P, P,
                           ctypes.POINTER(I64), P, I, D, P], I),
         "krux_scan_grouped": ([P, ctypes.POINTER(Cohort), I, ctypes.POINTER(Opts), P], I),
@@ -120,6 +122,13 @@ def _ptr(t):
     return None if t is None else ctypes.c_void_p(t.data_ptr())
 
 
+def _ld(t):
+    """Row stride (elements) of a 2-D tensor as a leading dimension: a one-row
+    matrix may carry any stride for its single row (numpy gives 0 to an inserted
+    axis), so its leading dimension is its row length."""
+    return t.stride(0) if t.shape[0] > 1 else t.shape[1]
+
+
 def _stream(stream=None):
     import torch
     s = stream if stream is not None else torch.cuda.current_stream()
@@ -148,8 +157,8 @@ def krux_scan_noalloc(expr, geno, pthresh, hits, hit_H, hit_p, stream=None):
         raise ValueError("krux_scan_noalloc: all tensors must be on one device")
     n = ctypes.c_int64()
     st = load_library().krux_scan_noalloc(
-        ctypes.c_void_p(expr.data_ptr()), expr.shape[0], expr.shape[1], expr.stride(0),
-        ctypes.c_void_p(geno.data_ptr()), geno.shape[0], geno.stride(0), float(pthresh),
+        ctypes.c_void_p(expr.data_ptr()), expr.shape[0], expr.shape[1], _ld(expr),
+        ctypes.c_void_p(geno.data_ptr()), geno.shape[0], _ld(geno), float(pthresh),
         ctypes.c_void_p(hits.data_ptr()), ctypes.c_void_p(hit_H.data_ptr()),
         ctypes.c_void_p(hit_p.data_ptr()), hits.shape[0], ctypes.byref(n), _stream(stream))
     return st, n.value
@@ -247,7 +256,7 @@ class Krux:
         assert expr.is_cuda and expr.dtype == torch.float32 and expr.dim() == 2 and expr.stride(1) == 1
         T, N = expr.shape
         h = ctypes.c_void_p()
-        st = self.lib.krux_rank(self.handle, _ptr(expr), T, N, expr.stride(0), ctypes.byref(h),
+        st = self.lib.krux_rank(self.handle, _ptr(expr), T, N, _ld(expr), ctypes.byref(h),
                                 _stream(stream))
         self._check(st, "krux_rank")
         return RankSet(self, h, T, N)
@@ -289,7 +298,7 @@ class Krux:
                   torch.empty((rs.T, e - snp_begin), dtype=torch.float64, device=self.device))
         o = self._opts(pthresh, capacity, snp_begin, snp_end, dn, margin, flags)
         n = ctypes.c_int64()
-        st = fn(self.handle, rs.handle, _ptr(geno), S, geno.stride(0), ctypes.byref(o), _ptr(hits),
+        st = fn(self.handle, rs.handle, _ptr(geno), S, _ld(geno), ctypes.byref(o), _ptr(hits),
                 _ptr(H), _ptr(P), ctypes.byref(n), _stream(stream))
         st = self._check(st, fn.__name__)
         k = min(n.value, capacity)
@@ -313,7 +322,7 @@ class Krux:
         hits, H, P = self._outputs(capacity)
         o = self._opts(pthresh, capacity, flags=KRUX_FLAG_MULTIALLELIC if multiallelic else 0)
         n = ctypes.c_int64()
-        st = self.lib.krux_scan_cis(self.handle, rs.handle, _ptr(geno), geno.shape[0], geno.stride(0),
+        st = self.lib.krux_scan_cis(self.handle, rs.handle, _ptr(geno), geno.shape[0], _ld(geno),
                                     _ptr(snp_pos), _ptr(trait_pos), int(window), ctypes.byref(o),
                                     _ptr(hits), _ptr(H), _ptr(P), ctypes.byref(n), _stream(stream))
         st = self._check(st, "krux_scan_cis")
@@ -330,7 +339,7 @@ class Krux:
         o = self._opts(pthresh, capacity)
         n = ctypes.c_int64()
         st = self.lib.krux_scan_parametric(self.handle, _ptr(expr), expr.shape[0], expr.shape[1],
-                                           expr.stride(0), _ptr(geno), geno.shape[0], geno.stride(0),
+                                           _ld(expr), _ptr(geno), geno.shape[0], _ld(geno),
                                            m, ctypes.byref(o), _ptr(hits), _ptr(H), _ptr(P),
                                            ctypes.byref(n), _stream(stream))
         st = self._check(st, "krux_scan_parametric")
@@ -360,7 +369,7 @@ class Krux:
         Pv = torch.empty(max(capacity, 1), dtype=torch.float64, device=self.device)
         o = self._opts(pthresh, capacity)
         n = ctypes.c_int64()
-        st = self.lib.krux_permute(self.handle, rs.handle, _ptr(geno), S, geno.stride(0), _ptr(perms),
+        st = self.lib.krux_permute(self.handle, rs.handle, _ptr(geno), S, _ld(geno), _ptr(perms),
                                    P_, ctypes.byref(o), _ptr(minp), _ptr(hits), _ptr(H), _ptr(Pv),
                                    ctypes.byref(n), _ptr(hist), fdr_bins, float(fdr_bin_width),
                                    _stream(stream))
@@ -384,7 +393,7 @@ class Krux:
             arr[i].rs = c["rs"].handle
             arr[i].geno = g.data_ptr()
             arr[i].S = g.shape[0]
-            arr[i].ldg = g.stride(0)
+            arr[i].ldg = _ld(g)
             arr[i].hits = hits.data_ptr()
             arr[i].hit_H = H.data_ptr()
             arr[i].hit_p = P.data_ptr()
@@ -405,7 +414,7 @@ class Krux:
         """Times every launch shape on a sample of geno and keeps the fastest for
         this rank set's width.  Returns (layout, nc, nA, ka) of the winner."""
         shape = (ctypes.c_int32 * 4)()
-        st = self.lib.krux_autotune(self.handle, rs.handle, _ptr(geno), geno.shape[0], geno.stride(0),
+        st = self.lib.krux_autotune(self.handle, rs.handle, _ptr(geno), geno.shape[0], _ld(geno),
                                     float(pthresh), _stream(stream), shape)
         self._check(st, "krux_autotune")
         return tuple(shape)
@@ -427,7 +436,7 @@ class Krux:
         o = self._opts(pthresh, capacity, dense=dn,
                        flags=KRUX_FLAG_MULTIALLELIC if multiallelic else 0)
         h = ctypes.c_void_p()
-        st = self.lib.krux_graph_scan(self.handle, rs.handle, _ptr(geno), geno.shape[0], geno.stride(0),
+        st = self.lib.krux_graph_scan(self.handle, rs.handle, _ptr(geno), geno.shape[0], _ld(geno),
                                       ctypes.byref(o), _ptr(hits), _ptr(H), _ptr(P), ctypes.byref(h))
         self._check(st, "krux_graph_scan")
         g = Graph(self, h, [(hits, H, P, capacity)], keep=(geno, rs))
@@ -447,7 +456,7 @@ class Krux:
         o = self._opts(pthresh, capacity)
         h = ctypes.c_void_p()
         st = self.lib.krux_graph_permute(self.handle, rs.handle, _ptr(geno), geno.shape[0],
-                                         geno.stride(0), _ptr(perms), P_, ctypes.byref(o), _ptr(minp),
+                                         _ld(geno), _ptr(perms), P_, ctypes.byref(o), _ptr(minp),
                                          _ptr(hits), _ptr(H), _ptr(P), _ptr(hist), fdr_bins,
                                          float(fdr_bin_width), ctypes.byref(h))
         self._check(st, "krux_graph_permute")
@@ -466,7 +475,7 @@ class Krux:
             arr[i].rs = c["rs"].handle
             arr[i].geno = g.data_ptr()
             arr[i].S = g.shape[0]
-            arr[i].ldg = g.stride(0)
+            arr[i].ldg = _ld(g)
             arr[i].hits = hits.data_ptr()
             arr[i].hit_H = H.data_ptr()
             arr[i].hit_p = P.data_ptr()
@@ -478,48 +487,40 @@ class Krux:
         return Graph(self, h, outs, keep=tuple(cohorts))
 
     # ---- end to end from host arrays -------------------------------------------
-    def scan_pinned(self, expr_h, geno_h, pthresh, capacity, stream=None):
-        """End-to-end scan from pinned host tensors (float32 [T,N], int8 [S,N]):
-        host->device copies, rank, fused scan, device->host copy of the hits."""
-        e_d = expr_h.to(self.device, non_blocking=True)
-        g_d = geno_h.to(self.device, non_blocking=True)
-        rs = self.krux_rank(e_d, stream)
-        r = self.krux_scan(rs, g_d, pthresh, capacity, stream=stream)
-        k = int(r["hits"].shape[0])
-        hits, H, P = _to_pinned_host(r["hits"], r["H"], r["p"])
-        out = dict(n_hits=r["n_hits"], hits=hits, H=H, p=P, d2h_bytes=k * (16 + 8 + 8) + 8)
-        rs.free()
-        return out
-
-    def scan_host(self, expr, geno, pthresh, capacity, stream=None):
-        """End-to-end call from host numpy arrays: pinned host->device copies, rank,
-        fused scan, and device->host copy of the hit list.  Returns numpy arrays
-        (hits [k,4] int32, H, p) and the exact hit count."""
+    def krux_scan_host(self, expr, geno, pthresh, capacity, out=None, stream=None):
+        """End-to-end scan through the C ABI on host memory (krux_scan_host): the
+        library copies expr (float32 [T, N]) and geno (int8 [S, N]) to the device,
+        ranks, scans and copies the hit list back.  expr / geno: numpy arrays or
+        CPU torch tensors (page-locked ones copy at the link's rate).  out: optional
+        preallocated host torch tensors (hits int32 [cap, 4], H, p float64 [cap]),
+        reused across calls.  Returns dict(n_hits, overflow, hits, H, p) with numpy
+        views of the first min(n_hits, capacity) records and d2h_bytes."""
         import torch
-        e_h = torch.from_numpy(np.ascontiguousarray(expr, dtype=np.float32)).pin_memory()
-        g_h = torch.from_numpy(np.ascontiguousarray(geno, dtype=np.int8)).pin_memory()
-        e_d = e_h.to(self.device, non_blocking=True)
-        g_d = g_h.to(self.device, non_blocking=True)
-        rs = self.krux_rank(e_d, stream)
-        r = self.krux_scan(rs, g_d, pthresh, capacity, stream=stream)
-        hits, H, P = _to_pinned_host(r["hits"], r["H"], r["p"])
-        out = dict(n_hits=r["n_hits"], hits=hits, H=H, p=P)
-        rs.free()
-        return out
+        e = torch.as_tensor(expr)
+        g = torch.as_tensor(geno)
+        assert e.device.type == "cpu" and e.dtype == torch.float32 and e.dim() == 2 and e.stride(1) == 1
+        assert g.device.type == "cpu" and g.dtype == torch.int8 and g.dim() == 2 and g.stride(1) == 1
+        assert g.shape[1] == e.shape[1] or g.shape[0] == 0
+        cap = max(int(capacity), 0)
+        if out is None:
+            out = (torch.empty((max(cap, 1), 4), dtype=torch.int32),
+                   torch.empty(max(cap, 1), dtype=torch.float64),
+                   torch.empty(max(cap, 1), dtype=torch.float64))
+        hits, H, P = out
+        assert hits.shape[0] >= cap and H.shape[0] >= cap and P.shape[0] >= cap
+        o = self._opts(pthresh, cap)
+        n = ctypes.c_int64()
+        st = self.lib.krux_scan_host(self.handle, ctypes.c_void_p(e.data_ptr()), e.shape[0], e.shape[1],
+                                     _ld(e), ctypes.c_void_p(g.data_ptr()), g.shape[0],
+                                     _ld(g), ctypes.byref(o),
+                                     ctypes.c_void_p(hits.data_ptr()), ctypes.c_void_p(H.data_ptr()),
+                                     ctypes.c_void_p(P.data_ptr()), ctypes.byref(n), _stream(stream))
+        st = self._check(st, "krux_scan_host")
+        k = min(n.value, cap)
+        return dict(n_hits=n.value, overflow=st == KRUX_EOVERFLOW, hits=hits[:k].numpy(),
+                    H=H[:k].numpy(), p=P[:k].numpy(), d2h_bytes=k * (16 + 8 + 8))
 
-
-def _to_pinned_host(*tensors):
-    """Device tensors -> numpy arrays backed by pinned host memory (torch's caching
-    host allocator, so repeated calls reuse the blocks): the copies run at the
-    link's rate instead of through a pageable bounce buffer."""
-    import torch
-    outs = []
-    for t in tensors:
-        h = torch.empty(t.shape, dtype=t.dtype, pin_memory=True)
-        h.copy_(t, non_blocking=True)
-        outs.append(h)
-    torch.cuda.current_stream(tensors[0].device).synchronize()
-    return [h.numpy() for h in outs]
+    scan_host = krux_scan_host
 
 
 class Graph:

@@ -197,7 +197,8 @@ struct krux_ctx {
   PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   cudaEvent_t ev[kEv] = {};
   DevBuf B, meta, codes, groups, items, status, counters, aux, cfacptr, miss_idx, miss_mask,
-      list, gemm_out, bucket_ranks, permA, minpkey, seg, permNan, aux2, param, paramOut, packjobs;
+      list, gemm_out, bucket_ranks, permA, minpkey, seg, permNan, aux2, param, paramOut, packjobs,
+      host_in, host_out;  // krux_scan_host: device copies of the inputs, device hit list
   HostBuf list_host;  // staging of the SNP lists
   void *blas = nullptr;
   std::vector<std::pair<size_t, void *>> pool;  // freed rank-set blocks, reused by size
@@ -515,7 +516,8 @@ void krux_destroy(krux_ctx *ctx) {
   DevBuf *bufs[] = {&ctx->B, &ctx->meta, &ctx->codes, &ctx->groups, &ctx->items, &ctx->status,
                     &ctx->counters, &ctx->aux, &ctx->cfacptr, &ctx->miss_idx, &ctx->miss_mask,
                     &ctx->list, &ctx->gemm_out, &ctx->bucket_ranks, &ctx->permA, &ctx->minpkey, &ctx->seg,
-                    &ctx->permNan, &ctx->aux2, &ctx->param, &ctx->paramOut, &ctx->packjobs};
+                    &ctx->permNan, &ctx->aux2, &ctx->param, &ctx->paramOut, &ctx->packjobs,
+                    &ctx->host_in, &ctx->host_out};
   for (DevBuf *b : bufs) b->release();
   ctx->list_host.release();
   for (auto &pb : ctx->pool) cudaFree(pb.second);
@@ -1539,6 +1541,73 @@ extern "C" krux_status krux_scan(krux_ctx *ctx, const krux_rankset *rs, const in
     return fail(ctx, KRUX_EOVERFLOW, "%lld hits exceed capacity %lld", (long long)*n_hits,
                 (long long)opts->hit_capacity);
   return KRUX_OK;
+}
+
+// Host-memory wrapper of krux_rank + krux_scan: one copy per input into the
+// context's device buffer (packed to leading dimension N), the scan into a
+// device hit list the context keeps, and one copy per output array back.
+extern "C" krux_status krux_scan_host(krux_ctx *ctx, const float *expr, int T, int N, int64_t lde,
+                                      const int8_t *geno, int64_t S, int64_t ldg,
+                                      const krux_opts *opts, krux_hit *hits, double *hit_H,
+                                      double *hit_p, int64_t *n_hits, void *stream) {
+  if (!ctx) return KRUX_EINVAL;
+  if (!n_hits || !expr) return fail(ctx, KRUX_EINVAL, "NULL n_hits or expr");
+  *n_hits = 0;
+  krux_status st = check_opts(ctx, opts);
+  if (st != KRUX_OK) return st;
+  if (opts->dense_H || opts->dense_p)
+    return fail(ctx, KRUX_EINVAL, "krux_scan_host: dense output is device-only (use krux_scan)");
+  if (T < 1 || N < 1 || N > kMaxN || lde < N)
+    return fail(ctx, KRUX_EINVAL, "krux_scan_host: need T >= 1, 1 <= N <= %d, lde >= N", kMaxN);
+  if (S < 0 || (S > 0 && (ldg < N || !geno)))
+    return fail(ctx, KRUX_EINVAL, "krux_scan_host: need S >= 0 and, for S > 0, geno and ldg >= N");
+  if (opts->hit_capacity > 0 && (!hits || !hit_H || !hit_p))
+    return fail(ctx, KRUX_EINVAL, "hit outputs are NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  KRUX_CUDA(ctx, cudaSetDevice(ctx->device));
+  const size_t ebytes = (size_t)T * N * 4, gbytes = (size_t)S * N;
+  const size_t goff = (ebytes + 255) / 256 * 256;
+  KRUX_CUDA(ctx, ctx->host_in.ensure(goff + std::max<size_t>(gbytes, 1)));
+  char *din = ctx->host_in.as<char>();
+  if (lde == N)
+    KRUX_CUDA(ctx, cudaMemcpyAsync(din, expr, ebytes, cudaMemcpyHostToDevice, s));
+  else
+    KRUX_CUDA(ctx, cudaMemcpy2DAsync(din, (size_t)N * 4, expr, (size_t)lde * 4, (size_t)N * 4, T,
+                                     cudaMemcpyHostToDevice, s));
+  if (S > 0) {
+    if (ldg == N)
+      KRUX_CUDA(ctx, cudaMemcpyAsync(din + goff, geno, gbytes, cudaMemcpyHostToDevice, s));
+    else
+      KRUX_CUDA(ctx, cudaMemcpy2DAsync(din + goff, (size_t)N, geno, (size_t)ldg, (size_t)N, S,
+                                       cudaMemcpyHostToDevice, s));
+  }
+  const int64_t cap = std::max<int64_t>(opts->hit_capacity, 0);
+  const size_t hoff = 0, Hoff = (size_t)std::max<int64_t>(cap, 1) * sizeof(krux_hit);
+  const size_t poff = Hoff + (size_t)std::max<int64_t>(cap, 1) * 8;
+  KRUX_CUDA(ctx, ctx->host_out.ensure(poff + (size_t)std::max<int64_t>(cap, 1) * 8));
+  char *dout = ctx->host_out.as<char>();
+  krux_rankset *rs = nullptr;
+  st = krux_rank(ctx, reinterpret_cast<const float *>(din), T, N, N, &rs, stream);
+  if (st != KRUX_OK) return st;
+  const float ms_rank = ctx->profiling ? ctx->prof.ms_rank : 0.f;
+  st = krux_scan(ctx, rs, reinterpret_cast<const int8_t *>(din + goff), S, N, opts,
+                 reinterpret_cast<krux_hit *>(dout + hoff), reinterpret_cast<double *>(dout + Hoff),
+                 reinterpret_cast<double *>(dout + poff), n_hits, stream);
+  krux_rankset_free(ctx, rs);
+  if (st != KRUX_OK && st != KRUX_EOVERFLOW) return st;
+  if (ctx->profiling) {
+    ctx->prof.ms_rank = ms_rank;
+    ctx->prof.launches += 2;  // the rank transform's two kernels
+  }
+  const int64_t k = std::min<int64_t>(*n_hits, cap);
+  if (k > 0) {
+    KRUX_CUDA(ctx, cudaMemcpyAsync(hits, dout + hoff, (size_t)k * sizeof(krux_hit),
+                                   cudaMemcpyDeviceToHost, s));
+    KRUX_CUDA(ctx, cudaMemcpyAsync(hit_H, dout + Hoff, (size_t)k * 8, cudaMemcpyDeviceToHost, s));
+    KRUX_CUDA(ctx, cudaMemcpyAsync(hit_p, dout + poff, (size_t)k * 8, cudaMemcpyDeviceToHost, s));
+  }
+  KRUX_CUDA(ctx, cudaStreamSynchronize(s));
+  return st;
 }
 
 extern "C" krux_status krux_scan_cis(krux_ctx *ctx, const krux_rankset *rs, const int8_t *geno,

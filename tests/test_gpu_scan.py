@@ -223,14 +223,42 @@ def test_missing_genotypes(kx, oracle_mod):
     check_dense(dn["dense_H"].cpu().numpy(), dn["dense_p"].cpu().numpy(), orc)
 
 
+def _as_res(out):
+    import torch
+    return {k: torch.from_numpy(np.ascontiguousarray(out[k])) for k in ("hits", "H", "p")}
+
+
 def test_host_end_to_end(kx, oracle_mod):
     d = synth.config(1, T=50, S=400, seed=8)
-    out = kx.scan_host(d["expr"], d["geno"], 0.01, capacity=50 * 400)
+    out = kx.krux_scan_host(d["expr"], d["geno"], 0.01, capacity=50 * 400)
     orc = oracle_mod.scan(d["expr"], d["geno"], 0.01)
     assert out["n_hits"] == int(orc["hit"].sum())
-    got = {(int(a), int(b)) for a, b in out["hits"][:, :2]}
-    want = {tuple(x) for x in np.argwhere(orc["hit"]).tolist()}
-    assert got == want
+    check_hits(_as_res(out), orc, np.arange(50), np.arange(400), 0.01)
+
+
+def test_host_entry_strided_pinned_missing(kx, oracle_mod):
+    """krux_scan_host on page-locked host buffers whose leading dimensions exceed
+    N (the 2-D copies), with missing genotypes and NaN expression, against the
+    oracle; then a capacity below the hit count: KRUX_EOVERFLOW, the exact count
+    and real hit records."""
+    import torch
+    d = synth.config(3, T=300, S=4000, seed=21)
+    T, S, N = d["expr"].shape[0], d["geno"].shape[0], d["expr"].shape[1]
+    pth = 1e-3
+    e_h = torch.zeros((T, N + 5), dtype=torch.float32).pin_memory()
+    g_h = torch.zeros((S, N + 3), dtype=torch.int8).pin_memory()
+    e_h[:, :N] = torch.from_numpy(d["expr"])
+    g_h[:, :N] = torch.from_numpy(d["geno"])
+    out = kx.krux_scan_host(e_h[:, :N], g_h[:, :N], pth, capacity=T * S)
+    orc = oracle_mod.scan(d["expr"], d["geno"], pth)
+    assert not out["overflow"] and out["n_hits"] == out["hits"].shape[0]
+    check_hits(_as_res(out), orc, np.arange(T), np.arange(S), pth)
+    cap = out["n_hits"] // 3
+    small = kx.krux_scan_host(d["expr"], d["geno"], pth, capacity=cap)
+    assert small["overflow"] and small["n_hits"] == out["n_hits"] and small["hits"].shape[0] == cap
+    key = lambda h: h[:, 0].astype(np.int64) * S + h[:, 1]
+    full = dict(zip(key(out["hits"]).tolist(), map(tuple, out["hits"].tolist())))
+    assert all(full[k_] == tuple(r) for k_, r in zip(key(small["hits"]).tolist(), small["hits"].tolist()))
 
 
 @pytest.mark.parametrize("layout,nc,nA,ka", [(0, 0, 0, 0), (1, 0, 0, 0), (1, 2, 4, 0), (0, 3, 3, 0),
