@@ -177,8 +177,9 @@ krux_status krux_scan_plain(krux_ctx *ctx, const krux_rankset *rs, const int8_t 
  *           complete only when the hits fit the capacity (else KRUX_EOVERFLOW).
  * The unpermuted scan's hits are returned as in krux_scan.  With more than 65,536
  * SNPs a short seed pass over the first 16,384 runs first and primes the minimum-p
- * search with lower bounds (the stream is synchronised once in between; the graph
- * form krux_graph_permute has no seed pass and gives the same results). */
+ * search with lower bounds; both launches are enqueued back to back on `stream`
+ * (the rows of perms are checked on the host first, the hit counts read back at
+ * the end), and krux_graph_permute captures the same two launches. */
 krux_status krux_permute(krux_ctx *ctx, const krux_rankset *rs, const int8_t *geno, int64_t S,
                          int64_t ldg, const int32_t *perms, int P, const krux_opts *opts,
                          double *minp, krux_hit *hits, double *hit_H, double *hit_p,

@@ -198,7 +198,8 @@ struct krux_ctx {
   cudaEvent_t ev[kEv] = {};
   DevBuf B, meta, codes, groups, items, status, counters, aux, cfacptr, miss_idx, miss_mask,
       list, gemm_out, bucket_ranks, permA, minpkey, seg, permNan, aux2, param, paramOut, packjobs,
-      host_in, host_out;  // krux_scan_host: device copies of the inputs, device hit list
+      host_in, host_out,  // krux_scan_host: device copies of the inputs, device hit list
+      groups2, items2, packjobs2, cfacptr2;  // launch tables of a second launch in the same call
   HostBuf list_host;  // staging of the SNP lists
   void *blas = nullptr;
   std::vector<std::pair<size_t, void *>> pool;  // freed rank-set blocks, reused by size
@@ -517,7 +518,8 @@ void krux_destroy(krux_ctx *ctx) {
                     &ctx->counters, &ctx->aux, &ctx->cfacptr, &ctx->miss_idx, &ctx->miss_mask,
                     &ctx->list, &ctx->gemm_out, &ctx->bucket_ranks, &ctx->permA, &ctx->minpkey, &ctx->seg,
                     &ctx->permNan, &ctx->aux2, &ctx->param, &ctx->paramOut, &ctx->packjobs,
-                    &ctx->host_in, &ctx->host_out};
+                    &ctx->host_in, &ctx->host_out, &ctx->groups2, &ctx->items2, &ctx->packjobs2,
+                    &ctx->cfacptr2};
   for (DevBuf *b : bufs) b->release();
   ctx->list_host.release();
   for (auto &pb : ctx->pool) cudaFree(pb.second);
@@ -1054,10 +1056,19 @@ struct FusedLaunch {
   bool batched_pack = false;
   int n_pack_jobs = 0;
   int64_t pack_slots = 0, pack_halves = 0;
+  const PackJob *packjobs = nullptr;        // this launch's tables (device)
+  const double *const *cfacptr = nullptr;
 };
 
+// tables = 1 puts this launch's tables (group descriptors, work items, pack jobs,
+// tie-factor pointers) in the context's second set, so that two prepared launches
+// can be enqueued back to back without a host synchronisation between them.
 krux_status prepare_fused(krux_ctx *ctx, CallPlan &cp, const krux_opts *o, FusedLaunch &fl,
-                          cudaStream_t s) {
+                          cudaStream_t s, int tables = 0) {
+  DevBuf &t_groups = tables ? ctx->groups2 : ctx->groups;
+  DevBuf &t_items = tables ? ctx->items2 : ctx->items;
+  DevBuf &t_packjobs = tables ? ctx->packjobs2 : ctx->packjobs;
+  DevBuf &t_cfacptr = tables ? ctx->cfacptr2 : ctx->cfacptr;
   fl.h1 = cp.param.model == 0 ? cp.param.h1 : h_df1(o->pthresh);
   fl.h2 = cp.param.model == 0 ? cp.param.h2 : h_df2(o->pthresh);
   const int ng = (int)cp.groups.size();
@@ -1210,13 +1221,13 @@ krux_status prepare_fused(krux_ctx *ctx, CallPlan &cp, const krux_opts *o, Fused
   }
   std::vector<WorkItem> items =
       cp.cis.on ? make_items_cis(cp, plans) : make_items(plans, nc_max, ctx->sm_count);
-  KRUX_CUDA(ctx, ctx->groups.ensure(sizeof(GroupDesc) * ng));
-  KRUX_CUDA(ctx, ctx->items.ensure(sizeof(WorkItem) * std::max<size_t>(items.size(), 1)));
+  KRUX_CUDA(ctx, t_groups.ensure(sizeof(GroupDesc) * ng));
+  KRUX_CUDA(ctx, t_items.ensure(sizeof(WorkItem) * std::max<size_t>(items.size(), 1)));
   // pageable uploads: staged before the calls return, so the host vectors may go
-  KRUX_CUDA(ctx, cudaMemcpyAsync(ctx->groups.p, descs.data(), sizeof(GroupDesc) * ng,
+  KRUX_CUDA(ctx, cudaMemcpyAsync(t_groups.p, descs.data(), sizeof(GroupDesc) * ng,
                                  cudaMemcpyHostToDevice, s));
   if (!items.empty())
-    KRUX_CUDA(ctx, cudaMemcpyAsync(ctx->items.p, items.data(), sizeof(WorkItem) * items.size(),
+    KRUX_CUDA(ctx, cudaMemcpyAsync(t_items.p, items.data(), sizeof(WorkItem) * items.size(),
                                    cudaMemcpyHostToDevice, s));
   fl.batched_pack = !cp.multi && cp.param.model != 1;
   if (fl.batched_pack) {
@@ -1246,20 +1257,22 @@ krux_status prepare_fused(krux_ctx *ctx, CallPlan &cp, const krux_opts *o, Fused
     fl.n_pack_jobs = ng;
     fl.pack_slots = slots;
     fl.pack_halves = halves;
-    KRUX_CUDA(ctx, ctx->packjobs.ensure(sizeof(PackJob) * ng));
-    KRUX_CUDA(ctx, cudaMemcpyAsync(ctx->packjobs.p, jobs.data(), sizeof(PackJob) * ng,
+    KRUX_CUDA(ctx, t_packjobs.ensure(sizeof(PackJob) * ng));
+    KRUX_CUDA(ctx, cudaMemcpyAsync(t_packjobs.p, jobs.data(), sizeof(PackJob) * ng,
                                    cudaMemcpyHostToDevice, s));
+    fl.packjobs = t_packjobs.as<PackJob>();
   }
   std::vector<const double *> cf(ng);
   for (int i = 0; i < ng; ++i) cf[i] = cp.groups[i].cfac;
-  KRUX_CUDA(ctx, ctx->cfacptr.ensure(sizeof(double *) * ng));
-  KRUX_CUDA(ctx, cudaMemcpyAsync(ctx->cfacptr.p, cf.data(), sizeof(double *) * ng,
+  KRUX_CUDA(ctx, t_cfacptr.ensure(sizeof(double *) * ng));
+  KRUX_CUDA(ctx, cudaMemcpyAsync(t_cfacptr.p, cf.data(), sizeof(double *) * ng,
                                  cudaMemcpyHostToDevice, s));
+  fl.cfacptr = t_cfacptr.as<const double *>();
   KRUX_CUDA(ctx, finalize_prepare());
   ScanParams &p = fl.p;
   p = ScanParams{};
-  p.groups = ctx->groups.as<GroupDesc>();
-  p.items = ctx->items.as<WorkItem>();
+  p.groups = t_groups.as<GroupDesc>();
+  p.items = t_items.as<WorkItem>();
   p.n_items = (int32_t)items.size();
   p.nc = nc_max;
   p.nA = sh.nA;
@@ -1372,7 +1385,7 @@ krux_status enqueue_fused(krux_ctx *ctx, CallPlan &cp, const FusedLaunch &fl, cu
   }
   ev_record(ctx, 2, s);
   if (fl.batched_pack)
-    KRUX_CUDA(ctx, launch_pack_batch(ctx->packjobs.as<PackJob>(), fl.n_pack_jobs, fl.pack_slots,
+    KRUX_CUDA(ctx, launch_pack_batch(fl.packjobs, fl.n_pack_jobs, fl.pack_slots,
                                      fl.pack_halves, fl.h1, fl.h2, fl.signed_coef, status, s));
   for (int i = 0; i < ng && !fl.batched_pack; ++i) {
     const ScanGroupIn &g = cp.groups[i];
@@ -1425,7 +1438,7 @@ krux_status enqueue_fused(krux_ctx *ctx, CallPlan &cp, const FusedLaunch &fl, cu
     const OutSlot &os = cp.slots[k];
     if (os.capacity <= 0) continue;
     KRUX_CUDA(ctx, launch_finalize_dev(os.hits, os.aux, os.aux2, totals + k, os.capacity,
-                                       ctx->cfacptr.as<const double *>(), os.H, os.P,
+                                       fl.cfacptr, os.H, os.P,
                                        ctx->sm_count, s, cp.fdr_hist, cp.fdr_bins, cp.fdr_l0,
                                        cp.fdr_w));
   }
@@ -1488,6 +1501,23 @@ krux_status run_fused(krux_ctx *ctx, CallPlan &cp, const krux_opts *o, cudaStrea
   st = enqueue_fused(ctx, cp, fl, s);
   if (st != KRUX_OK) return st;
   return finish_fused(ctx, cp, fl, s, counts);
+}
+
+// Seed pass of a permutation batch (section "P-value calculation and empirical
+// FDR correction": the minimum p of each permuted trait over all SNPs): the
+// permuted groups against the first kSeedSnps SNPs, so that the main launch
+// starts from running minima over thousands of SNPs instead of none (without it
+// the first wave of CTAs refines nearly every chunk in FP64).  False when the
+// call is too small to gain from one.
+bool make_seed_plan(const CallPlan &cp, CallPlan &seed) {
+  constexpr int64_t kSeedSnps = 16384;
+  if (cp.groups.size() != 1 || cp.groups[0].n_snps <= 4 * kSeedSnps) return false;
+  seed = cp;
+  seed.groups[0].n_snps = kSeedSnps;
+  seed.slots[0].capacity = 0;
+  seed.fdr_hist = nullptr;
+  seed.perm.seed = true;
+  return true;
 }
 
 krux_status check_scan_args(krux_ctx *ctx, const krux_rankset *rs, const int8_t *geno, int64_t S,
@@ -2008,28 +2038,27 @@ extern "C" krux_status krux_permute(krux_ctx *ctx, const krux_rankset *rs, const
   st = plan_permute(ctx, cp, rs, geno, S, ldg, perms, P, opts, minp, hits, hit_H, hit_p, fdr_hist,
                     fdr_bins, fdr_bin_width, s);
   if (st != KRUX_OK) return st;
-  // Seed pass: the permuted agroups against the first kSeedSnps SNPs, so that
-  // the main launch starts from running minima over thousands of SNPs instead of
-  // none (without it the first wave of CTAs refines nearly every chunk in FP64).
-  constexpr int64_t kSeedSnps = 16384;
-  if (cp.groups.size() == 1 && cp.groups[0].n_snps > 4 * kSeedSnps) {
-    CallPlan seed = cp;
-    seed.groups[0].n_snps = kSeedSnps;
-    seed.slots[0].capacity = 0;
-    seed.fdr_hist = nullptr;
-    seed.perm.seed = true;
-    FusedLaunch fs;
-    st = prepare_fused(ctx, seed, opts, fs, s);
+  // the main launch is prepared first (it sizes every buffer the two launches
+  // share), the seed pass into the second table set, then both are enqueued back
+  // to back with no host synchronisation between them
+  CallPlan seed;
+  const bool with_seed = make_seed_plan(cp, seed);
+  FusedLaunch fm, fs;
+  st = prepare_fused(ctx, cp, opts, fm, s, 0);
+  if (st != KRUX_OK) return st;
+  if (with_seed) {
+    st = prepare_fused(ctx, seed, opts, fs, s, 1);
     if (st != KRUX_OK) return st;
+    KRUX_CUDA(ctx, scan_set_smem(std::max(fs.smem, fm.smem)));
     st = enqueue_fused(ctx, seed, fs, s);
     if (st != KRUX_OK) return st;
     if (ctx->profiling) ctx->prof.launches += fused_launches(seed, fs);
-    // the main launch's planning may reallocate buffers the seed pass still reads
-    KRUX_CUDA(ctx, cudaStreamSynchronize(s));
     cp.perm.pre_done = true;
   }
+  st = enqueue_fused(ctx, cp, fm, s);
+  if (st != KRUX_OK) return st;
   std::vector<unsigned long long> counts;
-  st = run_fused(ctx, cp, opts, s, counts);
+  st = finish_fused(ctx, cp, fm, s, counts);
   if (st != KRUX_OK) return st;
   *n_hits = (int64_t)counts[0];
   if (*n_hits > opts->hit_capacity)
@@ -2047,6 +2076,9 @@ struct krux_graph {
   krux_ctx *w = nullptr;           // private workspace context
   CallPlan cp;
   FusedLaunch fl;
+  bool with_seed = false;          // a permutation batch's seed pass runs first
+  CallPlan seed_cp;
+  FusedLaunch seed_fl;
   krux_opts opts{};
   cudaStream_t cs = nullptr;       // capture stream
   cudaGraph_t graph = nullptr;
@@ -2101,13 +2133,20 @@ krux_status graph_capture(krux_ctx *ctx, krux_graph *g) {
     return fail(ctx, KRUX_EUNSUPPORTED, "graphs take complete genotypes (no -1 codes)");
   krux_status st = prepare_fused(w, g->cp, &g->opts, g->fl, g->cs);
   if (st != KRUX_OK) return st;
+  if (g->with_seed) {
+    st = prepare_fused(w, g->seed_cp, &g->opts, g->seed_fl, g->cs, 1);
+    if (st != KRUX_OK) return st;
+    KRUX_CUDA(w, scan_set_smem(std::max(g->seed_fl.smem, g->fl.smem)));
+    g->cp.perm.pre_done = true;
+  }
   const int nslots = g->fl.nslots;
   KRUX_CUDA(w, cudaHostAlloc(reinterpret_cast<void **>(&g->host), (size_t)(nslots + 1) * 8,
                              cudaHostAllocDefault));
   std::memset(g->host, 0, (size_t)(nslots + 1) * 8);
   KRUX_CUDA(w, cudaStreamSynchronize(g->cs));
   KRUX_CUDA(w, cudaStreamBeginCapture(g->cs, cudaStreamCaptureModeThreadLocal));
-  st = enqueue_fused(w, g->cp, g->fl, g->cs);
+  if (g->with_seed) st = enqueue_fused(w, g->seed_cp, g->seed_fl, g->cs);
+  if (st == KRUX_OK) st = enqueue_fused(w, g->cp, g->fl, g->cs);
   if (st == KRUX_OK && cudaMemcpyAsync(g->host, w->counters.as<unsigned long long>() + nslots,
                                        (size_t)nslots * 8, cudaMemcpyDeviceToHost, g->cs) != cudaSuccess)
     st = fail(w, KRUX_ECUDA, "capture of the count read-back failed");
@@ -2191,6 +2230,7 @@ extern "C" krux_status krux_graph_permute(krux_ctx *ctx, const krux_rankset *rs,
   g->opts = *opts;
   st = plan_permute(g->w, g->cp, rs, geno, S, ldg, perms, P, opts, minp, hits, hit_H, hit_p,
                     fdr_hist, fdr_bins, fdr_bin_width, g->cs);
+  if (st == KRUX_OK) g->with_seed = make_seed_plan(g->cp, g->seed_cp);
   if (st == KRUX_OK) st = graph_capture(ctx, g);
   if (st != KRUX_OK) return graph_fail(ctx, g, st);
   *out = g;

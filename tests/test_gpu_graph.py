@@ -98,6 +98,30 @@ def test_graph_permute_matches_direct(kx, oracle_mod, nan):
     graph.close()
 
 
+def test_graph_permute_with_seed_pass(kx, oracle_mod):
+    """More than 65,536 SNPs: the direct call and the graph both run the seed pass
+    over the first 16,384 SNPs and the main launch back to back; their minima,
+    hits and FDR histogram agree exactly, and the minima match the oracle."""
+    T, S, P, N = 128, 70000, 4, 102
+    d = synth.config(4, T=T, S=S, N=N, seed=41)
+    perms = _dev(synth.make_perms(7, P, N))
+    rs = kx.krux_rank(_dev(d["expr"]))
+    g = _dev(d["geno"])
+    pth = 1e-4
+    graph = kx.graph_permute(rs, g, perms, pth, capacity=T * S, fdr_bins=10, fdr_bin_width=0.5)
+    graph.launch()
+    got = graph.wait()[0]
+    direct = kx.krux_permute(rs, g, perms, pth, capacity=T * S, fdr_bins=10, fdr_bin_width=0.5)
+    _same(got, direct)
+    assert np.array_equal(graph.minp.cpu().numpy(), direct["minp"].cpu().numpy())
+    assert np.array_equal(graph.fdr_hist.cpu().numpy(), direct["fdr_hist"].cpu().numpy())
+    sel = np.arange(0, T, 8)
+    want = oracle_mod.perm_minp(d["expr"][sel], d["geno"], perms.cpu().numpy())
+    gm = direct["minp"].cpu().numpy()[:, sel]
+    assert np.all(np.abs(gm - want) <= 1e-6 * want)
+    graph.close()
+
+
 def test_graph_grouped_cohorts(kx, oracle_mod):
     rng = np.random.default_rng(41)
     cohorts, data = [], []
