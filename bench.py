@@ -631,6 +631,7 @@ def run_row_timings(args):
     import paper_1307_3519_gb300 as k
     import synth
     kx = k.Krux(0)
+    kx.set_profiling(True)
     st = torch.cuda.current_stream()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
@@ -646,7 +647,7 @@ def run_row_timings(args):
             best = t if best is None else min(best, t)
         hits = out if isinstance(out, int) else -1
         print(f"row {name}: {pairs:.4g} pairs in {best:.3f} ms = {pairs / best * 1e3:.4g} pairs/s "
-              f"(hits {hits})", flush=True)
+              f"(hits {hits}, scan kernel form {kx.profile()['scan_form']})", flush=True)
 
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     want = set(args.rows.split(","))

@@ -89,6 +89,10 @@ typedef struct {
   int32_t launches;     /* kernels the last call launched */
   int32_t scan_grid;    /* CTAs of the fused scan launch */
   int64_t pairs;        /* SNP x trait pairs the last call tested */
+  int32_t scan_form;    /* kernel form of the fused scan launch: 0 plain, 1 markers with up to
+                           five groups, 2 permutation batch, 3 general (NaN, dense, cis),
+                           4 plain permutation batch */
+  int32_t reserved_;
 } krux_profile;
 
 /* Create a context on CUDA device `device` (must be sm_103 for the fused path).

@@ -51,7 +51,8 @@ class Profile(ctypes.Structure):
     _fields_ = [("ms_rank", ctypes.c_float), ("ms_pack", ctypes.c_float),
                 ("ms_scan", ctypes.c_float), ("ms_finalize", ctypes.c_float),
                 ("ms_gemm", ctypes.c_float), ("launches", ctypes.c_int32),
-                ("scan_grid", ctypes.c_int32), ("pairs", ctypes.c_int64)]
+                ("scan_grid", ctypes.c_int32), ("pairs", ctypes.c_int64),
+                ("scan_form", ctypes.c_int32), ("reserved_", ctypes.c_int32)]
 
 
 class Cohort(ctypes.Structure):

@@ -199,7 +199,8 @@ struct krux_ctx {
   DevBuf B, meta, codes, groups, items, status, counters, aux, cfacptr, miss_idx, miss_mask,
       list, gemm_out, bucket_ranks, permA, minpkey, seg, permNan, aux2, param, paramOut, packjobs,
       host_in, host_out,  // krux_scan_host: device copies of the inputs, device hit list
-      groups2, items2, packjobs2, cfacptr2;  // launch tables of a second launch in the same call
+      groups2, items2, packjobs2, cfacptr2,  // launch tables of a second launch in the same call
+      mcand;  // plain-form permutation batches: pairs for the deferred FP64 pass
   HostBuf list_host;  // staging of the SNP lists
   void *blas = nullptr;
   std::vector<std::pair<size_t, void *>> pool;  // freed rank-set blocks, reused by size
@@ -270,7 +271,10 @@ size_t shape_overhead(int nA, int codes_k) {
   return scan_smem_bytes2(kTmemSlots, nA, 0, 0, std::max(codes_k, 16));
 }
 
-bool pick_launch_shape(const krux_ctx *ctx, int kpad, int codes_k, LaunchShape &sh) {
+// reserve: shared memory kept free for the plain form's hit-event ring (0 when
+// the call cannot take that form).
+bool pick_launch_shape(const krux_ctx *ctx, int kpad, int codes_k, LaunchShape &sh,
+                       size_t reserve = 0) {
   const size_t chunk = (size_t)256 * kpad;
   if (ctx->tune_nc > 0) {  // explicit shape (tests, autotuner)
     sh.ka = ctx->tune_ka > 0 ? ctx->tune_ka : kpad;
@@ -279,6 +283,21 @@ bool pick_launch_shape(const krux_ctx *ctx, int kpad, int codes_k, LaunchShape &
     sh.force_nc = ctx->tune_nc;
     if (sh.ka % 64 != 0 && sh.ka != kpad) return false;
     return shape_overhead(sh.nA, codes_k) + (size_t)sh.nA * 256 * sh.ka + sh.b_region <= kSmemLimit;
+  }
+  if (reserve > 0) {  // the plain form: whole K per stage and an even number of chunks
+    int best = 0;
+    for (int a = 3; a >= 2; --a) {
+      const size_t used = shape_overhead(a, codes_k) + (size_t)a * chunk + reserve;
+      if (used >= kSmemLimit) continue;
+      const int ncf = (int)std::min<size_t>(kTmemSlots, (kSmemLimit - used) / chunk) & ~1;
+      if (ncf > best) {
+        best = ncf;
+        sh.ka = kpad;
+        sh.nA = a;
+        sh.b_region = (int)(ncf * chunk);
+      }
+    }
+    if (best >= 2) return true;
   }
   for (int a = 3; a >= 2; --a) {  // whole K per stage
     const size_t used = shape_overhead(a, codes_k) + (size_t)a * chunk;
@@ -519,7 +538,7 @@ void krux_destroy(krux_ctx *ctx) {
                     &ctx->list, &ctx->gemm_out, &ctx->bucket_ranks, &ctx->permA, &ctx->minpkey, &ctx->seg,
                     &ctx->permNan, &ctx->aux2, &ctx->param, &ctx->paramOut, &ctx->packjobs,
                     &ctx->host_in, &ctx->host_out, &ctx->groups2, &ctx->items2, &ctx->packjobs2,
-                    &ctx->cfacptr2};
+                    &ctx->cfacptr2, &ctx->mcand};
   for (DevBuf *b : bufs) b->release();
   ctx->list_host.release();
   for (auto &pb : ctx->pool) cudaFree(pb.second);
@@ -762,6 +781,8 @@ struct ScanGroupIn {
   double *dense_H = nullptr, *dense_p = nullptr;
   int64_t dense_ld = 0, dense_snp0 = 0;
   double *minp_key = nullptr;
+  uint32_t *minp_bound = nullptr;     // the plain form's bounds beside the keys
+  unsigned long long *minp_seed = nullptr;  // and its seed pass's records
   int bucket = -1;                    // index into the call's bucket rank sets
   // tensor map of A: groups whose rank matrices sit back to back in one buffer
   // (missing-pattern buckets of one rank set) share it, each at row a_row0
@@ -1102,13 +1123,17 @@ krux_status prepare_fused(krux_ctx *ctx, CallPlan &cp, const krux_opts *o, Fused
     kpad = std::max(kpad, round_up(g.rs->Np, atom));
     if (g.nan_cnt) codes_k = std::max(codes_k, g.rs->Np);
   }
+  // a call that can take the plain form keeps room for its hit-event ring
+  bool fast_shape = layout == 1 && !cp.multi && cp.param.model < 0 && o->dense_H == nullptr &&
+                    !cp.cis.on;
+  for (auto &g : cp.groups) fast_shape = fast_shape && g.nan_cnt == nullptr;
   LaunchShape sh;
   {
     const int s_nc = ctx->tune_nc, s_nA = ctx->tune_nA, s_ka = ctx->tune_ka;
     ctx->tune_nc = tnc;
     ctx->tune_nA = tnA;
     ctx->tune_ka = tka;
-    const bool ok = pick_launch_shape(ctx, kpad, codes_k, sh);
+    const bool ok = pick_launch_shape(ctx, kpad, codes_k, sh, fast_shape ? kEvRegion : 0);
     ctx->tune_nc = s_nc;
     ctx->tune_nA = s_nA;
     ctx->tune_ka = s_ka;
@@ -1203,6 +1228,8 @@ krux_status prepare_fused(krux_ctx *ctx, CallPlan &cp, const krux_opts *o, Fused
     d.dense_ld = g.dense_ld;
     d.dense_snp0 = g.dense_snp0;
     d.minp_key = g.minp_key;
+    d.minp_bound = g.minp_bound;
+    d.minp_seed = g.minp_seed;
     d.T = rs->T;
     d.N = rs->N;
     d.Np = rs->Np;
@@ -1311,8 +1338,8 @@ krux_status prepare_fused(krux_ctx *ctx, CallPlan &cp, const krux_opts *o, Fused
   // in one rank stage, complete data, no dense output, cis window, provisional
   // hits, permutations or markers with more than three groups
   {
-    bool fast = layout == 1 && !p.multi && !p.perm && !p.has_nan && !p.dense && !p.provisional &&
-                !p.signed_coef && p.cis_window < 0;
+    bool fast = layout == 1 && !p.multi && !p.has_nan && !p.dense && !p.provisional &&
+                (!p.signed_coef || p.perm) && p.cis_window < 0;
     for (const GroupDesc &d : descs) fast = fast && d.pair == 1 && d.nkb == 1;
     p.fast = fast ? 1 : 0;
   }
@@ -1339,6 +1366,17 @@ krux_status prepare_fused(krux_ctx *ctx, CallPlan &cp, const krux_opts *o, Fused
   if (p.fast) {  // the plain scan form also holds its ring of hit-event buffers
     if (fl.smem + kEvRegion <= kSmemLimit) fl.smem += kEvRegion;
     else p.fast = 0;
+  }
+  if (p.fast && p.perm && !cp.perm.seed && fl.grid > 0) {
+    // each event warp's list for the deferred FP64 pass: about three times the
+    // pairs a 200k-SNP batch passes on, at least 8192 and at most 65536 entries
+    const int64_t per = (int64_t)48 * cp.perm.P * cp.perm.rs->rows_pad / (2 * fl.grid);
+    const int cap = (int)std::min<int64_t>(65536, std::max<int64_t>(8192, per));
+    const size_t lists = (size_t)2 * fl.grid * cap * sizeof(MinpPair);
+    KRUX_CUDA(ctx, ctx->mcand.ensure(lists + (size_t)2 * fl.grid * 4 + 256));
+    p.mc_list = ctx->mcand.as<MinpPair>();
+    p.mc_cnt = reinterpret_cast<unsigned int *>(ctx->mcand.as<char>() + lists);
+    p.mc_cap = cap;
   }
   const std::string why = validate_plan(p, descs, fl.smem);
   if (!why.empty()) return fail(ctx, KRUX_EUNSUPPORTED, "%s", why.c_str());
@@ -1371,7 +1409,7 @@ krux_status enqueue_fused(krux_ctx *ctx, CallPlan &cp, const FusedLaunch &fl, cu
     KRUX_CUDA(ctx, cudaMemcpyAsync(pj.stack, rs->dev.A, one * 2, cudaMemcpyDeviceToDevice, s));
     KRUX_CUDA(ctx, launch_permute_rows(rs->dev.A, pj.stack + one, rs->rows_pad, rs->Np, rs->N,
                                        pj.perms, pj.P, status, s));
-    KRUX_CUDA(ctx, cudaMemsetAsync(ctx->minpkey.p, 0, (size_t)pj.P * rs->rows_pad * 8, s));
+    KRUX_CUDA(ctx, cudaMemsetAsync(ctx->minpkey.p, 0, (size_t)pj.P * rs->rows_pad * 32, s));
     if (pj.lists) {
       // NaN samples of permutation q sit at inv_q(original position)
       const size_t lst = (size_t)rs->T * rs->N;
@@ -1406,6 +1444,8 @@ krux_status enqueue_fused(krux_ctx *ctx, CallPlan &cp, const FusedLaunch &fl, cu
                                   status, s));
   }
   ev_record(ctx, 3, s);
+  if (fl.p.mc_cnt)
+    KRUX_CUDA(ctx, cudaMemsetAsync(fl.p.mc_cnt, 0, (size_t)2 * fl.grid * 4, s));
   ev_record(ctx, 7, s);  // the scan kernel alone: events 7 .. 4
   if (fl.grid > 0) KRUX_CUDA(ctx, launch_scan_only(fl.p, fl.grid, fl.smem, s));
   ev_record(ctx, 4, s);
@@ -1443,9 +1483,22 @@ krux_status enqueue_fused(krux_ctx *ctx, CallPlan &cp, const FusedLaunch &fl, cu
                                        cp.fdr_w));
   }
   ev_record(ctx, 6, s);
+  if (fl.p.mc_list)  // the pairs the event warps passed on, decided in FP64
+    KRUX_CUDA(ctx, launch_minp_cands(fl.p.mc_list, fl.p.mc_cnt, 2 * fl.grid, fl.p.mc_cap,
+                                     cp.perm.rs->dev.cfac, cp.perm.rs->rows_pad, fl.p.pthresh,
+                                     ctx->minpkey.as<double>(), cp.fdr_hist, cp.fdr_bins, cp.fdr_l0,
+                                     cp.fdr_w, s));
   if (cp.perm.on && !cp.perm.seed)
     KRUX_CUDA(ctx, launch_minp_from_key(ctx->minpkey.as<double>(), cp.perm.minp, cp.perm.P,
                                         cp.perm.rs->T, cp.perm.rs->rows_pad, s));
+  if (cp.perm.on && cp.perm.seed && fl.p.fast) {  // the plain form's seed records, decided
+    const ScanGroupIn &g = cp.groups[0];
+    const krux_rankset *rs = cp.perm.rs;
+    KRUX_CUDA(ctx, launch_seed_decide(g.minp_seed, cp.perm.stack, rs->rows_pad, rs->Np, rs->N, rs->T,
+                                      cp.perm.P, g.geno, g.ldg, g.snp_begin, g.n_snps,
+                                      ctx->meta.as<ChunkMeta>() + fl.moff[0], rs->dev.cfac,
+                                      g.minp_key, g.minp_bound, s));
+  }
   return KRUX_OK;
 }
 
@@ -1457,7 +1510,13 @@ int fused_launches(const CallPlan &cp, const FusedLaunch &fl) {
     for (auto &g : cp.groups) n += g.nan_cnt ? 2 : 1;
   for (auto &os : cp.slots) n += (os.capacity > 0 && cp.param.model < 0) ? 1 : 0;
   if (cp.param.model >= 0) n += 2;
-  if (cp.perm.on) n += 2 + (cp.perm.lists ? 2 : 0);
+  if (cp.perm.on) {
+    // the permuted stack (and NaN lists) unless a seed pass built them; then the
+    // minimum-p read-out, or after a plain-form seed pass its exact decisions
+    if (!cp.perm.pre_done) n += 1 + (cp.perm.lists ? 2 : 0);
+    if (!cp.perm.seed || fl.p.fast) n += 1;
+    if (fl.p.mc_list) n += 1;
+  }
   return n;
 }
 
@@ -1486,6 +1545,7 @@ krux_status finish_fused(krux_ctx *ctx, CallPlan &cp, const FusedLaunch &fl, cud
     ctx->prof.ms_scan = ev_ms(ctx, 7, 4);
     ctx->prof.ms_finalize = ev_ms(ctx, 5, 6);
     ctx->prof.scan_grid = fl.grid;
+    ctx->prof.scan_form = scan_form_of(fl.p);
     ctx->prof.launches += fused_launches(cp, fl);
   }
   return device_status(ctx, hst);
@@ -1509,11 +1569,16 @@ krux_status run_fused(krux_ctx *ctx, CallPlan &cp, const krux_opts *o, cudaStrea
 // starts from running minima over thousands of SNPs instead of none (without it
 // the first wave of CTAs refines nearly every chunk in FP64).  False when the
 // call is too small to gain from one.
-bool make_seed_plan(const CallPlan &cp, CallPlan &seed) {
+bool make_seed_plan(const CallPlan &cp, CallPlan &seed, bool plain_form) {
   constexpr int64_t kSeedSnps = 16384;
   if (cp.groups.size() != 1 || cp.groups[0].n_snps <= 4 * kSeedSnps) return false;
   seed = cp;
-  seed.groups[0].n_snps = kSeedSnps;
+  // the plain form decides every pair past its bounds exactly, so its seed covers a
+  // quarter of the SNPs (whole chunks): about three later pairs per class then
+  // beat the seed's best instead of eleven
+  seed.groups[0].n_snps =
+      plain_form ? std::max<int64_t>(kSeedSnps, cp.groups[0].n_snps / 4 / kChunkSnps * kChunkSnps)
+                 : kSeedSnps;
   seed.slots[0].capacity = 0;
   seed.fdr_hist = nullptr;
   seed.perm.seed = true;
@@ -1968,7 +2033,9 @@ static krux_status plan_permute(krux_ctx *ctx, CallPlan &cp, const krux_rankset 
   const int64_t b = opts->snp_begin, e = opts->snp_end > 0 ? opts->snp_end : S;
   const size_t one = (size_t)rs->rows_pad * rs->Np;
   KRUX_CUDA(ctx, ctx->permA.ensure(one * 2 * (size_t)(1 + P)));
-  KRUX_CUDA(ctx, ctx->minpkey.ensure((size_t)P * rs->rows_pad * 8));
+  // [P][rows_pad] FP64 keys, then the plain form's [P][rows_pad][2] FP32 bounds and
+  // [P][rows_pad][2] 64-bit seed records
+  KRUX_CUDA(ctx, ctx->minpkey.ensure((size_t)P * rs->rows_pad * 32));
   KRUX_CUDA(ctx, ctx->aux.ensure((size_t)std::max<int64_t>(opts->hit_capacity, 1) * sizeof(HitAux)));
   cp.slots.push_back(OutSlot{hits, hit_H, hit_p, opts->hit_capacity, ctx->aux.as<HitAux>()});
   cp.fdr_hist = reinterpret_cast<unsigned long long *>(fdr_hist);
@@ -1985,6 +2052,12 @@ static krux_status plan_permute(krux_ctx *ctx, CallPlan &cp, const krux_rankset 
   krux_status st = plan_groups(ctx, cp, rs, geno, ldg, b, e, cp.perm.stack, 1 + P, 0, nullptr,
                                nullptr, ctx->minpkey.as<double>(), s);
   if (st != KRUX_OK) return st;
+  for (auto &g : cp.groups)
+    if (g.minp_key) {
+      g.minp_bound = reinterpret_cast<uint32_t *>(ctx->minpkey.as<double>() + (size_t)P * rs->rows_pad);
+      g.minp_seed = reinterpret_cast<unsigned long long *>(ctx->minpkey.as<double>() +
+                                                           (size_t)2 * P * rs->rows_pad);
+    }
   if (rs->has_nan) {
     const size_t lst = (size_t)rs->T * rs->N;
     const size_t inv_off = (lst * 2 * (size_t)(1 + P) + 255) / 256 * 256;
@@ -2042,10 +2115,10 @@ extern "C" krux_status krux_permute(krux_ctx *ctx, const krux_rankset *rs, const
   // share), the seed pass into the second table set, then both are enqueued back
   // to back with no host synchronisation between them
   CallPlan seed;
-  const bool with_seed = make_seed_plan(cp, seed);
   FusedLaunch fm, fs;
   st = prepare_fused(ctx, cp, opts, fm, s, 0);
   if (st != KRUX_OK) return st;
+  const bool with_seed = make_seed_plan(cp, seed, fm.p.fast != 0);
   if (with_seed) {
     st = prepare_fused(ctx, seed, opts, fs, s, 1);
     if (st != KRUX_OK) return st;
@@ -2133,6 +2206,7 @@ krux_status graph_capture(krux_ctx *ctx, krux_graph *g) {
     return fail(ctx, KRUX_EUNSUPPORTED, "graphs take complete genotypes (no -1 codes)");
   krux_status st = prepare_fused(w, g->cp, &g->opts, g->fl, g->cs);
   if (st != KRUX_OK) return st;
+  if (g->with_seed) g->with_seed = make_seed_plan(g->cp, g->seed_cp, g->fl.p.fast != 0);
   if (g->with_seed) {
     st = prepare_fused(w, g->seed_cp, &g->opts, g->seed_fl, g->cs, 1);
     if (st != KRUX_OK) return st;
@@ -2230,7 +2304,7 @@ extern "C" krux_status krux_graph_permute(krux_ctx *ctx, const krux_rankset *rs,
   g->opts = *opts;
   st = plan_permute(g->w, g->cp, rs, geno, S, ldg, perms, P, opts, minp, hits, hit_H, hit_p,
                     fdr_hist, fdr_bins, fdr_bin_width, g->cs);
-  if (st == KRUX_OK) g->with_seed = make_seed_plan(g->cp, g->seed_cp);
+  if (st == KRUX_OK) g->with_seed = true;  // the plan is made once the main launch is prepared
   if (st == KRUX_OK) st = graph_capture(ctx, g);
   if (st != KRUX_OK) return graph_fail(ctx, g, st);
   *out = g;

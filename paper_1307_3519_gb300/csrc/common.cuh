@@ -50,6 +50,17 @@ static_assert(4 * (kFastRegsLaunch - kFastRegsLow) >= kFastEpiWarps * (kFastRegs
 // entry's pairs (FP64 inside the band) and appends the hit records.
 constexpr int kEvSnps = kFastSnps / 2;  // 16
 constexpr int kEvEntries = 32;
+// A permuted pair the event warps passed on for its FP64 -ln p, decided after the
+// launch: exact centred sums, group sizes, trait, and rank-matrix group | FDR-band
+// flag << 16.
+struct MinpPair {
+  int32_t u, v;
+  uint32_t n01, n2df;
+  int32_t trait;
+  int32_t agb;
+};
+static_assert(sizeof(MinpPair) == 24, "MinpPair is 24 bytes");
+
 struct EvEntry {
   float u[kEvSnps], v[kEvSnps];                 // D_0, D_1 of SNP j for this trait
   float alpha[kEvSnps], beta[kEvSnps], gamma[kEvSnps];  // the SNPs' fast-test coefficients
@@ -60,7 +71,8 @@ struct EvEntry {
   float tau;                                    // its fast-test bound
   int32_t trait;                                // its trait row
   int32_t group;
-  int32_t pad_[3];
+  int32_t ag;                                   // rank-matrix group (> 0: a permutation)
+  float b1, b2;                                 // permutation: the submitting lane's bounds
 };
 static_assert(sizeof(EvEntry) % 16 == 0, "event entries keep 16-byte alignment");
 // shared memory of the ring: alignment slack, entries, a full barrier and a
@@ -210,6 +222,10 @@ struct alignas(64) GroupDesc {
   unsigned long long *counter;  // hits found (keeps counting past capacity)
   double *dense_H, *dense_p;    // optional [T][dense_ld]
   double *minp_key;         // permutation mode: [n_agroups-1][rows_per_agroup] best -ln p (as double bits)
+  uint32_t *minp_bound;     // plain-form permutations: [n_agroups-1][rows_per_agroup][2] float bits
+                            // of the largest df-1 |value| and df-2 value decided so far
+  unsigned long long *minp_seed;  // their seed pass: [n_agroups-1][rows_per_agroup][2]
+                            // (float bits of the largest value << 32) | (its 16-SNP block + 1)
   int64_t capacity;
   int64_t dense_ld;
   int64_t dense_snp0;       // SNP index of dense column 0
@@ -276,8 +292,14 @@ struct ScanParams {
   int32_t seed_bound = 0;
   // some group's rank set has NaN (its traits get the exact-size hot test)
   int32_t has_nan = 0;
+  // plain-form permutation batches: each event warp's list of pairs for the
+  // deferred FP64 pass ([grid][2][mc_cap]) and its count ([grid][2])
+  MinpPair *mc_list = nullptr;
+  unsigned int *mc_cnt = nullptr;
+  int32_t mc_cap = 0;
   // the plain scan form applies: 32-byte swizzle, every group's chunks paired, no
-  // NaN, no dense output, no cis window, no provisional hits, no permutations
+  // NaN, no dense output, no cis window, no provisional hits (permutation batches
+  // take its two-sided variant)
   int32_t fast = 0;
 };
 
@@ -310,6 +332,18 @@ cudaError_t launch_seg_compact(const krux_hit *seg_hits, const HitAux *seg_aux,
                                unsigned long long *total, cudaStream_t s);
 cudaError_t launch_minp_from_key(const double *key, double *minp, int P, int T, int ld,
                                  cudaStream_t s);
+// After a plain-form permutation launch: the FP64 -ln p of every pair the event
+// warps passed on, folded into the keys and, in the FDR band, into the histogram.
+cudaError_t launch_minp_cands(const MinpPair *list, const unsigned int *cnt, int n_lists, int cap,
+                              const double *cfac, int rows_pad, double pthresh, double *key,
+                              unsigned long long *fdr_hist, int fdr_bins, double fdr_l0,
+                              double fdr_w, cudaStream_t s);
+// After a plain-form seed pass: decides, per (permutation, trait, class), the pair
+// with the seed's largest value exactly (see seed_decide_kernel).
+cudaError_t launch_seed_decide(const unsigned long long *rec, const __half *stack, int rows_pad,
+                               int Np, int N, int T, int P, const int8_t *geno, int64_t ldg,
+                               int64_t snp_begin, int64_t n_snps, const ChunkMeta *meta,
+                               const double *cfac, double *key, uint32_t *bound, cudaStream_t s);
 cudaError_t launch_pad_traits(int T, int rows_pad, float *tau, double *cfac, uint16_t *nan_cnt,
                               cudaStream_t s);
 // Uploads the 1/n table the finalisation uses (once per device; not during a
@@ -323,6 +357,7 @@ cudaError_t launch_finalize_dev(const krux_hit *hits, const HitAux *aux, const H
                                 int sm_count, cudaStream_t s, unsigned long long *fdr_hist,
                                 int fdr_bins, double fdr_l0, double fdr_w);
 cudaError_t scan_set_smem(size_t smem);
+int scan_form_of(const ScanParams &p);
 cudaError_t launch_scan_only(const ScanParams &p, int grid, size_t smem, cudaStream_t s);
 cudaError_t launch_finalize(const krux_hit *hits, const HitAux *aux, int64_t n,
                             const double *const *cfac_by_group, double *H, double *p,

@@ -857,6 +857,82 @@ __device__ __forceinline__ bool hit_fast_w(const uint32_t (&d0)[NS], const uint3
   return (int)(acc0 & acc1) >= 0;
 }
 
+// Two-sided hot test of a permutation batch, whose df-1 SNPs carry a negated form
+// value s (signed coefficients): true when some pair has s >= b2 (df 2) or
+// s <= -b1 (df 1), with nb2 = -b2 and sb = b1 + b2 (both finite); two SNPs per
+// packed instruction, as hit_fast_w.
+template <int NS>
+__device__ __forceinline__ bool hit_fast_w2(const uint32_t (&d0)[NS], const uint32_t (&d1)[NS],
+                                            const ChunkMeta &m, int off, float nb2, float sb) {
+  const uint64_t nt2 = pk2(__float_as_uint(nb2), __float_as_uint(nb2));
+  const uint64_t sb2 = pk2(__float_as_uint(sb), __float_as_uint(sb));
+  uint32_t hi = 0xffffffffu, lo = 0u;  // AND of the signs of s - b2, OR of those of s + b1
+#pragma unroll
+  for (int b = 0; b < NS / 16; ++b) {
+    const uint64_t *al = reinterpret_cast<const uint64_t *>(m.alpha + off + 16 * b);
+    const uint64_t *be = reinterpret_cast<const uint64_t *>(m.beta + off + 16 * b);
+    const uint64_t *ga = reinterpret_cast<const uint64_t *>(m.gamma + off + 16 * b);
+#pragma unroll
+    for (int j = 0; j < 8; j += 2) {
+      const ulonglong2 A = *reinterpret_cast<const ulonglong2 *>(al + j);
+      const ulonglong2 B = *reinterpret_cast<const ulonglong2 *>(be + j);
+      const ulonglong2 G = *reinterpret_cast<const ulonglong2 *>(ga + j);
+#pragma unroll
+      for (int t = 0; t < 2; ++t) {
+        const int jj = 16 * b + 2 * (j + t);
+        const uint64_t u2 = pk2(d0[jj], d0[jj + 1]);
+        const uint64_t v2 = pk2(d1[jj], d1[jj + 1]);
+        const uint64_t a2 = t ? A.y : A.x, b2 = t ? B.y : B.x, g2 = t ? G.y : G.x;
+        const uint64_t w2 = ffma2(b2, v2, u2);
+        const uint64_t e2 = fmul2(g2, v2);
+        uint64_t q2 = ffma2(e2, v2, nt2);
+        q2 = ffma2(fmul2(a2, w2), w2, q2);
+        const uint64_t r2 = fadd2(q2, sb2);
+        uint32_t qa, qb, ra, rb;
+        upk2(q2, qa, qb);
+        upk2(r2, ra, rb);
+        hi &= qa & qb;
+        lo |= ra | rb;
+      }
+    }
+    if (b + 1 < NS / 16) asm volatile("" ::: "memory");
+  }
+  return (int)hi >= 0 || (int)lo < 0;
+}
+
+// Seed pass of a permutation batch in the plain form: the largest df-2 value and
+// the most negative df-1 value of NS SNPs for this lane's trait, into smax / smin.
+template <int NS>
+__device__ __forceinline__ void range_w(const uint32_t (&d0)[NS], const uint32_t (&d1)[NS],
+                                        const ChunkMeta &m, int off, float &smax, float &smin) {
+#pragma unroll
+  for (int b = 0; b < NS / 16; ++b) {
+    const uint64_t *al = reinterpret_cast<const uint64_t *>(m.alpha + off + 16 * b);
+    const uint64_t *be = reinterpret_cast<const uint64_t *>(m.beta + off + 16 * b);
+    const uint64_t *ga = reinterpret_cast<const uint64_t *>(m.gamma + off + 16 * b);
+#pragma unroll
+    for (int j = 0; j < 8; j += 2) {
+      const ulonglong2 A = *reinterpret_cast<const ulonglong2 *>(al + j);
+      const ulonglong2 B = *reinterpret_cast<const ulonglong2 *>(be + j);
+      const ulonglong2 G = *reinterpret_cast<const ulonglong2 *>(ga + j);
+#pragma unroll
+      for (int t = 0; t < 2; ++t) {
+        const int jj = 16 * b + 2 * (j + t);
+        const uint64_t u2 = pk2(d0[jj], d0[jj + 1]);
+        const uint64_t v2 = pk2(d1[jj], d1[jj + 1]);
+        const uint64_t a2 = t ? A.y : A.x, b2 = t ? B.y : B.x, g2 = t ? G.y : G.x;
+        const uint64_t w2 = ffma2(b2, v2, u2);
+        const uint64_t e2 = fmul2(g2, v2);
+        const uint64_t s2 = ffma2(fmul2(a2, w2), w2, fmul2(e2, v2));
+        uint32_t sa, sb;
+        upk2(s2, sa, sb);
+        smax = fmax3(smax, __uint_as_float(sa), __uint_as_float(sb));
+        smin = fmin3(smin, __uint_as_float(sa), __uint_as_float(sb));
+      }
+    }
+  }
+}
+
 // ---- hit events of the plain scan form, handled by the event warps ---------
 // Several epilogue warps claim tickets at once, so one of them may claim an
 // entry's use k while uses k-1, k-2 are still pending: a phase-parity wait
@@ -903,8 +979,8 @@ __device__ __forceinline__ bool ev_gate(const EvRing &ev, unsigned long long t, 
 __device__ __forceinline__ bool ev_submit(const EvRing &ev, const uint32_t (&u)[kEvSnps],
                                           const uint32_t (&v)[kEvSnps], bool need,
                                           const ChunkMeta &m, int off, float tau, double cfac,
-                                          int trait, int group, const ScanParams &p,
-                                          uint32_t abort_addr, int lane) {
+                                          int trait, int group, int ag, float b1, float b2,
+                                          const ScanParams &p, uint32_t abort_addr, int lane) {
   uint32_t lanes = __ballot_sync(0xffffffffu, need);
   unsigned long long t = 0;
   if (lane == 0) t = atomicAdd(ev.word, (unsigned long long)__popc(lanes)) & kEvTicketMask;
@@ -944,6 +1020,9 @@ __device__ __forceinline__ bool ev_submit(const EvRing &ev, const uint32_t (&u)[
       E.tau = tau;
       E.trait = trait;
       E.group = group;
+      E.ag = ag;
+      E.b1 = b1;
+      E.b2 = b2;
     }
     __threadfence_block();
     __syncwarp();
@@ -961,7 +1040,99 @@ struct EvGroup {
   unsigned long long *counter;
   int64_t capacity;
   uint16_t gid;
+  double *minp_key;
+  uint32_t *minp_bound;
+  int64_t rows;
 };
+
+__device__ __forceinline__ void ev_group(EvGroup &G, const ScanParams &p, int group) {
+  if (group == G.index) return;
+  const GroupDesc &g = p.groups[group];
+  G.index = group;
+  G.hits = g.hits;
+  G.aux = g.aux;
+  G.counter = g.counter;
+  G.capacity = g.capacity;
+  G.gid = (uint16_t)g.group_id;
+  G.minp_key = g.minp_key;
+  G.minp_bound = g.minp_bound;
+  G.rows = g.rows_per_agroup;
+}
+
+// A permuted pair's entry (section "P-value calculation and empirical FDR
+// correction": the minimum p of each permuted trait over all SNPs): lanes j <
+// kEvSnps take the pairs past the submitting lane's bounds, decide them on their
+// FP64 -ln p, raise the trait's key to the largest, and raise its class bounds
+// (largest df-1 |s| and df-2 s of the pairs decided, less the margin: a later
+// pair of the class below them cannot beat those pairs).  With the FDR histogram
+// on, every pair at or above the band with p < P_c is counted in row ag.
+__device__ __forceinline__ void ev_minp(const EvEntry &E, EvGroup &G, const ScanParams &p, int lane,
+                                        float s, unsigned int &mcn, int ev_warp) {
+  const int j = lane & (kEvSnps - 1);
+  const bool valid = lane < kEvSnps && E.snp[j] >= 0;
+  // E.b1, E.b2: the classes' largest decided values when the entry was filled;
+  // values equal to them are copies of decided pairs (or tie them within an ulp)
+  const float keep = 1.f - p.margin;
+  const float b1 = E.b1, b2 = E.b2;
+  bool cand = valid && ((s > b2 * keep && s != b2) || (-s > b1 * keep && -s != b1));
+  // within a class the key grows with the value: only the entry's largest value
+  // of each class, and values within the margin of it, can hold the class's best
+  float c1 = cand && s < 0.f ? -s : 0.f, c2 = cand && s > 0.f ? s : 0.f;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    c1 = fmaxf(c1, __shfl_xor_sync(0xffffffffu, c1, o));
+    c2 = fmaxf(c2, __shfl_xor_sync(0xffffffffu, c2, o));
+  }
+  cand = cand && (s > 0.f ? s >= c2 * keep : -s >= c1 * keep);
+  const bool band = valid && p.fdr_hist != nullptr && fabsf(s) >= E.tau * (1.f - p.margin);
+  const bool need = cand || band;
+  const uint32_t bal = __ballot_sync(0xffffffffu, need);
+  const unsigned int n = (unsigned int)__popc(bal);
+  const uint32_t n01 = E.n01[j], n2df = E.n2df[j];
+  if (mcn + n <= (unsigned int)p.mc_cap) {
+    // the list has room: the FP64 work runs after the launch, in parallel
+    if (need) {
+      MinpPair r;
+      r.u = (int32_t)E.u[j];
+      r.v = (int32_t)E.v[j];
+      r.n01 = n01;
+      r.n2df = n2df;
+      r.trait = E.trait;
+      r.agb = E.ag | (band ? 1 << 16 : 0) | (cand ? 1 << 17 : 0);
+      const size_t base = ((size_t)blockIdx.x * 2 + ev_warp) * (size_t)p.mc_cap;
+      p.mc_list[base + mcn + (unsigned int)__popc(bal & ((1u << lane) - 1u))] = r;
+    }
+    mcn += n;
+  } else {
+    // full: decide here
+    double key = -1.0;
+    if (need) {
+      const int df = (int)(n2df >> 16);
+      if (df > 0 && E.cfac > 0.0)
+        key = key64_of(kw_H64((int)E.u[j], (int)E.v[j], (int)(n01 & 0xffffu), (int)(n01 >> 16),
+                              (int)(n2df & 0xffffu), E.cfac),
+                       df);
+    }
+    if (band && key > -log(p.pthresh))
+      atomicAdd(p.fdr_hist + (int64_t)E.ag * p.fdr_bins + fdr_bin(key, p.fdr_l0, p.fdr_w, p.fdr_bins),
+                1ull);
+    double kmax = cand ? key : -1.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) kmax = fmax(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
+    if (lane == 0 && kmax > 0.0) {
+      ev_group(G, p, E.group);
+      atomicMax(reinterpret_cast<unsigned long long *>(G.minp_key + (int64_t)(E.ag - 1) * G.rows +
+                                                       E.trait),
+                (unsigned long long)__double_as_longlong(kmax));
+    }
+  }
+  if (lane == 0) {
+    ev_group(G, p, E.group);
+    const int64_t idx = (int64_t)(E.ag - 1) * G.rows + E.trait;
+    if (c1 > b1) atomicMax(G.minp_bound + 2 * idx, __float_as_uint(c1));
+    if (c2 > b2) atomicMax(G.minp_bound + 2 * idx + 1, __float_as_uint(c2));
+  }
+}
 
 // An event warp's work on one entry: lanes j < kEvSnps classify the pair (trait,
 // SNP j) in the same FP32 form as the hot test (at or above the upper band edge:
@@ -969,14 +1140,24 @@ struct EvGroup {
 // appended in SNP order, one record per lane, into this warp's staging region of
 // kEpiWarps / 2 segments of the CTA (`wn` records already there); what does not
 // fit goes to the group's list through its counter.  Returns the number of hits.
+template <bool kPerm>
 __device__ __forceinline__ unsigned int ev_process(const EvEntry &E, EvGroup &G, const ScanParams &p,
-                                                   unsigned int wn, int lane, int ev_warp) {
+                                                   unsigned int wn, int lane, int ev_warp,
+                                                   unsigned int &mcn) {
   const int j = lane & (kEvSnps - 1);
   const bool act = lane < kEvSnps;
   const float tau = E.tau;
   const float u = E.u[j], v = E.v[j];
   const float w = fmaf(E.beta[j], v, u);
-  const float s = fmaf(E.alpha[j] * w, w, (E.gamma[j] * v) * v);
+  const float sv = fmaf(E.alpha[j] * w, w, (E.gamma[j] * v) * v);
+  float s = sv;
+  if constexpr (kPerm) {
+    if (E.ag > 0) {  // a permuted pair: min-p and FDR work, no hit record
+      ev_minp(E, G, p, lane, sv, mcn, ev_warp);
+      return 0u;
+    }
+    s = fabsf(sv);  // df-1 values are negated in permutation batches
+  }
   const bool cand = act && s + -tau * (1.f - p.margin) >= 0.f;
   bool hit = cand && s + -tau * (1.f + p.margin) >= 0.f;
   const uint32_t n01 = E.n01[j], n2df = E.n2df[j];
@@ -988,15 +1169,7 @@ __device__ __forceinline__ unsigned int ev_process(const EvEntry &E, EvGroup &G,
   const uint32_t bal = __ballot_sync(0xffffffffu, hit);
   const unsigned int n = (unsigned int)__popc(bal);
   if (n == 0u) return 0u;
-  if (E.group != G.index) {
-    const GroupDesc &g = p.groups[E.group];
-    G.index = E.group;
-    G.hits = g.hits;
-    G.aux = g.aux;
-    G.counter = g.counter;
-    G.capacity = g.capacity;
-    G.gid = (uint16_t)g.group_id;
-  }
+  ev_group(G, p, E.group);
   constexpr int kSegs = kEpiWarps / 2;  // staging segments per event warp
   const unsigned int cap = (unsigned int)(kSegs * p.seg_cap);
   const unsigned int over_from = wn > cap ? wn : cap;  // first index beyond the region
@@ -1352,16 +1525,18 @@ __device__ __noinline__ double minp_step_best(MinpLead *L, double cfac) {
 // plain scan of rank sets with NaN (exact group sizes in the hot test); the
 // producer and MMA warps are the same in all four.  Separate forms keep the
 // state of one out of the registers of the others.
-enum ScanForm { kFormScan = 0, kFormMulti = 1, kFormPerm = 2, kFormNan = 3 };
+enum ScanForm { kFormScan = 0, kFormMulti = 1, kFormPerm = 2, kFormNan = 3, kFormScanPerm = 4 };
+// the plain scan form and its two-sided variant for permutation batches
+constexpr bool fast_form(int f) { return f == kFormScan || f == kFormScanPerm; }
 
 // Warp roles of a kernel form: the epilogue warps first, then the producer and
 // the MMA issuer (the plain scan form also has two idle warps after them).
 template <int kForm>
 struct ScanRoles {
-  static constexpr int kEpi = kForm == kFormScan ? kFastEpiWarps : kEpiWarps;
+  static constexpr int kEpi = fast_form(kForm) ? kFastEpiWarps : kEpiWarps;
   static constexpr int kProducer = kEpi;
   static constexpr int kMma = kEpi + 1;
-  static constexpr int kThreads = kForm == kFormScan ? kFastThreads : kScanThreads;
+  static constexpr int kThreads = fast_form(kForm) ? kFastThreads : kScanThreads;
 };
 
 template <int kForm>
@@ -1435,7 +1610,7 @@ __global__ void __launch_bounds__(ScanRoles<kForm>::kThreads, 1)
       mbar_init(tc_empty(e), R::kEpi);
     }
     *abort_flag = 0;
-    if constexpr (kForm == kFormScan) {
+    if constexpr (fast_form(kForm)) {
       for (int e = 0; e < kEvEntries; ++e) {
         mbar_init(ev.full(e), 1);
         ev.released[e] = 0u;
@@ -1461,7 +1636,7 @@ __global__ void __launch_bounds__(ScanRoles<kForm>::kThreads, 1)
   // the epilogue warps; each role's code sits under its own setmaxnreg
 
   if (warp == R::kProducer) {
-    if constexpr (kForm == kFormScan)
+    if constexpr (fast_form(kForm))
       asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kFastRegsLow) : "memory");
     if (lane == 0) {
       uint32_t a_stage = 0, a_phase = 0, b_bits = 0;
@@ -1529,9 +1704,14 @@ __global__ void __launch_bounds__(ScanRoles<kForm>::kThreads, 1)
             mbar_expect_tx(tc_full(tc_e), tx);
             bulk_load(dst, g->tau + r0, 512u, tc_full(tc_e));
             bulk_load(dst + 512u, g->cfac + r0, 1024u, tc_full(tc_e));
-            if (with_key)
-              bulk_load(dst + 1536u, g->minp_key + (int64_t)(ag - 1) * g->rows_per_agroup + r0, 1024u,
-                        tc_full(tc_e));
+            if (with_key) {
+              const int64_t kr = (int64_t)(ag - 1) * g->rows_per_agroup + r0;
+              // the two-sided plain form reads the class bounds, the others the key
+              if constexpr (kForm == kFormScanPerm)
+                bulk_load(dst + 1536u, g->minp_bound + 2 * kr, 1024u, tc_full(tc_e));
+              else
+                bulk_load(dst + 1536u, g->minp_key + kr, 1024u, tc_full(tc_e));
+            }
             if (g->nan_cnt) bulk_load(dst + 2560u, g->nan_cnt + r0, 256u, tc_full(tc_e));
             tc_used |= 1u << tc_e;
             tc_last = (tc_last & ~(1u << tc_e)) | (tc_phase << tc_e);
@@ -1552,7 +1732,7 @@ __global__ void __launch_bounds__(ScanRoles<kForm>::kThreads, 1)
         if ((tc_used >> e) & 1u) wait_drain(tc_full(e), (tc_last >> e) & 1u, p.status, 13);
     }
     __syncwarp();
-  } else if (warp == R::kMma && kForm == kFormScan) {
+  } else if (warp == R::kMma && fast_form(kForm)) {
     // MMA issuer of the plain scan form: one N = 256 MMA chain per chunk pair (N =
     // 128 for an odd last chunk) into accumulator pair `ps` (TMEM columns ps *
     // 256 ..), released by the 8 epilogue warps as soon as they have loaded it
@@ -1709,7 +1889,7 @@ __global__ void __launch_bounds__(ScanRoles<kForm>::kThreads, 1)
       wait_drain(drain, 0, p.status, 12);
     }
     __syncwarp();
-  } else if constexpr (kForm == kFormScan) {
+  } else if constexpr (fast_form(kForm)) {
     // epilogue warps of the plain scan form: warp 4k + q owns lane quarter q of
     // kFastSnps SNPs of one chunk of every accumulator pair; it loads their D_0 and
     // D_1 with one wait, releases the pair at once, then runs the hot test (and,
@@ -1718,6 +1898,7 @@ __global__ void __launch_bounds__(ScanRoles<kForm>::kThreads, 1)
       asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kFastRegsLow) : "memory");
       const int e = warp - (R::kMma + 1);
       unsigned int wn = 0;  // hits this event warp has appended to its staging region
+      unsigned int mcn = 0;  // permuted pairs it has passed on to the deferred FP64 pass
       EvGroup G;
       for (unsigned long long t = (unsigned long long)e;; t += 2) {
         const int b = (int)(t % kEvEntries);
@@ -1744,13 +1925,15 @@ __global__ void __launch_bounds__(ScanRoles<kForm>::kThreads, 1)
         }
         got = __shfl_sync(0xffffffffu, got, 0);
         if (!got) break;
-        wn += ev_process(ev.ent[b], G, p, wn, lane, e);
+        wn += ev_process<kForm == kFormScanPerm>(ev.ent[b], G, p, wn, lane, e, mcn);
         __syncwarp();
         if (lane == 0) {  // this use of the buffer is finished
           __threadfence_block();
           atomicAdd(ev.released + b, 1u);
         }
       }
+      if constexpr (kForm == kFormScanPerm)
+        if (lane == 0 && p.mc_cnt != nullptr) p.mc_cnt[blockIdx.x * 2 + e] = min(mcn, (unsigned int)p.mc_cap);
       if (lane == 0 && p.seg_cap > 0) {  // this event warp's staging segments
         constexpr int kSegs = kEpiWarps / 2;
         const unsigned int cap = (unsigned int)p.seg_cap;
@@ -1771,9 +1954,64 @@ __global__ void __launch_bounds__(ScanRoles<kForm>::kThreads, 1)
           tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(128 * h + off);
       uint32_t ps = 0, ps_phase = 0, b_bits = 0, tc_e = 0, tc_phase = 0;
       constexpr int kH = kFastSnps / 2;
+      // permutation batches (two-sided form): this lane's bounds on the form value
+      // in the current step (df 1: -s >= bnd1, df 2: s >= bnd2 may pass), the
+      // step's rank-matrix group, and whether it is a permuted one
+      constexpr bool kTwo = kForm == kFormScanPerm;
+      constexpr float kBoundMin = 1e-30f, kBoundMax = 1e30f;
+      float bnd1 = 0.f, bnd2 = 0.f;  // the hot test's bounds
+      float mx1 = 0.f, mx2 = 0.f;    // permuted step: the classes' largest decided values
+      int ag = 0;
+      bool mstep = false;
+      // seed pass: this lane's largest df-2 value and df-1 |value| in the step and
+      // the 16-SNP blocks (positions in the group's SNP order) that hold them
+      const bool seed = kTwo && p.seed_bound != 0;
+      float smax = 0.f, smin = 0.f;
+      int pos2 = 0, pos1 = 0;
+      int chunk0 = 0;  // the work item's first chunk in the group
+      auto test = [&](const uint32_t(&x0)[kH], const uint32_t(&x1)[kH], const ChunkMeta &mc, int o,
+                      float ntlo) -> bool {
+        if constexpr (kTwo) return hit_fast_w2<kH>(x0, x1, mc, o, -bnd2, bnd1 + bnd2);
+        else return hit_fast_w<kH>(x0, x1, mc, o, ntlo);
+      };
+      // the hot test's bounds of a permuted step from the classes' largest decided
+      // values (a pair at or below value * (1 - margin) cannot beat the pair that
+      // has it), kept at or below the band's lower edge while FDR counts are on
+      auto set_bounds = [&](float tau) {
+        const float keep = 1.f - p.margin;
+        bnd1 = mx1 * keep;
+        bnd2 = mx2 * keep;
+        if (p.fdr_hist != nullptr) {
+          bnd1 = fminf(bnd1, tau * keep);
+          bnd2 = fminf(bnd2, tau * keep);
+        }
+        bnd1 = fminf(bnd1, kBoundMax);
+        bnd2 = fminf(bnd2, kBoundMax);
+      };
+      // a permuted block past the hot test: the lane's pairs that still need the
+      // event warps (past the bounds but not equal to a class's largest decided
+      // value, which an exact copy of that pair has -- copies are common inside LD
+      // blocks -- or in the FDR band), and the classes' new largest values
+      auto minp_filter = [&](const uint32_t(&x0)[kH], const uint32_t(&x1)[kH], const ChunkMeta &mc,
+                             int o, float tau, float &n1, float &n2) -> bool {
+        const float tlo = p.fdr_hist != nullptr ? tau * (1.f - p.margin) : kBoundMax;
+        bool any = false;
+        n1 = mx1;
+        n2 = mx2;
+        for (int j = 0; j < kH; ++j) {
+          const float sv = kw_s(__uint_as_float(x0[j]), __uint_as_float(x1[j]), mc.alpha[o + j],
+                                mc.beta[o + j], mc.gamma[o + j]);
+          const bool c2 = sv > bnd2 && sv != mx2, c1 = -sv > bnd1 && -sv != mx1;
+          any = any || c1 || c2 || fabsf(sv) >= tlo;
+          if (c2) n2 = fmaxf(n2, sv);
+          if (c1) n1 = fmaxf(n1, -sv);
+        }
+        return any;
+      };
       // one accumulator pair: wait for it, load this warp's two halves (the second
       // while the first is tested), release it, test the second half, hand any
       // candidate half-block to the event warps; false if a wait gave up
+      int cpair = 0;  // the chunk pair_slot works on, within the work item
       auto pair_slot = [&](uint32_t ps, uint32_t phase, const ChunkMeta &mc, float tau,
                            double cfac, float ntlo, int trait, int group) -> bool {
         if (!__all_sync(0xffffffffu, wait_bar_p(t_full(ps), phase, p, abort_addr, 7))) return false;
@@ -1783,18 +2021,63 @@ __global__ void __launch_bounds__(ScanRoles<kForm>::kThreads, 1)
         tmem_ld_half(taddr, a0, a1);
         tmem_wait_ld();
         tmem_ld_half(taddr + (uint32_t)kH, b0, b1);
-        const bool need_a = hit_fast_w<kH>(a0, a1, mc, off, ntlo);
+        if constexpr (kTwo) {
+          if (seed) {
+            const int pos = (chunk0 + cpair) * kChunkSnps + off;
+            float hi = 0.f, lo = 0.f;
+            range_w<kH>(a0, a1, mc, off, hi, lo);
+            tmem_wait_ld();
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(t_empty(ps));
+            if (hi > smax) { smax = hi; pos2 = pos; }
+            if (lo < smin) { smin = lo; pos1 = pos; }
+            hi = 0.f;
+            lo = 0.f;
+            range_w<kH>(b0, b1, mc, off + kH, hi, lo);
+            if (hi > smax) { smax = hi; pos2 = pos + kH; }
+            if (lo < smin) { smin = lo; pos1 = pos + kH; }
+            return true;
+          }
+        }
+        const bool need_a = test(a0, a1, mc, off, ntlo);
         tmem_wait_ld();
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(t_empty(ps));
-        const bool need_b = hit_fast_w<kH>(b0, b1, mc, off + kH, ntlo);
-        if (__any_sync(0xffffffffu, need_a) &&
-            !ev_submit(ev, a0, a1, need_a, mc, off, tau, cfac, trait, group, p, abort_addr, lane))
-          return false;
-        if (__any_sync(0xffffffffu, need_b) &&
-            !ev_submit(ev, b0, b1, need_b, mc, off + kH, tau, cfac, trait, group, p, abort_addr, lane))
-          return false;
+        const bool need_b = test(b0, b1, mc, off + kH, ntlo);
+        if (__any_sync(0xffffffffu, need_a)) {
+          bool real = need_a;
+          float n1 = 0.f, n2 = 0.f;
+          if constexpr (kTwo)
+            if (mstep && need_a) real = minp_filter(a0, a1, mc, off, tau, n1, n2);
+          if (__any_sync(0xffffffffu, real) &&
+              !ev_submit(ev, a0, a1, real, mc, off, tau, cfac, trait, group, ag, mx1, mx2, p,
+                         abort_addr, lane))
+            return false;
+          if constexpr (kTwo)
+            if (mstep && real) {
+              mx1 = n1;
+              mx2 = n2;
+              set_bounds(tau);
+            }
+        }
+        if (__any_sync(0xffffffffu, need_b)) {
+          bool real = need_b;
+          float n1 = 0.f, n2 = 0.f;
+          if constexpr (kTwo)
+            if (mstep && need_b) real = minp_filter(b0, b1, mc, off + kH, tau, n1, n2);
+          if (__any_sync(0xffffffffu, real) &&
+              !ev_submit(ev, b0, b1, real, mc, off + kH, tau, cfac, trait, group, ag, mx1, mx2, p,
+                         abort_addr, lane))
+            return false;
+          if constexpr (kTwo)
+            if (mstep && real) {
+              mx1 = n1;
+              mx2 = n2;
+              set_bounds(tau);
+            }
+        }
         return true;
       };
       for (int it = blockIdx.x; it < p.n_items; it += gridDim.x) {
@@ -1809,6 +2092,7 @@ __global__ void __launch_bounds__(ScanRoles<kForm>::kThreads, 1)
           if (!__all_sync(0xffffffffu, ok)) goto epi_done_scan;
         }
         int tt = w.step_begin % g_ntt;  // trait tile of the step
+        chunk0 = w.btile * g_nc;
         for (int step = w.step_begin; step < w.step_end; ++step) {
           // this step's trait constants, staged by the producer (copied out at once)
           if (!__all_sync(0xffffffffu, wait_bar_p(tc_full(tc_e), tc_phase, p, abort_addr, 9)))
@@ -1816,6 +2100,26 @@ __global__ void __launch_bounds__(ScanRoles<kForm>::kThreads, 1)
           const uint8_t *tcp = stc + (size_t)tc_e * kTcBytes;
           const float tau = reinterpret_cast<const float *>(tcp)[row];
           const double cfac = reinterpret_cast<const double *>(tcp + 512)[row];
+          if constexpr (kTwo) {
+            // unpermuted group: both signs against the band's lower edge; a permuted
+            // one: the class bounds the event warps have raised so far
+            ag = step / g_ntt;
+            mstep = g.minp_key != nullptr && ag > 0;
+            const float tlo = tau * (1.f - p.margin);
+            if (mstep) {
+              const uint2 bb = reinterpret_cast<const uint2 *>(tcp + 1536)[row];
+              mx1 = fmaxf(__uint_as_float(bb.x), kBoundMin);
+              mx2 = fmaxf(__uint_as_float(bb.y), kBoundMin);
+              set_bounds(tau);
+            } else {
+              bnd1 = fminf(tlo, kBoundMax);
+              bnd2 = bnd1;
+            }
+            smax = 0.f;
+            smin = 0.f;
+            pos2 = 0;
+            pos1 = 0;
+          }
           __syncwarp();
           if (lane == 0) mbar_arrive(tc_empty(tc_e));
           if (++tc_e == (uint32_t)kTcDepth) {
@@ -1828,6 +2132,7 @@ __global__ void __launch_bounds__(ScanRoles<kForm>::kThreads, 1)
             for (int c0 = 0; c0 < nc_item; c0 += 2) {
               const int c = c0 + h;
               if (c < nc_item) {
+                cpair = c;
                 if (!pair_slot(ps, ps_phase, smeta[c], tau, cfac, ntlo, trait, w.group))
                   goto epi_done_scan;
               } else {  // an odd last chunk leaves warps 8-15 idle: release only
@@ -1840,6 +2145,18 @@ __global__ void __launch_bounds__(ScanRoles<kForm>::kThreads, 1)
               }
               ps ^= 1u;
               if (ps == 0u) ps_phase ^= 1u;
+            }
+          }
+          if constexpr (kTwo) {
+            // seed pass: the step's largest values and their blocks (the largest
+            // over all steps is decided exactly after the launch)
+            if (seed && mstep && trait < g.T) {
+              unsigned long long *rp =
+                  g.minp_seed + 2 * ((int64_t)(ag - 1) * g.rows_per_agroup + trait);
+              if (smin < 0.f)
+                atomicMax(rp, ((unsigned long long)__float_as_uint(-smin) << 32) | (uint32_t)(pos1 + 1));
+              if (smax > 0.f)
+                atomicMax(rp + 1, ((unsigned long long)__float_as_uint(smax) << 32) | (uint32_t)(pos2 + 1));
             }
           }
           if (++tt == g_ntt) tt = 0;
@@ -2201,6 +2518,100 @@ __global__ void finalize_dev_kernel(const krux_hit *__restrict__ hits,
     finalize_one(hits, aux, aux2, i, cfac_by_group, H, P, fdr_hist, fdr_bins, fdr_l0, fdr_w);
 }
 
+// The deferred FP64 pass of a plain-form permutation launch: every listed pair's
+// -ln p (section "P-value calculation and empirical FDR correction"), the largest
+// per (permutation, trait) into the key, and pairs of the FDR band with p < P_c
+// into the histogram row of their permutation.
+__global__ void minp_cands_kernel(const MinpPair *__restrict__ list, const unsigned int *__restrict__ cnt,
+                                  int n_lists, int cap, const double *__restrict__ cfac, int rows_pad,
+                                  double lp, double *key, unsigned long long *fdr_hist, int fdr_bins,
+                                  double fdr_l0, double fdr_w) {
+  for (int l = blockIdx.y; l < n_lists; l += gridDim.y) {
+    const unsigned int n = min(cnt[l], (unsigned int)cap);
+    for (unsigned int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+      const MinpPair r = list[(size_t)l * cap + i];
+      const int df = (int)(r.n2df >> 16), ag = r.agb & 0xffff;
+      const double cf = cfac[r.trait];
+      if (df <= 0 || !(cf > 0.0)) continue;
+      const double k = key64_of(kw_H64(r.u, r.v, (int)(r.n01 & 0xffffu), (int)(r.n01 >> 16),
+                                       (int)(r.n2df & 0xffffu), cf),
+                                df);
+      if (r.agb & (1 << 17))
+        atomicMax(reinterpret_cast<unsigned long long *>(key + (int64_t)(ag - 1) * rows_pad + r.trait),
+                  (unsigned long long)__double_as_longlong(k));
+      if ((r.agb & (1 << 16)) && fdr_hist != nullptr && k > lp)
+        atomicAdd(fdr_hist + (int64_t)ag * fdr_bins + fdr_bin(k, fdr_l0, fdr_w, fdr_bins), 1ull);
+    }
+  }
+}
+
+// After a plain-form seed pass of a permutation batch: one warp per (permutation
+// q, trait, class) whose seed record names a 16-SNP block.  The block's centred
+// rank sums are recomputed as integers (the permuted centred ranks against the
+// genotype indicators, as the contraction forms them), its largest value of the
+// class is found again with the fast test's FP32 expression, that pair's FP64 -ln p
+// (section "P-value calculation and empirical FDR correction") is folded into the
+// key, and its value becomes the class's largest decided value.
+__global__ void seed_decide_kernel(const unsigned long long *__restrict__ rec,
+                                   const __half *__restrict__ stack, int rows_pad, int Np, int N,
+                                   int T, int P, const int8_t *__restrict__ geno, int64_t ldg,
+                                   int64_t snp_begin, int64_t n_snps,
+                                   const ChunkMeta *__restrict__ meta,
+                                   const double *__restrict__ cfac, double *key, uint32_t *bound) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nrec = (int64_t)P * T * 2;
+  for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < nrec;
+       r += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const int cls = (int)(r & 1);
+    const int64_t qt = r >> 1;
+    const int q = (int)(qt / T), trait = (int)(qt % T);
+    const int64_t idx = (int64_t)q * rows_pad + trait;
+    const unsigned long long v = rec[2 * idx + cls];
+    if (v == 0ull) continue;
+    const int64_t pos0 = (int64_t)(uint32_t)(v & 0xffffffffull) - 1;
+    const __half *a = stack + ((int64_t)(1 + q) * rows_pad + trait) * Np;
+    float best = 0.f;
+    int bj = -1, bu = 0, bv = 0;
+    for (int j = 0; j < 16 && pos0 + j < n_snps; ++j) {
+      const int64_t pos = pos0 + j;
+      const int8_t *g = geno + (snp_begin + pos) * ldg;
+      int d0 = 0, d1 = 0;
+      for (int k = lane; k < N; k += 32) {
+        const int ak = (int)__half2float(a[k]);
+        const int8_t gk = g[k];
+        d0 += gk == 0 ? ak : 0;
+        d1 += gk == 1 ? ak : 0;
+      }
+      d0 = __reduce_add_sync(0xffffffffu, d0);
+      d1 = __reduce_add_sync(0xffffffffu, d1);
+      const ChunkMeta &m = meta[pos / kChunkSnps];
+      const int w = (int)(pos % kChunkSnps);
+      if (m.snp[w] < 0) continue;
+      const float sv = kw_s((float)d0, (float)d1, m.alpha[w], m.beta[w], m.gamma[w]);
+      const float val = cls ? sv : -sv;
+      if (val > best) {
+        best = val;
+        bj = j;
+        bu = d0;
+        bv = d1;
+      }
+    }
+    if (lane == 0 && bj >= 0) {
+      const int64_t pos = pos0 + bj;
+      const ChunkMeta &m = meta[pos / kChunkSnps];
+      const int w = (int)(pos % kChunkSnps);
+      const int df = m.df[w];
+      const double cf = cfac[trait];
+      if (df > 0 && cf > 0.0) {
+        const double k64 = key64_of(kw_H64(bu, bv, m.n[0][w], m.n[1][w], m.n[2][w], cf), df);
+        atomicMax(reinterpret_cast<unsigned long long *>(key + idx),
+                  (unsigned long long)__double_as_longlong(k64));
+      }
+      atomicMax(bound + 2 * idx + cls, __float_as_uint(best));
+    }
+  }
+}
+
 // minimum p of each (permutation, trait) from its best -ln p (key rows of ld entries)
 __global__ void minp_from_key_kernel(const double *__restrict__ key, double *__restrict__ minp,
                                      int P, int T, int ld) {
@@ -2233,6 +2644,31 @@ cudaError_t launch_minp_from_key(const double *key, double *minp, int P, int T, 
   return cudaGetLastError();
 }
 
+cudaError_t launch_minp_cands(const MinpPair *list, const unsigned int *cnt, int n_lists, int cap,
+                              const double *cfac, int rows_pad, double pthresh, double *key,
+                              unsigned long long *fdr_hist, int fdr_bins, double fdr_l0,
+                              double fdr_w, cudaStream_t s) {
+  if (n_lists <= 0 || cap <= 0) return cudaSuccess;
+  const dim3 grid((unsigned)((cap + 255) / 256 < 64 ? (cap + 255) / 256 : 64),
+                  (unsigned)(n_lists < 65535 ? n_lists : 65535));
+  minp_cands_kernel<<<grid, 256, 0, s>>>(list, cnt, n_lists, cap, cfac, rows_pad, -log(pthresh), key,
+                                         fdr_hist, fdr_bins, fdr_l0, fdr_w);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_seed_decide(const unsigned long long *rec, const __half *stack, int rows_pad,
+                               int Np, int N, int T, int P, const int8_t *geno, int64_t ldg,
+                               int64_t snp_begin, int64_t n_snps, const ChunkMeta *meta,
+                               const double *cfac, double *key, uint32_t *bound, cudaStream_t s) {
+  const int64_t warps = (int64_t)P * T * 2;
+  if (warps <= 0) return cudaSuccess;
+  const int64_t blocks = (warps + 7) / 8;
+  const int grid = (int)(blocks < 65535 ? blocks : 65535);
+  seed_decide_kernel<<<grid, 256, 0, s>>>(rec, stack, rows_pad, Np, N, T, P, geno, ldg, snp_begin,
+                                          n_snps, meta, cfac, key, bound);
+  return cudaGetLastError();
+}
+
 size_t scan_smem_bytes(int nc, int nA, int kpad) {
   return scan_smem_bytes2(nc, nA, (size_t)128 * kpad * 2, (size_t)nc * 128 * kpad * 2, kpad);
 }
@@ -2250,6 +2686,9 @@ cudaError_t scan_set_smem(size_t smem) {
   cudaError_t e = cudaFuncSetAttribute(krux_scan_kernel<kFormScan>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(krux_scan_kernel<kFormScanPerm>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(krux_scan_kernel<kFormMulti>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -2260,9 +2699,18 @@ cudaError_t scan_set_smem(size_t smem) {
                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
+// The kernel form launch_scan_only picks for these parameters (the ScanForm value).
+int scan_form_of(const ScanParams &p) {
+  if (p.multi) return kFormMulti;
+  if (p.perm) return p.fast && fast_form_ok() ? kFormScanPerm : kFormPerm;
+  return p.fast && fast_form_ok() ? kFormScan : kFormNan;
+}
+
 cudaError_t launch_scan_only(const ScanParams &p, int grid, size_t smem, cudaStream_t s) {
   if (p.multi)
     krux_scan_kernel<kFormMulti><<<grid, kScanThreads, smem, s>>>(p);
+  else if (p.perm && p.fast && fast_form_ok())
+    krux_scan_kernel<kFormScanPerm><<<grid, kFastThreads, smem, s>>>(p);
   else if (p.perm)
     krux_scan_kernel<kFormPerm><<<grid, kScanThreads, smem, s>>>(p);
   else if (p.fast && fast_form_ok())
@@ -2282,9 +2730,13 @@ bool fast_form_ok() {
   static std::atomic<int> ok{-1};
   int v = ok.load(std::memory_order_acquire);
   if (v < 0) {
-    cudaFuncAttributes a;
+    // both plain-form kernels were built at the register count their warp
+    // roles' setmaxnreg split assumes
+    cudaFuncAttributes a, b;
     v = cudaFuncGetAttributes(&a, krux_scan_kernel<kFormScan>) == cudaSuccess &&
-                a.numRegs == kFastRegsLaunch && a.maxThreadsPerBlock >= kFastThreads
+                cudaFuncGetAttributes(&b, krux_scan_kernel<kFormScanPerm>) == cudaSuccess &&
+                a.numRegs == kFastRegsLaunch && a.maxThreadsPerBlock >= kFastThreads &&
+                b.numRegs == kFastRegsLaunch && b.maxThreadsPerBlock >= kFastThreads
             ? 1
             : 0;
     ok.store(v, std::memory_order_release);

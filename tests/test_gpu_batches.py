@@ -184,3 +184,26 @@ def test_permutation_fdr_histogram(kx, oracle_mod, T, S, P, N, nan):
     n_real, pc, fdr = oracle_mod.fdr_from_pvalues(rows[0], rows[1:], pth, c["threshold"])
     assert np.array_equal(c["n_real"], n_real) and np.array_equal(c["mean_perm"] * P, pc.sum(axis=0))
     assert np.allclose(c["fdr"], fdr, rtol=1e-12, atol=0, equal_nan=True)
+
+
+def test_plain_forms_are_the_default(kx):
+    """Without any tuning, complete data take the plain scan form (0) and a
+    permutation batch its two-sided variant (4); NaN expression takes the general
+    form (3), and a permutation batch with NaN the permutation form (2)."""
+    import paper_1307_3519_gb300 as k
+    ctx = k.Krux(0)
+    ctx.set_profiling(True)
+    d = synth.config(4, T=300, S=5000, seed=3)
+    rs, g, pm = ctx.krux_rank(_dev(d["expr"])), _dev(d["geno"]), _dev(d["perms"][:3])
+    ctx.krux_scan(rs, g, 1e-4, capacity=300 * 5000)
+    assert ctx.profile()["scan_form"] == 0
+    ctx.krux_permute(rs, g, pm, 1e-4, capacity=300 * 5000, fdr_bins=8)
+    assert ctx.profile()["scan_form"] == 4
+    x = d["expr"].copy()
+    x[5, 7] = np.nan
+    rsn = ctx.krux_rank(_dev(x))
+    ctx.krux_scan(rsn, g, 1e-4, capacity=300 * 5000)
+    assert ctx.profile()["scan_form"] == 3
+    ctx.krux_permute(rsn, g, pm, 1e-4, capacity=300 * 5000)
+    assert ctx.profile()["scan_form"] == 2
+    ctx.close()
