@@ -263,6 +263,93 @@ __device__ __forceinline__ int find_job(const PackJob *__restrict__ jobs, int n_
   return lo;
 }
 
+// Staged packing of 32 consecutive genotype rows of at most kStageLd bytes each
+// (no SNP list): the warp copies the rows' byte span into shared memory with
+// 16-byte loads, writes both indicator blocks (32 rows of I_0, then 32 of I_1, each
+// contiguous) with 16-byte stores, and lane i counts the groups of row i.
+constexpr int kStageLd = 128;
+constexpr int kStageBytes = 32 * kStageLd + 32;
+
+// Four codes starting at byte offset o of the staged span (any alignment).
+__device__ __forceinline__ uint32_t stage_word(const uint8_t *st, int o) {
+  const uint32_t *w = reinterpret_cast<const uint32_t *>(st + (o & ~3));
+  return __funnelshift_r(w[0], w[1], 8 * (o & 3));
+}
+// Bytes 0..3 of a 0x00 / 0xff byte mask as two FP16 pairs (1.0 where 0xff).
+__device__ __forceinline__ uint2 mask_to_halves(uint32_t m) {
+  return make_uint2(__byte_perm(m, 0u, 0x1100) & 0x3c003c00u, __byte_perm(m, 0u, 0x3322) & 0x3c003c00u);
+}
+
+__device__ __forceinline__ void pack_staged(const PackJob &J, int64_t j0, uint8_t *st, int lane,
+                                            int &my_n0, int &my_n1, int &my_n2, bool &my_miss,
+                                            bool &any_bad, int64_t &my_s) {
+  const int N = J.N, Np = J.Np;
+  const int64_t ldg = J.ldg;
+  const int64_t left = J.n_snps - j0;
+  const int rows = left < 32 ? (int)left : 32;
+  const uint8_t *src = reinterpret_cast<const uint8_t *>(J.geno + (J.snp_begin + j0) * ldg);
+  // the span [src, src + L) in shared memory at offset pad + b, so that 16-byte
+  // aligned global chunks land on 16-byte aligned shared addresses
+  const int64_t L = (int64_t)(rows - 1) * ldg + N;
+  const int pad = (int)((uintptr_t)src & 15u);
+  const int head = (16 - pad) & 15;
+  const int64_t mid = L > head ? (L - head) / 16 : 0;
+  const int64_t hl = (int64_t)head < L ? (int64_t)head : L;
+  for (int64_t b = lane; b < hl; b += 32) st[pad + b] = src[b];
+  for (int64_t c = lane; c < mid; c += 32)
+    *reinterpret_cast<uint4 *>(st + pad + head + 16 * c) =
+        *reinterpret_cast<const uint4 *>(src + head + 16 * c);
+  for (int64_t b = head + 16 * mid + lane; b < L; b += 32) st[pad + b] = src[b];
+  __syncwarp();
+  // both indicator blocks: item t = row r, samples 8q .. 8q + 7
+  const int c = (int)(j0 / kChunkSnps), jj0 = (int)(j0 % kChunkSnps);
+  const int per_row = Np / 8;
+  uint4 *d0 = reinterpret_cast<uint4 *>(J.B + ((int64_t)c * kChunkRows + jj0) * Np);
+  uint4 *d1 = reinterpret_cast<uint4 *>(J.B + ((int64_t)c * kChunkRows + kChunkSnps + jj0) * Np);
+  for (int t = lane; t < 32 * per_row; t += 32) {
+    const int r = t / per_row, k8 = 8 * (t - r * per_row);
+    uint32_t lo = 0x03030303u, hi = 0x03030303u;  // 3: neither group 0 nor 1
+    if (r < rows) {
+      const int o = pad + (int)(r * ldg) + k8;
+      lo = stage_word(st, o);
+      hi = stage_word(st, o + 4);
+      // samples at or beyond N are padding
+      const int vl = min(max(N - k8, 0), 4), vh = min(max(N - k8 - 4, 0), 4);
+      const uint32_t ml = vl >= 4 ? 0xffffffffu : (1u << (8 * vl)) - 1u;
+      const uint32_t mh = vh >= 4 ? 0xffffffffu : (1u << (8 * vh)) - 1u;
+      lo = (lo & ml) | (0x03030303u & ~ml);
+      hi = (hi & mh) | (0x03030303u & ~mh);
+    }
+    const uint2 a = mask_to_halves(__vcmpeq4(lo, 0u)), b = mask_to_halves(__vcmpeq4(hi, 0u));
+    const uint2 e = mask_to_halves(__vcmpeq4(lo, 0x01010101u)),
+                f = mask_to_halves(__vcmpeq4(hi, 0x01010101u));
+    d0[t] = make_uint4(a.x, a.y, b.x, b.y);
+    d1[t] = make_uint4(e.x, e.y, f.x, f.y);
+  }
+  // lane i: the group sizes, missing and invalid codes of row i
+  if (lane < rows) {
+    int n0 = 0, n1 = 0, n2 = 0, nm = 0;
+    const int o0 = pad + (int)(lane * ldg);
+    for (int k = 0; k < N; k += 4) {
+      uint32_t w = stage_word(st, o0 + k);
+      const int v = min(N - k, 4);
+      const uint32_t m = v >= 4 ? 0xffffffffu : (1u << (8 * v)) - 1u;
+      w = (w & m) | (0x04040404u & ~m);  // 4: outside every class below
+      n0 += __popc(__vcmpeq4(w, 0u)) >> 3;
+      n1 += __popc(__vcmpeq4(w, 0x01010101u)) >> 3;
+      n2 += __popc(__vcmpeq4(w, 0x02020202u)) >> 3;
+      nm += __popc(__vcmpeq4(w, 0xffffffffu)) >> 3;
+    }
+    my_n0 = n0;
+    my_n1 = n1;
+    my_n2 = n2;
+    my_miss = nm > 0;
+    any_bad = n0 + n1 + n2 + nm != N;
+    my_s = J.snp_begin + j0 + lane;
+  }
+  __syncwarp();
+}
+
 // All SNP sets of a call in one launch (rank-sum form): one warp per 32 flattened
 // slots (half a chunk; every job spans whole chunks).  Lane t writes samples
 // 4t .. 4t + 3 (+ 128 per pass) of both indicator rows of each slot with 8-byte
@@ -271,12 +358,27 @@ __device__ __forceinline__ int find_job(const PackJob *__restrict__ jobs, int n_
 __global__ void __launch_bounds__(kPackWarps * 32)
 pack_batch_kernel(const PackJob *__restrict__ jobs, int n_jobs, int64_t total_slots, float rh1,
                   float rh2, int signed_df1, unsigned int *status) {
+  __shared__ __align__(16) uint8_t stage[kPackWarps][kStageBytes];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t x0 = ((int64_t)blockIdx.x * kPackWarps + warp) * 32;
   if (x0 >= total_slots) return;
   const PackJob &J = jobs[find_job(jobs, n_jobs, x0, false)];
   const int64_t j0 = x0 - J.slot0;  // a multiple of 32
   const int N = J.N, Np = J.Np;
+  if (!J.snp_list && J.ldg <= kStageLd && Np <= kStageLd && j0 < J.n_snps) {
+    int n0 = 0, n1 = 0, n2 = 0;
+    bool miss = false, bad = false;
+    int64_t sn = -1;
+    pack_staged(J, j0, stage[warp], lane, n0, n1, n2, miss, bad, sn);
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(status, kDevBadCode);
+    const bool excl = miss && !J.allow_missing;
+    if (__any_sync(0xffffffffu, excl) && lane == 0) atomicOr(status, kDevMissing);
+    ChunkMeta &m = J.meta[j0 / kChunkSnps];
+    const int jj = (int)(j0 % kChunkSnps) + lane;
+    if (sn < 0) write_meta(m, jj, 0, 0, 0, true, 0, rh1, rh2, signed_df1, 0, 0.f);
+    else write_meta(m, jj, n0, n1, n2, excl, sn, rh1, rh2, signed_df1, 0, 0.f);
+    return;
+  }
   const int64_t c = j0 / kChunkSnps;
   const int jj0 = (int)(j0 % kChunkSnps);
   const uint32_t one2 = 0x3c003c00u;  // two FP16 ones
