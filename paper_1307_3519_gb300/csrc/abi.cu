@@ -325,6 +325,19 @@ bool pick_launch_shape(const krux_ctx *ctx, int kpad, int codes_k, LaunchShape &
   return best_nc >= 1;
 }
 
+// True when a group of this width can take the plain scan form: a launch shape
+// with the whole K per rank stage, an even number of resident chunks and room for
+// the hit-event ring (the 32-byte swizzle layout).
+bool plain_form_fits(const krux_ctx *ctx, int Np) {
+  if (ctx->tune_layout == 0) return false;
+  const int kpad = round_up(Np, 16);
+  LaunchShape sh;
+  if (!pick_launch_shape(ctx, kpad, 0, sh, kEvRegion)) return false;
+  const int nc = (int)(sh.b_region / (256 * kpad));
+  return sh.ka == kpad && nc >= 2 && nc % 2 == 0 &&
+         shape_overhead(sh.nA, 0) + (size_t)sh.nA * 256 * sh.ka + sh.b_region + kEvRegion <= kSmemLimit;
+}
+
 // Refuses a launch plan whose shared-memory regions or per-group shapes are not
 // aligned or do not fit: every TMA destination and vector load must stay
 // aligned and inside its region.  Returns an empty string when the plan is sound.
@@ -1918,12 +1931,37 @@ extern "C" krux_status krux_scan_grouped(krux_ctx *ctx, krux_cohort *cohorts, in
   }
   st = materialise(ctx, cp, s);
   if (st != KRUX_OK) return st;
-  std::vector<unsigned long long> counts;
-  st = run_fused(ctx, cp, opts, s, counts);
-  if (st != KRUX_OK) return st;
+  // Cohorts whose every group can take the plain scan form run in one launch of
+  // that form, the others in one launch of the general form (one launch holds one
+  // form); each cohort's groups stay in one launch, so its hit list has one writer.
+  std::vector<char> plain(n_cohorts, cp.multi ? 0 : 1);
+  for (const ScanGroupIn &g : cp.groups)
+    if (g.nan_cnt || g.bucket >= 0 || !plain_form_fits(ctx, g.rs->Np)) plain[g.out_slot] = 0;
+  CallPlan parts[2];
+  for (int k = 0; k < 2; ++k) {
+    parts[k] = cp;
+    parts[k].groups.clear();
+  }
+  for (const ScanGroupIn &g : cp.groups) parts[plain[g.out_slot] ? 0 : 1].groups.push_back(g);
+  std::vector<unsigned long long> total(n_cohorts, 0ull);
+  float ms_scan = 0.f;
+  int launches = 0;
+  for (int k = 0; k < 2; ++k) {
+    if (parts[k].groups.empty()) continue;
+    std::vector<unsigned long long> counts;
+    st = run_fused(ctx, parts[k], opts, s, counts);
+    if (st != KRUX_OK) return st;
+    for (const ScanGroupIn &g : parts[k].groups) total[g.out_slot] = counts[g.out_slot];
+    ms_scan += ctx->prof.ms_scan;
+    launches = ctx->prof.launches;
+  }
+  if (ctx->profiling) {
+    ctx->prof.ms_scan = ms_scan;
+    ctx->prof.launches = launches;
+  }
   bool over = false;
   for (int c = 0; c < n_cohorts; ++c) {
-    cohorts[c].n_hits = (int64_t)counts[c];
+    cohorts[c].n_hits = (int64_t)total[c];
     over |= cohorts[c].n_hits > cohorts[c].hit_capacity;
   }
   if (over) return fail(ctx, KRUX_EOVERFLOW, "a cohort's hits exceed its capacity");
