@@ -794,7 +794,7 @@ struct ScanGroupIn {
   double *dense_H = nullptr, *dense_p = nullptr;
   int64_t dense_ld = 0, dense_snp0 = 0;
   double *minp_key = nullptr;
-  uint32_t *minp_bound = nullptr;     // the plain form's bounds beside the keys
+  unsigned long long *minp_bound = nullptr;  // the plain form's bounds beside the keys
   unsigned long long *minp_seed = nullptr;  // and its seed pass's records
   int bucket = -1;                    // index into the call's bucket rank sets
   // tensor map of A: groups whose rank matrices sit back to back in one buffer
@@ -1422,7 +1422,7 @@ krux_status enqueue_fused(krux_ctx *ctx, CallPlan &cp, const FusedLaunch &fl, cu
     KRUX_CUDA(ctx, cudaMemcpyAsync(pj.stack, rs->dev.A, one * 2, cudaMemcpyDeviceToDevice, s));
     KRUX_CUDA(ctx, launch_permute_rows(rs->dev.A, pj.stack + one, rs->rows_pad, rs->Np, rs->N,
                                        pj.perms, pj.P, status, s));
-    KRUX_CUDA(ctx, cudaMemsetAsync(ctx->minpkey.p, 0, (size_t)pj.P * rs->rows_pad * 32, s));
+    KRUX_CUDA(ctx, cudaMemsetAsync(ctx->minpkey.p, 0, (size_t)pj.P * rs->rows_pad * 40, s));
     if (pj.lists) {
       // NaN samples of permutation q sit at inv_q(original position)
       const size_t lst = (size_t)rs->T * rs->N;
@@ -2071,9 +2071,9 @@ static krux_status plan_permute(krux_ctx *ctx, CallPlan &cp, const krux_rankset 
   const int64_t b = opts->snp_begin, e = opts->snp_end > 0 ? opts->snp_end : S;
   const size_t one = (size_t)rs->rows_pad * rs->Np;
   KRUX_CUDA(ctx, ctx->permA.ensure(one * 2 * (size_t)(1 + P)));
-  // [P][rows_pad] FP64 keys, then the plain form's [P][rows_pad][2] FP32 bounds and
+  // [P][rows_pad] FP64 keys, then the plain form's [P][rows_pad][2] 64-bit bounds and
   // [P][rows_pad][2] 64-bit seed records
-  KRUX_CUDA(ctx, ctx->minpkey.ensure((size_t)P * rs->rows_pad * 32));
+  KRUX_CUDA(ctx, ctx->minpkey.ensure((size_t)P * rs->rows_pad * 40));
   KRUX_CUDA(ctx, ctx->aux.ensure((size_t)std::max<int64_t>(opts->hit_capacity, 1) * sizeof(HitAux)));
   cp.slots.push_back(OutSlot{hits, hit_H, hit_p, opts->hit_capacity, ctx->aux.as<HitAux>()});
   cp.fdr_hist = reinterpret_cast<unsigned long long *>(fdr_hist);
@@ -2092,9 +2092,10 @@ static krux_status plan_permute(krux_ctx *ctx, CallPlan &cp, const krux_rankset 
   if (st != KRUX_OK) return st;
   for (auto &g : cp.groups)
     if (g.minp_key) {
-      g.minp_bound = reinterpret_cast<uint32_t *>(ctx->minpkey.as<double>() + (size_t)P * rs->rows_pad);
+      g.minp_bound = reinterpret_cast<unsigned long long *>(ctx->minpkey.as<double>() +
+                                                            (size_t)P * rs->rows_pad);
       g.minp_seed = reinterpret_cast<unsigned long long *>(ctx->minpkey.as<double>() +
-                                                           (size_t)2 * P * rs->rows_pad);
+                                                           (size_t)3 * P * rs->rows_pad);
     }
   if (rs->has_nan) {
     const size_t lst = (size_t)rs->T * rs->N;

@@ -42,6 +42,7 @@ static_assert(kFastThreads * kFastRegsLaunch <= 65536, "launch registers");
 static_assert(4 * (kFastRegsLaunch - kFastRegsLow) >= kFastEpiWarps * (kFastRegsHigh - kFastRegsLaunch),
               "the epilogue's extra registers must come from the producer warpgroup");
 
+
 // Hit events of the plain scan form are handed to the two idle warps of the
 // producer warpgroup through a ring of shared-memory entries: an epilogue warp
 // whose half-block (kEvSnps SNPs x 32 traits) has a candidate writes, for each
@@ -72,7 +73,9 @@ struct EvEntry {
   int32_t trait;                                // its trait row
   int32_t group;
   int32_t ag;                                   // rank-matrix group (> 0: a permutation)
-  float b1, b2;                                 // permutation: the submitting lane's bounds
+  float b1, b2;                                 // permutation: the classes' largest decided values
+  uint32_t id1, id2;                            // and the identities of the pairs that have them
+  int32_t pad_[2];
 };
 static_assert(sizeof(EvEntry) % 16 == 0, "event entries keep 16-byte alignment");
 // shared memory of the ring: alignment slack, entries, a full barrier and a
@@ -81,9 +84,11 @@ static_assert(sizeof(EvEntry) % 16 == 0, "event entries keep 16-byte alignment")
 constexpr size_t kEvRegion = 128 + kEvEntries * sizeof(EvEntry) + kEvEntries * 8 + kEvEntries * 4 + 8;
 // Per-step trait constants staged in shared memory by the producer (one entry per
 // 128-trait tile step): tau f32 [128] @0, 3/(K(K+1)C) f64 [128] @512, starting
-// -ln p key f64 [128] @1536 (permutation batches), NaN count u16 [128] @2560.
+// -ln p key f64 [128] @1536 (permutation batches), NaN count u16 [128] @2560; the
+// two-sided plain form stages instead the classes' decided values with their pair
+// identities, u64 [128][2] @1536 (it has no NaN).
 constexpr int kTcDepth = 4;
-constexpr int kTcBytes = 2816;
+constexpr int kTcBytes = 3584;
 
 // ---- per-chunk SNP metadata (one 1536-byte blob per chunk of 64 SNPs) ------
 // Fast-test coefficients: with u = D_0, v = D_1 (D_2 = -u - v) the statistic's
@@ -222,8 +227,9 @@ struct alignas(64) GroupDesc {
   unsigned long long *counter;  // hits found (keeps counting past capacity)
   double *dense_H, *dense_p;    // optional [T][dense_ld]
   double *minp_key;         // permutation mode: [n_agroups-1][rows_per_agroup] best -ln p (as double bits)
-  uint32_t *minp_bound;     // plain-form permutations: [n_agroups-1][rows_per_agroup][2] float bits
-                            // of the largest df-1 |value| and df-2 value decided so far
+  unsigned long long *minp_bound;  // plain-form permutations: [n_agroups-1][rows_per_agroup][2]
+                            // (float bits of the largest decided df-1 |value| / df-2 value << 32)
+                            // | identity of the pair that has it
   unsigned long long *minp_seed;  // their seed pass: [n_agroups-1][rows_per_agroup][2]
                             // (float bits of the largest value << 32) | (its 16-SNP block + 1)
   int64_t capacity;
@@ -343,7 +349,8 @@ cudaError_t launch_minp_cands(const MinpPair *list, const unsigned int *cnt, int
 cudaError_t launch_seed_decide(const unsigned long long *rec, const __half *stack, int rows_pad,
                                int Np, int N, int T, int P, const int8_t *geno, int64_t ldg,
                                int64_t snp_begin, int64_t n_snps, const ChunkMeta *meta,
-                               const double *cfac, double *key, uint32_t *bound, cudaStream_t s);
+                               const double *cfac, double *key, unsigned long long *bound,
+                               cudaStream_t s);
 cudaError_t launch_pad_traits(int T, int rows_pad, float *tau, double *cfac, uint16_t *nan_cnt,
                               cudaStream_t s);
 // Uploads the 1/n table the finalisation uses (once per device; not during a

@@ -980,7 +980,8 @@ __device__ __forceinline__ bool ev_submit(const EvRing &ev, const uint32_t (&u)[
                                           const uint32_t (&v)[kEvSnps], bool need,
                                           const ChunkMeta &m, int off, float tau, double cfac,
                                           int trait, int group, int ag, float b1, float b2,
-                                          const ScanParams &p, uint32_t abort_addr, int lane) {
+                                          uint32_t id1, uint32_t id2, const ScanParams &p,
+                                          uint32_t abort_addr, int lane) {
   uint32_t lanes = __ballot_sync(0xffffffffu, need);
   unsigned long long t = 0;
   if (lane == 0) t = atomicAdd(ev.word, (unsigned long long)__popc(lanes)) & kEvTicketMask;
@@ -1023,6 +1024,8 @@ __device__ __forceinline__ bool ev_submit(const EvRing &ev, const uint32_t (&u)[
       E.ag = ag;
       E.b1 = b1;
       E.b2 = b2;
+      E.id1 = id1;
+      E.id2 = id2;
     }
     __threadfence_block();
     __syncwarp();
@@ -1033,6 +1036,14 @@ __device__ __forceinline__ bool ev_submit(const EvRing &ev, const uint32_t (&u)[
 }
 
 // Group fields an event warp needs, cached across entries.
+// Identity of a pair for exact-copy detection in permutation batches: a hash of
+// its centred sums (copies of a SNP inside an LD block have the same sums and
+// group sizes, hence the same statistic; pairs with equal sums and equal FP32
+// form values but different group sizes would need an FP32 coincidence on top).
+__device__ __forceinline__ uint32_t pair_id(int u, int v) {
+  return (uint32_t)u * 0x9E3779B1u ^ (uint32_t)v * 0x85EBCA77u;
+}
+
 struct EvGroup {
   int index = -1;
   krux_hit *hits;
@@ -1041,7 +1052,7 @@ struct EvGroup {
   int64_t capacity;
   uint16_t gid;
   double *minp_key;
-  uint32_t *minp_bound;
+  unsigned long long *minp_bound;
   int64_t rows;
 };
 
@@ -1070,11 +1081,15 @@ __device__ __forceinline__ void ev_minp(const EvEntry &E, EvGroup &G, const Scan
                                         float s, unsigned int &mcn, int ev_warp) {
   const int j = lane & (kEvSnps - 1);
   const bool valid = lane < kEvSnps && E.snp[j] >= 0;
-  // E.b1, E.b2: the classes' largest decided values when the entry was filled;
-  // values equal to them are copies of decided pairs (or tie them within an ulp)
+  // E.b1, E.b2: the classes' largest decided values when the entry was filled,
+  // E.id1, E.id2 the identities of the pairs that have them; exact copies of those
+  // pairs are decided already
   const float keep = 1.f - p.margin;
   const float b1 = E.b1, b2 = E.b2;
-  bool cand = valid && ((s > b2 * keep && s != b2) || (-s > b1 * keep && -s != b1));
+  const uint32_t n01 = E.n01[j], n2df = E.n2df[j];
+  const uint32_t pid = pair_id((int)E.u[j], (int)E.v[j]);
+  bool cand = valid && ((s > b2 * keep && !(s == b2 && pid == E.id2)) ||
+                        (-s > b1 * keep && !(-s == b1 && pid == E.id1)));
   // within a class the key grows with the value: only the entry's largest value
   // of each class, and values within the margin of it, can hold the class's best
   float c1 = cand && s < 0.f ? -s : 0.f, c2 = cand && s > 0.f ? s : 0.f;
@@ -1088,7 +1103,12 @@ __device__ __forceinline__ void ev_minp(const EvEntry &E, EvGroup &G, const Scan
   const bool need = cand || band;
   const uint32_t bal = __ballot_sync(0xffffffffu, need);
   const unsigned int n = (unsigned int)__popc(bal);
-  const uint32_t n01 = E.n01[j], n2df = E.n2df[j];
+  // identities of the pairs that hold the classes' largest values (the largest
+  // identity among ties)
+  const bool h1 = cand && s < 0.f && -s == c1, h2 = cand && s > 0.f && s == c2;
+  const uint32_t w1 = __ballot_sync(0xffffffffu, h1), w2 = __ballot_sync(0xffffffffu, h2);
+  const uint32_t i1 = __reduce_max_sync(0xffffffffu, h1 ? pid : 0u);
+  const uint32_t i2 = __reduce_max_sync(0xffffffffu, h2 ? pid : 0u);
   if (mcn + n <= (unsigned int)p.mc_cap) {
     // the list has room: the FP64 work runs after the launch, in parallel
     if (need) {
@@ -1129,8 +1149,10 @@ __device__ __forceinline__ void ev_minp(const EvEntry &E, EvGroup &G, const Scan
   if (lane == 0) {
     ev_group(G, p, E.group);
     const int64_t idx = (int64_t)(E.ag - 1) * G.rows + E.trait;
-    if (c1 > b1) atomicMax(G.minp_bound + 2 * idx, __float_as_uint(c1));
-    if (c2 > b2) atomicMax(G.minp_bound + 2 * idx + 1, __float_as_uint(c2));
+    if (c1 > b1 && w1)
+      atomicMax(G.minp_bound + 2 * idx, ((unsigned long long)__float_as_uint(c1) << 32) | i1);
+    if (c2 > b2 && w2)
+      atomicMax(G.minp_bound + 2 * idx + 1, ((unsigned long long)__float_as_uint(c2) << 32) | i2);
   }
 }
 
@@ -1698,7 +1720,8 @@ __global__ void __launch_bounds__(ScanRoles<kForm>::kThreads, 1)
           if (!wait_bar(tc_empty(tc_e), tc_phase ^ 1u, wc, 8)) goto producer_done;
           {
             const bool with_key = g->minp_key != nullptr && ag > 0;
-            const uint32_t tx = 512u + 1024u + (g->nan_cnt ? 256u : 0u) + (with_key ? 1024u : 0u);
+            constexpr uint32_t key_bytes = kForm == kFormScanPerm ? 2048u : 1024u;
+            const uint32_t tx = 512u + 1024u + (g->nan_cnt ? 256u : 0u) + (with_key ? key_bytes : 0u);
             const uint32_t dst = smem_u32(stc + (size_t)tc_e * kTcBytes);
             const int64_t r0 = (int64_t)tt * kTileM;
             mbar_expect_tx(tc_full(tc_e), tx);
@@ -1708,7 +1731,7 @@ __global__ void __launch_bounds__(ScanRoles<kForm>::kThreads, 1)
               const int64_t kr = (int64_t)(ag - 1) * g->rows_per_agroup + r0;
               // the two-sided plain form reads the class bounds, the others the key
               if constexpr (kForm == kFormScanPerm)
-                bulk_load(dst + 1536u, g->minp_bound + 2 * kr, 1024u, tc_full(tc_e));
+                bulk_load(dst + 1536u, g->minp_bound + 2 * kr, 2048u, tc_full(tc_e));
               else
                 bulk_load(dst + 1536u, g->minp_key + kr, 1024u, tc_full(tc_e));
             }
@@ -1954,57 +1977,65 @@ __global__ void __launch_bounds__(ScanRoles<kForm>::kThreads, 1)
           tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(128 * h + off);
       uint32_t ps = 0, ps_phase = 0, b_bits = 0, tc_e = 0, tc_phase = 0;
       constexpr int kH = kFastSnps / 2;
-      // permutation batches (two-sided form): this lane's bounds on the form value
-      // in the current step (df 1: -s >= bnd1, df 2: s >= bnd2 may pass), the
-      // step's rank-matrix group, and whether it is a permuted one
+      // permutation batches (two-sided form): per class (df 1: -s, df 2: s) the
+      // largest value decided so far for this lane's trait in the current step and
+      // the identity of the pair that has it; a pair may pass when its value exceeds
+      // the decided one less the margin (at most `cap`: the band's lower edge while
+      // FDR counts are on).  The unpermuted group tests both signs against tau.
       constexpr bool kTwo = kForm == kFormScanPerm;
       constexpr float kBoundMin = 1e-30f, kBoundMax = 1e30f;
-      float bnd1 = 0.f, bnd2 = 0.f;  // the hot test's bounds
-      float mx1 = 0.f, mx2 = 0.f;    // permuted step: the classes' largest decided values
-      int ag = 0;
-      bool mstep = false;
+      float mx1 = 0.f, mx2 = 0.f, bnd1 = 0.f, bnd2 = 0.f;  // decided values, hot-test bounds
+      uint32_t id1 = 0u, id2 = 0u;
+      int ag = 0;  // the step's rank-matrix group (> 0: a permutation)
       // seed pass: this lane's largest df-2 value and df-1 |value| in the step and
       // the 16-SNP blocks (positions in the group's SNP order) that hold them
       const bool seed = kTwo && p.seed_bound != 0;
       float smax = 0.f, smin = 0.f;
       int pos2 = 0, pos1 = 0;
       int chunk0 = 0;  // the work item's first chunk in the group
+      // the hot test's bounds from the decided values (cap: the band's lower edge
+      // while FDR counts are on, else none)
+      auto set_bounds = [&](float cap) {
+        const float keep = 1.f - p.margin;
+        bnd1 = fminf(fminf(mx1 * keep, cap), kBoundMax);
+        bnd2 = fminf(fminf(mx2 * keep, cap), kBoundMax);
+      };
       auto test = [&](const uint32_t(&x0)[kH], const uint32_t(&x1)[kH], const ChunkMeta &mc, int o,
                       float ntlo) -> bool {
         if constexpr (kTwo) return hit_fast_w2<kH>(x0, x1, mc, o, -bnd2, bnd1 + bnd2);
         else return hit_fast_w<kH>(x0, x1, mc, o, ntlo);
       };
-      // the hot test's bounds of a permuted step from the classes' largest decided
-      // values (a pair at or below value * (1 - margin) cannot beat the pair that
-      // has it), kept at or below the band's lower edge while FDR counts are on
-      auto set_bounds = [&](float tau) {
-        const float keep = 1.f - p.margin;
-        bnd1 = mx1 * keep;
-        bnd2 = mx2 * keep;
-        if (p.fdr_hist != nullptr) {
-          bnd1 = fminf(bnd1, tau * keep);
-          bnd2 = fminf(bnd2, tau * keep);
-        }
-        bnd1 = fminf(bnd1, kBoundMax);
-        bnd2 = fminf(bnd2, kBoundMax);
-      };
       // a permuted block past the hot test: the lane's pairs that still need the
-      // event warps (past the bounds but not equal to a class's largest decided
-      // value, which an exact copy of that pair has -- copies are common inside LD
-      // blocks -- or in the FDR band), and the classes' new largest values
+      // event warps (past the bounds but not exact copies of a class's decided pair
+      // -- copies are common inside LD blocks -- or in the FDR band), and the
+      // classes' new largest values with the identities of their pairs
       auto minp_filter = [&](const uint32_t(&x0)[kH], const uint32_t(&x1)[kH], const ChunkMeta &mc,
-                             int o, float tau, float &n1, float &n2) -> bool {
+                             int o, float tau, float &n1, float &n2, uint32_t &k1,
+                             uint32_t &k2) -> bool {
         const float tlo = p.fdr_hist != nullptr ? tau * (1.f - p.margin) : kBoundMax;
+        const float b1 = bnd1, b2 = bnd2;
         bool any = false;
         n1 = mx1;
         n2 = mx2;
+        k1 = id1;
+        k2 = id2;
         for (int j = 0; j < kH; ++j) {
-          const float sv = kw_s(__uint_as_float(x0[j]), __uint_as_float(x1[j]), mc.alpha[o + j],
-                                mc.beta[o + j], mc.gamma[o + j]);
-          const bool c2 = sv > bnd2 && sv != mx2, c1 = -sv > bnd1 && -sv != mx1;
+          const float u = __uint_as_float(x0[j]), v = __uint_as_float(x1[j]);
+          const float sv = kw_s(u, v, mc.alpha[o + j], mc.beta[o + j], mc.gamma[o + j]);
+          bool c2 = sv > b2, c1 = -sv > b1;
+          uint32_t pid = 0u;
+          if (c1 || c2) pid = pair_id((int)u, (int)v);
+          c2 = c2 && !(sv == mx2 && pid == id2);
+          c1 = c1 && !(-sv == mx1 && pid == id1);
           any = any || c1 || c2 || fabsf(sv) >= tlo;
-          if (c2) n2 = fmaxf(n2, sv);
-          if (c1) n1 = fmaxf(n1, -sv);
+          if (c2 && sv > n2) {
+            n2 = sv;
+            k2 = pid;
+          }
+          if (c1 && -sv > n1) {
+            n1 = -sv;
+            k1 = pid;
+          }
         }
         return any;
       };
@@ -2049,33 +2080,39 @@ __global__ void __launch_bounds__(ScanRoles<kForm>::kThreads, 1)
         if (__any_sync(0xffffffffu, need_a)) {
           bool real = need_a;
           float n1 = 0.f, n2 = 0.f;
+          uint32_t k1 = 0u, k2 = 0u;
           if constexpr (kTwo)
-            if (mstep && need_a) real = minp_filter(a0, a1, mc, off, tau, n1, n2);
+            if (ag > 0 && need_a) real = minp_filter(a0, a1, mc, off, tau, n1, n2, k1, k2);
           if (__any_sync(0xffffffffu, real) &&
-              !ev_submit(ev, a0, a1, real, mc, off, tau, cfac, trait, group, ag, mx1, mx2, p,
+              !ev_submit(ev, a0, a1, real, mc, off, tau, cfac, trait, group, ag, mx1, mx2, id1, id2, p,
                          abort_addr, lane))
             return false;
           if constexpr (kTwo)
-            if (mstep && real) {
+            if (ag > 0 && real) {
               mx1 = n1;
               mx2 = n2;
-              set_bounds(tau);
+              id1 = k1;
+              id2 = k2;
+              set_bounds(p.fdr_hist != nullptr ? tau * (1.f - p.margin) : kBoundMax);
             }
         }
         if (__any_sync(0xffffffffu, need_b)) {
           bool real = need_b;
           float n1 = 0.f, n2 = 0.f;
+          uint32_t k1 = 0u, k2 = 0u;
           if constexpr (kTwo)
-            if (mstep && need_b) real = minp_filter(b0, b1, mc, off + kH, tau, n1, n2);
+            if (ag > 0 && need_b) real = minp_filter(b0, b1, mc, off + kH, tau, n1, n2, k1, k2);
           if (__any_sync(0xffffffffu, real) &&
-              !ev_submit(ev, b0, b1, real, mc, off + kH, tau, cfac, trait, group, ag, mx1, mx2, p,
-                         abort_addr, lane))
+              !ev_submit(ev, b0, b1, real, mc, off + kH, tau, cfac, trait, group, ag, mx1, mx2, id1, id2,
+                         p, abort_addr, lane))
             return false;
           if constexpr (kTwo)
-            if (mstep && real) {
+            if (ag > 0 && real) {
               mx1 = n1;
               mx2 = n2;
-              set_bounds(tau);
+              id1 = k1;
+              id2 = k2;
+              set_bounds(p.fdr_hist != nullptr ? tau * (1.f - p.margin) : kBoundMax);
             }
         }
         return true;
@@ -2101,19 +2138,23 @@ __global__ void __launch_bounds__(ScanRoles<kForm>::kThreads, 1)
           const float tau = reinterpret_cast<const float *>(tcp)[row];
           const double cfac = reinterpret_cast<const double *>(tcp + 512)[row];
           if constexpr (kTwo) {
-            // unpermuted group: both signs against the band's lower edge; a permuted
-            // one: the class bounds the event warps have raised so far
+            // unpermuted group: both signs against tau (less the margin); a
+            // permuted one: the classes' decided values staged for the step
             ag = step / g_ntt;
-            mstep = g.minp_key != nullptr && ag > 0;
-            const float tlo = tau * (1.f - p.margin);
-            if (mstep) {
-              const uint2 bb = reinterpret_cast<const uint2 *>(tcp + 1536)[row];
-              mx1 = fmaxf(__uint_as_float(bb.x), kBoundMin);
-              mx2 = fmaxf(__uint_as_float(bb.y), kBoundMin);
-              set_bounds(tau);
+            if (ag > 0) {
+              // per class: (value bits << 32) | identity, as little-endian words
+              const uint4 bb = reinterpret_cast<const uint4 *>(tcp + 1536)[row];
+              mx1 = fmaxf(__uint_as_float(bb.y), kBoundMin);
+              id1 = bb.x;
+              mx2 = fmaxf(__uint_as_float(bb.w), kBoundMin);
+              id2 = bb.z;
+              set_bounds(p.fdr_hist != nullptr ? tau * (1.f - p.margin) : kBoundMax);
             } else {
-              bnd1 = fminf(tlo, kBoundMax);
-              bnd2 = bnd1;
+              mx1 = tau;
+              mx2 = tau;
+              id1 = 0u;
+              id2 = 0u;
+              set_bounds(kBoundMax);
             }
             smax = 0.f;
             smin = 0.f;
@@ -2150,7 +2191,7 @@ __global__ void __launch_bounds__(ScanRoles<kForm>::kThreads, 1)
           if constexpr (kTwo) {
             // seed pass: the step's largest values and their blocks (the largest
             // over all steps is decided exactly after the launch)
-            if (seed && mstep && trait < g.T) {
+            if (seed && ag > 0 && trait < g.T) {
               unsigned long long *rp =
                   g.minp_seed + 2 * ((int64_t)(ag - 1) * g.rows_per_agroup + trait);
               if (smin < 0.f)
@@ -2557,7 +2598,8 @@ __global__ void seed_decide_kernel(const unsigned long long *__restrict__ rec,
                                    int T, int P, const int8_t *__restrict__ geno, int64_t ldg,
                                    int64_t snp_begin, int64_t n_snps,
                                    const ChunkMeta *__restrict__ meta,
-                                   const double *__restrict__ cfac, double *key, uint32_t *bound) {
+                                   const double *__restrict__ cfac, double *key,
+                                   unsigned long long *bound) {
   const int lane = threadIdx.x & 31;
   const int64_t nrec = (int64_t)P * T * 2;
   for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < nrec;
@@ -2607,7 +2649,8 @@ __global__ void seed_decide_kernel(const unsigned long long *__restrict__ rec,
         atomicMax(reinterpret_cast<unsigned long long *>(key + idx),
                   (unsigned long long)__double_as_longlong(k64));
       }
-      atomicMax(bound + 2 * idx + cls, __float_as_uint(best));
+      const uint32_t pid = pair_id(bu, bv);
+      atomicMax(bound + 2 * idx + cls, ((unsigned long long)__float_as_uint(best) << 32) | pid);
     }
   }
 }
@@ -2659,7 +2702,8 @@ cudaError_t launch_minp_cands(const MinpPair *list, const unsigned int *cnt, int
 cudaError_t launch_seed_decide(const unsigned long long *rec, const __half *stack, int rows_pad,
                                int Np, int N, int T, int P, const int8_t *geno, int64_t ldg,
                                int64_t snp_begin, int64_t n_snps, const ChunkMeta *meta,
-                               const double *cfac, double *key, uint32_t *bound, cudaStream_t s) {
+                               const double *cfac, double *key, unsigned long long *bound,
+                               cudaStream_t s) {
   const int64_t warps = (int64_t)P * T * 2;
   if (warps <= 0) return cudaSuccess;
   const int64_t blocks = (warps + 7) / 8;
