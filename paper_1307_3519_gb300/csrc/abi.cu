@@ -200,7 +200,8 @@ struct krux_ctx {
       list, gemm_out, bucket_ranks, permA, minpkey, seg, permNan, aux2, param, paramOut, packjobs,
       host_in, host_out,  // krux_scan_host: device copies of the inputs, device hit list
       groups2, items2, packjobs2, cfacptr2,  // launch tables of a second launch in the same call
-      mcand;  // plain-form permutation batches: pairs for the deferred FP64 pass
+      mcand,  // plain-form permutation batches: pairs for the deferred FP64 pass
+      pattern, dlist;  // device-side missing-pattern grouping: scratch, SNP lists
   HostBuf list_host;  // staging of the SNP lists
   void *blas = nullptr;
   std::vector<std::pair<size_t, void *>> pool;  // freed rank-set blocks, reused by size
@@ -551,7 +552,7 @@ void krux_destroy(krux_ctx *ctx) {
                     &ctx->list, &ctx->gemm_out, &ctx->bucket_ranks, &ctx->permA, &ctx->minpkey, &ctx->seg,
                     &ctx->permNan, &ctx->aux2, &ctx->param, &ctx->paramOut, &ctx->packjobs,
                     &ctx->host_in, &ctx->host_out, &ctx->groups2, &ctx->items2, &ctx->packjobs2,
-                    &ctx->cfacptr2, &ctx->mcand};
+                    &ctx->cfacptr2, &ctx->mcand, &ctx->pattern, &ctx->dlist};
   for (DevBuf *b : bufs) b->release();
   ctx->list_host.release();
   for (auto &pb : ctx->pool) cudaFree(pb.second);
@@ -682,15 +683,115 @@ namespace {
 
 struct Bucket {
   std::vector<int32_t> drop;   // samples removed
-  std::vector<int64_t> snps;   // SNP rows with exactly this pattern, ascending
+  std::vector<int64_t> snps;   // SNP rows with exactly this pattern, ascending (host grouping)
+  int64_t dev_off = -1;        // device grouping: the rows at ctx->dlist + dev_off
+  int64_t count = 0;           //   (count of them)
 };
+
+// Device grouping result: where a call's lists sit in ctx->dlist.
+struct DevLists {
+  int64_t base = -1;           // first entry this grouping may use (-1: group on the host)
+  int64_t complete_off = -1;   // the complete rows at ctx->dlist + complete_off
+  int64_t complete_count = 0;
+};
+
+// Device-side grouping of the flagged SNPs (after the missing-code pre-pass): the
+// buckets' rows and the complete rows are written into ctx->dlist from dl.base on;
+// the host reads only the bucket count, sizes, first rows and masks.  Returns false
+// (and leaves the host to group) on a hash collision between two patterns.
+krux_status group_on_device(krux_ctx *ctx, int N, int64_t b, int64_t n, int64_t m,
+                            bool flags_ready, cudaStream_t s, std::vector<Bucket> &buckets,
+                            DevLists &dl, bool &done) {
+  done = false;
+  constexpr int W = kMaxN / 64;
+  int64_t cap = 16;
+  while (cap < 2 * n) cap <<= 1;
+  // scratch layout, each part 256-byte aligned
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off += (bytes + 255) / 256 * 256;
+    return o;
+  };
+  const size_t o_hash = take((size_t)cap * 8), o_rep = take((size_t)cap * 4), o_id = take((size_t)cap * 4);
+  const size_t o_slot = take((size_t)n * 4), o_bof = take((size_t)n * 4), o_nb = take(4);
+  const size_t o_cnt = take((size_t)n * 4), o_fill = take((size_t)n * 4), o_first = take((size_t)n * 8);
+  const size_t o_mask = take((size_t)n * W * 8), o_off = take((size_t)n * 8);
+  const size_t o_woff = take((size_t)((n + 31) / 32 + 1) * 8);
+  KRUX_CUDA(ctx, ctx->pattern.ensure(off));
+  char *pb = ctx->pattern.as<char>();
+  PatternScratch w;
+  w.tab_hash = reinterpret_cast<unsigned long long *>(pb + o_hash);
+  w.tab_rep = reinterpret_cast<int *>(pb + o_rep);
+  w.tab_id = reinterpret_cast<int *>(pb + o_id);
+  w.slot_of = reinterpret_cast<int *>(pb + o_slot);
+  w.bucket_of = reinterpret_cast<int *>(pb + o_bof);
+  w.n_buckets = reinterpret_cast<unsigned int *>(pb + o_nb);
+  w.count = reinterpret_cast<unsigned int *>(pb + o_cnt);
+  w.fill = reinterpret_cast<unsigned int *>(pb + o_fill);
+  w.first = reinterpret_cast<unsigned long long *>(pb + o_first);
+  w.bucket_mask = reinterpret_cast<uint64_t *>(pb + o_mask);
+  w.offset = reinterpret_cast<int64_t *>(pb + o_off);
+  w.woff = reinterpret_cast<int64_t *>(pb + o_woff);
+  w.cap = cap;
+  unsigned int *cnt = ctx->counters.as<unsigned int>();
+  unsigned int *status = ctx->status.as<unsigned int>();
+  const size_t mask_bytes = (size_t)std::max<int64_t>(n, 1) * (kMaxN / 8);
+  uint32_t *flags = reinterpret_cast<uint32_t *>(ctx->miss_mask.as<char>() + mask_bytes);
+  KRUX_CUDA(ctx, launch_pattern_group(cnt, ctx->miss_mask.as<uint64_t>(), ctx->miss_idx.as<int64_t>(),
+                                      n, w, status, s));
+  unsigned int nb = 0, st = 0;
+  KRUX_CUDA(ctx, cudaMemcpyAsync(&nb, w.n_buckets, 4, cudaMemcpyDeviceToHost, s));
+  KRUX_CUDA(ctx, cudaMemcpyAsync(&st, status, 4, cudaMemcpyDeviceToHost, s));
+  KRUX_CUDA(ctx, cudaStreamSynchronize(s));
+  if (st & kDevHashCollision) {
+    KRUX_CUDA(ctx, cudaMemsetAsync(status, 0, 64, s));  // the host groups instead
+    return KRUX_OK;
+  }
+  std::vector<unsigned int> count(nb);
+  std::vector<unsigned long long> first(nb);
+  std::vector<uint64_t> bmask((size_t)nb * W);
+  KRUX_CUDA(ctx, cudaMemcpyAsync(count.data(), w.count, (size_t)nb * 4, cudaMemcpyDeviceToHost, s));
+  KRUX_CUDA(ctx, cudaMemcpyAsync(first.data(), w.first, (size_t)nb * 8, cudaMemcpyDeviceToHost, s));
+  KRUX_CUDA(ctx, cudaMemcpyAsync(bmask.data(), w.bucket_mask, bmask.size() * 8, cudaMemcpyDeviceToHost, s));
+  KRUX_CUDA(ctx, cudaStreamSynchronize(s));
+  // buckets in order of their first SNP; lists back to back, then the complete rows
+  std::vector<int> order(nb);
+  for (unsigned int i = 0; i < nb; ++i) order[i] = (int)i;
+  std::sort(order.begin(), order.end(), [&](int x, int y) { return first[x] < first[y]; });
+  std::vector<int64_t> offset(nb);
+  int64_t run = 0;
+  for (int id : order) {
+    offset[id] = run;
+    run += count[id];
+  }
+  KRUX_CUDA(ctx, cudaMemcpyAsync(w.offset, offset.data(), (size_t)nb * 8, cudaMemcpyHostToDevice, s));
+  int64_t *lists = ctx->dlist.as<int64_t>() + dl.base;
+  KRUX_CUDA(ctx, launch_pattern_lists(cnt, ctx->miss_idx.as<int64_t>(), flags, flags_ready, b, n, w,
+                                      lists, lists + m, s));
+  buckets.clear();
+  for (int id : order) {
+    Bucket bk;
+    const uint64_t *key = bmask.data() + (size_t)id * W;
+    for (int k = 0; k < N; ++k)
+      if ((key[k / 64] >> (k % 64)) & 1ull) bk.drop.push_back(k);
+    bk.dev_off = dl.base + offset[id];
+    bk.count = count[id];
+    buckets.push_back(std::move(bk));
+  }
+  dl.complete_off = dl.base + m;
+  dl.complete_count = n - m;
+  done = true;
+  return KRUX_OK;
+}
 
 // Finds SNPs of rows [b, b+n) that carry a -1, groups them by their exact
 // missing-sample set, and lists the complete rows.  `bad` reports codes outside
 // {-1,0,1,2}.  Synchronises the stream.
 krux_status find_missing(krux_ctx *ctx, const int8_t *geno, int64_t ldg, int N, int64_t b,
                          int64_t n, cudaStream_t s, std::vector<Bucket> &buckets,
-                         std::vector<int64_t> &complete, bool &bad, int max_code) {
+                         std::vector<int64_t> &complete, bool &bad, int max_code,
+                         DevLists *dl = nullptr) {
   KRUX_CUDA(ctx, ctx->status.ensure(64));
   KRUX_CUDA(ctx, ctx->counters.ensure(64));
   KRUX_CUDA(ctx, ctx->miss_idx.ensure((size_t)std::max<int64_t>(n, 1) * 8));
@@ -714,6 +815,12 @@ krux_status find_missing(krux_ctx *ctx, const int8_t *geno, int64_t ldg, int N, 
   complete.clear();
   if (bad || m32 == 0) return KRUX_OK;
   const int64_t m = m32;
+  if (dl && dl->base >= 0) {  // group on the device when the lists have room there
+    bool done = false;
+    krux_status gs = group_on_device(ctx, N, b, n, m, ldg == N, s, buckets, *dl, done);
+    if (gs != KRUX_OK || done) return gs;
+    dl->base = -1;
+  }
   constexpr int W = kMaxN / 64;
   std::vector<int64_t> idx(m);
   std::vector<uint64_t> mask((size_t)m * W);
@@ -732,28 +839,43 @@ krux_status find_missing(krux_ctx *ctx, const int8_t *geno, int64_t ldg, int N, 
     if (slot_of[(size_t)j] >= 0) order.push_back(slot_of[(size_t)j]);
     else complete.push_back(b + j);
   }
-  // buckets in order of their first SNP; a hash of the sample mask finds them
-  using Key = std::array<uint64_t, W>;
-  struct KeyHash {
-    size_t operator()(const Key &k) const {
-      uint64_t h = 0x9e3779b97f4a7c15ull;
-      for (uint64_t w : k) h = (h ^ w) * 0x100000001b3ull;
-      return (size_t)(h ^ (h >> 29));
-    }
+  // buckets in order of their first SNP, found through an open-addressing table of
+  // 64-bit mask hashes (a hash match is confirmed on the whole mask)
+  auto mask_of = [&](int64_t oi) { return mask.data() + (size_t)oi * W; };
+  auto hash_of = [&](const uint64_t *k) {
+    uint64_t h = 0x9e3779b97f4a7c15ull;
+    for (int w = 0; w < W; ++w) h = (h ^ k[w]) * 0x100000001b3ull;
+    return h ^ (h >> 29);
   };
-  std::unordered_map<Key, size_t, KeyHash> where;
-  where.reserve((size_t)m);
+  size_t cap = 16;
+  while (cap < 2 * (size_t)m) cap <<= 1;
+  std::vector<int64_t> table(cap, -1);       // bucket index, -1 = empty
+  std::vector<int64_t> first;                // each bucket's first slot (its mask)
+  std::vector<uint64_t> hashes;              // and its hash
   for (int64_t oi : order) {
-    Key key;
-    std::copy(mask.begin() + oi * W, mask.begin() + (oi + 1) * W, key.begin());
-    auto ins = where.emplace(key, buckets.size());
-    if (ins.second) {
+    const uint64_t *key = mask_of(oi);
+    const uint64_t h = hash_of(key);
+    size_t t = (size_t)h & (cap - 1);
+    int64_t bi = -1;
+    while (table[t] >= 0) {
+      const int64_t c = table[t];
+      if (hashes[(size_t)c] == h && std::memcmp(mask_of(first[(size_t)c]), key, W * 8) == 0) {
+        bi = c;
+        break;
+      }
+      t = (t + 1) & (cap - 1);
+    }
+    if (bi < 0) {
+      bi = (int64_t)buckets.size();
+      table[t] = bi;
+      first.push_back(oi);
+      hashes.push_back(h);
       Bucket bk;
       for (int k = 0; k < N; ++k)
         if ((key[k / 64] >> (k % 64)) & 1ull) bk.drop.push_back(k);
       buckets.push_back(std::move(bk));
     }
-    buckets[ins.first->second].snps.push_back(idx[oi]);
+    buckets[(size_t)bi].snps.push_back(idx[oi]);
   }
   return KRUX_OK;
 }
@@ -845,6 +967,7 @@ struct CallPlan {
     std::vector<int64_t> h_snp, h_trait;                      // host copies
     int64_t window = -1;
   } cis;
+  int64_t dlist_used = 0;  // entries of ctx->dlist this call's device groupings use
   unsigned long long *fdr_hist = nullptr;  // permutation calls: [fdr_rows = 1 + P][fdr_bins] or null
   int fdr_rows = 0, fdr_bins = 0;
   double fdr_l0 = 0.0, fdr_w = 1.0;
@@ -874,9 +997,12 @@ krux_status plan_groups(krux_ctx *ctx, CallPlan &cp, const krux_rankset *rs, con
   std::vector<Bucket> buckets;
   std::vector<int64_t> complete;
   bool bad = false;
-  krux_status st =
-      find_missing(ctx, geno, ldg, rs->N, b, n, s, buckets, complete, bad, cp.multi ? kMaxCodeM : 2);
+  DevLists dl;
+  if ((int64_t)(ctx->dlist.n / 8) >= cp.dlist_used + n) dl.base = cp.dlist_used;
+  krux_status st = find_missing(ctx, geno, ldg, rs->N, b, n, s, buckets, complete, bad,
+                                cp.multi ? kMaxCodeM : 2, &dl);
   if (st != KRUX_OK) return st;
+  if (dl.base >= 0 && !buckets.empty()) cp.dlist_used += n;
   if (bad)
     return fail(ctx, KRUX_EINVAL, cp.multi ? "genotype code outside {-1, 0..4}"
                                            : "genotype code outside {-1,0,1,2}");
@@ -907,7 +1033,11 @@ krux_status plan_groups(krux_ctx *ctx, CallPlan &cp, const krux_rankset *rs, con
     cp.groups.push_back(g0);
     return KRUX_OK;
   }
-  if (!complete.empty()) {
+  if (dl.base >= 0 && dl.complete_count > 0) {  // device lists
+    g0.snp_list = ctx->dlist.as<int64_t>() + dl.complete_off;
+    g0.n_snps = dl.complete_count;
+    cp.groups.push_back(g0);
+  } else if (!complete.empty()) {
     g0.list_off = (int64_t)cp.lists.size();
     g0.n_snps = (int64_t)complete.size();
     cp.lists.insert(cp.lists.end(), complete.begin(), complete.end());
@@ -916,6 +1046,16 @@ krux_status plan_groups(krux_ctx *ctx, CallPlan &cp, const krux_rankset *rs, con
   for (auto &bk : buckets) {
     ScanGroupIn gb = g0;
     gb.minp_key = nullptr;
+    if (bk.dev_off >= 0) {
+      gb.list_off = -1;
+      gb.snp_list = ctx->dlist.as<int64_t>() + bk.dev_off;
+      gb.n_snps = bk.count;
+      gb.allow_missing = 1;
+      gb.bucket = (int)cp.bucket_jobs.size();
+      cp.bucket_jobs.push_back(BucketJob{rs, bk.drop});
+      cp.groups.push_back(gb);
+      continue;
+    }
     gb.list_off = (int64_t)cp.lists.size();
     gb.n_snps = (int64_t)bk.snps.size();
     gb.allow_missing = 1;
@@ -1633,6 +1773,7 @@ extern "C" krux_status krux_scan(krux_ctx *ctx, const krux_rankset *rs, const in
     ctx->prof.pairs = (int64_t)rs->T * (e - b);
   }
   KRUX_CUDA(ctx, ctx->aux.ensure((size_t)std::max<int64_t>(opts->hit_capacity, 1) * sizeof(HitAux)));
+  KRUX_CUDA(ctx, ctx->dlist.ensure((size_t)std::max<int64_t>(e - b, 1) * 8));
   CallPlan cp;
   cp.multi = (opts->flags & KRUX_FLAG_MULTIALLELIC) != 0;
   cp.slots.push_back(OutSlot{hits, hit_H, hit_p, opts->hit_capacity, ctx->aux.as<HitAux>()});
@@ -1756,6 +1897,7 @@ extern "C" krux_status krux_scan_cis(krux_ctx *ctx, const krux_rankset *rs, cons
   }
   KRUX_CUDA(ctx, ctx->aux.ensure((size_t)std::max<int64_t>(opts->hit_capacity, 1) * sizeof(HitAux)));
   cp.slots.push_back(OutSlot{hits, hit_H, hit_p, opts->hit_capacity, ctx->aux.as<HitAux>()});
+  KRUX_CUDA(ctx, ctx->dlist.ensure((size_t)std::max<int64_t>(e - b, 1) * 8));
   st = plan_groups(ctx, cp, rs, geno, ldg, b, e, nullptr, 1, 0, nullptr, nullptr, nullptr, s);
   if (st != KRUX_OK) return st;
   st = materialise(ctx, cp, s);
@@ -1919,6 +2061,11 @@ extern "C" krux_status krux_scan_grouped(krux_ctx *ctx, krux_cohort *cohorts, in
     for (int c = 0; c < n_cohorts; ++c) ctx->prof.pairs += (int64_t)cohorts[c].rs->T * cohorts[c].S;
   }
   KRUX_CUDA(ctx, ctx->aux.ensure((size_t)std::max<int64_t>(captot, 1) * sizeof(HitAux)));
+  {
+    int64_t snps = 1;
+    for (int c = 0; c < n_cohorts; ++c) snps += cohorts[c].S;
+    KRUX_CUDA(ctx, ctx->dlist.ensure((size_t)snps * 8));
+  }
   CallPlan cp;
   cp.multi = (opts->flags & KRUX_FLAG_MULTIALLELIC) != 0;
   int64_t aoff = 0;

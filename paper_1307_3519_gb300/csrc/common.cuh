@@ -314,6 +314,7 @@ enum : unsigned int {
   kDevBadCode = 2u,
   kDevBadPerm = 4u,     // a permutation entry outside 0..N-1 (its row is gathered as zeros)
   kDevMissing = 8u,     // a -1 code in a group packed as complete (graph replays)
+  kDevHashCollision = 16u,  // two missing-sample patterns with one 64-bit hash
 };
 
 // ---- launch wrappers (defined in the .cu files) -----------------------------
@@ -338,6 +339,26 @@ cudaError_t launch_seg_compact(const krux_hit *seg_hits, const HitAux *seg_aux,
                                unsigned long long *total, cudaStream_t s);
 cudaError_t launch_minp_from_key(const double *key, double *minp, int P, int T, int ld,
                                  cudaStream_t s);
+// Device-side grouping of the flagged SNPs by missing-sample pattern: scratch of
+// one call (cap table slots, a power of two above twice the SNP count; per-SNP and
+// per-bucket arrays of n_snps entries).
+struct PatternScratch {
+  unsigned long long *tab_hash;
+  int *tab_rep, *tab_id, *slot_of, *bucket_of;
+  unsigned int *n_buckets, *count, *fill;
+  unsigned long long *first;  // smallest SNP row of each bucket
+  uint64_t *bucket_mask;      // [bucket][kMaxN / 64]
+  int64_t *offset;            // [bucket] list offsets (set by the host)
+  int64_t *woff;              // [n_snps / 32 + 1] complete-row offsets
+  int64_t cap;
+};
+cudaError_t launch_pattern_group(const unsigned int *n_missing, const uint64_t *mask,
+                                 const int64_t *miss_idx, int64_t n_snps, PatternScratch &w,
+                                 unsigned int *status, cudaStream_t s);
+cudaError_t launch_pattern_lists(const unsigned int *n_missing, const int64_t *miss_idx,
+                                 const uint32_t *flags, bool flags_ready, int64_t snp_begin,
+                                 int64_t n_snps, PatternScratch &w, int64_t *bucket_list,
+                                 int64_t *complete_list, cudaStream_t s);
 // After a plain-form permutation launch: the FP64 -ln p of every pair the event
 // warps passed on, folded into the keys and, in the FDR band, into the histogram.
 cudaError_t launch_minp_cands(const MinpPair *list, const unsigned int *cnt, int n_lists, int cap,

@@ -132,6 +132,159 @@ missing_collect_kernel(const int8_t *__restrict__ geno, int64_t ldg, int N, int6
   }
 }
 
+// ---- device-side grouping of the flagged SNPs by missing-sample pattern ----------
+// (section "Handling missing values": one matrix per pattern).  An open-addressing
+// table over 64-bit hashes of the sample masks (0 = empty slot) finds each pattern's
+// bucket; every member's mask is then compared with its bucket representative's
+// (a hash collision is reported, and the host groups on its own instead).
+__device__ __forceinline__ uint64_t pattern_hash(const uint64_t *m) {
+  uint64_t h = 0x9e3779b97f4a7c15ull;
+#pragma unroll
+  for (int w = 0; w < kMaxN / 64; ++w) h = (h ^ m[w]) * 0x100000001b3ull;
+  return (h ^ (h >> 29)) | 1ull;
+}
+
+__global__ void pattern_insert_kernel(const unsigned int *__restrict__ n_missing,
+                                      const uint64_t *__restrict__ mask,
+                                      unsigned long long *tab_hash, int *tab_rep, int64_t cap,
+                                      int *slot_of) {
+  const int64_t m = *n_missing;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned long long h = pattern_hash(mask + i * (kMaxN / 64));
+    int64_t t = (int64_t)(h & (unsigned long long)(cap - 1));
+    for (int64_t probe = 0; probe < cap; ++probe) {  // the table has room for every mask
+      const unsigned long long prev = atomicCAS(tab_hash + t, 0ull, h);
+      if (prev == 0ull || prev == h) {
+        atomicMin(tab_rep + t, (int)i);
+        slot_of[i] = (int)t;
+        break;
+      }
+      t = (t + 1) & (cap - 1);
+    }
+  }
+}
+
+// Numbers the occupied slots (bucket ids) and copies each bucket's representative
+// mask out.
+__global__ void pattern_number_kernel(const unsigned long long *__restrict__ tab_hash,
+                                      const int *__restrict__ tab_rep, int64_t cap, int *tab_id,
+                                      unsigned int *n_buckets, const uint64_t *__restrict__ mask,
+                                      uint64_t *bucket_mask) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < cap;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    if (tab_hash[t] == 0ull) continue;
+    const int id = (int)atomicAdd(n_buckets, 1u);
+    tab_id[t] = id;
+    const int rep = tab_rep[t];
+#pragma unroll
+    for (int w = 0; w < kMaxN / 64; ++w)
+      bucket_mask[(int64_t)id * (kMaxN / 64) + w] = mask[(int64_t)rep * (kMaxN / 64) + w];
+  }
+}
+
+// Bucket of every flagged SNP, bucket sizes and first SNPs, and the check of every
+// mask against its bucket's.
+__global__ void pattern_count_kernel(const unsigned int *__restrict__ n_missing,
+                                     const int *__restrict__ slot_of, const int *__restrict__ tab_id,
+                                     const uint64_t *__restrict__ mask,
+                                     const uint64_t *__restrict__ bucket_mask,
+                                     const int64_t *__restrict__ miss_idx, int *bucket_of,
+                                     unsigned int *count, unsigned long long *first,
+                                     unsigned int *status) {
+  const int64_t m = *n_missing;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int b = tab_id[slot_of[i]];
+    bucket_of[i] = b;
+    atomicAdd(count + b, 1u);
+    atomicMin(first + b, (unsigned long long)miss_idx[i]);
+    bool same = true;
+#pragma unroll
+    for (int w = 0; w < kMaxN / 64; ++w)
+      same = same && mask[i * (kMaxN / 64) + w] == bucket_mask[(int64_t)b * (kMaxN / 64) + w];
+    if (!same) atomicOr(status, kDevHashCollision);
+  }
+}
+
+// Writes every flagged SNP into its bucket's list (offset[b] .. + count[b]).
+__global__ void pattern_scatter_kernel(const unsigned int *__restrict__ n_missing,
+                                       const int *__restrict__ bucket_of,
+                                       const int64_t *__restrict__ offset,
+                                       const int64_t *__restrict__ miss_idx, unsigned int *fill,
+                                       int64_t *list) {
+  const int64_t m = *n_missing;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int b = bucket_of[i];
+    list[offset[b] + atomicAdd(fill + b, 1u)] = miss_idx[i];
+  }
+}
+
+// The rows without a missing code, in order: one block scans the per-word counts of
+// the flag bits, then every word writes its complete rows.
+__global__ void __launch_bounds__(1024)
+complete_offsets_kernel(const uint32_t *__restrict__ flags, int64_t n_snps, int64_t *woff) {
+  __shared__ int64_t part[1024];
+  const int64_t nw = (n_snps + 31) / 32;
+  const int64_t per = (nw + 1023) / 1024;
+  const int64_t w0 = threadIdx.x * per, w1 = w0 + per < nw ? w0 + per : nw;
+  int64_t sum = 0;
+  for (int64_t w = w0; w < w1; ++w) {
+    const int64_t left = n_snps - 32 * w;
+    const int valid = left < 32 ? (int)left : 32;
+    const uint32_t vm = valid >= 32 ? 0xffffffffu : (1u << valid) - 1u;
+    sum += __popc(~flags[w] & vm);
+  }
+  part[threadIdx.x] = sum;
+  __syncthreads();
+  for (int d = 1; d < 1024; d <<= 1) {  // inclusive scan of the partial sums
+    const int64_t v = threadIdx.x >= (unsigned)d ? part[threadIdx.x - d] : 0;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  int64_t run = threadIdx.x ? part[threadIdx.x - 1] : 0;
+  for (int64_t w = w0; w < w1; ++w) {
+    woff[w] = run;
+    const int64_t left = n_snps - 32 * w;
+    const int valid = left < 32 ? (int)left : 32;
+    const uint32_t vm = valid >= 32 ? 0xffffffffu : (1u << valid) - 1u;
+    run += __popc(~flags[w] & vm);
+  }
+  if (threadIdx.x == 1023) woff[nw] = part[1023];
+}
+
+__global__ void complete_scatter_kernel(const uint32_t *__restrict__ flags,
+                                        const int64_t *__restrict__ woff, int64_t snp_begin,
+                                        int64_t n_snps, int64_t *list) {
+  const int64_t nw = (n_snps + 31) / 32;
+  for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < nw;
+       w += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t left = n_snps - 32 * w;
+    const int valid = left < 32 ? (int)left : 32;
+    uint32_t bits = ~flags[w] & (valid >= 32 ? 0xffffffffu : (1u << valid) - 1u);
+    int64_t o = woff[w];
+    while (bits) {
+      const int j = __ffs((int)bits) - 1;
+      bits &= bits - 1u;
+      list[o++] = snp_begin + 32 * w + j;
+    }
+  }
+}
+
+// Flag bits of the flagged SNPs (the pre-pass that produces no flag array).
+__global__ void flags_from_idx_kernel(const unsigned int *__restrict__ n_missing,
+                                      const int64_t *__restrict__ miss_idx, int64_t snp_begin,
+                                      uint32_t *flags) {
+  const int64_t m = *n_missing;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = miss_idx[i] - snp_begin;
+    atomicOr(flags + (j >> 5), 1u << (j & 31));
+  }
+}
+
 // Metadata of SNP slot jj of a chunk: group sizes, df and the coefficients of the
 // hot test (zero for an excluded SNP: one with a missing code outside its bucket).
 __device__ __forceinline__ void write_meta(ChunkMeta &m, int jj, int n0, int n1, int n2,
@@ -658,6 +811,46 @@ cudaError_t launch_pack_batch(const PackJob *jobs, int n_jobs, int64_t total_slo
     return cudaGetLastError();
   }
   return cudaSuccess;
+}
+
+cudaError_t launch_pattern_group(const unsigned int *n_missing, const uint64_t *mask,
+                                 const int64_t *miss_idx, int64_t n_snps, PatternScratch &w,
+                                 unsigned int *status, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(w.tab_hash, 0, (size_t)w.cap * 8, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(w.tab_rep, 0x7f, (size_t)w.cap * 4, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(w.n_buckets, 0, 4, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(w.count, 0, (size_t)n_snps * 4, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(w.fill, 0, (size_t)n_snps * 4, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(w.first, 0xff, (size_t)n_snps * 8, s);
+  if (e != cudaSuccess) return e;
+  const unsigned g1 = (unsigned)std::min<int64_t>((n_snps + 255) / 256, 152 * 8);
+  const unsigned g2 = (unsigned)std::min<int64_t>((w.cap + 255) / 256, 152 * 8);
+  pattern_insert_kernel<<<g1, 256, 0, s>>>(n_missing, mask, w.tab_hash, w.tab_rep, w.cap, w.slot_of);
+  pattern_number_kernel<<<g2, 256, 0, s>>>(w.tab_hash, w.tab_rep, w.cap, w.tab_id, w.n_buckets, mask,
+                                           w.bucket_mask);
+  pattern_count_kernel<<<g1, 256, 0, s>>>(n_missing, w.slot_of, w.tab_id, mask, w.bucket_mask,
+                                          miss_idx, w.bucket_of, w.count, w.first, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pattern_lists(const unsigned int *n_missing, const int64_t *miss_idx,
+                                 const uint32_t *flags, bool flags_ready, int64_t snp_begin,
+                                 int64_t n_snps, PatternScratch &w, int64_t *bucket_list,
+                                 int64_t *complete_list, cudaStream_t s) {
+  const unsigned g1 = (unsigned)std::min<int64_t>((n_snps + 255) / 256, 152 * 8);
+  const int64_t nw = (n_snps + 31) / 32;
+  uint32_t *fl = const_cast<uint32_t *>(flags);
+  if (!flags_ready) {
+    cudaError_t e = cudaMemsetAsync(fl, 0, (size_t)nw * 4, s);
+    if (e != cudaSuccess) return e;
+    flags_from_idx_kernel<<<g1, 256, 0, s>>>(n_missing, miss_idx, snp_begin, fl);
+  }
+  pattern_scatter_kernel<<<g1, 256, 0, s>>>(n_missing, w.bucket_of, w.offset, miss_idx, w.fill,
+                                            bucket_list);
+  complete_offsets_kernel<<<1, 1024, 0, s>>>(flags, n_snps, w.woff);
+  complete_scatter_kernel<<<(unsigned)std::min<int64_t>((nw + 255) / 256, 152 * 8), 256, 0, s>>>(
+      flags, w.woff, snp_begin, n_snps, complete_list);
+  return cudaGetLastError();
 }
 
 }  // namespace krux
