@@ -2724,9 +2724,22 @@ size_t scan_smem_bytes2(int nc, int nA, size_t a_tile_bytes, size_t b_region, in
 }
 
 bool fast_form_ok();
+cudaError_t scan_set_smem_all(size_t smem);
 
 cudaError_t scan_set_smem(size_t smem) {
   (void)fast_form_ok();  // its one-time check happens here, before any graph capture
+  // the attribute is per device: skip the calls when it already has this value
+  static std::atomic<size_t> last[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64 &&
+      last[dev].load(std::memory_order_acquire) == smem + 1)
+    return cudaSuccess;
+  cudaError_t e = scan_set_smem_all(smem);
+  if (e == cudaSuccess && dev >= 0 && dev < 64) last[dev].store(smem + 1, std::memory_order_release);
+  return e;
+}
+
+cudaError_t scan_set_smem_all(size_t smem) {
   cudaError_t e = cudaFuncSetAttribute(krux_scan_kernel<kFormScan>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
