@@ -55,12 +55,12 @@ WORKLOAD = ("paper-scale fused scan: N=102 samples, T=20000 traits, S=500000 SNP
 #            -k regex:krux_scan_kernel -s 1 -c 1 python bench.py --scan-only --traits 20000
 #            --snps 100000 --data paper --tile 1,4,2,0 --reps 2
 #            (warp instructions x 32 lanes / pairs = lane issue slots per pair)
-# Measured on the kernel below: 241.51 MB read + 73.37 MB written per 500k-SNP launch;
-# 667.18 M warp instructions (565.75 M on the FMA-heavy, FMA-lite and ALU pipes) per
+# Measured on the kernel below: 241.19 MB read + 73.67 MB written per 500k-SNP launch;
+# 676.26 M warp instructions (567.58 M on the FMA-heavy, FMA-lite and ALU pipes) per
 # 100k-SNP launch of 2x10^9 pairs.
-SCAN_TRAFFIC = {"blob": "f7279c3fe8798c4d2df657ddd53329b7e4056ee5", "bytes": 314.88e6}
-SCAN_ISSUE = {"blob": "f7279c3fe8798c4d2df657ddd53329b7e4056ee5", "slots_per_pair": 10.68,
-              "fp32_int_slots_per_pair": 9.05,
+SCAN_TRAFFIC = {"blob": "a1dbef2c21d3270bf6bdcf12a8d1e9bd6d947e8d", "bytes": 314.86e6}
+SCAN_ISSUE = {"blob": "a1dbef2c21d3270bf6bdcf12a8d1e9bd6d947e8d", "slots_per_pair": 10.82,
+              "fp32_int_slots_per_pair": 9.08,
               "workload": "planted 20000 x 100000 x 102 (0.19% of pairs are hits)"}
 # Epilogue issue slots per pair by the operation count of the fused test: one add
 # for D_2, three multiplies by 1/n_i, one multiply and two fused multiply-adds for
