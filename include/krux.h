@@ -90,8 +90,9 @@ typedef struct {
   int32_t scan_grid;    /* CTAs of the fused scan launch */
   int64_t pairs;        /* SNP x trait pairs the last call tested */
   int32_t scan_form;    /* kernel form of the fused scan launch: 0 plain, 1 markers with up to
-                           five groups, 2 permutation batch, 3 general (NaN, dense, cis),
-                           4 plain permutation batch */
+                           five groups, 2 permutation batch, 3 general (dense, cis, NaN
+                           beyond the plain form's coefficient sets), 4 plain permutation
+                           batch, 5 plain with NaN expression */
   int32_t reserved_;
 } krux_profile;
 

@@ -180,6 +180,7 @@ double h_dfk(double p, int df) {
 struct krux_rankset {
   int T = 0, N = 0, Np = 0, rows_pad = 0, n_ttiles = 0;
   bool has_nan = false;  // decided on the host after ranking
+  int nan_tiles_over = 0;  // trait tiles with a trait of more than kNanCMax NaN samples
   RankDev dev{};
   void *mem = nullptr;
   size_t bytes = 0;
@@ -361,7 +362,7 @@ std::string validate_plan(const ScanParams &p, const std::vector<GroupDesc> &g, 
     if ((int64_t)d.nkb * p.ka < (int64_t)d.n_atoms * atom || d.nkb < 1) return bad("group K blocks");
     if (d.nkb > 1 && d.nc * 2 > kTmemSlots) return bad("TMEM slots for K blocks");
     if (d.Np % 16 || d.Np > d.n_atoms * atom) return bad("group K width");
-    if (d.codes && d.Np > p.kpad) return bad("codes width");
+    if (d.codes && (d.codes_k > p.kpad || d.codes_k < 1)) return bad("codes width");
     if (d.pair && (p.layout != 1 || d.nc % 2 != 0)) return bad("chunk pairs");
   }
   return std::string();
@@ -634,7 +635,10 @@ krux_status krux_rank(krux_ctx *ctx, const float *expr, int T, int N, int64_t ld
     std::vector<uint32_t> tn(rs->n_ttiles);
     e = cudaMemcpyAsync(tn.data(), rs->dev.tile_nan, tn.size() * 4, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    for (uint32_t v : tn) any_nan |= v;
+    for (uint32_t v : tn) {
+      any_nan |= v;
+      rs->nan_tiles_over += v > (uint32_t)kNanCMax ? 1 : 0;
+    }
   }
   if (e != cudaSuccess) {
     krux_rankset_free(ctx, rs);
@@ -1115,6 +1119,7 @@ krux_status materialise(krux_ctx *ctx, CallPlan &cp, cudaStream_t s) {
     bs.rows_pad = rs->rows_pad;
     bs.n_ttiles = rs->n_ttiles;
     bs.has_nan = rs->has_nan;
+    bs.nan_tiles_over = rs->nan_tiles_over;
     char *p = base + off[i];
     size_t o2 = 0;
     auto take = [&](size_t bytes) {
@@ -1223,6 +1228,7 @@ struct FusedLaunch {
   int nslots = 0;
   double h1 = 0.0, h2 = 0.0;
   int signed_coef = 0;
+  bool fast_nan = false;  // the plain form's NaN variant (coefficient sets in the codes)
   std::vector<int64_t> boff, moff, coff;
   int layout = 1;
   double hm[4] = {0.0, 0.0, 0.0, 0.0};  // markers with codes 0..4: h_d for d = 1..4
@@ -1237,8 +1243,10 @@ struct FusedLaunch {
 // tables = 1 puts this launch's tables (group descriptors, work items, pack jobs,
 // tie-factor pointers) in the context's second set, so that two prepared launches
 // can be enqueued back to back without a host synchronisation between them.
+// allow_fast_nan = false keeps a call with NaN expression in the general form (the
+// plan is made again that way when the plain form's NaN variant does not fit).
 krux_status prepare_fused(krux_ctx *ctx, CallPlan &cp, const krux_opts *o, FusedLaunch &fl,
-                          cudaStream_t s, int tables = 0) {
+                          cudaStream_t s, int tables = 0, bool allow_fast_nan = true) {
   DevBuf &t_groups = tables ? ctx->groups2 : ctx->groups;
   DevBuf &t_items = tables ? ctx->items2 : ctx->items;
   DevBuf &t_packjobs = tables ? ctx->packjobs2 : ctx->packjobs;
@@ -1271,15 +1279,25 @@ krux_status prepare_fused(krux_ctx *ctx, CallPlan &cp, const krux_opts *o, Fused
   const int layout = lay >= 0 ? lay : 1;
   fl.layout = layout;
   const int atom = layout_atom(layout);
+  // a call that can take the plain form keeps room for its hit-event ring; with
+  // NaN expression it takes the form's NaN variant (per-chunk coefficient sets in
+  // place of the 2-bit codes) when few trait tiles hold traits beyond the last set
+  bool fast_shape = layout == 1 && !cp.multi && cp.param.model < 0 && o->dense_H == nullptr &&
+                    !cp.cis.on;
+  bool any_nan = false, fast_nan = allow_fast_nan && fast_shape;
+  for (auto &g : cp.groups) {
+    fast_nan = fast_nan && g.minp_key == nullptr &&
+               (g.nan_cnt == nullptr || 8 * g.rs->nan_tiles_over <= g.rs->n_ttiles);
+    any_nan = any_nan || g.nan_cnt != nullptr;
+  }
+  fast_nan = fast_nan && any_nan;
+  fast_shape = fast_shape && (!any_nan || fast_nan);
+  fl.fast_nan = fast_nan;
   int kpad = atom, codes_k = 0;
   for (auto &g : cp.groups) {
     kpad = std::max(kpad, round_up(g.rs->Np, atom));
-    if (g.nan_cnt) codes_k = std::max(codes_k, g.rs->Np);
+    if (g.nan_cnt) codes_k = std::max(codes_k, fast_nan ? kCoefNanRows : g.rs->Np);
   }
-  // a call that can take the plain form keeps room for its hit-event ring
-  bool fast_shape = layout == 1 && !cp.multi && cp.param.model < 0 && o->dense_H == nullptr &&
-                    !cp.cis.on;
-  for (auto &g : cp.groups) fast_shape = fast_shape && g.nan_cnt == nullptr;
   LaunchShape sh;
   {
     const int s_nc = ctx->tune_nc, s_nA = ctx->tune_nA, s_ka = ctx->tune_ka;
@@ -1307,7 +1325,7 @@ krux_status prepare_fused(krux_ctx *ctx, CallPlan &cp, const krux_opts *o, Fused
     fl.coff[i] = ctot;
     btot += (nch * kChunkRows * cp.groups[i].rs->Np * 2 + 255) / 256 * 256;
     mtot += nch;
-    if (cp.groups[i].nan_cnt) ctot += nch * cp.groups[i].rs->Np * 2;
+    if (cp.groups[i].nan_cnt) ctot += nch * (fast_nan ? kCoefNanRows : cp.groups[i].rs->Np) * 2;
   }
   KRUX_CUDA(ctx, ctx->B.ensure(std::max<int64_t>(btot, 256)));
   if (cp.multi) {  // second side records, at the same offsets as the first
@@ -1365,6 +1383,9 @@ krux_status prepare_fused(krux_ctx *ctx, CallPlan &cp, const krux_opts *o, Fused
     if (st != KRUX_OK) return st;
     d.meta = ctx->meta.as<ChunkMeta>() + fl.moff[i];
     d.codes = g.nan_cnt ? ctx->codes.as<uint64_t>() + fl.coff[i] : nullptr;
+    d.codes_k = g.nan_cnt ? (fast_nan ? kCoefNanRows : rs->Np) : 0;
+    d.geno = g.geno;
+    d.ldg = g.ldg;
     d.tau = g.tau;
     d.cfac = g.cfac;
     d.nan_cnt = g.nan_cnt;
@@ -1431,8 +1452,9 @@ krux_status prepare_fused(krux_ctx *ctx, CallPlan &cp, const krux_opts *o, Fused
       j.N = g.rs->N;
       j.Np = g.rs->Np;
       j.allow_missing = g.allow_missing;
+      j.coef_nan = j.codes != nullptr && fast_nan ? 1 : 0;
       slots += nch * kChunkSnps;
-      if (j.codes) halves += nch * 2;
+      if (j.codes && !j.coef_nan) halves += nch * 2;
     }
     fl.n_pack_jobs = ng;
     fl.pack_slots = slots;
@@ -1491,7 +1513,7 @@ krux_status prepare_fused(krux_ctx *ctx, CallPlan &cp, const krux_opts *o, Fused
   // in one rank stage, complete data, no dense output, cis window, provisional
   // hits, permutations or markers with more than three groups
   {
-    bool fast = layout == 1 && !p.multi && !p.has_nan && !p.dense && !p.provisional &&
+    bool fast = layout == 1 && !p.multi && (!p.has_nan || fast_nan) && !p.dense && !p.provisional &&
                 (!p.signed_coef || p.perm) && p.cis_window < 0;
     for (const GroupDesc &d : descs) fast = fast && d.pair == 1 && d.nkb == 1;
     p.fast = fast ? 1 : 0;
@@ -1520,6 +1542,9 @@ krux_status prepare_fused(krux_ctx *ctx, CallPlan &cp, const krux_opts *o, Fused
     if (fl.smem + kEvRegion <= kSmemLimit) fl.smem += kEvRegion;
     else p.fast = 0;
   }
+  if (fast_nan && !p.fast)  // the coefficient sets need the plain form: plan again
+    return prepare_fused(ctx, cp, o, fl, s, tables, false);
+  p.fast_nan = fast_nan ? 1 : 0;
   if (p.fast && p.perm && !cp.perm.seed && fl.grid > 0) {
     // each event warp's list for the deferred FP64 pass: about three times the
     // pairs a 200k-SNP batch passes on, at least 8192 and at most 65536 entries
@@ -2697,6 +2722,7 @@ extern "C" krux_status krux_debug_plan(int N, int with_nan, int layout, int nc, 
   d.Np = Np;
   d.n_atoms = (Np + atom - 1) / atom;
   d.codes = with_nan ? reinterpret_cast<const uint64_t *>(16) : nullptr;
+  d.codes_k = codes_k;
   group_shape(sh, kpad, atom, d);
   ScanParams p{};
   p.nc = d.nc;

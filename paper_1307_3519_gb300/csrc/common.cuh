@@ -75,7 +75,8 @@ struct EvEntry {
   int32_t ag;                                   // rank-matrix group (> 0: a permutation)
   float b1, b2;                                 // permutation: the classes' largest decided values
   uint32_t id1, id2;                            // and the identities of the pairs that have them
-  int32_t pad_[2];
+  int32_t nan;                                  // plain form with NaN: the trait's NaN samples
+  int32_t pad_;
 };
 static_assert(sizeof(EvEntry) % 16 == 0, "event entries keep 16-byte alignment");
 // shared memory of the ring: alignment slack, entries, a full barrier and a
@@ -177,7 +178,7 @@ struct RankDev {
   double *cfac;         // [rows_pad] 3 / (K(K+1)C), 0 when degenerate or padding
   uint16_t *nan_cnt;    // [rows_pad] NaN samples of the trait (0 for padding)
   uint16_t *nan_idx;    // [T][N] their sample indices (first nan_cnt entries)
-  uint32_t *tile_nan;   // [rows_pad/128] 1 if any trait of the tile has a NaN
+  uint32_t *tile_nan;   // [rows_pad/128] the largest NaN count of the tile's traits
 };
 
 // One missing-pattern bucket of a scan call: the base rank set's ranks re-derived
@@ -206,7 +207,8 @@ struct PackJob {
   __half *B;
   ChunkMeta *meta;
   uint64_t *codes;          // null: no codes (and no halves)
-  int32_t N, Np, allow_missing, pad_;
+  int32_t N, Np, allow_missing;
+  int32_t coef_nan;         // 1: codes holds ChunkCoefNan blocks instead of 2-bit codes
 };
 
 // ---- one group of a scan launch (a cohort, a missing-pattern bucket, or the
@@ -241,11 +243,37 @@ struct alignas(64) GroupDesc {
   int32_t b_stride;         // shared-memory bytes of one resident B chunk
   int32_t nkb;              // rank-tile K blocks per step (1 = the whole K at once)
   int32_t pair;             // 1: chunks 2j, 2j+1 interleaved per K atom, one N = 256 MMA per pair
-  int32_t pad_;
+  int32_t codes_k;          // 16-byte rows of one chunk's codes block (Np, or kCoefNanRows
+                            // for the plain form's NaN coefficient sets)
   int32_t a_row0, b_row0;   // first row of this group's A / B in tmA / tmB (maps may be shared)
   int64_t nan_ag_stride;    // elements between the NaN index lists of consecutive agroups
                             // (permuted groups: NaN samples sit at permuted positions)
+  const int8_t *geno;       // plain form with NaN: the genotypes, for exact group sizes
+  int64_t ldg;
 };
+
+// The plain form's hot-test coefficients for traits with NaN samples, one block
+// per chunk (in place of the 2-bit codes): set s serves traits with up to
+// kNanSetC[s] NaN samples, the same alpha (u + beta v)^2 + gamma v^2 form as
+// ChunkMeta's first three arrays, built from group sizes max(N_i - C, 1) and the
+// threshold of the smallest df the pair can keep, so that it bounds
+// sum_i D_i^2 / N_i' / h_df' from above whatever genotypes the NaN samples carry
+// (section "Handling missing values": N_i' counts the samples present for both).
+// Traits with more NaN samples than the last set allows always reach the exact test.
+constexpr int kNanSets = 5;
+__host__ __device__ constexpr int nan_set_c(int s) { return s < 4 ? s + 1 : 6; }
+__host__ __device__ constexpr int nan_set_of(int c) {  // -1: beyond the last set
+  return c <= 4 ? c - 1 : (c <= 6 ? 4 : -1);
+}
+constexpr int kNanCMax = 6;
+struct CoefSet {
+  float alpha[kChunkSnps], beta[kChunkSnps], gamma[kChunkSnps];
+};
+struct ChunkCoefNan {
+  CoefSet set[kNanSets];
+};
+constexpr int kCoefNanRows = (int)(sizeof(ChunkCoefNan) / 16);
+static_assert(sizeof(ChunkCoefNan) % 16 == 0 && kCoefNanRows == 240, "coefficient block rows");
 
 // Work item: B tile `btile` (chunks btile*nc .. +nc) of group `group`, against the
 // (agroup, trait-tile) steps [step_begin, step_end) of that group.
@@ -304,9 +332,12 @@ struct ScanParams {
   unsigned int *mc_cnt = nullptr;
   int32_t mc_cap = 0;
   // the plain scan form applies: 32-byte swizzle, every group's chunks paired, no
-  // NaN, no dense output, no cis window, no provisional hits (permutation batches
-  // take its two-sided variant)
+  // dense output, no cis window, no provisional hits (permutation batches take its
+  // two-sided variant; NaN in the expression its variant with coefficient sets,
+  // fast_nan = 1, when few trait tiles hold a trait with more than kNanCMax NaN
+  // samples)
   int32_t fast = 0;
+  int32_t fast_nan = 0;
 };
 
 enum : unsigned int {

@@ -212,6 +212,7 @@ extern "C" krux_status krux_scan_noalloc(const float *expr, int T, int N, int64_
       return KRUX_ECUDA;
     g.meta = meta;
     g.codes = codes;
+    g.codes_k = Np;
     g.tau = r.tau;
     g.cfac = r.cfac;
     g.nan_cnt = r.nan_cnt;

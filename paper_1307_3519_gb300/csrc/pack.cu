@@ -326,6 +326,39 @@ __device__ __forceinline__ void write_meta(ChunkMeta &m, int jj, int n0, int n1,
   m.df[jj] = (uint8_t)df;
 }
 
+// The plain form's coefficient sets of SNP slot jj for traits with NaN samples:
+// set s takes write_meta's alpha, beta, gamma from group sizes max(N_i - C, 1),
+// C = nan_set_c(s) (an empty group stays empty), with the threshold of the
+// smallest df the pair can keep (1/h_1 when some group may vanish).  For a trait
+// with c <= C NaN samples they bound the pair's exact sum_i D_i^2 / N_i' / h_df'
+// from above, whichever groups the NaN samples fall in.
+__device__ __forceinline__ void write_coef_nan(ChunkCoefNan &cb, int jj, int n0, int n1, int n2,
+                                               bool excluded, float rh1, float rh2) {
+  const int groups = (n0 > 0) + (n1 > 0) + (n2 > 0);
+#pragma unroll
+  for (int si = 0; si < kNanSets; ++si) {
+    const int c = nan_set_c(si);
+    float al = 0.f, be = 0.f, ga = 0.f;
+    if (groups > 1 && !excluded) {
+      const int sure = (n0 > c) + (n1 > c) + (n2 > c);  // groups no c NaN samples can empty
+      const float rh = sure >= 3 ? rh2 : rh1;
+      const float q0 = n0 ? 1.f / (float)max(n0 - c, 1) : 0.f, q1 = n1 ? 1.f / (float)max(n1 - c, 1) : 0.f,
+                  q2 = n2 ? 1.f / (float)max(n2 - c, 1) : 0.f;
+      const float a = q0 + q2;
+      if (a > 0.f) {
+        al = a * rh;
+        be = q2 / a;
+        ga = (q1 + q2 * q0 / a) * rh;
+      } else {
+        ga = q1 * rh;  // groups 0 and 2 empty (cannot happen with two groups or more)
+      }
+    }
+    cb.set[si].alpha[jj] = al;
+    cb.set[si].beta[jj] = be;
+    cb.set[si].gamma[jj] = ga;
+  }
+}
+
 // Packs SNP slot j (one warp; j may be the padding of the last chunk).  SNP j is
 // snp_list[j] if a list is given, else snp_begin + j.  SNPs that carry a missing
 // code are packed with zero coefficients here (they are scanned in their
@@ -530,6 +563,9 @@ pack_batch_kernel(const PackJob *__restrict__ jobs, int n_jobs, int64_t total_sl
     const int jj = (int)(j0 % kChunkSnps) + lane;
     if (sn < 0) write_meta(m, jj, 0, 0, 0, true, 0, rh1, rh2, signed_df1, 0, 0.f);
     else write_meta(m, jj, n0, n1, n2, excl, sn, rh1, rh2, signed_df1, 0, 0.f);
+    if (J.coef_nan)
+      write_coef_nan(reinterpret_cast<ChunkCoefNan *>(J.codes)[j0 / kChunkSnps], jj, sn < 0 ? 0 : n0,
+                     sn < 0 ? 0 : n1, sn < 0 ? 0 : n2, sn < 0 || excl, rh1, rh2);
     return;
   }
   const int64_t c = j0 / kChunkSnps;
@@ -596,6 +632,9 @@ pack_batch_kernel(const PackJob *__restrict__ jobs, int n_jobs, int64_t total_sl
   } else {
     write_meta(m, jj0 + lane, my_n0, my_n1, my_n2, excl, my_s, rh1, rh2, signed_df1, 0, 0.f);
   }
+  if (J.coef_nan)
+    write_coef_nan(reinterpret_cast<ChunkCoefNan *>(J.codes)[c], jj0 + lane, my_s < 0 ? 0 : my_n0,
+                   my_s < 0 ? 0 : my_n1, my_s < 0 ? 0 : my_n2, my_s < 0 || excl, rh1, rh2);
 }
 
 __device__ __forceinline__ uint64_t spread_bits(uint32_t v) {
@@ -650,7 +689,7 @@ codes_batch_kernel(const PackJob *__restrict__ jobs, int n_jobs, int64_t total_h
   const int64_t x = (int64_t)blockIdx.x * kPackWarps + warp;
   if (x >= total_halves) return;
   const PackJob &J = jobs[find_job(jobs, n_jobs, x, true)];
-  if (J.codes == nullptr) return;  // (such jobs span no halves)
+  if (J.codes == nullptr || J.coef_nan) return;  // (such jobs span no halves)
   codes_half(J.geno, J.ldg, J.N, J.Np, J.snp_list, J.snp_begin, J.n_snps, x - J.half0, J.codes,
              lane);
 }

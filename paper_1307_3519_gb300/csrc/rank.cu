@@ -89,7 +89,7 @@ rank_kernel(const float *__restrict__ expr, int T, int N, int64_t ld, int Np, Ra
     r.tie[t] = tie;
     r.K[t] = K;
     r.nan_cnt[t] = (uint16_t)(N - K);
-    if (N - K > 0) atomicOr(&r.tile_nan[t / kTileM], 1u);
+    if (N - K > 0) atomicMax(&r.tile_nan[t / kTileM], (uint32_t)(N - K));
   }
 }
 

@@ -819,16 +819,18 @@ __device__ __forceinline__ void tmem_ld_half(uint32_t taddr, uint32_t (&u)[kFast
 // true when some pair may lie at or above the lower edge of the band (q >= 0),
 // two SNPs per packed instruction, w = u + beta v, q = alpha w^2 + gamma v^2 -
 // tau (1 - margin).  Blocks of 16 SNPs; two sign accumulators.
+// The coefficients come from three arrays of a chunk (ChunkMeta's, or a CoefSet).
 template <int NS>
-__device__ __forceinline__ bool hit_fast_w(const uint32_t (&d0)[NS], const uint32_t (&d1)[NS],
-                                           const ChunkMeta &m, int off, float ntlo) {
+__device__ __forceinline__ bool hit_fast_wc(const uint32_t (&d0)[NS], const uint32_t (&d1)[NS],
+                                            const float *alpha, const float *beta,
+                                            const float *gamma, int off, float ntlo) {
   const uint64_t nt2 = pk2(__float_as_uint(ntlo), __float_as_uint(ntlo));
   uint32_t acc0 = 0xffffffffu, acc1 = 0xffffffffu;  // AND of the sign bits (two chains)
 #pragma unroll
   for (int b = 0; b < NS / 16; ++b) {
-    const uint64_t *al = reinterpret_cast<const uint64_t *>(m.alpha + off + 16 * b);
-    const uint64_t *be = reinterpret_cast<const uint64_t *>(m.beta + off + 16 * b);
-    const uint64_t *ga = reinterpret_cast<const uint64_t *>(m.gamma + off + 16 * b);
+    const uint64_t *al = reinterpret_cast<const uint64_t *>(alpha + off + 16 * b);
+    const uint64_t *be = reinterpret_cast<const uint64_t *>(beta + off + 16 * b);
+    const uint64_t *ga = reinterpret_cast<const uint64_t *>(gamma + off + 16 * b);
 #pragma unroll
     for (int j = 0; j < 8; j += 2) {
       const ulonglong2 A = *reinterpret_cast<const ulonglong2 *>(al + j);
@@ -855,6 +857,11 @@ __device__ __forceinline__ bool hit_fast_w(const uint32_t (&d0)[NS], const uint3
     if (b + 1 < NS / 16) asm volatile("" ::: "memory");
   }
   return (int)(acc0 & acc1) >= 0;
+}
+template <int NS>
+__device__ __forceinline__ bool hit_fast_w(const uint32_t (&d0)[NS], const uint32_t (&d1)[NS],
+                                           const ChunkMeta &m, int off, float ntlo) {
+  return hit_fast_wc<NS>(d0, d1, m.alpha, m.beta, m.gamma, off, ntlo);
 }
 
 // Two-sided hot test of a permutation batch, whose df-1 SNPs carry a negated form
@@ -980,8 +987,8 @@ __device__ __forceinline__ bool ev_submit(const EvRing &ev, const uint32_t (&u)[
                                           const uint32_t (&v)[kEvSnps], bool need,
                                           const ChunkMeta &m, int off, float tau, double cfac,
                                           int trait, int group, int ag, float b1, float b2,
-                                          uint32_t id1, uint32_t id2, const ScanParams &p,
-                                          uint32_t abort_addr, int lane) {
+                                          uint32_t id1, uint32_t id2, int nan,
+                                          const ScanParams &p, uint32_t abort_addr, int lane) {
   uint32_t lanes = __ballot_sync(0xffffffffu, need);
   unsigned long long t = 0;
   if (lane == 0) t = atomicAdd(ev.word, (unsigned long long)__popc(lanes)) & kEvTicketMask;
@@ -1026,6 +1033,7 @@ __device__ __forceinline__ bool ev_submit(const EvRing &ev, const uint32_t (&u)[
       E.b2 = b2;
       E.id1 = id1;
       E.id2 = id2;
+      E.nan = nan;
     }
     __threadfence_block();
     __syncwarp();
@@ -1054,6 +1062,10 @@ struct EvGroup {
   double *minp_key;
   unsigned long long *minp_bound;
   int64_t rows;
+  const uint16_t *nan_idx;  // NaN sample lists, N entries per trait
+  const int8_t *geno;       // genotype rows (by output SNP index)
+  int64_t ldg;
+  int N;
 };
 
 __device__ __forceinline__ void ev_group(EvGroup &G, const ScanParams &p, int group) {
@@ -1068,6 +1080,10 @@ __device__ __forceinline__ void ev_group(EvGroup &G, const ScanParams &p, int gr
   G.minp_key = g.minp_key;
   G.minp_bound = g.minp_bound;
   G.rows = g.rows_per_agroup;
+  G.nan_idx = g.nan_idx;
+  G.geno = g.geno;
+  G.ldg = g.ldg;
+  G.N = g.N;
 }
 
 // A permuted pair's entry (section "P-value calculation and empirical FDR
@@ -1156,13 +1172,20 @@ __device__ __forceinline__ void ev_minp(const EvEntry &E, EvGroup &G, const Scan
   }
 }
 
+// Event modes: the plain scan, a permutation batch, the plain scan with NaN.
+enum EvMode { kEvPlain = 0, kEvPerm = 1, kEvNan = 2 };
+
 // An event warp's work on one entry: lanes j < kEvSnps classify the pair (trait,
 // SNP j) in the same FP32 form as the hot test (at or above the upper band edge:
 // hit; inside the band: decided in FP64 from the exact sums) and the hits are
 // appended in SNP order, one record per lane, into this warp's staging region of
 // kEpiWarps / 2 segments of the CTA (`wn` records already there); what does not
-// fit goes to the group's list through its counter.  Returns the number of hits.
-template <bool kPerm>
+// fit goes to the group's list through its counter.  For a trait with NaN
+// samples (kEvNan) the pair's group sizes are first made exact (section "Handling
+// missing values": N_i' counts the samples present for both): the genotypes of
+// the trait's NaN samples at the SNP are taken off N_i, and the form is evaluated
+// with those sizes and the df they leave.  Returns the number of hits.
+template <int kMode>
 __device__ __forceinline__ unsigned int ev_process(const EvEntry &E, EvGroup &G, const ScanParams &p,
                                                    unsigned int wn, int lane, int ev_warp,
                                                    unsigned int &mcn) {
@@ -1173,16 +1196,45 @@ __device__ __forceinline__ unsigned int ev_process(const EvEntry &E, EvGroup &G,
   const float w = fmaf(E.beta[j], v, u);
   const float sv = fmaf(E.alpha[j] * w, w, (E.gamma[j] * v) * v);
   float s = sv;
-  if constexpr (kPerm) {
+  uint32_t n01 = E.n01[j], n2df = E.n2df[j];
+  if constexpr (kMode == kEvPerm) {
     if (E.ag > 0) {  // a permuted pair: min-p and FDR work, no hit record
       ev_minp(E, G, p, lane, sv, mcn, ev_warp);
       return 0u;
     }
     s = fabsf(sv);  // df-1 values are negated in permutation batches
   }
+  if constexpr (kMode == kEvNan) {
+    if (E.nan > 0) {
+      ev_group(G, p, E.group);
+      int n0 = (int)(n01 & 0xffffu), n1 = (int)(n01 >> 16), n2 = (int)(n2df & 0xffffu);
+      const int sn = E.snp[j];
+      if (act && sn >= 0) {
+        const uint16_t *ni = G.nan_idx + (int64_t)E.trait * G.N;
+        const int8_t *gr = G.geno + (int64_t)sn * G.ldg;
+        for (int i = 0; i < E.nan; ++i) {
+          const int code = gr[ni[i]];  // -1 (missing): in no group
+          n0 -= code == 0;
+          n1 -= code == 1;
+          n2 -= code == 2;
+        }
+      }
+      const int df = df_of(n0, n1, n2);
+      s = 0.f;
+      if (act && sn >= 0 && df > 0) {
+        const float w = -(u + v);
+        float q = 0.f;
+        if (n0 > 0) q += u * u / (float)n0;
+        if (n1 > 0) q += v * v / (float)n1;
+        if (n2 > 0) q += w * w / (float)n2;
+        s = q / (df == 1 ? p.h1 : p.h2);
+      }
+      n01 = (uint32_t)n0 | ((uint32_t)n1 << 16);
+      n2df = (uint32_t)n2 | ((uint32_t)df << 16);
+    }
+  }
   const bool cand = act && s + -tau * (1.f - p.margin) >= 0.f;
   bool hit = cand && s + -tau * (1.f + p.margin) >= 0.f;
-  const uint32_t n01 = E.n01[j], n2df = E.n2df[j];
   if (__any_sync(0xffffffffu, cand && !hit)) {  // inside the band: FP64 (rare)
     if (cand && !hit)
       hit = decide64_inl(u, v, (int)(n01 & 0xffffu), (int)(n01 >> 16), (int)(n2df & 0xffffu),
@@ -1547,9 +1599,17 @@ __device__ __noinline__ double minp_step_best(MinpLead *L, double cfac) {
 // plain scan of rank sets with NaN (exact group sizes in the hot test); the
 // producer and MMA warps are the same in all four.  Separate forms keep the
 // state of one out of the registers of the others.
-enum ScanForm { kFormScan = 0, kFormMulti = 1, kFormPerm = 2, kFormNan = 3, kFormScanPerm = 4 };
-// the plain scan form and its two-sided variant for permutation batches
-constexpr bool fast_form(int f) { return f == kFormScan || f == kFormScanPerm; }
+enum ScanForm {
+  kFormScan = 0,
+  kFormMulti = 1,
+  kFormPerm = 2,
+  kFormNan = 3,
+  kFormScanPerm = 4,
+  kFormScanNan = 5
+};
+// the plain scan form, its two-sided variant for permutation batches and its
+// variant for expression with NaN
+constexpr bool fast_form(int f) { return f == kFormScan || f == kFormScanPerm || f == kFormScanNan; }
 
 // Warp roles of a kernel form: the epilogue warps first, then the producer and
 // the MMA issuer (the plain scan form also has two idle warps after them).
@@ -1675,7 +1735,7 @@ __global__ void __launch_bounds__(ScanRoles<kForm>::kThreads, 1)
         const uint32_t abytes = atom_bytes(p.layout);
         const int ak = (int)atom_k(p.layout);
         const uint32_t b_tx = (uint32_t)g->n_atoms * abytes;
-        const uint32_t codes_bytes = g->codes ? (uint32_t)g->Np * 16u : 0u;
+        const uint32_t codes_bytes = g->codes ? (uint32_t)g->codes_k * 16u : 0u;
         for (int c = 0; c < nc_item; ++c) {
           const uint32_t ph = (b_bits >> c) & 1u;
           if (!wait_bar(b_empty(c), ph ^ 1u, wc, 1)) goto producer_done;
@@ -1690,7 +1750,7 @@ __global__ void __launch_bounds__(ScanRoles<kForm>::kThreads, 1)
                         b_full(c));
           bulk_load(smem_u32(smeta + c), g->meta + chunk, (uint32_t)sizeof(ChunkMeta), b_full(c));
           if (codes_bytes)
-            bulk_load(smem_u32(scodes + (size_t)c * codes_stride), g->codes + (size_t)chunk * g->Np * 2,
+            bulk_load(smem_u32(scodes + (size_t)c * codes_stride), g->codes + (size_t)chunk * g->codes_k * 2,
                       codes_bytes, b_full(c));
           b_used |= 1u << c;
           b_last = (b_last & ~(1u << c)) | (ph << c);
@@ -1948,7 +2008,8 @@ __global__ void __launch_bounds__(ScanRoles<kForm>::kThreads, 1)
         }
         got = __shfl_sync(0xffffffffu, got, 0);
         if (!got) break;
-        wn += ev_process<kForm == kFormScanPerm>(ev.ent[b], G, p, wn, lane, e, mcn);
+        wn += ev_process<kForm == kFormScanPerm ? kEvPerm : (kForm == kFormScanNan ? kEvNan : kEvPlain)>(
+            ev.ent[b], G, p, wn, lane, e, mcn);
         __syncwarp();
         if (lane == 0) {  // this use of the buffer is finished
           __threadfence_block();
@@ -1983,7 +2044,14 @@ __global__ void __launch_bounds__(ScanRoles<kForm>::kThreads, 1)
       // the decided one less the margin (at most `cap`: the band's lower edge while
       // FDR counts are on).  The unpermuted group tests both signs against tau.
       constexpr bool kTwo = kForm == kFormScanPerm;
+      constexpr bool kNan = kForm == kFormScanNan;
       constexpr float kBoundMin = 1e-30f, kBoundMax = 1e30f;
+      // expression with NaN: this lane's trait has nan_c NaN samples; its hot test
+      // takes coefficient set nset - 1 of the chunk's block (0: the chunk metadata's
+      // exact coefficients; -1: more NaN samples than any set covers, every pair
+      // goes to the exact test)
+      int nan_c = 0, nset = 0;
+      int cpair = 0;  // the chunk pair_slot works on, within the work item
       float mx1 = 0.f, mx2 = 0.f, bnd1 = 0.f, bnd2 = 0.f;  // decided values, hot-test bounds
       uint32_t id1 = 0u, id2 = 0u;
       int ag = 0;  // the step's rank-matrix group (> 0: a permutation)
@@ -2002,8 +2070,15 @@ __global__ void __launch_bounds__(ScanRoles<kForm>::kThreads, 1)
       };
       auto test = [&](const uint32_t(&x0)[kH], const uint32_t(&x1)[kH], const ChunkMeta &mc, int o,
                       float ntlo) -> bool {
-        if constexpr (kTwo) return hit_fast_w2<kH>(x0, x1, mc, o, -bnd2, bnd1 + bnd2);
-        else return hit_fast_w<kH>(x0, x1, mc, o, ntlo);
+        if constexpr (kTwo) {
+          return hit_fast_w2<kH>(x0, x1, mc, o, -bnd2, bnd1 + bnd2);
+        } else if constexpr (kNan) {
+          const float *cf = nset > 0 ? reinterpret_cast<const CoefSet *>(scodes + (size_t)cpair * codes_stride)[nset - 1].alpha
+                                     : mc.alpha;
+          return hit_fast_wc<kH>(x0, x1, cf, cf + kChunkSnps, cf + 2 * kChunkSnps, o, ntlo);
+        } else {
+          return hit_fast_w<kH>(x0, x1, mc, o, ntlo);
+        }
       };
       // a permuted block past the hot test: the lane's pairs that still need the
       // event warps (past the bounds but not exact copies of a class's decided pair
@@ -2042,7 +2117,6 @@ __global__ void __launch_bounds__(ScanRoles<kForm>::kThreads, 1)
       // one accumulator pair: wait for it, load this warp's two halves (the second
       // while the first is tested), release it, test the second half, hand any
       // candidate half-block to the event warps; false if a wait gave up
-      int cpair = 0;  // the chunk pair_slot works on, within the work item
       auto pair_slot = [&](uint32_t ps, uint32_t phase, const ChunkMeta &mc, float tau,
                            double cfac, float ntlo, int trait, int group) -> bool {
         if (!__all_sync(0xffffffffu, wait_bar_p(t_full(ps), phase, p, abort_addr, 7))) return false;
@@ -2084,8 +2158,8 @@ __global__ void __launch_bounds__(ScanRoles<kForm>::kThreads, 1)
           if constexpr (kTwo)
             if (ag > 0 && need_a) real = minp_filter(a0, a1, mc, off, tau, n1, n2, k1, k2);
           if (__any_sync(0xffffffffu, real) &&
-              !ev_submit(ev, a0, a1, real, mc, off, tau, cfac, trait, group, ag, mx1, mx2, id1, id2, p,
-                         abort_addr, lane))
+              !ev_submit(ev, a0, a1, real, mc, off, tau, cfac, trait, group, ag, mx1, mx2, id1, id2,
+                         nan_c, p, abort_addr, lane))
             return false;
           if constexpr (kTwo)
             if (ag > 0 && real) {
@@ -2104,7 +2178,7 @@ __global__ void __launch_bounds__(ScanRoles<kForm>::kThreads, 1)
             if (ag > 0 && need_b) real = minp_filter(b0, b1, mc, off + kH, tau, n1, n2, k1, k2);
           if (__any_sync(0xffffffffu, real) &&
               !ev_submit(ev, b0, b1, real, mc, off + kH, tau, cfac, trait, group, ag, mx1, mx2, id1, id2,
-                         p, abort_addr, lane))
+                         nan_c, p, abort_addr, lane))
             return false;
           if constexpr (kTwo)
             if (ag > 0 && real) {
@@ -2137,6 +2211,10 @@ __global__ void __launch_bounds__(ScanRoles<kForm>::kThreads, 1)
           const uint8_t *tcp = stc + (size_t)tc_e * kTcBytes;
           const float tau = reinterpret_cast<const float *>(tcp)[row];
           const double cfac = reinterpret_cast<const double *>(tcp + 512)[row];
+          if constexpr (kNan) {
+            nan_c = g.nan_cnt ? (int)reinterpret_cast<const uint16_t *>(tcp + 2560)[row] : 0;
+            nset = nan_c == 0 ? 0 : (nan_c <= kNanCMax ? nan_set_of(nan_c) + 1 : -1);
+          }
           if constexpr (kTwo) {
             // unpermuted group: both signs against tau (less the margin); a
             // permuted one: the classes' decided values staged for the step
@@ -2167,7 +2245,10 @@ __global__ void __launch_bounds__(ScanRoles<kForm>::kThreads, 1)
             tc_e = 0;
             tc_phase ^= 1u;
           }
-          const float ntlo = -tau * (1.f - p.margin);
+          float ntlo = -tau * (1.f - p.margin);
+          // (a trait beyond the last set: +inf lets every pair through)
+          if constexpr (kNan)
+            if (nset < 0 && tau < kBoundMax) ntlo = __int_as_float(0x7f800000);
           const int trait = tt * kTileM + row;
           {
             for (int c0 = 0; c0 < nc_item; c0 += 2) {
@@ -2743,6 +2824,9 @@ cudaError_t scan_set_smem_all(size_t smem) {
   cudaError_t e = cudaFuncSetAttribute(krux_scan_kernel<kFormScan>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(krux_scan_kernel<kFormScanNan>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem);
+  if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(krux_scan_kernel<kFormScanPerm>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -2760,7 +2844,8 @@ cudaError_t scan_set_smem_all(size_t smem) {
 int scan_form_of(const ScanParams &p) {
   if (p.multi) return kFormMulti;
   if (p.perm) return p.fast && fast_form_ok() ? kFormScanPerm : kFormPerm;
-  return p.fast && fast_form_ok() ? kFormScan : kFormNan;
+  if (p.fast && fast_form_ok()) return p.fast_nan ? kFormScanNan : kFormScan;
+  return kFormNan;
 }
 
 cudaError_t launch_scan_only(const ScanParams &p, int grid, size_t smem, cudaStream_t s) {
@@ -2770,6 +2855,8 @@ cudaError_t launch_scan_only(const ScanParams &p, int grid, size_t smem, cudaStr
     krux_scan_kernel<kFormScanPerm><<<grid, kFastThreads, smem, s>>>(p);
   else if (p.perm)
     krux_scan_kernel<kFormPerm><<<grid, kScanThreads, smem, s>>>(p);
+  else if (p.fast && p.fast_nan && fast_form_ok())
+    krux_scan_kernel<kFormScanNan><<<grid, kFastThreads, smem, s>>>(p);
   else if (p.fast && fast_form_ok())
     krux_scan_kernel<kFormScan><<<grid, kFastThreads, smem, s>>>(p);
   else
@@ -2787,13 +2874,15 @@ bool fast_form_ok() {
   static std::atomic<int> ok{-1};
   int v = ok.load(std::memory_order_acquire);
   if (v < 0) {
-    // both plain-form kernels were built at the register count their warp
-    // roles' setmaxnreg split assumes
-    cudaFuncAttributes a, b;
+    // the plain-form kernels were built at the register count their warp roles'
+    // setmaxnreg split assumes
+    cudaFuncAttributes a, b, c;
     v = cudaFuncGetAttributes(&a, krux_scan_kernel<kFormScan>) == cudaSuccess &&
                 cudaFuncGetAttributes(&b, krux_scan_kernel<kFormScanPerm>) == cudaSuccess &&
+                cudaFuncGetAttributes(&c, krux_scan_kernel<kFormScanNan>) == cudaSuccess &&
                 a.numRegs == kFastRegsLaunch && a.maxThreadsPerBlock >= kFastThreads &&
-                b.numRegs == kFastRegsLaunch && b.maxThreadsPerBlock >= kFastThreads
+                b.numRegs == kFastRegsLaunch && b.maxThreadsPerBlock >= kFastThreads &&
+                c.numRegs == kFastRegsLaunch && c.maxThreadsPerBlock >= kFastThreads
             ? 1
             : 0;
     ok.store(v, std::memory_order_release);

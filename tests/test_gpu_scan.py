@@ -210,6 +210,35 @@ def test_nan_counts_per_trait(kx, oracle_mod, with_missing_geno):
     check_hits(res, orc, np.arange(168), np.arange(2100), pth)
 
 
+@pytest.mark.parametrize("with_missing_geno", [False, True])
+def test_nan_plain_form_variant(kx, oracle_mod, with_missing_geno):
+    """The plain form's NaN variant: traits with 0..6 NaN samples (trait t has t
+    mod 7) take the coefficient set of their count, and a few traits of the first
+    tile have more (9, 30, and 101 of 102: degenerate), so that every pair of
+    theirs reaches the exact test with its exact group sizes.  Nine trait tiles
+    (the last ragged), one of them with traits beyond the sets: the call takes form
+    5, and its hit set must be the oracle's."""
+    d = synth.config(2, T=1030, S=2100, seed=35)
+    x = d["expr"].copy()
+    g = d["geno"].copy()
+    rng = np.random.default_rng(11)
+    for t in range(x.shape[0]):
+        c = {5: 9, 6: 30, 13: 101}.get(t, t % 7)
+        x[t, rng.choice(x.shape[1], c, replace=False)] = np.nan
+    if with_missing_geno:
+        synth.add_missing_genotypes(rng, g, snp_frac=0.2, n_patterns=12, per_pattern=3)
+    pth = 2e-3
+    orc = oracle_mod.scan(x, g, pth)
+    import paper_1307_3519_gb300 as k
+    ctx = k.Krux(0)
+    ctx.set_profiling(True)
+    rs = ctx.krux_rank(_dev(x))
+    res = ctx.krux_scan(rs, _dev(g), pth, capacity=1030 * 2100)
+    assert ctx.profile()["scan_form"] == 5
+    check_hits(res, orc, np.arange(1030), np.arange(2100), pth)
+    ctx.close()
+
+
 def test_missing_genotypes(kx, oracle_mod):
     """Missing-value workload at reduced size: -1 genotypes in missing-sample
     patterns and NaN expression; ranks over the samples present in both."""
