@@ -353,7 +353,7 @@ std::string validate_plan(const ScanParams &p, const std::vector<GroupDesc> &g, 
   if (smem > kSmemLimit) return bad("shared memory above the per-CTA limit");
   if (p.nA < 1 || p.nc < 1 || p.nc > kTmemSlots) return bad("stage or chunk count");
   if (p.a_tile_bytes % 1024 || p.b_region % 1024 || p.a_tile_bytes != 256 * p.ka) return bad("region alignment");
-  if (p.ka % atom || p.kpad % 16) return bad("K widths");
+  if (p.ka % atom || p.kpad < 16) return bad("K widths");
   if ((size_t)p.nA * p.a_tile_bytes + (size_t)p.b_region + 1024 > smem) return bad("regions exceed the allocation");
   for (const GroupDesc &d : g) {
     if (d.nc < 1 || d.nc > p.nc) return bad("group chunk count");

@@ -208,7 +208,8 @@ struct PackJob {
   ChunkMeta *meta;
   uint64_t *codes;          // null: no codes (and no halves)
   int32_t N, Np, allow_missing;
-  int32_t coef_nan;         // 1: codes holds ChunkCoefNan blocks instead of 2-bit codes
+  int32_t coef_nan;         // 1: codes holds the plain form's coefficient blocks (kCoefNanBytes
+                            // per chunk) instead of 2-bit codes
 };
 
 // ---- one group of a scan launch (a cohort, a missing-pattern bucket, or the
@@ -269,11 +270,21 @@ constexpr int kNanCMax = 6;
 struct CoefSet {
   float alpha[kChunkSnps], beta[kChunkSnps], gamma[kChunkSnps];
 };
-struct ChunkCoefNan {
-  CoefSet set[kNanSets];
-};
-constexpr int kCoefNanRows = (int)(sizeof(ChunkCoefNan) / 16);
-static_assert(sizeof(ChunkCoefNan) % 16 == 0 && kCoefNanRows == 240, "coefficient block rows");
+// Set s starts at byte 16 (s + 1) + 768 s of a chunk's block: for one SNP the sets
+// and the chunk metadata's coefficients then sit in different 16-byte bank groups
+// of shared memory, and a warp whose lanes use different sets reads them in one pass.
+constexpr int kCoefSetStride = (int)sizeof(CoefSet) + 16;
+constexpr int kCoefNanBytes = 16 + kNanSets * kCoefSetStride;
+constexpr int kCoefNanRows = kCoefNanBytes / 16;
+static_assert(sizeof(CoefSet) == 768 && kCoefNanBytes % 16 == 0 && kCoefNanRows == 246,
+              "coefficient block layout");
+__host__ __device__ inline CoefSet *coef_set(void *block, int s) {
+  return reinterpret_cast<CoefSet *>(static_cast<uint8_t *>(block) + 16 + s * kCoefSetStride);
+}
+__host__ __device__ inline const CoefSet *coef_set(const void *block, int s) {
+  return reinterpret_cast<const CoefSet *>(static_cast<const uint8_t *>(block) + 16 +
+                                           s * kCoefSetStride);
+}
 
 // Work item: B tile `btile` (chunks btile*nc .. +nc) of group `group`, against the
 // (agroup, trait-tile) steps [step_begin, step_end) of that group.

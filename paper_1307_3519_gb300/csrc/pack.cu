@@ -332,7 +332,7 @@ __device__ __forceinline__ void write_meta(ChunkMeta &m, int jj, int n0, int n1,
 // smallest df the pair can keep (1/h_1 when some group may vanish).  For a trait
 // with c <= C NaN samples they bound the pair's exact sum_i D_i^2 / N_i' / h_df'
 // from above, whichever groups the NaN samples fall in.
-__device__ __forceinline__ void write_coef_nan(ChunkCoefNan &cb, int jj, int n0, int n1, int n2,
+__device__ __forceinline__ void write_coef_nan(void *block, int jj, int n0, int n1, int n2,
                                                bool excluded, float rh1, float rh2) {
   const int groups = (n0 > 0) + (n1 > 0) + (n2 > 0);
 #pragma unroll
@@ -353,9 +353,10 @@ __device__ __forceinline__ void write_coef_nan(ChunkCoefNan &cb, int jj, int n0,
         ga = q1 * rh;  // groups 0 and 2 empty (cannot happen with two groups or more)
       }
     }
-    cb.set[si].alpha[jj] = al;
-    cb.set[si].beta[jj] = be;
-    cb.set[si].gamma[jj] = ga;
+    CoefSet *cs = coef_set(block, si);
+    cs->alpha[jj] = al;
+    cs->beta[jj] = be;
+    cs->gamma[jj] = ga;
   }
 }
 
@@ -564,7 +565,7 @@ pack_batch_kernel(const PackJob *__restrict__ jobs, int n_jobs, int64_t total_sl
     if (sn < 0) write_meta(m, jj, 0, 0, 0, true, 0, rh1, rh2, signed_df1, 0, 0.f);
     else write_meta(m, jj, n0, n1, n2, excl, sn, rh1, rh2, signed_df1, 0, 0.f);
     if (J.coef_nan)
-      write_coef_nan(reinterpret_cast<ChunkCoefNan *>(J.codes)[j0 / kChunkSnps], jj, sn < 0 ? 0 : n0,
+      write_coef_nan(reinterpret_cast<uint8_t *>(J.codes) + (j0 / kChunkSnps) * kCoefNanBytes, jj, sn < 0 ? 0 : n0,
                      sn < 0 ? 0 : n1, sn < 0 ? 0 : n2, sn < 0 || excl, rh1, rh2);
     return;
   }
@@ -633,7 +634,7 @@ pack_batch_kernel(const PackJob *__restrict__ jobs, int n_jobs, int64_t total_sl
     write_meta(m, jj0 + lane, my_n0, my_n1, my_n2, excl, my_s, rh1, rh2, signed_df1, 0, 0.f);
   }
   if (J.coef_nan)
-    write_coef_nan(reinterpret_cast<ChunkCoefNan *>(J.codes)[c], jj0 + lane, my_s < 0 ? 0 : my_n0,
+    write_coef_nan(reinterpret_cast<uint8_t *>(J.codes) + c * kCoefNanBytes, jj0 + lane, my_s < 0 ? 0 : my_n0,
                    my_s < 0 ? 0 : my_n1, my_s < 0 ? 0 : my_n2, my_s < 0 || excl, rh1, rh2);
 }
 

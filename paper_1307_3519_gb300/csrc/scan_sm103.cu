@@ -987,8 +987,8 @@ __device__ __forceinline__ bool ev_submit(const EvRing &ev, const uint32_t (&u)[
                                           const uint32_t (&v)[kEvSnps], bool need,
                                           const ChunkMeta &m, int off, float tau, double cfac,
                                           int trait, int group, int ag, float b1, float b2,
-                                          uint32_t id1, uint32_t id2, int nan,
-                                          const ScanParams &p, uint32_t abort_addr, int lane) {
+                                          uint32_t id1, uint32_t id2, int nan, const ScanParams &p,
+                                          uint32_t abort_addr, int lane) {
   uint32_t lanes = __ballot_sync(0xffffffffu, need);
   unsigned long long t = 0;
   if (lane == 0) t = atomicAdd(ev.word, (unsigned long long)__popc(lanes)) & kEvTicketMask;
@@ -1205,18 +1205,25 @@ __device__ __forceinline__ unsigned int ev_process(const EvEntry &E, EvGroup &G,
     s = fabsf(sv);  // df-1 values are negated in permutation batches
   }
   if constexpr (kMode == kEvNan) {
-    if (E.nan > 0) {
+    const int c = E.nan;
+    if (c > 0) {
       ev_group(G, p, E.group);
       int n0 = (int)(n01 & 0xffffu), n1 = (int)(n01 >> 16), n2 = (int)(n2df & 0xffffu);
       const int sn = E.snp[j];
       if (act && sn >= 0) {
         const uint16_t *ni = G.nan_idx + (int64_t)E.trait * G.N;
         const int8_t *gr = G.geno + (int64_t)sn * G.ldg;
-        for (int i = 0; i < E.nan; ++i) {
-          const int code = gr[ni[i]];  // -1 (missing): in no group
-          n0 -= code == 0;
-          n1 -= code == 1;
-          n2 -= code == 2;
+        for (int i = 0; i < c; i += 4) {  // four samples' loads in flight at once
+          int k[4];
+#pragma unroll
+          for (int t = 0; t < 4; ++t) k[t] = i + t < c ? (int)ni[i + t] : -1;
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            const int code = k[t] >= 0 ? (int)gr[k[t]] : -1;  // -1 (missing): in no group
+            n0 -= code == 0;
+            n1 -= code == 1;
+            n2 -= code == 2;
+          }
         }
       }
       const int df = df_of(n0, n1, n2);
@@ -2046,11 +2053,16 @@ __global__ void __launch_bounds__(ScanRoles<kForm>::kThreads, 1)
       constexpr bool kTwo = kForm == kFormScanPerm;
       constexpr bool kNan = kForm == kFormScanNan;
       constexpr float kBoundMin = 1e-30f, kBoundMax = 1e30f;
-      // expression with NaN: this lane's trait has nan_c NaN samples; its hot test
-      // takes coefficient set nset - 1 of the chunk's block (0: the chunk metadata's
-      // exact coefficients; -1: more NaN samples than any set covers, every pair
-      // goes to the exact test)
-      int nan_c = 0, nset = 0;
+      // expression with NaN: the bound of this lane's trait is coefficient set
+      // nset - 1 of the chunk's block (0: the chunk metadata's exact coefficients;
+      // -1: more NaN samples than any set covers, every pair goes to the exact
+      // test).  The warp first tests all its lanes with the loosest set any of them
+      // needs (wset: one address for the whole warp), and only when some lane
+      // passes, and the lanes' sets differ (mixed), each lane again with its own set
+      // (lanes reading different addresses cost several shared-memory passes per
+      // load).  One register: nset + 1 in bits 0-3, wset in bits 4-7, mixed bit 8,
+      // the trait's NaN count from bit 9.
+      int nsw = 1;
       int cpair = 0;  // the chunk pair_slot works on, within the work item
       float mx1 = 0.f, mx2 = 0.f, bnd1 = 0.f, bnd2 = 0.f;  // decided values, hot-test bounds
       uint32_t id1 = 0u, id2 = 0u;
@@ -2073,9 +2085,15 @@ __global__ void __launch_bounds__(ScanRoles<kForm>::kThreads, 1)
         if constexpr (kTwo) {
           return hit_fast_w2<kH>(x0, x1, mc, o, -bnd2, bnd1 + bnd2);
         } else if constexpr (kNan) {
-          const float *cf = nset > 0 ? reinterpret_cast<const CoefSet *>(scodes + (size_t)cpair * codes_stride)[nset - 1].alpha
-                                     : mc.alpha;
-          return hit_fast_wc<kH>(x0, x1, cf, cf + kChunkSnps, cf + 2 * kChunkSnps, o, ntlo);
+          const uint8_t *blk = scodes + (size_t)cpair * codes_stride;
+          const int wset = (nsw >> 4) & 15, nset = (nsw & 15) - 1;
+          const float *cw = wset > 0 ? coef_set(blk, wset - 1)->alpha : mc.alpha;
+          bool need = hit_fast_wc<kH>(x0, x1, cw, cw + kChunkSnps, cw + 2 * kChunkSnps, o, ntlo);
+          if (((nsw >> 8) & 1) && __any_sync(0xffffffffu, need)) {
+            const float *cf = nset > 0 ? coef_set(blk, nset - 1)->alpha : mc.alpha;
+            need = hit_fast_wc<kH>(x0, x1, cf, cf + kChunkSnps, cf + 2 * kChunkSnps, o, ntlo) && need;
+          }
+          return need;
         } else {
           return hit_fast_w<kH>(x0, x1, mc, o, ntlo);
         }
@@ -2159,7 +2177,7 @@ __global__ void __launch_bounds__(ScanRoles<kForm>::kThreads, 1)
             if (ag > 0 && need_a) real = minp_filter(a0, a1, mc, off, tau, n1, n2, k1, k2);
           if (__any_sync(0xffffffffu, real) &&
               !ev_submit(ev, a0, a1, real, mc, off, tau, cfac, trait, group, ag, mx1, mx2, id1, id2,
-                         nan_c, p, abort_addr, lane))
+                         kNan ? nsw >> 9 : 0, p, abort_addr, lane))
             return false;
           if constexpr (kTwo)
             if (ag > 0 && real) {
@@ -2178,7 +2196,7 @@ __global__ void __launch_bounds__(ScanRoles<kForm>::kThreads, 1)
             if (ag > 0 && need_b) real = minp_filter(b0, b1, mc, off + kH, tau, n1, n2, k1, k2);
           if (__any_sync(0xffffffffu, real) &&
               !ev_submit(ev, b0, b1, real, mc, off + kH, tau, cfac, trait, group, ag, mx1, mx2, id1, id2,
-                         nan_c, p, abort_addr, lane))
+                         kNan ? nsw >> 9 : 0, p, abort_addr, lane))
             return false;
           if constexpr (kTwo)
             if (ag > 0 && real) {
@@ -2211,9 +2229,13 @@ __global__ void __launch_bounds__(ScanRoles<kForm>::kThreads, 1)
           const uint8_t *tcp = stc + (size_t)tc_e * kTcBytes;
           const float tau = reinterpret_cast<const float *>(tcp)[row];
           const double cfac = reinterpret_cast<const double *>(tcp + 512)[row];
+          const int trait = tt * kTileM + row;
           if constexpr (kNan) {
-            nan_c = g.nan_cnt ? (int)reinterpret_cast<const uint16_t *>(tcp + 2560)[row] : 0;
-            nset = nan_c == 0 ? 0 : (nan_c <= kNanCMax ? nan_set_of(nan_c) + 1 : -1);
+            const int nan_c = g.nan_cnt ? (int)reinterpret_cast<const uint16_t *>(tcp + 2560)[row] : 0;
+            const int nset = nan_c == 0 ? 0 : (nan_c <= kNanCMax ? nan_set_of(nan_c) + 1 : -1);
+            const int wset = (int)__reduce_max_sync(0xffffffffu, (unsigned)max(nset, 0));
+            const bool mixed = __any_sync(0xffffffffu, nset >= 0 && nset != wset);
+            nsw = (nset + 1) | (wset << 4) | (mixed ? 256 : 0) | (nan_c << 9);
           }
           if constexpr (kTwo) {
             // unpermuted group: both signs against tau (less the margin); a
@@ -2248,8 +2270,7 @@ __global__ void __launch_bounds__(ScanRoles<kForm>::kThreads, 1)
           float ntlo = -tau * (1.f - p.margin);
           // (a trait beyond the last set: +inf lets every pair through)
           if constexpr (kNan)
-            if (nset < 0 && tau < kBoundMax) ntlo = __int_as_float(0x7f800000);
-          const int trait = tt * kTileM + row;
+            if ((nsw & 15) == 0 && tau < kBoundMax) ntlo = __int_as_float(0x7f800000);
           {
             for (int c0 = 0; c0 < nc_item; c0 += 2) {
               const int c = c0 + h;
