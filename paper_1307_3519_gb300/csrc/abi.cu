@@ -55,8 +55,8 @@ cudaError_t launch_pack2(const int8_t *geno, int64_t ldg, int N, int Np, const i
 cudaError_t launch_pack_batch(const PackJob *jobs, int n_jobs, int64_t total_slots,
                               int64_t total_halves, double h1, double h2, int signed_df1,
                               unsigned int *status, cudaStream_t s);
-cudaError_t launch_rerank_buckets(const RerankJob *jobs, const int32_t *drops, int n_jobs,
-                                  int max_rows_pad, cudaStream_t s);
+cudaError_t launch_rerank_buckets(const RerankJob *djobs, const RerankJob *hjobs,
+                                  const int32_t *drops, int n_jobs, cudaStream_t s);
 cudaError_t launch_plain_epilogue2(const float *C, int64_t ldc, int T, int n_slots,
                                    const ChunkMeta *meta, const float *tau, const double *cfac,
                                    const uint16_t *nan_cnt, const uint16_t *nan_idx, int N,
@@ -1109,7 +1109,6 @@ krux_status materialise(krux_ctx *ctx, CallPlan &cp, cudaStream_t s) {
   KRUX_CUDA(ctx, ctx->bucket_ranks.ensure(tot));
   char *base = ctx->bucket_ranks.as<char>();
   cp.bucket_sets.assign(nb, krux_rankset());
-  int max_rows = 0;
   for (size_t i = 0; i < nb; ++i) {
     const krux_rankset *rs = cp.bucket_jobs[i].base;
     krux_rankset &bs = cp.bucket_sets[i];
@@ -1147,14 +1146,13 @@ krux_status materialise(krux_ctx *ctx, CallPlan &cp, cudaStream_t s) {
     j.N = rs->N;
     j.Np = rs->Np;
     j.rows_pad = rs->rows_pad;
-    max_rows = std::max(max_rows, rs->rows_pad);
   }
   // pageable uploads: staged before the calls return, so the host vectors may go
   RerankJob *djobs = reinterpret_cast<RerankJob *>(base + jobs_off);
   int32_t *ddrop = reinterpret_cast<int32_t *>(base + drop_off);
   KRUX_CUDA(ctx, cudaMemcpyAsync(djobs, jobs.data(), nb * sizeof(RerankJob), cudaMemcpyHostToDevice, s));
   KRUX_CUDA(ctx, cudaMemcpyAsync(ddrop, drops.data(), drops.size() * 4, cudaMemcpyHostToDevice, s));
-  KRUX_CUDA(ctx, launch_rerank_buckets(djobs, ddrop, (int)nb, max_rows, s));
+  KRUX_CUDA(ctx, launch_rerank_buckets(djobs, jobs.data(), ddrop, (int)nb, s));
   if (ctx->profiling) ctx->prof.launches += 1;
   // runs of buckets of the same rank set: one A map each
   std::vector<size_t> run(nb);

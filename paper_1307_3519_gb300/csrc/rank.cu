@@ -18,13 +18,13 @@ constexpr int kRankWarps = 8;
 // Tie factor C = 1 - sum(t^3-t)/(K^3-K) and the trait constants of the scan:
 // H = 3/(K(K+1)C) * sum_i D_i^2/N_i, so cfac = 3/(K(K+1)C) and the fast-test
 // bound tau = K(K+1)C/3; degenerate traits (K < 2 or C = 0) get cfac 0, tau +inf.
+// With M = K^3 - K - sum(t^3-t) (an exact integer), K(K+1)C = M/(K-1): cfac is one
+// correctly rounded FP64 division, 3(K-1)/M, and tau an FP32 one.
 __device__ __forceinline__ void trait_consts(int K, long long tie, float &tau, double &cfac) {
-  const double Kd = (double)K;
-  const double C = K >= 2 ? 1.0 - (double)tie / (Kd * Kd * Kd - Kd) : 0.0;
-  if (K >= 2 && C > 0.0) {
-    const double s = Kd * (Kd + 1.0) * C;
-    cfac = 3.0 / s;
-    tau = (float)(s / 3.0);
+  const long long M = K >= 2 ? (long long)K * K * K - K - tie : 0;
+  if (M > 0) {
+    cfac = 3.0 * (double)(K - 1) / (double)M;
+    tau = (float)M / (float)(3 * (K - 1));
   } else {
     cfac = 0.0;
     tau = __int_as_float(0x7f800000);  // +inf: never a hit
@@ -224,88 +224,167 @@ cudaError_t launch_permute_rows(const __half *A, __half *out, int rows_pad, int 
 // samples of the pattern removed, re-ranked).  No re-sort: for present samples,
 // x_q < x_k exactly when lo_q < lo_k and x_q == x_k exactly when lo_q == lo_k,
 // so lo' = lo - #{q dropped, present, lo_q < lo_k} and
-// eq' = eq - #{q dropped, present, lo_q == lo_k}.  One launch re-ranks every
-// bucket of a call (grid.y = bucket).
+// eq' = eq - #{q dropped, present, lo_q == lo_k}.
+//
+// One warp per trait row and kRerankChunk buckets of a run (buckets of one base
+// rank set; grid.y = chunk of buckets): the row's lo and eq are read once, into
+// registers (lane l owns samples 4l..4l+3 of every 128) and into the warp's
+// shared-memory copy (where the dropped samples' values are looked up), the
+// chunk's job fields are staged in shared memory, then each bucket costs a pass
+// over the registers, one 8-byte store per lane and 128 samples, and an integer
+// reduction of the tie sum.  Lane b keeps bucket b's K and tie sum and turns them
+// into the FP64 constants at the end, all buckets of the chunk at once.
 namespace krux {
 namespace {
-__global__ void __launch_bounds__(256)
-rerank_kernel(const RerankJob *__restrict__ jobs, const int32_t *__restrict__ drops) {
-  const RerankJob &J = jobs[blockIdx.y];
-  const int N = J.N, Np = J.Np, T = J.T, n_drop = J.n_drop;
-  __shared__ uint32_t dmask[kMaxN / 32];
-  __shared__ int32_t dlist[kMaxN];
-  for (int i = threadIdx.x; i < kMaxN / 32; i += blockDim.x) dmask[i] = 0u;
-  __syncthreads();
-  for (int i = threadIdx.x; i < n_drop; i += blockDim.x) {
-    const int q = drops[J.drop_off + i];
-    dlist[i] = q;
-    atomicOr(&dmask[q >> 5], 1u << (q & 31));
+constexpr int kRerankWarps = 8;
+constexpr int kRerankChunk = 16;            // buckets per warp
+constexpr int kRerankDrops = 1024;          // drop-list entries staged per block
+constexpr int kRerankPasses = kMaxN / 128;  // 4 samples per lane and pass
+
+struct RerankOut {  // a bucket's outputs and drop list, staged per block
+  __half *A;
+  int64_t *tie;
+  int32_t *K;
+  float *tau;
+  double *cfac;
+  int32_t drop_off, n_drop;
+};
+
+__global__ void __launch_bounds__(kRerankWarps * 32)
+rerank_kernel(const RerankJob *__restrict__ jobs, int n_jobs_all, const int32_t *__restrict__ drops) {
+  __shared__ uint32_t srow[kRerankWarps][kMaxN];  // lo | eq << 16 of the warp's row
+  __shared__ RerankOut sj[kRerankChunk];
+  __shared__ int32_t sdrop[kRerankDrops];          // the chunk's drop lists, when they fit
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int jbase = blockIdx.y * kRerankChunk;
+  const int n_jobs = min(kRerankChunk, n_jobs_all - jbase);
+  if (threadIdx.x < n_jobs) {
+    const RerankJob &J = jobs[jbase + threadIdx.x];
+    sj[threadIdx.x] = RerankOut{J.A, J.tie, J.K, J.tau, J.cfac, J.drop_off, J.n_drop};
   }
   __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int t = blockIdx.x * 8 + warp;
-  if (t >= J.rows_pad) return;
-  if (t >= T) {  // padding row (its constants come from rerank_consts_kernel)
-    for (int k = lane; k < Np; k += 32) J.A[(int64_t)t * Np + k] = __int2half_rn(0);
+  // the chunk's drop lists lie back to back in `drops`
+  const int d0 = sj[0].drop_off;
+  const int nd = sj[n_jobs - 1].drop_off + sj[n_jobs - 1].n_drop - d0;
+  const bool staged = nd <= kRerankDrops;
+  if (staged)
+    for (int i = threadIdx.x; i < nd; i += blockDim.x) sdrop[i] = drops[d0 + i];
+  __syncthreads();
+  const RerankJob &J0 = jobs[0];  // every job of the run has this base and shape
+  const int N = J0.N, Np = J0.Np, T = J0.T, rows_pad = J0.rows_pad;
+  const int t = blockIdx.x * kRerankWarps + warp;
+  if (t >= rows_pad) return;  // whole warps leave; no block barrier follows
+  const int passes = Np / 128 + (Np % 128 ? 1 : 0);
+  if (t >= T) {  // padding row: zeros, never a hit
+    for (int j = 0; j < n_jobs; ++j) {
+      const RerankOut &J = sj[j];
+      for (int k = lane; k < Np; k += 32) J.A[(int64_t)t * Np + k] = __int2half_rn(0);
+      if (lane == 0) {
+        J.tau[t] = __int_as_float(0x7f800000);
+        J.cfac[t] = 0.0;
+      }
+    }
     return;
   }
-  const uint16_t *lo = J.base.lo + (int64_t)t * N;
-  const uint16_t *eq = J.base.eq + (int64_t)t * N;
-  int Kdrop = 0;
-  for (int i = 0; i < n_drop; ++i) Kdrop += eq[dlist[i]] > 0;
-  const int K = J.base.K[t] - Kdrop;
-  long long tie = 0;
-  for (int k = lane; k < Np; k += 32) {
-    int a = 0;
-    if (k < N && eq[k] > 0 && !((dmask[k >> 5] >> (k & 31)) & 1u)) {
-      const int lk = lo[k];
-      int l = lk, e = eq[k];
-      for (int i = 0; i < n_drop; ++i) {
-        const int q = dlist[i];
-        if (eq[q] > 0) {
-          l -= lo[q] < lk;
-          e -= lo[q] == lk;
+  const uint16_t *lo = J0.base.lo + (int64_t)t * N;
+  const uint16_t *eq = J0.base.eq + (int64_t)t * N;
+  for (int k = lane; k < N; k += 32) srow[warp][k] = (uint32_t)lo[k] | ((uint32_t)eq[k] << 16);
+  uint32_t own[kRerankPasses][4];
+#pragma unroll
+  for (int ps = 0; ps < kRerankPasses; ++ps)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int k = 128 * ps + 4 * lane + i;
+      own[ps][i] = ps < passes && k < N ? (uint32_t)lo[k] | ((uint32_t)eq[k] << 16) : 0u;
+    }
+  __syncwarp();
+  const int K0 = J0.base.K[t];
+  int myK = 0, mytie = 0;  // bucket lane's, for the constants
+  for (int j = 0; j < n_jobs; ++j) {
+    const RerankOut &J = sj[j];
+    const int n_drop = J.n_drop;
+    const int32_t *dl = staged ? sdrop + (J.drop_off - d0) : drops + J.drop_off;
+    int Kdrop = 0;  // dropped samples with a value
+    for (int d = 0; d < n_drop; ++d) Kdrop += (srow[warp][dl[d]] >> 16) > 0u;
+    const int K = K0 - Kdrop;
+    int tie = 0;
+#pragma unroll
+    for (int ps = 0; ps < kRerankPasses; ++ps) {
+      if (ps >= passes) break;
+      const int k0 = 128 * ps + 4 * lane;
+      int lk[4], l[4], e[4];
+      bool present[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        lk[i] = (int)(own[ps][i] & 0xffffu);
+        l[i] = lk[i];
+        e[i] = (int)(own[ps][i] >> 16);
+        present[i] = e[i] > 0;
+      }
+      for (int d = 0; d < n_drop; ++d) {
+        const int q = dl[d];
+        const uint32_t w = srow[warp][q];
+        const int lq = (int)(w & 0xffffu);
+        const bool qp = (w >> 16) > 0u;  // the dropped sample has a value
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          present[i] = present[i] && q != k0 + i;
+          l[i] -= qp && lq < lk[i];
+          e[i] -= qp && lq == lk[i];
         }
       }
-      tie += (long long)e * e - 1;
-      a = 2 * l + e - K;
-    }
-    J.A[(int64_t)t * Np + k] = __int2half_rn(a);
-  }
+      int a[4];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) tie += __shfl_xor_sync(0xffffffffu, tie, o);
-  if (lane == 0) {
-    J.tie[t] = tie;
-    J.K[t] = K;
+      for (int i = 0; i < 4; ++i) {
+        a[i] = 0;
+        if (present[i]) {
+          tie += e[i] * e[i] - 1;
+          a[i] = 2 * l[i] + e[i] - K;
+        }
+      }
+      if (k0 < Np) {
+        const __half2 h01 = __halves2half2(__int2half_rn(a[0]), __int2half_rn(a[1]));
+        const __half2 h23 = __halves2half2(__int2half_rn(a[2]), __int2half_rn(a[3]));
+        uint2 v;
+        v.x = *reinterpret_cast<const uint32_t *>(&h01);
+        v.y = *reinterpret_cast<const uint32_t *>(&h23);
+        *reinterpret_cast<uint2 *>(J.A + (int64_t)t * Np + k0) = v;
+      }
+    }
+    tie = (int)__reduce_add_sync(0xffffffffu, (unsigned)tie);
+    if (lane == 0) {
+      J.tie[t] = tie;
+      J.K[t] = K;
+    }
+    if (lane == j) {
+      myK = K;
+      mytie = tie;
+    }
   }
-}
-
-// The FP64 trait constants of every bucket, one thread per row (FP64 issue is
-// slow on this part, so it gets whole warps); padding rows get cfac 0, tau +inf.
-__global__ void __launch_bounds__(256) rerank_consts_kernel(const RerankJob *__restrict__ jobs) {
-  const RerankJob &J = jobs[blockIdx.y];
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= J.rows_pad) return;
-  float tau = __int_as_float(0x7f800000);
-  double cfac = 0.0;
-  if (t < J.T) trait_consts(J.K[t], J.tie[t], tau, cfac);
-  J.tau[t] = tau;
-  J.cfac[t] = cfac;
+  if (lane < n_jobs) {  // the chunk's FP64 constants, one bucket per lane
+    float tau;
+    double cfac;
+    trait_consts(myK, (long long)mytie, tau, cfac);
+    sj[lane].tau[t] = tau;
+    sj[lane].cfac[t] = cfac;
+  }
 }
 }  // namespace
 
-cudaError_t launch_rerank_buckets(const RerankJob *jobs, const int32_t *drops, int n_jobs,
-                                  int max_rows_pad, cudaStream_t s) {
-  for (int j0 = 0; j0 < n_jobs; j0 += 65535) {  // grid.y limit
-    const int nj = n_jobs - j0 < 65535 ? n_jobs - j0 : 65535;
-    rerank_kernel<<<dim3((unsigned)((max_rows_pad + 7) / 8), (unsigned)nj), 256, 0, s>>>(jobs + j0,
-                                                                                       drops);
-    cudaError_t e = cudaGetLastError();
+// One launch per run of buckets with the same base rank set (hjobs: the host copy
+// of the device table djobs).
+cudaError_t launch_rerank_buckets(const RerankJob *djobs, const RerankJob *hjobs,
+                                  const int32_t *drops, int n_jobs, cudaStream_t s) {
+  for (int j0 = 0; j0 < n_jobs;) {
+    int j1 = j0 + 1;
+    while (j1 < n_jobs && hjobs[j1].base.lo == hjobs[j0].base.lo) ++j1;
+    const int rows_pad = hjobs[j0].rows_pad;
+    const dim3 grid((unsigned)((rows_pad + kRerankWarps - 1) / kRerankWarps),
+                    (unsigned)((j1 - j0 + kRerankChunk - 1) / kRerankChunk));
+    rerank_kernel<<<grid, kRerankWarps * 32, 0, s>>>(djobs + j0, j1 - j0, drops);
+    const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    rerank_consts_kernel<<<dim3((unsigned)((max_rows_pad + 255) / 256), (unsigned)nj), 256, 0, s>>>(
-        jobs + j0);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    j0 = j1;
   }
   return cudaSuccess;
 }
