@@ -239,7 +239,6 @@ namespace {
 constexpr int kRerankWarps = 8;
 constexpr int kRerankChunk = 16;            // buckets per warp
 constexpr int kRerankDrops = 1024;          // drop-list entries staged per block
-constexpr int kRerankPasses = kMaxN / 128;  // 4 samples per lane and pass
 
 struct RerankOut {  // a bucket's outputs and drop list, staged per block
   __half *A;
@@ -250,7 +249,9 @@ struct RerankOut {  // a bucket's outputs and drop list, staged per block
   int32_t drop_off, n_drop;
 };
 
-__global__ void __launch_bounds__(kRerankWarps * 32)
+// kPasses = ceil(Np / 128) passes of 4 samples per lane (the row in registers).
+template <int kPasses>
+__global__ void __launch_bounds__(kRerankWarps * 32, kPasses == 1 ? 5 : (kPasses == 2 ? 2 : 1))
 rerank_kernel(const RerankJob *__restrict__ jobs, int n_jobs_all, const int32_t *__restrict__ drops) {
   __shared__ uint32_t srow[kRerankWarps][kMaxN];  // lo | eq << 16 of the warp's row
   __shared__ RerankOut sj[kRerankChunk];
@@ -274,7 +275,6 @@ rerank_kernel(const RerankJob *__restrict__ jobs, int n_jobs_all, const int32_t 
   const int N = J0.N, Np = J0.Np, T = J0.T, rows_pad = J0.rows_pad;
   const int t = blockIdx.x * kRerankWarps + warp;
   if (t >= rows_pad) return;  // whole warps leave; no block barrier follows
-  const int passes = Np / 128 + (Np % 128 ? 1 : 0);
   if (t >= T) {  // padding row: zeros, never a hit
     for (int j = 0; j < n_jobs; ++j) {
       const RerankOut &J = sj[j];
@@ -289,13 +289,13 @@ rerank_kernel(const RerankJob *__restrict__ jobs, int n_jobs_all, const int32_t 
   const uint16_t *lo = J0.base.lo + (int64_t)t * N;
   const uint16_t *eq = J0.base.eq + (int64_t)t * N;
   for (int k = lane; k < N; k += 32) srow[warp][k] = (uint32_t)lo[k] | ((uint32_t)eq[k] << 16);
-  uint32_t own[kRerankPasses][4];
+  uint32_t own[kPasses][4];
 #pragma unroll
-  for (int ps = 0; ps < kRerankPasses; ++ps)
+  for (int ps = 0; ps < kPasses; ++ps)
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int k = 128 * ps + 4 * lane + i;
-      own[ps][i] = ps < passes && k < N ? (uint32_t)lo[k] | ((uint32_t)eq[k] << 16) : 0u;
+      own[ps][i] = k < N ? (uint32_t)lo[k] | ((uint32_t)eq[k] << 16) : 0u;
     }
   __syncwarp();
   const int K0 = J0.base.K[t];
@@ -309,8 +309,7 @@ rerank_kernel(const RerankJob *__restrict__ jobs, int n_jobs_all, const int32_t 
     const int K = K0 - Kdrop;
     int tie = 0;
 #pragma unroll
-    for (int ps = 0; ps < kRerankPasses; ++ps) {
-      if (ps >= passes) break;
+    for (int ps = 0; ps < kPasses; ++ps) {
       const int k0 = 128 * ps + 4 * lane;
       int lk[4], l[4], e[4];
       bool present[4];
@@ -381,7 +380,13 @@ cudaError_t launch_rerank_buckets(const RerankJob *djobs, const RerankJob *hjobs
     const int rows_pad = hjobs[j0].rows_pad;
     const dim3 grid((unsigned)((rows_pad + kRerankWarps - 1) / kRerankWarps),
                     (unsigned)((j1 - j0 + kRerankChunk - 1) / kRerankChunk));
-    rerank_kernel<<<grid, kRerankWarps * 32, 0, s>>>(djobs + j0, j1 - j0, drops);
+    const int Np = hjobs[j0].Np;
+    if (Np <= 128)
+      rerank_kernel<1><<<grid, kRerankWarps * 32, 0, s>>>(djobs + j0, j1 - j0, drops);
+    else if (Np <= 256)
+      rerank_kernel<2><<<grid, kRerankWarps * 32, 0, s>>>(djobs + j0, j1 - j0, drops);
+    else
+      rerank_kernel<4><<<grid, kRerankWarps * 32, 0, s>>>(djobs + j0, j1 - j0, drops);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     j0 = j1;
