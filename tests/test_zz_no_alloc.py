@@ -4,13 +4,15 @@ Callers that run under an allocator owning the whole device, plugins inside such
 processes, or latency-critical code where an allocation may block or fail use
 this entry point: the library takes all scratch from a fixed array of its own.
 Its results must equal those of krux_scan on the same inputs (exact hit set and
-rank sums, H and p within the same 1e-6 relative tolerance), on two calls in a
-row, so that what one call leaves in the shared array cannot leak into the
-next.  This file is collected last; it also passes when run alone."""
+rank sums, H and p within the same 1e-6 relative tolerance) and, checked on their
+own, the FP64 oracle's, on two calls in a row, so that what one call leaves in the
+shared array cannot leak into the next.  This file is collected last; it also
+passes when run alone."""
 import numpy as np
 import pytest
 
 import synth
+from kwcheck import check_hits
 
 pytestmark = pytest.mark.gpu
 
@@ -36,7 +38,7 @@ def _case(seed, T, S, N, nan):
     return x, g
 
 
-def test_noalloc_matches_krux_scan_on_two_calls():
+def test_noalloc_matches_krux_scan_on_two_calls(oracle_mod):
     import torch
     if not torch.cuda.is_available():
         pytest.skip("no GPU")
@@ -62,6 +64,10 @@ def test_noalloc_matches_krux_scan_on_two_calls():
         assert np.array_equal(a[0], b[0])  # same pairs, same exact rank sums
         assert np.all(np.abs(a[1] - b[1]) <= 1e-6 * np.abs(b[1]) + 1e-10)
         assert np.all(np.abs(a[2] - b[2]) <= 1e-6 * b[2])
+        # and the oracle's, directly
+        orc = oracle_mod.scan(x, g, pth)
+        check_hits({"hits": hits[:n], "H": H[:n], "p": P[:n]}, orc, np.arange(x.shape[0]),
+                   np.arange(g.shape[0]), pth)
     kx.close()
 
 
