@@ -290,6 +290,40 @@ def test_host_entry_strided_pinned_missing(kx, oracle_mod):
     assert all(full[k_] == tuple(r) for k_, r in zip(key(small["hits"]).tolist(), small["hits"].tolist()))
 
 
+def test_host_entry_large_with_missing(kx, oracle_mod):
+    """krux_scan_host at 300,000 SNPs with missing genotypes (196-odd pattern
+    buckets) and NaN expression: the same hit set, rank sums, H and p as the
+    device-side krux_scan on the same inputs, the oracle's on sampled traits, and
+    with a capacity below the hit count KRUX_EOVERFLOW, the exact count and real
+    records."""
+    import torch
+    d = synth.config(3, T=256, S=300000, seed=23)
+    x, g = d["expr"], d["geno"]
+    T, S = x.shape[0], g.shape[0]
+    pth = 1e-4
+    out = kx.krux_scan_host(x, g, pth, capacity=T * 2000)
+    assert not out["overflow"] and out["n_hits"] > 0
+    rs = kx.krux_rank(_dev(x))
+    ref = kx.krux_scan(rs, _dev(g), pth, capacity=T * 2000)
+    rs.free()
+    key = lambda h: h[:, 0].astype(np.int64) * S + h[:, 1]
+    a = np.argsort(key(out["hits"]))
+    rh = ref["hits"].cpu().numpy()
+    b = np.argsort(key(rh))
+    assert out["n_hits"] == ref["n_hits"]
+    assert np.array_equal(out["hits"][a], rh[b])
+    assert np.array_equal(out["H"][a], ref["H"].cpu().numpy()[b])
+    assert np.array_equal(out["p"][a], ref["p"].cpu().numpy()[b])
+    sel = np.arange(0, T, 37)
+    orc = oracle_mod.scan(x[sel], g, pth)
+    check_hits(_as_res(out), orc, sel, np.arange(S), pth)
+    cap = out["n_hits"] // 3
+    small = kx.krux_scan_host(x, g, pth, capacity=cap)
+    assert small["overflow"] and small["n_hits"] == out["n_hits"] and small["hits"].shape[0] == cap
+    full = dict(zip(key(out["hits"]).tolist(), map(tuple, out["hits"].tolist())))
+    assert all(full[k_] == tuple(r) for k_, r in zip(key(small["hits"]).tolist(), small["hits"].tolist()))
+
+
 @pytest.mark.parametrize("layout,nc,nA,ka", [(0, 0, 0, 0), (1, 0, 0, 0), (1, 2, 4, 0), (0, 3, 3, 0),
                                              (1, 1, 2, 0), (1, 4, 2, 0), (1, 2, 4, 64), (0, 2, 3, 64),
                                              (1, 1, 4, 64), (1, 4, 3, 64)])
