@@ -147,8 +147,11 @@ krux_status krux_scan(krux_ctx *ctx, const krux_rankset *rs, const int8_t *geno,
  * Page-locked host buffers (cudaHostAlloc or cudaHostRegister) copy at the
  * link's rate; pageable ones work but copy through a bounce buffer.  Each input
  * is one cudaMemcpyAsync (cudaMemcpy2DAsync when its leading dimension exceeds
- * N) into device memory the context keeps between calls; the outputs are three
- * copies of min(*n_hits, capacity) records.  opts->dense_H / dense_p must be
+ * N) into device memory the context keeps between calls.  Outputs in page-locked
+ * memory mapped into the device's address space (cudaHostAlloc, or
+ * cudaHostRegister with cudaHostRegisterMapped; `hits` 16-byte aligned) are
+ * written by the library's kernels directly; other outputs are filled by three
+ * copies of min(*n_hits, capacity) records from a device list.  opts->dense_H / dense_p must be
  * NULL (dense output is a device-side option of krux_scan).  The call
  * synchronises `stream` before returning. */
 krux_status krux_scan_host(krux_ctx *ctx, const float *expr, int T, int N, int64_t lde,

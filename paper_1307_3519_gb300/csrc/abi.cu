@@ -1815,6 +1815,17 @@ extern "C" krux_status krux_scan(krux_ctx *ctx, const krux_rankset *rs, const in
   return KRUX_OK;
 }
 
+// The device address of page-locked host memory mapped into the device's address
+// space (cudaHostAlloc; cudaHostRegister with the mapped flag), else null.
+static void *mapped_device_ptr(const void *host) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, host) != cudaSuccess) {
+    cudaGetLastError();  // (an unknown pointer is not an error here)
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 // Host-memory wrapper of krux_rank + krux_scan: one copy per input into the
 // context's device buffer (packed to leading dimension N), the scan into a
 // device hit list the context keeps, and one copy per output array back.
@@ -1854,24 +1865,36 @@ extern "C" krux_status krux_scan_host(krux_ctx *ctx, const float *expr, int T, i
                                        cudaMemcpyHostToDevice, s));
   }
   const int64_t cap = std::max<int64_t>(opts->hit_capacity, 0);
-  const size_t hoff = 0, Hoff = (size_t)std::max<int64_t>(cap, 1) * sizeof(krux_hit);
-  const size_t poff = Hoff + (size_t)std::max<int64_t>(cap, 1) * 8;
-  KRUX_CUDA(ctx, ctx->host_out.ensure(poff + (size_t)std::max<int64_t>(cap, 1) * 8));
+  // outputs in page-locked memory mapped into the device's address space are
+  // written by the compaction and finalisation kernels directly (no copy after
+  // the launch); other outputs get a device list and three copies
+  krux_hit *mh = nullptr;
+  double *mH = nullptr, *mp = nullptr;
+  if (cap > 0) {
+    mh = static_cast<krux_hit *>(mapped_device_ptr(hits));
+    mH = static_cast<double *>(mapped_device_ptr(hit_H));
+    mp = static_cast<double *>(mapped_device_ptr(hit_p));
+  }
+  const bool direct = mh && mH && mp && ((uintptr_t)mh & 15u) == 0;
+  const size_t hoff = 0, Hoff = (size_t)std::max<int64_t>(direct ? 0 : cap, 1) * sizeof(krux_hit);
+  const size_t poff = Hoff + (size_t)std::max<int64_t>(direct ? 0 : cap, 1) * 8;
+  KRUX_CUDA(ctx, ctx->host_out.ensure(poff + (size_t)std::max<int64_t>(direct ? 0 : cap, 1) * 8));
   char *dout = ctx->host_out.as<char>();
   krux_rankset *rs = nullptr;
   st = krux_rank(ctx, reinterpret_cast<const float *>(din), T, N, N, &rs, stream);
   if (st != KRUX_OK) return st;
   const float ms_rank = ctx->profiling ? ctx->prof.ms_rank : 0.f;
   st = krux_scan(ctx, rs, reinterpret_cast<const int8_t *>(din + goff), S, N, opts,
-                 reinterpret_cast<krux_hit *>(dout + hoff), reinterpret_cast<double *>(dout + Hoff),
-                 reinterpret_cast<double *>(dout + poff), n_hits, stream);
+                 direct ? mh : reinterpret_cast<krux_hit *>(dout + hoff),
+                 direct ? mH : reinterpret_cast<double *>(dout + Hoff),
+                 direct ? mp : reinterpret_cast<double *>(dout + poff), n_hits, stream);
   krux_rankset_free(ctx, rs);
   if (st != KRUX_OK && st != KRUX_EOVERFLOW) return st;
   if (ctx->profiling) {
     ctx->prof.ms_rank = ms_rank;
     ctx->prof.launches += 2;  // the rank transform's two kernels
   }
-  const int64_t k = std::min<int64_t>(*n_hits, cap);
+  const int64_t k = direct ? 0 : std::min<int64_t>(*n_hits, cap);
   if (k > 0) {
     KRUX_CUDA(ctx, cudaMemcpyAsync(hits, dout + hoff, (size_t)k * sizeof(krux_hit),
                                    cudaMemcpyDeviceToHost, s));

@@ -288,6 +288,20 @@ def test_host_entry_strided_pinned_missing(kx, oracle_mod):
     key = lambda h: h[:, 0].astype(np.int64) * S + h[:, 1]
     full = dict(zip(key(out["hits"]).tolist(), map(tuple, out["hits"].tolist())))
     assert all(full[k_] == tuple(r) for k_, r in zip(key(small["hits"]).tolist(), small["hits"].tolist()))
+    # page-locked outputs: the kernels write them directly; the same records
+    n = out["n_hits"]
+    outs = (torch.zeros((n, 4), dtype=torch.int32).pin_memory(),
+            torch.zeros(n, dtype=torch.float64).pin_memory(), torch.zeros(n, dtype=torch.float64).pin_memory())
+    pin = kx.krux_scan_host(e_h[:, :N], g_h[:, :N], pth, capacity=n, out=outs)
+    assert not pin["overflow"] and pin["n_hits"] == n
+    a, b = np.argsort(key(pin["hits"])), np.argsort(key(out["hits"]))
+    assert np.array_equal(pin["hits"][a], out["hits"][b])
+    assert np.array_equal(pin["H"][a], out["H"][b]) and np.array_equal(pin["p"][a], out["p"][b])
+    # and past their capacity: the exact count, real records
+    outs2 = tuple(t[: n // 2] for t in outs)
+    pin2 = kx.krux_scan_host(e_h[:, :N], g_h[:, :N], pth, capacity=n // 2, out=outs2)
+    assert pin2["overflow"] and pin2["n_hits"] == n
+    assert all(full[k_] == tuple(r) for k_, r in zip(key(pin2["hits"]).tolist(), pin2["hits"].tolist()))
 
 
 def test_host_entry_large_with_missing(kx, oracle_mod):
