@@ -147,7 +147,8 @@ krux_status krux_scan(krux_ctx *ctx, const krux_rankset *rs, const int8_t *geno,
  * Page-locked host buffers (cudaHostAlloc or cudaHostRegister) copy at the
  * link's rate; pageable ones work but copy through a bounce buffer.  Each input
  * is one cudaMemcpyAsync (cudaMemcpy2DAsync when its leading dimension exceeds
- * N) into device memory the context keeps between calls.  Outputs in page-locked
+ * N) into device memory the context keeps between calls; the genotypes' copy runs
+ * on a stream the context owns, beside the rank transform on `stream`.  Outputs in page-locked
  * memory mapped into the device's address space (cudaHostAlloc, or
  * cudaHostRegister with cudaHostRegisterMapped; `hits` 16-byte aligned) are
  * written by the library's kernels directly; other outputs are filled by three

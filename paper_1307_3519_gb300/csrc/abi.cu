@@ -197,6 +197,9 @@ struct krux_ctx {
   int tune_layout = -1, tune_nc = 0, tune_nA = 0, tune_ka = 0;  // 0 / -1 = automatic
   PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   cudaEvent_t ev[kEv] = {};
+  // krux_scan_host: the genotypes' copy runs on its own stream beside the rank transform
+  cudaStream_t xs = nullptr;
+  cudaEvent_t xev = nullptr;
   DevBuf B, meta, codes, groups, items, status, counters, aux, cfacptr, miss_idx, miss_mask,
       list, gemm_out, bucket_ranks, permA, minpkey, seg, permNan, aux2, param, paramOut, packjobs,
       host_in, host_out,  // krux_scan_host: device copies of the inputs, device hit list
@@ -559,6 +562,8 @@ void krux_destroy(krux_ctx *ctx) {
   for (auto &pb : ctx->pool) cudaFree(pb.second);
   for (int i = 0; i < kEv; ++i)
     if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
+  if (ctx->xev) cudaEventDestroy(ctx->xev);
+  if (ctx->xs) cudaStreamDestroy(ctx->xs);
   if (ctx->blas) plain_handle_destroy(ctx->blas);
   delete ctx;
 }
@@ -1857,12 +1862,19 @@ extern "C" krux_status krux_scan_host(krux_ctx *ctx, const float *expr, int T, i
   else
     KRUX_CUDA(ctx, cudaMemcpy2DAsync(din, (size_t)N * 4, expr, (size_t)lde * 4, (size_t)N * 4, T,
                                      cudaMemcpyHostToDevice, s));
-  if (S > 0) {
+  if (S > 0) {  // on the context's copy stream, while `stream` ranks
+    if (!ctx->xs) {
+      KRUX_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->xs, cudaStreamNonBlocking));
+      KRUX_CUDA(ctx, cudaEventCreateWithFlags(&ctx->xev, cudaEventDisableTiming));
+    }
+    KRUX_CUDA(ctx, cudaEventRecord(ctx->xev, s));  // (after whatever `stream` holds)
+    KRUX_CUDA(ctx, cudaStreamWaitEvent(ctx->xs, ctx->xev, 0));
     if (ldg == N)
-      KRUX_CUDA(ctx, cudaMemcpyAsync(din + goff, geno, gbytes, cudaMemcpyHostToDevice, s));
+      KRUX_CUDA(ctx, cudaMemcpyAsync(din + goff, geno, gbytes, cudaMemcpyHostToDevice, ctx->xs));
     else
       KRUX_CUDA(ctx, cudaMemcpy2DAsync(din + goff, (size_t)N, geno, (size_t)ldg, (size_t)N, S,
-                                       cudaMemcpyHostToDevice, s));
+                                       cudaMemcpyHostToDevice, ctx->xs));
+    KRUX_CUDA(ctx, cudaEventRecord(ctx->xev, ctx->xs));
   }
   const int64_t cap = std::max<int64_t>(opts->hit_capacity, 0);
   // outputs in page-locked memory mapped into the device's address space are
@@ -1882,14 +1894,21 @@ extern "C" krux_status krux_scan_host(krux_ctx *ctx, const float *expr, int T, i
   char *dout = ctx->host_out.as<char>();
   krux_rankset *rs = nullptr;
   st = krux_rank(ctx, reinterpret_cast<const float *>(din), T, N, N, &rs, stream);
-  if (st != KRUX_OK) return st;
+  if (st != KRUX_OK) {
+    if (S > 0) cudaStreamSynchronize(ctx->xs);  // the caller's genotypes are read no more
+    return st;
+  }
   const float ms_rank = ctx->profiling ? ctx->prof.ms_rank : 0.f;
+  if (S > 0) KRUX_CUDA(ctx, cudaStreamWaitEvent(s, ctx->xev, 0));  // the genotypes are in
   st = krux_scan(ctx, rs, reinterpret_cast<const int8_t *>(din + goff), S, N, opts,
                  direct ? mh : reinterpret_cast<krux_hit *>(dout + hoff),
                  direct ? mH : reinterpret_cast<double *>(dout + Hoff),
                  direct ? mp : reinterpret_cast<double *>(dout + poff), n_hits, stream);
   krux_rankset_free(ctx, rs);
-  if (st != KRUX_OK && st != KRUX_EOVERFLOW) return st;
+  if (st != KRUX_OK && st != KRUX_EOVERFLOW) {
+    cudaStreamSynchronize(s);  // (and with it the genotypes' copy it waited for)
+    return st;
+  }
   if (ctx->profiling) {
     ctx->prof.ms_rank = ms_rank;
     ctx->prof.launches += 2;  // the rank transform's two kernels
