@@ -1661,7 +1661,7 @@ krux_status enqueue_fused(krux_ctx *ctx, CallPlan &cp, const FusedLaunch &fl, cu
     KRUX_CUDA(ctx, launch_finalize_dev(os.hits, os.aux, os.aux2, totals + k, os.capacity,
                                        fl.cfacptr, os.H, os.P,
                                        ctx->sm_count, s, cp.fdr_hist, cp.fdr_bins, cp.fdr_l0,
-                                       cp.fdr_w));
+                                       cp.fdr_w, fl.p.pthresh));
   }
   ev_record(ctx, 6, s);
   if (fl.p.mc_list)  // the pairs the event warps passed on, decided in FP64
@@ -2257,7 +2257,7 @@ extern "C" krux_status krux_scan_plain(krux_ctx *ctx, const krux_rankset *rs, co
   const int64_t nst = std::min<int64_t>((int64_t)cnt, opts->hit_capacity);
   if (nst > 0)
     KRUX_CUDA(ctx, launch_finalize(hits, ctx->aux.as<HitAux>(), nst, ctx->cfacptr.as<const double *>(),
-                                   hit_H, hit_p, s));
+                                   hit_H, hit_p, s, nullptr, 0, 0.0, 1.0, opts->pthresh));
   ev_record(ctx, 6, s);
   if (ctx->profiling) {
     KRUX_CUDA(ctx, cudaStreamSynchronize(s));

@@ -420,18 +420,19 @@ cudaError_t launch_pad_traits(int T, int rows_pad, float *tau, double *cfac, uin
 // graph capture).
 cudaError_t finalize_prepare();
 // Finalisation of min(*count, capacity) hits, the count read on the device;
-// aux2 is non-null for markers with more than three groups.
+// aux2 is non-null for markers with more than three groups.  pthresh: the hits'
+// threshold P_c (a reported p at or above it is taken again in full FP64).
 cudaError_t launch_finalize_dev(const krux_hit *hits, const HitAux *aux, const HitAux2 *aux2,
                                 const unsigned long long *count, int64_t capacity,
                                 const double *const *cfac_by_group, double *H, double *p,
                                 int sm_count, cudaStream_t s, unsigned long long *fdr_hist,
-                                int fdr_bins, double fdr_l0, double fdr_w);
+                                int fdr_bins, double fdr_l0, double fdr_w, double pthresh);
 cudaError_t scan_set_smem(size_t smem);
 int scan_form_of(const ScanParams &p);
 cudaError_t launch_scan_only(const ScanParams &p, int grid, size_t smem, cudaStream_t s);
 cudaError_t launch_finalize(const krux_hit *hits, const HitAux *aux, int64_t n,
                             const double *const *cfac_by_group, double *H, double *p,
-                            cudaStream_t s, unsigned long long *fdr_hist = nullptr, int fdr_bins = 0,
-                            double fdr_l0 = 0.0, double fdr_w = 1.0);
+                            cudaStream_t s, unsigned long long *fdr_hist, int fdr_bins,
+                            double fdr_l0, double fdr_w, double pthresh);
 
 }  // namespace krux

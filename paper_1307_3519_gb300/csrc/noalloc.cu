@@ -283,7 +283,7 @@ extern "C" krux_status krux_scan_noalloc(const float *expr, int T, int N, int64_
   if (hst[0] & kDevTimeout) return KRUX_ETIMEOUT;
   const int64_t stored = std::min<int64_t>((int64_t)cnt, cap);
   if (stored > 0) {
-    NA_CUDA(launch_finalize(hits, aux, stored, cfacptr, hit_H, hit_p, s));
+    NA_CUDA(launch_finalize(hits, aux, stored, cfacptr, hit_H, hit_p, s, nullptr, 0, 0.0, 1.0, pthresh));
     NA_CUDA(cudaStreamSynchronize(s));
   }
   *n_hits = (int64_t)cnt;

@@ -285,6 +285,22 @@ __device__ __forceinline__ double kw_p64(double H, int df) {
   if (df == 2) return exp(-0.5 * H);
   return 1.0;
 }
+// The reported p of a hit (df 1, 2; the decisions use kw_p64): exp(-x), x = H/2, as
+// 2^-k 2^-f with k = floor(x log2 e) and f the fraction, both from FP64, and 2^-f
+// from exp2f; for df = 1, erfc(z) = exp(-z^2) erfcx(z), z = sqrt(x), with erfcx in
+// FP32 (smooth, so its argument's rounding barely moves it).  Relative error a few
+// 1e-7; no FP64 transcendental.
+__device__ __forceinline__ double kw_p_report(double H, int df) {
+  const double x = 0.5 * H;
+  if (!(x > 0.0)) return 1.0;
+  const double t = x * 1.4426950408889634074;  // x log2(e)
+  const double k = floor(t);
+  if (k > 1000.0) return 0.0;
+  const double two_mk = __longlong_as_double((long long)(1023 - (int)k) << 52);  // 2^-k
+  double e = (double)exp2f(-(float)(t - k)) * two_mk;
+  if (df == 1) e *= (double)erfcxf(sqrtf((float)x));
+  return e;
+}
 __device__ __forceinline__ double kw_H64(int u, int v, int n0, int n1, int n2, double cfac) {
   const double D0 = (double)u, D1 = (double)v, D2 = -(double)(u + v);
   double Q = 0.0;
@@ -2593,7 +2609,7 @@ __global__ void seg_compact_kernel(const krux_hit *__restrict__ seg_hits,
 
 // 1/n in FP64 for n = 0..kMaxN (entry 0 unused): the finalisation multiplies
 // instead of dividing (FP64 division is slow on this part).
-__constant__ double c_rcp[kMaxN + 1];
+__device__ double c_rcp[kMaxN + 1];  // (global, read through L1: the indices differ by lane)
 
 // FP64 statistic and p-value of each stored hit, from its exact centred sums.
 __device__ __forceinline__ void finalize_one(const krux_hit *__restrict__ hits,
@@ -2602,7 +2618,7 @@ __device__ __forceinline__ void finalize_one(const krux_hit *__restrict__ hits,
                                              const double *const *__restrict__ cfac_by_group,
                                              double *__restrict__ H, double *__restrict__ P,
                                              unsigned long long *fdr_hist, int fdr_bins,
-                                             double fdr_l0, double fdr_w) {
+                                             double fdr_l0, double fdr_w, double pthresh) {
   const krux_hit r = ld_hit(hits + i);
   const HitAux a = ld_aux(aux + i);
   const double cf = cfac_by_group[a.group][r.trait];
@@ -2611,9 +2627,9 @@ __device__ __forceinline__ void finalize_one(const krux_hit *__restrict__ hits,
   if (aux2 == nullptr) {
     df = df_of(a.n0, a.n1, a.n2);
     const double D0 = (double)r.d0, D1 = (double)r.d1, D2 = -(double)(r.d0 + r.d1);
-    Q = D0 * D0 * c_rcp[a.n0];
-    Q = fma(D1 * D1, c_rcp[a.n1], Q);
-    Q = fma(D2 * D2, c_rcp[a.n2], Q);
+    Q = D0 * D0 * __ldg(&c_rcp[a.n0]);
+    Q = fma(D1 * D1, __ldg(&c_rcp[a.n1]), Q);
+    Q = fma(D2 * D2, __ldg(&c_rcp[a.n2]), Q);
   } else {  // five groups: D_4 = -(D_0 + D_1 + D_2 + D_3)
     const HitAux2 b = aux2[i];
     const int n[5] = {a.n0, a.n1, a.n2, b.n3, b.n4};
@@ -2623,13 +2639,20 @@ __device__ __forceinline__ void finalize_one(const krux_hit *__restrict__ hits,
     Q = 0.0;
     for (int k = 0; k < 5; ++k) {
       groups += n[k] > 0;
-      Q = fma(D[k] * D[k], c_rcp[n[k]], Q);
+      Q = fma(D[k] * D[k], __ldg(&c_rcp[n[k]]), Q);
     }
     df = groups > 0 ? groups - 1 : 0;
   }
   const double h = cf * Q;
   H[i] = h;
-  P[i] = aux2 == nullptr ? kw_p64(h, df) : chi2_tail64(h, df);
+  double pv;
+  if (df < 1 || df > 2) {  // markers with more groups: df 3, 4
+    pv = chi2_tail64(h, df);
+  } else {
+    pv = kw_p_report(h, df);
+    if (pv >= pthresh) pv = kw_p64(h, df);  // a hit's p stays below P_c as decided
+  }
+  P[i] = pv;
   if (fdr_hist != nullptr)  // row 0: the real data's hits by -log10 p bin
     atomicAdd(fdr_hist + fdr_bin(key64_of(h, df), fdr_l0, fdr_w, fdr_bins), 1ull);
 }
@@ -2638,10 +2661,11 @@ __global__ void finalize_kernel(const krux_hit *__restrict__ hits, const HitAux 
                                 int64_t n, const double *const *__restrict__ cfac_by_group,
                                 double *__restrict__ H, double *__restrict__ P,
                                 unsigned long long *fdr_hist, int fdr_bins, double fdr_l0,
-                                double fdr_w) {
+                                double fdr_w, double pthresh) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
-    finalize_one(hits, aux, nullptr, i, cfac_by_group, H, P, fdr_hist, fdr_bins, fdr_l0, fdr_w);
+    finalize_one(hits, aux, nullptr, i, cfac_by_group, H, P, fdr_hist, fdr_bins, fdr_l0, fdr_w,
+                 pthresh);
 }
 
 // The same over min(*count, capacity) hits, the count read on the device (no host
@@ -2653,12 +2677,12 @@ __global__ void finalize_dev_kernel(const krux_hit *__restrict__ hits,
                                     const double *const *__restrict__ cfac_by_group,
                                     double *__restrict__ H, double *__restrict__ P,
                                     unsigned long long *fdr_hist, int fdr_bins, double fdr_l0,
-                                    double fdr_w) {
+                                    double fdr_w, double pthresh) {
   const unsigned long long c = *count;
   const int64_t n = c < (unsigned long long)capacity ? (int64_t)c : capacity;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
-    finalize_one(hits, aux, aux2, i, cfac_by_group, H, P, fdr_hist, fdr_bins, fdr_l0, fdr_w);
+    finalize_one(hits, aux, aux2, i, cfac_by_group, H, P, fdr_hist, fdr_bins, fdr_l0, fdr_w, pthresh);
 }
 
 // The deferred FP64 pass of a plain-form permutation launch: every listed pair's
@@ -2937,14 +2961,14 @@ cudaError_t finalize_prepare() {
 cudaError_t launch_finalize(const krux_hit *hits, const HitAux *aux, int64_t n,
                             const double *const *cfac_by_group, double *H, double *p,
                             cudaStream_t s, unsigned long long *fdr_hist, int fdr_bins,
-                            double fdr_l0, double fdr_w) {
+                            double fdr_l0, double fdr_w, double pthresh) {
   if (n <= 0) return cudaSuccess;
   cudaError_t e = finalize_prepare();
   if (e != cudaSuccess) return e;
   int grid = (int)((n + 255) / 256);
   if (grid > 152 * 8) grid = 152 * 8;
   finalize_kernel<<<grid, 256, 0, s>>>(hits, aux, n, cfac_by_group, H, p, fdr_hist, fdr_bins, fdr_l0,
-                                       fdr_w);
+                                       fdr_w, pthresh);
   return cudaGetLastError();
 }
 
@@ -2952,13 +2976,13 @@ cudaError_t launch_finalize_dev(const krux_hit *hits, const HitAux *aux, const H
                                 const unsigned long long *count, int64_t capacity,
                                 const double *const *cfac_by_group, double *H, double *p,
                                 int sm_count, cudaStream_t s, unsigned long long *fdr_hist,
-                                int fdr_bins, double fdr_l0, double fdr_w) {
+                                int fdr_bins, double fdr_l0, double fdr_w, double pthresh) {
   if (capacity <= 0) return cudaSuccess;
   int grid = sm_count * 4;
   const int64_t need = (capacity + 255) / 256;
   if (need < grid) grid = (int)need;
   finalize_dev_kernel<<<grid, 256, 0, s>>>(hits, aux, aux2, count, capacity, cfac_by_group, H, p,
-                                           fdr_hist, fdr_bins, fdr_l0, fdr_w);
+                                           fdr_hist, fdr_bins, fdr_l0, fdr_w, pthresh);
   return cudaGetLastError();
 }
 
