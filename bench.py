@@ -55,11 +55,11 @@ WORKLOAD = ("paper-scale fused scan: N=102 samples, T=20000 traits, S=500000 SNP
 #            -k regex:krux_scan_kernel -s 1 -c 1 python bench.py --scan-only --traits 20000
 #            --snps 100000 --data paper --tile 1,4,2,0 --reps 2
 #            (warp instructions x 32 lanes / pairs = lane issue slots per pair)
-# Measured on the kernel below: 241.38 MB read + 73.69 MB written per 500k-SNP launch;
-# 676.62 M warp instructions (567.50 M on the FMA-heavy, FMA-lite and ALU pipes) per
+# Measured on the kernel below: 241.71 MB read + 74.28 MB written per 500k-SNP launch;
+# 676.60 M warp instructions (567.48 M on the FMA-heavy, FMA-lite and ALU pipes) per
 # 100k-SNP launch of 2x10^9 pairs.
-SCAN_TRAFFIC = {"blob": "af2409f11175fe872d00a81edc9cf69cc4319dbf", "bytes": 315.07e6}
-SCAN_ISSUE = {"blob": "af2409f11175fe872d00a81edc9cf69cc4319dbf", "slots_per_pair": 10.83,
+SCAN_TRAFFIC = {"blob": "bcf763037070c5d9692f0da6d0549752132f2260", "bytes": 315.98e6}
+SCAN_ISSUE = {"blob": "bcf763037070c5d9692f0da6d0549752132f2260", "slots_per_pair": 10.83,
               "fp32_int_slots_per_pair": 9.08,
               "workload": "planted 20000 x 100000 x 102 (0.19% of pairs are hits)"}
 # Epilogue issue slots per pair by the operation count of the fused test: one add
