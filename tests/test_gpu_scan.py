@@ -239,6 +239,28 @@ def test_nan_plain_form_variant(kx, oracle_mod, with_missing_geno):
     ctx.close()
 
 
+@pytest.mark.parametrize("N", [60, 150, 250])
+def test_nan_expression_other_widths(kx, oracle_mod, N):
+    """NaN expression at other sample counts: the NaN variant of the plain form where
+    its coefficient sets fit shared memory beside the wider operands, the general
+    form where they do not (the plan is made again); the hit set is the oracle's
+    either way."""
+    d = synth.config(2, T=260, S=1400, N=N, seed=40 + N)
+    x = d["expr"].copy()
+    rng = np.random.default_rng(N)
+    x[rng.random(x.shape) < 0.015] = np.nan
+    pth = 2e-3
+    orc = oracle_mod.scan(x, d["geno"], pth)
+    import paper_1307_3519_gb300 as k
+    ctx = k.Krux(0)
+    ctx.set_profiling(True)
+    rs = ctx.krux_rank(_dev(x))
+    res = ctx.krux_scan(rs, _dev(d["geno"]), pth, capacity=260 * 1400)
+    assert ctx.profile()["scan_form"] in (3, 5)
+    check_hits(res, orc, np.arange(260), np.arange(1400), pth)
+    ctx.close()
+
+
 def test_missing_genotypes(kx, oracle_mod):
     """Missing-value workload at reduced size: -1 genotypes in missing-sample
     patterns and NaN expression; ranks over the samples present in both."""
