@@ -124,7 +124,11 @@ krux_status krux_rankset_export(krux_ctx *ctx, const krux_rankset *rs, int16_t *
  *          code -> KRUX_EINVAL.  Same sample order and N as the rank set.
  *   hits, hit_H, hit_p : device outputs of opts->hit_capacity entries, in
  *          unspecified order; hits must be 16-byte aligned (else KRUX_EINVAL).
- *          SNP indices are rows of geno (slice offsets included).
+ *          SNP indices are rows of geno (slice offsets included).  Which pairs
+ *          are hits is decided with the FP64 chi-square tail (p < pthresh); H is
+ *          computed in FP64 from the exact rank sums; the reported p of df 1 and 2
+ *          comes from an FP64 range reduction with FP32 exp2 / erfcx parts
+ *          (relative error a few 1e-7, always below pthresh for a hit).
  *   n_hits : host; receives the exact number of hits, also when it exceeds the
  *          capacity (then the first hit_capacity found are stored and the call
  *          returns KRUX_EOVERFLOW).
