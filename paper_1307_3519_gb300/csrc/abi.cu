@@ -1755,14 +1755,14 @@ bool make_seed_plan(const CallPlan &cp, CallPlan &seed, bool plain_form) {
   if (cp.groups.size() != 1) return false;
   const int64_t n = cp.groups[0].n_snps;
   // the plain form decides every pair past its bounds exactly, so its seed covers a
-  // quarter of the SNPs (whole chunks): about three later pairs per class then
-  // beat the seed's best instead of eleven.  It needs one at any size: from zero
-  // bounds nearly every pair of its first chunks would go to the event warps (a
-  // 20,000-SNP batch took 83 ms without one)
+  // third of the SNPs (whole chunks; a quarter took 4 % longer over 200,000 SNPs at
+  // P = 16, a sixth 7 %): few later pairs per class then beat the seed's best.  It
+  // needs one at any size: from zero bounds nearly every pair of its first chunks
+  // would go to the event warps (a 20,000-SNP batch took 83 ms without one)
   if (plain_form ? n < 16 * kChunkSnps : n <= 4 * kSeedSnps) return false;
   seed = cp;
   seed.groups[0].n_snps =
-      plain_form ? std::max<int64_t>(4 * kChunkSnps, n / 4 / kChunkSnps * kChunkSnps) : kSeedSnps;
+      plain_form ? std::max<int64_t>(4 * kChunkSnps, n / 3 / kChunkSnps * kChunkSnps) : kSeedSnps;
   seed.slots[0].capacity = 0;
   seed.fdr_hist = nullptr;
   seed.perm.seed = true;
