@@ -363,9 +363,12 @@ void krux_graph_destroy(krux_graph *g);
 
 /* Test hook (no GPU needed): the pipeline shape a scan of one group of N samples
  * would use, after the same shared-memory plan check every launch passes.
- * out[7] = {samples per rank stage, rank stages, B region bytes, resident
- * chunks, K blocks per step, B chunk stride, shared-memory bytes}.  Returns
- * KRUX_OK, or KRUX_EUNSUPPORTED if no sound plan exists. */
+ * with_nan: 0 complete data, 1 NaN expression in the general form (2-bit codes),
+ * 2 the plain form on complete data (with its hit-event ring), 3 the plain form's
+ * NaN variant (coefficient sets).  out[7] = {samples per rank stage, rank stages,
+ * B region bytes, resident chunks, K blocks per step, B chunk stride,
+ * shared-memory bytes}.  Returns KRUX_OK, KRUX_EUNSUPPORTED if no sound plan of
+ * that kind exists, KRUX_EINVAL for arguments out of range. */
 krux_status krux_debug_plan(int N, int with_nan, int layout, int nc, int nA, int ka, int32_t *out);
 
 /* Test hook: device-side waits give up after `cycles` SM clock cycles (0 = the

@@ -2757,16 +2757,24 @@ extern "C" krux_status krux_debug_plan(int N, int with_nan, int layout, int nc, 
   const int atom = layout_atom(lay);
   const int Np = round_up(N, 16);
   const int kpad = round_up(Np, atom);
-  const int codes_k = with_nan ? Np : 0;
+  // with_nan: 0 complete data, 1 the general form's 2-bit codes, 2 the plain form
+  // (complete data, room for its hit-event ring), 3 the plain form's NaN variant
+  // (its coefficient sets in place of the codes)
+  if (with_nan < 0 || with_nan > 3) return KRUX_EINVAL;
+  const bool plain = with_nan >= 2;
+  if (plain && lay != 1) return KRUX_EUNSUPPORTED;
+  const int codes_k = with_nan == 1 ? Np : (with_nan == 3 ? kCoefNanRows : 0);
   LaunchShape sh;
-  if (!pick_launch_shape(&tmp, kpad, codes_k, sh)) return KRUX_EUNSUPPORTED;
+  if (!pick_launch_shape(&tmp, kpad, codes_k, sh, plain ? kEvRegion : 0)) return KRUX_EUNSUPPORTED;
   GroupDesc d;
   std::memset(&d, 0, sizeof d);
   d.Np = Np;
   d.n_atoms = (Np + atom - 1) / atom;
-  d.codes = with_nan ? reinterpret_cast<const uint64_t *>(16) : nullptr;
+  d.codes = codes_k ? reinterpret_cast<const uint64_t *>(16) : nullptr;
   d.codes_k = codes_k;
   group_shape(sh, kpad, atom, d);
+  // the plain forms: the whole K per rank stage, chunk pairs
+  if (plain && (sh.ka != kpad || d.pair != 1 || d.nkb != 1)) return KRUX_EUNSUPPORTED;
   ScanParams p{};
   p.nc = d.nc;
   p.nA = sh.nA;
@@ -2775,7 +2783,8 @@ extern "C" krux_status krux_debug_plan(int N, int with_nan, int layout, int nc, 
   p.a_tile_bytes = 256 * sh.ka;
   p.b_region = sh.b_region;
   p.layout = lay;
-  const size_t smem = scan_smem_bytes2(p.nc, p.nA, (size_t)p.a_tile_bytes, (size_t)p.b_region, p.kpad);
+  const size_t smem = scan_smem_bytes2(p.nc, p.nA, (size_t)p.a_tile_bytes, (size_t)p.b_region, p.kpad) +
+                     (plain ? kEvRegion : 0);
   out[0] = sh.ka;
   out[1] = sh.nA;
   out[2] = sh.b_region;

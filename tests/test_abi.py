@@ -88,6 +88,29 @@ def test_every_launch_plan_is_sound(lib):
             assert st in (0, 6)  # sound, or refused (never an unchecked plan)
 
 
+def test_plain_form_plans(lib):
+    """The plain form's launch plans (the whole K in one rank stage, an even number
+    of resident chunks as N = 256 MMA pairs, room for the hit-event ring) and those
+    of its NaN variant (the coefficient sets in place of the codes): sound wherever
+    they exist, the NaN variant only where the plain form is, and both with four
+    resident chunks at the benchmark's N = 102."""
+    import paper_1307_3519_gb300 as k
+    for N in range(1, 513):
+        st2, p2 = k.krux_debug_plan(N, 2)
+        st3, p3 = k.krux_debug_plan(N, 3)
+        assert st2 in (0, 6) and st3 in (0, 6), (N, st2, st3)
+        assert st3 != 0 or st2 == 0, N
+        for st, pl in ((st2, p2), (st3, p3)):
+            if st == 0:
+                assert pl["smem"] <= 232448 and pl["nkb"] == 1, (N, pl)
+                assert pl["nc"] >= 2 and pl["nc"] % 2 == 0, (N, pl)
+    for mode in (2, 3):
+        st, pl = k.krux_debug_plan(102, mode)
+        assert st == 0 and pl["nc"] == 4 and pl["nA"] == 2, (mode, pl)
+    assert k.krux_debug_plan(102, 2, layout=0)[0] == 6  # the plain forms need the 32-byte swizzle
+    assert k.krux_debug_plan(102, 4)[0] == 1
+
+
 def test_every_autotune_candidate_is_sound_or_refused(lib):
     """The shapes krux_autotune tries: each one either passes the plan check or
     is refused before any launch."""
