@@ -180,7 +180,7 @@ double h_dfk(double p, int df) {
 struct krux_rankset {
   int T = 0, N = 0, Np = 0, rows_pad = 0, n_ttiles = 0;
   bool has_nan = false;  // decided on the host after ranking
-  int nan_tiles_over = 0;  // trait tiles with a trait of more than kNanCMax NaN samples
+  int nan_traits_over = 0;  // traits with more than kNanCMax NaN samples
   RankDev dev{};
   void *mem = nullptr;
   size_t bytes = 0;
@@ -641,8 +641,8 @@ krux_status krux_rank(krux_ctx *ctx, const float *expr, int T, int N, int64_t ld
     e = cudaMemcpyAsync(tn.data(), rs->dev.tile_nan, tn.size() * 4, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     for (uint32_t v : tn) {
-      any_nan |= v;
-      rs->nan_tiles_over += v > (uint32_t)kNanCMax ? 1 : 0;
+      any_nan |= v & 0xffffu;
+      rs->nan_traits_over += (int)(v >> 16);
     }
   }
   if (e != cudaSuccess) {
@@ -1123,7 +1123,7 @@ krux_status materialise(krux_ctx *ctx, CallPlan &cp, cudaStream_t s) {
     bs.rows_pad = rs->rows_pad;
     bs.n_ttiles = rs->n_ttiles;
     bs.has_nan = rs->has_nan;
-    bs.nan_tiles_over = rs->nan_tiles_over;
+    bs.nan_traits_over = rs->nan_traits_over;
     char *p = base + off[i];
     size_t o2 = 0;
     auto take = [&](size_t bytes) {
@@ -1284,13 +1284,15 @@ krux_status prepare_fused(krux_ctx *ctx, CallPlan &cp, const krux_opts *o, Fused
   const int atom = layout_atom(layout);
   // a call that can take the plain form keeps room for its hit-event ring; with
   // NaN expression it takes the form's NaN variant (per-chunk coefficient sets in
-  // place of the 2-bit codes) when few trait tiles hold traits beyond the last set
+  // place of the 2-bit codes) when at most one trait in 128 has more NaN samples
+  // than the last set covers (each such trait sends all its pairs to the exact
+  // test; beyond that share the general form is faster)
   bool fast_shape = layout == 1 && !cp.multi && cp.param.model < 0 && o->dense_H == nullptr &&
                     !cp.cis.on;
   bool any_nan = false, fast_nan = allow_fast_nan && fast_shape;
   for (auto &g : cp.groups) {
     fast_nan = fast_nan && g.minp_key == nullptr &&
-               (g.nan_cnt == nullptr || 8 * g.rs->nan_tiles_over <= g.rs->n_ttiles);
+               (g.nan_cnt == nullptr || 128 * g.rs->nan_traits_over <= g.rs->T);
     any_nan = any_nan || g.nan_cnt != nullptr;
   }
   fast_nan = fast_nan && any_nan;

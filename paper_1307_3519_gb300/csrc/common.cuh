@@ -178,7 +178,8 @@ struct RankDev {
   double *cfac;         // [rows_pad] 3 / (K(K+1)C), 0 when degenerate or padding
   uint16_t *nan_cnt;    // [rows_pad] NaN samples of the trait (0 for padding)
   uint16_t *nan_idx;    // [T][N] their sample indices (first nan_cnt entries)
-  uint32_t *tile_nan;   // [rows_pad/128] the largest NaN count of the tile's traits
+  uint32_t *tile_nan;   // [rows_pad/128] the tile's traits with NaN (low 16 bits) and
+                        // with more than kNanCMax NaN samples (high 16 bits)
 };
 
 // One missing-pattern bucket of a scan call: the base rank set's ranks re-derived
@@ -345,8 +346,7 @@ struct ScanParams {
   // the plain scan form applies: 32-byte swizzle, every group's chunks paired, no
   // dense output, no cis window, no provisional hits (permutation batches take its
   // two-sided variant; NaN in the expression its variant with coefficient sets,
-  // fast_nan = 1, when few trait tiles hold a trait with more than kNanCMax NaN
-  // samples)
+  // fast_nan = 1, when at most one trait in 128 has more than kNanCMax NaN samples)
   int32_t fast = 0;
   int32_t fast_nan = 0;
 };

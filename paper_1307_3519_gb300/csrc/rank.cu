@@ -89,7 +89,8 @@ rank_kernel(const float *__restrict__ expr, int T, int N, int64_t ld, int Np, Ra
     r.tie[t] = tie;
     r.K[t] = K;
     r.nan_cnt[t] = (uint16_t)(N - K);
-    if (N - K > 0) atomicMax(&r.tile_nan[t / kTileM], (uint32_t)(N - K));
+    // the tile's traits with NaN (low 16 bits) and with more than kNanCMax (high)
+    if (N - K > 0) atomicAdd(&r.tile_nan[t / kTileM], 1u + (N - K > kNanCMax ? 1u << 16 : 0u));
   }
 }
 

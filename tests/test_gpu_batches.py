@@ -189,9 +189,9 @@ def test_permutation_fdr_histogram(kx, oracle_mod, T, S, P, N, nan):
 def test_plain_forms_are_the_default(kx):
     """Without any tuning, complete data take the plain scan form (0) and a
     permutation batch its two-sided variant (4); NaN expression takes the plain
-    form's NaN variant (5), unless more than one trait tile in eight holds a trait
-    with more than six NaN samples (the general form, 3); a permutation batch with
-    NaN takes the permutation form (2)."""
+    form's NaN variant (5), unless more than one trait in 128 has more than six NaN
+    samples (the general form, 3); a permutation batch with NaN takes the
+    permutation form (2)."""
     import paper_1307_3519_gb300 as k
     ctx = k.Krux(0)
     ctx.set_profiling(True)
@@ -208,7 +208,7 @@ def test_plain_forms_are_the_default(kx):
     assert ctx.profile()["scan_form"] == 5
     ctx.krux_permute(rsn, g, pm, 1e-4, capacity=300 * 5000)
     assert ctx.profile()["scan_form"] == 2
-    x[200, :7] = np.nan  # 1 of 3 trait tiles has a trait with 7 NaN samples
+    x[200:203, :7] = np.nan  # 3 of 300 traits with 7 NaN samples
     rsm = ctx.krux_rank(_dev(x))
     ctx.krux_scan(rsm, g, 1e-4, capacity=300 * 5000)
     assert ctx.profile()["scan_form"] == 3

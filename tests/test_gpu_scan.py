@@ -213,11 +213,11 @@ def test_nan_counts_per_trait(kx, oracle_mod, with_missing_geno):
 @pytest.mark.parametrize("with_missing_geno", [False, True])
 def test_nan_plain_form_variant(kx, oracle_mod, with_missing_geno):
     """The plain form's NaN variant: traits with 0..6 NaN samples (trait t has t
-    mod 7) take the coefficient set of their count, and a few traits of the first
-    tile have more (9, 30, and 101 of 102: degenerate), so that every pair of
-    theirs reaches the exact test with its exact group sizes.  Nine trait tiles
-    (the last ragged), one of them with traits beyond the sets: the call takes form
-    5, and its hit set must be the oracle's."""
+    mod 7) take the coefficient set of their count, and three traits have more (9,
+    30, and 101 of 102: degenerate), so that every pair of theirs reaches the exact
+    test with its exact group sizes.  Nine trait tiles (the last ragged); three
+    traits in 1030 beyond the sets: the call takes form 5, and its hit set must be
+    the oracle's."""
     d = synth.config(2, T=1030, S=2100, seed=35)
     x = d["expr"].copy()
     g = d["geno"].copy()
